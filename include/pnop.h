@@ -1,0 +1,180 @@
+/*
+ * pnop — forward and adjoint time steps of the perturbation Navier–Stokes
+ * equations in a periodic pipe around a Sexl–Womersley base flow, and the
+ * checkpointed adjoint sweep that returns the gradient of the final
+ * perturbation energy with respect to the initial perturbation
+ * (Keuchel & Avila, "Nonlinear optimal perturbation growth in pulsatile pipe
+ * flow": Section 2, Eq. 2.1–2.12 for the equations, Section 2.4 for the
+ * discretisation and the predictor–corrector step, Section 2.5 and
+ * Eq. 2.18–2.20 for the binomial checkpointing).
+ *
+ * C ABI, one CUDA device, plain pointers.  Every entry point returns an int
+ * status (PNOP_OK = 0, negative on error) unless stated otherwise; no
+ * exception crosses the ABI.  The text of the last error of a context is
+ * returned by pnop_last_error().
+ *
+ * Field layout (all field pointers): complex128, interleaved (re, im),
+ * C order [3][nr][2M+1][K+1]:
+ *   component c = 0,1,2  ->  u_r, u_theta, u_z
+ *   radial index j       ->  r_j, j = 0 is the wall r = 1, r decreasing
+ *   azimuthal index      ->  m = -M .. M
+ *   axial index          ->  k = 0 .. K, wavenumber kz = 2 pi k / Lz
+ * f(r,theta,z) = sum_{k=-K..K} sum_{m=-M..M} fhat_{m,k}(r) e^{i(m theta + kz z)}
+ * with fhat_{-m,-k} = conj(fhat_{m,k}) (Eq. 2.16); only k >= 0 is stored, so
+ * the k = 0 plane must satisfy fhat_{-m,0} = conj(fhat_{m,0}).
+ *
+ * Ownership: callers own every field buffer they pass; the library never
+ * frees them and keeps no pointer to them after a call returns.  The context
+ * owns its operators, workspace and checkpoint pool (device memory).
+ *
+ * Streams: all device work of a context is ordered on the stream given to
+ * pnop_create (NULL = legacy default stream).  Calls that return host scalars
+ * (energy, inner, gradient) synchronise that stream.  A context must not be
+ * used from two host threads at once.
+ */
+#ifndef PNOP_H
+#define PNOP_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    PNOP_OK = 0,
+    PNOP_ERR_INVALID_ARG = -1,  /* bad size, NULL pointer, unsupported combination */
+    PNOP_ERR_OOM = -2,          /* device allocation failed or HBM budget exceeded */
+    PNOP_ERR_CUDA = -3,         /* a CUDA runtime call or kernel launch failed */
+    PNOP_ERR_NONFINITE = -4,    /* a NaN/Inf energy was produced */
+    PNOP_ERR_TIMEOUT = -5,      /* device work did not complete within the host limit */
+    PNOP_ERR_UNSUPPORTED = -6   /* grid/solver combination not supported */
+};
+
+enum { PNOP_FP64 = 0, PNOP_MIXED = 1 };
+
+/* Grid.  nr radial points (>= 9); ntheta, nz nominal azimuthal/axial sizes,
+ * giving |m| <= M = ntheta/2 - 1 and 0 <= k <= K = nz/2 - 1; the physical
+ * (3/2-dealiased) grid is 3(M+1) x 3(K+1) and both must factor into 2s and
+ * 3s.  Lz is the pipe length in radii; stretch in [0,1) blends the Chebyshev
+ * radial points with uniform spacing (Section 2.4, "relaxation"; 0 = pure
+ * Chebyshev). */
+typedef struct {
+    int nr, ntheta, nz;
+    double Lz, stretch;
+} pnop_grid;
+
+/* Physics and run parameters.  Re = D Ubar / nu (mean), Wo and A as in
+ * Section 1 (Eq. 2.4); time unit R/(2 Ubar), so the pulsation period is
+ * 2 pi Re / Wo^2.  dt is the fixed time step, tau0 the start time of the
+ * perturbation.  precision: PNOP_FP64, or PNOP_MIXED (FP32 transforms and
+ * products, FP64 everything else).  snap_budget: checkpoint slots for
+ * pnop_gradient including the initial state (>= 1; Section 2.5).
+ * hbm_budget: bytes the context may allocate (0 = no limit). */
+typedef struct {
+    double Re, Wo, A, dt, tau0;
+    int precision;
+    int snap_budget;
+    size_t hbm_budget;
+} pnop_params;
+
+typedef struct pnop_ctx pnop_ctx;
+
+/* Build the grid, the finite-difference and banded-LU operators, the
+ * influence and flux vectors (Section 2.4) and the workspace on the current
+ * device.  cuda_stream is a cudaStream_t (may be NULL).  On success *out
+ * receives a new context; on failure *out is NULL and the status says why
+ * (use pnop_error_string for the text). */
+int pnop_create(const pnop_grid* grid, const pnop_params* params, void* cuda_stream, pnop_ctx** out);
+
+/* Replace Re, Wo, A and tau0 (Eq. 2.3–2.4).  Rebuilds the Re-dependent
+ * operators when Re changes. */
+int pnop_set_base_flow(pnop_ctx* ctx, double Re, double Wo, double A, double tau0);
+
+/* Sizes of a context: nr, M, K; any pointer may be NULL. */
+int pnop_dims(const pnop_ctx* ctx, int* nr, int* M, int* K);
+
+/* Radial points r_j (host array of nr doubles, j = 0 at the wall). */
+int pnop_grid_points(const pnop_ctx* ctx, double* r_out);
+
+/* Advance the device field u (in/out, layout above) by nsteps predictor-
+ * corrector steps (Section 2.4) starting at time t. */
+int pnop_step_forward(pnop_ctx* ctx, void* u, double t, int nsteps);
+
+/* One adjoint step: lam (device, in/out) <- J^+ lam, where J is the
+ * Jacobian of the forward step taken from the device state u_n at time t_n,
+ * and J^+ its adjoint in the energy inner product of Eq. 2.2 (so that
+ * <J v, lam> = <v, J^+ lam> for all v).  This is the exact transpose of the
+ * discrete step, the discrete counterpart of Eq. 2.9–2.11. */
+int pnop_step_adjoint(pnop_ctx* ctx, const void* u_n, void* lam, double t_n);
+
+/* Gradient of E(tau0 + horizon) with respect to the initial perturbation
+ * (Eq. 2.8 and 2.12 without the energy multiplier; the paper's u_dagger at
+ * tau0 is the negative of grad_out).  u0 (device, read only) is first scaled
+ * to energy E0 when E0 > 0, else used as given.  The forward sweep stores
+ * snap_budget checkpoints on the binomial schedule of Eq. 2.18–2.20 and the
+ * backward sweep recomputes the missing states.  grad_out (device) receives
+ * the Riesz representer of dE(T)/du0 in the energy inner product; gain_out
+ * (host, may be NULL) receives G = E(T)/E(tau0) (Eq. 2.1).  horizon must be
+ * a whole number of time steps (to 1e-9 relative). */
+int pnop_gradient(pnop_ctx* ctx, const void* u0, double E0, double horizon, void* grad_out, double* gain_out);
+
+/* Same as pnop_gradient with host buffers: u0_host and grad_host are host
+ * arrays in the field layout; the copies are part of the call. */
+int pnop_gradient_host(pnop_ctx* ctx, const double* u0_host, double E0, double horizon, double* grad_host,
+                       double* gain_out);
+
+/* Counts of the last pnop_gradient: forward steps executed outside the
+ * adjoint steps (recomputation included), adjoint steps, checkpoint stores.
+ * Any pointer may be NULL. */
+int pnop_gradient_stats(const pnop_ctx* ctx, long long* advances, long long* adjoint_steps, long long* stores);
+
+/* Operators of the step, applied to device fields (for testing and for
+ * users who compose their own schemes; layout as above, all FP64 in/out):
+ *   PNOP_OP_CURL       out = curl a                              (Eq. 2.5)
+ *   PNOP_OP_NONLINEAR  out = N(a, t) = a x w + (U e_z) x w + a x (-U' e_theta),
+ *                      w = curl a, products on the 3/2-padded grid
+ *   PNOP_OP_STAGE      out = S(a, b): one predictor-corrector stage with
+ *                      velocity a and forcing b (pressure projection, Crank-
+ *                      Nicolson Helmholtz solves, influence and flux
+ *                      corrections; Section 2.4)
+ *   PNOP_OP_NONLINEAR_T out = (dN/da at a, t)^T b
+ *   PNOP_OP_STAGE_T_U  out = (dS/da)^T a      (b unused)
+ *   PNOP_OP_STAGE_T_F  out = (dS/db)^T a      (b unused)
+ * Transposes act on Euclidean cotangents of the stored real and imaginary
+ * parts.  out must not alias a or b. */
+enum {
+    PNOP_OP_CURL = 0,
+    PNOP_OP_NONLINEAR = 1,
+    PNOP_OP_STAGE = 2,
+    PNOP_OP_NONLINEAR_T = 3,
+    PNOP_OP_STAGE_T_U = 4,
+    PNOP_OP_STAGE_T_F = 5
+};
+int pnop_apply(pnop_ctx* ctx, int op, const void* a, const void* b, void* out, double t);
+
+/* E = (1/2) <u, u> (Eq. 2.1–2.2) of a device field; written to *E_out. */
+int pnop_energy(pnop_ctx* ctx, const void* u, double* E_out);
+
+/* <a, b> = int int int a . b r dr dtheta dz (Eq. 2.2) of two device fields. */
+int pnop_inner(pnop_ctx* ctx, const void* a, const void* b, double* out);
+
+/* Binomial checkpoint plan (Section 2.5) for nsteps steps and snaps slots,
+ * computed on the host: minimal forward recomputations (Eq. 2.18), stores.
+ * Needs no device. */
+int pnop_revolve_counts(int nsteps, int snaps, long long* advances, long long* stores);
+
+/* Error text of the last failing call on ctx ("" when none). */
+const char* pnop_last_error(const pnop_ctx* ctx);
+
+/* Static text for a status code. */
+const char* pnop_error_string(int status);
+
+/* Free the context and everything it owns.  NULL is allowed. */
+void pnop_destroy(pnop_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PNOP_H */

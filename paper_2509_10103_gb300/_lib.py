@@ -1,0 +1,173 @@
+"""ctypes binding of libpnop (argument marshalling only).
+
+The names mirror the C ABI in include/pnop.h.  Field arguments may be torch
+tensors (complex128, contiguous, shape [3, nr, 2M+1, K+1], on the context's
+device) or raw integer device pointers.  There is no fallback: if the shared
+library is missing the import fails.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from ctypes import POINTER, byref, c_char_p, c_double, c_int, c_longlong, c_size_t, c_void_p
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libpnop.so")
+
+PNOP_OK = 0
+PNOP_FP64 = 0
+PNOP_MIXED = 1
+OP_CURL, OP_NONLINEAR, OP_STAGE, OP_NONLINEAR_T, OP_STAGE_T_U, OP_STAGE_T_F = range(6)
+
+EXPORTS = (
+    "pnop_create", "pnop_set_base_flow", "pnop_dims", "pnop_grid_points", "pnop_step_forward",
+    "pnop_step_adjoint", "pnop_gradient", "pnop_gradient_host", "pnop_gradient_stats", "pnop_energy",
+    "pnop_inner", "pnop_apply", "pnop_revolve_counts", "pnop_last_error", "pnop_error_string", "pnop_destroy",
+)
+
+
+class pnop_grid(ctypes.Structure):
+    _fields_ = [("nr", c_int), ("ntheta", c_int), ("nz", c_int), ("Lz", c_double), ("stretch", c_double)]
+
+
+class pnop_params(ctypes.Structure):
+    _fields_ = [("Re", c_double), ("Wo", c_double), ("A", c_double), ("dt", c_double), ("tau0", c_double),
+                ("precision", c_int), ("snap_budget", c_int), ("hbm_budget", c_size_t)]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libpnop.so is not built ({LIB_PATH}); run paper_2509_10103_gb300/build.py")
+    lib = ctypes.CDLL(LIB_PATH)
+    sig = {
+        "pnop_create": (c_int, [POINTER(pnop_grid), POINTER(pnop_params), c_void_p, POINTER(c_void_p)]),
+        "pnop_set_base_flow": (c_int, [c_void_p, c_double, c_double, c_double, c_double]),
+        "pnop_dims": (c_int, [c_void_p, POINTER(c_int), POINTER(c_int), POINTER(c_int)]),
+        "pnop_grid_points": (c_int, [c_void_p, POINTER(c_double)]),
+        "pnop_step_forward": (c_int, [c_void_p, c_void_p, c_double, c_int]),
+        "pnop_step_adjoint": (c_int, [c_void_p, c_void_p, c_void_p, c_double]),
+        "pnop_gradient": (c_int, [c_void_p, c_void_p, c_double, c_double, c_void_p, POINTER(c_double)]),
+        "pnop_gradient_host": (c_int, [c_void_p, c_void_p, c_double, c_double, c_void_p, POINTER(c_double)]),
+        "pnop_gradient_stats": (c_int, [c_void_p, POINTER(c_longlong), POINTER(c_longlong), POINTER(c_longlong)]),
+        "pnop_energy": (c_int, [c_void_p, c_void_p, POINTER(c_double)]),
+        "pnop_inner": (c_int, [c_void_p, c_void_p, c_void_p, POINTER(c_double)]),
+        "pnop_apply": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_void_p, c_double]),
+        "pnop_revolve_counts": (c_int, [c_int, c_int, POINTER(c_longlong), POINTER(c_longlong)]),
+        "pnop_last_error": (c_char_p, [c_void_p]),
+        "pnop_error_string": (c_char_p, [c_int]),
+        "pnop_destroy": (None, [c_void_p]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+lib = _load()
+
+
+class PnopError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{lib.pnop_error_string(code).decode()} ({code}): {msg}")
+        self.code = code
+
+
+def _ptr(x) -> int:
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        if not x.is_contiguous():
+            raise ValueError("field tensors must be contiguous")
+        return x.data_ptr()
+    raise TypeError("expected a torch tensor or an integer pointer")
+
+
+def pnop_revolve_counts(nsteps: int, snaps: int):
+    a, s = c_longlong(), c_longlong()
+    rc = lib.pnop_revolve_counts(nsteps, snaps, byref(a), byref(s))
+    if rc != PNOP_OK:
+        raise PnopError(rc, "revolve_counts")
+    return a.value, s.value
+
+
+class Context:
+    """One solver context (pnop_ctx) on the current CUDA device and a stream."""
+
+    def __init__(self, nr, ntheta, nz, Lz, Re, dt, Wo=8.0, A=1.0, tau0=0.0, precision=PNOP_FP64,
+                 snap_budget=8, hbm_budget=0, stretch=0.0, stream=0):
+        g = pnop_grid(nr, ntheta, nz, Lz, stretch)
+        p = pnop_params(Re, Wo, A, dt, tau0, precision, snap_budget, hbm_budget)
+        h = c_void_p()
+        rc = lib.pnop_create(byref(g), byref(p), c_void_p(stream), byref(h))
+        if rc != PNOP_OK:
+            raise PnopError(rc, "pnop_create")
+        self._h = h
+        nr_, M, K = c_int(), c_int(), c_int()
+        lib.pnop_dims(h, byref(nr_), byref(M), byref(K))
+        self.nr, self.M, self.K = nr_.value, M.value, K.value
+        self.Lz, self.dt, self.Re = Lz, dt, Re
+        self.shape = (3, self.nr, 2 * self.M + 1, self.K + 1)
+
+    def _check(self, rc, what):
+        if rc != PNOP_OK:
+            raise PnopError(rc, f"{what}: {lib.pnop_last_error(self._h).decode()}")
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib.pnop_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        self.close()
+
+    def pnop_grid_points(self):
+        buf = (c_double * self.nr)()
+        self._check(lib.pnop_grid_points(self._h, buf), "grid_points")
+        return list(buf)
+
+    def pnop_set_base_flow(self, Re, Wo, A, tau0):
+        self._check(lib.pnop_set_base_flow(self._h, Re, Wo, A, tau0), "set_base_flow")
+        self.Re = Re
+
+    def pnop_step_forward(self, u, t, nsteps=1):
+        self._check(lib.pnop_step_forward(self._h, c_void_p(_ptr(u)), t, nsteps), "step_forward")
+
+    def pnop_step_adjoint(self, u_n, lam, t_n):
+        self._check(lib.pnop_step_adjoint(self._h, c_void_p(_ptr(u_n)), c_void_p(_ptr(lam)), t_n), "step_adjoint")
+
+    def pnop_gradient(self, u0, E0, horizon, grad_out):
+        gain = c_double()
+        self._check(lib.pnop_gradient(self._h, c_void_p(_ptr(u0)), E0, horizon, c_void_p(_ptr(grad_out)),
+                                      byref(gain)), "gradient")
+        return gain.value
+
+    def pnop_gradient_host(self, u0_host, E0, horizon, grad_host):
+        """u0_host, grad_host: host arrays (numpy complex128 or pinned torch tensors)."""
+        def hp(a):
+            if hasattr(a, "ctypes"):
+                return a.ctypes.data
+            return _ptr(a)
+        gain = c_double()
+        self._check(lib.pnop_gradient_host(self._h, c_void_p(hp(u0_host)), E0, horizon, c_void_p(hp(grad_host)),
+                                           byref(gain)), "gradient_host")
+        return gain.value
+
+    def pnop_gradient_stats(self):
+        a, b, c = c_longlong(), c_longlong(), c_longlong()
+        self._check(lib.pnop_gradient_stats(self._h, byref(a), byref(b), byref(c)), "gradient_stats")
+        return a.value, b.value, c.value
+
+    def pnop_apply(self, op, a, b, out, t=0.0):
+        bp = c_void_p(_ptr(b)) if b is not None else c_void_p(0)
+        self._check(lib.pnop_apply(self._h, op, c_void_p(_ptr(a)), bp, c_void_p(_ptr(out)), t), "apply")
+
+    def pnop_energy(self, u):
+        e = c_double()
+        self._check(lib.pnop_energy(self._h, c_void_p(_ptr(u)), byref(e)), "energy")
+        return e.value
+
+    def pnop_inner(self, a, b):
+        e = c_double()
+        self._check(lib.pnop_inner(self._h, c_void_p(_ptr(a)), c_void_p(_ptr(b)), byref(e)), "inner")
+        return e.value

@@ -1,0 +1,897 @@
+// Device kernels of the pseudo-spectral pipe-flow step (Keuchel & Avila,
+// Section 2.4) and of its exact discrete transpose (the adjoint step that
+// replaces Eq. 2.9-2.11).
+//
+// Spectral fields are FP64 complex, layout [c][j][m + M][k].  The 3/2-padded
+// theta/z transforms are hand-written shared-memory Stockham FFTs (radix 2, 3,
+// 4) templated on FP64 or FP32; everything radial (banded matvecs, banded LU
+// solves, influence and flux corrections) is FP64.
+#include "kernels.hpp"
+
+#include <cstdio>
+#include <stdexcept>
+
+namespace pnop {
+
+constexpr int kB = 13;  // stored band (columns j-4 .. j+8)
+
+// ------------------------------------------------------------------ complex helpers
+template <class T2> struct RealOf;
+template <> struct RealOf<double2> { using T = double; };
+template <> struct RealOf<float2> { using T = float; };
+
+template <class T2>
+__device__ __forceinline__ T2 mk(typename RealOf<T2>::T x, typename RealOf<T2>::T y) {
+    T2 r;
+    r.x = x;
+    r.y = y;
+    return r;
+}
+template <class T2> __device__ __forceinline__ T2 cadd(T2 a, T2 b) { return mk<T2>(a.x + b.x, a.y + b.y); }
+template <class T2> __device__ __forceinline__ T2 csub(T2 a, T2 b) { return mk<T2>(a.x - b.x, a.y - b.y); }
+template <class T2> __device__ __forceinline__ T2 cmul(T2 a, T2 b) {
+    return mk<T2>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+// s * i * z
+template <class T2> __device__ __forceinline__ T2 imul(T2 z, typename RealOf<T2>::T s) { return mk<T2>(-s * z.y, s * z.x); }
+__device__ __forceinline__ double2 dscale(double2 a, double s) { return make_double2(a.x * s, a.y * s); }
+__device__ __forceinline__ double2 dfma(double s, double2 a, double2 acc) {
+    return make_double2(fma(s, a.x, acc.x), fma(s, a.y, acc.y));
+}
+
+template <class T2> __device__ __forceinline__ T2 from_d(double2 v);
+template <> __device__ __forceinline__ double2 from_d<double2>(double2 v) { return v; }
+template <> __device__ __forceinline__ float2 from_d<float2>(double2 v) { return make_float2((float)v.x, (float)v.y); }
+template <class T2> __device__ __forceinline__ double2 to_d(T2 v) { return make_double2((double)v.x, (double)v.y); }
+
+__device__ __forceinline__ int par_idx(int m) { return m & 1; }  // 0 even, 1 odd (two's complement)
+
+// ------------------------------------------------------------------ shared-memory FFT
+// Batched Stockham FFT (autosort) over `ncol` columns of length N stored as
+// a[n * ld + col].  Radix 4, then 2, then 3 stages; N = 2^p 3^q.  tw holds
+// e^{-2 pi i n / N}; sign = -1 forward, +1 inverse (unnormalised).  Returns the
+// buffer holding the result.  All threads of the block must call it.
+template <class T2>
+__device__ __forceinline__ void small_dft(T2* v, int R, int sign) {
+    using T = typename RealOf<T2>::T;
+    if (R == 2) {
+        T2 a = v[0], b = v[1];
+        v[0] = cadd(a, b);
+        v[1] = csub(a, b);
+    } else if (R == 4) {
+        T2 s02 = cadd(v[0], v[2]), d02 = csub(v[0], v[2]);
+        T2 s13 = cadd(v[1], v[3]), d13 = csub(v[1], v[3]);
+        T2 id = imul(d13, (T)sign);
+        v[0] = cadd(s02, s13);
+        v[2] = csub(s02, s13);
+        v[1] = cadd(d02, id);
+        v[3] = csub(d02, id);
+    } else {  // R == 3
+        const T h = (T)0.86602540378443864676;  // sqrt(3)/2
+        T2 t1 = cadd(v[1], v[2]);
+        T2 t2 = mk<T2>(v[0].x - (T)0.5 * t1.x, v[0].y - (T)0.5 * t1.y);
+        T2 d = csub(v[1], v[2]);
+        T2 t3 = imul(d, (T)sign * h);
+        v[0] = cadd(v[0], t1);
+        v[1] = cadd(t2, t3);
+        v[2] = csub(t2, t3);
+    }
+}
+
+template <class T2>
+__device__ T2* fft_cols(T2* a, T2* b, int N, int ncol, int ld, const T2* tw, int sign) {
+    int n2 = 0, n3 = 0, t = N;
+    while ((t & 1) == 0) { t >>= 1; ++n2; }
+    while (t % 3 == 0) { t /= 3; ++n3; }
+    int nstage = n2 / 2 + (n2 & 1) + n3;
+    int Ns = 1;
+    for (int st = 0; st < nstage; ++st) {
+        int R = st < n2 / 2 ? 4 : ((st == n2 / 2 && (n2 & 1)) ? 2 : 3);
+        const int stride = N / R;
+        const int nb = stride * ncol;
+        const int tstep = N / (Ns * R);
+        for (int idx = threadIdx.x; idx < nb; idx += blockDim.x) {
+            const int col = idx % ncol;
+            const int jb = idx / ncol;
+            const int kk = jb % Ns;
+            T2 v[4];
+#pragma unroll
+            for (int r = 0; r < 4; ++r)
+                if (r < R) v[r] = a[(jb + r * stride) * ld + col];
+#pragma unroll
+            for (int r = 1; r < 4; ++r)
+                if (r < R) {
+                    T2 w = tw[(r * kk * tstep) % N];
+                    if (sign > 0) w.y = -w.y;
+                    v[r] = cmul(v[r], w);
+                }
+            small_dft(v, R, sign);
+            const int idxD = (jb / Ns) * Ns * R + kk;
+#pragma unroll
+            for (int r = 0; r < 4; ++r)
+                if (r < R) b[(idxD + r * Ns) * ld + col] = v[r];
+        }
+        __syncthreads();
+        T2* tmp = a;
+        a = b;
+        b = tmp;
+        Ns *= R;
+    }
+    return a;
+}
+
+// ------------------------------------------------------------------ theta synthesis
+// Y[f][j][a][k] = sum_m X_f[j][m][k] e^{i m theta_a}   (zero-padded to nt points)
+template <class T2>
+__global__ void k_synth_theta(Geo g, FieldPtrs f, T2* __restrict__ Y, const T2* __restrict__ twg, int KB) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    T2* buf0 = reinterpret_cast<T2*>(smem);
+    T2* buf1 = buf0 + g.nt * KB;
+    T2* tw = buf1 + g.nt * KB;
+    const int k0 = blockIdx.x * KB, j = blockIdx.y, fi = blockIdx.z;
+    const int kw = min(KB, g.nk - k0);
+    for (int i = threadIdx.x; i < g.nt; i += blockDim.x) tw[i] = twg[i];
+    for (int i = threadIdx.x; i < g.nt * KB; i += blockDim.x) buf0[i] = mk<T2>(0, 0);
+    __syncthreads();
+    const double2* src = f.in[fi] + (size_t)j * g.nm * g.nk;
+    for (int i = threadIdx.x; i < g.nm * KB; i += blockDim.x) {
+        const int im = i / KB, kk = i % KB;
+        if (kk < kw) {
+            const int m = im - g.M;
+            const int a = (m + g.nt) % g.nt;
+            buf0[a * KB + kk] = from_d<T2>(src[(size_t)im * g.nk + k0 + kk]);
+        }
+    }
+    __syncthreads();
+    T2* res = fft_cols(buf0, buf1, g.nt, KB, KB, tw, +1);
+    T2* dst = Y + ((size_t)(fi * g.nr + j) * g.nt) * g.nk;
+    for (int i = threadIdx.x; i < g.nt * KB; i += blockDim.x) {
+        const int a = i / KB, kk = i % KB;
+        if (kk < kw) dst[(size_t)a * g.nk + k0 + kk] = res[i];
+    }
+}
+
+// ------------------------------------------------------------------ z pass + products
+// One block per (j, theta_a) row.  The Hermitian z spectra of two real fields
+// are packed into one complex inverse FFT; the pointwise products of the
+// physical fields are formed; two real products are packed into one forward
+// FFT and separated; the result is truncated to k <= K and scaled.
+//   ZFWD: inputs u (3), w (3)          -> outputs u x w (3)
+//   ZADJ: inputs u (3), w (3), g (3)   -> outputs w x g (3), g x u (3)
+template <class T2, int MODE>
+__global__ void k_zpass(Geo g, const T2* __restrict__ Y, T2* __restrict__ Z, ZScales sc, const T2* __restrict__ twg) {
+    using T = typename RealOf<T2>::T;
+    constexpr int NIN = MODE == ZFWD ? 6 : 9;
+    constexpr int NPI = (NIN + 1) / 2;
+    constexpr int NOUT = MODE == ZFWD ? 3 : 6;
+    constexpr int NPO = (NOUT + 1) / 2;
+    constexpr int LD = NPI;  // NPI >= NPO
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int N = g.nzp, K = g.K, nk = g.nk;
+    T2* bufA = reinterpret_cast<T2*>(smem);
+    T2* bufB = bufA + N * LD;
+    T2* tw = bufB + N * LD;
+    const int a = blockIdx.x, j = blockIdx.y;
+    for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = twg[i];
+    // Hermitian-extended spectra, two fields per column
+    for (int i = threadIdx.x; i < NPI * N; i += blockDim.x) {
+        const int p = i / N, n = i % N;
+        int k = -1;
+        bool neg = false;
+        if (n <= K) k = n;
+        else if (n >= N - K) { k = N - n; neg = true; }
+        T2 q = mk<T2>(0, 0);
+        if (k >= 0) {
+            const int f1 = 2 * p, f2 = 2 * p + 1;
+            T2 y1 = Y[((size_t)(f1 * g.nr + j) * g.nt + a) * nk + k];
+            T2 h1 = k == 0 ? mk<T2>((T)sc.h0[f1] * y1.x, 0) : mk<T2>((T)sc.hk[f1] * y1.x, (T)sc.hk[f1] * y1.y);
+            T2 h2 = mk<T2>(0, 0);
+            if (f2 < NIN) {
+                T2 y2 = Y[((size_t)(f2 * g.nr + j) * g.nt + a) * nk + k];
+                h2 = k == 0 ? mk<T2>((T)sc.h0[f2] * y2.x, 0) : mk<T2>((T)sc.hk[f2] * y2.x, (T)sc.hk[f2] * y2.y);
+            }
+            if (!neg) q = mk<T2>(h1.x - h2.y, h1.y + h2.x);   // H1 + i H2
+            else q = mk<T2>(h1.x + h2.y, -h1.y + h2.x);       // conj(H1) + i conj(H2)
+        }
+        bufA[n * LD + p] = q;
+    }
+    __syncthreads();
+    T2* ph = fft_cols(bufA, bufB, N, NPI, LD, tw, +1);
+    T2* pr = (ph == bufA) ? bufB : bufA;
+    for (int n = threadIdx.x; n < N; n += blockDim.x) {
+        const T2* row = ph + n * LD;
+        const T ur = row[0].x, ut = row[0].y, uz = row[1].x;
+        const T wr = row[1].y, wt = row[2].x, wz = row[2].y;
+        T2* o = pr + n * LD;
+        if (MODE == ZFWD) {
+            o[0] = mk<T2>(ut * wz - uz * wt, uz * wr - ur * wz);
+            o[1] = mk<T2>(ur * wt - ut * wr, 0);
+        } else {
+            const T gr = row[3].x, gt = row[3].y, gz = row[4].x;
+            // w x g
+            o[0] = mk<T2>(wt * gz - wz * gt, wz * gr - wr * gz);
+            // (w x g)_z, (g x u)_r
+            o[1] = mk<T2>(wr * gt - wt * gr, gt * uz - gz * ut);
+            // (g x u)_theta, (g x u)_z
+            o[2] = mk<T2>(gz * ur - gr * uz, gr * ut - gt * ur);
+        }
+    }
+    __syncthreads();
+    T2* sp = fft_cols(pr, ph, N, NPO, LD, tw, -1);
+    for (int i = threadIdx.x; i < NPO * nk; i += blockDim.x) {
+        const int p = i / nk, k = i % nk;
+        const T2 P = sp[k * LD + p];
+        const T2 Pm = sp[((N - k) % N) * LD + p];
+        const int o1 = 2 * p, o2 = 2 * p + 1;
+        const T s1 = (T)(k == 0 ? sc.o0[o1] : sc.ok[o1]);
+        T2 z1 = mk<T2>((T)0.5 * (P.x + Pm.x) * s1, (T)0.5 * (P.y - Pm.y) * s1);
+        Z[((size_t)(o1 * g.nr + j) * g.nt + a) * nk + k] = z1;
+        if (o2 < NOUT) {
+            const T s2 = (T)(k == 0 ? sc.o0[o2] : sc.ok[o2]);
+            T2 z2 = mk<T2>((T)0.5 * (P.y + Pm.y) * s2, (T)-0.5 * (P.x - Pm.x) * s2);
+            Z[((size_t)(o2 * g.nr + j) * g.nt + a) * nk + k] = z2;
+        }
+    }
+}
+
+// ------------------------------------------------------------------ theta analysis
+// X_f[j][m][k] = sum_a Z_f[j][a][k] e^{-i m theta_a}, |m| <= M, with the k = 0
+// plane projected onto Hermitian symmetry.
+template <class T2>
+__global__ void k_anal_theta(Geo g, FieldPtrs f, const T2* __restrict__ Z, const T2* __restrict__ twg, int KB) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    T2* buf0 = reinterpret_cast<T2*>(smem);
+    T2* buf1 = buf0 + g.nt * KB;
+    T2* tw = buf1 + g.nt * KB;
+    const int k0 = blockIdx.x * KB, j = blockIdx.y, fi = blockIdx.z;
+    const int kw = min(KB, g.nk - k0);
+    for (int i = threadIdx.x; i < g.nt; i += blockDim.x) tw[i] = twg[i];
+    const T2* src = Z + ((size_t)(fi * g.nr + j) * g.nt) * g.nk;
+    for (int i = threadIdx.x; i < g.nt * KB; i += blockDim.x) {
+        const int a = i / KB, kk = i % KB;
+        buf0[i] = kk < kw ? src[(size_t)a * g.nk + k0 + kk] : mk<T2>(0, 0);
+    }
+    __syncthreads();
+    T2* res = fft_cols(buf0, buf1, g.nt, KB, KB, tw, -1);
+    double2* dst = f.out[fi] + (size_t)j * g.nm * g.nk;
+    for (int i = threadIdx.x; i < g.nm * KB; i += blockDim.x) {
+        const int im = i / KB, kk = i % KB;
+        if (kk >= kw) continue;
+        const int m = im - g.M;
+        double2 v = to_d(res[((m + g.nt) % g.nt) * KB + kk]);
+        if (k0 + kk == 0) {
+            double2 vm = to_d(res[((-m + g.nt) % g.nt) * KB + kk]);
+            v = make_double2(0.5 * (v.x + vm.x), 0.5 * (v.y - vm.y));
+        }
+        dst[(size_t)im * g.nk + k0 + kk] = v;
+    }
+}
+
+// ------------------------------------------------------------------ spectral FP64 kernels
+struct Idx {
+    int j, im, k, m;
+    size_t S;
+};
+__device__ __forceinline__ bool decode(const Geo& g, size_t idx, Idx& d) {
+    d.S = (size_t)g.nr * g.nm * g.nk;
+    if (idx >= d.S) return false;
+    d.k = (int)(idx % g.nk);
+    d.im = (int)((idx / g.nk) % g.nm);
+    d.j = (int)(idx / ((size_t)g.nk * g.nm));
+    d.m = d.im - g.M;
+    return true;
+}
+__device__ __forceinline__ size_t sidx(const Geo& g, int j, int im, int k) {
+    return ((size_t)j * g.nm + im) * g.nk + k;
+}
+
+// Banded row product sum_s B[j][s] x[j-4+s]
+__device__ __forceinline__ double2 band_row(const Geo& g, const double* B, const double2* x, int j, int im, int k) {
+    double2 acc = make_double2(0, 0);
+#pragma unroll
+    for (int s = 0; s < kB; ++s) {
+        const int c = j - 4 + s;
+        if (c >= 0 && c < g.nr) acc = dfma(__ldg(B + s), x[sidx(g, c, im, k)], acc);
+    }
+    return acc;
+}
+// Transposed banded product (B^T x)_j = sum_{j'} B[j'][j - j' + 4] x[j']
+__device__ __forceinline__ double2 band_col(const Geo& g, const double* B0, const double2* x, int j, int im, int k) {
+    double2 acc = make_double2(0, 0);
+#pragma unroll
+    for (int t = -8; t <= 4; ++t) {
+        const int c = j + t;
+        if (c >= 0 && c < g.nr) acc = dfma(__ldg(B0 + (size_t)c * kB + (4 - t)), x[sidx(g, c, im, k)], acc);
+    }
+    return acc;
+}
+
+__global__ void k_curl(Geo g, const double2* __restrict__ u, double2* __restrict__ w) {
+    Idx d;
+    if (!decode(g, (size_t)blockIdx.x * blockDim.x + threadIdx.x, d)) return;
+    const double2 *ur = u, *ut = u + d.S, *uz = u + 2 * d.S;
+    const double kz = d.k * g.kz0, ir = g.invr[d.j], mr = d.m * ir;
+    const size_t o = sidx(g, d.j, d.im, d.k);
+    const double2 dz = band_row(g, g.D1 + ((size_t)par_idx(d.m) * g.nr + d.j) * kB, uz, d.j, d.im, d.k);
+    const double2 dt = band_row(g, g.D1 + ((size_t)par_idx(d.m + 1) * g.nr + d.j) * kB, ut, d.j, d.im, d.k);
+    const double2 a = ur[o], b = ut[o], c = uz[o];
+    w[o] = make_double2(-mr * c.y + kz * b.y, mr * c.x - kz * b.x);
+    w[o + d.S] = make_double2(-kz * a.y - dz.x, kz * a.x - dz.y);
+    w[o + 2 * d.S] = make_double2(dt.x + ir * b.x + mr * a.y, dt.y + ir * b.y - mr * a.x);
+}
+
+__global__ void k_curlT_acc(Geo g, const double2* __restrict__ wb, double2* __restrict__ ub) {
+    Idx d;
+    if (!decode(g, (size_t)blockIdx.x * blockDim.x + threadIdx.x, d)) return;
+    const double2 *wr = wb, *wt = wb + d.S, *wz = wb + 2 * d.S;
+    const double kz = d.k * g.kz0, ir = g.invr[d.j], mr = d.m * ir;
+    const size_t o = sidx(g, d.j, d.im, d.k);
+    const double2 sT = band_col(g, g.D1 + (size_t)par_idx(d.m + 1) * g.nr * kB, wz, d.j, d.im, d.k);
+    const double2 sP = band_col(g, g.D1 + (size_t)par_idx(d.m) * g.nr * kB, wt, d.j, d.im, d.k);
+    const double2 a = wr[o], b = wt[o], c = wz[o];
+    double2 x = ub[o];
+    ub[o] = make_double2(x.x + kz * b.y - mr * c.y, x.y - kz * b.x + mr * c.x);
+    x = ub[o + d.S];
+    ub[o + d.S] = make_double2(x.x - kz * a.y + sT.x + ir * c.x, x.y + kz * a.x + sT.y + ir * c.y);
+    x = ub[o + 2 * d.S];
+    ub[o + 2 * d.S] = make_double2(x.x + mr * a.y - sP.x, x.y - mr * a.x - sP.y);
+}
+
+__device__ __forceinline__ void base_at(const Geo& g, int j, double c, double s, double& U, double& dU) {
+    const double r = g.r[j];
+    const double2 a = g.Uh[j], b = g.dUh[j];
+    U = 1.0 - r * r + (a.x * c - a.y * s);
+    dU = -2.0 * r + (b.x * c - b.y * s);
+}
+
+// N += (U e_z) x w + u x (-dU/dr e_theta)
+__global__ void k_base_add(Geo g, const double2* __restrict__ u, const double2* __restrict__ w, double2* __restrict__ N,
+                           double c, double s) {
+    Idx d;
+    if (!decode(g, (size_t)blockIdx.x * blockDim.x + threadIdx.x, d)) return;
+    double U, dU;
+    base_at(g, d.j, c, s, U, dU);
+    const size_t o = sidx(g, d.j, d.im, d.k), S = d.S;
+    const double2 ur = u[o], uz = u[o + 2 * S], wr = w[o], wt = w[o + S];
+    double2 x = N[o];
+    N[o] = make_double2(x.x - U * wt.x + dU * uz.x, x.y - U * wt.y + dU * uz.y);
+    x = N[o + S];
+    N[o + S] = make_double2(x.x + U * wr.x, x.y + U * wr.y);
+    x = N[o + 2 * S];
+    N[o + 2 * S] = make_double2(x.x - dU * ur.x, x.y - dU * ur.y);
+}
+
+__global__ void k_baseT_acc(Geo g, const double2* __restrict__ nb, double2* __restrict__ ub, double2* __restrict__ wb,
+                            double c, double s) {
+    Idx d;
+    if (!decode(g, (size_t)blockIdx.x * blockDim.x + threadIdx.x, d)) return;
+    double U, dU;
+    base_at(g, d.j, c, s, U, dU);
+    const size_t o = sidx(g, d.j, d.im, d.k), S = d.S;
+    const double2 nr_ = nb[o], nt = nb[o + S], nz = nb[o + 2 * S];
+    double2 x = wb[o + S];
+    wb[o + S] = make_double2(x.x - U * nr_.x, x.y - U * nr_.y);
+    x = ub[o + 2 * S];
+    ub[o + 2 * S] = make_double2(x.x + dU * nr_.x, x.y + dU * nr_.y);
+    x = wb[o];
+    wb[o] = make_double2(x.x + U * nt.x, x.y + U * nt.y);
+    x = ub[o];
+    ub[o] = make_double2(x.x - dU * nz.x, x.y - dU * nz.y);
+}
+
+// ------------------------------------------------------------------ radial stage (forward)
+// q = div F (rows j >= 1; q_0 = 0 is the tentative Neumann datum)
+__global__ void k_stage_div(Geo g, const double2* __restrict__ F, double2* __restrict__ q) {
+    Idx d;
+    if (!decode(g, (size_t)blockIdx.x * blockDim.x + threadIdx.x, d)) return;
+    const size_t o = sidx(g, d.j, d.im, d.k), S = d.S;
+    if (d.j == 0 || (d.m == 0 && d.k == 0)) {
+        q[o] = make_double2(0, 0);
+        return;
+    }
+    const double kz = d.k * g.kz0, ir = g.invr[d.j], mr = d.m * ir;
+    double2 acc = band_row(g, g.D1 + ((size_t)par_idx(d.m + 1) * g.nr + d.j) * kB, F, d.j, d.im, d.k);
+    const double2 fr = F[o], ft = F[o + S], fz = F[o + 2 * S];
+    acc.x += ir * fr.x - mr * ft.y - kz * fz.y;
+    acc.y += ir * fr.y + mr * ft.x + kz * fz.x;
+    q[o] = acc;
+}
+
+// In-place banded solve A x = b with LU factors fac[mat][j][13][nk] (one system per thread).
+__device__ void band_solve_dev(const Geo& g, const double* __restrict__ fac, int mat, int im, int k, double2* x) {
+    const int nr = g.nr, nk = g.nk;
+    const double* F = fac + (size_t)mat * nr * kB * nk + k;
+    double2 yw[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) yw[e] = make_double2(0, 0);
+    for (int j = 0; j < nr; ++j) {
+        const double* Fj = F + (size_t)j * kB * nk;
+        double2 s = x[sidx(g, j, im, k)];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) s = dfma(-__ldg(Fj + (size_t)e * nk), yw[e], s);  // yw[e] = y_{j-4+e}
+#pragma unroll
+        for (int e = 0; e < 3; ++e) yw[e] = yw[e + 1];
+        yw[3] = s;
+        x[sidx(g, j, im, k)] = s;
+    }
+    double2 xw[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) xw[e] = make_double2(0, 0);
+    for (int j = nr - 1; j >= 0; --j) {
+        const double* Fj = F + (size_t)j * kB * nk;
+        double2 s = x[sidx(g, j, im, k)];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) s = dfma(-__ldg(Fj + (size_t)(5 + e) * nk), xw[e], s);  // xw[e] = x_{j+1+e}
+        s = dscale(s, __ldg(Fj + (size_t)4 * nk));
+#pragma unroll
+        for (int e = 7; e > 0; --e) xw[e] = xw[e - 1];
+        xw[0] = s;
+        x[sidx(g, j, im, k)] = s;
+    }
+}
+
+// In-place transposed solve A^T x = b with the same factors (A^T = U^T L^T).
+__device__ void band_solveT_dev(const Geo& g, const double* __restrict__ fac, int mat, int im, int k, double2* x) {
+    const int nr = g.nr, nk = g.nk;
+    const double* F = fac + (size_t)mat * nr * kB * nk + k;
+    double2 ww[8];  // ww[i-1] = w_{j-i}
+#pragma unroll
+    for (int e = 0; e < 8; ++e) ww[e] = make_double2(0, 0);
+    for (int j = 0; j < nr; ++j) {
+        double2 s = x[sidx(g, j, im, k)];
+#pragma unroll
+        for (int i = 1; i <= 8; ++i) {
+            const int c = j - i;
+            if (c >= 0) s = dfma(-__ldg(F + ((size_t)c * kB + 4 + i) * nk), ww[i - 1], s);
+        }
+        s = dscale(s, __ldg(F + ((size_t)j * kB + 4) * nk));
+#pragma unroll
+        for (int e = 7; e > 0; --e) ww[e] = ww[e - 1];
+        ww[0] = s;
+        x[sidx(g, j, im, k)] = s;
+    }
+    double2 xw[4];  // xw[i-1] = x_{j+i}
+#pragma unroll
+    for (int e = 0; e < 4; ++e) xw[e] = make_double2(0, 0);
+    for (int j = nr - 1; j >= 0; --j) {
+        double2 s = x[sidx(g, j, im, k)];
+#pragma unroll
+        for (int i = 1; i <= 4; ++i) {
+            const int c = j + i;
+            if (c < nr) s = dfma(-__ldg(F + ((size_t)c * kB + 4 - i) * nk), xw[i - 1], s);
+        }
+#pragma unroll
+        for (int e = 3; e > 0; --e) xw[e] = xw[e - 1];
+        xw[0] = s;
+        x[sidx(g, j, im, k)] = s;
+    }
+}
+
+__global__ void k_stage_psolve(Geo g, double2* __restrict__ q) {
+    const int mode = blockIdx.x * blockDim.x + threadIdx.x;
+    if (mode >= g.nm * g.nk) return;
+    const int im = mode / g.nk, k = mode % g.nk, m = im - g.M;
+    if (m == 0 && k == 0) {
+        for (int j = 0; j < g.nr; ++j) q[sidx(g, j, im, k)] = make_double2(0, 0);
+        return;
+    }
+    band_solve_dev(g, g.facP, abs(m), im, k, q);
+}
+
+// R_v = B_v u_v + F'_v for v = +, -, z (rows j >= 1), F' = F - grad p
+__global__ void k_stage_rhs(Geo g, const double2* __restrict__ u, const double2* __restrict__ F,
+                            const double2* __restrict__ p, double2* __restrict__ R) {
+    Idx d;
+    if (!decode(g, (size_t)blockIdx.x * blockDim.x + threadIdx.x, d)) return;
+    const size_t o = sidx(g, d.j, d.im, d.k), S = d.S;
+    if (d.j == 0) {
+        R[o] = R[o + S] = R[o + 2 * S] = make_double2(0, 0);
+        return;
+    }
+    const double kz = d.k * g.kz0, ir = g.invr[d.j], mr = d.m * ir;
+    const double2 dp = band_row(g, g.D1 + ((size_t)par_idx(d.m) * g.nr + d.j) * kB, p, d.j, d.im, d.k);
+    const double2 pj = p[o], fr0 = F[o], ft0 = F[o + S], fz0 = F[o + 2 * S];
+    const double2 fr = make_double2(fr0.x - dp.x, fr0.y - dp.y);
+    const double2 ft = make_double2(ft0.x + mr * pj.y, ft0.y - mr * pj.x);
+    const double2 fz = make_double2(fz0.x + kz * pj.y, fz0.y - kz * pj.x);
+    // band sums of L_{m'} applied to u+, u-, u_z
+    const double* Lp = g.Lb + ((size_t)abs(d.m + 1) * g.nr + d.j) * kB;
+    const double* Lm = g.Lb + ((size_t)abs(d.m - 1) * g.nr + d.j) * kB;
+    const double* Lz = g.Lb + ((size_t)abs(d.m) * g.nr + d.j) * kB;
+    double2 sp = make_double2(0, 0), sm = make_double2(0, 0), sz = make_double2(0, 0);
+    const double2 *ur = u, *ut = u + S, *uz = u + 2 * S;
+#pragma unroll
+    for (int s = 0; s < kB; ++s) {
+        const int c = d.j - 4 + s;
+        if (c < 0 || c >= g.nr) continue;
+        const size_t oc = sidx(g, c, d.im, d.k);
+        const double2 a = ur[oc], b = ut[oc];
+        const double2 up = make_double2(a.x - b.y, a.y + b.x);
+        const double2 um = make_double2(a.x + b.y, a.y - b.x);
+        sp = dfma(__ldg(Lp + s), up, sp);
+        sm = dfma(__ldg(Lm + s), um, sm);
+        sz = dfma(__ldg(Lz + s), uz[oc], sz);
+    }
+    const double dg = g.inv_dt - kz * kz * g.inv_2re;
+    const double2 a = ur[o], b = ut[o], c = uz[o];
+    const double2 up = make_double2(a.x - b.y, a.y + b.x);
+    const double2 um = make_double2(a.x + b.y, a.y - b.x);
+    R[o] = make_double2(dg * up.x + g.inv_2re * sp.x + (fr.x - ft.y), dg * up.y + g.inv_2re * sp.y + (fr.y + ft.x));
+    R[o + S] = make_double2(dg * um.x + g.inv_2re * sm.x + (fr.x + ft.y), dg * um.y + g.inv_2re * sm.y + (fr.y - ft.x));
+    R[o + 2 * S] = make_double2(dg * c.x + g.inv_2re * sz.x + fz.x, dg * c.y + g.inv_2re * sz.y + fz.y);
+}
+
+__global__ void k_stage_hsolve(Geo g, double2* __restrict__ R) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int nmode = g.nm * g.nk;
+    if (t >= 3 * nmode) return;
+    const int v = t / nmode, mode = t % nmode;
+    const int im = mode / g.nk, k = mode % g.nk, m = im - g.M;
+    const int mv = v == 0 ? m + 1 : (v == 1 ? m - 1 : m);
+    const size_t S = (size_t)g.nr * g.nm * g.nk;
+    band_solve_dev(g, g.facH, abs(mv), im, k, R + v * S);
+}
+
+// back to (r, theta, z); influence correction (div u = 0 at the wall) or, for
+// mode (0,0), flux correction and u_r = 0.
+__global__ void k_stage_finish(Geo g, const double2* __restrict__ R, double2* __restrict__ out) {
+    Idx d;
+    if (!decode(g, (size_t)blockIdx.x * blockDim.x + threadIdx.x, d)) return;
+    const size_t o = sidx(g, d.j, d.im, d.k), S = d.S;
+    const double2 xp = R[o], xm = R[o + S];
+    double2 ur = make_double2(0.5 * (xp.x + xm.x), 0.5 * (xp.y + xm.y));
+    double2 ut = make_double2(0.5 * (xp.y - xm.y), -0.5 * (xp.x - xm.x));
+    double2 uz = R[o + 2 * S];
+    if (d.m == 0 && d.k == 0) {
+        double2 acc = make_double2(0, 0);
+        for (int c = 0; c < g.nr; ++c) acc = dfma(g.W[c], R[sidx(g, c, d.im, d.k) + 2 * S], acc);
+        const double gj = g.fluxg[d.j] * (-g.flux_inv);
+        uz = dfma(gj, acc, uz);
+        ur = make_double2(0, 0);
+    } else {
+        const double* d0 = g.D1 + (size_t)par_idx(d.m + 1) * g.nr * kB;  // row 0 of D1 (u_r parity)
+        double2 a0 = make_double2(0, 0);
+        for (int c = 0; c <= 8 && c < g.nr; ++c) {
+            const size_t oc = sidx(g, c, d.im, d.k);
+            const double2 p = R[oc], q = R[oc + S];
+            a0 = dfma(0.5 * __ldg(d0 + 4 + c), make_double2(p.x + q.x, p.y + q.y), a0);
+        }
+        const double* h = g.infl + ((size_t)d.im * g.nk + d.k) * 3 * g.nr;
+        const double h0 = h[d.j], h1 = h[g.nr + d.j], h2 = h[2 * g.nr + d.j];
+        ur = dfma(h0, a0, ur);
+        ut = make_double2(ut.x - h1 * a0.y, ut.y + h1 * a0.x);
+        uz = make_double2(uz.x - h2 * a0.y, uz.y + h2 * a0.x);
+    }
+    out[o] = ur;
+    out[o + S] = ut;
+    out[o + 2 * S] = uz;
+}
+
+// ------------------------------------------------------------------ radial stage (transpose)
+// One thread per mode: ybar = Fin^H ubar_new, then xbar = Ti^H ybar.
+__global__ void k_stageT_finish(Geo g, const double2* __restrict__ un, double2* __restrict__ R) {
+    const int mode = blockIdx.x * blockDim.x + threadIdx.x;
+    if (mode >= g.nm * g.nk) return;
+    const int im = mode / g.nk, k = mode % g.nk, m = im - g.M;
+    const size_t S = (size_t)g.nr * g.nm * g.nk;
+    const bool mean = (m == 0 && k == 0);
+    double2 acc = make_double2(0, 0);
+    const double* h = g.infl + ((size_t)im * g.nk + k) * 3 * g.nr;
+    for (int j = 0; j < g.nr; ++j) {
+        const size_t o = sidx(g, j, im, k);
+        if (mean) {
+            acc = dfma(g.fluxg[j], un[o + 2 * S], acc);
+        } else {
+            const double2 a = un[o], b = un[o + S], c = un[o + 2 * S];
+            // infl0 a - i infl1 b - i infl2 c
+            acc.x += h[j] * a.x + h[g.nr + j] * b.y + h[2 * g.nr + j] * c.y;
+            acc.y += h[j] * a.y - h[g.nr + j] * b.x - h[2 * g.nr + j] * c.x;
+        }
+    }
+    const double* d0 = g.D1 + (size_t)par_idx(m + 1) * g.nr * kB;
+    for (int j = 0; j < g.nr; ++j) {
+        const size_t o = sidx(g, j, im, k);
+        double2 yr = un[o], yt = un[o + S], yz = un[o + 2 * S];
+        if (mean) {
+            yr = make_double2(0, 0);
+            yz = dfma(-g.flux_inv * g.W[j], acc, yz);
+        } else if (j <= 8) {
+            yr = dfma(__ldg(d0 + 4 + j), acc, yr);
+        }
+        R[o] = make_double2(0.5 * (yr.x - yt.y), 0.5 * (yr.y + yt.x));
+        R[o + S] = make_double2(0.5 * (yr.x + yt.y), 0.5 * (yr.y - yt.x));
+        R[o + 2 * S] = yz;
+    }
+}
+
+__global__ void k_stageT_hsolve(Geo g, double2* __restrict__ R) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int nmode = g.nm * g.nk;
+    if (t >= 3 * nmode) return;
+    const int v = t / nmode, mode = t % nmode;
+    const int im = mode / g.nk, k = mode % g.nk, m = im - g.M;
+    const int mv = v == 0 ? m + 1 : (v == 1 ? m - 1 : m);
+    const size_t S = (size_t)g.nr * g.nm * g.nk;
+    band_solveT_dev(g, g.facH, abs(mv), im, k, R + v * S);
+    R[v * S + sidx(g, 0, im, k)] = make_double2(0, 0);
+}
+
+// ubar (+)= T^H B^T rbar ; Fb = T^H rbar
+__global__ void k_stageT_rhs(Geo g, const double2* __restrict__ R, double2* __restrict__ ub, int acc,
+                             double2* __restrict__ Fb) {
+    Idx d;
+    if (!decode(g, (size_t)blockIdx.x * blockDim.x + threadIdx.x, d)) return;
+    const size_t o = sidx(g, d.j, d.im, d.k), S = d.S;
+    const double kz = d.k * g.kz0;
+    const double dg = g.inv_dt - kz * kz * g.inv_2re;
+    const double2 bp0 = band_col(g, g.Lb + (size_t)abs(d.m + 1) * g.nr * kB, R, d.j, d.im, d.k);
+    const double2 bm0 = band_col(g, g.Lb + (size_t)abs(d.m - 1) * g.nr * kB, R + S, d.j, d.im, d.k);
+    const double2 bz0 = band_col(g, g.Lb + (size_t)abs(d.m) * g.nr * kB, R + 2 * S, d.j, d.im, d.k);
+    const double2 rp = R[o], rm = R[o + S], rz = R[o + 2 * S];
+    const double2 bp = make_double2(dg * rp.x + g.inv_2re * bp0.x, dg * rp.y + g.inv_2re * bp0.y);
+    const double2 bm = make_double2(dg * rm.x + g.inv_2re * bm0.x, dg * rm.y + g.inv_2re * bm0.y);
+    const double2 bz = make_double2(dg * rz.x + g.inv_2re * bz0.x, dg * rz.y + g.inv_2re * bz0.y);
+    double2 vr = make_double2(bp.x + bm.x, bp.y + bm.y);
+    double2 vt = make_double2(bp.y - bm.y, -bp.x + bm.x);
+    double2 vz = bz;
+    if (acc) {
+        const double2 a = ub[o], b = ub[o + S], c = ub[o + 2 * S];
+        vr.x += a.x; vr.y += a.y;
+        vt.x += b.x; vt.y += b.y;
+        vz.x += c.x; vz.y += c.y;
+    }
+    ub[o] = vr;
+    ub[o + S] = vt;
+    ub[o + 2 * S] = vz;
+    Fb[o] = make_double2(rp.x + rm.x, rp.y + rm.y);
+    Fb[o + S] = make_double2(rp.y - rm.y, -rp.x + rm.x);
+    Fb[o + 2 * S] = rz;
+}
+
+// qbar = G^H Fb' = D1p^T Fb'_r - i (m/r) Fb'_t - i kz Fb'_z
+__global__ void k_stageT_qbar(Geo g, const double2* __restrict__ Fb, double2* __restrict__ q) {
+    Idx d;
+    if (!decode(g, (size_t)blockIdx.x * blockDim.x + threadIdx.x, d)) return;
+    const size_t o = sidx(g, d.j, d.im, d.k), S = d.S;
+    if (d.m == 0 && d.k == 0) {
+        q[o] = make_double2(0, 0);
+        return;
+    }
+    const double kz = d.k * g.kz0, mr = d.m * g.invr[d.j];
+    double2 acc = band_col(g, g.D1 + (size_t)par_idx(d.m) * g.nr * kB, Fb, d.j, d.im, d.k);
+    const double2 ft = Fb[o + S], fz = Fb[o + 2 * S];
+    acc.x += mr * ft.y + kz * fz.y;
+    acc.y += -mr * ft.x - kz * fz.x;
+    q[o] = acc;
+}
+
+__global__ void k_stageT_psolve(Geo g, double2* __restrict__ q) {
+    const int mode = blockIdx.x * blockDim.x + threadIdx.x;
+    if (mode >= g.nm * g.nk) return;
+    const int im = mode / g.nk, k = mode % g.nk, m = im - g.M;
+    if (m == 0 && k == 0) return;  // q already zero
+    band_solveT_dev(g, g.facP, abs(m), im, k, q);
+    q[sidx(g, 0, im, k)] = make_double2(0, 0);
+}
+
+// Fb = Fb' - Dv^H z: Fb_r -= D1v^T z + z/r ; Fb_t += i (m/r) z ; Fb_z += i kz z
+__global__ void k_stageT_div(Geo g, const double2* __restrict__ z, double2* __restrict__ Fb) {
+    Idx d;
+    if (!decode(g, (size_t)blockIdx.x * blockDim.x + threadIdx.x, d)) return;
+    if (d.m == 0 && d.k == 0) return;
+    const size_t o = sidx(g, d.j, d.im, d.k), S = d.S;
+    const double kz = d.k * g.kz0, ir = g.invr[d.j], mr = d.m * ir;
+    const double2 dz = band_col(g, g.D1 + (size_t)par_idx(d.m + 1) * g.nr * kB, z, d.j, d.im, d.k);
+    const double2 zj = z[o];
+    double2 x = Fb[o];
+    Fb[o] = make_double2(x.x - dz.x - ir * zj.x, x.y - dz.y - ir * zj.y);
+    x = Fb[o + S];
+    Fb[o + S] = make_double2(x.x - mr * zj.y, x.y + mr * zj.x);
+    x = Fb[o + 2 * S];
+    Fb[o + 2 * S] = make_double2(x.x - kz * zj.y, x.y + kz * zj.x);
+}
+
+// ------------------------------------------------------------------ elementwise / reductions
+__global__ void k_axpby(size_t n, double a, const double2* __restrict__ x, double b, const double2* __restrict__ y,
+                        double2* __restrict__ out) {
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double2 p = x[i];
+    double2 r = make_double2(a * p.x, a * p.y);
+    if (y) {
+        const double2 q = y[i];
+        r.x += b * q.x;
+        r.y += b * q.y;
+    }
+    out[i] = r;
+}
+
+__global__ void k_weight(Geo g, const double2* __restrict__ x, double2* __restrict__ out, int divide) {
+    const size_t S = (size_t)g.nr * g.nm * g.nk;
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= 3 * S) return;
+    const size_t e = i % S;
+    const int k = (int)(e % g.nk), j = (int)(e / ((size_t)g.nk * g.nm));
+    const double w = g.ewt * g.W[j] * (k == 0 ? 1.0 : 2.0);
+    const double f = divide ? 1.0 / w : w;
+    out[i] = make_double2(x[i].x * f, x[i].y * f);
+}
+
+__global__ void k_inner_partial(Geo g, const double2* __restrict__ a, const double2* __restrict__ b,
+                                double* __restrict__ partial) {
+    __shared__ double red[256];
+    const size_t S = (size_t)g.nr * g.nm * g.nk, n = 3 * S;
+    double acc = 0;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const size_t e = i % S;
+        const int k = (int)(e % g.nk), j = (int)(e / ((size_t)g.nk * g.nm));
+        const double w = g.W[j] * (k == 0 ? 1.0 : 2.0);
+        const double2 p = a[i], q = b[i];
+        acc += w * (p.x * q.x + p.y * q.y);
+    }
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) partial[blockIdx.x] = red[0];
+}
+
+__global__ void k_inner_final(const double* __restrict__ partial, int np, double scale, double* __restrict__ out) {
+    __shared__ double red[1024];
+    double acc = 0;
+    for (int i = threadIdx.x; i < np; i += blockDim.x) acc += partial[i];
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[0] = red[0] * scale;
+}
+
+// ------------------------------------------------------------------ launchers
+static void check_launch(const char* what) {
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        char buf[256];
+        std::snprintf(buf, sizeof buf, "%s: %s", what, cudaGetErrorString(e));
+        throw std::runtime_error(buf);
+    }
+}
+static inline unsigned nblk(size_t n, int bs) { return (unsigned)((n + bs - 1) / bs); }
+static inline size_t S_of(const Geo& g) { return (size_t)g.nr * g.nm * g.nk; }
+
+void launch_curl(const Geo& g, const double2* u, double2* w, cudaStream_t s) {
+    k_curl<<<nblk(S_of(g), 256), 256, 0, s>>>(g, u, w);
+    check_launch("curl");
+}
+void launch_curlT_acc(const Geo& g, const double2* wb, double2* ub, cudaStream_t s) {
+    k_curlT_acc<<<nblk(S_of(g), 256), 256, 0, s>>>(g, wb, ub);
+    check_launch("curlT");
+}
+void launch_base_add(const Geo& g, const double2* u, const double2* w, double2* N, double c, double sn, cudaStream_t s) {
+    k_base_add<<<nblk(S_of(g), 256), 256, 0, s>>>(g, u, w, N, c, sn);
+    check_launch("base_add");
+}
+void launch_baseT_acc(const Geo& g, const double2* nb, double2* ub, double2* wb, double c, double sn, cudaStream_t s) {
+    k_baseT_acc<<<nblk(S_of(g), 256), 256, 0, s>>>(g, nb, ub, wb, c, sn);
+    check_launch("baseT");
+}
+
+template <class T2> static const T2* tw_theta(const Twiddles& t);
+template <> const double2* tw_theta<double2>(const Twiddles& t) { return t.th_d; }
+template <> const float2* tw_theta<float2>(const Twiddles& t) { return t.th_f; }
+template <class T2> static const T2* tw_z(const Twiddles& t);
+template <> const double2* tw_z<double2>(const Twiddles& t) { return t.z_d; }
+template <> const float2* tw_z<float2>(const Twiddles& t) { return t.z_f; }
+
+template <class T2> static int theta_kb(const Geo& g) {
+    int kb = 32;
+    while (kb > 4 && (kb / 2 >= g.nk || (size_t)(2 * g.nt * kb + g.nt) * sizeof(T2) > 100 * 1024)) kb /= 2;
+    return kb;
+}
+
+template <class T2>
+void launch_synth_theta(const Geo& g, const FieldPtrs& f, int nfield, T2* Y, const Twiddles& tw, cudaStream_t s) {
+    const int KB = theta_kb<T2>(g);
+    const size_t sm = (size_t)(2 * g.nt * KB + g.nt) * sizeof(T2);
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_synth_theta<T2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        attr = true;
+    }
+    dim3 grid((g.nk + KB - 1) / KB, g.nr, nfield);
+    k_synth_theta<T2><<<grid, 256, sm, s>>>(g, f, Y, tw_theta<T2>(tw), KB);
+    check_launch("synth_theta");
+}
+
+template <class T2>
+void launch_anal_theta(const Geo& g, const FieldPtrs& f, int nfield, const T2* Z, const Twiddles& tw, cudaStream_t s) {
+    const int KB = theta_kb<T2>(g);
+    const size_t sm = (size_t)(2 * g.nt * KB + g.nt) * sizeof(T2);
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_anal_theta<T2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        attr = true;
+    }
+    dim3 grid((g.nk + KB - 1) / KB, g.nr, nfield);
+    k_anal_theta<T2><<<grid, 256, sm, s>>>(g, f, Z, tw_theta<T2>(tw), KB);
+    check_launch("anal_theta");
+}
+
+template <class T2>
+void launch_zpass(const Geo& g, int mode, const T2* Y, T2* Z, const ZScales& sc, const Twiddles& tw, cudaStream_t s) {
+    const int ld = mode == ZFWD ? 3 : 5;
+    const size_t sm = (size_t)(2 * g.nzp * ld + g.nzp) * sizeof(T2);
+    dim3 grid(g.nt, g.nr);
+    if (mode == ZFWD) {
+        static bool attr = false;
+        if (!attr) {
+            cudaFuncSetAttribute(k_zpass<T2, ZFWD>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+            attr = true;
+        }
+        k_zpass<T2, ZFWD><<<grid, 256, sm, s>>>(g, Y, Z, sc, tw_z<T2>(tw));
+    } else {
+        static bool attr = false;
+        if (!attr) {
+            cudaFuncSetAttribute(k_zpass<T2, ZADJ>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+            attr = true;
+        }
+        k_zpass<T2, ZADJ><<<grid, 256, sm, s>>>(g, Y, Z, sc, tw_z<T2>(tw));
+    }
+    check_launch("zpass");
+}
+
+template void launch_synth_theta<double2>(const Geo&, const FieldPtrs&, int, double2*, const Twiddles&, cudaStream_t);
+template void launch_synth_theta<float2>(const Geo&, const FieldPtrs&, int, float2*, const Twiddles&, cudaStream_t);
+template void launch_anal_theta<double2>(const Geo&, const FieldPtrs&, int, const double2*, const Twiddles&,
+                                         cudaStream_t);
+template void launch_anal_theta<float2>(const Geo&, const FieldPtrs&, int, const float2*, const Twiddles&,
+                                        cudaStream_t);
+template void launch_zpass<double2>(const Geo&, int, const double2*, double2*, const ZScales&, const Twiddles&,
+                                    cudaStream_t);
+template void launch_zpass<float2>(const Geo&, int, const float2*, float2*, const ZScales&, const Twiddles&,
+                                   cudaStream_t);
+
+void launch_stage(const Geo& g, const double2* u, const double2* F, double2* out, double2* q, double2* R,
+                  cudaStream_t s) {
+    const size_t S = S_of(g);
+    const int nmode = g.nm * g.nk;
+    k_stage_div<<<nblk(S, 256), 256, 0, s>>>(g, F, q);
+    k_stage_psolve<<<nblk(nmode, 64), 64, 0, s>>>(g, q);
+    k_stage_rhs<<<nblk(S, 256), 256, 0, s>>>(g, u, F, q, R);
+    k_stage_hsolve<<<nblk(3 * (size_t)nmode, 64), 64, 0, s>>>(g, R);
+    k_stage_finish<<<nblk(S, 256), 256, 0, s>>>(g, R, out);
+    check_launch("stage");
+}
+
+void launch_stageT(const Geo& g, const double2* ubn, double2* ub, int acc, double2* Fb, double2* q, double2* R,
+                   cudaStream_t s) {
+    const size_t S = S_of(g);
+    const int nmode = g.nm * g.nk;
+    k_stageT_finish<<<nblk(nmode, 64), 64, 0, s>>>(g, ubn, R);
+    k_stageT_hsolve<<<nblk(3 * (size_t)nmode, 64), 64, 0, s>>>(g, R);
+    k_stageT_rhs<<<nblk(S, 256), 256, 0, s>>>(g, R, ub, acc, Fb);
+    k_stageT_qbar<<<nblk(S, 256), 256, 0, s>>>(g, Fb, q);
+    k_stageT_psolve<<<nblk(nmode, 64), 64, 0, s>>>(g, q);
+    k_stageT_div<<<nblk(S, 256), 256, 0, s>>>(g, q, Fb);
+    check_launch("stageT");
+}
+
+void launch_axpby(size_t n, double a, const double2* x, double b, const double2* y, double2* out, cudaStream_t s) {
+    k_axpby<<<nblk(n, 256), 256, 0, s>>>(n, a, x, b, y, out);
+    check_launch("axpby");
+}
+void launch_weight(const Geo& g, const double2* x, double2* out, int divide, cudaStream_t s) {
+    k_weight<<<nblk(3 * S_of(g), 256), 256, 0, s>>>(g, x, out, divide);
+    check_launch("weight");
+}
+void launch_inner(const Geo& g, const double2* a, const double2* b, double* partial, double* dev_out, cudaStream_t s) {
+    k_inner_partial<<<kInnerBlocks, 256, 0, s>>>(g, a, b, partial);
+    k_inner_final<<<1, 1024, 0, s>>>(partial, kInnerBlocks, g.ewt, dev_out);
+    check_launch("inner");
+}
+
+}  // namespace pnop

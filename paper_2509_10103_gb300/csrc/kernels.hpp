@@ -1,0 +1,81 @@
+// Device kernels of the forward/adjoint pipe-flow step and their launchers.
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace pnop {
+
+// Read-only geometry and operators, passed to kernels by value.
+struct Geo {
+    int nr, M, K, nm, nk, nt, nzp;
+    double kz0;      // 2 pi / Lz
+    double inv_dt;   // 1 / dt
+    double inv_2re;  // 1 / (2 Re)
+    const double* r;
+    const double* invr;
+    const double* W;
+    const double* D1;    // [2][nr][13]
+    const double* Lb;    // [M+2][nr][13]
+    const double* facH;  // [M+2][nr][13][nk]
+    const double* facP;  // [M+1][nr][13][nk]
+    const double* infl;  // [nm][nk][3][nr]
+    const double* fluxg; // [nr]
+    double flux_inv;
+    const double2* Uh;   // [nr]
+    const double2* dUh;  // [nr]
+    double ewt;          // 2 pi Lz (energy weight prefactor)
+};
+
+// Up to 9 input / 6 output spectral component planes for the transforms.
+struct FieldPtrs {
+    const double2* in[9];
+    double2* out[6];
+};
+
+// Per-field multipliers applied when forming the Hermitian z spectrum:
+// H_0 = h0 * Re(Y_0), H_k = hk * Y_k (k >= 1); per-output k-scales o0, ok.
+struct ZScales {
+    double h0[9], hk[9];
+    double o0[6], ok[6];
+};
+
+// Twiddle tables e^{-2 pi i n / N} for N = nt and N = nzp, FP64 and FP32.
+struct Twiddles {
+    const double2* th_d;
+    const double2* z_d;
+    const float2* th_f;
+    const float2* z_f;
+};
+
+enum ZMode { ZFWD = 0, ZADJ = 1 };
+
+// ---- spectral FP64 kernels ----
+void launch_curl(const Geo& g, const double2* u, double2* w, cudaStream_t s);
+void launch_curlT_acc(const Geo& g, const double2* wb, double2* ub, cudaStream_t s);
+void launch_base_add(const Geo& g, const double2* u, const double2* w, double2* N, double c, double sn, cudaStream_t s);
+void launch_baseT_acc(const Geo& g, const double2* nb, double2* ub, double2* wb, double c, double sn, cudaStream_t s);
+
+// ---- transforms (T = double for FP64, float for mixed) ----
+template <class T2>
+void launch_synth_theta(const Geo& g, const FieldPtrs& f, int nfield, T2* Y, const Twiddles& tw, cudaStream_t s);
+template <class T2>
+void launch_zpass(const Geo& g, int mode, const T2* Y, T2* Z, const ZScales& sc, const Twiddles& tw, cudaStream_t s);
+template <class T2>
+void launch_anal_theta(const Geo& g, const FieldPtrs& f, int nfield, const T2* Z, const Twiddles& tw, cudaStream_t s);
+
+// ---- radial stage (forward) ----
+// out = S(u, F): pressure projection, Helmholtz solves, influence and flux corrections.
+void launch_stage(const Geo& g, const double2* u, const double2* F, double2* out, double2* q, double2* R,
+                  cudaStream_t s);
+// Transpose: ub (=, or += when acc) gets S_u^H ubn, Fb gets S_F^H ubn.
+void launch_stageT(const Geo& g, const double2* ubn, double2* ub, int acc, double2* Fb, double2* q, double2* R,
+                   cudaStream_t s);
+
+// ---- elementwise / reductions ----
+void launch_axpby(size_t n, double a, const double2* x, double b, const double2* y, double2* out, cudaStream_t s);
+void launch_weight(const Geo& g, const double2* x, double2* out, int divide, cudaStream_t s);
+// Deterministic weighted inner product sum W_hat Re(conj(a) b); result to dev_out[0].
+void launch_inner(const Geo& g, const double2* a, const double2* b, double* partial, double* dev_out, cudaStream_t s);
+constexpr int kInnerBlocks = 608;  // 4 x 152 SMs; fixed so the reduction order never changes
+
+}  // namespace pnop

@@ -1,0 +1,627 @@
+// C ABI of the GB300 pipe-flow forward/adjoint solver: context set-up, the
+// predictor-corrector step (Section 2.4), its exact transpose, and the
+// binomially checkpointed gradient sweep (Section 2.5, Eq. 2.18-2.20).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <complex>
+#include <cstring>
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+#include "../../include/pnop.h"
+#include "kernels.hpp"
+#include "setup.hpp"
+
+using pnop::Geo;
+
+namespace {
+
+struct CudaError : std::runtime_error {
+    using std::runtime_error::runtime_error;
+};
+struct Status : std::runtime_error {
+    int code;
+    Status(int c, const std::string& m) : std::runtime_error(m), code(c) {}
+};
+
+void ck(cudaError_t e, const char* what) {
+    if (e != cudaSuccess) throw CudaError(std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+bool smooth_size(int n) {
+    if (n < 2) return false;
+    while (n % 2 == 0) n /= 2;
+    while (n % 3 == 0) n /= 3;
+    return n == 1;
+}
+
+}  // namespace
+
+struct pnop_ctx {
+    pnop::HostOps h;
+    pnop_params prm{};
+    cudaStream_t stream = nullptr;
+    Geo geo{};
+    size_t bytes = 0;
+    std::vector<void*> allocs;
+    // operators
+    double *d_r = nullptr, *d_invr = nullptr, *d_W = nullptr, *d_D1 = nullptr, *d_Lb = nullptr;
+    double *d_facH = nullptr, *d_facP = nullptr, *d_infl = nullptr, *d_fluxg = nullptr;
+    double2 *d_Uh = nullptr, *d_dUh = nullptr;
+    pnop::Twiddles tw{};
+    // workspace
+    double2* omega = nullptr;
+    double2* N0 = nullptr;  // also second F-bar of the adjoint step
+    double2* N1 = nullptr;
+    double2* us = nullptr;
+    double2* ua = nullptr;
+    double2* Fb = nullptr;
+    double2* Nb = nullptr;
+    double2* ubs = nullptr;
+    double2* wb = nullptr;
+    double2* R = nullptr;
+    double2* q = nullptr;
+    double2 *tmpA = nullptr, *tmpB = nullptr, *lamA = nullptr, *lamB = nullptr;
+    void* Y = nullptr;
+    void* Z = nullptr;
+    double* partial = nullptr;
+    double* dscal = nullptr;  // [4] device scalars
+    std::vector<double2*> snaps;
+    std::string err;
+    long long st_adv = 0, st_adj = 0, st_store = 0;
+    // gradient sweep state
+    long long g_nsteps = 0;
+    bool g_terminal = false;
+
+    size_t S() const { return (size_t)h.d.nr * h.d.nm * h.d.nk; }
+    size_t field_bytes() const { return 3 * S() * sizeof(double2); }
+
+    void* dalloc(size_t n) {
+        if (prm.hbm_budget && bytes + n > prm.hbm_budget)
+            throw Status(PNOP_ERR_OOM, "HBM budget exceeded (" + std::to_string(bytes + n) + " > " +
+                                           std::to_string(prm.hbm_budget) + " bytes)");
+        void* p = nullptr;
+        cudaError_t e = cudaMalloc(&p, n);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            throw Status(PNOP_ERR_OOM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+        }
+        allocs.push_back(p);
+        bytes += n;
+        return p;
+    }
+    template <class T> T* upload(const std::vector<T>& v) {
+        T* p = (T*)dalloc(std::max<size_t>(1, v.size()) * sizeof(T));
+        if (!v.empty()) ck(cudaMemcpy(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice), "upload");
+        return p;
+    }
+    double2* field() { return (double2*)dalloc(field_bytes()); }
+};
+
+namespace {
+
+std::vector<double2> cvec(const std::vector<std::complex<double>>& v) {
+    std::vector<double2> o(v.size());
+    for (size_t i = 0; i < v.size(); ++i) o[i] = make_double2(v[i].real(), v[i].imag());
+    return o;
+}
+
+template <class T2> std::vector<T2> twiddle_table(int N) {
+    std::vector<T2> t(N);
+    for (int n = 0; n < N; ++n) {
+        long double a = -2.0L * 3.14159265358979323846264338327950288L * n / N;
+        t[n].x = (decltype(t[n].x))std::cos(a);
+        t[n].y = (decltype(t[n].y))std::sin(a);
+    }
+    return t;
+}
+
+void upload_operators(pnop_ctx* c) {
+    // operator tables that depend on Re/dt/Wo/A are re-uploaded on change
+    const auto& h = c->h;
+    auto put = [&](double*& dst, const std::vector<double>& v) {
+        if (!dst) dst = c->upload(v);
+        else ck(cudaMemcpy(dst, v.data(), v.size() * sizeof(double), cudaMemcpyHostToDevice), "upload");
+    };
+    put(c->d_Lb, h.Lb);
+    put(c->d_facH, h.facH);
+    put(c->d_facP, h.facP);
+    put(c->d_infl, h.infl);
+    put(c->d_fluxg, h.fluxg);
+    auto uh = cvec(h.Uh), duh = cvec(h.dUh);
+    if (!c->d_Uh) {
+        c->d_Uh = c->upload(uh);
+        c->d_dUh = c->upload(duh);
+    } else {
+        ck(cudaMemcpy(c->d_Uh, uh.data(), uh.size() * sizeof(double2), cudaMemcpyHostToDevice), "upload");
+        ck(cudaMemcpy(c->d_dUh, duh.data(), duh.size() * sizeof(double2), cudaMemcpyHostToDevice), "upload");
+    }
+    Geo& g = c->geo;
+    g.inv_dt = 1.0 / h.ph.dt;
+    g.inv_2re = 1.0 / (2.0 * h.ph.Re);
+    g.Lb = c->d_Lb;
+    g.facH = c->d_facH;
+    g.facP = c->d_facP;
+    g.infl = c->d_infl;
+    g.fluxg = c->d_fluxg;
+    g.flux_inv = h.flux_inv;
+    g.Uh = c->d_Uh;
+    g.dUh = c->d_dUh;
+}
+
+bool mixed(const pnop_ctx* c) { return c->prm.precision == PNOP_MIXED; }
+
+// ------------------------------------------------------------------ nonlinear term
+// N = P[I(u) x I(w)] + (U e_z) x w + u x (-dU/dr e_theta), w = curl u  (Eq. 2.5)
+void nonlinear(pnop_ctx* c, const double2* u, double t, double2* N) {
+    const Geo& g = c->geo;
+    const size_t S = c->S();
+    cudaStream_t s = c->stream;
+    pnop::launch_curl(g, u, c->omega, s);
+    pnop::FieldPtrs f{};
+    for (int i = 0; i < 3; ++i) {
+        f.in[i] = u + i * S;
+        f.in[3 + i] = c->omega + i * S;
+        f.out[i] = N + i * S;
+    }
+    pnop::ZScales sc{};
+    const double inv_n = 1.0 / ((double)g.nt * g.nzp);
+    for (int i = 0; i < 6; ++i) sc.h0[i] = sc.hk[i] = 1.0;
+    for (int i = 0; i < 3; ++i) sc.o0[i] = sc.ok[i] = inv_n;
+    if (mixed(c)) {
+        pnop::launch_synth_theta<float2>(g, f, 6, (float2*)c->Y, c->tw, s);
+        pnop::launch_zpass<float2>(g, pnop::ZFWD, (const float2*)c->Y, (float2*)c->Z, sc, c->tw, s);
+        pnop::launch_anal_theta<float2>(g, f, 3, (const float2*)c->Z, c->tw, s);
+    } else {
+        pnop::launch_synth_theta<double2>(g, f, 6, (double2*)c->Y, c->tw, s);
+        pnop::launch_zpass<double2>(g, pnop::ZFWD, (const double2*)c->Y, (double2*)c->Z, sc, c->tw, s);
+        pnop::launch_anal_theta<double2>(g, f, 3, (const double2*)c->Z, c->tw, s);
+    }
+    const double ph = c->h.omega * t;
+    pnop::launch_base_add(g, u, c->omega, N, std::cos(ph), std::sin(ph), s);
+}
+
+// ub = (dN/du at u)^T nb  (Euclidean cotangents)
+void nonlinearT(pnop_ctx* c, const double2* u, double t, const double2* nb, double2* ub) {
+    const Geo& g = c->geo;
+    const size_t S = c->S();
+    cudaStream_t s = c->stream;
+    pnop::launch_curl(g, u, c->omega, s);
+    pnop::FieldPtrs f{};
+    for (int i = 0; i < 3; ++i) {
+        f.in[i] = u + i * S;
+        f.in[3 + i] = c->omega + i * S;
+        f.in[6 + i] = nb + i * S;
+        f.out[i] = ub + i * S;
+        f.out[3 + i] = c->wb + i * S;
+    }
+    pnop::ZScales sc{};
+    const double inv_n = 1.0 / ((double)g.nt * g.nzp);
+    for (int i = 0; i < 6; ++i) sc.h0[i] = sc.hk[i] = 1.0;
+    // transpose of the truncated analysis: (1/N) sum_k Re(nb e^{i phi}), no c_k
+    for (int i = 6; i < 9; ++i) {
+        sc.h0[i] = inv_n;
+        sc.hk[i] = 0.5 * inv_n;
+    }
+    // transpose of the synthesis: c_k sum g e^{-i phi}
+    for (int i = 0; i < 6; ++i) {
+        sc.o0[i] = 1.0;
+        sc.ok[i] = 2.0;
+    }
+    if (mixed(c)) {
+        pnop::launch_synth_theta<float2>(g, f, 9, (float2*)c->Y, c->tw, s);
+        pnop::launch_zpass<float2>(g, pnop::ZADJ, (const float2*)c->Y, (float2*)c->Z, sc, c->tw, s);
+        pnop::launch_anal_theta<float2>(g, f, 6, (const float2*)c->Z, c->tw, s);
+    } else {
+        pnop::launch_synth_theta<double2>(g, f, 9, (double2*)c->Y, c->tw, s);
+        pnop::launch_zpass<double2>(g, pnop::ZADJ, (const double2*)c->Y, (double2*)c->Z, sc, c->tw, s);
+        pnop::launch_anal_theta<double2>(g, f, 6, (const double2*)c->Z, c->tw, s);
+    }
+    const double ph = c->h.omega * t;
+    pnop::launch_baseT_acc(g, nb, ub, c->wb, std::cos(ph), std::sin(ph), s);
+    pnop::launch_curlT_acc(g, c->wb, ub, s);
+}
+
+// ------------------------------------------------------------------ steps
+void fwd_step(pnop_ctx* c, const double2* u, double2* out, double t) {
+    const Geo& g = c->geo;
+    const size_t n = 3 * c->S();
+    nonlinear(c, u, t, c->N0);
+    pnop::launch_stage(g, u, c->N0, c->us, c->q, c->R, c->stream);
+    nonlinear(c, c->us, t + c->h.ph.dt, c->N1);
+    pnop::launch_axpby(n, 0.5, c->N0, 0.5, c->N1, c->N1, c->stream);
+    pnop::launch_stage(g, u, c->N1, out, c->q, c->R, c->stream);
+}
+
+// lout = J^T lin (Euclidean cotangents) for the step from state u at time t
+void adj_step(pnop_ctx* c, const double2* u, double t, const double2* lin, double2* lout) {
+    const Geo& g = c->geo;
+    const size_t n = 3 * c->S();
+    cudaStream_t s = c->stream;
+    nonlinear(c, u, t, c->N0);
+    pnop::launch_stage(g, u, c->N0, c->us, c->q, c->R, s);
+    pnop::launch_stageT(g, lin, c->ua, 0, c->Fb, c->q, c->R, s);
+    pnop::launch_axpby(n, 0.5, c->Fb, 0.0, nullptr, c->Nb, s);
+    nonlinearT(c, c->us, t + c->h.ph.dt, c->Nb, c->ubs);
+    pnop::launch_stageT(g, c->ubs, c->ua, 1, c->N0, c->q, c->R, s);
+    pnop::launch_axpby(n, 1.0, c->N0, 0.5, c->Fb, c->Nb, s);
+    nonlinearT(c, u, t, c->Nb, c->ubs);
+    pnop::launch_axpby(n, 1.0, c->ua, 1.0, c->ubs, lout, s);
+}
+
+double inner_sync(pnop_ctx* c, const double2* a, const double2* b) {
+    pnop::launch_inner(c->geo, a, b, c->partial, c->dscal, c->stream);
+    double v = 0;
+    ck(cudaMemcpyAsync(&v, c->dscal, sizeof(double), cudaMemcpyDeviceToHost, c->stream), "inner copy");
+    ck(cudaStreamSynchronize(c->stream), "inner sync");
+    return v;
+}
+
+// ------------------------------------------------------------------ checkpointed sweep
+const double2* advance(pnop_ctx* c, const double2* src, long long start, long long n, double2* dst_final) {
+    const double2* cur = src;
+    for (long long i = 0; i < n; ++i) {
+        double2* out = (i == n - 1 && dst_final) ? dst_final : (cur == c->tmpA ? c->tmpB : c->tmpA);
+        fwd_step(c, cur, out, c->h.ph.tau0 + (start + i) * c->h.ph.dt);
+        ++c->st_adv;
+        cur = out;
+    }
+    return cur;
+}
+
+void adjoint_at(pnop_ctx* c, long long n, const double2* state) {
+    const double t = c->h.ph.tau0 + n * c->h.ph.dt;
+    if (!c->g_terminal) {
+        if (n != c->g_nsteps - 1) throw Status(PNOP_ERR_INVALID_ARG, "checkpoint schedule out of order");
+        // terminal state u_N and compatibility condition (Eq. 2.8): cotangent W_hat u_N
+        fwd_step(c, state, c->lamB, t);
+        ++c->st_adv;
+        pnop::launch_inner(c->geo, c->lamB, c->lamB, c->partial, c->dscal + 1, c->stream);
+        pnop::launch_weight(c->geo, c->lamB, c->lamA, 0, c->stream);
+        c->g_terminal = true;
+    }
+    adj_step(c, state, t, c->lamA, c->lamB);
+    std::swap(c->lamA, c->lamB);
+    ++c->st_adj;
+}
+
+// Reverse steps [start, start+l) whose first state sits in snapshot `slot`,
+// with s slots available (that one included).
+void reverse(pnop_ctx* c, long long start, long long l, int slot, int s) {
+    if (l <= 0) return;
+    if (l == 1) {
+        adjoint_at(c, start, c->snaps[slot]);
+        return;
+    }
+    if (s == 1) {
+        for (long long i = l - 1; i >= 0; --i) {
+            const double2* st = c->snaps[slot];
+            if (i > 0) st = advance(c, st, start, i, nullptr);
+            adjoint_at(c, start + i, st);
+        }
+        return;
+    }
+    const int r = pnop::revolve_repetitions(l, s);
+    long long m = std::max<long long>(1, std::max(pnop::binom_beta(s, r - 2), l - pnop::binom_beta(s - 1, r)));
+    m = std::min(m, l - 1);
+    advance(c, c->snaps[slot], start, m, c->snaps[slot + 1]);
+    ++c->st_store;
+    reverse(c, start + m, l - m, slot + 1, s - 1);
+    reverse(c, start, m, slot, s);
+}
+
+// Count-only replay of the same schedule (host logic, no device work).
+void count_reverse(long long l, int s, long long& adv, long long& stores) {
+    if (l <= 1) return;
+    if (s == 1) {
+        adv += l * (l - 1) / 2;
+        return;
+    }
+    const int r = pnop::revolve_repetitions(l, s);
+    long long m = std::max<long long>(1, std::max(pnop::binom_beta(s, r - 2), l - pnop::binom_beta(s - 1, r)));
+    m = std::min(m, l - 1);
+    adv += m;
+    ++stores;
+    count_reverse(l - m, s - 1, adv, stores);
+    count_reverse(m, s, adv, stores);
+}
+
+int fail(pnop_ctx* c, int code, const std::string& msg) {
+    if (c) c->err = msg;
+    return code;
+}
+
+template <class F> int guarded(pnop_ctx* c, F&& fn) {
+    if (!c) return PNOP_ERR_INVALID_ARG;
+    c->err.clear();
+    try {
+        return fn();
+    } catch (const Status& s) {
+        return fail(c, s.code, s.what());
+    } catch (const CudaError& e) {
+        return fail(c, PNOP_ERR_CUDA, e.what());
+    } catch (const std::runtime_error& e) {
+        return fail(c, PNOP_ERR_CUDA, e.what());
+    } catch (const std::bad_alloc&) {
+        return fail(c, PNOP_ERR_OOM, "host allocation failed");
+    }
+}
+
+int gradient_impl(pnop_ctx* c, const double2* u0, double E0, double horizon, double2* grad, double* gain) {
+    const double dt = c->h.ph.dt;
+    const double nd = horizon / dt;
+    const long long N = (long long)std::llround(nd);
+    if (!(horizon > 0) || N < 1 || std::fabs(nd - (double)N) > 1e-9 * std::max(1.0, nd))
+        throw Status(PNOP_ERR_INVALID_ARG, "horizon must be a positive whole number of time steps");
+    const int s = std::max(1, c->prm.snap_budget);
+    while ((int)c->snaps.size() < s) c->snaps.push_back(c->field());
+    const size_t fb = c->field_bytes();
+    ck(cudaMemcpyAsync(c->snaps[0], u0, fb, cudaMemcpyDeviceToDevice, c->stream), "copy u0");
+    double Einit = 0.5 * inner_sync(c, c->snaps[0], c->snaps[0]);
+    if (E0 > 0) {
+        if (!(Einit > 0) || !std::isfinite(Einit)) throw Status(PNOP_ERR_NONFINITE, "initial field has no finite energy");
+        pnop::launch_axpby(3 * c->S(), std::sqrt(E0 / Einit), c->snaps[0], 0.0, nullptr, c->snaps[0], c->stream);
+        Einit = 0.5 * inner_sync(c, c->snaps[0], c->snaps[0]);
+    }
+    c->st_adv = c->st_adj = c->st_store = 0;
+    c->g_nsteps = N;
+    c->g_terminal = false;
+    reverse(c, 0, N, 0, s);
+    pnop::launch_weight(c->geo, c->lamA, grad, 1, c->stream);
+    double ET2 = 0;
+    ck(cudaMemcpyAsync(&ET2, c->dscal + 1, sizeof(double), cudaMemcpyDeviceToHost, c->stream), "copy E");
+    ck(cudaStreamSynchronize(c->stream), "gradient sync");
+    const double ET = 0.5 * ET2;
+    if (!std::isfinite(ET)) throw Status(PNOP_ERR_NONFINITE, "final energy is not finite");
+    if (gain) *gain = ET / Einit;
+    return PNOP_OK;
+}
+
+}  // namespace
+
+// ====================================================================== C ABI
+extern "C" {
+
+const char* pnop_error_string(int status) {
+    switch (status) {
+        case PNOP_OK: return "ok";
+        case PNOP_ERR_INVALID_ARG: return "invalid argument";
+        case PNOP_ERR_OOM: return "out of device memory or HBM budget";
+        case PNOP_ERR_CUDA: return "CUDA error";
+        case PNOP_ERR_NONFINITE: return "non-finite result";
+        case PNOP_ERR_TIMEOUT: return "timeout";
+        case PNOP_ERR_UNSUPPORTED: return "unsupported configuration";
+        default: return "unknown status";
+    }
+}
+
+const char* pnop_last_error(const pnop_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+int pnop_revolve_counts(int nsteps, int snaps, long long* advances, long long* stores) {
+    if (nsteps < 1 || snaps < 1) return PNOP_ERR_INVALID_ARG;
+    long long adv = 0, st = 0;
+    count_reverse(nsteps, snaps, adv, st);
+    if (advances) *advances = adv;
+    if (stores) *stores = st;
+    return PNOP_OK;
+}
+
+void pnop_destroy(pnop_ctx* ctx) {
+    if (!ctx) return;
+    for (void* p : ctx->allocs) cudaFree(p);
+    delete ctx;
+}
+
+int pnop_create(const pnop_grid* grid, const pnop_params* params, void* cuda_stream, pnop_ctx** out) {
+    if (!out) return PNOP_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!grid || !params) return PNOP_ERR_INVALID_ARG;
+    if (grid->nr < 9 || grid->ntheta < 4 || grid->nz < 4 || (grid->ntheta & 1) || (grid->nz & 1) ||
+        !(grid->Lz > 0) || !(grid->stretch >= 0 && grid->stretch < 1))
+        return PNOP_ERR_INVALID_ARG;
+    if (!(params->Re > 0) || !(params->dt > 0) || params->snap_budget < 1 ||
+        (params->precision != PNOP_FP64 && params->precision != PNOP_MIXED) || !(params->A >= 0) ||
+        !(params->Wo > 0 || params->A == 0))
+        return PNOP_ERR_INVALID_ARG;
+    const int M = grid->ntheta / 2 - 1, K = grid->nz / 2 - 1;
+    if (!smooth_size(3 * (M + 1)) || !smooth_size(3 * (K + 1))) return PNOP_ERR_UNSUPPORTED;
+    pnop_ctx* c = new pnop_ctx();
+    c->prm = *params;
+    c->stream = (cudaStream_t)cuda_stream;
+    pnop::Dims& d = c->h.d;
+    d.nr = grid->nr;
+    d.M = M;
+    d.K = K;
+    d.nm = 2 * M + 1;
+    d.nk = K + 1;
+    d.nth = 3 * (M + 1);
+    d.nzp = 3 * (K + 1);
+    d.Lz = grid->Lz;
+    d.stretch = grid->stretch;
+    c->h.ph = {params->Re, params->Wo, params->A, params->dt, params->tau0};
+    int rc = guarded(c, [&]() -> int {
+        std::string err;
+        if (!pnop::build_grid(c->h, err)) throw Status(PNOP_ERR_UNSUPPORTED, err);
+        if (!pnop::build_operators(c->h, err)) throw Status(PNOP_ERR_UNSUPPORTED, err);
+        Geo& g = c->geo;
+        g.nr = d.nr;
+        g.M = M;
+        g.K = K;
+        g.nm = d.nm;
+        g.nk = d.nk;
+        g.nt = d.nth;
+        g.nzp = d.nzp;
+        g.kz0 = 2.0 * M_PI / d.Lz;
+        g.ewt = 2.0 * M_PI * d.Lz;
+        c->d_r = c->upload(c->h.r);
+        c->d_invr = c->upload(c->h.invr);
+        c->d_W = c->upload(c->h.W);
+        c->d_D1 = c->upload(c->h.D1);
+        g.r = c->d_r;
+        g.invr = c->d_invr;
+        g.W = c->d_W;
+        g.D1 = c->d_D1;
+        upload_operators(c);
+        auto thd = twiddle_table<double2>(d.nth), zd = twiddle_table<double2>(d.nzp);
+        auto thf = twiddle_table<float2>(d.nth), zf = twiddle_table<float2>(d.nzp);
+        c->tw.th_d = c->upload(thd);
+        c->tw.z_d = c->upload(zd);
+        c->tw.th_f = c->upload(thf);
+        c->tw.z_f = c->upload(zf);
+        for (double2** b : {&c->omega, &c->N0, &c->N1, &c->us, &c->ua, &c->Fb, &c->Nb, &c->ubs, &c->wb, &c->R,
+                            &c->tmpA, &c->tmpB, &c->lamA, &c->lamB})
+            *b = c->field();
+        c->q = (double2*)c->dalloc(c->S() * sizeof(double2));
+        const size_t cz = mixed(c) ? sizeof(float2) : sizeof(double2);
+        const size_t plane = (size_t)d.nr * d.nth * d.nk * cz;
+        c->Y = c->dalloc(9 * plane);
+        c->Z = c->dalloc(6 * plane);
+        c->partial = (double*)c->dalloc(pnop::kInnerBlocks * sizeof(double));
+        c->dscal = (double*)c->dalloc(4 * sizeof(double));
+        ck(cudaDeviceSynchronize(), "create");
+        return PNOP_OK;
+    });
+    if (rc != PNOP_OK) {
+        pnop_destroy(c);
+        return rc;
+    }
+    *out = c;
+    return PNOP_OK;
+}
+
+int pnop_set_base_flow(pnop_ctx* ctx, double Re, double Wo, double A, double tau0) {
+    return guarded(ctx, [&]() -> int {
+        if (!(Re > 0) || !(A >= 0) || !(Wo > 0 || A == 0)) throw Status(PNOP_ERR_INVALID_ARG, "bad base-flow parameters");
+        ctx->h.ph.Re = Re;
+        ctx->h.ph.Wo = Wo;
+        ctx->h.ph.A = A;
+        ctx->h.ph.tau0 = tau0;
+        ctx->prm.Re = Re;
+        ctx->prm.Wo = Wo;
+        ctx->prm.A = A;
+        ctx->prm.tau0 = tau0;
+        std::string err;
+        ck(cudaStreamSynchronize(ctx->stream), "sync");
+        if (!pnop::build_operators(ctx->h, err)) throw Status(PNOP_ERR_UNSUPPORTED, err);
+        upload_operators(ctx);
+        return PNOP_OK;
+    });
+}
+
+int pnop_dims(const pnop_ctx* ctx, int* nr, int* M, int* K) {
+    if (!ctx) return PNOP_ERR_INVALID_ARG;
+    if (nr) *nr = ctx->h.d.nr;
+    if (M) *M = ctx->h.d.M;
+    if (K) *K = ctx->h.d.K;
+    return PNOP_OK;
+}
+
+int pnop_grid_points(const pnop_ctx* ctx, double* r_out) {
+    if (!ctx || !r_out) return PNOP_ERR_INVALID_ARG;
+    std::memcpy(r_out, ctx->h.r.data(), ctx->h.r.size() * sizeof(double));
+    return PNOP_OK;
+}
+
+int pnop_step_forward(pnop_ctx* ctx, void* u, double t, int nsteps) {
+    return guarded(ctx, [&]() -> int {
+        if (!u || nsteps < 0) throw Status(PNOP_ERR_INVALID_ARG, "bad arguments");
+        double2* uu = (double2*)u;
+        for (int i = 0; i < nsteps; ++i) {
+            fwd_step(ctx, uu, ctx->tmpA, t + i * ctx->h.ph.dt);
+            ck(cudaMemcpyAsync(uu, ctx->tmpA, ctx->field_bytes(), cudaMemcpyDeviceToDevice, ctx->stream), "copy");
+        }
+        ck(cudaGetLastError(), "step_forward");
+        return PNOP_OK;
+    });
+}
+
+int pnop_step_adjoint(pnop_ctx* ctx, const void* u_n, void* lam, double t_n) {
+    return guarded(ctx, [&]() -> int {
+        if (!u_n || !lam) throw Status(PNOP_ERR_INVALID_ARG, "bad arguments");
+        double2* l = (double2*)lam;
+        pnop::launch_weight(ctx->geo, l, ctx->tmpA, 0, ctx->stream);
+        adj_step(ctx, (const double2*)u_n, t_n, ctx->tmpA, ctx->tmpB);
+        pnop::launch_weight(ctx->geo, ctx->tmpB, l, 1, ctx->stream);
+        ck(cudaGetLastError(), "step_adjoint");
+        return PNOP_OK;
+    });
+}
+
+int pnop_gradient(pnop_ctx* ctx, const void* u0, double E0, double horizon, void* grad_out, double* gain_out) {
+    return guarded(ctx, [&]() -> int {
+        if (!u0 || !grad_out) throw Status(PNOP_ERR_INVALID_ARG, "bad arguments");
+        return gradient_impl(ctx, (const double2*)u0, E0, horizon, (double2*)grad_out, gain_out);
+    });
+}
+
+int pnop_gradient_host(pnop_ctx* ctx, const double* u0_host, double E0, double horizon, double* grad_host,
+                       double* gain_out) {
+    return guarded(ctx, [&]() -> int {
+        if (!u0_host || !grad_host) throw Status(PNOP_ERR_INVALID_ARG, "bad arguments");
+        const size_t fb = ctx->field_bytes();
+        ck(cudaMemcpyAsync(ctx->tmpA, u0_host, fb, cudaMemcpyHostToDevice, ctx->stream), "h2d");
+        // tmpA is reused by the sweep: stage the input in the gradient output slot of lamB
+        ck(cudaMemcpyAsync(ctx->lamB, ctx->tmpA, fb, cudaMemcpyDeviceToDevice, ctx->stream), "stage");
+        int rc = gradient_impl(ctx, ctx->lamB, E0, horizon, ctx->tmpB, gain_out);
+        if (rc != PNOP_OK) return rc;
+        ck(cudaMemcpyAsync(grad_host, ctx->tmpB, fb, cudaMemcpyDeviceToHost, ctx->stream), "d2h");
+        ck(cudaStreamSynchronize(ctx->stream), "sync");
+        return PNOP_OK;
+    });
+}
+
+int pnop_gradient_stats(const pnop_ctx* ctx, long long* advances, long long* adjoint_steps, long long* stores) {
+    if (!ctx) return PNOP_ERR_INVALID_ARG;
+    if (advances) *advances = ctx->st_adv;
+    if (adjoint_steps) *adjoint_steps = ctx->st_adj;
+    if (stores) *stores = ctx->st_store;
+    return PNOP_OK;
+}
+
+int pnop_apply(pnop_ctx* ctx, int op, const void* a, const void* b, void* out, double t) {
+    return guarded(ctx, [&]() -> int {
+        if (!a || !out || a == out || (b && b == out)) throw Status(PNOP_ERR_INVALID_ARG, "bad arguments");
+        const double2* A = (const double2*)a;
+        const double2* B = (const double2*)b;
+        double2* O = (double2*)out;
+        const Geo& g = ctx->geo;
+        switch (op) {
+            case PNOP_OP_CURL: pnop::launch_curl(g, A, O, ctx->stream); break;
+            case PNOP_OP_NONLINEAR: nonlinear(ctx, A, t, O); break;
+            case PNOP_OP_STAGE:
+                if (!B) throw Status(PNOP_ERR_INVALID_ARG, "stage needs a forcing field");
+                pnop::launch_stage(g, A, B, O, ctx->q, ctx->R, ctx->stream);
+                break;
+            case PNOP_OP_NONLINEAR_T:
+                if (!B) throw Status(PNOP_ERR_INVALID_ARG, "transpose needs a cotangent field");
+                nonlinearT(ctx, A, t, B, O);
+                break;
+            case PNOP_OP_STAGE_T_U: pnop::launch_stageT(g, A, O, 0, ctx->Fb, ctx->q, ctx->R, ctx->stream); break;
+            case PNOP_OP_STAGE_T_F: pnop::launch_stageT(g, A, ctx->ua, 0, O, ctx->q, ctx->R, ctx->stream); break;
+            default: throw Status(PNOP_ERR_INVALID_ARG, "unknown operator");
+        }
+        ck(cudaStreamSynchronize(ctx->stream), "apply");
+        return PNOP_OK;
+    });
+}
+
+int pnop_energy(pnop_ctx* ctx, const void* u, double* E_out) {
+    return guarded(ctx, [&]() -> int {
+        if (!u || !E_out) throw Status(PNOP_ERR_INVALID_ARG, "bad arguments");
+        *E_out = 0.5 * inner_sync(ctx, (const double2*)u, (const double2*)u);
+        return PNOP_OK;
+    });
+}
+
+int pnop_inner(pnop_ctx* ctx, const void* a, const void* b, double* out) {
+    return guarded(ctx, [&]() -> int {
+        if (!a || !b || !out) throw Status(PNOP_ERR_INVALID_ARG, "bad arguments");
+        *out = inner_sync(ctx, (const double2*)a, (const double2*)b);
+        return PNOP_OK;
+    });
+}
+
+}  // extern "C"

@@ -1,0 +1,79 @@
+"""Host-side checks of the C ABI: the library builds, loads, exports every
+declared entry point, validates arguments, and its binomial checkpoint plan
+matches Eq. 2.18 and the brute-force optimum.  No device compute is called."""
+import os
+import re
+
+import pytest
+
+from oracle import pipe_oracle as po
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_2509_10103_gb300 import build
+    build.build()
+    from paper_2509_10103_gb300 import _lib
+    return _lib
+
+
+def declared_entry_points():
+    names = []
+    for h in os.listdir(os.path.join(ROOT, "include")):
+        if h.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", h)).read()
+            names += re.findall(r"^\s*(?:const\s+)?\w+\**\s+\**(pnop_\w+)\s*\(", txt, re.M)
+    return sorted(set(names))
+
+
+def test_every_declared_symbol_is_exported(L):
+    names = declared_entry_points()
+    assert len(names) >= 15
+    for n in names:
+        assert hasattr(L.lib, n), n
+    assert set(names) == set(L.EXPORTS)
+
+
+def test_error_strings(L):
+    for code in (0, -1, -2, -3, -4, -5, -6):
+        assert L.lib.pnop_error_string(code)
+
+
+def test_create_rejects_bad_arguments_before_touching_the_device(L):
+    import ctypes
+    h = ctypes.c_void_p()
+    bad = [
+        L.pnop_grid(4, 16, 32, 10.0, 0.0),      # nr too small
+        L.pnop_grid(32, 15, 32, 10.0, 0.0),     # odd ntheta
+        L.pnop_grid(32, 16, 32, -1.0, 0.0),     # negative length
+    ]
+    p = L.pnop_params(2000.0, 8.0, 1.0, 0.01, 0.0, 0, 8, 0)
+    for g in bad:
+        assert L.lib.pnop_create(ctypes.byref(g), ctypes.byref(p), None, ctypes.byref(h)) == -1
+        assert not h.value
+    g = L.pnop_grid(32, 16, 32, 10.0, 0.0)
+    for q in (L.pnop_params(-1.0, 8.0, 1.0, 0.01, 0.0, 0, 8, 0), L.pnop_params(2000.0, 8.0, 1.0, 0.0, 0.0, 0, 8, 0),
+              L.pnop_params(2000.0, 8.0, 1.0, 0.01, 0.0, 7, 8, 0), L.pnop_params(2000.0, 8.0, 1.0, 0.01, 0.0, 0, 0, 0)):
+        assert L.lib.pnop_create(ctypes.byref(g), ctypes.byref(q), None, ctypes.byref(h)) == -1
+    # physical sizes that are not 2^a 3^b: ntheta = 10 -> 15 points
+    g = L.pnop_grid(32, 10, 32, 10.0, 0.0)
+    assert L.lib.pnop_create(ctypes.byref(g), ctypes.byref(p), None, ctypes.byref(h)) == -6
+
+
+def test_revolve_plan_matches_eq_2_18_and_bruteforce(L):
+    C = po.revolve_advances_dp(120, 7)
+    for n in range(1, 121):
+        for s in range(1, 8):
+            adv, stores = L.pnop_revolve_counts(n, s)
+            assert adv == C[n, s] == po.revolve_advances(n, s), (n, s)
+            assert stores <= max(0, n - 1)
+
+
+def test_revolve_plan_large_horizons(L):
+    # workloads of the paper's size: 4000 steps / 32 slots, 19635 steps / budgets
+    for n, s in ((4000, 32), (1000, 4), (1000, 8), (1000, 16), (1000, 64), (19635, 40)):
+        adv, _ = L.pnop_revolve_counts(n, s)
+        assert adv == po.revolve_advances(n, s)
+    assert L.pnop_revolve_counts(4000, 32)[0] == 11405
