@@ -1,0 +1,435 @@
+#!/usr/bin/env python
+"""Throughput of the checkpointed forward+adjoint gradient on one GB300.
+
+Workload (the metric's 64x64x256 configuration): nr=64 radial points,
+|m| <= 31, 0 <= k <= 127 (96 x 384 physical, 3/2 rule), Lz = 100 radii,
+Re = 2000 (mean), Wo = 8, A = 1, dt = 0.0025, start at tau0 = T/4
+(deceleration, T = 2 pi Re / Wo^2), oblique m = +-1 seed (axial length 1.25
+radii) plus a weak random background scaled to E0 = 1e-5.  One bench step is
+one pnop_gradient over a horizon of H time steps (default 100) with a
+binomial checkpoint budget of s snapshots (default 10): forward sweep,
+recomputation from checkpoints and H adjoint steps.  The metric is
+forward+adjoint time steps per second (H x steps / time), reported for the
+mixed path (FP32 transforms and products, FP64 radial solves and inner
+products) as `value`, and for the plain FP64 path under "fp64".
+
+--impl reference times the FP64 CPU oracle on a bounded sample of the same
+workload on the host cores (the baseline of this build).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+# ------------------------------------------------------------------ workload
+NR, NTHETA, NZ = 64, 64, 256
+LZ, RE, WO, AMP, DT = 100.0, 2000.0, 8.0, 1.0, 0.0025
+TAU0 = 0.25 * 2.0 * math.pi * RE / WO ** 2
+E0 = 1e-5
+M, K = NTHETA // 2 - 1, NZ // 2 - 1
+NT, NZP = 3 * (M + 1), 3 * (K + 1)
+S_VALUES = NR * (2 * M + 1) * (K + 1)
+FIELD_BYTES = 3 * S_VALUES * 16
+L2_BYTES = 129 * 2 ** 20
+
+FP64_FLOPS_PER_CLK_SM = 4      # 2 FP64 FMA lanes per SM (GB300)
+FP32_FLOPS_PER_CLK_SM = 256    # 128 FP32 FMA lanes per SM
+N_SM = 152
+
+
+def workload_name(h, s):
+    return (f"checkpointed fwd+adj gradient, nr={NR} ntheta={NTHETA} nz={NZ} (|m|<={M}, |k|<={K}, {NT}x{NZP} physical),"
+            f" Lz={LZ:g}, Re={RE:g}, Wo={WO:g}, A={AMP:g}, dt={DT:g}, tau0=T/4, horizon {h} steps, {s} snapshots,"
+            f" oblique m=+-1 seed at E0={E0:g}")
+
+
+def make_u0(r):
+    from paper_2509_10103_gb300 import synth
+    return synth.oblique_field(r, M, K, LZ, seed=0)
+
+
+# ------------------------------------------------------------------ peaks
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def alu_peak_tflops(per_clk_sm, sm_max_mhz):
+    return N_SM * per_clk_sm * sm_max_mhz * 1e6 / 1e12
+
+
+# ------------------------------------------------------------------ algorithmic work per unit
+def fft_flops(n, real=False):
+    f = 5.0 * n * math.log2(n)
+    return 0.5 * f if real else f
+
+
+def class_work(cls, units, mixed):
+    """(flops, bytes) of `units` work units of a kernel class (algorithmic, ideal reuse)."""
+    cz = 8 if mixed else 16  # complex element bytes of transform intermediates
+    if cls == "synth_theta":   # one column: Nm spectral FP64 in, Nt out
+        return units * fft_flops(NT), units * ((2 * M + 1) * 16 + NT * cz)
+    if cls == "anal_theta":
+        return units * fft_flops(NT), units * (NT * cz + (2 * M + 1) * 16)
+    if cls in ("zpass_fwd", "zpass_adj"):
+        nin, nout = (6, 3) if cls == "zpass_fwd" else (9, 6)
+        fl = (nin + nout) * fft_flops(NZP, real=True) + (9 if cls == "zpass_fwd" else 18) * NZP
+        return units * fl, units * (nin + nout) * (K + 1) * cz
+    if cls == "radial_solve":  # one system: nr rows, 4 + up to 8 off-diagonals + scale, complex rhs
+        fl = NR * (4 + 8 + 1) * 4.0
+        by = NR * (13 * 8 + 4 * 16)
+        return units * fl, units * by
+    return None, None
+
+
+def traffic_table():
+    """Measured DRAM bytes per launch from the committed ncu summaries."""
+    out = {}
+    p = os.path.join(ROOT, "profiles", "dram_traffic_per_launch.txt")
+    if os.path.exists(p):
+        for line in open(p):
+            parts = line.split()
+            if len(parts) == 4 and parts[0] == "traffic":
+                out[(parts[1], parts[2])] = float(parts[3])
+    return out
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.idx = str(gpu_index)
+        try:
+            import torch
+            u = str(torch.cuda.get_device_properties(gpu_index).uuid)
+            self.idx = u if u.startswith("GPU-") else "GPU-" + u
+        except Exception:
+            pass
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.Q}", "--format=csv",
+                                       "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+        time.sleep(0.3)
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        self.p.wait(timeout=10)
+        self.f.flush()
+        self.f.seek(0)
+        rows = [l.strip() for l in self.f.read().splitlines() if l.strip() and not l.startswith("index")]
+        os.unlink(self.f.name)
+        sm, mx, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for r in rows:
+            c = [x.strip() for x in r.split(",")]
+            if len(c) < 9:
+                continue
+            try:
+                sm.append(float(c[1].split()[0]))
+                mx.append(float(c[2].split()[0]))
+            except ValueError:
+                continue
+            for n, v in zip(names, c[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ distributed helpers
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if os.environ.get("PNOP_BENCH_GLOO") is None else "gloo")
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, ws):
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ------------------------------------------------------------------ GPU arm
+def time_gradient(L, torch, precision, steps, warmup, H, snaps, ws, rank, sampler=None):
+    ctx = L.Context(NR, NTHETA, NZ, LZ, RE, DT, WO, AMP, TAU0, precision, snaps)
+    import numpy as np
+    r = np.array(ctx.pnop_grid_points())
+    u0 = torch.from_numpy(make_u0(r)).to("cuda")
+    g = torch.zeros(ctx.shape, dtype=torch.complex128, device="cuda")
+    horizon = H * DT
+    # warm-up; the first warm-up step times every kernel class to find the dominant one
+    ctx.pnop_profile((1 << len(L.KCLASSES)) - 1)
+    gain = ctx.pnop_gradient(u0, E0, horizon, g)
+    prof = ctx.pnop_profile_read()
+    for _ in range(max(0, warmup - 1)):
+        gain = ctx.pnop_gradient(u0, E0, horizon, g)
+    dom = max(prof, key=lambda k: prof[k][0])
+    ctx.pnop_profile(1 << L.KCLASSES.index(dom))
+    barrier(ws)
+    torch.cuda.synchronize()
+    if sampler:
+        sampler.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        gain = ctx.pnop_gradient(u0, E0, horizon, g)
+    e1.record()
+    torch.cuda.synchronize()
+    clocks = sampler.stop() if sampler else None
+    barrier(ws)
+    ms = e0.elapsed_time(e1)
+    tprof = ctx.pnop_profile_read()
+    adv, nadj, stores = ctx.pnop_gradient_stats()
+    ctx.close()
+    return {"ms": ms, "gain": gain, "warm_profile": prof, "timed_profile": tprof, "dominant": dom,
+            "advances": adv, "adjoint_steps": nadj, "stores": stores, "clocks": clocks}
+
+
+def time_e2e(L, torch, precision, steps, warmup, H, snaps):
+    ctx = L.Context(NR, NTHETA, NZ, LZ, RE, DT, WO, AMP, TAU0, precision, snaps)
+    import numpy as np
+    r = np.array(ctx.pnop_grid_points())
+    u0h = torch.from_numpy(make_u0(r)).pin_memory()
+    gh = torch.zeros(ctx.shape, dtype=torch.complex128).pin_memory()
+    for _ in range(warmup):
+        ctx.pnop_gradient_host(u0h, E0, H * DT, gh)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        ctx.pnop_gradient_host(u0h, E0, H * DT, gh)
+    torch.cuda.synchronize()
+    s = time.perf_counter() - t0
+    ctx.close()
+    return s
+
+
+def roofline(L, res, mixed, peaks, pk_src):
+    cls = res["dominant"]
+    ms, launches, units = res["timed_profile"][cls]
+    fl, by = class_work(cls, units, mixed)
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    smx = peaks.get("sm_max_mhz", 2070.0)
+    if fl is None or launches == 0 or ms <= 0:
+        return None
+    fp_peak = alu_peak_tflops(FP32_FLOPS_PER_CLK_SM if (mixed and cls not in ("radial_solve",)) else
+                              FP64_FLOPS_PER_CLK_SM, smx)
+    t = ms / 1e3
+    ach_f = fl / t / 1e12
+    ach_b = by / t / 1e9
+    frac_f, frac_b = ach_f / fp_peak, ach_b / hbm
+    tt = traffic_table().get((cls, "mixed" if mixed else "fp64"))
+    base = {"kernel": cls, "launches": launches, "avg_launch_us": ms * 1e3 / launches,
+            "traffic": tt}
+    if frac_f >= frac_b:
+        base.update({"bound": "alu", "achieved": ach_f, "peak": fp_peak, "unit": "TFLOP/s", "frac": frac_f,
+                     "peak_source": f"derived: {N_SM} SMs x {FP32_FLOPS_PER_CLK_SM if fp_peak > 10 else FP64_FLOPS_PER_CLK_SM} flop/clk x {smx:g} MHz",
+                     "hbm_frac": frac_b})
+    else:
+        base.update({"bound": "hbm", "achieved": ach_b, "peak": hbm, "unit": "GB/s", "frac": frac_b,
+                     "peak_source": f"{pk_src} (MEASURED_PEAKS.json hbm_gbs)" if pk_src == "measured" else "fallback",
+                     "alu_frac": frac_f})
+    return base
+
+
+# ------------------------------------------------------------------ CPU oracle (baseline / reference arm)
+ORACLE_SAMPLE_CODE = r"""
+import os, sys, time, json, math
+sys.path.insert(0, sys.argv[1])
+import numpy as np
+from oracle import pipe_oracle as po
+import bench as B
+planes, modes = int(sys.argv[2]), int(sys.argv[3])
+o = po.Oracle(po.Params(nr=B.NR, M=B.M, K=B.K, Lz=B.LZ, Re=B.RE, dt=B.DT, Wo=B.WO, A=B.AMP))
+u = o.scale_to(B.make_u0(o.r), B.E0)
+t = B.TAU0
+T = {}
+t0 = time.perf_counter(); w = o.curl(u); T['curl'] = time.perf_counter() - t0
+sl = slice(0, planes)
+t0 = time.perf_counter()
+up = np.stack([o.synth(c[sl]) for c in u]); wp = np.stack([o.synth(c[sl]) for c in w])
+n = np.stack([o.analysis(c) for c in np.cross(up, wp, axis=0)])
+T['nl_planes'] = time.perf_counter() - t0
+t0 = time.perf_counter()
+gb = np.stack([o.analysisT(c) for c in n])
+upb = np.cross(wp, gb, axis=0); wpb = np.cross(gb, up, axis=0)
+ub = np.stack([o.synthT(c) for c in upb]); wb = np.stack([o.synthT(c) for c in wpb])
+T['nlT_planes'] = time.perf_counter() - t0
+rng = np.random.default_rng(0)
+sel = [(int(rng.integers(-B.M, B.M + 1)), int(rng.integers(0, B.K + 1))) for _ in range(modes)]
+t0 = time.perf_counter()
+for (m, k) in sel: o.mode_maps(m, k)
+T['maps_build'] = time.perf_counter() - t0
+t0 = time.perf_counter()
+for rep in range(10):
+    for (m, k) in sel:
+        Su, SF = o.mode_maps(m, k)
+        v = u[:, :, m + B.M, k].reshape(-1); Su @ v + SF @ v
+T['stage_apply'] = (time.perf_counter() - t0) / 10
+scale_p = B.NR / planes
+scale_m = (2 * B.M + 1) * (B.K + 1) / modes
+nl = T['curl'] + T['nl_planes'] * scale_p
+nlT = 2 * T['curl'] + T['nlT_planes'] * scale_p
+st = T['stage_apply'] * scale_m
+# oracle gradient per time step (store-all): forward 2 NL + 2 stages; adjoint 1 NL + 1 stage
+# (re-run predictor) + 2 transposed NL + 2 transposed stages (two matvecs each)
+per_step = 3 * nl + 2 * nlT + 3 * st + 2 * 2 * st
+T['per_step_s'] = per_step
+T['maps_build_total_s'] = T['maps_build'] * scale_m
+print(json.dumps(T))
+"""
+
+
+def oracle_sample(planes=4, modes=16):
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    p = subprocess.run([sys.executable, "-c", ORACLE_SAMPLE_CODE, ROOT, str(planes), str(modes)],
+                       stdout=subprocess.PIPE, stderr=subprocess.PIPE, text=True, env=env, timeout=900)
+    if p.returncode != 0:
+        raise RuntimeError("oracle sample failed: " + p.stderr[-2000:])
+    return json.loads(p.stdout.strip().splitlines()[-1])
+
+
+def oracle_sample_desc(planes, modes):
+    return (f"FP64 numpy oracle, 1 thread: curl + 3/2-padded transforms/products on {planes} of {NR} radial planes"
+            f" (x{NR // planes}), stage maps applied on {modes} random (m,k) modes (x{(2 * M + 1) * (K + 1) // modes}),"
+            f" combined as 3 N + 2 N^T + 3 S + 2 S^T per fwd+adj step (store-all sweep); map construction excluded")
+
+
+def reference_main(args):
+    ws, rank, _ = int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")), 0
+    if rank != 0:
+        return 0
+    planes, modes = 8, 32
+    for _ in range(args.warmup):
+        oracle_sample(planes, modes)
+    ts = []
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        ts.append(oracle_sample(planes, modes)["per_step_s"])
+    wall = time.perf_counter() - t0
+    per = statistics.median(ts)
+    val = 1.0 / per
+    line = {"impl": "reference", "metric": "fwd+adj steps/s at 64x64x256", "value": val, "unit": "steps/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": per * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": workload_name(args.horizon_steps, args.snaps), "sample": "bounded oracle sample"},
+            "cpu_baseline": {"value": val, "unit": "steps/s", "cores": 1, "kind": "oracle",
+                             "sample": oracle_sample_desc(planes, modes)},
+            "e2e": {"value": val, "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "wall_s": wall}
+    print(json.dumps(line))
+    return 0
+
+
+# ------------------------------------------------------------------ main
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--horizon-steps", type=int, default=100)
+    ap.add_argument("--snaps", type=int, default=10)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return reference_main(args)
+    if args.warmup < 3:
+        print("warning: fewer than 3 warm-up steps", file=sys.stderr)
+
+    import torch
+    ws, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    from paper_2509_10103_gb300 import build
+    if rank == 0:
+        build.build()
+    barrier(ws)
+    from paper_2509_10103_gb300 import _lib as L
+
+    peaks, pk_src = load_peaks()
+    H, s = args.horizon_steps, args.snaps
+    sampler = ClockSampler(local) if rank == 0 else None
+    mix = time_gradient(L, torch, L.PNOP_MIXED, args.steps, args.warmup, H, s, ws, rank, sampler)
+    ms = max_over_ranks(mix["ms"], ws)
+    value = H * args.steps * ws / (ms / 1e3)
+    fp64 = None
+    if not args.no_fp64:
+        f = time_gradient(L, torch, L.PNOP_FP64, args.steps, args.warmup, H, s, ws, rank, None)
+        fms = max_over_ranks(f["ms"], ws)
+        fp64 = {"value": H * args.steps * ws / (fms / 1e3), "unit": "steps/s", "ms_per_step": fms / args.steps,
+                "gain": f["gain"], "dtype": "f64", "roofline": roofline(L, f, False, peaks, pk_src),
+                "kernels_ms_per_step": {k: v[0] for k, v in f["warm_profile"].items()}}
+    e2e_s = time_e2e(L, torch, L.PNOP_MIXED, args.steps, args.warmup, H, s)
+    e2e_s = max_over_ranks(e2e_s, ws)
+    if rank != 0:
+        return 0
+    launches = sum(v[1] for v in mix["timed_profile"].values())
+    out = {
+        "metric": "fwd+adj steps/s at 64x64x256, mixed vs FP64 on 1 GB300",
+        "value": value, "unit": "steps/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": workload_name(H, s), "horizon_steps": H, "snap_budget": s,
+                   "advances_per_gradient": mix["advances"], "adjoint_steps_per_gradient": mix["adjoint_steps"],
+                   "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
+                   "l2": f"inputs and working set > L2 (state {FIELD_BYTES / 2**20:.1f} MiB x >20 buffers + transform"
+                         " scratch); no flush"},
+        "gain": mix["gain"],
+        "roofline": roofline(L, mix, True, peaks, pk_src),
+        "kernels_ms_per_step": {k: v[0] for k, v in mix["warm_profile"].items()},
+        "fp64": fp64,
+        "speedup_mixed_over_fp64": (value / fp64["value"]) if fp64 else None,
+        "e2e": {"value": H * args.steps * ws / e2e_s, "unit": "steps/s", "h2d_bytes_per_step": FIELD_BYTES,
+                "d2h_bytes_per_step": FIELD_BYTES + 24},
+        "gpu_launches": launches,
+        "clocks": mix["clocks"],
+    }
+    if not args.no_cpu_baseline and ws == 1:
+        planes, modes = 16, 64
+        smp = oracle_sample(planes, modes)
+        out["cpu_baseline"] = {"value": 1.0 / smp["per_step_s"], "unit": "steps/s", "cores": 1, "kind": "oracle",
+                               "sample": oracle_sample_desc(planes, modes)}
+    print(json.dumps(out))
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -153,6 +153,30 @@ enum {
 };
 int pnop_apply(pnop_ctx* ctx, int op, const void* a, const void* b, void* out, double t);
 
+/* Kernel classes for launch counting and device timing. */
+enum {
+    PNOP_K_SYNTH_THETA = 0,  /* zero-padded inverse theta FFTs (units: FFT columns) */
+    PNOP_K_ZPASS_FWD = 1,    /* z FFTs + u x w products (units: (j, theta) rows) */
+    PNOP_K_ZPASS_ADJ = 2,    /* z FFTs + transposed products (units: rows) */
+    PNOP_K_ANAL_THETA = 3,   /* forward theta FFTs + truncation (units: FFT columns) */
+    PNOP_K_SPECTRAL = 4,     /* curl, base-flow terms and their transposes (units: modes x r) */
+    PNOP_K_RADIAL_BAND = 5,  /* banded radial matvecs, +/- basis, influence (units: values) */
+    PNOP_K_RADIAL_SOLVE = 6, /* banded LU solves (units: systems of nr unknowns) */
+    PNOP_K_ELEMENTWISE = 7,  /* axpby, energy weights (units: values) */
+    PNOP_K_REDUCE = 8,       /* inner-product reductions (units: values) */
+    PNOP_K_NCLASS = 9
+};
+
+/* Start counting (and, for the classes set in class_mask, timing with CUDA
+ * events on the context stream around each launch); resets the counters.
+ * class_mask = 0 counts launches without timing. */
+int pnop_profile(pnop_ctx* ctx, unsigned class_mask);
+
+/* Read the counters since pnop_profile: per class device milliseconds (timed
+ * classes only), kernel launches and work units (arrays of PNOP_K_NCLASS;
+ * any may be NULL).  Synchronises the stream. */
+int pnop_profile_read(pnop_ctx* ctx, double* ms, long long* launches, double* units);
+
 /* E = (1/2) <u, u> (Eq. 2.1–2.2) of a device field; written to *E_out. */
 int pnop_energy(pnop_ctx* ctx, const void* u, double* E_out);
 

@@ -17,12 +17,14 @@ LIB_PATH = os.path.join(HERE, "libpnop.so")
 PNOP_OK = 0
 PNOP_FP64 = 0
 PNOP_MIXED = 1
+KCLASSES = ("synth_theta", "zpass_fwd", "zpass_adj", "anal_theta", "spectral", "radial_band", "radial_solve",
+            "elementwise", "reduce")
 OP_CURL, OP_NONLINEAR, OP_STAGE, OP_NONLINEAR_T, OP_STAGE_T_U, OP_STAGE_T_F = range(6)
 
 EXPORTS = (
     "pnop_create", "pnop_set_base_flow", "pnop_dims", "pnop_grid_points", "pnop_step_forward",
     "pnop_step_adjoint", "pnop_gradient", "pnop_gradient_host", "pnop_gradient_stats", "pnop_energy",
-    "pnop_inner", "pnop_apply", "pnop_revolve_counts", "pnop_last_error", "pnop_error_string", "pnop_destroy",
+    "pnop_inner", "pnop_apply", "pnop_profile", "pnop_profile_read", "pnop_revolve_counts", "pnop_last_error", "pnop_error_string", "pnop_destroy",
 )
 
 
@@ -52,6 +54,8 @@ def _load():
         "pnop_energy": (c_int, [c_void_p, c_void_p, POINTER(c_double)]),
         "pnop_inner": (c_int, [c_void_p, c_void_p, c_void_p, POINTER(c_double)]),
         "pnop_apply": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_void_p, c_double]),
+        "pnop_profile": (c_int, [c_void_p, ctypes.c_uint]),
+        "pnop_profile_read": (c_int, [c_void_p, POINTER(c_double), POINTER(c_longlong), POINTER(c_double)]),
         "pnop_revolve_counts": (c_int, [c_int, c_int, POINTER(c_longlong), POINTER(c_longlong)]),
         "pnop_last_error": (c_char_p, [c_void_p]),
         "pnop_error_string": (c_char_p, [c_int]),
@@ -161,6 +165,15 @@ class Context:
     def pnop_apply(self, op, a, b, out, t=0.0):
         bp = c_void_p(_ptr(b)) if b is not None else c_void_p(0)
         self._check(lib.pnop_apply(self._h, op, c_void_p(_ptr(a)), bp, c_void_p(_ptr(out)), t), "apply")
+
+    def pnop_profile(self, class_mask=0):
+        self._check(lib.pnop_profile(self._h, class_mask), "profile")
+
+    def pnop_profile_read(self):
+        n = len(KCLASSES)
+        ms, la, un = (c_double * n)(), (c_longlong * n)(), (c_double * n)()
+        self._check(lib.pnop_profile_read(self._h, ms, la, un), "profile_read")
+        return {k: (ms[i], la[i], un[i]) for i, k in enumerate(KCLASSES)}
 
     def pnop_energy(self, u):
         e = c_double()

@@ -855,29 +855,49 @@ template void launch_zpass<double2>(const Geo&, int, const double2*, double2*, c
 template void launch_zpass<float2>(const Geo&, int, const float2*, float2*, const ZScales&, const Twiddles&,
                                    cudaStream_t);
 
-void launch_stage(const Geo& g, const double2* u, const double2* F, double2* out, double2* q, double2* R,
-                  cudaStream_t s) {
-    const size_t S = S_of(g);
-    const int nmode = g.nm * g.nk;
-    k_stage_div<<<nblk(S, 256), 256, 0, s>>>(g, F, q);
-    k_stage_psolve<<<nblk(nmode, 64), 64, 0, s>>>(g, q);
-    k_stage_rhs<<<nblk(S, 256), 256, 0, s>>>(g, u, F, q, R);
-    k_stage_hsolve<<<nblk(3 * (size_t)nmode, 64), 64, 0, s>>>(g, R);
-    k_stage_finish<<<nblk(S, 256), 256, 0, s>>>(g, R, out);
-    check_launch("stage");
+void launch_stage_div(const Geo& g, const double2* F, double2* q, cudaStream_t s) {
+    k_stage_div<<<nblk(S_of(g), 256), 256, 0, s>>>(g, F, q);
+    check_launch("stage_div");
 }
-
-void launch_stageT(const Geo& g, const double2* ubn, double2* ub, int acc, double2* Fb, double2* q, double2* R,
-                   cudaStream_t s) {
-    const size_t S = S_of(g);
-    const int nmode = g.nm * g.nk;
-    k_stageT_finish<<<nblk(nmode, 64), 64, 0, s>>>(g, ubn, R);
-    k_stageT_hsolve<<<nblk(3 * (size_t)nmode, 64), 64, 0, s>>>(g, R);
-    k_stageT_rhs<<<nblk(S, 256), 256, 0, s>>>(g, R, ub, acc, Fb);
-    k_stageT_qbar<<<nblk(S, 256), 256, 0, s>>>(g, Fb, q);
-    k_stageT_psolve<<<nblk(nmode, 64), 64, 0, s>>>(g, q);
-    k_stageT_div<<<nblk(S, 256), 256, 0, s>>>(g, q, Fb);
-    check_launch("stageT");
+void launch_stage_psolve(const Geo& g, double2* q, cudaStream_t s) {
+    k_stage_psolve<<<nblk((size_t)g.nm * g.nk, 64), 64, 0, s>>>(g, q);
+    check_launch("stage_psolve");
+}
+void launch_stage_rhs(const Geo& g, const double2* u, const double2* F, const double2* p, double2* R, cudaStream_t s) {
+    k_stage_rhs<<<nblk(S_of(g), 256), 256, 0, s>>>(g, u, F, p, R);
+    check_launch("stage_rhs");
+}
+void launch_stage_hsolve(const Geo& g, double2* R, cudaStream_t s) {
+    k_stage_hsolve<<<nblk(3 * (size_t)g.nm * g.nk, 64), 64, 0, s>>>(g, R);
+    check_launch("stage_hsolve");
+}
+void launch_stage_finish(const Geo& g, const double2* R, double2* out, cudaStream_t s) {
+    k_stage_finish<<<nblk(S_of(g), 256), 256, 0, s>>>(g, R, out);
+    check_launch("stage_finish");
+}
+void launch_stageT_finish(const Geo& g, const double2* ubn, double2* R, cudaStream_t s) {
+    k_stageT_finish<<<nblk((size_t)g.nm * g.nk, 64), 64, 0, s>>>(g, ubn, R);
+    check_launch("stageT_finish");
+}
+void launch_stageT_hsolve(const Geo& g, double2* R, cudaStream_t s) {
+    k_stageT_hsolve<<<nblk(3 * (size_t)g.nm * g.nk, 64), 64, 0, s>>>(g, R);
+    check_launch("stageT_hsolve");
+}
+void launch_stageT_rhs(const Geo& g, const double2* R, double2* ub, int acc, double2* Fb, cudaStream_t s) {
+    k_stageT_rhs<<<nblk(S_of(g), 256), 256, 0, s>>>(g, R, ub, acc, Fb);
+    check_launch("stageT_rhs");
+}
+void launch_stageT_qbar(const Geo& g, const double2* Fb, double2* q, cudaStream_t s) {
+    k_stageT_qbar<<<nblk(S_of(g), 256), 256, 0, s>>>(g, Fb, q);
+    check_launch("stageT_qbar");
+}
+void launch_stageT_psolve(const Geo& g, double2* q, cudaStream_t s) {
+    k_stageT_psolve<<<nblk((size_t)g.nm * g.nk, 64), 64, 0, s>>>(g, q);
+    check_launch("stageT_psolve");
+}
+void launch_stageT_div(const Geo& g, const double2* z, double2* Fb, cudaStream_t s) {
+    k_stageT_div<<<nblk(S_of(g), 256), 256, 0, s>>>(g, z, Fb);
+    check_launch("stageT_div");
 }
 
 void launch_axpby(size_t n, double a, const double2* x, double b, const double2* y, double2* out, cudaStream_t s) {

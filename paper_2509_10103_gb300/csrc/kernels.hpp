@@ -63,13 +63,21 @@ void launch_zpass(const Geo& g, int mode, const T2* Y, T2* Z, const ZScales& sc,
 template <class T2>
 void launch_anal_theta(const Geo& g, const FieldPtrs& f, int nfield, const T2* Z, const Twiddles& tw, cudaStream_t s);
 
-// ---- radial stage (forward) ----
-// out = S(u, F): pressure projection, Helmholtz solves, influence and flux corrections.
-void launch_stage(const Geo& g, const double2* u, const double2* F, double2* out, double2* q, double2* R,
-                  cudaStream_t s);
-// Transpose: ub (=, or += when acc) gets S_u^H ubn, Fb gets S_F^H ubn.
-void launch_stageT(const Geo& g, const double2* ubn, double2* ub, int acc, double2* Fb, double2* q, double2* R,
-                   cudaStream_t s);
+// ---- radial stage (forward): out = S(u, F) ----
+// q = div F; p = A_p^{-1} q; R = B u_pm + (F - grad p)_pm; R = A_v^{-1} R;
+// out = back to (r, theta, z) + influence / flux corrections (Section 2.4).
+void launch_stage_div(const Geo& g, const double2* F, double2* q, cudaStream_t s);
+void launch_stage_psolve(const Geo& g, double2* q, cudaStream_t s);
+void launch_stage_rhs(const Geo& g, const double2* u, const double2* F, const double2* p, double2* R, cudaStream_t s);
+void launch_stage_hsolve(const Geo& g, double2* R, cudaStream_t s);
+void launch_stage_finish(const Geo& g, const double2* R, double2* out, cudaStream_t s);
+// ---- radial stage (transpose): ub (=, or += when acc) S_u^H ubn, Fb = S_F^H ubn ----
+void launch_stageT_finish(const Geo& g, const double2* ubn, double2* R, cudaStream_t s);
+void launch_stageT_hsolve(const Geo& g, double2* R, cudaStream_t s);
+void launch_stageT_rhs(const Geo& g, const double2* R, double2* ub, int acc, double2* Fb, cudaStream_t s);
+void launch_stageT_qbar(const Geo& g, const double2* Fb, double2* q, cudaStream_t s);
+void launch_stageT_psolve(const Geo& g, double2* q, cudaStream_t s);
+void launch_stageT_div(const Geo& g, const double2* z, double2* Fb, cudaStream_t s);
 
 // ---- elementwise / reductions ----
 void launch_axpby(size_t n, double a, const double2* x, double b, const double2* y, double2* out, cudaStream_t s);

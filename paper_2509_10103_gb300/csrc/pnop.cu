@@ -75,6 +75,14 @@ struct pnop_ctx {
     // gradient sweep state
     long long g_nsteps = 0;
     bool g_terminal = false;
+    // per-class launch counters, work units and optional event timing
+    unsigned prof_mask = 0;
+    std::vector<cudaEvent_t> ev;     // pairs (start, stop)
+    std::vector<int> ev_cls;         // class of each recorded pair
+    size_t ev_used = 0;
+    double prof_ms[PNOP_K_NCLASS] = {};
+    long long launches[PNOP_K_NCLASS] = {};
+    double units[PNOP_K_NCLASS] = {};
 
     size_t S() const { return (size_t)h.d.nr * h.d.nm * h.d.nk; }
     size_t field_bytes() const { return 3 * S() * sizeof(double2); }
@@ -154,13 +162,101 @@ void upload_operators(pnop_ctx* c) {
 
 bool mixed(const pnop_ctx* c) { return c->prm.precision == PNOP_MIXED; }
 
+void prof_flush(pnop_ctx* c) {
+    if (!c->ev_used) return;
+    ck(cudaEventSynchronize(c->ev[2 * c->ev_used - 1]), "profile sync");
+    for (size_t i = 0; i < c->ev_used; ++i) {
+        float ms = 0;
+        ck(cudaEventElapsedTime(&ms, c->ev[2 * i], c->ev[2 * i + 1]), "profile elapsed");
+        c->prof_ms[c->ev_cls[i]] += ms;
+    }
+    c->ev_used = 0;
+}
+
+// Launch `nk` kernels of class `cls` doing `units` work units; bracket them
+// with CUDA events on the context stream when that class is being timed.
+template <class F> void run(pnop_ctx* c, int cls, int nk, double units, F&& f) {
+    c->launches[cls] += nk;
+    c->units[cls] += units;
+    if (!(c->prof_mask & (1u << cls))) {
+        f();
+        return;
+    }
+    const size_t pool = 8192;
+    if (c->ev.empty()) {
+        c->ev.resize(2 * pool);
+        c->ev_cls.resize(pool);
+        for (auto& e : c->ev) ck(cudaEventCreate(&e), "event create");
+    }
+    if (c->ev_used == pool) prof_flush(c);
+    ck(cudaEventRecord(c->ev[2 * c->ev_used], c->stream), "event record");
+    f();
+    ck(cudaEventRecord(c->ev[2 * c->ev_used + 1], c->stream), "event record");
+    c->ev_cls[c->ev_used++] = cls;
+}
+
+double nmodes(const pnop_ctx* c) { return (double)c->h.d.nm * c->h.d.nk; }
+
+// out = S(u, F), one predictor-corrector stage (Section 2.4)
+void stage(pnop_ctx* c, const double2* u, const double2* F, double2* out) {
+    const Geo& g = c->geo;
+    cudaStream_t s = c->stream;
+    const double S = (double)c->S();
+    run(c, PNOP_K_RADIAL_BAND, 1, S, [&] { pnop::launch_stage_div(g, F, c->q, s); });
+    run(c, PNOP_K_RADIAL_SOLVE, 1, nmodes(c), [&] { pnop::launch_stage_psolve(g, c->q, s); });
+    run(c, PNOP_K_RADIAL_BAND, 1, 3 * S, [&] { pnop::launch_stage_rhs(g, u, F, c->q, c->R, s); });
+    run(c, PNOP_K_RADIAL_SOLVE, 1, 3 * nmodes(c), [&] { pnop::launch_stage_hsolve(g, c->R, s); });
+    run(c, PNOP_K_RADIAL_BAND, 1, 3 * S, [&] { pnop::launch_stage_finish(g, c->R, out, s); });
+}
+
+// ub (=, or += when acc) S_u^H ubn ; Fb = S_F^H ubn
+void stageT(pnop_ctx* c, const double2* ubn, double2* ub, int acc, double2* Fb) {
+    const Geo& g = c->geo;
+    cudaStream_t s = c->stream;
+    const double S = (double)c->S();
+    run(c, PNOP_K_RADIAL_BAND, 1, 3 * S, [&] { pnop::launch_stageT_finish(g, ubn, c->R, s); });
+    run(c, PNOP_K_RADIAL_SOLVE, 1, 3 * nmodes(c), [&] { pnop::launch_stageT_hsolve(g, c->R, s); });
+    run(c, PNOP_K_RADIAL_BAND, 1, 3 * S, [&] { pnop::launch_stageT_rhs(g, c->R, ub, acc, Fb, s); });
+    run(c, PNOP_K_RADIAL_BAND, 1, S, [&] { pnop::launch_stageT_qbar(g, Fb, c->q, s); });
+    run(c, PNOP_K_RADIAL_SOLVE, 1, nmodes(c), [&] { pnop::launch_stageT_psolve(g, c->q, s); });
+    run(c, PNOP_K_RADIAL_BAND, 1, S, [&] { pnop::launch_stageT_div(g, c->q, Fb, s); });
+}
+
+void axpby(pnop_ctx* c, double a, const double2* x, double b, const double2* y, double2* out) {
+    const size_t n = 3 * c->S();
+    run(c, PNOP_K_ELEMENTWISE, 1, (double)n, [&] { pnop::launch_axpby(n, a, x, b, y, out, c->stream); });
+}
+void weight(pnop_ctx* c, const double2* x, double2* out, int divide) {
+    run(c, PNOP_K_ELEMENTWISE, 1, 3.0 * c->S(), [&] { pnop::launch_weight(c->geo, x, out, divide, c->stream); });
+}
+void inner_dev(pnop_ctx* c, const double2* a, const double2* b, double* dst) {
+    run(c, PNOP_K_REDUCE, 2, 3.0 * c->S(), [&] { pnop::launch_inner(c->geo, a, b, c->partial, dst, c->stream); });
+}
+
+// theta synthesis / z pass / theta analysis in the context's transform precision
+void transforms(pnop_ctx* c, const pnop::FieldPtrs& f, int nin, int nout, int zmode, const pnop::ZScales& sc) {
+    const Geo& g = c->geo;
+    cudaStream_t s = c->stream;
+    const double cols = (double)g.nr * g.nk, rows = (double)g.nr * g.nt;
+    const int zk = zmode == pnop::ZFWD ? PNOP_K_ZPASS_FWD : PNOP_K_ZPASS_ADJ;
+    if (mixed(c)) {
+        run(c, PNOP_K_SYNTH_THETA, 1, nin * cols, [&] { pnop::launch_synth_theta<float2>(g, f, nin, (float2*)c->Y, c->tw, s); });
+        run(c, zk, 1, rows, [&] { pnop::launch_zpass<float2>(g, zmode, (const float2*)c->Y, (float2*)c->Z, sc, c->tw, s); });
+        run(c, PNOP_K_ANAL_THETA, 1, nout * cols, [&] { pnop::launch_anal_theta<float2>(g, f, nout, (const float2*)c->Z, c->tw, s); });
+    } else {
+        run(c, PNOP_K_SYNTH_THETA, 1, nin * cols, [&] { pnop::launch_synth_theta<double2>(g, f, nin, (double2*)c->Y, c->tw, s); });
+        run(c, zk, 1, rows, [&] { pnop::launch_zpass<double2>(g, zmode, (const double2*)c->Y, (double2*)c->Z, sc, c->tw, s); });
+        run(c, PNOP_K_ANAL_THETA, 1, nout * cols, [&] { pnop::launch_anal_theta<double2>(g, f, nout, (const double2*)c->Z, c->tw, s); });
+    }
+}
+
 // ------------------------------------------------------------------ nonlinear term
 // N = P[I(u) x I(w)] + (U e_z) x w + u x (-dU/dr e_theta), w = curl u  (Eq. 2.5)
 void nonlinear(pnop_ctx* c, const double2* u, double t, double2* N) {
     const Geo& g = c->geo;
     const size_t S = c->S();
     cudaStream_t s = c->stream;
-    pnop::launch_curl(g, u, c->omega, s);
+    run(c, PNOP_K_SPECTRAL, 1, (double)S, [&] { pnop::launch_curl(g, u, c->omega, s); });
     pnop::FieldPtrs f{};
     for (int i = 0; i < 3; ++i) {
         f.in[i] = u + i * S;
@@ -171,17 +267,9 @@ void nonlinear(pnop_ctx* c, const double2* u, double t, double2* N) {
     const double inv_n = 1.0 / ((double)g.nt * g.nzp);
     for (int i = 0; i < 6; ++i) sc.h0[i] = sc.hk[i] = 1.0;
     for (int i = 0; i < 3; ++i) sc.o0[i] = sc.ok[i] = inv_n;
-    if (mixed(c)) {
-        pnop::launch_synth_theta<float2>(g, f, 6, (float2*)c->Y, c->tw, s);
-        pnop::launch_zpass<float2>(g, pnop::ZFWD, (const float2*)c->Y, (float2*)c->Z, sc, c->tw, s);
-        pnop::launch_anal_theta<float2>(g, f, 3, (const float2*)c->Z, c->tw, s);
-    } else {
-        pnop::launch_synth_theta<double2>(g, f, 6, (double2*)c->Y, c->tw, s);
-        pnop::launch_zpass<double2>(g, pnop::ZFWD, (const double2*)c->Y, (double2*)c->Z, sc, c->tw, s);
-        pnop::launch_anal_theta<double2>(g, f, 3, (const double2*)c->Z, c->tw, s);
-    }
+    transforms(c, f, 6, 3, pnop::ZFWD, sc);
     const double ph = c->h.omega * t;
-    pnop::launch_base_add(g, u, c->omega, N, std::cos(ph), std::sin(ph), s);
+    run(c, PNOP_K_SPECTRAL, 1, (double)S, [&] { pnop::launch_base_add(g, u, c->omega, N, std::cos(ph), std::sin(ph), s); });
 }
 
 // ub = (dN/du at u)^T nb  (Euclidean cotangents)
@@ -189,7 +277,7 @@ void nonlinearT(pnop_ctx* c, const double2* u, double t, const double2* nb, doub
     const Geo& g = c->geo;
     const size_t S = c->S();
     cudaStream_t s = c->stream;
-    pnop::launch_curl(g, u, c->omega, s);
+    run(c, PNOP_K_SPECTRAL, 1, (double)S, [&] { pnop::launch_curl(g, u, c->omega, s); });
     pnop::FieldPtrs f{};
     for (int i = 0; i < 3; ++i) {
         f.in[i] = u + i * S;
@@ -211,49 +299,36 @@ void nonlinearT(pnop_ctx* c, const double2* u, double t, const double2* nb, doub
         sc.o0[i] = 1.0;
         sc.ok[i] = 2.0;
     }
-    if (mixed(c)) {
-        pnop::launch_synth_theta<float2>(g, f, 9, (float2*)c->Y, c->tw, s);
-        pnop::launch_zpass<float2>(g, pnop::ZADJ, (const float2*)c->Y, (float2*)c->Z, sc, c->tw, s);
-        pnop::launch_anal_theta<float2>(g, f, 6, (const float2*)c->Z, c->tw, s);
-    } else {
-        pnop::launch_synth_theta<double2>(g, f, 9, (double2*)c->Y, c->tw, s);
-        pnop::launch_zpass<double2>(g, pnop::ZADJ, (const double2*)c->Y, (double2*)c->Z, sc, c->tw, s);
-        pnop::launch_anal_theta<double2>(g, f, 6, (const double2*)c->Z, c->tw, s);
-    }
+    transforms(c, f, 9, 6, pnop::ZADJ, sc);
     const double ph = c->h.omega * t;
-    pnop::launch_baseT_acc(g, nb, ub, c->wb, std::cos(ph), std::sin(ph), s);
-    pnop::launch_curlT_acc(g, c->wb, ub, s);
+    run(c, PNOP_K_SPECTRAL, 1, (double)S, [&] { pnop::launch_baseT_acc(g, nb, ub, c->wb, std::cos(ph), std::sin(ph), s); });
+    run(c, PNOP_K_SPECTRAL, 1, (double)S, [&] { pnop::launch_curlT_acc(g, c->wb, ub, s); });
 }
 
 // ------------------------------------------------------------------ steps
 void fwd_step(pnop_ctx* c, const double2* u, double2* out, double t) {
-    const Geo& g = c->geo;
-    const size_t n = 3 * c->S();
     nonlinear(c, u, t, c->N0);
-    pnop::launch_stage(g, u, c->N0, c->us, c->q, c->R, c->stream);
+    stage(c, u, c->N0, c->us);
     nonlinear(c, c->us, t + c->h.ph.dt, c->N1);
-    pnop::launch_axpby(n, 0.5, c->N0, 0.5, c->N1, c->N1, c->stream);
-    pnop::launch_stage(g, u, c->N1, out, c->q, c->R, c->stream);
+    axpby(c, 0.5, c->N0, 0.5, c->N1, c->N1);
+    stage(c, u, c->N1, out);
 }
 
 // lout = J^T lin (Euclidean cotangents) for the step from state u at time t
 void adj_step(pnop_ctx* c, const double2* u, double t, const double2* lin, double2* lout) {
-    const Geo& g = c->geo;
-    const size_t n = 3 * c->S();
-    cudaStream_t s = c->stream;
     nonlinear(c, u, t, c->N0);
-    pnop::launch_stage(g, u, c->N0, c->us, c->q, c->R, s);
-    pnop::launch_stageT(g, lin, c->ua, 0, c->Fb, c->q, c->R, s);
-    pnop::launch_axpby(n, 0.5, c->Fb, 0.0, nullptr, c->Nb, s);
+    stage(c, u, c->N0, c->us);
+    stageT(c, lin, c->ua, 0, c->Fb);
+    axpby(c, 0.5, c->Fb, 0.0, nullptr, c->Nb);
     nonlinearT(c, c->us, t + c->h.ph.dt, c->Nb, c->ubs);
-    pnop::launch_stageT(g, c->ubs, c->ua, 1, c->N0, c->q, c->R, s);
-    pnop::launch_axpby(n, 1.0, c->N0, 0.5, c->Fb, c->Nb, s);
+    stageT(c, c->ubs, c->ua, 1, c->N0);
+    axpby(c, 1.0, c->N0, 0.5, c->Fb, c->Nb);
     nonlinearT(c, u, t, c->Nb, c->ubs);
-    pnop::launch_axpby(n, 1.0, c->ua, 1.0, c->ubs, lout, s);
+    axpby(c, 1.0, c->ua, 1.0, c->ubs, lout);
 }
 
 double inner_sync(pnop_ctx* c, const double2* a, const double2* b) {
-    pnop::launch_inner(c->geo, a, b, c->partial, c->dscal, c->stream);
+    inner_dev(c, a, b, c->dscal);
     double v = 0;
     ck(cudaMemcpyAsync(&v, c->dscal, sizeof(double), cudaMemcpyDeviceToHost, c->stream), "inner copy");
     ck(cudaStreamSynchronize(c->stream), "inner sync");
@@ -279,8 +354,8 @@ void adjoint_at(pnop_ctx* c, long long n, const double2* state) {
         // terminal state u_N and compatibility condition (Eq. 2.8): cotangent W_hat u_N
         fwd_step(c, state, c->lamB, t);
         ++c->st_adv;
-        pnop::launch_inner(c->geo, c->lamB, c->lamB, c->partial, c->dscal + 1, c->stream);
-        pnop::launch_weight(c->geo, c->lamB, c->lamA, 0, c->stream);
+        inner_dev(c, c->lamB, c->lamB, c->dscal + 1);
+        weight(c, c->lamB, c->lamA, 0);
         c->g_terminal = true;
     }
     adj_step(c, state, t, c->lamA, c->lamB);
@@ -363,14 +438,14 @@ int gradient_impl(pnop_ctx* c, const double2* u0, double E0, double horizon, dou
     double Einit = 0.5 * inner_sync(c, c->snaps[0], c->snaps[0]);
     if (E0 > 0) {
         if (!(Einit > 0) || !std::isfinite(Einit)) throw Status(PNOP_ERR_NONFINITE, "initial field has no finite energy");
-        pnop::launch_axpby(3 * c->S(), std::sqrt(E0 / Einit), c->snaps[0], 0.0, nullptr, c->snaps[0], c->stream);
+        axpby(c, std::sqrt(E0 / Einit), c->snaps[0], 0.0, nullptr, c->snaps[0]);
         Einit = 0.5 * inner_sync(c, c->snaps[0], c->snaps[0]);
     }
     c->st_adv = c->st_adj = c->st_store = 0;
     c->g_nsteps = N;
     c->g_terminal = false;
     reverse(c, 0, N, 0, s);
-    pnop::launch_weight(c->geo, c->lamA, grad, 1, c->stream);
+    weight(c, c->lamA, grad, 1);
     double ET2 = 0;
     ck(cudaMemcpyAsync(&ET2, c->dscal + 1, sizeof(double), cudaMemcpyDeviceToHost, c->stream), "copy E");
     ck(cudaStreamSynchronize(c->stream), "gradient sync");
@@ -411,6 +486,7 @@ int pnop_revolve_counts(int nsteps, int snaps, long long* advances, long long* s
 
 void pnop_destroy(pnop_ctx* ctx) {
     if (!ctx) return;
+    for (auto e : ctx->ev) cudaEventDestroy(e);
     for (void* p : ctx->allocs) cudaFree(p);
     delete ctx;
 }
@@ -542,9 +618,9 @@ int pnop_step_adjoint(pnop_ctx* ctx, const void* u_n, void* lam, double t_n) {
     return guarded(ctx, [&]() -> int {
         if (!u_n || !lam) throw Status(PNOP_ERR_INVALID_ARG, "bad arguments");
         double2* l = (double2*)lam;
-        pnop::launch_weight(ctx->geo, l, ctx->tmpA, 0, ctx->stream);
+        weight(ctx, l, ctx->tmpA, 0);
         adj_step(ctx, (const double2*)u_n, t_n, ctx->tmpA, ctx->tmpB);
-        pnop::launch_weight(ctx->geo, ctx->tmpB, l, 1, ctx->stream);
+        weight(ctx, ctx->tmpB, l, 1);
         ck(cudaGetLastError(), "step_adjoint");
         return PNOP_OK;
     });
@@ -589,21 +665,46 @@ int pnop_apply(pnop_ctx* ctx, int op, const void* a, const void* b, void* out, d
         double2* O = (double2*)out;
         const Geo& g = ctx->geo;
         switch (op) {
-            case PNOP_OP_CURL: pnop::launch_curl(g, A, O, ctx->stream); break;
+            case PNOP_OP_CURL: run(ctx, PNOP_K_SPECTRAL, 1, (double)ctx->S(), [&] { pnop::launch_curl(g, A, O, ctx->stream); }); break;
             case PNOP_OP_NONLINEAR: nonlinear(ctx, A, t, O); break;
             case PNOP_OP_STAGE:
                 if (!B) throw Status(PNOP_ERR_INVALID_ARG, "stage needs a forcing field");
-                pnop::launch_stage(g, A, B, O, ctx->q, ctx->R, ctx->stream);
+                stage(ctx, A, B, O);
                 break;
             case PNOP_OP_NONLINEAR_T:
                 if (!B) throw Status(PNOP_ERR_INVALID_ARG, "transpose needs a cotangent field");
                 nonlinearT(ctx, A, t, B, O);
                 break;
-            case PNOP_OP_STAGE_T_U: pnop::launch_stageT(g, A, O, 0, ctx->Fb, ctx->q, ctx->R, ctx->stream); break;
-            case PNOP_OP_STAGE_T_F: pnop::launch_stageT(g, A, ctx->ua, 0, O, ctx->q, ctx->R, ctx->stream); break;
+            case PNOP_OP_STAGE_T_U: stageT(ctx, A, O, 0, ctx->Fb); break;
+            case PNOP_OP_STAGE_T_F: stageT(ctx, A, ctx->ua, 0, O); break;
             default: throw Status(PNOP_ERR_INVALID_ARG, "unknown operator");
         }
         ck(cudaStreamSynchronize(ctx->stream), "apply");
+        return PNOP_OK;
+    });
+}
+
+int pnop_profile(pnop_ctx* ctx, unsigned class_mask) {
+    return guarded(ctx, [&]() -> int {
+        prof_flush(ctx);
+        ctx->prof_mask = class_mask;
+        for (int i = 0; i < PNOP_K_NCLASS; ++i) {
+            ctx->prof_ms[i] = 0;
+            ctx->launches[i] = 0;
+            ctx->units[i] = 0;
+        }
+        return PNOP_OK;
+    });
+}
+
+int pnop_profile_read(pnop_ctx* ctx, double* ms, long long* launches, double* units) {
+    return guarded(ctx, [&]() -> int {
+        prof_flush(ctx);
+        for (int i = 0; i < PNOP_K_NCLASS; ++i) {
+            if (ms) ms[i] = ctx->prof_ms[i];
+            if (launches) launches[i] = ctx->launches[i];
+            if (units) units[i] = ctx->units[i];
+        }
         return PNOP_OK;
     });
 }
