@@ -188,6 +188,35 @@ int pnop_inner(pnop_ctx* ctx, const void* a, const void* b, double* out);
  * Needs no device. */
 int pnop_revolve_counts(int nsteps, int snaps, long long* advances, long long* stores);
 
+/* Energy without any device allocation (the paper has no counterpart; this
+ * is a library convenience).  For callers that cannot call cudaMalloc where
+ * they need the result: code running after all device memory has been handed
+ * to another allocator or a fixed pool (a new cudaMalloc would fail there),
+ * or loops that must not call cudaMalloc/cudaFree because those can
+ * synchronise the device and stall other streams.  Such callers cannot create
+ * a context, so none is needed: pass the field u (device, layout above, nr,
+ * M, K as for a context), the radial quadrature weights W (device, nr
+ * doubles: sum_j W_j f(r_j) = int_0^1 f r dr, the same weights as the
+ * context's inner product, Eq. 2.2) and the pipe length Lz; *E_out (host)
+ * receives (1/2) <u, u>, as pnop_energy would.  The work is ordered on
+ * cuda_stream (NULL = legacy default stream) and the call synchronises it.
+ *
+ * Scratch: a fixed array in device global memory inside the library (32 KiB
+ * of partial sums plus one result slot); every GPU that loads the library
+ * holds it until the process exits.  The first call on a device resolves that
+ * array's device address (with the device current) and should therefore come
+ * before any stream capture on that device.  All calls share the array:
+ * calls whose device work overlaps (concurrent streams or host threads)
+ * race on it and must be serialised by the caller.  Each call clears the part it uses before writing.
+ *
+ * Limits and errors: 3 * nr * (2M+1) * (K+1) may be at most
+ * PNOP_NOALLOC_MAX_VALUES complex values; larger fields, NULL pointers or bad
+ * sizes return PNOP_ERR_INVALID_ARG before any device work; CUDA failures
+ * return PNOP_ERR_CUDA, a NaN/Inf energy PNOP_ERR_NONFINITE. */
+#define PNOP_NOALLOC_MAX_VALUES (16777216LL) /* 2^24 complex values (268 MB field) */
+int pnop_energy_noalloc(const void* u, const double* W, int nr, int M, int K, double Lz, double* E_out,
+                        void* cuda_stream);
+
 /* Error text of the last failing call on ctx ("" when none). */
 const char* pnop_last_error(const pnop_ctx* ctx);
 

@@ -24,7 +24,7 @@ OP_CURL, OP_NONLINEAR, OP_STAGE, OP_NONLINEAR_T, OP_STAGE_T_U, OP_STAGE_T_F = ra
 EXPORTS = (
     "pnop_create", "pnop_set_base_flow", "pnop_dims", "pnop_grid_points", "pnop_step_forward",
     "pnop_step_adjoint", "pnop_gradient", "pnop_gradient_host", "pnop_gradient_stats", "pnop_energy",
-    "pnop_inner", "pnop_apply", "pnop_profile", "pnop_profile_read", "pnop_revolve_counts", "pnop_last_error", "pnop_error_string", "pnop_destroy",
+    "pnop_inner", "pnop_apply", "pnop_profile", "pnop_profile_read", "pnop_revolve_counts", "pnop_energy_noalloc", "pnop_last_error", "pnop_error_string", "pnop_destroy",
 )
 
 
@@ -57,6 +57,8 @@ def _load():
         "pnop_profile": (c_int, [c_void_p, ctypes.c_uint]),
         "pnop_profile_read": (c_int, [c_void_p, POINTER(c_double), POINTER(c_longlong), POINTER(c_double)]),
         "pnop_revolve_counts": (c_int, [c_int, c_int, POINTER(c_longlong), POINTER(c_longlong)]),
+        "pnop_energy_noalloc": (c_int, [c_void_p, c_void_p, c_int, c_int, c_int, c_double, POINTER(c_double),
+                                        c_void_p]),
         "pnop_last_error": (c_char_p, [c_void_p]),
         "pnop_error_string": (c_char_p, [c_int]),
         "pnop_destroy": (None, [c_void_p]),
@@ -93,6 +95,18 @@ def pnop_revolve_counts(nsteps: int, snaps: int):
     if rc != PNOP_OK:
         raise PnopError(rc, "revolve_counts")
     return a.value, s.value
+
+
+def pnop_energy_noalloc(u, W, nr, M, K, Lz, stream=0):
+    """Energy (1/2)<u,u> of a device field with no device allocation and no context.
+
+    W: device array of the nr radial quadrature weights.  The library's scratch
+    for this call is a fixed device array shared by all calls (see pnop.h)."""
+    e = c_double()
+    rc = lib.pnop_energy_noalloc(c_void_p(_ptr(u)), c_void_p(_ptr(W)), nr, M, K, Lz, byref(e), c_void_p(stream))
+    if rc != PNOP_OK:
+        raise PnopError(rc, "energy_noalloc")
+    return e.value
 
 
 class Context:

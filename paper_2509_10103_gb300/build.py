@@ -32,7 +32,7 @@ def _run(cmd):
 
 
 def sources():
-    return [os.path.join(CSRC, f) for f in ("kernels.cu", "pnop.cu", "setup.cpp")]
+    return [os.path.join(CSRC, f) for f in ("kernels.cu", "pnop.cu", "noalloc.cu", "setup.cpp")]
 
 
 def up_to_date() -> bool:
