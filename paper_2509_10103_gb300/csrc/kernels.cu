@@ -397,85 +397,123 @@ __global__ void k_stage_div(Geo g, const double2* __restrict__ F, double2* __res
     q[o] = acc;
 }
 
-// In-place banded solve A x = b with LU factors fac[mat][j][13][nk] (one system per thread).
-__device__ void band_solve_dev(const Geo& g, const double* __restrict__ fac, int mat, int im, int k, double2* x) {
-    const int nr = g.nr, nk = g.nk;
-    const double* F = fac + (size_t)mat * nr * kB * nk + k;
-    double2 yw[4];
-#pragma unroll
-    for (int e = 0; e < 4; ++e) yw[e] = make_double2(0, 0);
-    for (int j = 0; j < nr; ++j) {
-        const double* Fj = F + (size_t)j * kB * nk;
-        double2 s = x[sidx(g, j, im, k)];
-#pragma unroll
-        for (int e = 0; e < 4; ++e) s = dfma(-__ldg(Fj + (size_t)e * nk), yw[e], s);  // yw[e] = y_{j-4+e}
-#pragma unroll
-        for (int e = 0; e < 3; ++e) yw[e] = yw[e + 1];
-        yw[3] = s;
-        x[sidx(g, j, im, k)] = s;
-    }
-    double2 xw[8];
-#pragma unroll
-    for (int e = 0; e < 8; ++e) xw[e] = make_double2(0, 0);
-    for (int j = nr - 1; j >= 0; --j) {
-        const double* Fj = F + (size_t)j * kB * nk;
-        double2 s = x[sidx(g, j, im, k)];
-#pragma unroll
-        for (int e = 0; e < 8; ++e) s = dfma(-__ldg(Fj + (size_t)(5 + e) * nk), xw[e], s);  // xw[e] = x_{j+1+e}
-        s = dscale(s, __ldg(Fj + (size_t)4 * nk));
-#pragma unroll
-        for (int e = 7; e > 0; --e) xw[e] = xw[e - 1];
-        xw[0] = s;
-        x[sidx(g, j, im, k)] = s;
-    }
-}
+// ------------------------------------------------------------------ banded solves
+// Two-sweep solve of one banded system per (matrix, k) with precomputed
+// row-local coefficients "lower | 1/diag | upper" (layout in setup.hpp).  A
+// block owns 32 consecutive k of one (component, m): the right-hand sides of
+// all rows sit in shared memory and the coefficient rows stream through a
+// double-buffered cp.async pipeline, kRC rows at a time.  Each of the 64
+// threads sweeps the real or the imaginary part of one system (the matrices
+// are real).  Terms are accumulated oldest first, so the dependence from one
+// row to the next is a single FMA.
+constexpr int kSK = 32;  // systems (consecutive k) per block
+constexpr int kRC = 8;   // rows per staged chunk
 
-// In-place transposed solve A^T x = b with the same factors (A^T = U^T L^T).
-__device__ void band_solveT_dev(const Geo& g, const double* __restrict__ fac, int mat, int im, int k, double2* x) {
-    const int nr = g.nr, nk = g.nk;
-    const double* F = fac + (size_t)mat * nr * kB * nk + k;
-    double2 ww[8];  // ww[i-1] = w_{j-i}
-#pragma unroll
-    for (int e = 0; e < 8; ++e) ww[e] = make_double2(0, 0);
-    for (int j = 0; j < nr; ++j) {
-        double2 s = x[sidx(g, j, im, k)];
-#pragma unroll
-        for (int i = 1; i <= 8; ++i) {
-            const int c = j - i;
-            if (c >= 0) s = dfma(-__ldg(F + ((size_t)c * kB + 4 + i) * nk), ww[i - 1], s);
-        }
-        s = dscale(s, __ldg(F + ((size_t)j * kB + 4) * nk));
-#pragma unroll
-        for (int e = 7; e > 0; --e) ww[e] = ww[e - 1];
-        ww[0] = s;
-        x[sidx(g, j, im, k)] = s;
-    }
-    double2 xw[4];  // xw[i-1] = x_{j+i}
-#pragma unroll
-    for (int e = 0; e < 4; ++e) xw[e] = make_double2(0, 0);
-    for (int j = nr - 1; j >= 0; --j) {
-        double2 s = x[sidx(g, j, im, k)];
-#pragma unroll
-        for (int i = 1; i <= 4; ++i) {
-            const int c = j + i;
-            if (c < nr) s = dfma(-__ldg(F + ((size_t)c * kB + 4 - i) * nk), xw[i - 1], s);
-        }
-#pragma unroll
-        for (int e = 3; e > 0; --e) xw[e] = xw[e - 1];
-        xw[0] = s;
-        x[sidx(g, j, im, k)] = s;
-    }
+__device__ __forceinline__ void cp_async16(void* sm, const void* gm) {
+    const unsigned a = (unsigned)__cvta_generic_to_shared(sm);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(a), "l"(gm) : "memory");
 }
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
 
-__global__ void k_stage_psolve(Geo g, double2* __restrict__ q) {
-    const int mode = blockIdx.x * blockDim.x + threadIdx.x;
-    if (mode >= g.nm * g.nk) return;
-    const int im = mode / g.nk, k = mode % g.nk, m = im - g.M;
-    if (m == 0 && k == 0) {
-        for (int j = 0; j < g.nr; ++j) q[sidx(g, j, im, k)] = make_double2(0, 0);
-        return;
+// NL lower coefficients (oldest first) for the forward sweep, diagonal in the
+// forward sweep when DIAG1 (else in the backward sweep), NU upper coefficients
+// (nearest first) for the backward sweep.
+template <int NL, int NU, bool DIAG1>
+__global__ void __launch_bounds__(64) k_band_solve(Geo g, const double* __restrict__ fac, double2* __restrict__ X,
+                                                  int helm, int zero_row0) {
+    constexpr int NC1 = NL + (DIAG1 ? 1 : 0);  // forward sweep: coefficients [0, NC1)
+    constexpr int E2 = NC1;                      // backward sweep: [E2, 13)
+    constexpr int NC2 = kB - E2;
+    constexpr int NCM = NC1 > NC2 ? NC1 : NC2;
+    extern __shared__ __align__(16) unsigned char smem[];
+    double2* Yb = reinterpret_cast<double2*>(smem);  // [nr][kSK]
+    double* Yd = reinterpret_cast<double*>(smem);
+    double* Cb = reinterpret_cast<double*>(Yb + (size_t)g.nr * kSK);  // [2][kRC][NCM][kSK]
+    const int nkb = (g.nk + kSK - 1) / kSK;
+    int bi = blockIdx.x;
+    const int kb = bi % nkb;
+    bi /= nkb;
+    const int im = bi % g.nm, v = bi / g.nm;
+    const int m = im - g.M;
+    const int mv = helm ? (v == 0 ? m + 1 : (v == 1 ? m - 1 : m)) : m;
+    const int k0 = kb * kSK;
+    const size_t S = (size_t)g.nr * g.nm * g.nk;
+    double2* x = X + (size_t)v * S;  // v = 0 for the pressure
+    const double* F = fac + (size_t)abs(mv) * g.nr * kB * g.nkp + k0;
+    const int tid = threadIdx.x, sy = tid & 31, comp = tid >> 5;
+    const int nch = (g.nr + kRC - 1) / kRC;
+
+    for (int i = tid; i < g.nr * kSK; i += blockDim.x) {
+        const int j = i / kSK, t = i % kSK;
+        if (k0 + t < g.nk) cp_async16(&Yb[i], &x[sidx(g, j, im, k0 + t)]);
+        else Yb[i] = make_double2(0, 0);
     }
-    band_solve_dev(g, g.facP, abs(m), im, k, q);
+    auto stage = [&](int t) {  // chunk t of the sweep sequence into buffer t & 1
+        if (t >= 2 * nch) return;
+        const bool fwd = t < nch;
+        const int c = fwd ? t : 2 * nch - 1 - t;
+        const int e0 = fwd ? 0 : E2, nc = fwd ? NC1 : NC2;
+        double* C = Cb + (size_t)(t & 1) * kRC * NCM * kSK;
+        const int nseg = kRC * nc * (kSK / 2);
+        for (int i = tid; i < nseg; i += blockDim.x) {
+            const int q = i % (kSK / 2), rest = i / (kSK / 2);
+            const int e = rest % nc, r = rest / nc, j = c * kRC + r;
+            if (j < g.nr) cp_async16(&C[(r * NCM + e) * kSK + 2 * q], F + ((size_t)j * kB + e0 + e) * g.nkp + 2 * q);
+        }
+    };
+    stage(0);
+    cp_async_commit();
+    double w1[NL], w2[NU];
+#pragma unroll
+    for (int e = 0; e < NL; ++e) w1[e] = 0.0;
+#pragma unroll
+    for (int e = 0; e < NU; ++e) w2[e] = 0.0;
+    for (int t = 0; t < 2 * nch; ++t) {
+        stage(t + 1);
+        cp_async_commit();
+        cp_async_wait1();
+        __syncthreads();
+        const double* C = Cb + (size_t)(t & 1) * kRC * NCM * kSK + sy;
+        if (t < nch) {
+            for (int r = 0; r < kRC; ++r) {
+                const int j = t * kRC + r;
+                if (j >= g.nr) break;
+                double val = Yd[(j * kSK + sy) * 2 + comp];
+                const bool full = !(NL == 8 && j > 8);  // columns of U beyond row 8 hold 4 entries
+#pragma unroll
+                for (int e = 0; e < NL; ++e)
+                    if (full || e >= NL - 4) val = fma(-C[(r * NCM + e) * kSK], w1[e], val);
+                if (DIAG1) val *= C[(r * NCM + NL) * kSK];
+#pragma unroll
+                for (int e = 0; e < NL - 1; ++e) w1[e] = w1[e + 1];
+                w1[NL - 1] = val;
+                Yd[(j * kSK + sy) * 2 + comp] = val;
+            }
+        } else {
+            const int c = 2 * nch - 1 - t;
+            constexpr int O = DIAG1 ? 0 : 1;  // first upper coefficient of the backward slice
+            for (int r = kRC - 1; r >= 0; --r) {
+                const int j = c * kRC + r;
+                if (j >= g.nr) continue;
+                double val = Yd[(j * kSK + sy) * 2 + comp];
+                const bool full = !(NU == 8 && j >= 4);  // rows of U from 4 on hold 4 entries
+#pragma unroll
+                for (int e = NU - 1; e >= 0; --e)
+                    if (full || e < 4) val = fma(-C[(r * NCM + O + e) * kSK], w2[e], val);
+                if (!DIAG1) val *= C[(r * NCM) * kSK];
+#pragma unroll
+                for (int e = NU - 1; e > 0; --e) w2[e] = w2[e - 1];
+                w2[0] = val;
+                Yd[(j * kSK + sy) * 2 + comp] = val;
+            }
+        }
+        __syncthreads();
+    }
+    for (int i = tid; i < g.nr * kSK; i += blockDim.x) {
+        const int j = i / kSK, t = i % kSK;
+        if (k0 + t < g.nk) x[sidx(g, j, im, k0 + t)] = (zero_row0 && j == 0) ? make_double2(0, 0) : Yb[i];
+    }
 }
 
 // R_v = B_v u_v + F'_v for v = +, -, z (rows j >= 1), F' = F - grad p
@@ -519,17 +557,6 @@ __global__ void k_stage_rhs(Geo g, const double2* __restrict__ u, const double2*
     R[o] = make_double2(dg * up.x + g.inv_2re * sp.x + (fr.x - ft.y), dg * up.y + g.inv_2re * sp.y + (fr.y + ft.x));
     R[o + S] = make_double2(dg * um.x + g.inv_2re * sm.x + (fr.x + ft.y), dg * um.y + g.inv_2re * sm.y + (fr.y - ft.x));
     R[o + 2 * S] = make_double2(dg * c.x + g.inv_2re * sz.x + fz.x, dg * c.y + g.inv_2re * sz.y + fz.y);
-}
-
-__global__ void k_stage_hsolve(Geo g, double2* __restrict__ R) {
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    const int nmode = g.nm * g.nk;
-    if (t >= 3 * nmode) return;
-    const int v = t / nmode, mode = t % nmode;
-    const int im = mode / g.nk, k = mode % g.nk, m = im - g.M;
-    const int mv = v == 0 ? m + 1 : (v == 1 ? m - 1 : m);
-    const size_t S = (size_t)g.nr * g.nm * g.nk;
-    band_solve_dev(g, g.facH, abs(mv), im, k, R + v * S);
 }
 
 // back to (r, theta, z); influence correction (div u = 0 at the wall) or, for
@@ -604,18 +631,6 @@ __global__ void k_stageT_finish(Geo g, const double2* __restrict__ un, double2* 
     }
 }
 
-__global__ void k_stageT_hsolve(Geo g, double2* __restrict__ R) {
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    const int nmode = g.nm * g.nk;
-    if (t >= 3 * nmode) return;
-    const int v = t / nmode, mode = t % nmode;
-    const int im = mode / g.nk, k = mode % g.nk, m = im - g.M;
-    const int mv = v == 0 ? m + 1 : (v == 1 ? m - 1 : m);
-    const size_t S = (size_t)g.nr * g.nm * g.nk;
-    band_solveT_dev(g, g.facH, abs(mv), im, k, R + v * S);
-    R[v * S + sidx(g, 0, im, k)] = make_double2(0, 0);
-}
-
 // ubar (+)= T^H B^T rbar ; Fb = T^H rbar
 __global__ void k_stageT_rhs(Geo g, const double2* __restrict__ R, double2* __restrict__ ub, int acc,
                              double2* __restrict__ Fb) {
@@ -663,15 +678,6 @@ __global__ void k_stageT_qbar(Geo g, const double2* __restrict__ Fb, double2* __
     acc.x += mr * ft.y + kz * fz.y;
     acc.y += -mr * ft.x - kz * fz.x;
     q[o] = acc;
-}
-
-__global__ void k_stageT_psolve(Geo g, double2* __restrict__ q) {
-    const int mode = blockIdx.x * blockDim.x + threadIdx.x;
-    if (mode >= g.nm * g.nk) return;
-    const int im = mode / g.nk, k = mode % g.nk, m = im - g.M;
-    if (m == 0 && k == 0) return;  // q already zero
-    band_solveT_dev(g, g.facP, abs(m), im, k, q);
-    q[sidx(g, 0, im, k)] = make_double2(0, 0);
 }
 
 // Fb = Fb' - Dv^H z: Fb_r -= D1v^T z + z/r ; Fb_t += i (m/r) z ; Fb_z += i kz z
@@ -855,12 +861,34 @@ template void launch_zpass<double2>(const Geo&, int, const double2*, double2*, c
 template void launch_zpass<float2>(const Geo&, int, const float2*, float2*, const ZScales&, const Twiddles&,
                                    cudaStream_t);
 
+// trans (zero_row0 == 1) selects the transposed coefficient layout
+static void launch_band_solve(const Geo& g, const double* fac, double2* X, int helm, int zero_row0, cudaStream_t s) {
+    const int nkb = (g.nk + kSK - 1) / kSK;
+    const unsigned nblocks = (unsigned)((helm ? 3 : 1) * g.nm * nkb);
+    const size_t sm = (size_t)g.nr * kSK * sizeof(double2) + 2 * (size_t)kRC * 9 * kSK * sizeof(double);
+    if (!zero_row0) {
+        static bool attr = false;
+        if (!attr) {
+            cudaFuncSetAttribute(k_band_solve<4, 8, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+            attr = true;
+        }
+        k_band_solve<4, 8, false><<<nblocks, 64, sm, s>>>(g, fac, X, helm, 0);
+    } else {
+        static bool attr = false;
+        if (!attr) {
+            cudaFuncSetAttribute(k_band_solve<8, 4, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+            attr = true;
+        }
+        k_band_solve<8, 4, true><<<nblocks, 64, sm, s>>>(g, fac, X, helm, 1);
+    }
+}
+
 void launch_stage_div(const Geo& g, const double2* F, double2* q, cudaStream_t s) {
     k_stage_div<<<nblk(S_of(g), 256), 256, 0, s>>>(g, F, q);
     check_launch("stage_div");
 }
 void launch_stage_psolve(const Geo& g, double2* q, cudaStream_t s) {
-    k_stage_psolve<<<nblk((size_t)g.nm * g.nk, 64), 64, 0, s>>>(g, q);
+    launch_band_solve(g, g.facP, q, 0, 0, s);
     check_launch("stage_psolve");
 }
 void launch_stage_rhs(const Geo& g, const double2* u, const double2* F, const double2* p, double2* R, cudaStream_t s) {
@@ -868,7 +896,7 @@ void launch_stage_rhs(const Geo& g, const double2* u, const double2* F, const do
     check_launch("stage_rhs");
 }
 void launch_stage_hsolve(const Geo& g, double2* R, cudaStream_t s) {
-    k_stage_hsolve<<<nblk(3 * (size_t)g.nm * g.nk, 64), 64, 0, s>>>(g, R);
+    launch_band_solve(g, g.facH, R, 1, 0, s);
     check_launch("stage_hsolve");
 }
 void launch_stage_finish(const Geo& g, const double2* R, double2* out, cudaStream_t s) {
@@ -880,7 +908,7 @@ void launch_stageT_finish(const Geo& g, const double2* ubn, double2* R, cudaStre
     check_launch("stageT_finish");
 }
 void launch_stageT_hsolve(const Geo& g, double2* R, cudaStream_t s) {
-    k_stageT_hsolve<<<nblk(3 * (size_t)g.nm * g.nk, 64), 64, 0, s>>>(g, R);
+    launch_band_solve(g, g.facHT, R, 1, 1, s);
     check_launch("stageT_hsolve");
 }
 void launch_stageT_rhs(const Geo& g, const double2* R, double2* ub, int acc, double2* Fb, cudaStream_t s) {
@@ -892,7 +920,7 @@ void launch_stageT_qbar(const Geo& g, const double2* Fb, double2* q, cudaStream_
     check_launch("stageT_qbar");
 }
 void launch_stageT_psolve(const Geo& g, double2* q, cudaStream_t s) {
-    k_stageT_psolve<<<nblk((size_t)g.nm * g.nk, 64), 64, 0, s>>>(g, q);
+    launch_band_solve(g, g.facPT, q, 0, 1, s);
     check_launch("stageT_psolve");
 }
 void launch_stageT_div(const Geo& g, const double2* z, double2* Fb, cudaStream_t s) {

@@ -16,8 +16,11 @@ struct Geo {
     const double* W;
     const double* D1;    // [2][nr][13]
     const double* Lb;    // [M+2][nr][13]
-    const double* facH;  // [M+2][nr][13][nk]
-    const double* facP;  // [M+1][nr][13][nk]
+    int nkp;             // k stride of the factor tables (multiple of 32)
+    const double* facH;  // [M+2][nr][13][nkp]  A x = b rows
+    const double* facP;  // [M+1][nr][13][nkp]
+    const double* facHT; // transposed-solve rows
+    const double* facPT;
     const double* infl;  // [nm][nk][3][nr]
     const double* fluxg; // [nr]
     double flux_inv;

@@ -50,6 +50,7 @@ struct pnop_ctx {
     // operators
     double *d_r = nullptr, *d_invr = nullptr, *d_W = nullptr, *d_D1 = nullptr, *d_Lb = nullptr;
     double *d_facH = nullptr, *d_facP = nullptr, *d_infl = nullptr, *d_fluxg = nullptr;
+    double *d_facHT = nullptr, *d_facPT = nullptr;
     double2 *d_Uh = nullptr, *d_dUh = nullptr;
     pnop::Twiddles tw{};
     // workspace
@@ -137,6 +138,8 @@ void upload_operators(pnop_ctx* c) {
     put(c->d_Lb, h.Lb);
     put(c->d_facH, h.facH);
     put(c->d_facP, h.facP);
+    put(c->d_facHT, h.facHT);
+    put(c->d_facPT, h.facPT);
     put(c->d_infl, h.infl);
     put(c->d_fluxg, h.fluxg);
     auto uh = cvec(h.Uh), duh = cvec(h.dUh);
@@ -153,6 +156,9 @@ void upload_operators(pnop_ctx* c) {
     g.Lb = c->d_Lb;
     g.facH = c->d_facH;
     g.facP = c->d_facP;
+    g.facHT = c->d_facHT;
+    g.facPT = c->d_facPT;
+    g.nkp = h.nkp;
     g.infl = c->d_infl;
     g.fluxg = c->d_fluxg;
     g.flux_inv = h.flux_inv;

@@ -273,10 +273,28 @@ static double band_backward_error(const Band& A, const std::vector<double>& f, u
     return rmax / (amax * xmax + 1e-300);
 }
 
-static void scatter_factors(std::vector<double>& dst, int mat, int k, int nr, int nk, const std::vector<double>& f) {
+static void scatter_factors(std::vector<double>& dst, int mat, int k, int nr, int nkp, const std::vector<double>& f) {
     for (int j = 0; j < nr; ++j)
         for (int e = 0; e < kBand; ++e)
-            dst[(((size_t)mat * nr + j) * kBand + e) * nk + k] = f[(size_t)j * kBand + e];
+            dst[(((size_t)mat * nr + j) * kBand + e) * nkp + k] = f[(size_t)j * kBand + e];
+}
+
+// Row-local coefficients of A^T = U^T L^T from the factors of A: row j holds
+// U_{j-8+e, j} (e = 0..7, oldest first), 1/U_jj, L_{j+1+e, j} (e = 0..3).
+static std::vector<double> transpose_factors(int nr, const std::vector<double>& f) {
+    std::vector<double> t((size_t)nr * kBand, 0.0);
+    for (int j = 0; j < nr; ++j) {
+        for (int e = 0; e < 8; ++e) {
+            const int i = j - 8 + e;  // U_{i, j} = f[i][4 + (j - i)]
+            if (i >= 0) t[(size_t)j * kBand + e] = f[(size_t)i * kBand + kLo + (j - i)];
+        }
+        t[(size_t)j * kBand + 8] = f[(size_t)j * kBand + kLo];
+        for (int e = 0; e < 4; ++e) {
+            const int i = j + 1 + e;  // L_{i, j} = f[i][j - i + 4]
+            if (i < nr) t[(size_t)j * kBand + 9 + e] = f[(size_t)i * kBand + (j - i + kLo)];
+        }
+    }
+    return t;
 }
 
 static Band laplacian_band(const HostOps& h, int mabs, double kz) {
@@ -327,8 +345,11 @@ bool build_operators(HostOps& h, std::string& err) {
             h.Lb[((size_t)ma * nr + j) * kBand + kLo] -= (double)ma * ma * h.invr[j] * h.invr[j];
         }
     }
-    h.facH.assign((size_t)(M + 2) * nr * kBand * nk, 0.0);
-    h.facP.assign((size_t)(M + 1) * nr * kBand * nk, 0.0);
+    const int nkp = h.nkp = (nk + 31) / 32 * 32;
+    h.facH.assign((size_t)(M + 2) * nr * kBand * nkp, 0.0);
+    h.facHT.assign(h.facH.size(), 0.0);
+    h.facP.assign((size_t)(M + 1) * nr * kBand * nkp, 0.0);
+    h.facPT.assign(h.facP.size(), 0.0);
     std::vector<double> f;
     double worst = 0, growth = 0;
     for (int k = 0; k < nk; ++k) {
@@ -340,14 +361,16 @@ bool build_operators(HostOps& h, std::string& err) {
                 return false;
             }
             worst = std::max(worst, band_backward_error(A, f, 1234u + ma * 977u + k));
-            scatter_factors(h.facH, ma, k, nr, nk, f);
+            scatter_factors(h.facH, ma, k, nr, nkp, f);
+            scatter_factors(h.facHT, ma, k, nr, nkp, transpose_factors(nr, f));
         }
         for (int ma = 0; ma <= M; ++ma) {
             if (ma == 0 && k == 0) {
                 // singular Neumann problem of the mean mode: never used (p = 0)
                 std::vector<double> id((size_t)nr * kBand, 0.0);
                 for (int j = 0; j < nr; ++j) id[(size_t)j * kBand + kLo] = 1.0;
-                scatter_factors(h.facP, ma, k, nr, nk, id);
+                scatter_factors(h.facP, ma, k, nr, nkp, id);
+                scatter_factors(h.facPT, ma, k, nr, nkp, transpose_factors(nr, id));
                 continue;
             }
             Band A = pressure_band(h, ma, kz);
@@ -356,7 +379,8 @@ bool build_operators(HostOps& h, std::string& err) {
                 return false;
             }
             worst = std::max(worst, band_backward_error(A, f, 4321u + ma * 131u + k));
-            scatter_factors(h.facP, ma, k, nr, nk, f);
+            scatter_factors(h.facP, ma, k, nr, nkp, f);
+            scatter_factors(h.facPT, ma, k, nr, nkp, transpose_factors(nr, f));
         }
     }
     if (!(worst < 1e-12)) {

@@ -33,8 +33,13 @@ struct HostOps {
     std::vector<double> r, invr, W;            // [nr]
     std::vector<double> D1, D2;                 // [2 parity][nr][kBand], parity 0 even, 1 odd
     std::vector<double> Lb;                     // [M+2][nr][kBand]  D2 + D1/r - m^2/r^2 (no kz^2)
-    std::vector<double> facH;                   // [M+2][nr][kBand][nk]   Helmholtz LU (per |m'|, k)
-    std::vector<double> facP;                   // [M+1][nr][kBand][nk]   pressure LU (per |m|, k)
+    // Banded LU factors, k padded to nkp (a multiple of 32, zeros beyond nk).
+    // Row layout "lower | 1/diag | upper" for a two-sweep solve:
+    //   facH/facP  (A x = b):   l_{j,j-4..j-1}, 1/U_jj, U_{j,j+1..j+8}
+    //   facHT/facPT (A^T x = b): U_{j-8..j-1,j}, 1/U_jj, L_{j+1..j+4,j}
+    int nkp = 0;
+    std::vector<double> facH, facHT;            // [M+2][nr][kBand][nkp]  Helmholtz (per |m'|, k)
+    std::vector<double> facP, facPT;            // [M+1][nr][kBand][nkp]  pressure (per |m|, k)
     std::vector<double> infl;                   // [nm][nk][3][nr] influence response, pre-scaled by -1/delta
     std::vector<double> fluxg;                  // [nr] flux response of mode (0,0)
     double flux_inv = 0;                        // 1 / sum_j W_j g_j
