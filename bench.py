@@ -89,6 +89,8 @@ def class_work(cls, units, mixed):
         nin, nout = (6, 3) if cls == "zpass_fwd" else (9, 6)
         fl = (nin + nout) * fft_flops(NZP, real=True) + (9 if cls == "zpass_fwd" else 18) * NZP
         return units * fl, units * (nin + nout) * (K + 1) * cz
+    if cls in ("radial_band", "spectral"):  # the library counts algorithmic FP64 flops as units
+        return units, None
     if cls == "radial_solve":  # one system: nr rows, 4 + up to 8 off-diagonals + scale, complex rhs
         fl = NR * (4 + 8 + 1) * 4.0
         by = NR * (13 * 8 + 4 * 16)
@@ -249,12 +251,13 @@ def roofline(L, res, mixed, peaks, pk_src):
     smx = peaks.get("sm_max_mhz", 2070.0)
     if fl is None or launches == 0 or ms <= 0:
         return None
-    fp_peak = alu_peak_tflops(FP32_FLOPS_PER_CLK_SM if (mixed and cls not in ("radial_solve",)) else
+    fp_peak = alu_peak_tflops(FP32_FLOPS_PER_CLK_SM if (mixed and cls not in ("radial_solve", "radial_band", "spectral")) else
                               FP64_FLOPS_PER_CLK_SM, smx)
     t = ms / 1e3
     ach_f = fl / t / 1e12
-    ach_b = by / t / 1e9
-    frac_f, frac_b = ach_f / fp_peak, ach_b / hbm
+    ach_b = by / t / 1e9 if by is not None else None
+    frac_f = ach_f / fp_peak
+    frac_b = ach_b / hbm if by is not None else 0.0
     tt = traffic_table().get((cls, "mixed" if mixed else "fp64"))
     base = {"kernel": cls, "launches": launches, "avg_launch_us": ms * 1e3 / launches,
             "traffic": tt}

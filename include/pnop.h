@@ -159,8 +159,8 @@ enum {
     PNOP_K_ZPASS_FWD = 1,    /* z FFTs + u x w products (units: (j, theta) rows) */
     PNOP_K_ZPASS_ADJ = 2,    /* z FFTs + transposed products (units: rows) */
     PNOP_K_ANAL_THETA = 3,   /* forward theta FFTs + truncation (units: FFT columns) */
-    PNOP_K_SPECTRAL = 4,     /* curl, base-flow terms and their transposes (units: modes x r) */
-    PNOP_K_RADIAL_BAND = 5,  /* banded radial matvecs, +/- basis, influence (units: values) */
+    PNOP_K_SPECTRAL = 4,     /* curl, base-flow terms and their transposes (units: algorithmic FP64 flops) */
+    PNOP_K_RADIAL_BAND = 5,  /* banded radial matvecs, +/- basis, influence (units: algorithmic FP64 flops) */
     PNOP_K_RADIAL_SOLVE = 6, /* banded LU solves (units: systems of nr unknowns) */
     PNOP_K_ELEMENTWISE = 7,  /* axpby, energy weights (units: values) */
     PNOP_K_REDUCE = 8,       /* inner-product reductions (units: values) */

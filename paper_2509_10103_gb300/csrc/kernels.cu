@@ -78,52 +78,76 @@ __device__ __forceinline__ void small_dft(T2* v, int R, int sign) {
     }
 }
 
-template <class T2>
-__device__ T2* fft_cols(T2* a, T2* b, int N, int ncol, int ld, const T2* tw, int sign) {
-    int n2 = 0, n3 = 0, t = N;
-    while ((t & 1) == 0) { t >>= 1; ++n2; }
-    while (t % 3 == 0) { t /= 3; ++n3; }
-    int nstage = n2 / 2 + (n2 & 1) + n3;
-    int Ns = 1;
-    for (int st = 0; st < nstage; ++st) {
-        int R = st < n2 / 2 ? 4 : ((st == n2 / 2 && (n2 & 1)) ? 2 : 3);
-        const int stride = N / R;
-        const int nb = stride * ncol;
-        const int tstep = N / (Ns * R);
-        for (int idx = threadIdx.x; idx < nb; idx += blockDim.x) {
-            const int col = idx % ncol;
-            const int jb = idx / ncol;
-            const int kk = jb % Ns;
-            T2 v[4];
-#pragma unroll
-            for (int r = 0; r < 4; ++r)
-                if (r < R) v[r] = a[(jb + r * stride) * ld + col];
-#pragma unroll
-            for (int r = 1; r < 4; ++r)
-                if (r < R) {
-                    T2 w = tw[(r * kk * tstep) % N];
-                    if (sign > 0) w.y = -w.y;
-                    v[r] = cmul(v[r], w);
-                }
-            small_dft(v, R, sign);
-            const int idxD = (jb / Ns) * Ns * R + kk;
-#pragma unroll
-            for (int r = 0; r < 4; ++r)
-                if (r < R) b[(idxD + r * Ns) * ld + col] = v[r];
+// One radix-R Stockham stage.  Ns (the size of the sub-transforms already
+// done) is a power of two 2^lgNs for every stage but the second and later
+// radix-3 stages (radix 3 runs last), so the index split is a shift there.
+template <class T2, int R, int NCOL, int LD>
+__device__ __forceinline__ void fft_stage(const T2* __restrict__ a, T2* __restrict__ b, int N, int Ns, int lgNs,
+                                          const T2* __restrict__ tw, int sign) {
+    const int stride = N / R;
+    const int nb = stride * NCOL;
+    const int tstep = N / (Ns * R);
+    for (int idx = threadIdx.x; idx < nb; idx += blockDim.x) {
+        const int col = idx % NCOL;
+        const int jb = idx / NCOL;
+        int q, kk;
+        if (lgNs >= 0) {
+            q = jb >> lgNs;
+            kk = jb & (Ns - 1);
+        } else {
+            q = jb / Ns;
+            kk = jb - q * Ns;
         }
+        T2 v[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[r] = a[(jb + r * stride) * LD + col];
+        const int tb = kk * tstep;  // r * tb < N
+#pragma unroll
+        for (int r = 1; r < R; ++r) {
+            T2 w = tw[r * tb];
+            if (sign > 0) w.y = -w.y;
+            v[r] = cmul(v[r], w);
+        }
+        small_dft(v, R, sign);
+        const int idxD = q * Ns * R + kk;
+#pragma unroll
+        for (int r = 0; r < R; ++r) b[(idxD + r * Ns) * LD + col] = v[r];
+    }
+}
+
+template <class T2, int NCOL, int LD>
+__device__ T2* fft_cols(T2* a, T2* b, int N, const T2* tw, int sign) {
+    const int n2 = __ffs(N) - 1;  // N = 2^n2 3^n3
+    int n3 = 0;
+    for (int t = N >> n2; t > 1; t /= 3) ++n3;
+    int Ns = 1, lgNs = 0;
+    for (int st = 0; st < n2 / 2; ++st) {
+        fft_stage<T2, 4, NCOL, LD>(a, b, N, Ns, lgNs, tw, sign);
         __syncthreads();
-        T2* tmp = a;
-        a = b;
-        b = tmp;
-        Ns *= R;
+        T2* t = a; a = b; b = t;
+        Ns *= 4;
+        lgNs += 2;
+    }
+    if (n2 & 1) {
+        fft_stage<T2, 2, NCOL, LD>(a, b, N, Ns, lgNs, tw, sign);
+        __syncthreads();
+        T2* t = a; a = b; b = t;
+        Ns *= 2;
+        lgNs += 1;
+    }
+    for (int st = 0; st < n3; ++st) {
+        fft_stage<T2, 3, NCOL, LD>(a, b, N, Ns, st == 0 ? lgNs : -1, tw, sign);
+        __syncthreads();
+        T2* t = a; a = b; b = t;
+        Ns *= 3;
     }
     return a;
 }
 
 // ------------------------------------------------------------------ theta synthesis
 // Y[f][j][a][k] = sum_m X_f[j][m][k] e^{i m theta_a}   (zero-padded to nt points)
-template <class T2>
-__global__ void k_synth_theta(Geo g, FieldPtrs f, T2* __restrict__ Y, const T2* __restrict__ twg, int KB) {
+template <class T2, int KB>
+__global__ void k_synth_theta(Geo g, FieldPtrs f, T2* __restrict__ Y, const T2* __restrict__ twg) {
     extern __shared__ __align__(16) unsigned char smem[];
     T2* buf0 = reinterpret_cast<T2*>(smem);
     T2* buf1 = buf0 + g.nt * KB;
@@ -143,7 +167,7 @@ __global__ void k_synth_theta(Geo g, FieldPtrs f, T2* __restrict__ Y, const T2* 
         }
     }
     __syncthreads();
-    T2* res = fft_cols(buf0, buf1, g.nt, KB, KB, tw, +1);
+    T2* res = fft_cols<T2, KB, KB>(buf0, buf1, g.nt, tw, +1);
     T2* dst = Y + ((size_t)(fi * g.nr + j) * g.nt) * g.nk;
     for (int i = threadIdx.x; i < g.nt * KB; i += blockDim.x) {
         const int a = i / KB, kk = i % KB;
@@ -196,7 +220,7 @@ __global__ void k_zpass(Geo g, const T2* __restrict__ Y, T2* __restrict__ Z, ZSc
         bufA[n * LD + p] = q;
     }
     __syncthreads();
-    T2* ph = fft_cols(bufA, bufB, N, NPI, LD, tw, +1);
+    T2* ph = fft_cols<T2, NPI, LD>(bufA, bufB, N, tw, +1);
     T2* pr = (ph == bufA) ? bufB : bufA;
     for (int n = threadIdx.x; n < N; n += blockDim.x) {
         const T2* row = ph + n * LD;
@@ -217,7 +241,7 @@ __global__ void k_zpass(Geo g, const T2* __restrict__ Y, T2* __restrict__ Z, ZSc
         }
     }
     __syncthreads();
-    T2* sp = fft_cols(pr, ph, N, NPO, LD, tw, -1);
+    T2* sp = fft_cols<T2, NPO, LD>(pr, ph, N, tw, -1);
     for (int i = threadIdx.x; i < NPO * nk; i += blockDim.x) {
         const int p = i / nk, k = i % nk;
         const T2 P = sp[k * LD + p];
@@ -237,8 +261,8 @@ __global__ void k_zpass(Geo g, const T2* __restrict__ Y, T2* __restrict__ Z, ZSc
 // ------------------------------------------------------------------ theta analysis
 // X_f[j][m][k] = sum_a Z_f[j][a][k] e^{-i m theta_a}, |m| <= M, with the k = 0
 // plane projected onto Hermitian symmetry.
-template <class T2>
-__global__ void k_anal_theta(Geo g, FieldPtrs f, const T2* __restrict__ Z, const T2* __restrict__ twg, int KB) {
+template <class T2, int KB>
+__global__ void k_anal_theta(Geo g, FieldPtrs f, const T2* __restrict__ Z, const T2* __restrict__ twg) {
     extern __shared__ __align__(16) unsigned char smem[];
     T2* buf0 = reinterpret_cast<T2*>(smem);
     T2* buf1 = buf0 + g.nt * KB;
@@ -252,7 +276,7 @@ __global__ void k_anal_theta(Geo g, FieldPtrs f, const T2* __restrict__ Z, const
         buf0[i] = kk < kw ? src[(size_t)a * g.nk + k0 + kk] : mk<T2>(0, 0);
     }
     __syncthreads();
-    T2* res = fft_cols(buf0, buf1, g.nt, KB, KB, tw, -1);
+    T2* res = fft_cols<T2, KB, KB>(buf0, buf1, g.nt, tw, -1);
     double2* dst = f.out[fi] + (size_t)j * g.nm * g.nk;
     for (int i = threadIdx.x; i < g.nm * KB; i += blockDim.x) {
         const int im = i / KB, kk = i % KB;
@@ -285,25 +309,56 @@ __device__ __forceinline__ size_t sidx(const Geo& g, int j, int im, int k) {
     return ((size_t)j * g.nm + im) * g.nk + k;
 }
 
-// Banded row product sum_s B[j][s] x[j-4+s]
+// Banded row product sum_s B[j][s] x[j-4+s].  Every row has at most 9
+// nonzeros: columns 0..8 for the one-sided wall rows j < 4, columns j-4..j+4
+// (clipped at the axis, where mirrored nodes fold inwards) otherwise.
 __device__ __forceinline__ double2 band_row(const Geo& g, const double* B, const double2* x, int j, int im, int k) {
     double2 acc = make_double2(0, 0);
+    if (j >= 4) {
 #pragma unroll
-    for (int s = 0; s < kB; ++s) {
-        const int c = j - 4 + s;
-        if (c >= 0 && c < g.nr) acc = dfma(__ldg(B + s), x[sidx(g, c, im, k)], acc);
+        for (int s = 0; s < 9; ++s) {
+            const int c = j - 4 + s;
+            if (c < g.nr) acc = dfma(__ldg(B + s), x[sidx(g, c, im, k)], acc);
+        }
+    } else {
+#pragma unroll
+        for (int s = 0; s < kB; ++s) {
+            const int c = j - 4 + s;
+            if (c >= 0 && c <= 8) acc = dfma(__ldg(B + s), x[sidx(g, c, im, k)], acc);
+        }
     }
     return acc;
 }
-// Transposed banded product (B^T x)_j = sum_{j'} B[j'][j - j' + 4] x[j']
-__device__ __forceinline__ double2 band_col(const Geo& g, const double* B0, const double2* x, int j, int im, int k) {
+// Transposed banded product (B^T x)_j = sum_{j'} B[j'][j - j' + 4] x[j'].
+// Column j > 8 is reached only from rows j-4..j+4; columns 0..8 also from the
+// wall rows 0..3.  With TWO the operand is c1 x1 + c2 x2.
+template <bool TWO>
+__device__ __forceinline__ double2 band_col2(const Geo& g, const double* B0, const double2* x1, double c1,
+                                             const double2* x2, double c2, int j, int im, int k) {
     double2 acc = make_double2(0, 0);
+    auto val = [&](int c) {
+        const size_t o = sidx(g, c, im, k);
+        if (!TWO) return x1[o];
+        const double2 a = x1[o], b = x2[o];
+        return make_double2(c1 * a.x + c2 * b.x, c1 * a.y + c2 * b.y);
+    };
+    if (j > 8) {
 #pragma unroll
-    for (int t = -8; t <= 4; ++t) {
-        const int c = j + t;
-        if (c >= 0 && c < g.nr) acc = dfma(__ldg(B0 + (size_t)c * kB + (4 - t)), x[sidx(g, c, im, k)], acc);
+        for (int t = -4; t <= 4; ++t) {
+            const int c = j + t;
+            if (c < g.nr) acc = dfma(__ldg(B0 + (size_t)c * kB + (4 - t)), val(c), acc);
+        }
+    } else {
+#pragma unroll
+        for (int t = -8; t <= 4; ++t) {
+            const int c = j + t;
+            if (c >= 0 && c < g.nr) acc = dfma(__ldg(B0 + (size_t)c * kB + (4 - t)), val(c), acc);
+        }
     }
     return acc;
+}
+__device__ __forceinline__ double2 band_col(const Geo& g, const double* B0, const double2* x, int j, int im, int k) {
+    return band_col2<false>(g, B0, x, 1.0, nullptr, 0.0, j, im, k);
 }
 
 __global__ void k_curl(Geo g, const double2* __restrict__ u, double2* __restrict__ w) {
@@ -532,16 +587,24 @@ __global__ void k_stage_rhs(Geo g, const double2* __restrict__ u, const double2*
     const double2 fr = make_double2(fr0.x - dp.x, fr0.y - dp.y);
     const double2 ft = make_double2(ft0.x + mr * pj.y, ft0.y - mr * pj.x);
     const double2 fz = make_double2(fz0.x + kz * pj.y, fz0.y - kz * pj.x);
+    if (!u) {  // forcing only: S(0, F)
+        R[o] = make_double2(fr.x - ft.y, fr.y + ft.x);
+        R[o + S] = make_double2(fr.x + ft.y, fr.y - ft.x);
+        R[o + 2 * S] = fz;
+        return;
+    }
     // band sums of L_{m'} applied to u+, u-, u_z
     const double* Lp = g.Lb + ((size_t)abs(d.m + 1) * g.nr + d.j) * kB;
     const double* Lm = g.Lb + ((size_t)abs(d.m - 1) * g.nr + d.j) * kB;
     const double* Lz = g.Lb + ((size_t)abs(d.m) * g.nr + d.j) * kB;
     double2 sp = make_double2(0, 0), sm = make_double2(0, 0), sz = make_double2(0, 0);
     const double2 *ur = u, *ut = u + S, *uz = u + 2 * S;
+    // rows j >= 4 touch columns j-4..j+4 only (9 entries), wall rows columns 0..8
+    const int s0 = d.j >= 4 ? 0 : 4 - d.j, s1 = d.j >= 4 ? 8 : 12 - d.j;
 #pragma unroll
     for (int s = 0; s < kB; ++s) {
         const int c = d.j - 4 + s;
-        if (c < 0 || c >= g.nr) continue;
+        if (s < s0 || s > s1 || c >= g.nr) continue;
         const size_t oc = sidx(g, c, d.im, d.k);
         const double2 a = ur[oc], b = ut[oc];
         const double2 up = make_double2(a.x - b.y, a.y + b.x);
@@ -559,9 +622,32 @@ __global__ void k_stage_rhs(Geo g, const double2* __restrict__ u, const double2*
     R[o + 2 * S] = make_double2(dg * c.x + g.inv_2re * sz.x + fz.x, dg * c.y + g.inv_2re * sz.y + fz.y);
 }
 
-// back to (r, theta, z); influence correction (div u = 0 at the wall) or, for
-// mode (0,0), flux correction and u_r = 0.
-__global__ void k_stage_finish(Geo g, const double2* __restrict__ R, double2* __restrict__ out) {
+// Per-mode wall coefficient of the influence correction, a0 = d/dr u_r at the
+// wall of the tentative velocity (u_r = (x+ + x-)/2); for mode (0,0) the flux
+// sum_j W_j x_z instead.  One thread per mode; result in a0[mode].
+__global__ void k_stage_a0(Geo g, const double2* __restrict__ R, double2* __restrict__ a0) {
+    const int mode = blockIdx.x * blockDim.x + threadIdx.x;
+    if (mode >= g.nm * g.nk) return;
+    const int im = mode / g.nk, k = mode % g.nk, m = im - g.M;
+    const size_t S = (size_t)g.nr * g.nm * g.nk;
+    double2 acc = make_double2(0, 0);
+    if (m == 0 && k == 0) {
+        for (int c = 0; c < g.nr; ++c) acc = dfma(g.W[c], R[sidx(g, c, im, k) + 2 * S], acc);
+    } else {
+        const double* d0 = g.D1 + (size_t)par_idx(m + 1) * g.nr * kB;  // row 0 of D1 (u_r parity)
+        for (int c = 0; c <= 8; ++c) {
+            const size_t oc = sidx(g, c, im, k);
+            const double2 p = R[oc], q = R[oc + S];
+            acc = dfma(0.5 * __ldg(d0 + 4 + c), make_double2(p.x + q.x, p.y + q.y), acc);
+        }
+    }
+    a0[mode] = acc;
+}
+
+// out = [addto +] back to (r, theta, z) with the influence correction
+// (div u = 0 at the wall) or, for mode (0,0), flux correction and u_r = 0.
+__global__ void k_stage_finish(Geo g, const double2* __restrict__ R, const double2* __restrict__ a0v,
+                               const double2* __restrict__ addto, double2* __restrict__ out) {
     Idx d;
     if (!decode(g, (size_t)blockIdx.x * blockDim.x + threadIdx.x, d)) return;
     const size_t o = sidx(g, d.j, d.im, d.k), S = d.S;
@@ -569,25 +655,22 @@ __global__ void k_stage_finish(Geo g, const double2* __restrict__ R, double2* __
     double2 ur = make_double2(0.5 * (xp.x + xm.x), 0.5 * (xp.y + xm.y));
     double2 ut = make_double2(0.5 * (xp.y - xm.y), -0.5 * (xp.x - xm.x));
     double2 uz = R[o + 2 * S];
+    const double2 a0 = a0v[d.im * g.nk + d.k];
     if (d.m == 0 && d.k == 0) {
-        double2 acc = make_double2(0, 0);
-        for (int c = 0; c < g.nr; ++c) acc = dfma(g.W[c], R[sidx(g, c, d.im, d.k) + 2 * S], acc);
-        const double gj = g.fluxg[d.j] * (-g.flux_inv);
-        uz = dfma(gj, acc, uz);
+        uz = dfma(g.fluxg[d.j] * (-g.flux_inv), a0, uz);
         ur = make_double2(0, 0);
     } else {
-        const double* d0 = g.D1 + (size_t)par_idx(d.m + 1) * g.nr * kB;  // row 0 of D1 (u_r parity)
-        double2 a0 = make_double2(0, 0);
-        for (int c = 0; c <= 8 && c < g.nr; ++c) {
-            const size_t oc = sidx(g, c, d.im, d.k);
-            const double2 p = R[oc], q = R[oc + S];
-            a0 = dfma(0.5 * __ldg(d0 + 4 + c), make_double2(p.x + q.x, p.y + q.y), a0);
-        }
         const double* h = g.infl + ((size_t)d.im * g.nk + d.k) * 3 * g.nr;
         const double h0 = h[d.j], h1 = h[g.nr + d.j], h2 = h[2 * g.nr + d.j];
         ur = dfma(h0, a0, ur);
         ut = make_double2(ut.x - h1 * a0.y, ut.y + h1 * a0.x);
         uz = make_double2(uz.x - h2 * a0.y, uz.y + h2 * a0.x);
+    }
+    if (addto) {
+        const double2 a = addto[o], b = addto[o + S], c = addto[o + 2 * S];
+        ur.x += a.x; ur.y += a.y;
+        ut.x += b.x; ut.y += b.y;
+        uz.x += c.x; uz.y += c.y;
     }
     out[o] = ur;
     out[o + S] = ut;
@@ -631,36 +714,54 @@ __global__ void k_stageT_finish(Geo g, const double2* __restrict__ un, double2* 
     }
 }
 
-// ubar (+)= T^H B^T rbar ; Fb = T^H rbar
-__global__ void k_stageT_rhs(Geo g, const double2* __restrict__ R, double2* __restrict__ ub, int acc,
+// With X = cu1 R1 + cu2 R2 and Y = cf1 R1 + cf2 R2 (R2 may be null):
+// ub (=, or += when acc) T^H B^T X when ub is given ; Fb = T^H Y when Fb is given.
+template <bool TWO>
+__global__ void k_stageT_rhs(Geo g, const double2* __restrict__ R1, const double2* __restrict__ R2, double cu1,
+                             double cu2, double cf1, double cf2, double2* __restrict__ ub, int acc,
                              double2* __restrict__ Fb) {
     Idx d;
     if (!decode(g, (size_t)blockIdx.x * blockDim.x + threadIdx.x, d)) return;
     const size_t o = sidx(g, d.j, d.im, d.k), S = d.S;
-    const double kz = d.k * g.kz0;
-    const double dg = g.inv_dt - kz * kz * g.inv_2re;
-    const double2 bp0 = band_col(g, g.Lb + (size_t)abs(d.m + 1) * g.nr * kB, R, d.j, d.im, d.k);
-    const double2 bm0 = band_col(g, g.Lb + (size_t)abs(d.m - 1) * g.nr * kB, R + S, d.j, d.im, d.k);
-    const double2 bz0 = band_col(g, g.Lb + (size_t)abs(d.m) * g.nr * kB, R + 2 * S, d.j, d.im, d.k);
-    const double2 rp = R[o], rm = R[o + S], rz = R[o + 2 * S];
-    const double2 bp = make_double2(dg * rp.x + g.inv_2re * bp0.x, dg * rp.y + g.inv_2re * bp0.y);
-    const double2 bm = make_double2(dg * rm.x + g.inv_2re * bm0.x, dg * rm.y + g.inv_2re * bm0.y);
-    const double2 bz = make_double2(dg * rz.x + g.inv_2re * bz0.x, dg * rz.y + g.inv_2re * bz0.y);
-    double2 vr = make_double2(bp.x + bm.x, bp.y + bm.y);
-    double2 vt = make_double2(bp.y - bm.y, -bp.x + bm.x);
-    double2 vz = bz;
-    if (acc) {
-        const double2 a = ub[o], b = ub[o + S], c = ub[o + 2 * S];
-        vr.x += a.x; vr.y += a.y;
-        vt.x += b.x; vt.y += b.y;
-        vz.x += c.x; vz.y += c.y;
+    auto comb = [&](size_t i, double a1, double a2) {
+        const double2 p = R1[i];
+        if (!TWO) return make_double2(a1 * p.x, a1 * p.y);
+        const double2 q = R2[i];
+        return make_double2(a1 * p.x + a2 * q.x, a1 * p.y + a2 * q.y);
+    };
+    if (ub) {
+        const double kz = d.k * g.kz0;
+        const double dg = g.inv_dt - kz * kz * g.inv_2re;
+        const double2 bp0 = band_col2<TWO>(g, g.Lb + (size_t)abs(d.m + 1) * g.nr * kB, R1, cu1, R2, cu2, d.j, d.im, d.k);
+        const double2 bm0 =
+            band_col2<TWO>(g, g.Lb + (size_t)abs(d.m - 1) * g.nr * kB, R1 + S, cu1, TWO ? R2 + S : nullptr, cu2, d.j, d.im, d.k);
+        const double2 bz0 =
+            band_col2<TWO>(g, g.Lb + (size_t)abs(d.m) * g.nr * kB, R1 + 2 * S, cu1, TWO ? R2 + 2 * S : nullptr, cu2, d.j, d.im, d.k);
+        const double2 rp = comb(o, cu1, cu2), rm = comb(o + S, cu1, cu2), rz = comb(o + 2 * S, cu1, cu2);
+        // band_col2<false> ignores the coefficient: scale here
+        const double sb = TWO ? 1.0 : cu1;
+        const double2 bp = make_double2(dg * rp.x + g.inv_2re * sb * bp0.x, dg * rp.y + g.inv_2re * sb * bp0.y);
+        const double2 bm = make_double2(dg * rm.x + g.inv_2re * sb * bm0.x, dg * rm.y + g.inv_2re * sb * bm0.y);
+        const double2 bz = make_double2(dg * rz.x + g.inv_2re * sb * bz0.x, dg * rz.y + g.inv_2re * sb * bz0.y);
+        double2 vr = make_double2(bp.x + bm.x, bp.y + bm.y);
+        double2 vt = make_double2(bp.y - bm.y, -bp.x + bm.x);
+        double2 vz = bz;
+        if (acc) {
+            const double2 a = ub[o], b = ub[o + S], c = ub[o + 2 * S];
+            vr.x += a.x; vr.y += a.y;
+            vt.x += b.x; vt.y += b.y;
+            vz.x += c.x; vz.y += c.y;
+        }
+        ub[o] = vr;
+        ub[o + S] = vt;
+        ub[o + 2 * S] = vz;
     }
-    ub[o] = vr;
-    ub[o + S] = vt;
-    ub[o + 2 * S] = vz;
-    Fb[o] = make_double2(rp.x + rm.x, rp.y + rm.y);
-    Fb[o + S] = make_double2(rp.y - rm.y, -rp.x + rm.x);
-    Fb[o + 2 * S] = rz;
+    if (Fb) {
+        const double2 rp = comb(o, cf1, cf2), rm = comb(o + S, cf1, cf2), rz = comb(o + 2 * S, cf1, cf2);
+        Fb[o] = make_double2(rp.x + rm.x, rp.y + rm.y);
+        Fb[o + S] = make_double2(rp.y - rm.y, -rp.x + rm.x);
+        Fb[o + 2 * S] = rz;
+    }
 }
 
 // qbar = G^H Fb' = D1p^T Fb'_r - i (m/r) Fb'_t - i kz Fb'_z
@@ -799,31 +900,49 @@ template <class T2> static int theta_kb(const Geo& g) {
     return kb;
 }
 
-template <class T2>
-void launch_synth_theta(const Geo& g, const FieldPtrs& f, int nfield, T2* Y, const Twiddles& tw, cudaStream_t s) {
-    const int KB = theta_kb<T2>(g);
+template <class T2, int KB>
+static void synth_theta_kb(const Geo& g, const FieldPtrs& f, int nfield, T2* Y, const T2* tw, cudaStream_t s) {
     const size_t sm = (size_t)(2 * g.nt * KB + g.nt) * sizeof(T2);
     static bool attr = false;
     if (!attr) {
-        cudaFuncSetAttribute(k_synth_theta<T2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        cudaFuncSetAttribute(k_synth_theta<T2, KB>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
         attr = true;
     }
     dim3 grid((g.nk + KB - 1) / KB, g.nr, nfield);
-    k_synth_theta<T2><<<grid, 256, sm, s>>>(g, f, Y, tw_theta<T2>(tw), KB);
+    k_synth_theta<T2, KB><<<grid, 256, sm, s>>>(g, f, Y, tw);
+}
+
+template <class T2, int KB>
+static void anal_theta_kb(const Geo& g, const FieldPtrs& f, int nfield, const T2* Z, const T2* tw, cudaStream_t s) {
+    const size_t sm = (size_t)(2 * g.nt * KB + g.nt) * sizeof(T2);
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_anal_theta<T2, KB>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        attr = true;
+    }
+    dim3 grid((g.nk + KB - 1) / KB, g.nr, nfield);
+    k_anal_theta<T2, KB><<<grid, 256, sm, s>>>(g, f, Z, tw);
+}
+
+template <class T2>
+void launch_synth_theta(const Geo& g, const FieldPtrs& f, int nfield, T2* Y, const Twiddles& tw, cudaStream_t s) {
+    switch (theta_kb<T2>(g)) {
+        case 32: synth_theta_kb<T2, 32>(g, f, nfield, Y, tw_theta<T2>(tw), s); break;
+        case 16: synth_theta_kb<T2, 16>(g, f, nfield, Y, tw_theta<T2>(tw), s); break;
+        case 8: synth_theta_kb<T2, 8>(g, f, nfield, Y, tw_theta<T2>(tw), s); break;
+        default: synth_theta_kb<T2, 4>(g, f, nfield, Y, tw_theta<T2>(tw), s); break;
+    }
     check_launch("synth_theta");
 }
 
 template <class T2>
 void launch_anal_theta(const Geo& g, const FieldPtrs& f, int nfield, const T2* Z, const Twiddles& tw, cudaStream_t s) {
-    const int KB = theta_kb<T2>(g);
-    const size_t sm = (size_t)(2 * g.nt * KB + g.nt) * sizeof(T2);
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(k_anal_theta<T2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        attr = true;
+    switch (theta_kb<T2>(g)) {
+        case 32: anal_theta_kb<T2, 32>(g, f, nfield, Z, tw_theta<T2>(tw), s); break;
+        case 16: anal_theta_kb<T2, 16>(g, f, nfield, Z, tw_theta<T2>(tw), s); break;
+        case 8: anal_theta_kb<T2, 8>(g, f, nfield, Z, tw_theta<T2>(tw), s); break;
+        default: anal_theta_kb<T2, 4>(g, f, nfield, Z, tw_theta<T2>(tw), s); break;
     }
-    dim3 grid((g.nk + KB - 1) / KB, g.nr, nfield);
-    k_anal_theta<T2><<<grid, 256, sm, s>>>(g, f, Z, tw_theta<T2>(tw), KB);
     check_launch("anal_theta");
 }
 
@@ -899,8 +1018,13 @@ void launch_stage_hsolve(const Geo& g, double2* R, cudaStream_t s) {
     launch_band_solve(g, g.facH, R, 1, 0, s);
     check_launch("stage_hsolve");
 }
-void launch_stage_finish(const Geo& g, const double2* R, double2* out, cudaStream_t s) {
-    k_stage_finish<<<nblk(S_of(g), 256), 256, 0, s>>>(g, R, out);
+void launch_stage_a0(const Geo& g, const double2* R, double2* a0, cudaStream_t s) {
+    k_stage_a0<<<nblk((size_t)g.nm * g.nk, 128), 128, 0, s>>>(g, R, a0);
+    check_launch("stage_a0");
+}
+void launch_stage_finish(const Geo& g, const double2* R, const double2* a0, const double2* addto, double2* out,
+                         cudaStream_t s) {
+    k_stage_finish<<<nblk(S_of(g), 256), 256, 0, s>>>(g, R, a0, addto, out);
     check_launch("stage_finish");
 }
 void launch_stageT_finish(const Geo& g, const double2* ubn, double2* R, cudaStream_t s) {
@@ -911,8 +1035,12 @@ void launch_stageT_hsolve(const Geo& g, double2* R, cudaStream_t s) {
     launch_band_solve(g, g.facHT, R, 1, 1, s);
     check_launch("stageT_hsolve");
 }
-void launch_stageT_rhs(const Geo& g, const double2* R, double2* ub, int acc, double2* Fb, cudaStream_t s) {
-    k_stageT_rhs<<<nblk(S_of(g), 256), 256, 0, s>>>(g, R, ub, acc, Fb);
+void launch_stageT_rhs(const Geo& g, const double2* R1, const double2* R2, double cu1, double cu2, double cf1,
+                       double cf2, double2* ub, int acc, double2* Fb, cudaStream_t s) {
+    if (R2)
+        k_stageT_rhs<true><<<nblk(S_of(g), 256), 256, 0, s>>>(g, R1, R2, cu1, cu2, cf1, cf2, ub, acc, Fb);
+    else
+        k_stageT_rhs<false><<<nblk(S_of(g), 256), 256, 0, s>>>(g, R1, R2, cu1, cu2, cf1, cf2, ub, acc, Fb);
     check_launch("stageT_rhs");
 }
 void launch_stageT_qbar(const Geo& g, const double2* Fb, double2* q, cudaStream_t s) {

@@ -71,13 +71,20 @@ void launch_anal_theta(const Geo& g, const FieldPtrs& f, int nfield, const T2* Z
 // out = back to (r, theta, z) + influence / flux corrections (Section 2.4).
 void launch_stage_div(const Geo& g, const double2* F, double2* q, cudaStream_t s);
 void launch_stage_psolve(const Geo& g, double2* q, cudaStream_t s);
+// u may be null: forcing-only stage S(0, F)
 void launch_stage_rhs(const Geo& g, const double2* u, const double2* F, const double2* p, double2* R, cudaStream_t s);
 void launch_stage_hsolve(const Geo& g, double2* R, cudaStream_t s);
-void launch_stage_finish(const Geo& g, const double2* R, double2* out, cudaStream_t s);
+// per-mode wall coefficients a0 (influence) / flux sums (mode (0,0)) into a0[nm*nk]
+void launch_stage_a0(const Geo& g, const double2* R, double2* a0, cudaStream_t s);
+// out = [addto +] finished stage (addto may be null)
+void launch_stage_finish(const Geo& g, const double2* R, const double2* a0, const double2* addto, double2* out,
+                         cudaStream_t s);
 // ---- radial stage (transpose): ub (=, or += when acc) S_u^H ubn, Fb = S_F^H ubn ----
 void launch_stageT_finish(const Geo& g, const double2* ubn, double2* R, cudaStream_t s);
 void launch_stageT_hsolve(const Geo& g, double2* R, cudaStream_t s);
-void launch_stageT_rhs(const Geo& g, const double2* R, double2* ub, int acc, double2* Fb, cudaStream_t s);
+// X = cu1 R1 + cu2 R2, Y = cf1 R1 + cf2 R2 (R2 may be null): ub (+)= T^H B^T X if ub, Fb = T^H Y if Fb
+void launch_stageT_rhs(const Geo& g, const double2* R1, const double2* R2, double cu1, double cu2, double cf1,
+                       double cf2, double2* ub, int acc, double2* Fb, cudaStream_t s);
 void launch_stageT_qbar(const Geo& g, const double2* Fb, double2* q, cudaStream_t s);
 void launch_stageT_psolve(const Geo& g, double2* q, cudaStream_t s);
 void launch_stageT_div(const Geo& g, const double2* z, double2* Fb, cudaStream_t s);

@@ -64,6 +64,7 @@ struct pnop_ctx {
     double2* ubs = nullptr;
     double2* wb = nullptr;
     double2* R = nullptr;
+    double2* Rl = nullptr;  // front part of the transposed stage for the incoming cotangent
     double2* q = nullptr;
     double2 *tmpA = nullptr, *tmpB = nullptr, *lamA = nullptr, *lamB = nullptr;
     void* Y = nullptr;
@@ -203,29 +204,57 @@ template <class F> void run(pnop_ctx* c, int cls, int nk, double units, F&& f) {
 
 double nmodes(const pnop_ctx* c) { return (double)c->h.d.nm * c->h.d.nk; }
 
-// out = S(u, F), one predictor-corrector stage (Section 2.4)
-void stage(pnop_ctx* c, const double2* u, const double2* F, double2* out) {
+// Algorithmic FP64 flops per value of the banded/spectral kernels (work units
+// of the RADIAL_BAND and SPECTRAL classes): a 9-entry band row on a complex
+// value is 36 flops; the remaining terms are counted as written.
+namespace flops {
+constexpr double div = 36 + 12, rhs_u = 36 + 12 + 3 * 36 + 24, rhs_f = 36 + 12 + 8, a0_mode = 72, finish = 20;
+constexpr double tfinish = 36, trhs_u = 3 * 36 + 30, trhs_f = 8, qbar = 36 + 8, tdiv = 36 + 12;
+constexpr double curl = 2 * 36 + 16, curlT = 2 * 36 + 20, base = 12;
+}  // namespace flops
+
+// out = [addto +] S(u, F), one predictor-corrector stage (Section 2.4); u may
+// be null (forcing only, S(0, F)), which skips the explicit viscous matvec.
+void stage(pnop_ctx* c, const double2* u, const double2* F, double2* out, const double2* addto = nullptr) {
     const Geo& g = c->geo;
     cudaStream_t s = c->stream;
     const double S = (double)c->S();
-    run(c, PNOP_K_RADIAL_BAND, 1, S, [&] { pnop::launch_stage_div(g, F, c->q, s); });
+    run(c, PNOP_K_RADIAL_BAND, 1, flops::div * S, [&] { pnop::launch_stage_div(g, F, c->q, s); });
     run(c, PNOP_K_RADIAL_SOLVE, 1, nmodes(c), [&] { pnop::launch_stage_psolve(g, c->q, s); });
-    run(c, PNOP_K_RADIAL_BAND, 1, 3 * S, [&] { pnop::launch_stage_rhs(g, u, F, c->q, c->R, s); });
+    run(c, PNOP_K_RADIAL_BAND, 1, (u ? flops::rhs_u : flops::rhs_f) * S,
+        [&] { pnop::launch_stage_rhs(g, u, F, c->q, c->R, s); });
     run(c, PNOP_K_RADIAL_SOLVE, 1, 3 * nmodes(c), [&] { pnop::launch_stage_hsolve(g, c->R, s); });
-    run(c, PNOP_K_RADIAL_BAND, 1, 3 * S, [&] { pnop::launch_stage_finish(g, c->R, out, s); });
+    // the pressure is consumed: q now holds the per-mode wall coefficients
+    run(c, PNOP_K_RADIAL_BAND, 1, flops::a0_mode * nmodes(c), [&] { pnop::launch_stage_a0(g, c->R, c->q, s); });
+    run(c, PNOP_K_RADIAL_BAND, 1, flops::finish * S, [&] { pnop::launch_stage_finish(g, c->R, c->q, addto, out, s); });
 }
 
-// ub (=, or += when acc) S_u^H ubn ; Fb = S_F^H ubn
-void stageT(pnop_ctx* c, const double2* ubn, double2* ub, int acc, double2* Fb) {
+// Rb = E A^{-T} Ti^H Fin^H ubn: the part of the transposed stage shared by
+// its velocity and forcing cotangents.
+void stageT_front(pnop_ctx* c, const double2* ubn, double2* Rb) {
+    const Geo& g = c->geo;
+    cudaStream_t s = c->stream;
+    run(c, PNOP_K_RADIAL_BAND, 1, flops::tfinish * c->S(), [&] { pnop::launch_stageT_finish(g, ubn, Rb, s); });
+    run(c, PNOP_K_RADIAL_SOLVE, 1, 3 * nmodes(c), [&] { pnop::launch_stageT_hsolve(g, Rb, s); });
+}
+
+// Fb <- Proj^H Fb (transposed pressure projection, in place)
+void stageT_proj(pnop_ctx* c, double2* Fb) {
     const Geo& g = c->geo;
     cudaStream_t s = c->stream;
     const double S = (double)c->S();
-    run(c, PNOP_K_RADIAL_BAND, 1, 3 * S, [&] { pnop::launch_stageT_finish(g, ubn, c->R, s); });
-    run(c, PNOP_K_RADIAL_SOLVE, 1, 3 * nmodes(c), [&] { pnop::launch_stageT_hsolve(g, c->R, s); });
-    run(c, PNOP_K_RADIAL_BAND, 1, 3 * S, [&] { pnop::launch_stageT_rhs(g, c->R, ub, acc, Fb, s); });
-    run(c, PNOP_K_RADIAL_BAND, 1, S, [&] { pnop::launch_stageT_qbar(g, Fb, c->q, s); });
+    run(c, PNOP_K_RADIAL_BAND, 1, flops::qbar * S, [&] { pnop::launch_stageT_qbar(g, Fb, c->q, s); });
     run(c, PNOP_K_RADIAL_SOLVE, 1, nmodes(c), [&] { pnop::launch_stageT_psolve(g, c->q, s); });
-    run(c, PNOP_K_RADIAL_BAND, 1, S, [&] { pnop::launch_stageT_div(g, c->q, Fb, s); });
+    run(c, PNOP_K_RADIAL_BAND, 1, flops::tdiv * S, [&] { pnop::launch_stageT_div(g, c->q, Fb, s); });
+}
+
+// ub (=, or += when acc) S_u^H ubn ; Fb = S_F^H ubn  (either may be null)
+void stageT(pnop_ctx* c, const double2* ubn, double2* ub, int acc, double2* Fb) {
+    const Geo& g = c->geo;
+    stageT_front(c, ubn, c->R);
+    run(c, PNOP_K_RADIAL_BAND, 1, ((ub ? flops::trhs_u : 0) + (Fb ? flops::trhs_f : 0)) * c->S(),
+        [&] { pnop::launch_stageT_rhs(g, c->R, nullptr, 1.0, 0.0, 1.0, 0.0, ub, acc, Fb, c->stream); });
+    if (Fb) stageT_proj(c, Fb);
 }
 
 void axpby(pnop_ctx* c, double a, const double2* x, double b, const double2* y, double2* out) {
@@ -262,7 +291,7 @@ void nonlinear(pnop_ctx* c, const double2* u, double t, double2* N) {
     const Geo& g = c->geo;
     const size_t S = c->S();
     cudaStream_t s = c->stream;
-    run(c, PNOP_K_SPECTRAL, 1, (double)S, [&] { pnop::launch_curl(g, u, c->omega, s); });
+    run(c, PNOP_K_SPECTRAL, 1, flops::curl * S, [&] { pnop::launch_curl(g, u, c->omega, s); });
     pnop::FieldPtrs f{};
     for (int i = 0; i < 3; ++i) {
         f.in[i] = u + i * S;
@@ -275,7 +304,7 @@ void nonlinear(pnop_ctx* c, const double2* u, double t, double2* N) {
     for (int i = 0; i < 3; ++i) sc.o0[i] = sc.ok[i] = inv_n;
     transforms(c, f, 6, 3, pnop::ZFWD, sc);
     const double ph = c->h.omega * t;
-    run(c, PNOP_K_SPECTRAL, 1, (double)S, [&] { pnop::launch_base_add(g, u, c->omega, N, std::cos(ph), std::sin(ph), s); });
+    run(c, PNOP_K_SPECTRAL, 1, flops::base * S, [&] { pnop::launch_base_add(g, u, c->omega, N, std::cos(ph), std::sin(ph), s); });
 }
 
 // ub = (dN/du at u)^T nb  (Euclidean cotangents)
@@ -283,7 +312,7 @@ void nonlinearT(pnop_ctx* c, const double2* u, double t, const double2* nb, doub
     const Geo& g = c->geo;
     const size_t S = c->S();
     cudaStream_t s = c->stream;
-    run(c, PNOP_K_SPECTRAL, 1, (double)S, [&] { pnop::launch_curl(g, u, c->omega, s); });
+    run(c, PNOP_K_SPECTRAL, 1, flops::curl * S, [&] { pnop::launch_curl(g, u, c->omega, s); });
     pnop::FieldPtrs f{};
     for (int i = 0; i < 3; ++i) {
         f.in[i] = u + i * S;
@@ -307,28 +336,40 @@ void nonlinearT(pnop_ctx* c, const double2* u, double t, const double2* nb, doub
     }
     transforms(c, f, 9, 6, pnop::ZADJ, sc);
     const double ph = c->h.omega * t;
-    run(c, PNOP_K_SPECTRAL, 1, (double)S, [&] { pnop::launch_baseT_acc(g, nb, ub, c->wb, std::cos(ph), std::sin(ph), s); });
-    run(c, PNOP_K_SPECTRAL, 1, (double)S, [&] { pnop::launch_curlT_acc(g, c->wb, ub, s); });
+    run(c, PNOP_K_SPECTRAL, 1, flops::base * S, [&] { pnop::launch_baseT_acc(g, nb, ub, c->wb, std::cos(ph), std::sin(ph), s); });
+    run(c, PNOP_K_SPECTRAL, 1, flops::curlT * S, [&] { pnop::launch_curlT_acc(g, c->wb, ub, s); });
 }
 
 // ------------------------------------------------------------------ steps
+// Predictor u* = S(u, N0), corrector S(u, (N0 + N*)/2) = u* + S(0, (N* - N0)/2)
+// (S is linear), so the corrector skips the explicit viscous matvec.
 void fwd_step(pnop_ctx* c, const double2* u, double2* out, double t) {
     nonlinear(c, u, t, c->N0);
     stage(c, u, c->N0, c->us);
     nonlinear(c, c->us, t + c->h.ph.dt, c->N1);
-    axpby(c, 0.5, c->N0, 0.5, c->N1, c->N1);
-    stage(c, u, c->N1, out);
+    axpby(c, 0.5, c->N1, -0.5, c->N0, c->N1);
+    stage(c, nullptr, c->N1, out, c->us);
 }
 
-// lout = J^T lin (Euclidean cotangents) for the step from state u at time t
+// lout = J^T lin (Euclidean cotangents) for the step from state u at time t.
+// With u' = S_u u + S_F (N0 + N*)/2, u* = S_u u + S_F N0, N* = N(u*), N0 = N(u):
+//   Fb = S_F^H lin, ub* = N*'^T (Fb/2),
+//   ubar = S_u^H (lin + ub*) + N0'^T S_F^H (lin/2 + ub*).
+// S_u^H and S_F^H share their front part (Rl for lin, R for ub*), so the
+// transposed viscous matvec runs once, on Rl + R.
 void adj_step(pnop_ctx* c, const double2* u, double t, const double2* lin, double2* lout) {
+    const Geo& g = c->geo;
     nonlinear(c, u, t, c->N0);
     stage(c, u, c->N0, c->us);
-    stageT(c, lin, c->ua, 0, c->Fb);
-    axpby(c, 0.5, c->Fb, 0.0, nullptr, c->Nb);
+    stageT_front(c, lin, c->Rl);
+    run(c, PNOP_K_RADIAL_BAND, 1, flops::trhs_f * c->S(),
+        [&] { pnop::launch_stageT_rhs(g, c->Rl, nullptr, 0.0, 0.0, 0.5, 0.0, nullptr, 0, c->Nb, c->stream); });
+    stageT_proj(c, c->Nb);  // Nb = S_F^H lin / 2
     nonlinearT(c, c->us, t + c->h.ph.dt, c->Nb, c->ubs);
-    stageT(c, c->ubs, c->ua, 1, c->N0);
-    axpby(c, 1.0, c->N0, 0.5, c->Fb, c->Nb);
+    stageT_front(c, c->ubs, c->R);
+    run(c, PNOP_K_RADIAL_BAND, 1, (flops::trhs_u + flops::trhs_f) * c->S(),
+        [&] { pnop::launch_stageT_rhs(g, c->Rl, c->R, 1.0, 1.0, 0.5, 1.0, c->ua, 0, c->Nb, c->stream); });
+    stageT_proj(c, c->Nb);  // Nb = S_F^H (lin/2 + ub*)
     nonlinearT(c, u, t, c->Nb, c->ubs);
     axpby(c, 1.0, c->ua, 1.0, c->ubs, lout);
 }
@@ -554,7 +595,7 @@ int pnop_create(const pnop_grid* grid, const pnop_params* params, void* cuda_str
         c->tw.th_f = c->upload(thf);
         c->tw.z_f = c->upload(zf);
         for (double2** b : {&c->omega, &c->N0, &c->N1, &c->us, &c->ua, &c->Fb, &c->Nb, &c->ubs, &c->wb, &c->R,
-                            &c->tmpA, &c->tmpB, &c->lamA, &c->lamB})
+                            &c->Rl, &c->tmpA, &c->tmpB, &c->lamA, &c->lamB})
             *b = c->field();
         c->q = (double2*)c->dalloc(c->S() * sizeof(double2));
         const size_t cz = mixed(c) ? sizeof(float2) : sizeof(double2);
@@ -671,7 +712,7 @@ int pnop_apply(pnop_ctx* ctx, int op, const void* a, const void* b, void* out, d
         double2* O = (double2*)out;
         const Geo& g = ctx->geo;
         switch (op) {
-            case PNOP_OP_CURL: run(ctx, PNOP_K_SPECTRAL, 1, (double)ctx->S(), [&] { pnop::launch_curl(g, A, O, ctx->stream); }); break;
+            case PNOP_OP_CURL: run(ctx, PNOP_K_SPECTRAL, 1, flops::curl * ctx->S(), [&] { pnop::launch_curl(g, A, O, ctx->stream); }); break;
             case PNOP_OP_NONLINEAR: nonlinear(ctx, A, t, O); break;
             case PNOP_OP_STAGE:
                 if (!B) throw Status(PNOP_ERR_INVALID_ARG, "stage needs a forcing field");
