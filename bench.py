@@ -372,6 +372,8 @@ def main():
     ap.add_argument("--snaps", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--precision", default="both", choices=["both", "mixed", "fp64"],
+                    help="which path(s) to time; 'fp64' reports the FP64 path as the main line")
     args = ap.parse_args()
     if args.impl == "reference":
         return reference_main(args)
@@ -390,17 +392,20 @@ def main():
     peaks, pk_src = load_peaks()
     H, s = args.horizon_steps, args.snaps
     sampler = ClockSampler(local) if rank == 0 else None
-    mix = time_gradient(L, torch, L.PNOP_MIXED, args.steps, args.warmup, H, s, ws, rank, sampler)
+    if args.precision == "fp64":
+        args.no_fp64 = True
+    main_prec = L.PNOP_FP64 if args.precision == "fp64" else L.PNOP_MIXED
+    mix = time_gradient(L, torch, main_prec, args.steps, args.warmup, H, s, ws, rank, sampler)
     ms = max_over_ranks(mix["ms"], ws)
     value = H * args.steps * ws / (ms / 1e3)
     fp64 = None
-    if not args.no_fp64:
+    if not args.no_fp64 and args.precision != "mixed":
         f = time_gradient(L, torch, L.PNOP_FP64, args.steps, args.warmup, H, s, ws, rank, None)
         fms = max_over_ranks(f["ms"], ws)
         fp64 = {"value": H * args.steps * ws / (fms / 1e3), "unit": "steps/s", "ms_per_step": fms / args.steps,
                 "gain": f["gain"], "dtype": "f64", "roofline": roofline(L, f, False, peaks, pk_src),
                 "kernels_ms_per_step": {k: v[0] for k, v in f["warm_profile"].items()}}
-    e2e_s = time_e2e(L, torch, L.PNOP_MIXED, args.steps, args.warmup, H, s)
+    e2e_s = time_e2e(L, torch, main_prec, args.steps, args.warmup, H, s)
     e2e_s = max_over_ranks(e2e_s, ws)
     if rank != 0:
         return 0
@@ -409,14 +414,14 @@ def main():
         "metric": "fwd+adj steps/s at 64x64x256, mixed vs FP64 on 1 GB300",
         "value": value, "unit": "steps/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32+f64", "data": "synthetic",
+        "dtype": "f64" if main_prec == L.PNOP_FP64 else "f32+f64", "data": "synthetic",
         "config": {"workload": workload_name(H, s), "horizon_steps": H, "snap_budget": s,
                    "advances_per_gradient": mix["advances"], "adjoint_steps_per_gradient": mix["adjoint_steps"],
                    "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
                    "l2": f"inputs and working set > L2 (state {FIELD_BYTES / 2**20:.1f} MiB x >20 buffers + transform"
                          " scratch); no flush"},
         "gain": mix["gain"],
-        "roofline": roofline(L, mix, True, peaks, pk_src),
+        "roofline": roofline(L, mix, main_prec == L.PNOP_MIXED, peaks, pk_src),
         "kernels_ms_per_step": {k: v[0] for k, v in mix["warm_profile"].items()},
         "fp64": fp64,
         "speedup_mixed_over_fp64": (value / fp64["value"]) if fp64 else None,
