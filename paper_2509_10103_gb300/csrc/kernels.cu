@@ -46,13 +46,18 @@ template <class T2> __device__ __forceinline__ double2 to_d(T2 v) { return make_
 
 __device__ __forceinline__ int par_idx(int m) { return m & 1; }  // 0 even, 1 odd (two's complement)
 
+// scale factor of the transform precision (no FP64->FP32 conversion in FP32 kernels)
+template <class T> __device__ __forceinline__ T zs(const double* d, const float* f, int i);
+template <> __device__ __forceinline__ double zs<double>(const double* d, const float*, int i) { return d[i]; }
+template <> __device__ __forceinline__ float zs<float>(const double*, const float* f, int i) { return f[i]; }
+
 // ------------------------------------------------------------------ shared-memory FFT
 // Batched Stockham FFT (autosort) over `ncol` columns of length N stored as
 // a[n * ld + col].  Radix 4, then 2, then 3 stages; N = 2^p 3^q.  tw holds
 // e^{-2 pi i n / N}; sign = -1 forward, +1 inverse (unnormalised).  Returns the
 // buffer holding the result.  All threads of the block must call it.
 template <class T2>
-__device__ __forceinline__ void small_dft(T2* v, int R, int sign) {
+__device__ __forceinline__ void small_dft(T2* v, const int R, const int sign) {
     using T = typename RealOf<T2>::T;
     if (R == 2) {
         T2 a = v[0], b = v[1];
@@ -81,9 +86,9 @@ __device__ __forceinline__ void small_dft(T2* v, int R, int sign) {
 // One radix-R Stockham stage.  Ns (the size of the sub-transforms already
 // done) is a power of two 2^lgNs for every stage but the second and later
 // radix-3 stages (radix 3 runs last), so the index split is a shift there.
-template <class T2, int R, int NCOL, int LD>
+template <class T2, int R, int NCOL, int LD, int SIGN>
 __device__ __forceinline__ void fft_stage(const T2* __restrict__ a, T2* __restrict__ b, int N, int Ns, int lgNs,
-                                          const T2* __restrict__ tw, int sign) {
+                                          const T2* __restrict__ tw) {
     const int stride = N / R;
     const int nb = stride * NCOL;
     const int tstep = N / (Ns * R);
@@ -101,42 +106,44 @@ __device__ __forceinline__ void fft_stage(const T2* __restrict__ a, T2* __restri
         T2 v[R];
 #pragma unroll
         for (int r = 0; r < R; ++r) v[r] = a[(jb + r * stride) * LD + col];
-        const int tb = kk * tstep;  // r * tb < N
+        if (Ns > 1) {  // the first stage has unit twiddles
+            const int tb = kk * tstep;  // r * tb < N
 #pragma unroll
-        for (int r = 1; r < R; ++r) {
-            T2 w = tw[r * tb];
-            if (sign > 0) w.y = -w.y;
-            v[r] = cmul(v[r], w);
+            for (int r = 1; r < R; ++r) {
+                T2 w = tw[r * tb];
+                if (SIGN > 0) w.y = -w.y;
+                v[r] = cmul(v[r], w);
+            }
         }
-        small_dft(v, R, sign);
+        small_dft(v, R, SIGN);
         const int idxD = q * Ns * R + kk;
 #pragma unroll
         for (int r = 0; r < R; ++r) b[(idxD + r * Ns) * LD + col] = v[r];
     }
 }
 
-template <class T2, int NCOL, int LD>
-__device__ T2* fft_cols(T2* a, T2* b, int N, const T2* tw, int sign) {
+template <class T2, int NCOL, int LD, int SIGN>
+__device__ T2* fft_cols(T2* a, T2* b, int N, const T2* tw) {
     const int n2 = __ffs(N) - 1;  // N = 2^n2 3^n3
     int n3 = 0;
     for (int t = N >> n2; t > 1; t /= 3) ++n3;
     int Ns = 1, lgNs = 0;
     for (int st = 0; st < n2 / 2; ++st) {
-        fft_stage<T2, 4, NCOL, LD>(a, b, N, Ns, lgNs, tw, sign);
+        fft_stage<T2, 4, NCOL, LD, SIGN>(a, b, N, Ns, lgNs, tw);
         __syncthreads();
         T2* t = a; a = b; b = t;
         Ns *= 4;
         lgNs += 2;
     }
     if (n2 & 1) {
-        fft_stage<T2, 2, NCOL, LD>(a, b, N, Ns, lgNs, tw, sign);
+        fft_stage<T2, 2, NCOL, LD, SIGN>(a, b, N, Ns, lgNs, tw);
         __syncthreads();
         T2* t = a; a = b; b = t;
         Ns *= 2;
         lgNs += 1;
     }
     for (int st = 0; st < n3; ++st) {
-        fft_stage<T2, 3, NCOL, LD>(a, b, N, Ns, st == 0 ? lgNs : -1, tw, sign);
+        fft_stage<T2, 3, NCOL, LD, SIGN>(a, b, N, Ns, st == 0 ? lgNs : -1, tw);
         __syncthreads();
         T2* t = a; a = b; b = t;
         Ns *= 3;
@@ -167,7 +174,7 @@ __global__ void k_synth_theta(Geo g, FieldPtrs f, T2* __restrict__ Y, const T2* 
         }
     }
     __syncthreads();
-    T2* res = fft_cols<T2, KB, KB>(buf0, buf1, g.nt, tw, +1);
+    T2* res = fft_cols<T2, KB, KB, +1>(buf0, buf1, g.nt, tw);
     T2* dst = Y + ((size_t)(fi * g.nr + j) * g.nt) * g.nk;
     for (int i = threadIdx.x; i < g.nt * KB; i += blockDim.x) {
         const int a = i / KB, kk = i % KB;
@@ -208,11 +215,13 @@ __global__ void k_zpass(Geo g, const T2* __restrict__ Y, T2* __restrict__ Z, ZSc
         if (k >= 0) {
             const int f1 = 2 * p, f2 = 2 * p + 1;
             T2 y1 = Y[((size_t)(f1 * g.nr + j) * g.nt + a) * nk + k];
-            T2 h1 = k == 0 ? mk<T2>((T)sc.h0[f1] * y1.x, 0) : mk<T2>((T)sc.hk[f1] * y1.x, (T)sc.hk[f1] * y1.y);
+            T2 h1 = k == 0 ? mk<T2>(zs<T>(sc.h0, sc.fh0, f1) * y1.x, 0)
+                           : mk<T2>(zs<T>(sc.hk, sc.fhk, f1) * y1.x, zs<T>(sc.hk, sc.fhk, f1) * y1.y);
             T2 h2 = mk<T2>(0, 0);
             if (f2 < NIN) {
                 T2 y2 = Y[((size_t)(f2 * g.nr + j) * g.nt + a) * nk + k];
-                h2 = k == 0 ? mk<T2>((T)sc.h0[f2] * y2.x, 0) : mk<T2>((T)sc.hk[f2] * y2.x, (T)sc.hk[f2] * y2.y);
+                h2 = k == 0 ? mk<T2>(zs<T>(sc.h0, sc.fh0, f2) * y2.x, 0)
+                            : mk<T2>(zs<T>(sc.hk, sc.fhk, f2) * y2.x, zs<T>(sc.hk, sc.fhk, f2) * y2.y);
             }
             if (!neg) q = mk<T2>(h1.x - h2.y, h1.y + h2.x);   // H1 + i H2
             else q = mk<T2>(h1.x + h2.y, -h1.y + h2.x);       // conj(H1) + i conj(H2)
@@ -220,7 +229,7 @@ __global__ void k_zpass(Geo g, const T2* __restrict__ Y, T2* __restrict__ Z, ZSc
         bufA[n * LD + p] = q;
     }
     __syncthreads();
-    T2* ph = fft_cols<T2, NPI, LD>(bufA, bufB, N, tw, +1);
+    T2* ph = fft_cols<T2, NPI, LD, +1>(bufA, bufB, N, tw);
     T2* pr = (ph == bufA) ? bufB : bufA;
     for (int n = threadIdx.x; n < N; n += blockDim.x) {
         const T2* row = ph + n * LD;
@@ -241,17 +250,17 @@ __global__ void k_zpass(Geo g, const T2* __restrict__ Y, T2* __restrict__ Z, ZSc
         }
     }
     __syncthreads();
-    T2* sp = fft_cols<T2, NPO, LD>(pr, ph, N, tw, -1);
+    T2* sp = fft_cols<T2, NPO, LD, -1>(pr, ph, N, tw);
     for (int i = threadIdx.x; i < NPO * nk; i += blockDim.x) {
         const int p = i / nk, k = i % nk;
         const T2 P = sp[k * LD + p];
         const T2 Pm = sp[((N - k) % N) * LD + p];
         const int o1 = 2 * p, o2 = 2 * p + 1;
-        const T s1 = (T)(k == 0 ? sc.o0[o1] : sc.ok[o1]);
+        const T s1 = k == 0 ? zs<T>(sc.o0, sc.fo0, o1) : zs<T>(sc.ok, sc.fok, o1);
         T2 z1 = mk<T2>((T)0.5 * (P.x + Pm.x) * s1, (T)0.5 * (P.y - Pm.y) * s1);
         Z[((size_t)(o1 * g.nr + j) * g.nt + a) * nk + k] = z1;
         if (o2 < NOUT) {
-            const T s2 = (T)(k == 0 ? sc.o0[o2] : sc.ok[o2]);
+            const T s2 = k == 0 ? zs<T>(sc.o0, sc.fo0, o2) : zs<T>(sc.ok, sc.fok, o2);
             T2 z2 = mk<T2>((T)0.5 * (P.y + Pm.y) * s2, (T)-0.5 * (P.x - Pm.x) * s2);
             Z[((size_t)(o2 * g.nr + j) * g.nt + a) * nk + k] = z2;
         }
@@ -276,7 +285,7 @@ __global__ void k_anal_theta(Geo g, FieldPtrs f, const T2* __restrict__ Z, const
         buf0[i] = kk < kw ? src[(size_t)a * g.nk + k0 + kk] : mk<T2>(0, 0);
     }
     __syncthreads();
-    T2* res = fft_cols<T2, KB, KB>(buf0, buf1, g.nt, tw, -1);
+    T2* res = fft_cols<T2, KB, KB, -1>(buf0, buf1, g.nt, tw);
     double2* dst = f.out[fi] + (size_t)j * g.nm * g.nk;
     for (int i = threadIdx.x; i < g.nm * KB; i += blockDim.x) {
         const int im = i / KB, kk = i % KB;
@@ -455,13 +464,13 @@ __global__ void k_stage_div(Geo g, const double2* __restrict__ F, double2* __res
 // ------------------------------------------------------------------ banded solves
 // Two-sweep solve of one banded system per (matrix, k) with precomputed
 // row-local coefficients "lower | 1/diag | upper" (layout in setup.hpp).  A
-// block owns 32 consecutive k of one (component, m): the right-hand sides of
+// block owns kSK consecutive k of one (component, m): the right-hand sides of
 // all rows sit in shared memory and the coefficient rows stream through a
-// double-buffered cp.async pipeline, kRC rows at a time.  Each of the 64
+// double-buffered cp.async pipeline, kRC rows at a time.  Each of the 2 kSK
 // threads sweeps the real or the imaginary part of one system (the matrices
 // are real).  Terms are accumulated oldest first, so the dependence from one
 // row to the next is a single FMA.
-constexpr int kSK = 32;  // systems (consecutive k) per block
+constexpr int kSK = 16;  // systems (consecutive k) per block; 2 threads (re, im) each
 constexpr int kRC = 8;   // rows per staged chunk
 
 __device__ __forceinline__ void cp_async16(void* sm, const void* gm) {
@@ -475,7 +484,7 @@ __device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_g
 // forward sweep when DIAG1 (else in the backward sweep), NU upper coefficients
 // (nearest first) for the backward sweep.
 template <int NL, int NU, bool DIAG1>
-__global__ void __launch_bounds__(64) k_band_solve(Geo g, const double* __restrict__ fac, double2* __restrict__ X,
+__global__ void __launch_bounds__(2 * kSK) k_band_solve(Geo g, const double* __restrict__ fac, double2* __restrict__ X,
                                                   int helm, int zero_row0) {
     constexpr int NC1 = NL + (DIAG1 ? 1 : 0);  // forward sweep: coefficients [0, NC1)
     constexpr int E2 = NC1;                      // backward sweep: [E2, 13)
@@ -496,7 +505,7 @@ __global__ void __launch_bounds__(64) k_band_solve(Geo g, const double* __restri
     const size_t S = (size_t)g.nr * g.nm * g.nk;
     double2* x = X + (size_t)v * S;  // v = 0 for the pressure
     const double* F = fac + (size_t)abs(mv) * g.nr * kB * g.nkp + k0;
-    const int tid = threadIdx.x, sy = tid & 31, comp = tid >> 5;
+    const int tid = threadIdx.x, sy = tid % kSK, comp = tid / kSK;
     const int nch = (g.nr + kRC - 1) / kRC;
 
     for (int i = tid; i < g.nr * kSK; i += blockDim.x) {
@@ -593,11 +602,12 @@ __global__ void k_stage_rhs(Geo g, const double2* __restrict__ u, const double2*
         R[o + 2 * S] = fz;
         return;
     }
-    // band sums of L_{m'} applied to u+, u-, u_z
+    // L_{m+1} and L_{m-1} share parity and differ only on the diagonal
+    // (L_{m-1} = L_{m+1} + 4m/r^2), so L_{m+1} is applied to u_r and u_theta
+    // separately and combined: L+ u+ = Lp u_r + i Lp u_t, L- u- = Lp u_r - i Lp u_t + 4m/r^2 u-.
     const double* Lp = g.Lb + ((size_t)abs(d.m + 1) * g.nr + d.j) * kB;
-    const double* Lm = g.Lb + ((size_t)abs(d.m - 1) * g.nr + d.j) * kB;
     const double* Lz = g.Lb + ((size_t)abs(d.m) * g.nr + d.j) * kB;
-    double2 sp = make_double2(0, 0), sm = make_double2(0, 0), sz = make_double2(0, 0);
+    double2 tr = make_double2(0, 0), tt = make_double2(0, 0), sz = make_double2(0, 0);
     const double2 *ur = u, *ut = u + S, *uz = u + 2 * S;
     // rows j >= 4 touch columns j-4..j+4 only (9 entries), wall rows columns 0..8
     const int s0 = d.j >= 4 ? 0 : 4 - d.j, s1 = d.j >= 4 ? 8 : 12 - d.j;
@@ -606,17 +616,18 @@ __global__ void k_stage_rhs(Geo g, const double2* __restrict__ u, const double2*
         const int c = d.j - 4 + s;
         if (s < s0 || s > s1 || c >= g.nr) continue;
         const size_t oc = sidx(g, c, d.im, d.k);
-        const double2 a = ur[oc], b = ut[oc];
-        const double2 up = make_double2(a.x - b.y, a.y + b.x);
-        const double2 um = make_double2(a.x + b.y, a.y - b.x);
-        sp = dfma(__ldg(Lp + s), up, sp);
-        sm = dfma(__ldg(Lm + s), um, sm);
+        const double lp = __ldg(Lp + s);
+        tr = dfma(lp, ur[oc], tr);
+        tt = dfma(lp, ut[oc], tt);
         sz = dfma(__ldg(Lz + s), uz[oc], sz);
     }
     const double dg = g.inv_dt - kz * kz * g.inv_2re;
     const double2 a = ur[o], b = ut[o], c = uz[o];
     const double2 up = make_double2(a.x - b.y, a.y + b.x);
     const double2 um = make_double2(a.x + b.y, a.y - b.x);
+    const double fm = 4.0 * d.m * ir * ir;
+    const double2 sp = make_double2(tr.x - tt.y, tr.y + tt.x);
+    const double2 sm = make_double2(tr.x + tt.y + fm * um.x, tr.y - tt.x + fm * um.y);
     R[o] = make_double2(dg * up.x + g.inv_2re * sp.x + (fr.x - ft.y), dg * up.y + g.inv_2re * sp.y + (fr.y + ft.x));
     R[o + S] = make_double2(dg * um.x + g.inv_2re * sm.x + (fr.x + ft.y), dg * um.y + g.inv_2re * sm.y + (fr.y - ft.x));
     R[o + 2 * S] = make_double2(dg * c.x + g.inv_2re * sz.x + fz.x, dg * c.y + g.inv_2re * sz.y + fz.y);
@@ -947,7 +958,16 @@ void launch_anal_theta(const Geo& g, const FieldPtrs& f, int nfield, const T2* Z
 }
 
 template <class T2>
-void launch_zpass(const Geo& g, int mode, const T2* Y, T2* Z, const ZScales& sc, const Twiddles& tw, cudaStream_t s) {
+void launch_zpass(const Geo& g, int mode, const T2* Y, T2* Z, const ZScales& sc_in, const Twiddles& tw, cudaStream_t s) {
+    ZScales sc = sc_in;
+    for (int i = 0; i < 9; ++i) {
+        sc.fh0[i] = (float)sc.h0[i];
+        sc.fhk[i] = (float)sc.hk[i];
+    }
+    for (int i = 0; i < 6; ++i) {
+        sc.fo0[i] = (float)sc.o0[i];
+        sc.fok[i] = (float)sc.ok[i];
+    }
     const int ld = mode == ZFWD ? 3 : 5;
     const size_t sm = (size_t)(2 * g.nzp * ld + g.nzp) * sizeof(T2);
     dim3 grid(g.nt, g.nr);
@@ -991,14 +1011,14 @@ static void launch_band_solve(const Geo& g, const double* fac, double2* X, int h
             cudaFuncSetAttribute(k_band_solve<4, 8, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
             attr = true;
         }
-        k_band_solve<4, 8, false><<<nblocks, 64, sm, s>>>(g, fac, X, helm, 0);
+        k_band_solve<4, 8, false><<<nblocks, 2 * kSK, sm, s>>>(g, fac, X, helm, 0);
     } else {
         static bool attr = false;
         if (!attr) {
             cudaFuncSetAttribute(k_band_solve<8, 4, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
             attr = true;
         }
-        k_band_solve<8, 4, true><<<nblocks, 64, sm, s>>>(g, fac, X, helm, 1);
+        k_band_solve<8, 4, true><<<nblocks, 2 * kSK, sm, s>>>(g, fac, X, helm, 1);
     }
 }
 

@@ -40,6 +40,7 @@ struct FieldPtrs {
 struct ZScales {
     double h0[9], hk[9];
     double o0[6], ok[6];
+    float fh0[9], fhk[9], fo0[6], fok[6];  // FP32 copies, filled by launch_zpass
 };
 
 // Twiddle tables e^{-2 pi i n / N} for N = nt and N = nzp, FP64 and FP32.
