@@ -8,6 +8,7 @@
 // solves, influence and flux corrections) is FP64.
 #include "kernels.hpp"
 
+#include <algorithm>
 #include <cstdio>
 #include <stdexcept>
 
@@ -169,7 +170,7 @@ __global__ void k_synth_theta(Geo g, FieldPtrs f, T2* __restrict__ Y, const T2* 
         const int im = i / KB, kk = i % KB;
         if (kk < kw) {
             const int m = im - g.M;
-            const int a = (m + g.nt) % g.nt;
+            const int a = m < 0 ? m + g.nt : m;
             buf0[a * KB + kk] = from_d<T2>(src[(size_t)im * g.nk + k0 + kk]);
         }
     }
@@ -205,8 +206,8 @@ __global__ void k_zpass(Geo g, const T2* __restrict__ Y, T2* __restrict__ Z, ZSc
     const int a = blockIdx.x, j = blockIdx.y;
     for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = twg[i];
     // Hermitian-extended spectra, two fields per column
-    for (int i = threadIdx.x; i < NPI * N; i += blockDim.x) {
-        const int p = i / N, n = i % N;
+    for (int p = 0; p < NPI; ++p)
+    for (int n = threadIdx.x; n < N; n += blockDim.x) {
         int k = -1;
         bool neg = false;
         if (n <= K) k = n;
@@ -251,8 +252,8 @@ __global__ void k_zpass(Geo g, const T2* __restrict__ Y, T2* __restrict__ Z, ZSc
     }
     __syncthreads();
     T2* sp = fft_cols<T2, NPO, LD, -1>(pr, ph, N, tw);
-    for (int i = threadIdx.x; i < NPO * nk; i += blockDim.x) {
-        const int p = i / nk, k = i % nk;
+    for (int p = 0; p < NPO; ++p)
+    for (int k = threadIdx.x; k < nk; k += blockDim.x) {
         const T2 P = sp[k * LD + p];
         const T2 Pm = sp[((N - k) % N) * LD + p];
         const int o1 = 2 * p, o2 = 2 * p + 1;
@@ -291,9 +292,9 @@ __global__ void k_anal_theta(Geo g, FieldPtrs f, const T2* __restrict__ Z, const
         const int im = i / KB, kk = i % KB;
         if (kk >= kw) continue;
         const int m = im - g.M;
-        double2 v = to_d(res[((m + g.nt) % g.nt) * KB + kk]);
+        double2 v = to_d(res[(m < 0 ? m + g.nt : m) * KB + kk]);
         if (k0 + kk == 0) {
-            double2 vm = to_d(res[((-m + g.nt) % g.nt) * KB + kk]);
+            double2 vm = to_d(res[(m > 0 ? g.nt - m : -m) * KB + kk]);
             v = make_double2(0.5 * (v.x + vm.x), 0.5 * (v.y - vm.y));
         }
         dst[(size_t)im * g.nk + k0 + kk] = v;
@@ -305,14 +306,15 @@ struct Idx {
     int j, im, k, m;
     size_t S;
 };
-__device__ __forceinline__ bool decode(const Geo& g, size_t idx, Idx& d) {
+// Spectral kernels run on a 3-D grid: x covers k, y the azimuthal index, z
+// the radial index, so no thread divides to find its (j, m, k).
+__device__ __forceinline__ bool decode(const Geo& g, Idx& d) {
     d.S = (size_t)g.nr * g.nm * g.nk;
-    if (idx >= d.S) return false;
-    d.k = (int)(idx % g.nk);
-    d.im = (int)((idx / g.nk) % g.nm);
-    d.j = (int)(idx / ((size_t)g.nk * g.nm));
+    d.k = blockIdx.x * blockDim.x + threadIdx.x;
+    d.im = blockIdx.y;
+    d.j = blockIdx.z;
     d.m = d.im - g.M;
-    return true;
+    return d.k < g.nk;
 }
 __device__ __forceinline__ size_t sidx(const Geo& g, int j, int im, int k) {
     return ((size_t)j * g.nm + im) * g.nk + k;
@@ -372,7 +374,7 @@ __device__ __forceinline__ double2 band_col(const Geo& g, const double* B0, cons
 
 __global__ void k_curl(Geo g, const double2* __restrict__ u, double2* __restrict__ w) {
     Idx d;
-    if (!decode(g, (size_t)blockIdx.x * blockDim.x + threadIdx.x, d)) return;
+    if (!decode(g, d)) return;
     const double2 *ur = u, *ut = u + d.S, *uz = u + 2 * d.S;
     const double kz = d.k * g.kz0, ir = g.invr[d.j], mr = d.m * ir;
     const size_t o = sidx(g, d.j, d.im, d.k);
@@ -386,7 +388,7 @@ __global__ void k_curl(Geo g, const double2* __restrict__ u, double2* __restrict
 
 __global__ void k_curlT_acc(Geo g, const double2* __restrict__ wb, double2* __restrict__ ub) {
     Idx d;
-    if (!decode(g, (size_t)blockIdx.x * blockDim.x + threadIdx.x, d)) return;
+    if (!decode(g, d)) return;
     const double2 *wr = wb, *wt = wb + d.S, *wz = wb + 2 * d.S;
     const double kz = d.k * g.kz0, ir = g.invr[d.j], mr = d.m * ir;
     const size_t o = sidx(g, d.j, d.im, d.k);
@@ -412,7 +414,7 @@ __device__ __forceinline__ void base_at(const Geo& g, int j, double c, double s,
 __global__ void k_base_add(Geo g, const double2* __restrict__ u, const double2* __restrict__ w, double2* __restrict__ N,
                            double c, double s) {
     Idx d;
-    if (!decode(g, (size_t)blockIdx.x * blockDim.x + threadIdx.x, d)) return;
+    if (!decode(g, d)) return;
     double U, dU;
     base_at(g, d.j, c, s, U, dU);
     const size_t o = sidx(g, d.j, d.im, d.k), S = d.S;
@@ -428,7 +430,7 @@ __global__ void k_base_add(Geo g, const double2* __restrict__ u, const double2* 
 __global__ void k_baseT_acc(Geo g, const double2* __restrict__ nb, double2* __restrict__ ub, double2* __restrict__ wb,
                             double c, double s) {
     Idx d;
-    if (!decode(g, (size_t)blockIdx.x * blockDim.x + threadIdx.x, d)) return;
+    if (!decode(g, d)) return;
     double U, dU;
     base_at(g, d.j, c, s, U, dU);
     const size_t o = sidx(g, d.j, d.im, d.k), S = d.S;
@@ -447,7 +449,7 @@ __global__ void k_baseT_acc(Geo g, const double2* __restrict__ nb, double2* __re
 // q = div F (rows j >= 1; q_0 = 0 is the tentative Neumann datum)
 __global__ void k_stage_div(Geo g, const double2* __restrict__ F, double2* __restrict__ q) {
     Idx d;
-    if (!decode(g, (size_t)blockIdx.x * blockDim.x + threadIdx.x, d)) return;
+    if (!decode(g, d)) return;
     const size_t o = sidx(g, d.j, d.im, d.k), S = d.S;
     if (d.j == 0 || (d.m == 0 && d.k == 0)) {
         q[o] = make_double2(0, 0);
@@ -584,7 +586,7 @@ __global__ void __launch_bounds__(2 * kSK) k_band_solve(Geo g, const double* __r
 __global__ void k_stage_rhs(Geo g, const double2* __restrict__ u, const double2* __restrict__ F,
                             const double2* __restrict__ p, double2* __restrict__ R) {
     Idx d;
-    if (!decode(g, (size_t)blockIdx.x * blockDim.x + threadIdx.x, d)) return;
+    if (!decode(g, d)) return;
     const size_t o = sidx(g, d.j, d.im, d.k), S = d.S;
     if (d.j == 0) {
         R[o] = R[o + S] = R[o + 2 * S] = make_double2(0, 0);
@@ -660,7 +662,7 @@ __global__ void k_stage_a0(Geo g, const double2* __restrict__ R, double2* __rest
 __global__ void k_stage_finish(Geo g, const double2* __restrict__ R, const double2* __restrict__ a0v,
                                const double2* __restrict__ addto, double2* __restrict__ out) {
     Idx d;
-    if (!decode(g, (size_t)blockIdx.x * blockDim.x + threadIdx.x, d)) return;
+    if (!decode(g, d)) return;
     const size_t o = sidx(g, d.j, d.im, d.k), S = d.S;
     const double2 xp = R[o], xm = R[o + S];
     double2 ur = make_double2(0.5 * (xp.x + xm.x), 0.5 * (xp.y + xm.y));
@@ -732,7 +734,7 @@ __global__ void k_stageT_rhs(Geo g, const double2* __restrict__ R1, const double
                              double cu2, double cf1, double cf2, double2* __restrict__ ub, int acc,
                              double2* __restrict__ Fb) {
     Idx d;
-    if (!decode(g, (size_t)blockIdx.x * blockDim.x + threadIdx.x, d)) return;
+    if (!decode(g, d)) return;
     const size_t o = sidx(g, d.j, d.im, d.k), S = d.S;
     auto comb = [&](size_t i, double a1, double a2) {
         const double2 p = R1[i];
@@ -778,7 +780,7 @@ __global__ void k_stageT_rhs(Geo g, const double2* __restrict__ R1, const double
 // qbar = G^H Fb' = D1p^T Fb'_r - i (m/r) Fb'_t - i kz Fb'_z
 __global__ void k_stageT_qbar(Geo g, const double2* __restrict__ Fb, double2* __restrict__ q) {
     Idx d;
-    if (!decode(g, (size_t)blockIdx.x * blockDim.x + threadIdx.x, d)) return;
+    if (!decode(g, d)) return;
     const size_t o = sidx(g, d.j, d.im, d.k), S = d.S;
     if (d.m == 0 && d.k == 0) {
         q[o] = make_double2(0, 0);
@@ -795,7 +797,7 @@ __global__ void k_stageT_qbar(Geo g, const double2* __restrict__ Fb, double2* __
 // Fb = Fb' - Dv^H z: Fb_r -= D1v^T z + z/r ; Fb_t += i (m/r) z ; Fb_z += i kz z
 __global__ void k_stageT_div(Geo g, const double2* __restrict__ z, double2* __restrict__ Fb) {
     Idx d;
-    if (!decode(g, (size_t)blockIdx.x * blockDim.x + threadIdx.x, d)) return;
+    if (!decode(g, d)) return;
     if (d.m == 0 && d.k == 0) return;
     const size_t o = sidx(g, d.j, d.im, d.k), S = d.S;
     const double kz = d.k * g.kz0, ir = g.invr[d.j], mr = d.m * ir;
@@ -825,27 +827,29 @@ __global__ void k_axpby(size_t n, double a, const double2* __restrict__ x, doubl
 }
 
 __global__ void k_weight(Geo g, const double2* __restrict__ x, double2* __restrict__ out, int divide) {
-    const size_t S = (size_t)g.nr * g.nm * g.nk;
-    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= 3 * S) return;
-    const size_t e = i % S;
-    const int k = (int)(e % g.nk), j = (int)(e / ((size_t)g.nk * g.nm));
-    const double w = g.ewt * g.W[j] * (k == 0 ? 1.0 : 2.0);
+    Idx d;
+    if (!decode(g, d)) return;
+    const double w = g.ewt * g.W[d.j] * (d.k == 0 ? 1.0 : 2.0);
     const double f = divide ? 1.0 / w : w;
-    out[i] = make_double2(x[i].x * f, x[i].y * f);
+    for (int c = 0; c < 3; ++c) {
+        const size_t i = c * d.S + sidx(g, d.j, d.im, d.k);
+        out[i] = make_double2(x[i].x * f, x[i].y * f);
+    }
 }
 
+// One partial per block of the 3-D spectral grid (fixed order: deterministic).
 __global__ void k_inner_partial(Geo g, const double2* __restrict__ a, const double2* __restrict__ b,
                                 double* __restrict__ partial) {
-    __shared__ double red[256];
-    const size_t S = (size_t)g.nr * g.nm * g.nk, n = 3 * S;
+    __shared__ double red[128];
+    Idx d;
     double acc = 0;
-    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-        const size_t e = i % S;
-        const int k = (int)(e % g.nk), j = (int)(e / ((size_t)g.nk * g.nm));
-        const double w = g.W[j] * (k == 0 ? 1.0 : 2.0);
-        const double2 p = a[i], q = b[i];
-        acc += w * (p.x * q.x + p.y * q.y);
+    if (decode(g, d)) {
+        const double w = g.W[d.j] * (d.k == 0 ? 1.0 : 2.0);
+        for (int c = 0; c < 3; ++c) {
+            const size_t i = c * d.S + sidx(g, d.j, d.im, d.k);
+            const double2 p = a[i], q = b[i];
+            acc += w * (p.x * q.x + p.y * q.y);
+        }
     }
     red[threadIdx.x] = acc;
     __syncthreads();
@@ -853,7 +857,7 @@ __global__ void k_inner_partial(Geo g, const double2* __restrict__ a, const doub
         if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
         __syncthreads();
     }
-    if (threadIdx.x == 0) partial[blockIdx.x] = red[0];
+    if (threadIdx.x == 0) partial[((size_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x] = red[0];
 }
 
 __global__ void k_inner_final(const double* __restrict__ partial, int np, double scale, double* __restrict__ out) {
@@ -879,22 +883,24 @@ static void check_launch(const char* what) {
     }
 }
 static inline unsigned nblk(size_t n, int bs) { return (unsigned)((n + bs - 1) / bs); }
-static inline size_t S_of(const Geo& g) { return (size_t)g.nr * g.nm * g.nk; }
+// block and grid of the 3-D spectral launches (x: k, y: m, z: r)
+static inline unsigned spec_bx(const Geo& g) { return g.nk <= 32 ? 32u : (g.nk <= 64 ? 64u : 128u); }
+static inline dim3 spec_grid(const Geo& g) { return dim3((g.nk + spec_bx(g) - 1) / spec_bx(g), g.nm, g.nr); }
 
 void launch_curl(const Geo& g, const double2* u, double2* w, cudaStream_t s) {
-    k_curl<<<nblk(S_of(g), 256), 256, 0, s>>>(g, u, w);
+    k_curl<<<spec_grid(g), spec_bx(g), 0, s>>>(g, u, w);
     check_launch("curl");
 }
 void launch_curlT_acc(const Geo& g, const double2* wb, double2* ub, cudaStream_t s) {
-    k_curlT_acc<<<nblk(S_of(g), 256), 256, 0, s>>>(g, wb, ub);
+    k_curlT_acc<<<spec_grid(g), spec_bx(g), 0, s>>>(g, wb, ub);
     check_launch("curlT");
 }
 void launch_base_add(const Geo& g, const double2* u, const double2* w, double2* N, double c, double sn, cudaStream_t s) {
-    k_base_add<<<nblk(S_of(g), 256), 256, 0, s>>>(g, u, w, N, c, sn);
+    k_base_add<<<spec_grid(g), spec_bx(g), 0, s>>>(g, u, w, N, c, sn);
     check_launch("base_add");
 }
 void launch_baseT_acc(const Geo& g, const double2* nb, double2* ub, double2* wb, double c, double sn, cudaStream_t s) {
-    k_baseT_acc<<<nblk(S_of(g), 256), 256, 0, s>>>(g, nb, ub, wb, c, sn);
+    k_baseT_acc<<<spec_grid(g), spec_bx(g), 0, s>>>(g, nb, ub, wb, c, sn);
     check_launch("baseT");
 }
 
@@ -1023,7 +1029,7 @@ static void launch_band_solve(const Geo& g, const double* fac, double2* X, int h
 }
 
 void launch_stage_div(const Geo& g, const double2* F, double2* q, cudaStream_t s) {
-    k_stage_div<<<nblk(S_of(g), 256), 256, 0, s>>>(g, F, q);
+    k_stage_div<<<spec_grid(g), spec_bx(g), 0, s>>>(g, F, q);
     check_launch("stage_div");
 }
 void launch_stage_psolve(const Geo& g, double2* q, cudaStream_t s) {
@@ -1031,7 +1037,7 @@ void launch_stage_psolve(const Geo& g, double2* q, cudaStream_t s) {
     check_launch("stage_psolve");
 }
 void launch_stage_rhs(const Geo& g, const double2* u, const double2* F, const double2* p, double2* R, cudaStream_t s) {
-    k_stage_rhs<<<nblk(S_of(g), 256), 256, 0, s>>>(g, u, F, p, R);
+    k_stage_rhs<<<spec_grid(g), spec_bx(g), 0, s>>>(g, u, F, p, R);
     check_launch("stage_rhs");
 }
 void launch_stage_hsolve(const Geo& g, double2* R, cudaStream_t s) {
@@ -1044,7 +1050,7 @@ void launch_stage_a0(const Geo& g, const double2* R, double2* a0, cudaStream_t s
 }
 void launch_stage_finish(const Geo& g, const double2* R, const double2* a0, const double2* addto, double2* out,
                          cudaStream_t s) {
-    k_stage_finish<<<nblk(S_of(g), 256), 256, 0, s>>>(g, R, a0, addto, out);
+    k_stage_finish<<<spec_grid(g), spec_bx(g), 0, s>>>(g, R, a0, addto, out);
     check_launch("stage_finish");
 }
 void launch_stageT_finish(const Geo& g, const double2* ubn, double2* R, cudaStream_t s) {
@@ -1058,13 +1064,13 @@ void launch_stageT_hsolve(const Geo& g, double2* R, cudaStream_t s) {
 void launch_stageT_rhs(const Geo& g, const double2* R1, const double2* R2, double cu1, double cu2, double cf1,
                        double cf2, double2* ub, int acc, double2* Fb, cudaStream_t s) {
     if (R2)
-        k_stageT_rhs<true><<<nblk(S_of(g), 256), 256, 0, s>>>(g, R1, R2, cu1, cu2, cf1, cf2, ub, acc, Fb);
+        k_stageT_rhs<true><<<spec_grid(g), spec_bx(g), 0, s>>>(g, R1, R2, cu1, cu2, cf1, cf2, ub, acc, Fb);
     else
-        k_stageT_rhs<false><<<nblk(S_of(g), 256), 256, 0, s>>>(g, R1, R2, cu1, cu2, cf1, cf2, ub, acc, Fb);
+        k_stageT_rhs<false><<<spec_grid(g), spec_bx(g), 0, s>>>(g, R1, R2, cu1, cu2, cf1, cf2, ub, acc, Fb);
     check_launch("stageT_rhs");
 }
 void launch_stageT_qbar(const Geo& g, const double2* Fb, double2* q, cudaStream_t s) {
-    k_stageT_qbar<<<nblk(S_of(g), 256), 256, 0, s>>>(g, Fb, q);
+    k_stageT_qbar<<<spec_grid(g), spec_bx(g), 0, s>>>(g, Fb, q);
     check_launch("stageT_qbar");
 }
 void launch_stageT_psolve(const Geo& g, double2* q, cudaStream_t s) {
@@ -1072,7 +1078,7 @@ void launch_stageT_psolve(const Geo& g, double2* q, cudaStream_t s) {
     check_launch("stageT_psolve");
 }
 void launch_stageT_div(const Geo& g, const double2* z, double2* Fb, cudaStream_t s) {
-    k_stageT_div<<<nblk(S_of(g), 256), 256, 0, s>>>(g, z, Fb);
+    k_stageT_div<<<spec_grid(g), spec_bx(g), 0, s>>>(g, z, Fb);
     check_launch("stageT_div");
 }
 
@@ -1081,12 +1087,17 @@ void launch_axpby(size_t n, double a, const double2* x, double b, const double2*
     check_launch("axpby");
 }
 void launch_weight(const Geo& g, const double2* x, double2* out, int divide, cudaStream_t s) {
-    k_weight<<<nblk(3 * S_of(g), 256), 256, 0, s>>>(g, x, out, divide);
+    k_weight<<<spec_grid(g), spec_bx(g), 0, s>>>(g, x, out, divide);
     check_launch("weight");
 }
+size_t inner_partials(const Geo& g) {
+    const dim3 grid = spec_grid(g);
+    return (size_t)grid.x * grid.y * grid.z;
+}
 void launch_inner(const Geo& g, const double2* a, const double2* b, double* partial, double* dev_out, cudaStream_t s) {
-    k_inner_partial<<<kInnerBlocks, 256, 0, s>>>(g, a, b, partial);
-    k_inner_final<<<1, 1024, 0, s>>>(partial, kInnerBlocks, g.ewt, dev_out);
+    const dim3 grid = spec_grid(g);
+    k_inner_partial<<<grid, spec_bx(g), 0, s>>>(g, a, b, partial);
+    k_inner_final<<<1, 1024, 0, s>>>(partial, (int)(grid.x * grid.y * grid.z), g.ewt, dev_out);
     check_launch("inner");
 }
 

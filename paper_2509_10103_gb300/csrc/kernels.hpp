@@ -94,7 +94,8 @@ void launch_stageT_div(const Geo& g, const double2* z, double2* Fb, cudaStream_t
 void launch_axpby(size_t n, double a, const double2* x, double b, const double2* y, double2* out, cudaStream_t s);
 void launch_weight(const Geo& g, const double2* x, double2* out, int divide, cudaStream_t s);
 // Deterministic weighted inner product sum W_hat Re(conj(a) b); result to dev_out[0].
+// partial must hold inner_partials(g) doubles (one per block, fixed order).
 void launch_inner(const Geo& g, const double2* a, const double2* b, double* partial, double* dev_out, cudaStream_t s);
-constexpr int kInnerBlocks = 608;  // 4 x 152 SMs; fixed so the reduction order never changes
+size_t inner_partials(const Geo& g);
 
 }  // namespace pnop

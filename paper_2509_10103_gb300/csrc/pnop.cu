@@ -602,7 +602,7 @@ int pnop_create(const pnop_grid* grid, const pnop_params* params, void* cuda_str
         const size_t plane = (size_t)d.nr * d.nth * d.nk * cz;
         c->Y = c->dalloc(9 * plane);
         c->Z = c->dalloc(6 * plane);
-        c->partial = (double*)c->dalloc(pnop::kInnerBlocks * sizeof(double));
+        c->partial = (double*)c->dalloc(pnop::inner_partials(g) * sizeof(double));
         c->dscal = (double*)c->dalloc(4 * sizeof(double));
         ck(cudaDeviceSynchronize(), "create");
         return PNOP_OK;
