@@ -468,12 +468,12 @@ __global__ void k_stage_div(Geo g, const double2* __restrict__ F, double2* __res
 // row-local coefficients "lower | 1/diag | upper" (layout in setup.hpp).  A
 // block owns kSK consecutive k of one (component, m): the right-hand sides of
 // all rows sit in shared memory and the coefficient rows stream through a
-// double-buffered cp.async pipeline, kRC rows at a time.  Each of the kSK
-// threads sweeps the real and the imaginary part of one system (the matrices
+// double-buffered cp.async pipeline, kRC rows at a time.  Each of the 2 kSK
+// threads sweeps the real or the imaginary part of one system (the matrices
 // are real).  Terms are accumulated oldest first, so the dependence from one
 // row to the next is a single FMA.
-constexpr int kSK = 32;  // systems (consecutive k) per block, one thread each
-constexpr int kRC = 8;   // rows per staged chunk
+constexpr int kSK = 16;  // systems (consecutive k) per block; 2 threads (re, im) each
+constexpr int kRC = 4;   // rows per staged chunk
 
 __device__ __forceinline__ void cp_async16(void* sm, const void* gm) {
     const unsigned a = (unsigned)__cvta_generic_to_shared(sm);
@@ -486,7 +486,7 @@ __device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_g
 // forward sweep when DIAG1 (else in the backward sweep), NU upper coefficients
 // (nearest first) for the backward sweep.
 template <int NL, int NU, bool DIAG1>
-__global__ void __launch_bounds__(kSK) k_band_solve(Geo g, const double* __restrict__ fac, double2* __restrict__ X,
+__global__ void __launch_bounds__(2 * kSK) k_band_solve(Geo g, const double* __restrict__ fac, double2* __restrict__ X,
                                                   int helm, int zero_row0) {
     constexpr int NC1 = NL + (DIAG1 ? 1 : 0);  // forward sweep: coefficients [0, NC1)
     constexpr int E2 = NC1;                      // backward sweep: [E2, 13)
@@ -494,6 +494,7 @@ __global__ void __launch_bounds__(kSK) k_band_solve(Geo g, const double* __restr
     constexpr int NCM = NC1 > NC2 ? NC1 : NC2;
     extern __shared__ __align__(16) unsigned char smem[];
     double2* Yb = reinterpret_cast<double2*>(smem);  // [nr][kSK]
+    double* Yd = reinterpret_cast<double*>(smem);
     double* Cb = reinterpret_cast<double*>(Yb + (size_t)g.nr * kSK);  // [2][kRC][NCM][kSK]
     const int nkb = (g.nk + kSK - 1) / kSK;
     int bi = blockIdx.x;
@@ -506,7 +507,7 @@ __global__ void __launch_bounds__(kSK) k_band_solve(Geo g, const double* __restr
     const size_t S = (size_t)g.nr * g.nm * g.nk;
     double2* x = X + (size_t)v * S;  // v = 0 for the pressure
     const double* F = fac + (size_t)abs(mv) * g.nr * kB * g.nkp + k0;
-    const int tid = threadIdx.x, sy = tid;
+    const int tid = threadIdx.x, sy = tid % kSK, comp = tid / kSK;
     const int nch = (g.nr + kRC - 1) / kRC;
 
     for (int i = tid; i < g.nr * kSK; i += blockDim.x) {
@@ -529,13 +530,11 @@ __global__ void __launch_bounds__(kSK) k_band_solve(Geo g, const double* __restr
     };
     stage(0);
     cp_async_commit();
-    // each thread sweeps the real and the imaginary part of its system: two
-    // independent chains sharing every coefficient load
-    double2 w1[NL], w2[NU];
+    double w1[NL], w2[NU];
 #pragma unroll
-    for (int e = 0; e < NL; ++e) w1[e] = make_double2(0.0, 0.0);
+    for (int e = 0; e < NL; ++e) w1[e] = 0.0;
 #pragma unroll
-    for (int e = 0; e < NU; ++e) w2[e] = make_double2(0.0, 0.0);
+    for (int e = 0; e < NU; ++e) w2[e] = 0.0;
     for (int t = 0; t < 2 * nch; ++t) {
         stage(t + 1);
         cp_async_commit();
@@ -546,16 +545,16 @@ __global__ void __launch_bounds__(kSK) k_band_solve(Geo g, const double* __restr
             for (int r = 0; r < kRC; ++r) {
                 const int j = t * kRC + r;
                 if (j >= g.nr) break;
-                double2 val = Yb[j * kSK + sy];
+                double val = Yd[(j * kSK + sy) * 2 + comp];
                 const bool full = !(NL == 8 && j > 8);  // columns of U beyond row 8 hold 4 entries
 #pragma unroll
                 for (int e = 0; e < NL; ++e)
-                    if (full || e >= NL - 4) val = dfma(-C[(r * NCM + e) * kSK], w1[e], val);
-                if (DIAG1) val = dscale(val, C[(r * NCM + NL) * kSK]);
+                    if (full || e >= NL - 4) val = fma(-C[(r * NCM + e) * kSK], w1[e], val);
+                if (DIAG1) val *= C[(r * NCM + NL) * kSK];
 #pragma unroll
                 for (int e = 0; e < NL - 1; ++e) w1[e] = w1[e + 1];
                 w1[NL - 1] = val;
-                Yb[j * kSK + sy] = val;
+                Yd[(j * kSK + sy) * 2 + comp] = val;
             }
         } else {
             const int c = 2 * nch - 1 - t;
@@ -563,16 +562,16 @@ __global__ void __launch_bounds__(kSK) k_band_solve(Geo g, const double* __restr
             for (int r = kRC - 1; r >= 0; --r) {
                 const int j = c * kRC + r;
                 if (j >= g.nr) continue;
-                double2 val = Yb[j * kSK + sy];
+                double val = Yd[(j * kSK + sy) * 2 + comp];
                 const bool full = !(NU == 8 && j >= 4);  // rows of U from 4 on hold 4 entries
 #pragma unroll
                 for (int e = NU - 1; e >= 0; --e)
-                    if (full || e < 4) val = dfma(-C[(r * NCM + O + e) * kSK], w2[e], val);
-                if (!DIAG1) val = dscale(val, C[(r * NCM) * kSK]);
+                    if (full || e < 4) val = fma(-C[(r * NCM + O + e) * kSK], w2[e], val);
+                if (!DIAG1) val *= C[(r * NCM) * kSK];
 #pragma unroll
                 for (int e = NU - 1; e > 0; --e) w2[e] = w2[e - 1];
                 w2[0] = val;
-                Yb[j * kSK + sy] = val;
+                Yd[(j * kSK + sy) * 2 + comp] = val;
             }
         }
         __syncthreads();
@@ -1025,14 +1024,14 @@ static void launch_band_solve(const Geo& g, const double* fac, double2* X, int h
             cudaFuncSetAttribute(k_band_solve<4, 8, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
             attr = true;
         }
-        k_band_solve<4, 8, false><<<nblocks, kSK, sm, s>>>(g, fac, X, helm, 0);
+        k_band_solve<4, 8, false><<<nblocks, 2 * kSK, sm, s>>>(g, fac, X, helm, 0);
     } else {
         static bool attr = false;
         if (!attr) {
             cudaFuncSetAttribute(k_band_solve<8, 4, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
             attr = true;
         }
-        k_band_solve<8, 4, true><<<nblocks, kSK, sm, s>>>(g, fac, X, helm, 1);
+        k_band_solve<8, 4, true><<<nblocks, 2 * kSK, sm, s>>>(g, fac, X, helm, 1);
     }
 }
 
