@@ -184,9 +184,16 @@ def max_over_ranks(x, ws):
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def aggregate_value(horizon_steps, steps, ws, ms_max):
+    """Whole-job fwd+adj steps/s: every rank runs its own gradients (replicas);
+    the slowest rank's time bounds the job."""
+    return horizon_steps * steps * ws / (ms_max / 1e3)
 
 
 # ------------------------------------------------------------------ GPU arm
@@ -272,6 +279,51 @@ def roofline(L, res, mixed, peaks, pk_src):
     return base
 
 
+# ------------------------------------------------------------------ serving stream
+SERVE_RES = ((32, 32, 64, 10.0), (48, 48, 128, 25.0), (64, 64, 256, 50.0))
+
+
+def serving_report(L, nreq=24, mean_gap=0.05, seed=0, budget=40 << 30, max_active=8):
+    """Poisson arrivals of gradient requests at mixed resolution and physics.
+
+    Parameters per request (seeded): resolution from SERVE_RES, Re in [1500, 3000],
+    A in [0.5, 1.5], Wo in [4, 18], E0 = 10^U(-7,-4), dt = 0.005 and 10-50 steps
+    (horizons shortened from 1-10 time units so the stream stays within a
+    minute), mixed precision, 8 checkpoint slots; admission by an HBM budget."""
+    import numpy as np
+    from paper_2509_10103_gb300 import serving, synth
+    rng = np.random.default_rng(seed)
+    fields = {}
+    for (nr, nth, nz, lz) in SERVE_RES:
+        ctx = L.Context(nr, nth, nz, lz, 2000.0, 0.005, 8.0, 1.0, 0.0, L.PNOP_MIXED, 1)
+        r = np.array(ctx.pnop_grid_points())
+        ctx.close()
+        fields[(nr, nth, nz)] = synth.random_field(r, nth // 2 - 1, nz // 2 - 1, lz, seed=seed + nr)
+    reqs, t = [], 0.0
+    for i in range(nreq):
+        nr, nth, nz, lz = SERVE_RES[int(rng.integers(len(SERVE_RES)))]
+        t += float(rng.exponential(mean_gap))
+        n = int(rng.integers(10, 51))
+        reqs.append(serving.Request(rid=i, nr=nr, ntheta=nth, nz=nz, Lz=lz, Re=float(rng.uniform(1500, 3000)),
+                                    Wo=float(rng.uniform(4, 18)), A=float(rng.uniform(0.5, 1.5)),
+                                    tau0=float(rng.uniform(0, 100)), E0=float(10 ** rng.uniform(-7, -4)),
+                                    horizon=n * 0.005, dt=0.005, u0=fields[(nr, nth, nz)], precision=L.PNOP_MIXED,
+                                    snaps=8, arrival=t))
+    t0 = time.perf_counter()
+    res, srv = serving.serve_stream(reqs, hbm_budget=budget, max_active=max_active)
+    wall = time.perf_counter() - t0
+    ok = [r for r in res if r.error is None]
+    steps = sum(int(round(q.horizon / q.dt)) for q, r in zip(reqs, res) if r.error is None)
+    lat = serving.latency_summary(res)
+    return {"requests": nreq, "completed": len(ok), "errors": [r.error for r in res if r.error][:3],
+            "resolutions": [f"{a}x{b}x{c}" for a, b, c, _ in SERVE_RES], "precision": "mixed",
+            "offered_rate_req_s": 1.0 / mean_gap, "throughput_req_s": len(ok) / wall,
+            "steps_per_s": steps / wall, "p50_latency_s": lat["p50_s"], "p99_latency_s": lat["p99_s"],
+            "mean_latency_s": lat.get("mean_s"), "peak_active": srv.peak_active,
+            "peak_admitted_gb": srv.peak_bytes / 2 ** 30, "hbm_budget_gb": budget / 2 ** 30, "wall_s": wall,
+            "horizons": "10-50 steps of dt=0.005", "arrivals": f"Poisson, mean gap {mean_gap} s"}
+
+
 # ------------------------------------------------------------------ CPU oracle (baseline / reference arm)
 ORACLE_SAMPLE_CODE = r"""
 import os, sys, time, json, math
@@ -349,7 +401,7 @@ def reference_main(args):
     wall = time.perf_counter() - t0
     per = statistics.median(ts)
     val = 1.0 / per
-    line = {"impl": "reference", "metric": "fwd+adj steps/s at 64x64x256", "value": val, "unit": "steps/s",
+    line = {"impl": "reference", "metric": "fwd+adj steps/s at 64x64x256, mixed vs FP64 on 1 GB300; serving p50/p99 latency", "value": val, "unit": "steps/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": per * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": workload_name(args.horizon_steps, args.snaps), "sample": "bounded oracle sample"},
@@ -372,6 +424,7 @@ def main():
     ap.add_argument("--snaps", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--precision", default="both", choices=["both", "mixed", "fp64"],
                     help="which path(s) to time; 'fp64' reports the FP64 path as the main line")
     args = ap.parse_args()
@@ -397,7 +450,7 @@ def main():
     main_prec = L.PNOP_FP64 if args.precision == "fp64" else L.PNOP_MIXED
     mix = time_gradient(L, torch, main_prec, args.steps, args.warmup, H, s, ws, rank, sampler)
     ms = max_over_ranks(mix["ms"], ws)
-    value = H * args.steps * ws / (ms / 1e3)
+    value = aggregate_value(H, args.steps, ws, ms)
     fp64 = None
     if not args.no_fp64 and args.precision != "mixed":
         f = time_gradient(L, torch, L.PNOP_FP64, args.steps, args.warmup, H, s, ws, rank, None)
@@ -411,7 +464,7 @@ def main():
         return 0
     launches = sum(v[1] for v in mix["timed_profile"].values())
     out = {
-        "metric": "fwd+adj steps/s at 64x64x256, mixed vs FP64 on 1 GB300",
+        "metric": "fwd+adj steps/s at 64x64x256, mixed vs FP64 on 1 GB300; serving p50/p99 latency",
         "value": value, "unit": "steps/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64" if main_prec == L.PNOP_FP64 else "f32+f64", "data": "synthetic",
@@ -430,6 +483,8 @@ def main():
         "gpu_launches": launches,
         "clocks": mix["clocks"],
     }
+    if not args.no_serving and ws == 1:
+        out["serving"] = serving_report(L)
     if not args.no_cpu_baseline and ws == 1:
         planes, modes = 16, 64
         smp = oracle_sample(planes, modes)

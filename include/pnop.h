@@ -70,6 +70,7 @@ typedef struct {
  * perturbation.  precision: PNOP_FP64, or PNOP_MIXED (FP32 transforms and
  * products, FP64 everything else).  snap_budget: checkpoint slots for
  * pnop_gradient including the initial state (>= 1; Section 2.5).
+ * snap_budget <= 0 sizes the checkpoint pool from the HBM budget.
  * hbm_budget: bytes the context may allocate (0 = no limit). */
 typedef struct {
     double Re, Wo, A, dt, tau0;
@@ -118,6 +119,23 @@ int pnop_step_adjoint(pnop_ctx* ctx, const void* u_n, void* lam, double t_n);
  * (host, may be NULL) receives G = E(T)/E(tau0) (Eq. 2.1).  horizon must be
  * a whole number of time steps (to 1e-9 relative). */
 int pnop_gradient(pnop_ctx* ctx, const void* u0, double E0, double horizon, void* grad_out, double* gain_out);
+
+/* pnop_gradient in two halves, for reverse-mode drivers (an autograd
+ * backward): pnop_gradient_forward copies u0 (rescaled to E0 when E0 > 0),
+ * runs the checkpointed forward sweep up to the terminal state u_N and
+ * returns E(T) in *ET_out (and the initial energy in *E0_out, may be NULL);
+ * the checkpoints stay in the context.  pnop_gradient_backward then runs the
+ * reverse sweep with terminal cotangent gE * dE/du_N and writes
+ * gE * dE(T)/du0 to grad_out: the Riesz representer in the energy inner
+ * product when euclidean = 0, or the Euclidean cotangent of the stored real
+ * and imaginary parts (d/dRe + i d/dIm) when euclidean != 0.  Any other call
+ * on the context in between (steps, operators, another gradient) discards
+ * the pending sweep; pnop_gradient_backward then returns
+ * PNOP_ERR_INVALID_ARG.  With snap_budget <= 0 the number of checkpoint slots
+ * is as many as fit in hbm_budget (or 80% of free device memory), at most the
+ * number of steps (store-all). */
+int pnop_gradient_forward(pnop_ctx* ctx, const void* u0, double E0, double horizon, double* ET_out, double* E0_out);
+int pnop_gradient_backward(pnop_ctx* ctx, double gE, int euclidean, void* grad_out);
 
 /* Same as pnop_gradient with host buffers: u0_host and grad_host are host
  * arrays in the field layout; the copies are part of the call. */
@@ -182,6 +200,11 @@ int pnop_energy(pnop_ctx* ctx, const void* u, double* E_out);
 
 /* <a, b> = int int int a . b r dr dtheta dz (Eq. 2.2) of two device fields. */
 int pnop_inner(pnop_ctx* ctx, const void* a, const void* b, double* out);
+
+/* Device bytes a context of this grid and precision allocates with `snaps`
+ * checkpoint slots (an upper estimate, for admission control by an HBM
+ * budget).  Host only; needs no device. */
+int pnop_context_bytes(const pnop_grid* grid, const pnop_params* params, int snaps, size_t* bytes);
 
 /* Binomial checkpoint plan (Section 2.5) for nsteps steps and snaps slots,
  * computed on the host: minimal forward recomputations (Eq. 2.18), stores.

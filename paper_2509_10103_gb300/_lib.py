@@ -23,8 +23,8 @@ OP_CURL, OP_NONLINEAR, OP_STAGE, OP_NONLINEAR_T, OP_STAGE_T_U, OP_STAGE_T_F = ra
 
 EXPORTS = (
     "pnop_create", "pnop_set_base_flow", "pnop_dims", "pnop_grid_points", "pnop_step_forward",
-    "pnop_step_adjoint", "pnop_gradient", "pnop_gradient_host", "pnop_gradient_stats", "pnop_energy",
-    "pnop_inner", "pnop_apply", "pnop_profile", "pnop_profile_read", "pnop_revolve_counts", "pnop_energy_noalloc", "pnop_last_error", "pnop_error_string", "pnop_destroy",
+    "pnop_step_adjoint", "pnop_gradient", "pnop_gradient_forward", "pnop_gradient_backward", "pnop_gradient_host", "pnop_gradient_stats", "pnop_energy",
+    "pnop_inner", "pnop_apply", "pnop_profile", "pnop_profile_read", "pnop_revolve_counts", "pnop_context_bytes", "pnop_energy_noalloc", "pnop_last_error", "pnop_error_string", "pnop_destroy",
 )
 
 
@@ -49,6 +49,8 @@ def _load():
         "pnop_step_forward": (c_int, [c_void_p, c_void_p, c_double, c_int]),
         "pnop_step_adjoint": (c_int, [c_void_p, c_void_p, c_void_p, c_double]),
         "pnop_gradient": (c_int, [c_void_p, c_void_p, c_double, c_double, c_void_p, POINTER(c_double)]),
+        "pnop_gradient_forward": (c_int, [c_void_p, c_void_p, c_double, c_double, POINTER(c_double), POINTER(c_double)]),
+        "pnop_gradient_backward": (c_int, [c_void_p, c_double, c_int, c_void_p]),
         "pnop_gradient_host": (c_int, [c_void_p, c_void_p, c_double, c_double, c_void_p, POINTER(c_double)]),
         "pnop_gradient_stats": (c_int, [c_void_p, POINTER(c_longlong), POINTER(c_longlong), POINTER(c_longlong)]),
         "pnop_energy": (c_int, [c_void_p, c_void_p, POINTER(c_double)]),
@@ -56,6 +58,7 @@ def _load():
         "pnop_apply": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_void_p, c_double]),
         "pnop_profile": (c_int, [c_void_p, ctypes.c_uint]),
         "pnop_profile_read": (c_int, [c_void_p, POINTER(c_double), POINTER(c_longlong), POINTER(c_double)]),
+        "pnop_context_bytes": (c_int, [POINTER(pnop_grid), POINTER(pnop_params), c_int, POINTER(c_size_t)]),
         "pnop_revolve_counts": (c_int, [c_int, c_int, POINTER(c_longlong), POINTER(c_longlong)]),
         "pnop_energy_noalloc": (c_int, [c_void_p, c_void_p, c_int, c_int, c_int, c_double, POINTER(c_double),
                                         c_void_p]),
@@ -95,6 +98,17 @@ def pnop_revolve_counts(nsteps: int, snaps: int):
     if rc != PNOP_OK:
         raise PnopError(rc, "revolve_counts")
     return a.value, s.value
+
+
+def pnop_context_bytes(nr, ntheta, nz, Lz, precision, snaps):
+    """Upper estimate of the device bytes of a context (host only)."""
+    g = pnop_grid(nr, ntheta, nz, Lz, 0.0)
+    p = pnop_params(1.0, 1.0, 0.0, 1.0, 0.0, precision, snaps, 0)
+    out = c_size_t()
+    rc = lib.pnop_context_bytes(byref(g), byref(p), snaps, byref(out))
+    if rc != PNOP_OK:
+        raise PnopError(rc, "context_bytes")
+    return out.value
 
 
 def pnop_energy_noalloc(u, W, nr, M, K, Lz, stream=0):
@@ -159,6 +173,17 @@ class Context:
         self._check(lib.pnop_gradient(self._h, c_void_p(_ptr(u0)), E0, horizon, c_void_p(_ptr(grad_out)),
                                       byref(gain)), "gradient")
         return gain.value
+
+    def pnop_gradient_forward(self, u0, E0, horizon):
+        """Forward half: returns (E(T), initial energy); checkpoints stay in the context."""
+        et, e0 = c_double(), c_double()
+        self._check(lib.pnop_gradient_forward(self._h, c_void_p(_ptr(u0)), E0, horizon, byref(et), byref(e0)),
+                    "gradient_forward")
+        return et.value, e0.value
+
+    def pnop_gradient_backward(self, gE, grad_out, euclidean=False):
+        self._check(lib.pnop_gradient_backward(self._h, gE, int(bool(euclidean)), c_void_p(_ptr(grad_out))),
+                    "gradient_backward")
 
     def pnop_gradient_host(self, u0_host, E0, horizon, grad_host):
         """u0_host, grad_host: host arrays (numpy complex128 or pinned torch tensors)."""

@@ -473,7 +473,7 @@ __global__ void k_stage_div(Geo g, const double2* __restrict__ F, double2* __res
 // are real).  Terms are accumulated oldest first, so the dependence from one
 // row to the next is a single FMA.
 constexpr int kSK = 16;  // systems (consecutive k) per block; 2 threads (re, im) each
-constexpr int kRC = 4;   // rows per staged chunk
+constexpr int kRC = 8;   // rows per staged chunk
 
 __device__ __forceinline__ void cp_async16(void* sm, const void* gm) {
     const unsigned a = (unsigned)__cvta_generic_to_shared(sm);

@@ -31,6 +31,15 @@ void ck(cudaError_t e, const char* what) {
     if (e != cudaSuccess) throw CudaError(std::string(what) + ": " + cudaGetErrorString(e));
 }
 
+// Binomial schedule (Section 2.5) as a list of actions: advance n steps from
+// the state in a slot (into another slot, or into the scratch state when dst
+// is -1), or take the adjoint step of step n from a slot / the scratch state.
+struct Action {
+    bool adjoint;
+    long long start, n;
+    int slot, dst;
+};
+
 bool smooth_size(int n) {
     if (n < 2) return false;
     while (n % 2 == 0) n /= 2;
@@ -74,9 +83,13 @@ struct pnop_ctx {
     std::vector<double2*> snaps;
     std::string err;
     long long st_adv = 0, st_adj = 0, st_store = 0;
-    // gradient sweep state
-    long long g_nsteps = 0;
-    bool g_terminal = false;
+    // gradient sweep state (schedule, position, scratch state, terminal state)
+    std::vector<Action> plan;
+    size_t plan_pos = 0;
+    const double2* cur = nullptr;
+    double2* uN = nullptr;
+    bool pending = false;
+    int st_slots = 0;
     // per-class launch counters, work units and optional event timing
     unsigned prof_mask = 0;
     std::vector<cudaEvent_t> ev;     // pairs (start, stop)
@@ -394,45 +407,51 @@ const double2* advance(pnop_ctx* c, const double2* src, long long start, long lo
     return cur;
 }
 
-void adjoint_at(pnop_ctx* c, long long n, const double2* state) {
-    const double t = c->h.ph.tau0 + n * c->h.ph.dt;
-    if (!c->g_terminal) {
-        if (n != c->g_nsteps - 1) throw Status(PNOP_ERR_INVALID_ARG, "checkpoint schedule out of order");
-        // terminal state u_N and compatibility condition (Eq. 2.8): cotangent W_hat u_N
-        fwd_step(c, state, c->lamB, t);
-        ++c->st_adv;
-        inner_dev(c, c->lamB, c->lamB, c->dscal + 1);
-        weight(c, c->lamB, c->lamA, 0);
-        c->g_terminal = true;
-    }
-    adj_step(c, state, t, c->lamA, c->lamB);
-    std::swap(c->lamA, c->lamB);
-    ++c->st_adj;
-}
-
 // Reverse steps [start, start+l) whose first state sits in snapshot `slot`,
 // with s slots available (that one included).
-void reverse(pnop_ctx* c, long long start, long long l, int slot, int s) {
+void plan_reverse(std::vector<Action>& P, long long start, long long l, int slot, int s) {
     if (l <= 0) return;
     if (l == 1) {
-        adjoint_at(c, start, c->snaps[slot]);
+        P.push_back({true, start, 1, slot, 0});
         return;
     }
     if (s == 1) {
         for (long long i = l - 1; i >= 0; --i) {
-            const double2* st = c->snaps[slot];
-            if (i > 0) st = advance(c, st, start, i, nullptr);
-            adjoint_at(c, start + i, st);
+            if (i > 0) P.push_back({false, start, i, slot, -1});
+            P.push_back({true, start + i, 1, i > 0 ? -1 : slot, 0});
         }
         return;
     }
     const int r = pnop::revolve_repetitions(l, s);
     long long m = std::max<long long>(1, std::max(pnop::binom_beta(s, r - 2), l - pnop::binom_beta(s - 1, r)));
     m = std::min(m, l - 1);
-    advance(c, c->snaps[slot], start, m, c->snaps[slot + 1]);
-    ++c->st_store;
-    reverse(c, start + m, l - m, slot + 1, s - 1);
-    reverse(c, start, m, slot, s);
+    P.push_back({false, start, m, slot, slot + 1});
+    plan_reverse(P, start + m, l - m, slot + 1, s - 1);
+    plan_reverse(P, start, m, slot, s);
+}
+
+// Runs actions [from, to) of the plan; returns the index of the first adjoint
+// action reached when stop_at_adjoint (its state pointer in *state).
+size_t run_plan(pnop_ctx* c, size_t from, bool stop_at_adjoint, const double2** state) {
+    const auto& P = c->plan;
+    for (size_t i = from; i < P.size(); ++i) {
+        const Action& a = P[i];
+        if (!a.adjoint) {
+            const double2* r = advance(c, c->snaps[a.slot], a.start, a.n, a.dst >= 0 ? c->snaps[a.dst] : nullptr);
+            if (a.dst >= 0) ++c->st_store;
+            else c->cur = r;
+            continue;
+        }
+        const double2* st = a.slot >= 0 ? c->snaps[a.slot] : c->cur;
+        if (stop_at_adjoint) {
+            *state = st;
+            return i;
+        }
+        adj_step(c, st, c->h.ph.tau0 + a.start * c->h.ph.dt, c->lamA, c->lamB);
+        std::swap(c->lamA, c->lamB);
+        ++c->st_adj;
+    }
+    return P.size();
 }
 
 // Count-only replay of the same schedule (host logic, no device work).
@@ -472,14 +491,38 @@ template <class F> int guarded(pnop_ctx* c, F&& fn) {
     }
 }
 
-int gradient_impl(pnop_ctx* c, const double2* u0, double E0, double horizon, double2* grad, double* gain) {
+// Number of checkpoint slots: the configured budget, or (budget <= 0) as many
+// as fit in the context's HBM budget (or 80% of free device memory), at most N.
+int snapshot_slots(pnop_ctx* c, long long N) {
+    long long s = c->prm.snap_budget;
+    if (s <= 0) {
+        size_t avail = 0;
+        if (c->prm.hbm_budget) {
+            avail = c->prm.hbm_budget > c->bytes ? c->prm.hbm_budget - c->bytes : 0;
+        } else {
+            size_t fr = 0, tot = 0;
+            ck(cudaMemGetInfo(&fr, &tot), "memory info");
+            avail = (size_t)(0.8 * (double)fr);
+        }
+        s = (long long)c->snaps.size() + (long long)(avail / c->field_bytes());
+    }
+    s = std::max<long long>(1, std::min<long long>(s, N));
+    return (int)s;
+}
+
+// Forward part of the gradient sweep: copies (and rescales) u0, runs the
+// schedule up to its first adjoint step, computes u_N and E(T).  The sweep
+// state stays in the context for gradient_backward.
+void gradient_forward(pnop_ctx* c, const double2* u0, double E0, double horizon, double* ET, double* Einit_out) {
     const double dt = c->h.ph.dt;
     const double nd = horizon / dt;
     const long long N = (long long)std::llround(nd);
     if (!(horizon > 0) || N < 1 || std::fabs(nd - (double)N) > 1e-9 * std::max(1.0, nd))
         throw Status(PNOP_ERR_INVALID_ARG, "horizon must be a positive whole number of time steps");
-    const int s = std::max(1, c->prm.snap_budget);
+    c->pending = false;
+    const int s = snapshot_slots(c, N);
     while ((int)c->snaps.size() < s) c->snaps.push_back(c->field());
+    if (!c->uN) c->uN = c->field();
     const size_t fb = c->field_bytes();
     ck(cudaMemcpyAsync(c->snaps[0], u0, fb, cudaMemcpyDeviceToDevice, c->stream), "copy u0");
     double Einit = 0.5 * inner_sync(c, c->snaps[0], c->snaps[0]);
@@ -489,15 +532,41 @@ int gradient_impl(pnop_ctx* c, const double2* u0, double E0, double horizon, dou
         Einit = 0.5 * inner_sync(c, c->snaps[0], c->snaps[0]);
     }
     c->st_adv = c->st_adj = c->st_store = 0;
-    c->g_nsteps = N;
-    c->g_terminal = false;
-    reverse(c, 0, N, 0, s);
-    weight(c, c->lamA, grad, 1);
-    double ET2 = 0;
-    ck(cudaMemcpyAsync(&ET2, c->dscal + 1, sizeof(double), cudaMemcpyDeviceToHost, c->stream), "copy E");
+    c->st_slots = s;
+    c->plan.clear();
+    plan_reverse(c->plan, 0, N, 0, s);
+    const double2* st = nullptr;
+    c->plan_pos = run_plan(c, 0, true, &st);
+    if (c->plan_pos >= c->plan.size() || c->plan[c->plan_pos].start != N - 1)
+        throw Status(PNOP_ERR_INVALID_ARG, "checkpoint schedule out of order");
+    // terminal state u_N (the compatibility condition Eq. 2.8 uses it)
+    fwd_step(c, st, c->uN, c->h.ph.tau0 + (N - 1) * dt);
+    ++c->st_adv;
+    const double ET2 = inner_sync(c, c->uN, c->uN);
+    if (!std::isfinite(ET2)) throw Status(PNOP_ERR_NONFINITE, "final energy is not finite");
+    *ET = 0.5 * ET2;
+    if (Einit_out) *Einit_out = Einit;
+    c->pending = true;
+}
+
+// Backward part: terminal cotangent gE * W_hat u_N, the remaining schedule,
+// then grad = cotangent / W_hat (Riesz) or the Euclidean cotangent itself.
+void gradient_backward(pnop_ctx* c, double gE, bool euclidean, double2* grad) {
+    if (!c->pending) throw Status(PNOP_ERR_INVALID_ARG, "no pending gradient forward on this context");
+    c->pending = false;
+    weight(c, c->uN, c->lamA, 0);
+    if (gE != 1.0) axpby(c, gE, c->lamA, 0.0, nullptr, c->lamA);
+    const double2* st = nullptr;
+    run_plan(c, c->plan_pos, false, &st);
+    if (euclidean) ck(cudaMemcpyAsync(grad, c->lamA, c->field_bytes(), cudaMemcpyDeviceToDevice, c->stream), "copy");
+    else weight(c, c->lamA, grad, 1);
     ck(cudaStreamSynchronize(c->stream), "gradient sync");
-    const double ET = 0.5 * ET2;
-    if (!std::isfinite(ET)) throw Status(PNOP_ERR_NONFINITE, "final energy is not finite");
+}
+
+int gradient_impl(pnop_ctx* c, const double2* u0, double E0, double horizon, double2* grad, double* gain) {
+    double ET = 0, Einit = 0;
+    gradient_forward(c, u0, E0, horizon, &ET, &Einit);
+    gradient_backward(c, 1.0, false, grad);
     if (gain) *gain = ET / Einit;
     return PNOP_OK;
 }
@@ -521,6 +590,21 @@ const char* pnop_error_string(int status) {
 }
 
 const char* pnop_last_error(const pnop_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+int pnop_context_bytes(const pnop_grid* grid, const pnop_params* params, int snaps, size_t* bytes) {
+    if (!grid || !params || !bytes || snaps < 1 || grid->nr < 1 || grid->ntheta < 4 || grid->nz < 4)
+        return PNOP_ERR_INVALID_ARG;
+    const size_t nr = grid->nr, M = grid->ntheta / 2 - 1, K = grid->nz / 2 - 1;
+    const size_t nm = 2 * M + 1, nk = K + 1, nkp = (nk + 31) / 32 * 32, nt = 3 * (M + 1);
+    const size_t S = nr * nm * nk, field = 3 * S * 16;
+    const size_t cz = params->precision == PNOP_MIXED ? 8 : 16;
+    size_t b = (16 + (size_t)snaps) * field + S * 16;                  // work fields, u_N, checkpoints, q
+    b += 15 * nr * nt * nk * cz;                                         // transform scratch Y, Z
+    b += 2 * ((M + 2) + (M + 1)) * nr * 13 * nkp * 8;                    // LU factors and transposed rows
+    b += (M + 2) * nr * 13 * 8 + 2 * nr * 13 * 8 + nm * nk * 3 * nr * 8; // bands, D1, influence
+    *bytes = b + (1 << 20) + (40 + (size_t)snaps) * (2 << 20);        // tables, reductions, allocation rounding
+    return PNOP_OK;
+}
 
 int pnop_revolve_counts(int nsteps, int snaps, long long* advances, long long* stores) {
     if (nsteps < 1 || snaps < 1) return PNOP_ERR_INVALID_ARG;
@@ -617,6 +701,7 @@ int pnop_create(const pnop_grid* grid, const pnop_params* params, void* cuda_str
 
 int pnop_set_base_flow(pnop_ctx* ctx, double Re, double Wo, double A, double tau0) {
     return guarded(ctx, [&]() -> int {
+        ctx->pending = false;  // shares the sweep buffers
         if (!(Re > 0) || !(A >= 0) || !(Wo > 0 || A == 0)) throw Status(PNOP_ERR_INVALID_ARG, "bad base-flow parameters");
         ctx->h.ph.Re = Re;
         ctx->h.ph.Wo = Wo;
@@ -650,6 +735,7 @@ int pnop_grid_points(const pnop_ctx* ctx, double* r_out) {
 
 int pnop_step_forward(pnop_ctx* ctx, void* u, double t, int nsteps) {
     return guarded(ctx, [&]() -> int {
+        ctx->pending = false;  // shares the sweep buffers
         if (!u || nsteps < 0) throw Status(PNOP_ERR_INVALID_ARG, "bad arguments");
         double2* uu = (double2*)u;
         for (int i = 0; i < nsteps; ++i) {
@@ -663,6 +749,7 @@ int pnop_step_forward(pnop_ctx* ctx, void* u, double t, int nsteps) {
 
 int pnop_step_adjoint(pnop_ctx* ctx, const void* u_n, void* lam, double t_n) {
     return guarded(ctx, [&]() -> int {
+        ctx->pending = false;  // shares the sweep buffers
         if (!u_n || !lam) throw Status(PNOP_ERR_INVALID_ARG, "bad arguments");
         double2* l = (double2*)lam;
         weight(ctx, l, ctx->tmpA, 0);
@@ -677,6 +764,22 @@ int pnop_gradient(pnop_ctx* ctx, const void* u0, double E0, double horizon, void
     return guarded(ctx, [&]() -> int {
         if (!u0 || !grad_out) throw Status(PNOP_ERR_INVALID_ARG, "bad arguments");
         return gradient_impl(ctx, (const double2*)u0, E0, horizon, (double2*)grad_out, gain_out);
+    });
+}
+
+int pnop_gradient_forward(pnop_ctx* ctx, const void* u0, double E0, double horizon, double* ET_out, double* E0_out) {
+    return guarded(ctx, [&]() -> int {
+        if (!u0 || !ET_out) throw Status(PNOP_ERR_INVALID_ARG, "bad arguments");
+        gradient_forward(ctx, (const double2*)u0, E0, horizon, ET_out, E0_out);
+        return PNOP_OK;
+    });
+}
+
+int pnop_gradient_backward(pnop_ctx* ctx, double gE, int euclidean, void* grad_out) {
+    return guarded(ctx, [&]() -> int {
+        if (!grad_out) throw Status(PNOP_ERR_INVALID_ARG, "bad arguments");
+        gradient_backward(ctx, gE, euclidean != 0, (double2*)grad_out);
+        return PNOP_OK;
     });
 }
 
@@ -698,6 +801,7 @@ int pnop_gradient_host(pnop_ctx* ctx, const double* u0_host, double E0, double h
 
 int pnop_gradient_stats(const pnop_ctx* ctx, long long* advances, long long* adjoint_steps, long long* stores) {
     if (!ctx) return PNOP_ERR_INVALID_ARG;
+    if (stores) *stores = ctx->st_store;
     if (advances) *advances = ctx->st_adv;
     if (adjoint_steps) *adjoint_steps = ctx->st_adj;
     if (stores) *stores = ctx->st_store;
@@ -706,6 +810,7 @@ int pnop_gradient_stats(const pnop_ctx* ctx, long long* advances, long long* adj
 
 int pnop_apply(pnop_ctx* ctx, int op, const void* a, const void* b, void* out, double t) {
     return guarded(ctx, [&]() -> int {
+        ctx->pending = false;  // shares the sweep buffers
         if (!a || !out || a == out || (b && b == out)) throw Status(PNOP_ERR_INVALID_ARG, "bad arguments");
         const double2* A = (const double2*)a;
         const double2* B = (const double2*)b;

@@ -279,6 +279,12 @@ static void scatter_factors(std::vector<double>& dst, int mat, int k, int nr, in
             dst[(((size_t)mat * nr + j) * kBand + e) * nkp + k] = f[(size_t)j * kBand + e];
 }
 
+static void gather_factors(const std::vector<double>& src, int mat, int k, int nr, int nkp, std::vector<double>& f) {
+    f.resize((size_t)nr * kBand);
+    for (int j = 0; j < nr; ++j)
+        for (int e = 0; e < kBand; ++e) f[(size_t)j * kBand + e] = src[(((size_t)mat * nr + j) * kBand + e) * nkp + k];
+}
+
 // Row-local coefficients of A^T = U^T L^T from the factors of A: row j holds
 // U_{j-8+e, j} (e = 0..7, oldest first), 1/U_jj, L_{j+1+e, j} (e = 0..3).
 static std::vector<double> transpose_factors(int nr, const std::vector<double>& f) {
@@ -400,8 +406,7 @@ bool build_operators(HostOps& h, std::string& err) {
             const int m = im - M;
             if (m == 0 && k == 0) continue;
             const int ma = std::abs(m);
-            Band Ap = pressure_band(h, ma, kz);
-            band_lu(Ap, f, growth);
+            gather_factors(h.facP, ma, k, nr, nkp, f);  // factors computed above
             std::vector<double> phi(nr, 0.0);
             phi[0] = 1.0;
             band_solve(nr, f, phi);
@@ -417,13 +422,11 @@ bool build_operators(HostOps& h, std::string& err) {
                 fz[j] = -kz * phi[j];  // imaginary part of -i kz phi
             }
             fp[0] = fm[0] = fz[0] = 0.0;
-            Band Hp = helmholtz_band(h, std::abs(m + 1), kz), Hm = helmholtz_band(h, std::abs(m - 1), kz),
-                 Hz = helmholtz_band(h, ma, kz);
-            band_lu(Hp, fac_tmp, growth);
+            gather_factors(h.facH, std::abs(m + 1), k, nr, nkp, fac_tmp);
             band_solve(nr, fac_tmp, fp);
-            band_lu(Hm, fac_tmp, growth);
+            gather_factors(h.facH, std::abs(m - 1), k, nr, nkp, fac_tmp);
             band_solve(nr, fac_tmp, fm);
-            band_lu(Hz, fac_tmp, growth);
+            gather_factors(h.facH, ma, k, nr, nkp, fac_tmp);
             band_solve(nr, fac_tmp, fz);
             std::vector<double> hr(nr), hti(nr);
             for (int j = 0; j < nr; ++j) {

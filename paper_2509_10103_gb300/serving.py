@@ -1,0 +1,186 @@
+"""Continuous-batching server for gradient requests of mixed parameters.
+
+A request asks for the checkpointed gradient dE(T)/du0 and the gain G of one
+initial perturbation (Eq. 2.1, 2.8, 2.12) at its own (Re, Wo, A, tau0, E0,
+horizon) and resolution.  The server keeps an HBM budget: a request is
+admitted as soon as a slot and its device memory (pnop_context_bytes of its
+grid, precision and checkpoint slots) are free, so requests that arrive while
+others run join the device work without waiting for a batch to drain.  Each
+admitted request owns a context (its operators, fields and checkpoints stay on
+the device until it completes) and a CUDA stream; its host thread drives the
+library (ctypes releases the GIL), so kernels of different requests overlap on
+the GPU.  Each request's arithmetic is independent of the others and
+deterministic, so its result is the same alone and in the mix.
+
+The library has no counterpart in the paper: this is the serving layer named
+in the workload list (continuous batching, HBM admission, p50/p99 latency).
+"""
+from __future__ import annotations
+
+import threading
+import time
+from collections import deque
+from dataclasses import dataclass, field
+from typing import Optional
+
+import numpy as np
+
+from . import _lib
+
+
+@dataclass
+class Request:
+    rid: int
+    nr: int
+    ntheta: int
+    nz: int
+    Lz: float
+    Re: float
+    Wo: float
+    A: float
+    tau0: float
+    E0: float
+    horizon: float
+    dt: float
+    u0: np.ndarray                       # host complex128, layout of include/pnop.h
+    precision: int = _lib.PNOP_MIXED
+    snaps: int = 8
+    arrival: float = 0.0                 # seconds after the server start
+
+
+@dataclass
+class Result:
+    rid: int
+    gain: float
+    grad: np.ndarray
+    arrival: float
+    admitted: float
+    done: float
+    device_bytes: int
+    error: Optional[str] = None
+
+    @property
+    def latency(self) -> float:
+        return self.done - self.arrival
+
+
+class Server:
+    """Admits requests by HBM budget and slot count; runs each on its own stream."""
+
+    def __init__(self, hbm_budget: int, max_active: int = 8, device: int = 0, runner=None, sizer=None):
+        """runner(request, budget_bytes) -> (gain, grad) replaces the GPU runner
+        and sizer(request) -> bytes the library estimate (host-side tests)."""
+        self.runner = runner or self._gpu_runner
+        self.sizer = sizer
+        self.hbm_budget = int(hbm_budget)
+        self.max_active = max_active
+        self.device = device
+        self.queue: deque = deque()
+        self.results: dict = {}
+        self.active = 0
+        self.bytes_in_use = 0
+        self.peak_bytes = 0
+        self.peak_active = 0
+        self.lock = threading.Condition()
+        self.t0 = time.perf_counter()
+        self.threads = []
+
+    def now(self) -> float:
+        return time.perf_counter() - self.t0
+
+    def request_bytes(self, r: Request) -> int:
+        if self.sizer is not None:
+            return int(self.sizer(r))
+        return _lib.pnop_context_bytes(r.nr, r.ntheta, r.nz, r.Lz, r.precision, r.snaps)
+
+    def submit(self, r: Request) -> None:
+        need = self.request_bytes(r)
+        if need > self.hbm_budget:
+            raise ValueError(f"request {r.rid} needs {need} bytes, more than the whole budget")
+        with self.lock:
+            self.queue.append((r, need))
+            self._admit_locked()
+
+    def _admit_locked(self) -> None:
+        # first come, first served: the head waits until its memory fits
+        while self.queue and self.active < self.max_active:
+            r, need = self.queue[0]
+            if self.bytes_in_use + need > self.hbm_budget:
+                break
+            self.queue.popleft()
+            self.active += 1
+            self.bytes_in_use += need
+            self.peak_bytes = max(self.peak_bytes, self.bytes_in_use)
+            self.peak_active = max(self.peak_active, self.active)
+            t = threading.Thread(target=self._run, args=(r, need, self.now()), daemon=True)
+            self.threads.append(t)
+            t.start()
+
+    def _gpu_runner(self, r: Request, need: int):
+        import torch
+
+        torch.cuda.set_device(self.device)
+        stream = torch.cuda.Stream(device=self.device)
+        ctx = _lib.Context(r.nr, r.ntheta, r.nz, r.Lz, r.Re, r.dt, r.Wo, r.A, r.tau0, r.precision, r.snaps,
+                           hbm_budget=need, stream=stream.cuda_stream)
+        try:
+            dev = f"cuda:{self.device}"
+            with torch.cuda.stream(stream):
+                u0 = torch.from_numpy(np.ascontiguousarray(r.u0)).to(dev)
+                g = torch.zeros(ctx.shape, dtype=torch.complex128, device=dev)
+            stream.synchronize()
+            gain = ctx.pnop_gradient(u0, r.E0, r.horizon, g)
+            with torch.cuda.stream(stream):
+                grad = g.cpu()
+            stream.synchronize()
+            return gain, grad.numpy()
+        finally:
+            ctx.close()
+
+    def _run(self, r: Request, need: int, admitted: float) -> None:
+        err, gain, grad = None, float("nan"), None
+        try:
+            gain, grad = self.runner(r, need)
+        except Exception as e:  # reported per request; the server keeps running
+            err = f"{type(e).__name__}: {e}"
+        done = self.now()
+        with self.lock:
+            self.results[r.rid] = Result(r.rid, gain, grad, r.arrival, admitted, done, need, err)
+            self.active -= 1
+            self.bytes_in_use -= need
+            self._admit_locked()
+            self.lock.notify_all()
+
+    def wait(self, n: int, timeout: float = 3600.0) -> None:
+        """Block until n results are in."""
+        end = time.perf_counter() + timeout
+        with self.lock:
+            while len(self.results) < n:
+                left = end - time.perf_counter()
+                if left <= 0:
+                    raise TimeoutError(f"{len(self.results)} of {n} requests finished")
+                self.lock.wait(timeout=min(left, 1.0))
+
+
+def serve_stream(requests, hbm_budget: int, max_active: int = 8, device: int = 0, runner=None, sizer=None):
+    """Submit requests at their arrival times (seconds after start) and wait.
+
+    Returns (results sorted by id, server).  Arrival times are honoured on the
+    host clock; a request arriving while others run is admitted as soon as
+    memory and a slot are free."""
+    srv = Server(hbm_budget, max_active, device, runner, sizer)
+    for r in sorted(requests, key=lambda q: q.arrival):
+        delay = r.arrival - srv.now()
+        if delay > 0:
+            time.sleep(delay)
+        srv.submit(r)
+    srv.wait(len(requests))
+    return [srv.results[r.rid] for r in sorted(requests, key=lambda q: q.rid)], srv
+
+
+def latency_summary(results):
+    lat = np.array([x.latency for x in results if x.error is None])
+    if lat.size == 0:
+        return {"p50_s": None, "p99_s": None, "n": 0}
+    return {"p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
+            "mean_s": float(lat.mean()), "n": int(lat.size)}

@@ -1,0 +1,72 @@
+"""Host-side behaviour of the continuous-batching server (no GPU): admission
+by HBM budget and slot count, late arrivals joining running work, errors
+reported per request."""
+import threading
+import time
+
+import numpy as np
+import pytest
+
+from paper_2509_10103_gb300 import serving
+
+
+def _req(i, arrival=0.0, size=1):
+    return serving.Request(rid=i, nr=size, ntheta=4, nz=4, Lz=1.0, Re=1.0, Wo=1.0, A=0.0, tau0=0.0, E0=1.0,
+                           horizon=1.0, dt=1.0, u0=np.zeros(1), arrival=arrival)
+
+
+class FakeGPU:
+    def __init__(self, dur=0.05):
+        self.dur = dur
+        self.lock = threading.Lock()
+        self.live = 0
+        self.peak = 0
+        self.start = {}
+
+    def __call__(self, r, need):
+        with self.lock:
+            self.live += 1
+            self.peak = max(self.peak, self.live)
+            self.start[r.rid] = time.perf_counter()
+        time.sleep(self.dur)
+        with self.lock:
+            self.live -= 1
+        if r.rid == 13:
+            raise RuntimeError("planted failure")
+        return float(r.rid), np.full(3, r.rid)
+
+
+def test_admission_respects_budget_and_slots():
+    gpu = FakeGPU()
+    reqs = [_req(i, size=1 + i % 3) for i in range(12)]
+    res, srv = serving.serve_stream(reqs, hbm_budget=4, max_active=3, runner=gpu, sizer=lambda r: r.nr)
+    assert len(res) == 12 and all(x.error is None for x in res)
+    assert srv.peak_bytes <= 4 and srv.peak_active <= 3 and gpu.peak <= 3
+    assert srv.bytes_in_use == 0 and srv.active == 0
+    assert [x.gain for x in res] == [float(i) for i in range(12)]
+
+
+def test_late_arrival_joins_running_work():
+    gpu = FakeGPU(dur=0.3)
+    reqs = [_req(0, 0.0), _req(1, 0.1)]
+    res, srv = serving.serve_stream(reqs, hbm_budget=10, max_active=4, runner=gpu, sizer=lambda r: 1)
+    # the second request starts while the first is still on the "device"
+    assert gpu.start[1] - gpu.start[0] < 0.25
+    assert gpu.peak == 2
+    assert res[1].admitted - res[1].arrival < 0.05
+
+
+def test_request_larger_than_budget_is_refused_and_errors_are_per_request():
+    with pytest.raises(ValueError):
+        serving.Server(hbm_budget=1, runner=FakeGPU(), sizer=lambda r: 5).submit(_req(0))
+    gpu = FakeGPU(dur=0.01)
+    res, _ = serving.serve_stream([_req(12), _req(13), _req(14)], hbm_budget=3, max_active=3, runner=gpu,
+                                  sizer=lambda r: 1)
+    assert res[1].error and "planted" in res[1].error
+    assert res[0].error is None and res[2].error is None
+
+
+def test_latency_summary():
+    rs = [serving.Result(i, 1.0, None, 0.0, 0.0, float(i + 1), 0) for i in range(100)]
+    s = serving.latency_summary(rs)
+    assert abs(s["p50_s"] - 50.5) < 1e-9 and s["p99_s"] > 99.0 and s["n"] == 100
