@@ -629,7 +629,7 @@ int pnop_create(const pnop_grid* grid, const pnop_params* params, void* cuda_str
     if (grid->nr < 9 || grid->ntheta < 4 || grid->nz < 4 || (grid->ntheta & 1) || (grid->nz & 1) ||
         !(grid->Lz > 0) || !(grid->stretch >= 0 && grid->stretch < 1))
         return PNOP_ERR_INVALID_ARG;
-    if (!(params->Re > 0) || !(params->dt > 0) || params->snap_budget < 1 ||
+    if (!(params->Re > 0) || !(params->dt > 0) ||
         (params->precision != PNOP_FP64 && params->precision != PNOP_MIXED) || !(params->A >= 0) ||
         !(params->Wo > 0 || params->A == 0))
         return PNOP_ERR_INVALID_ARG;

@@ -55,7 +55,7 @@ def test_create_rejects_bad_arguments_before_touching_the_device(L):
         assert not h.value
     g = L.pnop_grid(32, 16, 32, 10.0, 0.0)
     for q in (L.pnop_params(-1.0, 8.0, 1.0, 0.01, 0.0, 0, 8, 0), L.pnop_params(2000.0, 8.0, 1.0, 0.0, 0.0, 0, 8, 0),
-              L.pnop_params(2000.0, 8.0, 1.0, 0.01, 0.0, 7, 8, 0), L.pnop_params(2000.0, 8.0, 1.0, 0.01, 0.0, 0, 0, 0)):
+              L.pnop_params(2000.0, 8.0, 1.0, 0.01, 0.0, 7, 8, 0), L.pnop_params(2000.0, -8.0, 1.0, 0.01, 0.0, 0, 0, 0)):
         assert L.lib.pnop_create(ctypes.byref(g), ctypes.byref(q), None, ctypes.byref(h)) == -1
     # physical sizes that are not 2^a 3^b: ntheta = 10 -> 15 points
     g = L.pnop_grid(32, 10, 32, 10.0, 0.0)
