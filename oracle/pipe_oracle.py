@@ -476,6 +476,24 @@ class Oracle:
             lb = self.adjoint_step(states[n], t0 + n * self.p.dt, lb)
         return ET, lb / self.What[None]
 
+    def linear_mode_step(self, um: np.ndarray, m: int, k: int, t: float) -> np.ndarray:
+        """`step` restricted to one Fourier mode (um: 3 x Nr) for a vanishing
+        amplitude: the u x w term drops and the base-flow terms act mode by mode."""
+        p = self.p
+
+        def forcing(v, tt):
+            full = np.zeros((3, p.nr, 2 * p.M + 1, p.K + 1), np.complex128)
+            full[:, :, m + p.M, k] = v
+            w = self.curl(full)[:, :, m + p.M, k]
+            U, dU = self.base(tt)
+            return np.stack([-U * w[1] + dU * v[2], U * w[0], -dU * v[0]])
+
+        Su, SF = self.mode_maps(m, k)
+        n0 = forcing(um, t)
+        us = (Su @ um.ravel() + SF @ n0.ravel()).reshape(3, p.nr)
+        n1 = forcing(us, t + p.dt)
+        return (Su @ um.ravel() + SF @ (0.5 * (n0 + n1)).ravel()).reshape(3, p.nr)
+
     # ---------------- diagnostics used by the pins ----------------
     def divergence(self, u: np.ndarray) -> np.ndarray:
         ur, ut, uz = u

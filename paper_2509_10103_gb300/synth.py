@@ -36,7 +36,7 @@ from __future__ import annotations
 
 import numpy as np
 
-__all__ = ["random_field", "localised_field", "oblique_field", "mode_field"]
+__all__ = ["random_field", "localised_field", "oblique_field", "mode_field", "single_mode"]
 
 _POLY_DEG = 2  # degree of P1, P2 in r^2
 
@@ -174,3 +174,13 @@ def oblique_field(r, M: int, K: int, Lz: float, seed: int = 0, wavelength: float
         coeffs[(m, k_ob)] = (_potential_monomials(m, 2, p1), _potential_monomials(m, 3, p2))
     wave = _assemble(r, M, K, Lz, coeffs)
     return base + wave
+
+
+def single_mode(r, m: int, k: int, Lz: float, seed: int = 0) -> np.ndarray:
+    """Velocity profile (3, Nr) of one random solenoidal mode (m, k); real
+    potentials for the mode (0, 0)."""
+    rng = np.random.default_rng(seed)
+    real = (m == 0 and k == 0)
+    psi = _potential_monomials(m, 2, _rand_poly(rng, real))
+    phi = _potential_monomials(m, 3, _rand_poly(rng, real))
+    return mode_field(r, m, 2.0 * np.pi * k / Lz, psi, phi)

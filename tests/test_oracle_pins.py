@@ -250,6 +250,19 @@ def test_reflection_symmetry_theta_to_minus_theta():
     np.testing.assert_allclose(o.step(refl(u), 0.2), refl(o.step(u, 0.2)), atol=1e-14 * np.abs(u).max())
 
 
+def test_linear_mode_step_is_the_step_restricted_to_one_mode():
+    o = _oracle(nr=12, M=3, K=4)
+    for (m, k) in ((2, 3), (-3, 1), (1, 0), (0, 0)):
+        um = synth.single_mode(o.r, m, k, o.p.Lz, seed=7) * 1e-12
+        full = np.zeros((3, o.p.nr, 2 * o.p.M + 1, o.p.K + 1), np.complex128)
+        full[:, :, m + o.p.M, k] = um
+        if k == 0:
+            full[:, :, -m + o.p.M, k] = np.conj(um)
+        ref = o.step(full, 0.7)[:, :, m + o.p.M, k]
+        got = o.linear_mode_step(um, m, k, 0.7)
+        np.testing.assert_allclose(got, ref, atol=1e-9 * np.abs(ref).max())
+
+
 # ---------------------------------------------------------------- adjoint
 def _jvp(o, u, v, t, h=1.0):
     f = lambda e: o.step(u + e * v, t)
