@@ -582,31 +582,20 @@ __global__ void __launch_bounds__(2 * kSK) k_band_solve(Geo g, const double* __r
     }
 }
 
-// R_v = B_v u_v + F'_v for v = +, -, z (rows j >= 1), F' = F - grad p
-__global__ void k_stage_rhs(Geo g, const double2* __restrict__ u, const double2* __restrict__ F,
-                            const double2* __restrict__ p, double2* __restrict__ R) {
+// RB_v = B_v u_v for v = +, -, z (rows j >= 1; row 0 is the Dirichlet row):
+// the explicit Crank-Nicolson half [1/dt + L_v/(2 Re)] u_v, which depends on
+// the old velocity only.  L_{m+1} and L_{m-1} share parity and differ only on
+// the diagonal (L_{m-1} = L_{m+1} + 4m/r^2), so L_{m+1} is applied to u_r and
+// u_theta and combined: L+ u+ = Lp u_r + i Lp u_t, L- u- = Lp u_r - i Lp u_t + 4m/r^2 u-.
+__global__ void k_stage_bu(Geo g, const double2* __restrict__ u, double2* __restrict__ RB) {
     Idx d;
     if (!decode(g, d)) return;
     const size_t o = sidx(g, d.j, d.im, d.k), S = d.S;
     if (d.j == 0) {
-        R[o] = R[o + S] = R[o + 2 * S] = make_double2(0, 0);
+        RB[o] = RB[o + S] = RB[o + 2 * S] = make_double2(0, 0);
         return;
     }
-    const double kz = d.k * g.kz0, ir = g.invr[d.j], mr = d.m * ir;
-    const double2 dp = band_row(g, g.D1 + ((size_t)par_idx(d.m) * g.nr + d.j) * kB, p, d.j, d.im, d.k);
-    const double2 pj = p[o], fr0 = F[o], ft0 = F[o + S], fz0 = F[o + 2 * S];
-    const double2 fr = make_double2(fr0.x - dp.x, fr0.y - dp.y);
-    const double2 ft = make_double2(ft0.x + mr * pj.y, ft0.y - mr * pj.x);
-    const double2 fz = make_double2(fz0.x + kz * pj.y, fz0.y - kz * pj.x);
-    if (!u) {  // forcing only: S(0, F)
-        R[o] = make_double2(fr.x - ft.y, fr.y + ft.x);
-        R[o + S] = make_double2(fr.x + ft.y, fr.y - ft.x);
-        R[o + 2 * S] = fz;
-        return;
-    }
-    // L_{m+1} and L_{m-1} share parity and differ only on the diagonal
-    // (L_{m-1} = L_{m+1} + 4m/r^2), so L_{m+1} is applied to u_r and u_theta
-    // separately and combined: L+ u+ = Lp u_r + i Lp u_t, L- u- = Lp u_r - i Lp u_t + 4m/r^2 u-.
+    const double kz = d.k * g.kz0, ir = g.invr[d.j];
     const double* Lp = g.Lb + ((size_t)abs(d.m + 1) * g.nr + d.j) * kB;
     const double* Lz = g.Lb + ((size_t)abs(d.m) * g.nr + d.j) * kB;
     double2 tr = make_double2(0, 0), tt = make_double2(0, 0), sz = make_double2(0, 0);
@@ -630,9 +619,37 @@ __global__ void k_stage_rhs(Geo g, const double2* __restrict__ u, const double2*
     const double fm = 4.0 * d.m * ir * ir;
     const double2 sp = make_double2(tr.x - tt.y, tr.y + tt.x);
     const double2 sm = make_double2(tr.x + tt.y + fm * um.x, tr.y - tt.x + fm * um.y);
-    R[o] = make_double2(dg * up.x + g.inv_2re * sp.x + (fr.x - ft.y), dg * up.y + g.inv_2re * sp.y + (fr.y + ft.x));
-    R[o + S] = make_double2(dg * um.x + g.inv_2re * sm.x + (fr.x + ft.y), dg * um.y + g.inv_2re * sm.y + (fr.y - ft.x));
-    R[o + 2 * S] = make_double2(dg * c.x + g.inv_2re * sz.x + fz.x, dg * c.y + g.inv_2re * sz.y + fz.y);
+    RB[o] = make_double2(dg * up.x + g.inv_2re * sp.x, dg * up.y + g.inv_2re * sp.y);
+    RB[o + S] = make_double2(dg * um.x + g.inv_2re * sm.x, dg * um.y + g.inv_2re * sm.y);
+    RB[o + 2 * S] = make_double2(dg * c.x + g.inv_2re * sz.x, dg * c.y + g.inv_2re * sz.y);
+}
+
+// R_v = [RB_v +] F'_v for v = +, -, z (rows j >= 1), F' = F - grad p
+__global__ void k_stage_rhs(Geo g, const double2* __restrict__ RB, const double2* __restrict__ F,
+                            const double2* __restrict__ p, double2* __restrict__ R) {
+    Idx d;
+    if (!decode(g, d)) return;
+    const size_t o = sidx(g, d.j, d.im, d.k), S = d.S;
+    if (d.j == 0) {
+        R[o] = R[o + S] = R[o + 2 * S] = make_double2(0, 0);
+        return;
+    }
+    const double kz = d.k * g.kz0, ir = g.invr[d.j], mr = d.m * ir;
+    const double2 dp = band_row(g, g.D1 + ((size_t)par_idx(d.m) * g.nr + d.j) * kB, p, d.j, d.im, d.k);
+    const double2 pj = p[o], fr0 = F[o], ft0 = F[o + S], fz0 = F[o + 2 * S];
+    const double2 fr = make_double2(fr0.x - dp.x, fr0.y - dp.y);
+    const double2 ft = make_double2(ft0.x + mr * pj.y, ft0.y - mr * pj.x);
+    const double2 fz = make_double2(fz0.x + kz * pj.y, fz0.y - kz * pj.x);
+    double2 rp = make_double2(fr.x - ft.y, fr.y + ft.x), rm = make_double2(fr.x + ft.y, fr.y - ft.x), rz = fz;
+    if (RB) {
+        const double2 a = RB[o], b = RB[o + S], c = RB[o + 2 * S];
+        rp.x += a.x; rp.y += a.y;
+        rm.x += b.x; rm.y += b.y;
+        rz.x += c.x; rz.y += c.y;
+    }
+    R[o] = rp;
+    R[o + S] = rm;
+    R[o + 2 * S] = rz;
 }
 
 // Per-mode wall coefficient of the influence correction, a0 = d/dr u_r at the
@@ -1043,8 +1060,12 @@ void launch_stage_psolve(const Geo& g, double2* q, cudaStream_t s) {
     launch_band_solve(g, g.facP, q, 0, 0, s);
     check_launch("stage_psolve");
 }
-void launch_stage_rhs(const Geo& g, const double2* u, const double2* F, const double2* p, double2* R, cudaStream_t s) {
-    k_stage_rhs<<<spec_grid(g), spec_bx(g), 0, s>>>(g, u, F, p, R);
+void launch_stage_bu(const Geo& g, const double2* u, double2* RB, cudaStream_t s) {
+    k_stage_bu<<<spec_grid(g), spec_bx(g), 0, s>>>(g, u, RB);
+    check_launch("stage_bu");
+}
+void launch_stage_rhs(const Geo& g, const double2* RB, const double2* F, const double2* p, double2* R, cudaStream_t s) {
+    k_stage_rhs<<<spec_grid(g), spec_bx(g), 0, s>>>(g, RB, F, p, R);
     check_launch("stage_rhs");
 }
 void launch_stage_hsolve(const Geo& g, double2* R, cudaStream_t s) {

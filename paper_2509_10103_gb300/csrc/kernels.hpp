@@ -72,8 +72,10 @@ void launch_anal_theta(const Geo& g, const FieldPtrs& f, int nfield, const T2* Z
 // out = back to (r, theta, z) + influence / flux corrections (Section 2.4).
 void launch_stage_div(const Geo& g, const double2* F, double2* q, cudaStream_t s);
 void launch_stage_psolve(const Geo& g, double2* q, cudaStream_t s);
-// u may be null: forcing-only stage S(0, F)
-void launch_stage_rhs(const Geo& g, const double2* u, const double2* F, const double2* p, double2* R, cudaStream_t s);
+// RB = explicit Crank-Nicolson half B_v u_v (depends on the old velocity only)
+void launch_stage_bu(const Geo& g, const double2* u, double2* RB, cudaStream_t s);
+// R = [RB +] (F - grad p) in the +/- basis; RB may be null (forcing-only stage S(0, F))
+void launch_stage_rhs(const Geo& g, const double2* RB, const double2* F, const double2* p, double2* R, cudaStream_t s);
 void launch_stage_hsolve(const Geo& g, double2* R, cudaStream_t s);
 // per-mode wall coefficients a0 (influence) / flux sums (mode (0,0)) into a0[nm*nk]
 void launch_stage_a0(const Geo& g, const double2* R, double2* a0, cudaStream_t s);

@@ -74,7 +74,11 @@ struct pnop_ctx {
     double2* wb = nullptr;
     double2* R = nullptr;
     double2* Rl = nullptr;  // front part of the transposed stage for the incoming cotangent
+    double2* RB = nullptr;  // explicit viscous half B u
     double2* q = nullptr;
+    double2* q2 = nullptr;  // pressure scratch of the side stream
+    cudaStream_t side = nullptr;  // second stream for independent work within a step
+    cudaEvent_t ev_fork = nullptr, ev_bu = nullptr, ev_t = nullptr;
     double2 *tmpA = nullptr, *tmpB = nullptr, *lamA = nullptr, *lamB = nullptr;
     void* Y = nullptr;
     void* Z = nullptr;
@@ -193,9 +197,10 @@ void prof_flush(pnop_ctx* c) {
     c->ev_used = 0;
 }
 
-// Launch `nk` kernels of class `cls` doing `units` work units; bracket them
-// with CUDA events on the context stream when that class is being timed.
-template <class F> void run(pnop_ctx* c, int cls, int nk, double units, F&& f) {
+// Launch `nk` kernels of class `cls` doing `units` work units on stream `st`
+// (the context stream by default); bracket them with CUDA events on that
+// stream when the class is being timed.
+template <class F> void run(pnop_ctx* c, int cls, int nk, double units, F&& f, cudaStream_t st) {
     c->launches[cls] += nk;
     c->units[cls] += units;
     if (!(c->prof_mask & (1u << cls))) {
@@ -209,11 +214,24 @@ template <class F> void run(pnop_ctx* c, int cls, int nk, double units, F&& f) {
         for (auto& e : c->ev) ck(cudaEventCreate(&e), "event create");
     }
     if (c->ev_used == pool) prof_flush(c);
-    ck(cudaEventRecord(c->ev[2 * c->ev_used], c->stream), "event record");
+    ck(cudaEventRecord(c->ev[2 * c->ev_used], st), "event record");
     f();
-    ck(cudaEventRecord(c->ev[2 * c->ev_used + 1], c->stream), "event record");
+    ck(cudaEventRecord(c->ev[2 * c->ev_used + 1], st), "event record");
     c->ev_cls[c->ev_used++] = cls;
 }
+template <class F> void run(pnop_ctx* c, int cls, int nk, double units, F&& f) {
+    run(c, cls, nk, units, std::forward<F>(f), c->stream);
+}
+
+// Fork: work queued on the side stream after this call starts after all work
+// queued so far on the context stream.
+void fork_side(pnop_ctx* c) {
+    ck(cudaEventRecord(c->ev_fork, c->stream), "fork");
+    ck(cudaStreamWaitEvent(c->side, c->ev_fork, 0), "fork");
+}
+// Join: work queued on the context stream after this call waits for `e`,
+// recorded on the side stream.
+void join_side(pnop_ctx* c, cudaEvent_t e) { ck(cudaStreamWaitEvent(c->stream, e, 0), "join"); }
 
 double nmodes(const pnop_ctx* c) { return (double)c->h.d.nm * c->h.d.nk; }
 
@@ -221,53 +239,64 @@ double nmodes(const pnop_ctx* c) { return (double)c->h.d.nm * c->h.d.nk; }
 // of the RADIAL_BAND and SPECTRAL classes): a 9-entry band row on a complex
 // value is 36 flops; the remaining terms are counted as written.
 namespace flops {
-constexpr double div = 36 + 12, rhs_u = 36 + 12 + 3 * 36 + 24, rhs_f = 36 + 12 + 8, a0_mode = 72, finish = 20;
+constexpr double div = 36 + 12, bu = 3 * 36 + 24, rhs = 36 + 12 + 8, a0_mode = 72, finish = 20;
 constexpr double tfinish = 36, trhs_u = 3 * 36 + 30, trhs_f = 8, qbar = 36 + 8, tdiv = 36 + 12;
 constexpr double curl = 2 * 36 + 16, curlT = 2 * 36 + 20, base = 12;
 }  // namespace flops
 
-// out = [addto +] S(u, F), one predictor-corrector stage (Section 2.4); u may
-// be null (forcing only, S(0, F)), which skips the explicit viscous matvec.
-void stage(pnop_ctx* c, const double2* u, const double2* F, double2* out, const double2* addto = nullptr) {
+// RB = explicit Crank-Nicolson half B u (old velocity only) on stream st
+void stage_bu(pnop_ctx* c, const double2* u, double2* RB, cudaStream_t st) {
+    run(c, PNOP_K_RADIAL_BAND, 1, flops::bu * c->S(), [&] { pnop::launch_stage_bu(c->geo, u, RB, st); }, st);
+}
+
+// out = [addto +] S(u, F), one predictor-corrector stage (Section 2.4), where
+// the velocity enters through RB = B u (null: forcing only, S(0, F)).  When
+// rb_ready is given the context stream waits for it before using RB.
+void stage(pnop_ctx* c, const double2* RB, const double2* F, double2* out, const double2* addto,
+           cudaEvent_t rb_ready) {
     const Geo& g = c->geo;
     cudaStream_t s = c->stream;
     const double S = (double)c->S();
     run(c, PNOP_K_RADIAL_BAND, 1, flops::div * S, [&] { pnop::launch_stage_div(g, F, c->q, s); });
     run(c, PNOP_K_RADIAL_SOLVE, 1, nmodes(c), [&] { pnop::launch_stage_psolve(g, c->q, s); });
-    run(c, PNOP_K_RADIAL_BAND, 1, (u ? flops::rhs_u : flops::rhs_f) * S,
-        [&] { pnop::launch_stage_rhs(g, u, F, c->q, c->R, s); });
+    if (rb_ready) join_side(c, rb_ready);
+    run(c, PNOP_K_RADIAL_BAND, 1, flops::rhs * S, [&] { pnop::launch_stage_rhs(g, RB, F, c->q, c->R, s); });
     run(c, PNOP_K_RADIAL_SOLVE, 1, 3 * nmodes(c), [&] { pnop::launch_stage_hsolve(g, c->R, s); });
     // the pressure is consumed: q now holds the per-mode wall coefficients
     run(c, PNOP_K_RADIAL_BAND, 1, flops::a0_mode * nmodes(c), [&] { pnop::launch_stage_a0(g, c->R, c->q, s); });
     run(c, PNOP_K_RADIAL_BAND, 1, flops::finish * S, [&] { pnop::launch_stage_finish(g, c->R, c->q, addto, out, s); });
 }
 
-// Rb = E A^{-T} Ti^H Fin^H ubn: the part of the transposed stage shared by
-// its velocity and forcing cotangents.
-void stageT_front(pnop_ctx* c, const double2* ubn, double2* Rb) {
-    const Geo& g = c->geo;
-    cudaStream_t s = c->stream;
-    run(c, PNOP_K_RADIAL_BAND, 1, flops::tfinish * c->S(), [&] { pnop::launch_stageT_finish(g, ubn, Rb, s); });
-    run(c, PNOP_K_RADIAL_SOLVE, 1, 3 * nmodes(c), [&] { pnop::launch_stageT_hsolve(g, Rb, s); });
+// out = S(u, F) on the context stream alone (operator access)
+void stage_u(pnop_ctx* c, const double2* u, const double2* F, double2* out) {
+    if (u) stage_bu(c, u, c->RB, c->stream);
+    stage(c, u ? c->RB : nullptr, F, out, nullptr, nullptr);
 }
 
-// Fb <- Proj^H Fb (transposed pressure projection, in place)
-void stageT_proj(pnop_ctx* c, double2* Fb) {
+// Rb = E A^{-T} Ti^H Fin^H ubn: the part of the transposed stage shared by
+// its velocity and forcing cotangents.
+void stageT_front(pnop_ctx* c, const double2* ubn, double2* Rb, cudaStream_t s) {
     const Geo& g = c->geo;
-    cudaStream_t s = c->stream;
+    run(c, PNOP_K_RADIAL_BAND, 1, flops::tfinish * c->S(), [&] { pnop::launch_stageT_finish(g, ubn, Rb, s); }, s);
+    run(c, PNOP_K_RADIAL_SOLVE, 1, 3 * nmodes(c), [&] { pnop::launch_stageT_hsolve(g, Rb, s); }, s);
+}
+
+// Fb <- Proj^H Fb (transposed pressure projection, in place, scratch q)
+void stageT_proj(pnop_ctx* c, double2* Fb, double2* q, cudaStream_t s) {
+    const Geo& g = c->geo;
     const double S = (double)c->S();
-    run(c, PNOP_K_RADIAL_BAND, 1, flops::qbar * S, [&] { pnop::launch_stageT_qbar(g, Fb, c->q, s); });
-    run(c, PNOP_K_RADIAL_SOLVE, 1, nmodes(c), [&] { pnop::launch_stageT_psolve(g, c->q, s); });
-    run(c, PNOP_K_RADIAL_BAND, 1, flops::tdiv * S, [&] { pnop::launch_stageT_div(g, c->q, Fb, s); });
+    run(c, PNOP_K_RADIAL_BAND, 1, flops::qbar * S, [&] { pnop::launch_stageT_qbar(g, Fb, q, s); }, s);
+    run(c, PNOP_K_RADIAL_SOLVE, 1, nmodes(c), [&] { pnop::launch_stageT_psolve(g, q, s); }, s);
+    run(c, PNOP_K_RADIAL_BAND, 1, flops::tdiv * S, [&] { pnop::launch_stageT_div(g, q, Fb, s); }, s);
 }
 
 // ub (=, or += when acc) S_u^H ubn ; Fb = S_F^H ubn  (either may be null)
 void stageT(pnop_ctx* c, const double2* ubn, double2* ub, int acc, double2* Fb) {
     const Geo& g = c->geo;
-    stageT_front(c, ubn, c->R);
+    stageT_front(c, ubn, c->R, c->stream);
     run(c, PNOP_K_RADIAL_BAND, 1, ((ub ? flops::trhs_u : 0) + (Fb ? flops::trhs_f : 0)) * c->S(),
         [&] { pnop::launch_stageT_rhs(g, c->R, nullptr, 1.0, 0.0, 1.0, 0.0, ub, acc, Fb, c->stream); });
-    if (Fb) stageT_proj(c, Fb);
+    if (Fb) stageT_proj(c, Fb, c->q, c->stream);
 }
 
 void axpby(pnop_ctx* c, double a, const double2* x, double b, const double2* y, double2* out) {
@@ -355,13 +384,17 @@ void nonlinearT(pnop_ctx* c, const double2* u, double t, const double2* nb, doub
 
 // ------------------------------------------------------------------ steps
 // Predictor u* = S(u, N0), corrector S(u, (N0 + N*)/2) = u* + S(0, (N* - N0)/2)
-// (S is linear), so the corrector skips the explicit viscous matvec.
+// (S is linear), so the corrector skips the explicit viscous matvec.  B u
+// depends on u only and runs on the side stream while N(u) is transformed.
 void fwd_step(pnop_ctx* c, const double2* u, double2* out, double t) {
+    fork_side(c);
+    stage_bu(c, u, c->RB, c->side);
+    ck(cudaEventRecord(c->ev_bu, c->side), "record");
     nonlinear(c, u, t, c->N0);
-    stage(c, u, c->N0, c->us);
+    stage(c, c->RB, c->N0, c->us, nullptr, c->ev_bu);
     nonlinear(c, c->us, t + c->h.ph.dt, c->N1);
     axpby(c, 0.5, c->N1, -0.5, c->N0, c->N1);
-    stage(c, nullptr, c->N1, out, c->us);
+    stage(c, nullptr, c->N1, out, c->us, nullptr);
 }
 
 // lout = J^T lin (Euclidean cotangents) for the step from state u at time t.
@@ -369,20 +402,28 @@ void fwd_step(pnop_ctx* c, const double2* u, double2* out, double t) {
 //   Fb = S_F^H lin, ub* = N*'^T (Fb/2),
 //   ubar = S_u^H (lin + ub*) + N0'^T S_F^H (lin/2 + ub*).
 // S_u^H and S_F^H share their front part (Rl for lin, R for ub*), so the
-// transposed viscous matvec runs once, on Rl + R.
+// transposed viscous matvec runs once, on Rl + R.  B u and everything that
+// depends on lin alone (Rl, S_F^H lin) run on the side stream while the
+// predictor is re-run on the context stream.
 void adj_step(pnop_ctx* c, const double2* u, double t, const double2* lin, double2* lout) {
     const Geo& g = c->geo;
-    nonlinear(c, u, t, c->N0);
-    stage(c, u, c->N0, c->us);
-    stageT_front(c, lin, c->Rl);
+    fork_side(c);
+    stage_bu(c, u, c->RB, c->side);
+    ck(cudaEventRecord(c->ev_bu, c->side), "record");
+    stageT_front(c, lin, c->Rl, c->side);
     run(c, PNOP_K_RADIAL_BAND, 1, flops::trhs_f * c->S(),
-        [&] { pnop::launch_stageT_rhs(g, c->Rl, nullptr, 0.0, 0.0, 0.5, 0.0, nullptr, 0, c->Nb, c->stream); });
-    stageT_proj(c, c->Nb);  // Nb = S_F^H lin / 2
+        [&] { pnop::launch_stageT_rhs(g, c->Rl, nullptr, 0.0, 0.0, 0.5, 0.0, nullptr, 0, c->Nb, c->side); },
+        c->side);
+    stageT_proj(c, c->Nb, c->q2, c->side);  // Nb = S_F^H lin / 2
+    ck(cudaEventRecord(c->ev_t, c->side), "record");
+    nonlinear(c, u, t, c->N0);
+    stage(c, c->RB, c->N0, c->us, nullptr, c->ev_bu);
+    join_side(c, c->ev_t);
     nonlinearT(c, c->us, t + c->h.ph.dt, c->Nb, c->ubs);
-    stageT_front(c, c->ubs, c->R);
+    stageT_front(c, c->ubs, c->R, c->stream);
     run(c, PNOP_K_RADIAL_BAND, 1, (flops::trhs_u + flops::trhs_f) * c->S(),
         [&] { pnop::launch_stageT_rhs(g, c->Rl, c->R, 1.0, 1.0, 0.5, 1.0, c->ua, 0, c->Nb, c->stream); });
-    stageT_proj(c, c->Nb);  // Nb = S_F^H (lin/2 + ub*)
+    stageT_proj(c, c->Nb, c->q, c->stream);  // Nb = S_F^H (lin/2 + ub*)
     nonlinearT(c, u, t, c->Nb, c->ubs);
     axpby(c, 1.0, c->ua, 1.0, c->ubs, lout);
 }
@@ -598,7 +639,7 @@ int pnop_context_bytes(const pnop_grid* grid, const pnop_params* params, int sna
     const size_t nm = 2 * M + 1, nk = K + 1, nkp = (nk + 31) / 32 * 32, nt = 3 * (M + 1);
     const size_t S = nr * nm * nk, field = 3 * S * 16;
     const size_t cz = params->precision == PNOP_MIXED ? 8 : 16;
-    size_t b = (16 + (size_t)snaps) * field + S * 16;                  // work fields, u_N, checkpoints, q
+    size_t b = (17 + (size_t)snaps) * field + 2 * S * 16;              // work fields, u_N, checkpoints, q, q2
     b += 15 * nr * nt * nk * cz;                                         // transform scratch Y, Z
     b += 2 * ((M + 2) + (M + 1)) * nr * 13 * nkp * 8;                    // LU factors and transposed rows
     b += (M + 2) * nr * 13 * 8 + 2 * nr * 13 * 8 + nm * nk * 3 * nr * 8; // bands, D1, influence
@@ -618,6 +659,9 @@ int pnop_revolve_counts(int nsteps, int snaps, long long* advances, long long* s
 void pnop_destroy(pnop_ctx* ctx) {
     if (!ctx) return;
     for (auto e : ctx->ev) cudaEventDestroy(e);
+    for (cudaEvent_t e : {ctx->ev_fork, ctx->ev_bu, ctx->ev_t})
+        if (e) cudaEventDestroy(e);
+    if (ctx->side) cudaStreamDestroy(ctx->side);
     for (void* p : ctx->allocs) cudaFree(p);
     delete ctx;
 }
@@ -679,9 +723,13 @@ int pnop_create(const pnop_grid* grid, const pnop_params* params, void* cuda_str
         c->tw.th_f = c->upload(thf);
         c->tw.z_f = c->upload(zf);
         for (double2** b : {&c->omega, &c->N0, &c->N1, &c->us, &c->ua, &c->Fb, &c->Nb, &c->ubs, &c->wb, &c->R,
-                            &c->Rl, &c->tmpA, &c->tmpB, &c->lamA, &c->lamB})
+                            &c->Rl, &c->RB, &c->tmpA, &c->tmpB, &c->lamA, &c->lamB})
             *b = c->field();
         c->q = (double2*)c->dalloc(c->S() * sizeof(double2));
+        c->q2 = (double2*)c->dalloc(c->S() * sizeof(double2));
+        ck(cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking), "side stream");
+        for (cudaEvent_t* e : {&c->ev_fork, &c->ev_bu, &c->ev_t})
+            ck(cudaEventCreateWithFlags(e, cudaEventDisableTiming), "event");
         const size_t cz = mixed(c) ? sizeof(float2) : sizeof(double2);
         const size_t plane = (size_t)d.nr * d.nth * d.nk * cz;
         c->Y = c->dalloc(9 * plane);
@@ -821,7 +869,7 @@ int pnop_apply(pnop_ctx* ctx, int op, const void* a, const void* b, void* out, d
             case PNOP_OP_NONLINEAR: nonlinear(ctx, A, t, O); break;
             case PNOP_OP_STAGE:
                 if (!B) throw Status(PNOP_ERR_INVALID_ARG, "stage needs a forcing field");
-                stage(ctx, A, B, O);
+                stage_u(ctx, A, B, O);
                 break;
             case PNOP_OP_NONLINEAR_T:
                 if (!B) throw Status(PNOP_ERR_INVALID_ARG, "transpose needs a cotangent field");
