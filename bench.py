@@ -232,6 +232,42 @@ def time_gradient(L, torch, precision, steps, warmup, H, snaps, ws, rank, sample
             "advances": adv, "adjoint_steps": nadj, "stores": stores, "clocks": clocks}
 
 
+def time_single_steps(L, torch, precision, reps=20):
+    """Raw device time of one forward step and of one adjoint step (no checkpointing)."""
+    import numpy as np
+    ctx = L.Context(NR, NTHETA, NZ, LZ, RE, DT, WO, AMP, TAU0, precision, 1)
+    r = np.array(ctx.pnop_grid_points())
+    u = torch.from_numpy(make_u0(r)).to("cuda")
+    u *= math.sqrt(E0 / ctx.pnop_energy(u))
+    lam = u.clone()
+    x = u.clone()
+    for _ in range(3):
+        ctx.pnop_step_forward(x, TAU0, 1)
+        ctx.pnop_step_adjoint(u, lam, TAU0)
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    torch.cuda.synchronize()
+    e[0].record()
+    for _ in range(reps):
+        ctx.pnop_step_forward(x, TAU0, 1)
+    e[1].record()
+    for _ in range(reps):
+        ctx.pnop_step_adjoint(u, lam, TAU0)
+    e[2].record()
+    torch.cuda.synchronize()
+    out = {"forward_step_ms": e[0].elapsed_time(e[1]) / reps, "adjoint_step_ms": e[1].elapsed_time(e[2]) / reps}
+    ctx.close()
+    return out
+
+
+def budget_sweep(L, torch, precision, H, budgets=(10, 57, 100), steps=2):
+    """fwd+adj steps/s of the same gradient at several checkpoint budgets (recompute vs store)."""
+    out = {}
+    for s in budgets:
+        res = time_gradient(L, torch, precision, steps, 1, H, s, 1, 0, None)
+        out[str(s)] = {"steps_per_s": H * steps / (res["ms"] / 1e3), "advances": res["advances"]}
+    return out
+
+
 def time_e2e(L, torch, precision, steps, warmup, H, snaps):
     ctx = L.Context(NR, NTHETA, NZ, LZ, RE, DT, WO, AMP, TAU0, precision, snaps)
     import numpy as np
@@ -421,7 +457,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--horizon-steps", type=int, default=100)
-    ap.add_argument("--snaps", type=int, default=10)
+    ap.add_argument("--snaps", type=int, default=57,
+                    help="checkpoint slots; 57 per 100 steps is the slots-per-step ratio of the 19,635-step "
+                         "deceleration horizon when ~11,000 state slots fill 280 GB of HBM")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
@@ -483,6 +521,10 @@ def main():
         "gpu_launches": launches,
         "clocks": mix["clocks"],
     }
+    if ws == 1:
+        out["single_step"] = {"mixed": time_single_steps(L, torch, L.PNOP_MIXED),
+                              "fp64": time_single_steps(L, torch, L.PNOP_FP64)}
+        out["budget_sweep_mixed"] = budget_sweep(L, torch, L.PNOP_MIXED, H)
     if not args.no_serving and ws == 1:
         out["serving"] = serving_report(L)
     if not args.no_cpu_baseline and ws == 1:

@@ -171,6 +171,16 @@ enum {
 };
 int pnop_apply(pnop_ctx* ctx, int op, const void* a, const void* b, void* out, double t);
 
+/* Host limit (seconds, 0 = none) on every wait of the context for its device
+ * work.  When a wait passes the limit the call returns PNOP_ERR_TIMEOUT; the
+ * queued work is not aborted and keeps running on the device, and the
+ * context stays usable: pnop_sync (or any later synchronising call) waits
+ * for it.  Results of the timed-out call are undefined. */
+int pnop_set_timeout(pnop_ctx* ctx, double seconds);
+
+/* Waits (without limit) for all device work of the context. */
+int pnop_sync(pnop_ctx* ctx);
+
 /* Kernel classes for launch counting and device timing. */
 enum {
     PNOP_K_SYNTH_THETA = 0,  /* zero-padded inverse theta FFTs (units: FFT columns) */

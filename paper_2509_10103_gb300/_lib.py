@@ -24,7 +24,7 @@ OP_CURL, OP_NONLINEAR, OP_STAGE, OP_NONLINEAR_T, OP_STAGE_T_U, OP_STAGE_T_F = ra
 EXPORTS = (
     "pnop_create", "pnop_set_base_flow", "pnop_dims", "pnop_grid_points", "pnop_step_forward",
     "pnop_step_adjoint", "pnop_gradient", "pnop_gradient_forward", "pnop_gradient_backward", "pnop_gradient_host", "pnop_gradient_stats", "pnop_energy",
-    "pnop_inner", "pnop_apply", "pnop_profile", "pnop_profile_read", "pnop_revolve_counts", "pnop_context_bytes", "pnop_energy_noalloc", "pnop_last_error", "pnop_error_string", "pnop_destroy",
+    "pnop_inner", "pnop_apply", "pnop_set_timeout", "pnop_sync", "pnop_profile", "pnop_profile_read", "pnop_revolve_counts", "pnop_context_bytes", "pnop_energy_noalloc", "pnop_last_error", "pnop_error_string", "pnop_destroy",
 )
 
 
@@ -56,6 +56,8 @@ def _load():
         "pnop_energy": (c_int, [c_void_p, c_void_p, POINTER(c_double)]),
         "pnop_inner": (c_int, [c_void_p, c_void_p, c_void_p, POINTER(c_double)]),
         "pnop_apply": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_void_p, c_double]),
+        "pnop_set_timeout": (c_int, [c_void_p, c_double]),
+        "pnop_sync": (c_int, [c_void_p]),
         "pnop_profile": (c_int, [c_void_p, ctypes.c_uint]),
         "pnop_profile_read": (c_int, [c_void_p, POINTER(c_double), POINTER(c_longlong), POINTER(c_double)]),
         "pnop_context_bytes": (c_int, [POINTER(pnop_grid), POINTER(pnop_params), c_int, POINTER(c_size_t)]),
@@ -204,6 +206,12 @@ class Context:
     def pnop_apply(self, op, a, b, out, t=0.0):
         bp = c_void_p(_ptr(b)) if b is not None else c_void_p(0)
         self._check(lib.pnop_apply(self._h, op, c_void_p(_ptr(a)), bp, c_void_p(_ptr(out)), t), "apply")
+
+    def pnop_set_timeout(self, seconds):
+        self._check(lib.pnop_set_timeout(self._h, seconds), "set_timeout")
+
+    def pnop_sync(self):
+        self._check(lib.pnop_sync(self._h), "sync")
 
     def pnop_profile(self, class_mask=0):
         self._check(lib.pnop_profile(self._h, class_mask), "profile")

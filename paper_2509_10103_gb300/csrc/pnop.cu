@@ -4,7 +4,9 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <chrono>
 #include <cmath>
+#include <thread>
 #include <complex>
 #include <cstring>
 #include <stdexcept>
@@ -94,6 +96,7 @@ struct pnop_ctx {
     double2* uN = nullptr;
     bool pending = false;
     int st_slots = 0;
+    double timeout_s = 0;  // host limit on waits for device work (0: none)
     // per-class launch counters, work units and optional event timing
     unsigned prof_mask = 0;
     std::vector<cudaEvent_t> ev;     // pairs (start, stop)
@@ -234,6 +237,26 @@ void fork_side(pnop_ctx* c) {
 void join_side(pnop_ctx* c, cudaEvent_t e) { ck(cudaStreamWaitEvent(c->stream, e, 0), "join"); }
 
 double nmodes(const pnop_ctx* c) { return (double)c->h.d.nm * c->h.d.nk; }
+
+// Waits for the context stream.  With a timeout set, polls the stream until
+// the deadline and then gives up with PNOP_ERR_TIMEOUT: the queued work keeps
+// running and a later call (or pnop_sync) waits for it; nothing is aborted.
+void wait_stream(pnop_ctx* c, const char* what) {
+    if (!(c->timeout_s > 0)) {
+        ck(cudaStreamSynchronize(c->stream), what);
+        return;
+    }
+    const auto t0 = std::chrono::steady_clock::now();
+    for (;;) {
+        cudaError_t e = cudaStreamQuery(c->stream);
+        if (e == cudaSuccess) return;
+        if (e != cudaErrorNotReady) ck(e, what);
+        const double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        if (el > c->timeout_s)
+            throw Status(PNOP_ERR_TIMEOUT, std::string(what) + ": device work not finished within the host limit");
+        std::this_thread::sleep_for(std::chrono::microseconds(50));
+    }
+}
 
 // Algorithmic FP64 flops per value of the banded/spectral kernels (work units
 // of the RADIAL_BAND and SPECTRAL classes): a 9-entry band row on a complex
@@ -432,7 +455,7 @@ double inner_sync(pnop_ctx* c, const double2* a, const double2* b) {
     inner_dev(c, a, b, c->dscal);
     double v = 0;
     ck(cudaMemcpyAsync(&v, c->dscal, sizeof(double), cudaMemcpyDeviceToHost, c->stream), "inner copy");
-    ck(cudaStreamSynchronize(c->stream), "inner sync");
+    wait_stream(c, "inner sync");
     return v;
 }
 
@@ -601,7 +624,7 @@ void gradient_backward(pnop_ctx* c, double gE, bool euclidean, double2* grad) {
     run_plan(c, c->plan_pos, false, &st);
     if (euclidean) ck(cudaMemcpyAsync(grad, c->lamA, c->field_bytes(), cudaMemcpyDeviceToDevice, c->stream), "copy");
     else weight(c, c->lamA, grad, 1);
-    ck(cudaStreamSynchronize(c->stream), "gradient sync");
+    wait_stream(c, "gradient sync");
 }
 
 int gradient_impl(pnop_ctx* c, const double2* u0, double E0, double horizon, double2* grad, double* gain) {
@@ -879,7 +902,21 @@ int pnop_apply(pnop_ctx* ctx, int op, const void* a, const void* b, void* out, d
             case PNOP_OP_STAGE_T_F: stageT(ctx, A, ctx->ua, 0, O); break;
             default: throw Status(PNOP_ERR_INVALID_ARG, "unknown operator");
         }
-        ck(cudaStreamSynchronize(ctx->stream), "apply");
+        wait_stream(ctx, "apply");
+        return PNOP_OK;
+    });
+}
+
+int pnop_set_timeout(pnop_ctx* ctx, double seconds) {
+    if (!ctx || !(seconds >= 0)) return PNOP_ERR_INVALID_ARG;
+    ctx->timeout_s = seconds;
+    return PNOP_OK;
+}
+
+int pnop_sync(pnop_ctx* ctx) {
+    return guarded(ctx, [&]() -> int {
+        ck(cudaStreamSynchronize(ctx->stream), "sync");
+        ck(cudaStreamSynchronize(ctx->side), "sync");
         return PNOP_OK;
     });
 }
