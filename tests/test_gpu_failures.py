@@ -63,7 +63,7 @@ def test_hbm_budget_too_small_for_the_checkpoints(env):
     torch, L = env
     need = L.pnop_context_bytes(32, 16, 32, 10.0, 0, 4)
     with pytest.raises(L.PnopError) as e:
-        _ctx(L, hbm=need // 4)
+        _ctx(L, hbm=1 << 20)  # 1 MiB cannot hold the operators
     assert e.value.code == -2
     ctx = _ctx(L, hbm=need, snaps=200)  # the pool cannot grow to 200 slots inside the budget
     u = torch.zeros(ctx.shape, dtype=torch.complex128, device="cuda")
