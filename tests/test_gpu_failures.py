@@ -65,10 +65,10 @@ def test_hbm_budget_too_small_for_the_checkpoints(env):
     with pytest.raises(L.PnopError) as e:
         _ctx(L, hbm=1 << 20)  # 1 MiB cannot hold the operators
     assert e.value.code == -2
-    ctx = _ctx(L, hbm=need, snaps=200)  # the pool cannot grow to 200 slots inside the budget
+    ctx = _ctx(L, hbm=need, snaps=1000)  # 1000 slots (350 MB) cannot fit in the budget
     u = torch.zeros(ctx.shape, dtype=torch.complex128, device="cuda")
     u[2, 5, ctx.M, 0] = 1e-3
     with pytest.raises(L.PnopError) as e:
-        ctx.pnop_gradient(u, -1.0, 2.0, torch.zeros_like(u))
+        ctx.pnop_gradient(u, -1.0, 10.0, torch.zeros_like(u))
     assert e.value.code == -2
     ctx.close()
