@@ -7,8 +7,10 @@ Re = 2000 (mean), Wo = 8, A = 1, dt = 0.0025, start at tau0 = T/4
 (deceleration, T = 2 pi Re / Wo^2), oblique m = +-1 seed (axial length 1.25
 radii) plus a weak random background scaled to E0 = 1e-5.  One bench step is
 one pnop_gradient over a horizon of H time steps (default 100) with a
-binomial checkpoint budget of s snapshots (default 10): forward sweep,
-recomputation from checkpoints and H adjoint steps.  The metric is
+binomial checkpoint budget of s snapshots (default 57, the slots-per-step
+ratio that about 11,000 state slots in 280 GB give the 19,635-step
+deceleration horizon): forward sweep, recomputation from checkpoints and H
+adjoint steps.  The metric is
 forward+adjoint time steps per second (H x steps / time), reported for the
 mixed path (FP32 transforms and products, FP64 radial solves and inner
 products) as `value`, and for the plain FP64 path under "fp64".
