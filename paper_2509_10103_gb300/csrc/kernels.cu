@@ -342,34 +342,23 @@ __device__ __forceinline__ double2 band_row(const Geo& g, const double* B, const
 }
 // Transposed banded product (B^T x)_j = sum_{j'} B[j'][j - j' + 4] x[j'].
 // Column j > 8 is reached only from rows j-4..j+4; columns 0..8 also from the
-// wall rows 0..3.  With TWO the operand is c1 x1 + c2 x2.
-template <bool TWO>
-__device__ __forceinline__ double2 band_col2(const Geo& g, const double* B0, const double2* x1, double c1,
-                                             const double2* x2, double c2, int j, int im, int k) {
+// wall rows 0..3.
+__device__ __forceinline__ double2 band_col(const Geo& g, const double* B0, const double2* x, int j, int im, int k) {
     double2 acc = make_double2(0, 0);
-    auto val = [&](int c) {
-        const size_t o = sidx(g, c, im, k);
-        if (!TWO) return x1[o];
-        const double2 a = x1[o], b = x2[o];
-        return make_double2(c1 * a.x + c2 * b.x, c1 * a.y + c2 * b.y);
-    };
     if (j > 8) {
 #pragma unroll
         for (int t = -4; t <= 4; ++t) {
             const int c = j + t;
-            if (c < g.nr) acc = dfma(__ldg(B0 + (size_t)c * kB + (4 - t)), val(c), acc);
+            if (c < g.nr) acc = dfma(__ldg(B0 + (size_t)c * kB + (4 - t)), x[sidx(g, c, im, k)], acc);
         }
     } else {
 #pragma unroll
         for (int t = -8; t <= 4; ++t) {
             const int c = j + t;
-            if (c >= 0 && c < g.nr) acc = dfma(__ldg(B0 + (size_t)c * kB + (4 - t)), val(c), acc);
+            if (c >= 0 && c < g.nr) acc = dfma(__ldg(B0 + (size_t)c * kB + (4 - t)), x[sidx(g, c, im, k)], acc);
         }
     }
     return acc;
-}
-__device__ __forceinline__ double2 band_col(const Geo& g, const double* B0, const double2* x, int j, int im, int k) {
-    return band_col2<false>(g, B0, x, 1.0, nullptr, 0.0, j, im, k);
 }
 
 __global__ void k_curl(Geo g, const double2* __restrict__ u, double2* __restrict__ w) {
@@ -466,14 +455,15 @@ __global__ void k_stage_div(Geo g, const double2* __restrict__ F, double2* __res
 // ------------------------------------------------------------------ banded solves
 // Two-sweep solve of one banded system per (matrix, k) with precomputed
 // row-local coefficients "lower | 1/diag | upper" (layout in setup.hpp).  A
-// block owns kSK consecutive k of one (component, m): the right-hand sides of
-// all rows sit in shared memory and the coefficient rows stream through a
-// double-buffered cp.async pipeline, kRC rows at a time.  Each of the 2 kSK
-// threads sweeps the real or the imaginary part of one system (the matrices
-// are real).  Terms are accumulated oldest first, so the dependence from one
-// row to the next is a single FMA.
-constexpr int kSK = 16;  // systems (consecutive k) per block; 2 threads (re, im) each
-constexpr int kRC = 8;   // rows per staged chunk
+// block owns kSK consecutive k of one (component, m) -- one tile of the factor
+// table: the right-hand sides of all rows sit in shared memory and the
+// coefficient rows stream through a double-buffered cp.async pipeline, kRC
+// rows at a time.  In the tiled table the coefficients of kRC consecutive rows
+// of one sweep are one contiguous piece, so staging a chunk is a plain linear
+// copy.  Each of the 2 kSK threads sweeps the real or the imaginary part of one
+// system (the matrices are real).  Terms are accumulated oldest first, so the
+// dependence from one row to the next is a single FMA.
+constexpr int kRC = 8;  // rows per staged chunk
 
 __device__ __forceinline__ void cp_async16(void* sm, const void* gm) {
     const unsigned a = (unsigned)__cvta_generic_to_shared(sm);
@@ -484,33 +474,32 @@ __device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_g
 
 // NL lower coefficients (oldest first) for the forward sweep, diagonal in the
 // forward sweep when DIAG1 (else in the backward sweep), NU upper coefficients
-// (nearest first) for the backward sweep.
+// (nearest first) for the backward sweep.  X = A^{-1} X [+ add].
 template <int NL, int NU, bool DIAG1>
 __global__ void __launch_bounds__(2 * kSK) k_band_solve(Geo g, const double* __restrict__ fac, double2* __restrict__ X,
-                                                  int helm, int zero_row0) {
-    constexpr int NC1 = NL + (DIAG1 ? 1 : 0);  // forward sweep: coefficients [0, NC1)
-    constexpr int E2 = NC1;                      // backward sweep: [E2, 13)
-    constexpr int NC2 = kB - E2;
+                                                  const double2* __restrict__ add, int helm, int zero_row0) {
+    constexpr int NC1 = NL + (DIAG1 ? 1 : 0);  // forward sweep: columns [0, NC1)
+    constexpr int NC2 = kB - NC1;               // backward sweep: columns [NC1, 13)
     constexpr int NCM = NC1 > NC2 ? NC1 : NC2;
     extern __shared__ __align__(16) unsigned char smem[];
     double2* Yb = reinterpret_cast<double2*>(smem);  // [nr][kSK]
     double* Yd = reinterpret_cast<double*>(smem);
     double* Cb = reinterpret_cast<double*>(Yb + (size_t)g.nr * kSK);  // [2][kRC][NCM][kSK]
-    const int nkb = (g.nk + kSK - 1) / kSK;
     int bi = blockIdx.x;
-    const int kb = bi % nkb;
-    bi /= nkb;
+    const int kb = bi % g.ntile;
+    bi /= g.ntile;
     const int im = bi % g.nm, v = bi / g.nm;
     const int m = im - g.M;
     const int mv = helm ? (v == 0 ? m + 1 : (v == 1 ? m - 1 : m)) : m;
     const int k0 = kb * kSK;
     const size_t S = (size_t)g.nr * g.nm * g.nk;
     double2* x = X + (size_t)v * S;  // v = 0 for the pressure
-    const double* F = fac + (size_t)abs(mv) * g.nr * kB * g.nkp + k0;
+    const double* T1 = fac + ((size_t)abs(mv) * g.ntile + kb) * (size_t)g.nr * kB * kSK;  // [nr][NC1][kSK]
+    const double* T2 = T1 + (size_t)g.nr * NC1 * kSK;                                    // [nr][NC2][kSK]
     const int tid = threadIdx.x, sy = tid % kSK, comp = tid / kSK;
     const int nch = (g.nr + kRC - 1) / kRC;
 
-    for (int i = tid; i < g.nr * kSK; i += blockDim.x) {
+    for (int i = tid; i < g.nr * kSK; i += 2 * kSK) {
         const int j = i / kSK, t = i % kSK;
         if (k0 + t < g.nk) cp_async16(&Yb[i], &x[sidx(g, j, im, k0 + t)]);
         else Yb[i] = make_double2(0, 0);
@@ -519,14 +508,12 @@ __global__ void __launch_bounds__(2 * kSK) k_band_solve(Geo g, const double* __r
         if (t >= 2 * nch) return;
         const bool fwd = t < nch;
         const int c = fwd ? t : 2 * nch - 1 - t;
-        const int e0 = fwd ? 0 : E2, nc = fwd ? NC1 : NC2;
-        double* C = Cb + (size_t)(t & 1) * kRC * NCM * kSK;
-        const int nseg = kRC * nc * (kSK / 2);
-        for (int i = tid; i < nseg; i += blockDim.x) {
-            const int q = i % (kSK / 2), rest = i / (kSK / 2);
-            const int e = rest % nc, r = rest / nc, j = c * kRC + r;
-            if (j < g.nr) cp_async16(&C[(r * NCM + e) * kSK + 2 * q], F + ((size_t)j * kB + e0 + e) * g.nkp + 2 * q);
-        }
+        const int rows = min(kRC, g.nr - c * kRC);
+        const int nc = fwd ? NC1 : NC2;
+        const double* src = (fwd ? T1 : T2) + (size_t)c * kRC * nc * kSK;
+        double* dst = Cb + (size_t)(t & 1) * kRC * NCM * kSK;
+        const int nseg = rows * nc * (kSK / 2);
+        for (int i = tid; i < nseg; i += 2 * kSK) cp_async16(dst + 2 * i, src + 2 * i);
     };
     stage(0);
     cp_async_commit();
@@ -542,43 +529,55 @@ __global__ void __launch_bounds__(2 * kSK) k_band_solve(Geo g, const double* __r
         __syncthreads();
         const double* C = Cb + (size_t)(t & 1) * kRC * NCM * kSK + sy;
         if (t < nch) {
+#pragma unroll
             for (int r = 0; r < kRC; ++r) {
                 const int j = t * kRC + r;
-                if (j >= g.nr) break;
-                double val = Yd[(j * kSK + sy) * 2 + comp];
-                const bool full = !(NL == 8 && j > 8);  // columns of U beyond row 8 hold 4 entries
+                if (j < g.nr) {
+                    double val = Yd[(j * kSK + sy) * 2 + comp];
+                    const bool full = !(NL == 8 && j > 8);  // columns of U beyond row 8 hold 4 entries
 #pragma unroll
-                for (int e = 0; e < NL; ++e)
-                    if (full || e >= NL - 4) val = fma(-C[(r * NCM + e) * kSK], w1[e], val);
-                if (DIAG1) val *= C[(r * NCM + NL) * kSK];
+                    for (int e = 0; e < NL; ++e)
+                        if (full || e >= NL - 4) val = fma(-C[(r * NC1 + e) * kSK], w1[e], val);
+                    if (DIAG1) val *= C[(r * NC1 + NL) * kSK];
 #pragma unroll
-                for (int e = 0; e < NL - 1; ++e) w1[e] = w1[e + 1];
-                w1[NL - 1] = val;
-                Yd[(j * kSK + sy) * 2 + comp] = val;
+                    for (int e = 0; e < NL - 1; ++e) w1[e] = w1[e + 1];
+                    w1[NL - 1] = val;
+                    Yd[(j * kSK + sy) * 2 + comp] = val;
+                }
             }
         } else {
             const int c = 2 * nch - 1 - t;
             constexpr int O = DIAG1 ? 0 : 1;  // first upper coefficient of the backward slice
+#pragma unroll
             for (int r = kRC - 1; r >= 0; --r) {
                 const int j = c * kRC + r;
-                if (j >= g.nr) continue;
-                double val = Yd[(j * kSK + sy) * 2 + comp];
-                const bool full = !(NU == 8 && j >= 4);  // rows of U from 4 on hold 4 entries
+                if (j < g.nr) {
+                    double val = Yd[(j * kSK + sy) * 2 + comp];
+                    const bool full = !(NU == 8 && j >= 4);  // rows of U from 4 on hold 4 entries
 #pragma unroll
-                for (int e = NU - 1; e >= 0; --e)
-                    if (full || e < 4) val = fma(-C[(r * NCM + O + e) * kSK], w2[e], val);
-                if (!DIAG1) val *= C[(r * NCM) * kSK];
+                    for (int e = NU - 1; e >= 0; --e)
+                        if (full || e < 4) val = fma(-C[(r * NC2 + O + e) * kSK], w2[e], val);
+                    if (!DIAG1) val *= C[(r * NC2) * kSK];
 #pragma unroll
-                for (int e = NU - 1; e > 0; --e) w2[e] = w2[e - 1];
-                w2[0] = val;
-                Yd[(j * kSK + sy) * 2 + comp] = val;
+                    for (int e = NU - 1; e > 0; --e) w2[e] = w2[e - 1];
+                    w2[0] = val;
+                    Yd[(j * kSK + sy) * 2 + comp] = val;
+                }
             }
         }
         __syncthreads();
     }
-    for (int i = tid; i < g.nr * kSK; i += blockDim.x) {
+    for (int i = tid; i < g.nr * kSK; i += 2 * kSK) {
         const int j = i / kSK, t = i % kSK;
-        if (k0 + t < g.nk) x[sidx(g, j, im, k0 + t)] = (zero_row0 && j == 0) ? make_double2(0, 0) : Yb[i];
+        if (k0 + t >= g.nk) continue;
+        const size_t o = sidx(g, j, im, k0 + t);
+        double2 val = (zero_row0 && j == 0) ? make_double2(0, 0) : Yb[i];
+        if (add) {
+            const double2 a = add[(size_t)v * S + o];
+            val.x += a.x;
+            val.y += a.y;
+        }
+        x[o] = val;
     }
 }
 
@@ -652,84 +651,104 @@ __global__ void k_stage_rhs(Geo g, const double2* __restrict__ RB, const double2
     R[o + 2 * S] = rz;
 }
 
-// Per-mode wall coefficient of the influence correction, a0 = d/dr u_r at the
-// wall of the tentative velocity (u_r = (x+ + x-)/2); for mode (0,0) the flux
-// sum_j W_j x_z instead.  One thread per mode; result in a0[mode].
-__global__ void k_stage_a0(Geo g, const double2* __restrict__ R, double2* __restrict__ a0) {
-    const int mode = blockIdx.x * blockDim.x + threadIdx.x;
-    if (mode >= g.nm * g.nk) return;
-    const int im = mode / g.nk, k = mode % g.nk, m = im - g.M;
-    const size_t S = (size_t)g.nr * g.nm * g.nk;
-    double2 acc = make_double2(0, 0);
-    if (m == 0 && k == 0) {
-        for (int c = 0; c < g.nr; ++c) acc = dfma(g.W[c], R[sidx(g, c, im, k) + 2 * S], acc);
-    } else {
-        const double* d0 = g.D1 + (size_t)par_idx(m + 1) * g.nr * kB;  // row 0 of D1 (u_r parity)
-        for (int c = 0; c <= 8; ++c) {
-            const size_t oc = sidx(g, c, im, k);
-            const double2 p = R[oc], q = R[oc + S];
-            acc = dfma(0.5 * __ldg(d0 + 4 + c), make_double2(p.x + q.x, p.y + q.y), acc);
-        }
-    }
-    a0[mode] = acc;
-}
+// Per-mode kernels of the wall conditions run on blocks of kFK consecutive k
+// (x) times kFJ radial groups (y) of one m: a per-mode scalar is reduced over
+// j into shared memory in a fixed order (deterministic), then every thread
+// applies it to its rows j = y, y + kFJ, ...
+constexpr int kFK = 16, kFJ = 16;
 
 // out = [addto +] back to (r, theta, z) with the influence correction
 // (div u = 0 at the wall) or, for mode (0,0), flux correction and u_r = 0.
-__global__ void k_stage_finish(Geo g, const double2* __restrict__ R, const double2* __restrict__ a0v,
-                               const double2* __restrict__ addto, double2* __restrict__ out) {
-    Idx d;
-    if (!decode(g, d)) return;
-    const size_t o = sidx(g, d.j, d.im, d.k), S = d.S;
-    const double2 xp = R[o], xm = R[o + S];
-    double2 ur = make_double2(0.5 * (xp.x + xm.x), 0.5 * (xp.y + xm.y));
-    double2 ut = make_double2(0.5 * (xp.y - xm.y), -0.5 * (xp.x - xm.x));
-    double2 uz = R[o + 2 * S];
-    const double2 a0 = a0v[d.im * g.nk + d.k];
-    if (d.m == 0 && d.k == 0) {
-        uz = dfma(g.fluxg[d.j] * (-g.flux_inv), a0, uz);
-        ur = make_double2(0, 0);
-    } else {
-        const double* h = g.infl + ((size_t)d.im * g.nk + d.k) * 3 * g.nr;
-        const double h0 = h[d.j], h1 = h[g.nr + d.j], h2 = h[2 * g.nr + d.j];
-        ur = dfma(h0, a0, ur);
-        ut = make_double2(ut.x - h1 * a0.y, ut.y + h1 * a0.x);
-        uz = make_double2(uz.x - h2 * a0.y, uz.y + h2 * a0.x);
+// The wall coefficient a0 = d/dr u_r at the wall of the tentative velocity
+// (u_r = (x+ + x-)/2), or for mode (0,0) the flux sum_j W_j x_z, is reduced
+// first.
+__global__ void __launch_bounds__(kFK* kFJ) k_stage_finish(Geo g, const double2* __restrict__ R,
+                                                          const double2* __restrict__ addto,
+                                                          double2* __restrict__ out) {
+    __shared__ double2 red[kFJ][kFK];
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int k = blockIdx.x * kFK + tx, im = blockIdx.y, m = im - g.M;
+    const size_t S = (size_t)g.nr * g.nm * g.nk;
+    const bool on = k < g.nk, mean = (m == 0 && k == 0);
+    double2 part = make_double2(0, 0);
+    if (on) {
+        if (mean) {
+            for (int j = ty; j < g.nr; j += kFJ) part = dfma(g.W[j], R[sidx(g, j, im, k) + 2 * S], part);
+        } else {
+            const double* d0 = g.D1 + (size_t)par_idx(m + 1) * g.nr * kB;  // row 0 of D1 (u_r parity)
+            for (int c = ty; c <= 8 && c < g.nr; c += kFJ) {
+                const size_t oc = sidx(g, c, im, k);
+                const double2 p = R[oc], q = R[oc + S];
+                part = dfma(0.5 * __ldg(d0 + 4 + c), make_double2(p.x + q.x, p.y + q.y), part);
+            }
+        }
     }
-    if (addto) {
-        const double2 a = addto[o], b = addto[o + S], c = addto[o + 2 * S];
-        ur.x += a.x; ur.y += a.y;
-        ut.x += b.x; ut.y += b.y;
-        uz.x += c.x; uz.y += c.y;
+    red[ty][tx] = part;
+    __syncthreads();
+    if (!on) return;
+    double2 a0 = red[0][tx];
+#pragma unroll
+    for (int i = 1; i < kFJ; ++i) a0 = make_double2(a0.x + red[i][tx].x, a0.y + red[i][tx].y);
+    const double* h = g.infl + ((size_t)im * g.nk + k) * 3 * g.nr;
+    for (int j = ty; j < g.nr; j += kFJ) {
+        const size_t o = sidx(g, j, im, k);
+        const double2 xp = R[o], xm = R[o + S];
+        double2 ur = make_double2(0.5 * (xp.x + xm.x), 0.5 * (xp.y + xm.y));
+        double2 ut = make_double2(0.5 * (xp.y - xm.y), -0.5 * (xp.x - xm.x));
+        double2 uz = R[o + 2 * S];
+        if (mean) {
+            uz = dfma(g.fluxg[j] * (-g.flux_inv), a0, uz);
+            ur = make_double2(0, 0);
+        } else {
+            const double h0 = h[j], h1 = h[g.nr + j], h2 = h[2 * g.nr + j];
+            ur = dfma(h0, a0, ur);
+            ut = make_double2(ut.x - h1 * a0.y, ut.y + h1 * a0.x);
+            uz = make_double2(uz.x - h2 * a0.y, uz.y + h2 * a0.x);
+        }
+        if (addto) {
+            const double2 a = addto[o], b = addto[o + S], c = addto[o + 2 * S];
+            ur.x += a.x; ur.y += a.y;
+            ut.x += b.x; ut.y += b.y;
+            uz.x += c.x; uz.y += c.y;
+        }
+        out[o] = ur;
+        out[o + S] = ut;
+        out[o + 2 * S] = uz;
     }
-    out[o] = ur;
-    out[o + S] = ut;
-    out[o + 2 * S] = uz;
 }
 
 // ------------------------------------------------------------------ radial stage (transpose)
-// One thread per mode: ybar = Fin^H ubar_new, then xbar = Ti^H ybar.
-__global__ void k_stageT_finish(Geo g, const double2* __restrict__ un, double2* __restrict__ R) {
-    const int mode = blockIdx.x * blockDim.x + threadIdx.x;
-    if (mode >= g.nm * g.nk) return;
-    const int im = mode / g.nk, k = mode % g.nk, m = im - g.M;
+// Per mode: ybar = Fin^H ubar_new (a reduction over j), then xbar = Ti^H ybar.
+__global__ void __launch_bounds__(kFK* kFJ) k_stageT_finish(Geo g, const double2* __restrict__ un,
+                                                           double2* __restrict__ R) {
+    __shared__ double2 red[kFJ][kFK];
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int k = blockIdx.x * kFK + tx, im = blockIdx.y, m = im - g.M;
     const size_t S = (size_t)g.nr * g.nm * g.nk;
-    const bool mean = (m == 0 && k == 0);
-    double2 acc = make_double2(0, 0);
-    const double* h = g.infl + ((size_t)im * g.nk + k) * 3 * g.nr;
-    for (int j = 0; j < g.nr; ++j) {
-        const size_t o = sidx(g, j, im, k);
-        if (mean) {
-            acc = dfma(g.fluxg[j], un[o + 2 * S], acc);
-        } else {
-            const double2 a = un[o], b = un[o + S], c = un[o + 2 * S];
-            // infl0 a - i infl1 b - i infl2 c
-            acc.x += h[j] * a.x + h[g.nr + j] * b.y + h[2 * g.nr + j] * c.y;
-            acc.y += h[j] * a.y - h[g.nr + j] * b.x - h[2 * g.nr + j] * c.x;
+    const bool on = k < g.nk, mean = (m == 0 && k == 0);
+    const double* h = g.infl + ((size_t)im * g.nk + (on ? k : 0)) * 3 * g.nr;
+    double2 part = make_double2(0, 0);
+    if (on) {
+        for (int j = ty; j < g.nr; j += kFJ) {
+            const size_t o = sidx(g, j, im, k);
+            if (mean) {
+                part = dfma(g.fluxg[j], un[o + 2 * S], part);
+            } else {
+                const double2 a = un[o], b = un[o + S], c = un[o + 2 * S];
+                // infl0 a - i infl1 b - i infl2 c
+                part.x += h[j] * a.x + h[g.nr + j] * b.y + h[2 * g.nr + j] * c.y;
+                part.y += h[j] * a.y - h[g.nr + j] * b.x - h[2 * g.nr + j] * c.x;
+            }
         }
     }
+    red[ty][tx] = part;
+    __syncthreads();
+    if (!on) return;
+    double2 acc = red[0][tx];
+#pragma unroll
+    for (int i = 1; i < kFJ; ++i) acc = make_double2(acc.x + red[i][tx].x, acc.y + red[i][tx].y);
     const double* d0 = g.D1 + (size_t)par_idx(m + 1) * g.nr * kB;
-    for (int j = 0; j < g.nr; ++j) {
+    for (int j = ty; j < g.nr; j += kFJ) {
         const size_t o = sidx(g, j, im, k);
         double2 yr = un[o], yt = un[o + S], yz = un[o + 2 * S];
         if (mean) {
@@ -744,35 +763,24 @@ __global__ void k_stageT_finish(Geo g, const double2* __restrict__ un, double2* 
     }
 }
 
-// With X = cu1 R1 + cu2 R2 and Y = cf1 R1 + cf2 R2 (R2 may be null):
-// ub (=, or += when acc) T^H B^T X when ub is given ; Fb = T^H Y when Fb is given.
+// ub (=, or += when acc) T^H B^T X when ub is given; Fb = T^H (cf1 X + cf2 Y)
+// when Fb is given (Y is read only when TWO).
 template <bool TWO>
-__global__ void k_stageT_rhs(Geo g, const double2* __restrict__ R1, const double2* __restrict__ R2, double cu1,
-                             double cu2, double cf1, double cf2, double2* __restrict__ ub, int acc,
-                             double2* __restrict__ Fb) {
+__global__ void k_stageT_rhs(Geo g, const double2* __restrict__ X, const double2* __restrict__ Y, double cf1,
+                             double cf2, double2* __restrict__ ub, int acc, double2* __restrict__ Fb) {
     Idx d;
     if (!decode(g, d)) return;
     const size_t o = sidx(g, d.j, d.im, d.k), S = d.S;
-    auto comb = [&](size_t i, double a1, double a2) {
-        const double2 p = R1[i];
-        if (!TWO) return make_double2(a1 * p.x, a1 * p.y);
-        const double2 q = R2[i];
-        return make_double2(a1 * p.x + a2 * q.x, a1 * p.y + a2 * q.y);
-    };
+    const double2 rp = X[o], rm = X[o + S], rz = X[o + 2 * S];
     if (ub) {
         const double kz = d.k * g.kz0;
         const double dg = g.inv_dt - kz * kz * g.inv_2re;
-        const double2 bp0 = band_col2<TWO>(g, g.Lb + (size_t)abs(d.m + 1) * g.nr * kB, R1, cu1, R2, cu2, d.j, d.im, d.k);
-        const double2 bm0 =
-            band_col2<TWO>(g, g.Lb + (size_t)abs(d.m - 1) * g.nr * kB, R1 + S, cu1, TWO ? R2 + S : nullptr, cu2, d.j, d.im, d.k);
-        const double2 bz0 =
-            band_col2<TWO>(g, g.Lb + (size_t)abs(d.m) * g.nr * kB, R1 + 2 * S, cu1, TWO ? R2 + 2 * S : nullptr, cu2, d.j, d.im, d.k);
-        const double2 rp = comb(o, cu1, cu2), rm = comb(o + S, cu1, cu2), rz = comb(o + 2 * S, cu1, cu2);
-        // band_col2<false> ignores the coefficient: scale here
-        const double sb = TWO ? 1.0 : cu1;
-        const double2 bp = make_double2(dg * rp.x + g.inv_2re * sb * bp0.x, dg * rp.y + g.inv_2re * sb * bp0.y);
-        const double2 bm = make_double2(dg * rm.x + g.inv_2re * sb * bm0.x, dg * rm.y + g.inv_2re * sb * bm0.y);
-        const double2 bz = make_double2(dg * rz.x + g.inv_2re * sb * bz0.x, dg * rz.y + g.inv_2re * sb * bz0.y);
+        const double2 bp0 = band_col(g, g.Lb + (size_t)abs(d.m + 1) * g.nr * kB, X, d.j, d.im, d.k);
+        const double2 bm0 = band_col(g, g.Lb + (size_t)abs(d.m - 1) * g.nr * kB, X + S, d.j, d.im, d.k);
+        const double2 bz0 = band_col(g, g.Lb + (size_t)abs(d.m) * g.nr * kB, X + 2 * S, d.j, d.im, d.k);
+        const double2 bp = make_double2(dg * rp.x + g.inv_2re * bp0.x, dg * rp.y + g.inv_2re * bp0.y);
+        const double2 bm = make_double2(dg * rm.x + g.inv_2re * bm0.x, dg * rm.y + g.inv_2re * bm0.y);
+        const double2 bz = make_double2(dg * rz.x + g.inv_2re * bz0.x, dg * rz.y + g.inv_2re * bz0.y);
         double2 vr = make_double2(bp.x + bm.x, bp.y + bm.y);
         double2 vt = make_double2(bp.y - bm.y, -bp.x + bm.x);
         double2 vz = bz;
@@ -787,10 +795,17 @@ __global__ void k_stageT_rhs(Geo g, const double2* __restrict__ R1, const double
         ub[o + 2 * S] = vz;
     }
     if (Fb) {
-        const double2 rp = comb(o, cf1, cf2), rm = comb(o + S, cf1, cf2), rz = comb(o + 2 * S, cf1, cf2);
-        Fb[o] = make_double2(rp.x + rm.x, rp.y + rm.y);
-        Fb[o + S] = make_double2(rp.y - rm.y, -rp.x + rm.x);
-        Fb[o + 2 * S] = rz;
+        double2 p = make_double2(cf1 * rp.x, cf1 * rp.y), q = make_double2(cf1 * rm.x, cf1 * rm.y),
+                z = make_double2(cf1 * rz.x, cf1 * rz.y);
+        if (TWO) {
+            const double2 a = Y[o], b = Y[o + S], c = Y[o + 2 * S];
+            p = make_double2(fma(cf2, a.x, p.x), fma(cf2, a.y, p.y));
+            q = make_double2(fma(cf2, b.x, q.x), fma(cf2, b.y, q.y));
+            z = make_double2(fma(cf2, c.x, z.x), fma(cf2, c.y, z.y));
+        }
+        Fb[o] = make_double2(p.x + q.x, p.y + q.y);
+        Fb[o + S] = make_double2(p.y - q.y, -p.x + q.x);
+        Fb[o + 2 * S] = z;
     }
 }
 
@@ -1031,9 +1046,9 @@ template void launch_zpass<float2>(const Geo&, int, const float2*, float2*, cons
                                    cudaStream_t);
 
 // trans (zero_row0 == 1) selects the transposed coefficient layout
-static void launch_band_solve(const Geo& g, const double* fac, double2* X, int helm, int zero_row0, cudaStream_t s) {
-    const int nkb = (g.nk + kSK - 1) / kSK;
-    const unsigned nblocks = (unsigned)((helm ? 3 : 1) * g.nm * nkb);
+static void launch_band_solve(const Geo& g, const double* fac, double2* X, const double2* add, int helm, int zero_row0,
+                              cudaStream_t s) {
+    const unsigned nblocks = (unsigned)((helm ? 3 : 1) * g.nm * g.ntile);
     const size_t sm = (size_t)g.nr * kSK * sizeof(double2) + 2 * (size_t)kRC * 9 * kSK * sizeof(double);
     if (!zero_row0) {
         static bool attr = false;
@@ -1041,14 +1056,14 @@ static void launch_band_solve(const Geo& g, const double* fac, double2* X, int h
             cudaFuncSetAttribute(k_band_solve<4, 8, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
             attr = true;
         }
-        k_band_solve<4, 8, false><<<nblocks, 2 * kSK, sm, s>>>(g, fac, X, helm, 0);
+        k_band_solve<4, 8, false><<<nblocks, 2 * kSK, sm, s>>>(g, fac, X, add, helm, 0);
     } else {
         static bool attr = false;
         if (!attr) {
             cudaFuncSetAttribute(k_band_solve<8, 4, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
             attr = true;
         }
-        k_band_solve<8, 4, true><<<nblocks, 2 * kSK, sm, s>>>(g, fac, X, helm, 1);
+        k_band_solve<8, 4, true><<<nblocks, 2 * kSK, sm, s>>>(g, fac, X, add, helm, 1);
     }
 }
 
@@ -1057,7 +1072,7 @@ void launch_stage_div(const Geo& g, const double2* F, double2* q, cudaStream_t s
     check_launch("stage_div");
 }
 void launch_stage_psolve(const Geo& g, double2* q, cudaStream_t s) {
-    launch_band_solve(g, g.facP, q, 0, 0, s);
+    launch_band_solve(g, g.facP, q, nullptr, 0, 0, s);
     check_launch("stage_psolve");
 }
 void launch_stage_bu(const Geo& g, const double2* u, double2* RB, cudaStream_t s) {
@@ -1069,32 +1084,28 @@ void launch_stage_rhs(const Geo& g, const double2* RB, const double2* F, const d
     check_launch("stage_rhs");
 }
 void launch_stage_hsolve(const Geo& g, double2* R, cudaStream_t s) {
-    launch_band_solve(g, g.facH, R, 1, 0, s);
+    launch_band_solve(g, g.facH, R, nullptr, 1, 0, s);
     check_launch("stage_hsolve");
 }
-void launch_stage_a0(const Geo& g, const double2* R, double2* a0, cudaStream_t s) {
-    k_stage_a0<<<nblk((size_t)g.nm * g.nk, 128), 128, 0, s>>>(g, R, a0);
-    check_launch("stage_a0");
-}
-void launch_stage_finish(const Geo& g, const double2* R, const double2* a0, const double2* addto, double2* out,
-                         cudaStream_t s) {
-    k_stage_finish<<<spec_grid(g), spec_bx(g), 0, s>>>(g, R, a0, addto, out);
+static inline dim3 mode_grid(const Geo& g) { return dim3((g.nk + kFK - 1) / kFK, g.nm); }
+void launch_stage_finish(const Geo& g, const double2* R, const double2* addto, double2* out, cudaStream_t s) {
+    k_stage_finish<<<mode_grid(g), dim3(kFK, kFJ), 0, s>>>(g, R, addto, out);
     check_launch("stage_finish");
 }
 void launch_stageT_finish(const Geo& g, const double2* ubn, double2* R, cudaStream_t s) {
-    k_stageT_finish<<<nblk((size_t)g.nm * g.nk, 64), 64, 0, s>>>(g, ubn, R);
+    k_stageT_finish<<<mode_grid(g), dim3(kFK, kFJ), 0, s>>>(g, ubn, R);
     check_launch("stageT_finish");
 }
-void launch_stageT_hsolve(const Geo& g, double2* R, cudaStream_t s) {
-    launch_band_solve(g, g.facHT, R, 1, 1, s);
+void launch_stageT_hsolve(const Geo& g, double2* R, const double2* add, cudaStream_t s) {
+    launch_band_solve(g, g.facHT, R, add, 1, 1, s);
     check_launch("stageT_hsolve");
 }
-void launch_stageT_rhs(const Geo& g, const double2* R1, const double2* R2, double cu1, double cu2, double cf1,
-                       double cf2, double2* ub, int acc, double2* Fb, cudaStream_t s) {
-    if (R2)
-        k_stageT_rhs<true><<<spec_grid(g), spec_bx(g), 0, s>>>(g, R1, R2, cu1, cu2, cf1, cf2, ub, acc, Fb);
+void launch_stageT_rhs(const Geo& g, const double2* X, const double2* Y, double cf1, double cf2, double2* ub, int acc,
+                       double2* Fb, cudaStream_t s) {
+    if (Y)
+        k_stageT_rhs<true><<<spec_grid(g), spec_bx(g), 0, s>>>(g, X, Y, cf1, cf2, ub, acc, Fb);
     else
-        k_stageT_rhs<false><<<spec_grid(g), spec_bx(g), 0, s>>>(g, R1, R2, cu1, cu2, cf1, cf2, ub, acc, Fb);
+        k_stageT_rhs<false><<<spec_grid(g), spec_bx(g), 0, s>>>(g, X, Y, cf1, cf2, ub, acc, Fb);
     check_launch("stageT_rhs");
 }
 void launch_stageT_qbar(const Geo& g, const double2* Fb, double2* q, cudaStream_t s) {
@@ -1102,7 +1113,7 @@ void launch_stageT_qbar(const Geo& g, const double2* Fb, double2* q, cudaStream_
     check_launch("stageT_qbar");
 }
 void launch_stageT_psolve(const Geo& g, double2* q, cudaStream_t s) {
-    launch_band_solve(g, g.facPT, q, 0, 1, s);
+    launch_band_solve(g, g.facPT, q, nullptr, 0, 1, s);
     check_launch("stageT_psolve");
 }
 void launch_stageT_div(const Geo& g, const double2* z, double2* Fb, cudaStream_t s) {

@@ -5,6 +5,10 @@
 
 namespace pnop {
 
+// Systems per banded-solver block: consecutive k of one (component, m).  The
+// factor tables are tiled in k by the same count.
+constexpr int kSK = 16;
+
 // Read-only geometry and operators, passed to kernels by value.
 struct Geo {
     int nr, M, K, nm, nk, nt, nzp;
@@ -16,10 +20,10 @@ struct Geo {
     const double* W;
     const double* D1;    // [2][nr][13]
     const double* Lb;    // [M+2][nr][13]
-    int nkp;             // k stride of the factor tables (multiple of 32)
-    const double* facH;  // [M+2][nr][13][nkp]  A x = b rows
-    const double* facP;  // [M+1][nr][13][nkp]
-    const double* facHT; // transposed-solve rows
+    int ntile;           // k tiles of kSK values in the factor tables
+    const double* facH;  // M+2 Helmholtz matrices, A x = b rows, tiled (4 forward | 9 backward columns)
+    const double* facP;  // M+1 pressure matrices, same layout
+    const double* facHT; // transposed-solve rows, tiled (9 forward | 4 backward columns)
     const double* facPT;
     const double* infl;  // [nm][nk][3][nr]
     const double* fluxg; // [nr]
@@ -77,17 +81,16 @@ void launch_stage_bu(const Geo& g, const double2* u, double2* RB, cudaStream_t s
 // R = [RB +] (F - grad p) in the +/- basis; RB may be null (forcing-only stage S(0, F))
 void launch_stage_rhs(const Geo& g, const double2* RB, const double2* F, const double2* p, double2* R, cudaStream_t s);
 void launch_stage_hsolve(const Geo& g, double2* R, cudaStream_t s);
-// per-mode wall coefficients a0 (influence) / flux sums (mode (0,0)) into a0[nm*nk]
-void launch_stage_a0(const Geo& g, const double2* R, double2* a0, cudaStream_t s);
-// out = [addto +] finished stage (addto may be null)
-void launch_stage_finish(const Geo& g, const double2* R, const double2* a0, const double2* addto, double2* out,
-                         cudaStream_t s);
+// out = [addto +] finished stage (addto may be null): the per-mode wall coefficient
+// (influence) or flux sum (mode (0,0)) and the correction it drives, in one launch
+void launch_stage_finish(const Geo& g, const double2* R, const double2* addto, double2* out, cudaStream_t s);
 // ---- radial stage (transpose): ub (=, or += when acc) S_u^H ubn, Fb = S_F^H ubn ----
 void launch_stageT_finish(const Geo& g, const double2* ubn, double2* R, cudaStream_t s);
-void launch_stageT_hsolve(const Geo& g, double2* R, cudaStream_t s);
-// X = cu1 R1 + cu2 R2, Y = cf1 R1 + cf2 R2 (R2 may be null): ub (+)= T^H B^T X if ub, Fb = T^H Y if Fb
-void launch_stageT_rhs(const Geo& g, const double2* R1, const double2* R2, double cu1, double cu2, double cf1,
-                       double cf2, double2* ub, int acc, double2* Fb, cudaStream_t s);
+// R = A^{-T} R [+ add] (add may be null)
+void launch_stageT_hsolve(const Geo& g, double2* R, const double2* add, cudaStream_t s);
+// ub (+)= T^H B^T X if ub;  Fb = T^H (cf1 X + cf2 Y) if Fb (Y may be null)
+void launch_stageT_rhs(const Geo& g, const double2* X, const double2* Y, double cf1, double cf2, double2* ub, int acc,
+                       double2* Fb, cudaStream_t s);
 void launch_stageT_qbar(const Geo& g, const double2* Fb, double2* q, cudaStream_t s);
 void launch_stageT_psolve(const Geo& g, double2* q, cudaStream_t s);
 void launch_stageT_div(const Geo& g, const double2* z, double2* Fb, cudaStream_t s);

@@ -17,6 +17,8 @@
 #include "kernels.hpp"
 #include "setup.hpp"
 
+static_assert(pnop::kSK == pnop::kTileK, "solver block and factor tile must cover the same k");
+
 using pnop::Geo;
 
 namespace {
@@ -179,7 +181,7 @@ void upload_operators(pnop_ctx* c) {
     g.facP = c->d_facP;
     g.facHT = c->d_facHT;
     g.facPT = c->d_facPT;
-    g.nkp = h.nkp;
+    g.ntile = h.ntile;
     g.infl = c->d_infl;
     g.fluxg = c->d_fluxg;
     g.flux_inv = h.flux_inv;
@@ -285,9 +287,8 @@ void stage(pnop_ctx* c, const double2* RB, const double2* F, double2* out, const
     if (rb_ready) join_side(c, rb_ready);
     run(c, PNOP_K_RADIAL_BAND, 1, flops::rhs * S, [&] { pnop::launch_stage_rhs(g, RB, F, c->q, c->R, s); });
     run(c, PNOP_K_RADIAL_SOLVE, 1, 3 * nmodes(c), [&] { pnop::launch_stage_hsolve(g, c->R, s); });
-    // the pressure is consumed: q now holds the per-mode wall coefficients
-    run(c, PNOP_K_RADIAL_BAND, 1, flops::a0_mode * nmodes(c), [&] { pnop::launch_stage_a0(g, c->R, c->q, s); });
-    run(c, PNOP_K_RADIAL_BAND, 1, flops::finish * S, [&] { pnop::launch_stage_finish(g, c->R, c->q, addto, out, s); });
+    run(c, PNOP_K_RADIAL_BAND, 1, flops::finish * S + flops::a0_mode * nmodes(c),
+        [&] { pnop::launch_stage_finish(g, c->R, addto, out, s); });
 }
 
 // out = S(u, F) on the context stream alone (operator access)
@@ -296,12 +297,12 @@ void stage_u(pnop_ctx* c, const double2* u, const double2* F, double2* out) {
     stage(c, u ? c->RB : nullptr, F, out, nullptr, nullptr);
 }
 
-// Rb = E A^{-T} Ti^H Fin^H ubn: the part of the transposed stage shared by
-// its velocity and forcing cotangents.
-void stageT_front(pnop_ctx* c, const double2* ubn, double2* Rb, cudaStream_t s) {
+// Rb = E A^{-T} Ti^H Fin^H ubn [+ add]: the part of the transposed stage
+// shared by its velocity and forcing cotangents.
+void stageT_front(pnop_ctx* c, const double2* ubn, double2* Rb, cudaStream_t s, const double2* add = nullptr) {
     const Geo& g = c->geo;
     run(c, PNOP_K_RADIAL_BAND, 1, flops::tfinish * c->S(), [&] { pnop::launch_stageT_finish(g, ubn, Rb, s); }, s);
-    run(c, PNOP_K_RADIAL_SOLVE, 1, 3 * nmodes(c), [&] { pnop::launch_stageT_hsolve(g, Rb, s); }, s);
+    run(c, PNOP_K_RADIAL_SOLVE, 1, 3 * nmodes(c), [&] { pnop::launch_stageT_hsolve(g, Rb, add, s); }, s);
 }
 
 // Fb <- Proj^H Fb (transposed pressure projection, in place, scratch q)
@@ -318,7 +319,7 @@ void stageT(pnop_ctx* c, const double2* ubn, double2* ub, int acc, double2* Fb) 
     const Geo& g = c->geo;
     stageT_front(c, ubn, c->R, c->stream);
     run(c, PNOP_K_RADIAL_BAND, 1, ((ub ? flops::trhs_u : 0) + (Fb ? flops::trhs_f : 0)) * c->S(),
-        [&] { pnop::launch_stageT_rhs(g, c->R, nullptr, 1.0, 0.0, 1.0, 0.0, ub, acc, Fb, c->stream); });
+        [&] { pnop::launch_stageT_rhs(g, c->R, nullptr, 1.0, 0.0, ub, acc, Fb, c->stream); });
     if (Fb) stageT_proj(c, Fb, c->q, c->stream);
 }
 
@@ -425,7 +426,7 @@ void fwd_step(pnop_ctx* c, const double2* u, double2* out, double t) {
 //   Fb = S_F^H lin, ub* = N*'^T (Fb/2),
 //   ubar = S_u^H (lin + ub*) + N0'^T S_F^H (lin/2 + ub*).
 // S_u^H and S_F^H share their front part (Rl for lin, R for ub*), so the
-// transposed viscous matvec runs once, on Rl + R.  B u and everything that
+// transposed viscous matvec runs once, on Rl + R (added by the second solve).  B u and everything that
 // depends on lin alone (Rl, S_F^H lin) run on the side stream while the
 // predictor is re-run on the context stream.
 void adj_step(pnop_ctx* c, const double2* u, double t, const double2* lin, double2* lout) {
@@ -435,7 +436,7 @@ void adj_step(pnop_ctx* c, const double2* u, double t, const double2* lin, doubl
     ck(cudaEventRecord(c->ev_bu, c->side), "record");
     stageT_front(c, lin, c->Rl, c->side);
     run(c, PNOP_K_RADIAL_BAND, 1, flops::trhs_f * c->S(),
-        [&] { pnop::launch_stageT_rhs(g, c->Rl, nullptr, 0.0, 0.0, 0.5, 0.0, nullptr, 0, c->Nb, c->side); },
+        [&] { pnop::launch_stageT_rhs(g, c->Rl, nullptr, 0.5, 0.0, nullptr, 0, c->Nb, c->side); },
         c->side);
     stageT_proj(c, c->Nb, c->q2, c->side);  // Nb = S_F^H lin / 2
     ck(cudaEventRecord(c->ev_t, c->side), "record");
@@ -443,9 +444,9 @@ void adj_step(pnop_ctx* c, const double2* u, double t, const double2* lin, doubl
     stage(c, c->RB, c->N0, c->us, nullptr, c->ev_bu);
     join_side(c, c->ev_t);
     nonlinearT(c, c->us, t + c->h.ph.dt, c->Nb, c->ubs);
-    stageT_front(c, c->ubs, c->R, c->stream);
+    stageT_front(c, c->ubs, c->R, c->stream, c->Rl);  // R = front(ub*) + front(lin)
     run(c, PNOP_K_RADIAL_BAND, 1, (flops::trhs_u + flops::trhs_f) * c->S(),
-        [&] { pnop::launch_stageT_rhs(g, c->Rl, c->R, 1.0, 1.0, 0.5, 1.0, c->ua, 0, c->Nb, c->stream); });
+        [&] { pnop::launch_stageT_rhs(g, c->R, c->Rl, 1.0, -0.5, c->ua, 0, c->Nb, c->stream); });
     stageT_proj(c, c->Nb, c->q, c->stream);  // Nb = S_F^H (lin/2 + ub*)
     nonlinearT(c, u, t, c->Nb, c->ubs);
     axpby(c, 1.0, c->ua, 1.0, c->ubs, lout);
@@ -659,7 +660,7 @@ int pnop_context_bytes(const pnop_grid* grid, const pnop_params* params, int sna
     if (!grid || !params || !bytes || snaps < 1 || grid->nr < 1 || grid->ntheta < 4 || grid->nz < 4)
         return PNOP_ERR_INVALID_ARG;
     const size_t nr = grid->nr, M = grid->ntheta / 2 - 1, K = grid->nz / 2 - 1;
-    const size_t nm = 2 * M + 1, nk = K + 1, nkp = (nk + 31) / 32 * 32, nt = 3 * (M + 1);
+    const size_t nm = 2 * M + 1, nk = K + 1, nkp = (nk + pnop::kTileK - 1) / pnop::kTileK * pnop::kTileK, nt = 3 * (M + 1);
     const size_t S = nr * nm * nk, field = 3 * S * 16;
     const size_t cz = params->precision == PNOP_MIXED ? 8 : 16;
     size_t b = (17 + (size_t)snaps) * field + 2 * S * 16;              // work fields, u_N, checkpoints, q, q2

@@ -273,16 +273,17 @@ static double band_backward_error(const Band& A, const std::vector<double>& f, u
     return rmax / (amax * xmax + 1e-300);
 }
 
-static void scatter_factors(std::vector<double>& dst, int mat, int k, int nr, int nkp, const std::vector<double>& f) {
+static void scatter_factors(std::vector<double>& dst, int mat, int k, int nr, int ntile, int nc1,
+                            const std::vector<double>& f) {
     for (int j = 0; j < nr; ++j)
-        for (int e = 0; e < kBand; ++e)
-            dst[(((size_t)mat * nr + j) * kBand + e) * nkp + k] = f[(size_t)j * kBand + e];
+        for (int e = 0; e < kBand; ++e) dst[fac_index(mat, k, j, e, nr, ntile, nc1)] = f[(size_t)j * kBand + e];
 }
 
-static void gather_factors(const std::vector<double>& src, int mat, int k, int nr, int nkp, std::vector<double>& f) {
+static void gather_factors(const std::vector<double>& src, int mat, int k, int nr, int ntile, int nc1,
+                           std::vector<double>& f) {
     f.resize((size_t)nr * kBand);
     for (int j = 0; j < nr; ++j)
-        for (int e = 0; e < kBand; ++e) f[(size_t)j * kBand + e] = src[(((size_t)mat * nr + j) * kBand + e) * nkp + k];
+        for (int e = 0; e < kBand; ++e) f[(size_t)j * kBand + e] = src[fac_index(mat, k, j, e, nr, ntile, nc1)];
 }
 
 // Row-local coefficients of A^T = U^T L^T from the factors of A: row j holds
@@ -351,10 +352,11 @@ bool build_operators(HostOps& h, std::string& err) {
             h.Lb[((size_t)ma * nr + j) * kBand + kLo] -= (double)ma * ma * h.invr[j] * h.invr[j];
         }
     }
-    const int nkp = h.nkp = (nk + 31) / 32 * 32;
-    h.facH.assign((size_t)(M + 2) * nr * kBand * nkp, 0.0);
+    const int nt = h.ntile = (nk + kTileK - 1) / kTileK;
+    const int D = kNc1Direct, T = kNc1Transposed;
+    h.facH.assign((size_t)(M + 2) * nt * nr * kBand * kTileK, 0.0);
     h.facHT.assign(h.facH.size(), 0.0);
-    h.facP.assign((size_t)(M + 1) * nr * kBand * nkp, 0.0);
+    h.facP.assign((size_t)(M + 1) * nt * nr * kBand * kTileK, 0.0);
     h.facPT.assign(h.facP.size(), 0.0);
     std::vector<double> f;
     double worst = 0, growth = 0;
@@ -367,16 +369,16 @@ bool build_operators(HostOps& h, std::string& err) {
                 return false;
             }
             worst = std::max(worst, band_backward_error(A, f, 1234u + ma * 977u + k));
-            scatter_factors(h.facH, ma, k, nr, nkp, f);
-            scatter_factors(h.facHT, ma, k, nr, nkp, transpose_factors(nr, f));
+            scatter_factors(h.facH, ma, k, nr, nt, D, f);
+            scatter_factors(h.facHT, ma, k, nr, nt, T, transpose_factors(nr, f));
         }
         for (int ma = 0; ma <= M; ++ma) {
             if (ma == 0 && k == 0) {
                 // singular Neumann problem of the mean mode: never used (p = 0)
                 std::vector<double> id((size_t)nr * kBand, 0.0);
                 for (int j = 0; j < nr; ++j) id[(size_t)j * kBand + kLo] = 1.0;
-                scatter_factors(h.facP, ma, k, nr, nkp, id);
-                scatter_factors(h.facPT, ma, k, nr, nkp, transpose_factors(nr, id));
+                scatter_factors(h.facP, ma, k, nr, nt, D, id);
+                scatter_factors(h.facPT, ma, k, nr, nt, T, transpose_factors(nr, id));
                 continue;
             }
             Band A = pressure_band(h, ma, kz);
@@ -385,8 +387,8 @@ bool build_operators(HostOps& h, std::string& err) {
                 return false;
             }
             worst = std::max(worst, band_backward_error(A, f, 4321u + ma * 131u + k));
-            scatter_factors(h.facP, ma, k, nr, nkp, f);
-            scatter_factors(h.facPT, ma, k, nr, nkp, transpose_factors(nr, f));
+            scatter_factors(h.facP, ma, k, nr, nt, D, f);
+            scatter_factors(h.facPT, ma, k, nr, nt, T, transpose_factors(nr, f));
         }
     }
     if (!(worst < 1e-12)) {
@@ -406,7 +408,7 @@ bool build_operators(HostOps& h, std::string& err) {
             const int m = im - M;
             if (m == 0 && k == 0) continue;
             const int ma = std::abs(m);
-            gather_factors(h.facP, ma, k, nr, nkp, f);  // factors computed above
+            gather_factors(h.facP, ma, k, nr, nt, D, f);  // factors computed above
             std::vector<double> phi(nr, 0.0);
             phi[0] = 1.0;
             band_solve(nr, f, phi);
@@ -422,11 +424,11 @@ bool build_operators(HostOps& h, std::string& err) {
                 fz[j] = -kz * phi[j];  // imaginary part of -i kz phi
             }
             fp[0] = fm[0] = fz[0] = 0.0;
-            gather_factors(h.facH, std::abs(m + 1), k, nr, nkp, fac_tmp);
+            gather_factors(h.facH, std::abs(m + 1), k, nr, nt, D, fac_tmp);
             band_solve(nr, fac_tmp, fp);
-            gather_factors(h.facH, std::abs(m - 1), k, nr, nkp, fac_tmp);
+            gather_factors(h.facH, std::abs(m - 1), k, nr, nt, D, fac_tmp);
             band_solve(nr, fac_tmp, fm);
-            gather_factors(h.facH, ma, k, nr, nkp, fac_tmp);
+            gather_factors(h.facH, ma, k, nr, nt, D, fac_tmp);
             band_solve(nr, fac_tmp, fz);
             std::vector<double> hr(nr), hti(nr);
             for (int j = 0; j < nr; ++j) {

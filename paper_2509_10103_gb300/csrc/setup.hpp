@@ -26,6 +26,22 @@ struct Physics {
     double Re = 0, Wo = 0, A = 0, dt = 0, tau0 = 0;
 };
 
+// Banded LU factor tables are tiled for the device solver: k is grouped in
+// tiles of kTileK consecutive values (one tile = the systems of one solver
+// block), and within a (matrix, tile) the forward-sweep columns [0, nc1) of
+// every row come first, then the backward-sweep columns [nc1, kBand):
+//   table[mat][tile][part 0: j][e < nc1][kk] , [part 1: j][e - nc1][kk]
+// so a run of consecutive rows of one sweep is one contiguous piece.
+constexpr int kTileK = 16;
+inline size_t fac_index(int mat, int k, int j, int e, int nr, int ntile, int nc1) {
+    const size_t tile = ((size_t)mat * ntile + k / kTileK) * (size_t)nr * kBand * kTileK;
+    const size_t in = e < nc1 ? ((size_t)j * nc1 + e) * kTileK
+                              : (size_t)nr * nc1 * kTileK + ((size_t)j * (kBand - nc1) + (e - nc1)) * kTileK;
+    return tile + in + k % kTileK;
+}
+constexpr int kNc1Direct = kLo;          // A x = b rows: l (4) | 1/diag, U (9)
+constexpr int kNc1Transposed = kUp + 1;  // A^T x = b rows: U^T (8), 1/diag | L^T (4)
+
 // Everything the device needs, laid out for coalesced access across k.
 struct HostOps {
     Dims d;
@@ -33,13 +49,13 @@ struct HostOps {
     std::vector<double> r, invr, W;            // [nr]
     std::vector<double> D1, D2;                 // [2 parity][nr][kBand], parity 0 even, 1 odd
     std::vector<double> Lb;                     // [M+2][nr][kBand]  D2 + D1/r - m^2/r^2 (no kz^2)
-    // Banded LU factors, k padded to nkp (a multiple of 32, zeros beyond nk).
-    // Row layout "lower | 1/diag | upper" for a two-sweep solve:
-    //   facH/facP  (A x = b):   l_{j,j-4..j-1}, 1/U_jj, U_{j,j+1..j+8}
-    //   facHT/facPT (A^T x = b): U_{j-8..j-1,j}, 1/U_jj, L_{j+1..j+4,j}
-    int nkp = 0;
-    std::vector<double> facH, facHT;            // [M+2][nr][kBand][nkp]  Helmholtz (per |m'|, k)
-    std::vector<double> facP, facPT;            // [M+1][nr][kBand][nkp]  pressure (per |m|, k)
+    // Banded LU factors in the tiled layout of fac_index (ntile tiles of k,
+    // zeros beyond nk).  Row layout "lower | 1/diag | upper" for a two-sweep solve:
+    //   facH/facP  (A x = b):   l_{j,j-4..j-1}, 1/U_jj, U_{j,j+1..j+8}    (nc1 = kNc1Direct)
+    //   facHT/facPT (A^T x = b): U_{j-8..j-1,j}, 1/U_jj, L_{j+1..j+4,j}  (nc1 = kNc1Transposed)
+    int ntile = 0;
+    std::vector<double> facH, facHT;            // M+2 matrices (per |m'|, k)  Helmholtz
+    std::vector<double> facP, facPT;            // M+1 matrices (per |m|, k)   pressure
     std::vector<double> infl;                   // [nm][nk][3][nr] influence response, pre-scaled by -1/delta
     std::vector<double> fluxg;                  // [nr] flux response of mode (0,0)
     double flux_inv = 0;                        // 1 / sum_j W_j g_j
