@@ -1,6 +1,6 @@
 """Build libpnop.so in-tree for sm_103a (GB300).
 
-Three translation units are compiled in parallel (two CUDA, one host C++) and
+Five translation units are compiled in parallel (four CUDA, one host C++) and
 linked into paper_2509_10103_gb300/libpnop.so.  No cmake; nvcc and g++ only.
 """
 from __future__ import annotations
@@ -32,14 +32,14 @@ def _run(cmd):
 
 
 def sources():
-    return [os.path.join(CSRC, f) for f in ("kernels.cu", "pnop.cu", "noalloc.cu", "setup.cpp")]
+    return [os.path.join(CSRC, f) for f in ("kernels.cu", "transforms.cu", "pnop.cu", "noalloc.cu", "setup.cpp")]
 
 
 def up_to_date() -> bool:
     if not os.path.exists(OUT):
         return False
     t = os.path.getmtime(OUT)
-    deps = sources() + [os.path.join(CSRC, f) for f in ("kernels.hpp", "setup.hpp")]
+    deps = sources() + [os.path.join(CSRC, f) for f in ("kernels.hpp", "setup.hpp", "dev_common.cuh")]
     deps.append(os.path.join(os.path.dirname(HERE), "include", "pnop.h"))
     return all(os.path.getmtime(d) <= t for d in deps)
 

@@ -1,0 +1,60 @@
+// Device helpers shared by the kernel translation units: complex arithmetic in
+// FP64 or FP32, precision conversion, launch checks.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdio>
+#include <stdexcept>
+
+namespace pnop {
+
+constexpr int kB = 13;  // stored band (columns j-4 .. j+8)
+
+// ------------------------------------------------------------------ complex helpers
+template <class T2> struct RealOf;
+template <> struct RealOf<double2> { using T = double; };
+template <> struct RealOf<float2> { using T = float; };
+
+template <class T2>
+__device__ __forceinline__ T2 mk(typename RealOf<T2>::T x, typename RealOf<T2>::T y) {
+    T2 r;
+    r.x = x;
+    r.y = y;
+    return r;
+}
+template <class T2> __device__ __forceinline__ T2 cadd(T2 a, T2 b) { return mk<T2>(a.x + b.x, a.y + b.y); }
+template <class T2> __device__ __forceinline__ T2 csub(T2 a, T2 b) { return mk<T2>(a.x - b.x, a.y - b.y); }
+template <class T2> __device__ __forceinline__ T2 cmul(T2 a, T2 b) {
+    return mk<T2>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+// s * i * z
+template <class T2> __device__ __forceinline__ T2 imul(T2 z, typename RealOf<T2>::T s) { return mk<T2>(-s * z.y, s * z.x); }
+__device__ __forceinline__ double2 dscale(double2 a, double s) { return make_double2(a.x * s, a.y * s); }
+__device__ __forceinline__ double2 dfma(double s, double2 a, double2 acc) {
+    return make_double2(fma(s, a.x, acc.x), fma(s, a.y, acc.y));
+}
+
+template <class T2> __device__ __forceinline__ T2 from_d(double2 v);
+template <> __device__ __forceinline__ double2 from_d<double2>(double2 v) { return v; }
+template <> __device__ __forceinline__ float2 from_d<float2>(double2 v) { return make_float2((float)v.x, (float)v.y); }
+template <class T2> __device__ __forceinline__ double2 to_d(T2 v) { return make_double2((double)v.x, (double)v.y); }
+
+__device__ __forceinline__ int par_idx(int m) { return m & 1; }  // 0 even, 1 odd (two's complement)
+
+// scale factor of the transform precision (no FP64->FP32 conversion in FP32 kernels)
+template <class T> __device__ __forceinline__ T zs(const double* d, const float* f, int i);
+template <> __device__ __forceinline__ double zs<double>(const double* d, const float*, int i) { return d[i]; }
+template <> __device__ __forceinline__ float zs<float>(const double*, const float* f, int i) { return f[i]; }
+
+static inline void check_launch(const char* what) {
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        char buf[256];
+        std::snprintf(buf, sizeof buf, "%s: %s", what, cudaGetErrorString(e));
+        throw std::runtime_error(buf);
+    }
+}
+static inline unsigned nblk(size_t n, int bs) { return (unsigned)((n + bs - 1) / bs); }
+
+}  // namespace pnop

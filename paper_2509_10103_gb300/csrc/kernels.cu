@@ -2,304 +2,16 @@
 // Section 2.4) and of its exact discrete transpose (the adjoint step that
 // replaces Eq. 2.9-2.11).
 //
-// Spectral fields are FP64 complex, layout [c][j][m + M][k].  The 3/2-padded
-// theta/z transforms are hand-written shared-memory Stockham FFTs (radix 2, 3,
-// 4) templated on FP64 or FP32; everything radial (banded matvecs, banded LU
-// solves, influence and flux corrections) is FP64.
+// Spectral fields are FP64 complex, layout [c][j][m + M][k].  Everything here
+// is FP64: the curl and base-flow terms, and everything radial (banded
+// matvecs, banded LU solves, influence and flux corrections).  The theta/z
+// transforms are in transforms.cu.
+#include "dev_common.cuh"
 #include "kernels.hpp"
 
 #include <algorithm>
-#include <cstdio>
-#include <stdexcept>
 
 namespace pnop {
-
-constexpr int kB = 13;  // stored band (columns j-4 .. j+8)
-
-// ------------------------------------------------------------------ complex helpers
-template <class T2> struct RealOf;
-template <> struct RealOf<double2> { using T = double; };
-template <> struct RealOf<float2> { using T = float; };
-
-template <class T2>
-__device__ __forceinline__ T2 mk(typename RealOf<T2>::T x, typename RealOf<T2>::T y) {
-    T2 r;
-    r.x = x;
-    r.y = y;
-    return r;
-}
-template <class T2> __device__ __forceinline__ T2 cadd(T2 a, T2 b) { return mk<T2>(a.x + b.x, a.y + b.y); }
-template <class T2> __device__ __forceinline__ T2 csub(T2 a, T2 b) { return mk<T2>(a.x - b.x, a.y - b.y); }
-template <class T2> __device__ __forceinline__ T2 cmul(T2 a, T2 b) {
-    return mk<T2>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
-}
-// s * i * z
-template <class T2> __device__ __forceinline__ T2 imul(T2 z, typename RealOf<T2>::T s) { return mk<T2>(-s * z.y, s * z.x); }
-__device__ __forceinline__ double2 dscale(double2 a, double s) { return make_double2(a.x * s, a.y * s); }
-__device__ __forceinline__ double2 dfma(double s, double2 a, double2 acc) {
-    return make_double2(fma(s, a.x, acc.x), fma(s, a.y, acc.y));
-}
-
-template <class T2> __device__ __forceinline__ T2 from_d(double2 v);
-template <> __device__ __forceinline__ double2 from_d<double2>(double2 v) { return v; }
-template <> __device__ __forceinline__ float2 from_d<float2>(double2 v) { return make_float2((float)v.x, (float)v.y); }
-template <class T2> __device__ __forceinline__ double2 to_d(T2 v) { return make_double2((double)v.x, (double)v.y); }
-
-__device__ __forceinline__ int par_idx(int m) { return m & 1; }  // 0 even, 1 odd (two's complement)
-
-// scale factor of the transform precision (no FP64->FP32 conversion in FP32 kernels)
-template <class T> __device__ __forceinline__ T zs(const double* d, const float* f, int i);
-template <> __device__ __forceinline__ double zs<double>(const double* d, const float*, int i) { return d[i]; }
-template <> __device__ __forceinline__ float zs<float>(const double*, const float* f, int i) { return f[i]; }
-
-// ------------------------------------------------------------------ shared-memory FFT
-// Batched Stockham FFT (autosort) over `ncol` columns of length N stored as
-// a[n * ld + col].  Radix 4, then 2, then 3 stages; N = 2^p 3^q.  tw holds
-// e^{-2 pi i n / N}; sign = -1 forward, +1 inverse (unnormalised).  Returns the
-// buffer holding the result.  All threads of the block must call it.
-template <class T2>
-__device__ __forceinline__ void small_dft(T2* v, const int R, const int sign) {
-    using T = typename RealOf<T2>::T;
-    if (R == 2) {
-        T2 a = v[0], b = v[1];
-        v[0] = cadd(a, b);
-        v[1] = csub(a, b);
-    } else if (R == 4) {
-        T2 s02 = cadd(v[0], v[2]), d02 = csub(v[0], v[2]);
-        T2 s13 = cadd(v[1], v[3]), d13 = csub(v[1], v[3]);
-        T2 id = imul(d13, (T)sign);
-        v[0] = cadd(s02, s13);
-        v[2] = csub(s02, s13);
-        v[1] = cadd(d02, id);
-        v[3] = csub(d02, id);
-    } else {  // R == 3
-        const T h = (T)0.86602540378443864676;  // sqrt(3)/2
-        T2 t1 = cadd(v[1], v[2]);
-        T2 t2 = mk<T2>(v[0].x - (T)0.5 * t1.x, v[0].y - (T)0.5 * t1.y);
-        T2 d = csub(v[1], v[2]);
-        T2 t3 = imul(d, (T)sign * h);
-        v[0] = cadd(v[0], t1);
-        v[1] = cadd(t2, t3);
-        v[2] = csub(t2, t3);
-    }
-}
-
-// One radix-R Stockham stage.  Ns (the size of the sub-transforms already
-// done) is a power of two 2^lgNs for every stage but the second and later
-// radix-3 stages (radix 3 runs last), so the index split is a shift there.
-template <class T2, int R, int NCOL, int LD, int SIGN>
-__device__ __forceinline__ void fft_stage(const T2* __restrict__ a, T2* __restrict__ b, int N, int Ns, int lgNs,
-                                          const T2* __restrict__ tw) {
-    const int stride = N / R;
-    const int nb = stride * NCOL;
-    const int tstep = N / (Ns * R);
-    for (int idx = threadIdx.x; idx < nb; idx += blockDim.x) {
-        const int col = idx % NCOL;
-        const int jb = idx / NCOL;
-        int q, kk;
-        if (lgNs >= 0) {
-            q = jb >> lgNs;
-            kk = jb & (Ns - 1);
-        } else {
-            q = jb / Ns;
-            kk = jb - q * Ns;
-        }
-        T2 v[R];
-#pragma unroll
-        for (int r = 0; r < R; ++r) v[r] = a[(jb + r * stride) * LD + col];
-        if (Ns > 1) {  // the first stage has unit twiddles
-            const int tb = kk * tstep;  // r * tb < N
-#pragma unroll
-            for (int r = 1; r < R; ++r) {
-                T2 w = tw[r * tb];
-                if (SIGN > 0) w.y = -w.y;
-                v[r] = cmul(v[r], w);
-            }
-        }
-        small_dft(v, R, SIGN);
-        const int idxD = q * Ns * R + kk;
-#pragma unroll
-        for (int r = 0; r < R; ++r) b[(idxD + r * Ns) * LD + col] = v[r];
-    }
-}
-
-template <class T2, int NCOL, int LD, int SIGN>
-__device__ T2* fft_cols(T2* a, T2* b, int N, const T2* tw) {
-    const int n2 = __ffs(N) - 1;  // N = 2^n2 3^n3
-    int n3 = 0;
-    for (int t = N >> n2; t > 1; t /= 3) ++n3;
-    int Ns = 1, lgNs = 0;
-    for (int st = 0; st < n2 / 2; ++st) {
-        fft_stage<T2, 4, NCOL, LD, SIGN>(a, b, N, Ns, lgNs, tw);
-        __syncthreads();
-        T2* t = a; a = b; b = t;
-        Ns *= 4;
-        lgNs += 2;
-    }
-    if (n2 & 1) {
-        fft_stage<T2, 2, NCOL, LD, SIGN>(a, b, N, Ns, lgNs, tw);
-        __syncthreads();
-        T2* t = a; a = b; b = t;
-        Ns *= 2;
-        lgNs += 1;
-    }
-    for (int st = 0; st < n3; ++st) {
-        fft_stage<T2, 3, NCOL, LD, SIGN>(a, b, N, Ns, st == 0 ? lgNs : -1, tw);
-        __syncthreads();
-        T2* t = a; a = b; b = t;
-        Ns *= 3;
-    }
-    return a;
-}
-
-// ------------------------------------------------------------------ theta synthesis
-// Y[f][j][a][k] = sum_m X_f[j][m][k] e^{i m theta_a}   (zero-padded to nt points)
-template <class T2, int KB>
-__global__ void k_synth_theta(Geo g, FieldPtrs f, T2* __restrict__ Y, const T2* __restrict__ twg) {
-    extern __shared__ __align__(16) unsigned char smem[];
-    T2* buf0 = reinterpret_cast<T2*>(smem);
-    T2* buf1 = buf0 + g.nt * KB;
-    T2* tw = buf1 + g.nt * KB;
-    const int k0 = blockIdx.x * KB, j = blockIdx.y, fi = blockIdx.z;
-    const int kw = min(KB, g.nk - k0);
-    for (int i = threadIdx.x; i < g.nt; i += blockDim.x) tw[i] = twg[i];
-    for (int i = threadIdx.x; i < g.nt * KB; i += blockDim.x) buf0[i] = mk<T2>(0, 0);
-    __syncthreads();
-    const double2* src = f.in[fi] + (size_t)j * g.nm * g.nk;
-    for (int i = threadIdx.x; i < g.nm * KB; i += blockDim.x) {
-        const int im = i / KB, kk = i % KB;
-        if (kk < kw) {
-            const int m = im - g.M;
-            const int a = m < 0 ? m + g.nt : m;
-            buf0[a * KB + kk] = from_d<T2>(src[(size_t)im * g.nk + k0 + kk]);
-        }
-    }
-    __syncthreads();
-    T2* res = fft_cols<T2, KB, KB, +1>(buf0, buf1, g.nt, tw);
-    T2* dst = Y + ((size_t)(fi * g.nr + j) * g.nt) * g.nk;
-    for (int i = threadIdx.x; i < g.nt * KB; i += blockDim.x) {
-        const int a = i / KB, kk = i % KB;
-        if (kk < kw) dst[(size_t)a * g.nk + k0 + kk] = res[i];
-    }
-}
-
-// ------------------------------------------------------------------ z pass + products
-// One block per (j, theta_a) row.  The Hermitian z spectra of two real fields
-// are packed into one complex inverse FFT; the pointwise products of the
-// physical fields are formed; two real products are packed into one forward
-// FFT and separated; the result is truncated to k <= K and scaled.
-//   ZFWD: inputs u (3), w (3)          -> outputs u x w (3)
-//   ZADJ: inputs u (3), w (3), g (3)   -> outputs w x g (3), g x u (3)
-template <class T2, int MODE>
-__global__ void k_zpass(Geo g, const T2* __restrict__ Y, T2* __restrict__ Z, ZScales sc, const T2* __restrict__ twg) {
-    using T = typename RealOf<T2>::T;
-    constexpr int NIN = MODE == ZFWD ? 6 : 9;
-    constexpr int NPI = (NIN + 1) / 2;
-    constexpr int NOUT = MODE == ZFWD ? 3 : 6;
-    constexpr int NPO = (NOUT + 1) / 2;
-    constexpr int LD = NPI;  // NPI >= NPO
-    extern __shared__ __align__(16) unsigned char smem[];
-    const int N = g.nzp, K = g.K, nk = g.nk;
-    T2* bufA = reinterpret_cast<T2*>(smem);
-    T2* bufB = bufA + N * LD;
-    T2* tw = bufB + N * LD;
-    const int a = blockIdx.x, j = blockIdx.y;
-    for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = twg[i];
-    // Hermitian-extended spectra, two fields per column
-    for (int p = 0; p < NPI; ++p)
-    for (int n = threadIdx.x; n < N; n += blockDim.x) {
-        int k = -1;
-        bool neg = false;
-        if (n <= K) k = n;
-        else if (n >= N - K) { k = N - n; neg = true; }
-        T2 q = mk<T2>(0, 0);
-        if (k >= 0) {
-            const int f1 = 2 * p, f2 = 2 * p + 1;
-            T2 y1 = Y[((size_t)(f1 * g.nr + j) * g.nt + a) * nk + k];
-            T2 h1 = k == 0 ? mk<T2>(zs<T>(sc.h0, sc.fh0, f1) * y1.x, 0)
-                           : mk<T2>(zs<T>(sc.hk, sc.fhk, f1) * y1.x, zs<T>(sc.hk, sc.fhk, f1) * y1.y);
-            T2 h2 = mk<T2>(0, 0);
-            if (f2 < NIN) {
-                T2 y2 = Y[((size_t)(f2 * g.nr + j) * g.nt + a) * nk + k];
-                h2 = k == 0 ? mk<T2>(zs<T>(sc.h0, sc.fh0, f2) * y2.x, 0)
-                            : mk<T2>(zs<T>(sc.hk, sc.fhk, f2) * y2.x, zs<T>(sc.hk, sc.fhk, f2) * y2.y);
-            }
-            if (!neg) q = mk<T2>(h1.x - h2.y, h1.y + h2.x);   // H1 + i H2
-            else q = mk<T2>(h1.x + h2.y, -h1.y + h2.x);       // conj(H1) + i conj(H2)
-        }
-        bufA[n * LD + p] = q;
-    }
-    __syncthreads();
-    T2* ph = fft_cols<T2, NPI, LD, +1>(bufA, bufB, N, tw);
-    T2* pr = (ph == bufA) ? bufB : bufA;
-    for (int n = threadIdx.x; n < N; n += blockDim.x) {
-        const T2* row = ph + n * LD;
-        const T ur = row[0].x, ut = row[0].y, uz = row[1].x;
-        const T wr = row[1].y, wt = row[2].x, wz = row[2].y;
-        T2* o = pr + n * LD;
-        if (MODE == ZFWD) {
-            o[0] = mk<T2>(ut * wz - uz * wt, uz * wr - ur * wz);
-            o[1] = mk<T2>(ur * wt - ut * wr, 0);
-        } else {
-            const T gr = row[3].x, gt = row[3].y, gz = row[4].x;
-            // w x g
-            o[0] = mk<T2>(wt * gz - wz * gt, wz * gr - wr * gz);
-            // (w x g)_z, (g x u)_r
-            o[1] = mk<T2>(wr * gt - wt * gr, gt * uz - gz * ut);
-            // (g x u)_theta, (g x u)_z
-            o[2] = mk<T2>(gz * ur - gr * uz, gr * ut - gt * ur);
-        }
-    }
-    __syncthreads();
-    T2* sp = fft_cols<T2, NPO, LD, -1>(pr, ph, N, tw);
-    for (int p = 0; p < NPO; ++p)
-    for (int k = threadIdx.x; k < nk; k += blockDim.x) {
-        const T2 P = sp[k * LD + p];
-        const T2 Pm = sp[((N - k) % N) * LD + p];
-        const int o1 = 2 * p, o2 = 2 * p + 1;
-        const T s1 = k == 0 ? zs<T>(sc.o0, sc.fo0, o1) : zs<T>(sc.ok, sc.fok, o1);
-        T2 z1 = mk<T2>((T)0.5 * (P.x + Pm.x) * s1, (T)0.5 * (P.y - Pm.y) * s1);
-        Z[((size_t)(o1 * g.nr + j) * g.nt + a) * nk + k] = z1;
-        if (o2 < NOUT) {
-            const T s2 = k == 0 ? zs<T>(sc.o0, sc.fo0, o2) : zs<T>(sc.ok, sc.fok, o2);
-            T2 z2 = mk<T2>((T)0.5 * (P.y + Pm.y) * s2, (T)-0.5 * (P.x - Pm.x) * s2);
-            Z[((size_t)(o2 * g.nr + j) * g.nt + a) * nk + k] = z2;
-        }
-    }
-}
-
-// ------------------------------------------------------------------ theta analysis
-// X_f[j][m][k] = sum_a Z_f[j][a][k] e^{-i m theta_a}, |m| <= M, with the k = 0
-// plane projected onto Hermitian symmetry.
-template <class T2, int KB>
-__global__ void k_anal_theta(Geo g, FieldPtrs f, const T2* __restrict__ Z, const T2* __restrict__ twg) {
-    extern __shared__ __align__(16) unsigned char smem[];
-    T2* buf0 = reinterpret_cast<T2*>(smem);
-    T2* buf1 = buf0 + g.nt * KB;
-    T2* tw = buf1 + g.nt * KB;
-    const int k0 = blockIdx.x * KB, j = blockIdx.y, fi = blockIdx.z;
-    const int kw = min(KB, g.nk - k0);
-    for (int i = threadIdx.x; i < g.nt; i += blockDim.x) tw[i] = twg[i];
-    const T2* src = Z + ((size_t)(fi * g.nr + j) * g.nt) * g.nk;
-    for (int i = threadIdx.x; i < g.nt * KB; i += blockDim.x) {
-        const int a = i / KB, kk = i % KB;
-        buf0[i] = kk < kw ? src[(size_t)a * g.nk + k0 + kk] : mk<T2>(0, 0);
-    }
-    __syncthreads();
-    T2* res = fft_cols<T2, KB, KB, -1>(buf0, buf1, g.nt, tw);
-    double2* dst = f.out[fi] + (size_t)j * g.nm * g.nk;
-    for (int i = threadIdx.x; i < g.nm * KB; i += blockDim.x) {
-        const int im = i / KB, kk = i % KB;
-        if (kk >= kw) continue;
-        const int m = im - g.M;
-        double2 v = to_d(res[(m < 0 ? m + g.nt : m) * KB + kk]);
-        if (k0 + kk == 0) {
-            double2 vm = to_d(res[(m > 0 ? g.nt - m : -m) * KB + kk]);
-            v = make_double2(0.5 * (v.x + vm.x), 0.5 * (v.y - vm.y));
-        }
-        dst[(size_t)im * g.nk + k0 + kk] = v;
-    }
-}
 
 // ------------------------------------------------------------------ spectral FP64 kernels
 struct Idx {
@@ -906,15 +618,6 @@ __global__ void k_inner_final(const double* __restrict__ partial, int np, double
 }
 
 // ------------------------------------------------------------------ launchers
-static void check_launch(const char* what) {
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) {
-        char buf[256];
-        std::snprintf(buf, sizeof buf, "%s: %s", what, cudaGetErrorString(e));
-        throw std::runtime_error(buf);
-    }
-}
-static inline unsigned nblk(size_t n, int bs) { return (unsigned)((n + bs - 1) / bs); }
 // block and grid of the 3-D spectral launches (x: k, y: m, z: r)
 static inline unsigned spec_bx(const Geo& g) { return g.nk <= 32 ? 32u : (g.nk <= 64 ? 64u : 128u); }
 static inline dim3 spec_grid(const Geo& g) { return dim3((g.nk + spec_bx(g) - 1) / spec_bx(g), g.nm, g.nr); }
@@ -935,115 +638,6 @@ void launch_baseT_acc(const Geo& g, const double2* nb, double2* ub, double2* wb,
     k_baseT_acc<<<spec_grid(g), spec_bx(g), 0, s>>>(g, nb, ub, wb, c, sn);
     check_launch("baseT");
 }
-
-template <class T2> static const T2* tw_theta(const Twiddles& t);
-template <> const double2* tw_theta<double2>(const Twiddles& t) { return t.th_d; }
-template <> const float2* tw_theta<float2>(const Twiddles& t) { return t.th_f; }
-template <class T2> static const T2* tw_z(const Twiddles& t);
-template <> const double2* tw_z<double2>(const Twiddles& t) { return t.z_d; }
-template <> const float2* tw_z<float2>(const Twiddles& t) { return t.z_f; }
-
-template <class T2> static int theta_kb(const Geo& g) {
-    int kb = 32;
-    while (kb > 4 && (kb / 2 >= g.nk || (size_t)(2 * g.nt * kb + g.nt) * sizeof(T2) > 100 * 1024)) kb /= 2;
-    return kb;
-}
-
-template <class T2, int KB>
-static void synth_theta_kb(const Geo& g, const FieldPtrs& f, int nfield, T2* Y, const T2* tw, cudaStream_t s) {
-    const size_t sm = (size_t)(2 * g.nt * KB + g.nt) * sizeof(T2);
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(k_synth_theta<T2, KB>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        attr = true;
-    }
-    dim3 grid((g.nk + KB - 1) / KB, g.nr, nfield);
-    k_synth_theta<T2, KB><<<grid, 256, sm, s>>>(g, f, Y, tw);
-}
-
-template <class T2, int KB>
-static void anal_theta_kb(const Geo& g, const FieldPtrs& f, int nfield, const T2* Z, const T2* tw, cudaStream_t s) {
-    const size_t sm = (size_t)(2 * g.nt * KB + g.nt) * sizeof(T2);
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(k_anal_theta<T2, KB>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        attr = true;
-    }
-    dim3 grid((g.nk + KB - 1) / KB, g.nr, nfield);
-    k_anal_theta<T2, KB><<<grid, 256, sm, s>>>(g, f, Z, tw);
-}
-
-template <class T2>
-void launch_synth_theta(const Geo& g, const FieldPtrs& f, int nfield, T2* Y, const Twiddles& tw, cudaStream_t s) {
-    switch (theta_kb<T2>(g)) {
-        case 32: synth_theta_kb<T2, 32>(g, f, nfield, Y, tw_theta<T2>(tw), s); break;
-        case 16: synth_theta_kb<T2, 16>(g, f, nfield, Y, tw_theta<T2>(tw), s); break;
-        case 8: synth_theta_kb<T2, 8>(g, f, nfield, Y, tw_theta<T2>(tw), s); break;
-        default: synth_theta_kb<T2, 4>(g, f, nfield, Y, tw_theta<T2>(tw), s); break;
-    }
-    check_launch("synth_theta");
-}
-
-template <class T2>
-void launch_anal_theta(const Geo& g, const FieldPtrs& f, int nfield, const T2* Z, const Twiddles& tw, cudaStream_t s) {
-    switch (theta_kb<T2>(g)) {
-        case 32: anal_theta_kb<T2, 32>(g, f, nfield, Z, tw_theta<T2>(tw), s); break;
-        case 16: anal_theta_kb<T2, 16>(g, f, nfield, Z, tw_theta<T2>(tw), s); break;
-        case 8: anal_theta_kb<T2, 8>(g, f, nfield, Z, tw_theta<T2>(tw), s); break;
-        default: anal_theta_kb<T2, 4>(g, f, nfield, Z, tw_theta<T2>(tw), s); break;
-    }
-    check_launch("anal_theta");
-}
-
-// N/4 threads divide the radix-4 (and the radix-2, radix-3) stages of a
-// length-N column exactly; at least one warp, at most 256.
-static unsigned zpass_threads(const Geo& g) {
-    const int t = (g.nzp / 4 + 31) / 32 * 32;
-    return (unsigned)std::max(32, std::min(256, t));
-}
-
-template <class T2>
-void launch_zpass(const Geo& g, int mode, const T2* Y, T2* Z, const ZScales& sc_in, const Twiddles& tw, cudaStream_t s) {
-    ZScales sc = sc_in;
-    for (int i = 0; i < 9; ++i) {
-        sc.fh0[i] = (float)sc.h0[i];
-        sc.fhk[i] = (float)sc.hk[i];
-    }
-    for (int i = 0; i < 6; ++i) {
-        sc.fo0[i] = (float)sc.o0[i];
-        sc.fok[i] = (float)sc.ok[i];
-    }
-    const int ld = mode == ZFWD ? 3 : 5;
-    const size_t sm = (size_t)(2 * g.nzp * ld + g.nzp) * sizeof(T2);
-    dim3 grid(g.nt, g.nr);
-    if (mode == ZFWD) {
-        static bool attr = false;
-        if (!attr) {
-            cudaFuncSetAttribute(k_zpass<T2, ZFWD>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-            attr = true;
-        }
-        k_zpass<T2, ZFWD><<<grid, zpass_threads(g), sm, s>>>(g, Y, Z, sc, tw_z<T2>(tw));
-    } else {
-        static bool attr = false;
-        if (!attr) {
-            cudaFuncSetAttribute(k_zpass<T2, ZADJ>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-            attr = true;
-        }
-        k_zpass<T2, ZADJ><<<grid, zpass_threads(g), sm, s>>>(g, Y, Z, sc, tw_z<T2>(tw));
-    }
-    check_launch("zpass");
-}
-
-template void launch_synth_theta<double2>(const Geo&, const FieldPtrs&, int, double2*, const Twiddles&, cudaStream_t);
-template void launch_synth_theta<float2>(const Geo&, const FieldPtrs&, int, float2*, const Twiddles&, cudaStream_t);
-template void launch_anal_theta<double2>(const Geo&, const FieldPtrs&, int, const double2*, const Twiddles&,
-                                         cudaStream_t);
-template void launch_anal_theta<float2>(const Geo&, const FieldPtrs&, int, const float2*, const Twiddles&,
-                                        cudaStream_t);
-template void launch_zpass<double2>(const Geo&, int, const double2*, double2*, const ZScales&, const Twiddles&,
-                                    cudaStream_t);
-template void launch_zpass<float2>(const Geo&, int, const float2*, float2*, const ZScales&, const Twiddles&,
-                                   cudaStream_t);
 
 // trans (zero_row0 == 1) selects the transposed coefficient layout
 static void launch_band_solve(const Geo& g, const double* fac, double2* X, const double2* add, int helm, int zero_row0,
