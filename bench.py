@@ -321,13 +321,11 @@ def roofline(L, res, mixed, peaks, pk_src):
 SERVE_RES = ((32, 32, 64, 10.0), (48, 48, 128, 25.0), (64, 64, 256, 50.0))
 
 
-def serving_report(L, nreq=24, mean_gap=0.05, seed=0, budget=40 << 30, max_active=8):
-    """Poisson arrivals of gradient requests at mixed resolution and physics.
-
-    Parameters per request (seeded): resolution from SERVE_RES, Re in [1500, 3000],
-    A in [0.5, 1.5], Wo in [4, 18], E0 = 10^U(-7,-4), dt = 0.005 and 10-50 steps
+def _serving_requests(L, nreq, seed, arrivals):
+    """Seeded requests: resolution from SERVE_RES, Re in [1500, 3000], A in
+    [0.5, 1.5], Wo in [4, 18], E0 = 10^U(-7,-4), dt = 0.005 and 10-50 steps
     (horizons shortened from 1-10 time units so the stream stays within a
-    minute), mixed precision, 8 checkpoint slots; admission by an HBM budget."""
+    minute), mixed precision, 8 checkpoint slots."""
     import numpy as np
     from paper_2509_10103_gb300 import serving, synth
     rng = np.random.default_rng(seed)
@@ -337,16 +335,34 @@ def serving_report(L, nreq=24, mean_gap=0.05, seed=0, budget=40 << 30, max_activ
         r = np.array(ctx.pnop_grid_points())
         ctx.close()
         fields[(nr, nth, nz)] = synth.random_field(r, nth // 2 - 1, nz // 2 - 1, lz, seed=seed + nr)
-    reqs, t = [], 0.0
+    reqs = []
     for i in range(nreq):
         nr, nth, nz, lz = SERVE_RES[int(rng.integers(len(SERVE_RES)))]
-        t += float(rng.exponential(mean_gap))
         n = int(rng.integers(10, 51))
         reqs.append(serving.Request(rid=i, nr=nr, ntheta=nth, nz=nz, Lz=lz, Re=float(rng.uniform(1500, 3000)),
                                     Wo=float(rng.uniform(4, 18)), A=float(rng.uniform(0.5, 1.5)),
                                     tau0=float(rng.uniform(0, 100)), E0=float(10 ** rng.uniform(-7, -4)),
                                     horizon=n * 0.005, dt=0.005, u0=fields[(nr, nth, nz)], precision=L.PNOP_MIXED,
-                                    snaps=8, arrival=t))
+                                    snaps=8, arrival=float(arrivals[i])))
+    return reqs
+
+
+def serving_report(L, nreq=256, probe=48, load=0.7, seed=0, budget=40 << 30, max_active=8):
+    """Capacity probe, then a Poisson stream at `load` x that capacity.
+
+    The probe submits `probe` requests at once and takes completed / wall as
+    the capacity (requests/s).  The stream then offers `nreq` requests with
+    exponential gaps of mean 1 / (load x capacity) and reports p50/p99
+    latency (arrival to result on the host) and throughput."""
+    import numpy as np
+    from paper_2509_10103_gb300 import serving
+    reqs = _serving_requests(L, probe, seed + 1, np.zeros(probe))
+    t0 = time.perf_counter()
+    res, _ = serving.serve_stream(reqs, hbm_budget=budget, max_active=max_active)
+    cap = sum(r.error is None for r in res) / (time.perf_counter() - t0)
+    rate = load * cap
+    gaps = np.random.default_rng(seed + 2).exponential(1.0 / rate, nreq)
+    reqs = _serving_requests(L, nreq, seed, np.cumsum(gaps))
     t0 = time.perf_counter()
     res, srv = serving.serve_stream(reqs, hbm_budget=budget, max_active=max_active)
     wall = time.perf_counter() - t0
@@ -355,11 +371,12 @@ def serving_report(L, nreq=24, mean_gap=0.05, seed=0, budget=40 << 30, max_activ
     lat = serving.latency_summary(res)
     return {"requests": nreq, "completed": len(ok), "errors": [r.error for r in res if r.error][:3],
             "resolutions": [f"{a}x{b}x{c}" for a, b, c, _ in SERVE_RES], "precision": "mixed",
-            "offered_rate_req_s": 1.0 / mean_gap, "throughput_req_s": len(ok) / wall,
+            "capacity_req_s": cap, "capacity_probe": f"{probe} requests submitted at once",
+            "offered_load": load, "offered_rate_req_s": rate, "throughput_req_s": len(ok) / wall,
             "steps_per_s": steps / wall, "p50_latency_s": lat["p50_s"], "p99_latency_s": lat["p99_s"],
             "mean_latency_s": lat.get("mean_s"), "peak_active": srv.peak_active,
             "peak_admitted_gb": srv.peak_bytes / 2 ** 30, "hbm_budget_gb": budget / 2 ** 30, "wall_s": wall,
-            "horizons": "10-50 steps of dt=0.005", "arrivals": f"Poisson, mean gap {mean_gap} s"}
+            "horizons": "10-50 steps of dt=0.005", "arrivals": f"Poisson at {load} x measured capacity"}
 
 
 # ------------------------------------------------------------------ CPU oracle (baseline / reference arm)

@@ -6,6 +6,7 @@
 #include "kernels.hpp"
 
 #include <algorithm>
+#include <utility>
 
 namespace pnop {
 
@@ -258,6 +259,343 @@ __global__ void k_anal_theta(Geo g, FieldPtrs f, const T2* __restrict__ Z, const
     }
 }
 
+// ------------------------------------------------------------------ two-pass register FFT
+// A length N = N1 N2 transform as N2 DFTs of length N1 on stride-N2
+// subsequences, a twiddle W_N^{n2 k1}, and N1 DFTs of length N2 on
+// contiguous runs (Cooley-Tukey with one shared-memory exchange).  Each DFT
+// runs in the registers of one thread, fully unrolled, with its internal
+// twiddles folded to compile-time constants.  The inverse transforms below
+// take the spectrum in natural order and leave physical index k1 + N1 k2 in
+// slot k2 + N2 k1; the forward transforms take that slot order back to a
+// natural-order spectrum.  The physical-space work in between is pointwise,
+// so the permutation never has to be undone.
+
+// cos and sin of 2 pi e / L evaluated by the compiler: e is reduced to a
+// quadrant with integer arithmetic, the remaining angle x in [0, pi/2) goes
+// through the Taylor series of sin and cos (16 terms, below 1e-17 there).
+namespace ct {
+constexpr double kTwoPi = 6.283185307179586476925286766559;
+__host__ __device__ constexpr double tsin(double x) {
+    double t = x, s = x;
+    for (int i = 1; i < 16; ++i) {
+        t *= -x * x / ((2.0 * i) * (2.0 * i + 1.0));
+        s += t;
+    }
+    return s;
+}
+__host__ __device__ constexpr double tcos(double x) {
+    double t = 1.0, s = 1.0;
+    for (int i = 1; i < 16; ++i) {
+        t *= -x * x / ((2.0 * i - 1.0) * (2.0 * i));
+        s += t;
+    }
+    return s;
+}
+__host__ __device__ constexpr double cos2pi(long e, long L) {
+    const long n = ((e % L) + L) % L, q = 4 * n / L;
+    const double x = kTwoPi * (double)(4 * n - q * L) / (4.0 * (double)L);
+    return q == 0 ? tcos(x) : q == 1 ? -tsin(x) : q == 2 ? -tcos(x) : tsin(x);
+}
+__host__ __device__ constexpr double sin2pi(long e, long L) {
+    const long n = ((e % L) + L) % L, q = 4 * n / L;
+    const double x = kTwoPi * (double)(4 * n - q * L) / (4.0 * (double)L);
+    return q == 0 ? tsin(x) : q == 1 ? tcos(x) : q == 2 ? -tsin(x) : -tcos(x);
+}
+}  // namespace ct
+
+// x e^{SIGN 2 pi i E / L} for a compile-time exponent E
+template <class T2, int L, int SIGN, int E>
+__device__ __forceinline__ T2 twc(T2 x) {
+    using T = typename RealOf<T2>::T;
+    constexpr int e = ((E % L) + L) % L;
+    if constexpr (e == 0) {
+        return x;
+    } else if constexpr (2 * e == L) {
+        return mk<T2>(-x.x, -x.y);
+    } else if constexpr (4 * e == L) {  // SIGN i
+        return SIGN > 0 ? mk<T2>(-x.y, x.x) : mk<T2>(x.y, -x.x);
+    } else if constexpr (4 * e == 3 * L) {  // -SIGN i
+        return SIGN > 0 ? mk<T2>(x.y, -x.x) : mk<T2>(-x.y, x.x);
+    } else {
+        constexpr T c = (T)ct::cos2pi(e, L);
+        constexpr T sn = (T)(SIGN * ct::sin2pi(e, L));
+        return mk<T2>(c * x.x - sn * x.y, c * x.y + sn * x.x);
+    }
+}
+
+// x e^{SIGN 2 pi i e / N} for a run-time exponent 0 <= e < N, from the table
+// tw[n] = e^{-2 pi i n / N}
+template <class T2, int SIGN>
+__device__ __forceinline__ T2 twr(T2 x, const T2* tw, int e) {
+    T2 w = tw[e];
+    if (SIGN > 0) w.y = -w.y;
+    return cmul(x, w);
+}
+
+template <class T2, int L, int SIGN, int R, int Q, int... I>
+__device__ __forceinline__ void rtwiddle(T2 (&s)[R][Q], std::integer_sequence<int, I...>) {
+    ((s[I / Q][I % Q] = twc<T2, L, SIGN, (I / Q) * (I % Q)>(s[I / Q][I % Q])), ...);
+}
+
+// In-register DFT X[k] = sum_n v[n] e^{SIGN 2 pi i n k / L}, L = 2^a 3^b:
+// radix-2/3/4 butterflies at the leaves, mixed-radix Cooley-Tukey above them
+// (n = a + R b, k = kb + Q ka).
+template <class T2, int L, int SIGN>
+__device__ __forceinline__ void rdft(T2 (&v)[L]) {
+    using T = typename RealOf<T2>::T;
+    if constexpr (L == 1) {
+    } else if constexpr (L == 2) {
+        const T2 a = v[0], b = v[1];
+        v[0] = cadd(a, b);
+        v[1] = csub(a, b);
+    } else if constexpr (L == 3) {
+        constexpr T h = (T)(SIGN * 0.86602540378443864676);  // SIGN sqrt(3)/2
+        const T2 t1 = cadd(v[1], v[2]);
+        const T2 t2 = mk<T2>(v[0].x - (T)0.5 * t1.x, v[0].y - (T)0.5 * t1.y);
+        const T2 t3 = imul(csub(v[1], v[2]), h);
+        v[0] = cadd(v[0], t1);
+        v[1] = cadd(t2, t3);
+        v[2] = csub(t2, t3);
+    } else if constexpr (L == 4) {
+        const T2 s02 = cadd(v[0], v[2]), d02 = csub(v[0], v[2]);
+        const T2 s13 = cadd(v[1], v[3]), d13 = csub(v[1], v[3]);
+        const T2 id = imul(d13, (T)SIGN);
+        v[0] = cadd(s02, s13);
+        v[2] = csub(s02, s13);
+        v[1] = cadd(d02, id);
+        v[3] = csub(d02, id);
+    } else {
+        constexpr int R = (L % 4 == 0) ? 4 : ((L % 2 == 0) ? 2 : 3);
+        constexpr int Q = L / R;
+        T2 s[R][Q];
+#pragma unroll
+        for (int a = 0; a < R; ++a)
+#pragma unroll
+            for (int b = 0; b < Q; ++b) s[a][b] = v[a + R * b];
+#pragma unroll
+        for (int a = 0; a < R; ++a) rdft<T2, Q, SIGN>(s[a]);
+        rtwiddle<T2, L, SIGN, R, Q>(s, std::make_integer_sequence<int, R * Q>{});
+#pragma unroll
+        for (int b = 0; b < Q; ++b) {
+            T2 t[R];
+#pragma unroll
+            for (int a = 0; a < R; ++a) t[a] = s[a][b];
+            rdft<T2, R, SIGN>(t);
+#pragma unroll
+            for (int a = 0; a < R; ++a) v[b + Q * a] = t[a];
+        }
+    }
+}
+
+// theta synthesis, two-pass: block (k tile of KB, j, field), KB * N1 or
+// KB * N2 tasks per pass.  Slot s of the output rows holds theta index
+// (s / N2) + N1 (s % N2).
+template <class T2, int KB, int N1, int N2>
+__global__ void __launch_bounds__(128) k_synth2(Geo g, FieldPtrs f, T2* __restrict__ Y, const T2* __restrict__ twg) {
+    constexpr int N = N1 * N2;
+    extern __shared__ __align__(16) unsigned char smem[];
+    T2* buf = reinterpret_cast<T2*>(smem);  // [N][KB]
+    T2* tw = buf + N * KB;                   // [N]
+    const int k0 = blockIdx.x * KB, j = blockIdx.y, fi = blockIdx.z;
+    for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = twg[i];
+    __syncthreads();
+    const double2* src = f.in[fi] + (size_t)j * g.nm * g.nk;
+    for (int t = threadIdx.x; t < KB * N2; t += blockDim.x) {
+        const int kk = t % KB, n2 = t / KB, k = k0 + kk;
+        T2 v[N1];
+#pragma unroll
+        for (int n1 = 0; n1 < N1; ++n1) {
+            const int n = n2 + N2 * n1;  // m mod N; zero padding for |m| > M
+            const int m = n <= g.M ? n : n - N;
+            v[n1] = (k < g.nk && m >= -g.M) ? from_d<T2>(src[(size_t)(m + g.M) * g.nk + k]) : mk<T2>(0, 0);
+        }
+        rdft<T2, N1, +1>(v);
+#pragma unroll
+        for (int k1 = 0; k1 < N1; ++k1) buf[(n2 + N2 * k1) * KB + kk] = twr<T2, +1>(v[k1], tw, n2 * k1);
+    }
+    __syncthreads();
+    T2* dst = Y + ((size_t)(fi * g.nr + j) * N) * g.nk;
+    for (int t = threadIdx.x; t < KB * N1; t += blockDim.x) {
+        const int kk = t % KB, k1 = t / KB, k = k0 + kk;
+        T2 v[N2];
+#pragma unroll
+        for (int n2 = 0; n2 < N2; ++n2) v[n2] = buf[(N2 * k1 + n2) * KB + kk];
+        rdft<T2, N2, +1>(v);
+        if (k < g.nk) {
+#pragma unroll
+            for (int k2 = 0; k2 < N2; ++k2) dst[(size_t)(N2 * k1 + k2) * g.nk + k] = v[k2];
+        }
+    }
+}
+
+// theta analysis, two-pass (input rows in the slot order of k_synth2), with
+// the k = 0 plane projected onto Hermitian symmetry.
+template <class T2, int KB, int N1, int N2>
+__global__ void __launch_bounds__(128) k_anal2(Geo g, FieldPtrs f, const T2* __restrict__ Z,
+                                               const T2* __restrict__ twg) {
+    constexpr int N = N1 * N2;
+    extern __shared__ __align__(16) unsigned char smem[];
+    T2* buf = reinterpret_cast<T2*>(smem);  // [N][KB]
+    T2* tw = buf + N * KB;                   // [N]
+    const int k0 = blockIdx.x * KB, j = blockIdx.y, fi = blockIdx.z;
+    for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = twg[i];
+    __syncthreads();
+    const T2* src = Z + ((size_t)(fi * g.nr + j) * N) * g.nk;
+    for (int t = threadIdx.x; t < KB * N1; t += blockDim.x) {
+        const int kk = t % KB, k1 = t / KB, k = k0 + kk;
+        T2 v[N2];
+#pragma unroll
+        for (int n2 = 0; n2 < N2; ++n2) v[n2] = k < g.nk ? src[(size_t)(N2 * k1 + n2) * g.nk + k] : mk<T2>(0, 0);
+        rdft<T2, N2, -1>(v);
+#pragma unroll
+        for (int m2 = 0; m2 < N2; ++m2) buf[(N2 * k1 + m2) * KB + kk] = twr<T2, -1>(v[m2], tw, k1 * m2);
+    }
+    __syncthreads();
+    double2* dst = f.out[fi] + (size_t)j * g.nm * g.nk;
+    for (int t = threadIdx.x; t < KB * N2; t += blockDim.x) {
+        const int kk = t % KB, m2 = t / KB, k = k0 + kk;
+        T2 v[N1];
+#pragma unroll
+        for (int k1 = 0; k1 < N1; ++k1) v[k1] = buf[(m2 + N2 * k1) * KB + kk];
+        rdft<T2, N1, -1>(v);
+#pragma unroll
+        for (int m1 = 0; m1 < N1; ++m1) {
+            const int n = m2 + N2 * m1;
+            const int m = n <= g.M ? n : n - N;
+            if (k < g.nk && m >= -g.M) {
+                if (k == 0) buf[n * KB + kk] = v[m1];
+                else dst[(size_t)(m + g.M) * g.nk + k] = to_d(v[m1]);
+            }
+        }
+    }
+    if (k0 == 0) {  // block-uniform
+        __syncthreads();
+        for (int im = threadIdx.x; im < g.nm; im += blockDim.x) {
+            const int m = im - g.M;
+            const double2 v = to_d(buf[(m < 0 ? m + N : m) * KB]);
+            const double2 vm = to_d(buf[(m > 0 ? N - m : -m) * KB]);
+            dst[(size_t)im * g.nk] = make_double2(0.5 * (v.x + vm.x), 0.5 * (v.y - vm.y));
+        }
+    }
+}
+
+// z pass, two-pass FFTs in place in padded shared-memory columns (one gap
+// after every run of N2 slots keeps both access patterns free of bank
+// conflicts).  Same contract as k_zpass.
+template <class T2, int MODE, int N1, int N2>
+__global__ void k_zpass2(Geo g, const T2* __restrict__ Y, T2* __restrict__ Z, ZScales sc, const T2* __restrict__ twg) {
+    using T = typename RealOf<T2>::T;
+    constexpr int N = N1 * N2, NP = N + N1;
+    constexpr int NIN = MODE == ZFWD ? 6 : 9;
+    constexpr int NPI = (NIN + 1) / 2;
+    constexpr int NOUT = MODE == ZFWD ? 3 : 6;
+    constexpr int NPO = (NOUT + 1) / 2;
+    extern __shared__ __align__(16) unsigned char smem[];
+    T2* col = reinterpret_cast<T2*>(smem);  // [NPI][NP]
+    T2* tw = col + NPI * NP;                 // [N]
+    const int K = g.K, nk = g.nk, a = blockIdx.x, j = blockIdx.y;
+    auto at = [](int s) { return s + s / N2; };
+    for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = twg[i];
+    __syncthreads();
+    // inverse, strided pass: Hermitian-extended spectra, two real fields per column
+    for (int t = threadIdx.x; t < NPI * N2; t += blockDim.x) {
+        const int p = t / N2, n2 = t % N2;
+        const int f1 = 2 * p, f2 = 2 * p + 1;
+        const T2* y1 = Y + ((size_t)(f1 * g.nr + j) * g.nt + a) * nk;
+        const bool has2 = f2 < NIN;
+        const T2* y2 = Y + ((size_t)((has2 ? f2 : f1) * g.nr + j) * g.nt + a) * nk;
+        const T h01 = zs<T>(sc.h0, sc.fh0, f1), hk1 = zs<T>(sc.hk, sc.fhk, f1);
+        const T h02 = has2 ? zs<T>(sc.h0, sc.fh0, f2) : (T)0, hk2 = has2 ? zs<T>(sc.hk, sc.fhk, f2) : (T)0;
+        T2 v[N1];
+#pragma unroll
+        for (int n1 = 0; n1 < N1; ++n1) {
+            const int n = n2 + N2 * n1;
+            int k = -1;
+            bool neg = false;
+            if (n <= K) k = n;
+            else if (n >= N - K) { k = N - n; neg = true; }
+            T2 q = mk<T2>(0, 0);
+            if (k >= 0) {
+                const T2 a1 = y1[k], a2 = has2 ? y2[k] : mk<T2>(0, 0);
+                const T2 h1 = k == 0 ? mk<T2>(h01 * a1.x, 0) : mk<T2>(hk1 * a1.x, hk1 * a1.y);
+                const T2 h2 = k == 0 ? mk<T2>(h02 * a2.x, 0) : mk<T2>(hk2 * a2.x, hk2 * a2.y);
+                q = !neg ? mk<T2>(h1.x - h2.y, h1.y + h2.x)    // H1 + i H2
+                         : mk<T2>(h1.x + h2.y, -h1.y + h2.x);  // conj(H1) + i conj(H2)
+            }
+            v[n1] = q;
+        }
+        rdft<T2, N1, +1>(v);
+#pragma unroll
+        for (int k1 = 0; k1 < N1; ++k1) col[p * NP + at(n2 + N2 * k1)] = twr<T2, +1>(v[k1], tw, n2 * k1);
+    }
+    __syncthreads();
+    // inverse, contiguous pass: physical values
+    for (int t = threadIdx.x; t < NPI * N1; t += blockDim.x) {
+        const int p = t / N1, k1 = t % N1;
+        T2 v[N2];
+#pragma unroll
+        for (int n2 = 0; n2 < N2; ++n2) v[n2] = col[p * NP + at(N2 * k1 + n2)];
+        rdft<T2, N2, +1>(v);
+#pragma unroll
+        for (int k2 = 0; k2 < N2; ++k2) col[p * NP + at(N2 * k1 + k2)] = v[k2];
+    }
+    __syncthreads();
+    // pointwise products, in place (each slot read and written by one thread)
+    for (int s = threadIdx.x; s < N; s += blockDim.x) {
+        const int o = at(s);
+        const T2 c0 = col[o], c1 = col[NP + o], c2 = col[2 * NP + o];
+        const T ur = c0.x, ut = c0.y, uz = c1.x;
+        const T wr = c1.y, wt = c2.x, wz = c2.y;
+        if (MODE == ZFWD) {
+            col[o] = mk<T2>(ut * wz - uz * wt, uz * wr - ur * wz);
+            col[NP + o] = mk<T2>(ur * wt - ut * wr, 0);
+        } else {
+            const T2 c3 = col[3 * NP + o], c4 = col[4 * NP + o];
+            const T gr = c3.x, gt = c3.y, gz = c4.x;
+            col[o] = mk<T2>(wt * gz - wz * gt, wz * gr - wr * gz);           // w x g
+            col[NP + o] = mk<T2>(wr * gt - wt * gr, gt * uz - gz * ut);      // (w x g)_z, (g x u)_r
+            col[2 * NP + o] = mk<T2>(gz * ur - gr * uz, gr * ut - gt * ur);  // (g x u)_theta, (g x u)_z
+        }
+    }
+    __syncthreads();
+    // forward, contiguous pass
+    for (int t = threadIdx.x; t < NPO * N1; t += blockDim.x) {
+        const int p = t / N1, k1 = t % N1;
+        T2 v[N2];
+#pragma unroll
+        for (int k2 = 0; k2 < N2; ++k2) v[k2] = col[p * NP + at(N2 * k1 + k2)];
+        rdft<T2, N2, -1>(v);
+#pragma unroll
+        for (int m2 = 0; m2 < N2; ++m2) col[p * NP + at(N2 * k1 + m2)] = twr<T2, -1>(v[m2], tw, k1 * m2);
+    }
+    __syncthreads();
+    // forward, strided pass: natural-order spectra
+    for (int t = threadIdx.x; t < NPO * N2; t += blockDim.x) {
+        const int p = t / N2, m2 = t % N2;
+        T2 v[N1];
+#pragma unroll
+        for (int k1 = 0; k1 < N1; ++k1) v[k1] = col[p * NP + at(m2 + N2 * k1)];
+        rdft<T2, N1, -1>(v);
+#pragma unroll
+        for (int m1 = 0; m1 < N1; ++m1) col[p * NP + at(m2 + N2 * m1)] = v[m1];
+    }
+    __syncthreads();
+    // separate the two real products of each column, truncate to k <= K, scale
+    for (int p = 0; p < NPO; ++p)
+        for (int k = threadIdx.x; k < nk; k += blockDim.x) {
+            const T2 P = col[p * NP + at(k)];
+            const T2 Pm = col[p * NP + at((N - k) % N)];
+            const int o1 = 2 * p, o2 = 2 * p + 1;
+            const T s1 = k == 0 ? zs<T>(sc.o0, sc.fo0, o1) : zs<T>(sc.ok, sc.fok, o1);
+            Z[((size_t)(o1 * g.nr + j) * g.nt + a) * nk + k] = mk<T2>((T)0.5 * (P.x + Pm.x) * s1, (T)0.5 * (P.y - Pm.y) * s1);
+            if (o2 < NOUT) {
+                const T s2 = k == 0 ? zs<T>(sc.o0, sc.fo0, o2) : zs<T>(sc.ok, sc.fok, o2);
+                Z[((size_t)(o2 * g.nr + j) * g.nt + a) * nk + k] =
+                    mk<T2>((T)0.5 * (P.y + Pm.y) * s2, (T)-0.5 * (P.x - Pm.x) * s2);
+            }
+        }
+}
+
 // ------------------------------------------------------------------ launchers
 template <class T2> static const T2* tw_theta(const Twiddles& t);
 template <> const double2* tw_theta<double2>(const Twiddles& t) { return t.th_d; }
@@ -296,8 +634,40 @@ static void anal_theta_kb(const Geo& g, const FieldPtrs& f, int nfield, const T2
     k_anal_theta<T2, KB><<<grid, 256, sm, s>>>(g, f, Z, tw);
 }
 
+// Two-pass register kernels serve the lengths with a split N = N1 N2 below;
+// the Stockham kernels serve every other 2^a 3^b length.  The theta kernels
+// take KB k-columns per block.
+template <class T2, int KB, int N1, int N2>
+static void synth2(const Geo& g, const FieldPtrs& f, int nfield, T2* Y, const T2* tw, cudaStream_t s) {
+    const size_t sm = (size_t)(N1 * N2 * KB + N1 * N2) * sizeof(T2);
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_synth2<T2, KB, N1, N2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        attr = true;
+    }
+    dim3 grid((g.nk + KB - 1) / KB, g.nr, nfield);
+    k_synth2<T2, KB, N1, N2><<<grid, 128, sm, s>>>(g, f, Y, tw);
+}
+template <class T2, int KB, int N1, int N2>
+static void anal2(const Geo& g, const FieldPtrs& f, int nfield, const T2* Z, const T2* tw, cudaStream_t s) {
+    const size_t sm = (size_t)(N1 * N2 * KB + N1 * N2) * sizeof(T2);
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_anal2<T2, KB, N1, N2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        attr = true;
+    }
+    dim3 grid((g.nk + KB - 1) / KB, g.nr, nfield);
+    k_anal2<T2, KB, N1, N2><<<grid, 128, sm, s>>>(g, f, Z, tw);
+}
+
 template <class T2>
 void launch_synth_theta(const Geo& g, const FieldPtrs& f, int nfield, T2* Y, const Twiddles& tw, cudaStream_t s) {
+    switch (g.nt) {
+        case 96: synth2<T2, 32, 8, 12>(g, f, nfield, Y, tw_theta<T2>(tw), s); check_launch("synth_theta"); return;
+        case 192: synth2<T2, 32, 16, 12>(g, f, nfield, Y, tw_theta<T2>(tw), s); check_launch("synth_theta"); return;
+        case 384: synth2<T2, 16, 16, 24>(g, f, nfield, Y, tw_theta<T2>(tw), s); check_launch("synth_theta"); return;
+        default: break;
+    }
     switch (theta_kb<T2>(g)) {
         case 32: synth_theta_kb<T2, 32>(g, f, nfield, Y, tw_theta<T2>(tw), s); break;
         case 16: synth_theta_kb<T2, 16>(g, f, nfield, Y, tw_theta<T2>(tw), s); break;
@@ -309,6 +679,12 @@ void launch_synth_theta(const Geo& g, const FieldPtrs& f, int nfield, T2* Y, con
 
 template <class T2>
 void launch_anal_theta(const Geo& g, const FieldPtrs& f, int nfield, const T2* Z, const Twiddles& tw, cudaStream_t s) {
+    switch (g.nt) {
+        case 96: anal2<T2, 32, 8, 12>(g, f, nfield, Z, tw_theta<T2>(tw), s); check_launch("anal_theta"); return;
+        case 192: anal2<T2, 32, 16, 12>(g, f, nfield, Z, tw_theta<T2>(tw), s); check_launch("anal_theta"); return;
+        case 384: anal2<T2, 16, 16, 24>(g, f, nfield, Z, tw_theta<T2>(tw), s); check_launch("anal_theta"); return;
+        default: break;
+    }
     switch (theta_kb<T2>(g)) {
         case 32: anal_theta_kb<T2, 32>(g, f, nfield, Z, tw_theta<T2>(tw), s); break;
         case 16: anal_theta_kb<T2, 16>(g, f, nfield, Z, tw_theta<T2>(tw), s); break;
@@ -325,6 +701,27 @@ static unsigned zpass_threads(const Geo& g) {
     return (unsigned)std::max(32, std::min(256, t));
 }
 
+template <class T2, int MODE, int N1, int N2>
+static void zpass2(const Geo& g, const T2* Y, T2* Z, const ZScales& sc, const T2* tw, cudaStream_t s) {
+    constexpr int NPI = MODE == ZFWD ? 3 : 5;
+    const size_t sm = (size_t)(NPI * (N1 * N2 + N1) + N1 * N2) * sizeof(T2);
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_zpass2<T2, MODE, N1, N2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        attr = true;
+    }
+    k_zpass2<T2, MODE, N1, N2><<<dim3(g.nt, g.nr), zpass_threads(g), sm, s>>>(g, Y, Z, sc, tw);
+}
+template <class T2, int MODE>
+static bool zpass2_any(const Geo& g, const T2* Y, T2* Z, const ZScales& sc, const T2* tw, cudaStream_t s) {
+    switch (g.nzp) {
+        case 96: zpass2<T2, MODE, 8, 12>(g, Y, Z, sc, tw, s); return true;
+        case 192: zpass2<T2, MODE, 16, 12>(g, Y, Z, sc, tw, s); return true;
+        case 384: zpass2<T2, MODE, 16, 24>(g, Y, Z, sc, tw, s); return true;
+        default: return false;
+    }
+}
+
 template <class T2>
 void launch_zpass(const Geo& g, int mode, const T2* Y, T2* Z, const ZScales& sc_in, const Twiddles& tw, cudaStream_t s) {
     ZScales sc = sc_in;
@@ -335,6 +732,11 @@ void launch_zpass(const Geo& g, int mode, const T2* Y, T2* Z, const ZScales& sc_
     for (int i = 0; i < 6; ++i) {
         sc.fo0[i] = (float)sc.o0[i];
         sc.fok[i] = (float)sc.ok[i];
+    }
+    if (mode == ZFWD ? zpass2_any<T2, ZFWD>(g, Y, Z, sc, tw_z<T2>(tw), s)
+                     : zpass2_any<T2, ZADJ>(g, Y, Z, sc, tw_z<T2>(tw), s)) {
+        check_launch("zpass");
+        return;
     }
     const int ld = mode == ZFWD ? 3 : 5;
     const size_t sm = (size_t)(2 * g.nzp * ld + g.nzp) * sizeof(T2);

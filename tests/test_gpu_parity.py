@@ -81,6 +81,52 @@ def ragged(L):
     return Case(L, **RAGGED, Wo=5.6, A=0.85, tau0=3.0)
 
 
+# Lengths served by the two-pass register FFT kernels (N = N1 N2): theta and z
+# at 96 (8 x 12), z at 384 (16 x 24) with theta at 24 (Stockham), theta and z
+# at 192 (16 x 12).
+TWO_PASS = {
+    "tp96": dict(nr=10, M=31, K=31, Lz=9.0, Re=1800.0, dt=0.004),
+    "tp384": dict(nr=10, M=7, K=127, Lz=40.0, Re=1800.0, dt=0.004),
+    "tp192": dict(nr=10, M=63, K=63, Lz=20.0, Re=1800.0, dt=0.004),
+}
+
+
+@pytest.fixture(scope="module", params=sorted(TWO_PASS))
+def two_pass(L, request):
+    return Case(L, **TWO_PASS[request.param], Wo=6.0, A=0.9, tau0=0.5)
+
+
+@pytest.fixture(scope="module")
+def two_pass_mixed(L, two_pass):
+    prm = {k: getattr(two_pass.o.p, k) for k in ("nr", "M", "K", "Lz", "Re", "dt")}
+    c = Case(L, **prm, Wo=6.0, A=0.9, tau0=0.5, precision=1)
+    c.o = two_pass.o
+    return c
+
+
+def test_two_pass_transforms_nonlinear(two_pass, two_pass_mixed, L):
+    c = two_pass
+    u = c.field(21, 1e-2)
+    nb = c.field(22, 1.0)
+    t = c.tau0 + 0.41
+    ref = c.o.nonlinear(u, t)
+    refT = c.o.nonlinearT(u, t, nb)
+    for cc, tol in ((c, 1e-12), (two_pass_mixed, 1e-5)):
+        out = cc.zeros()
+        cc.ctx.pnop_apply(L.OP_NONLINEAR, dev(u), None, out, t)
+        assert rel(host(out), ref) < tol
+        cc.ctx.pnop_apply(L.OP_NONLINEAR_T, dev(u), dev(nb), out, t)
+        assert rel(host(out), refT) < tol
+
+
+def test_two_pass_forward_step(two_pass):
+    c = two_pass
+    u0 = c.field(23, 1e-2)
+    x = dev(u0)
+    c.ctx.pnop_step_forward(x, c.tau0, 1)
+    assert rel(host(x), c.o.forward(u0, c.tau0, 1)) < TOL
+
+
 def test_grid_points_match(small):
     np.testing.assert_allclose(small.ctx.pnop_grid_points(), small.o.r, rtol=0, atol=1e-15)
 
