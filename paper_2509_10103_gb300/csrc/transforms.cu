@@ -6,6 +6,7 @@
 #include "kernels.hpp"
 
 #include <algorithm>
+#include <type_traits>
 #include <utility>
 
 namespace pnop {
@@ -733,8 +734,13 @@ void launch_zpass(const Geo& g, int mode, const T2* Y, T2* Z, const ZScales& sc_
         sc.fo0[i] = (float)sc.o0[i];
         sc.fok[i] = (float)sc.ok[i];
     }
-    if (mode == ZFWD ? zpass2_any<T2, ZFWD>(g, Y, Z, sc, tw_z<T2>(tw), s)
-                     : zpass2_any<T2, ZADJ>(g, Y, Z, sc, tw_z<T2>(tw), s)) {
+    // FP64 z passes stay on the Stockham kernel: they are bound by the FP64
+    // pipe, where the register kernel's lower occupancy measured slower.
+    bool done = false;
+    if constexpr (std::is_same<T2, float2>::value)
+        done = mode == ZFWD ? zpass2_any<T2, ZFWD>(g, Y, Z, sc, tw_z<T2>(tw), s)
+                            : zpass2_any<T2, ZADJ>(g, Y, Z, sc, tw_z<T2>(tw), s);
+    if (done) {
         check_launch("zpass");
         return;
     }
