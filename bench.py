@@ -199,8 +199,10 @@ def aggregate_value(horizon_steps, steps, ws, ms_max):
 
 
 # ------------------------------------------------------------------ GPU arm
-def time_gradient(L, torch, precision, steps, warmup, H, snaps, ws, rank, sampler=None):
+def time_gradient(L, torch, precision, steps, warmup, H, snaps, ws, rank, sampler=None, host_slots=0):
     ctx = L.Context(NR, NTHETA, NZ, LZ, RE, DT, WO, AMP, TAU0, precision, snaps)
+    if host_slots:
+        ctx.pnop_set_host_tier(host_slots, -1.0)  # io ratio measured on this device
     import numpy as np
     r = np.array(ctx.pnop_grid_points())
     u0 = torch.from_numpy(make_u0(r)).to("cuda")
@@ -229,9 +231,10 @@ def time_gradient(L, torch, precision, steps, warmup, H, snaps, ws, rank, sample
     ms = e0.elapsed_time(e1)
     tprof = ctx.pnop_profile_read()
     adv, nadj, stores = ctx.pnop_gradient_stats()
+    host = ctx.pnop_host_tier_stats() if host_slots else None
     ctx.close()
     return {"ms": ms, "gain": gain, "warm_profile": prof, "timed_profile": tprof, "dominant": dom,
-            "advances": adv, "adjoint_steps": nadj, "stores": stores, "clocks": clocks}
+            "advances": adv, "adjoint_steps": nadj, "stores": stores, "clocks": clocks, "host": host}
 
 
 def time_single_steps(L, torch, precision, reps=20):
@@ -268,6 +271,14 @@ def budget_sweep(L, torch, precision, H, budgets=(10, 57, 100), steps=2):
         res = time_gradient(L, torch, precision, steps, 1, H, s, 1, 0, None)
         out[str(s)] = {"steps_per_s": H * steps / (res["ms"] / 1e3), "advances": res["advances"]}
     return out
+
+
+def host_tier_report(L, torch, precision, H, snaps=10, steps=2):
+    """The same gradient with `snaps` HBM checkpoint slots plus up to H - 1 pinned
+    host slots (two-level schedule, Eq. 2.21, io ratio measured)."""
+    res = time_gradient(L, torch, precision, steps, 1, H, snaps, 1, 0, None, host_slots=H - 1)
+    return {"hbm_slots": snaps, "max_host_slots": H - 1, "steps_per_s": H * steps / (res["ms"] / 1e3),
+            "advances": res["advances"], **res["host"]}
 
 
 def time_e2e(L, torch, precision, steps, warmup, H, snaps):
@@ -482,6 +493,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the single-step timings and the budget sweep (profiling runs)")
     ap.add_argument("--precision", default="both", choices=["both", "mixed", "fp64"],
                     help="which path(s) to time; 'fp64' reports the FP64 path as the main line")
     args = ap.parse_args()
@@ -540,10 +553,11 @@ def main():
         "gpu_launches": launches,
         "clocks": mix["clocks"],
     }
-    if ws == 1:
+    if ws == 1 and not args.no_extras:
         out["single_step"] = {"mixed": time_single_steps(L, torch, L.PNOP_MIXED),
                               "fp64": time_single_steps(L, torch, L.PNOP_FP64)}
         out["budget_sweep_mixed"] = budget_sweep(L, torch, L.PNOP_MIXED, H)
+        out["host_tier_mixed"] = host_tier_report(L, torch, L.PNOP_MIXED, H)
     if not args.no_serving and ws == 1:
         out["serving"] = serving_report(L)
     if not args.no_cpu_baseline and ws == 1:

@@ -147,6 +147,82 @@ int pnop_gradient_host(pnop_ctx* ctx, const double* u0_host, double E0, double h
  * Any pointer may be NULL. */
 int pnop_gradient_stats(const pnop_ctx* ctx, long long* advances, long long* adjoint_steps, long long* stores);
 
+/* Second checkpoint level in pinned host memory (the file level of the
+ * two-level schedule, Section 2.5, with Grace memory over the host link in
+ * place of disc).  With max_host_slots > 0, each later gradient sweep of N
+ * steps with s HBM slots picks the number nf <= max_host_slots of host
+ * checkpoints that minimises the recovery time of Eq. 2.21,
+ *   nf * T_io + (forward steps) * T_step,
+ * counting the forward steps of the schedule exactly (forward phase to the
+ * last of nf + 1 near-equal intervals, then each interval's binomial schedule,
+ * Eq. 2.18); nf = 0 keeps the single-level schedule.  io_ratio = T_io/T_step
+ * for one store plus one load of a field; io_ratio < 0 measures it now on
+ * this device.  Host slots (one field each, pinned) are allocated on demand
+ * and kept until pnop_destroy; their copies run on a copy stream and overlap
+ * the steps (the next load is prefetched).  The gradient is bitwise the same
+ * with or without the host level.  max_host_slots = 0 turns the level off.
+ * Errors: PNOP_ERR_INVALID_ARG for negative or absurd slot counts,
+ * PNOP_ERR_OOM when pinned host memory cannot be allocated. */
+int pnop_set_host_tier(pnop_ctx* ctx, long long max_host_slots, double io_ratio);
+
+/* Host level of the last gradient sweep: host checkpoints used, host stores
+ * and loads, and the io_ratio in force.  Any pointer may be NULL. */
+int pnop_host_tier_stats(const pnop_ctx* ctx, int* host_checkpoints, long long* host_stores, long long* host_loads,
+                         double* io_ratio);
+
+/* Host only: the schedule pnop_set_host_tier would choose for nsteps steps
+ * with snaps HBM slots, at most max_host_slots host checkpoints and the given
+ * io_ratio (>= 0): host checkpoints in *host_checkpoints and forward steps of
+ * the sweep (terminal step included) in *advances. */
+int pnop_two_level_counts(long long nsteps, int snaps, long long max_host_slots, double io_ratio,
+                          int* host_checkpoints, long long* advances);
+
+/* Energy of every Fourier mode of the device field u (Eq. 2.1 weights),
+ * split into the cross-section part (u_r, u_theta) in spectrum[0][m + M][k]
+ * and the axial part (u_z) in spectrum[1][m + M][k]; spectrum is a host array
+ * of 2 (2M+1)(K+1) doubles and sums to pnop_energy(u).  Sections 2.4 and 3 use
+ * it: the resolution measures e_M, e_K (the energy of |m| = M, respectively
+ * k = K, over 2 E0), the component growths G_z, G_(r,theta), and per-mode
+ * energy traces. */
+int pnop_mode_energy(pnop_ctx* ctx, const void* u, double* spectrum);
+
+/* Self-check of the FP64 <-> FP32 conversions the mixed-precision transforms
+ * perform on the integer pipes: runs them against the hardware conversions on
+ * n pseudo-random bit patterns plus edge cases on the current device and
+ * writes the number of disagreements (NaN payloads aside) to *mismatches. */
+int pnop_check_conversions(long long n, long long* mismatches);
+
+/* Counters and result of pnop_optimise. */
+typedef struct {
+    int iterations;    /* accepted updates */
+    int gradients;     /* reverse sweeps (one per accepted point, the start included) */
+    int forward_evals; /* forward sweeps of the line search (the start included) */
+    int converged;     /* 1 when R < tol ended the loop, or the gradient is parallel to u0 */
+    double gain;       /* G = E(T)/E0 of the returned u0 */
+    double rel_change; /* last R = |G^(s+1) - G^s| / G^(s+1) */
+} pnop_opt_stats;
+
+/* Adjoint-looping optimisation of the initial perturbation (Section 2.3):
+ * u0 (device, in/out) is projected onto admissible fields (PNOP_OP_PROJECT)
+ * and scaled to energy E0, then repeatedly replaced by
+ * (1 + lambda alpha) u0 - alpha u_dagger with u_dagger = -P grad (the paper's
+ * adjoint field at tau0; grad as returned by pnop_gradient, projected so that
+ * the iterates stay admissible), lambda the root lambda_+ of the energy
+ * constraint (Eq. 2.14) and alpha found by backtracking: alpha_max of
+ * Eq. 2.15 first, halved while the gain G does not grow.  A trial whose sweep
+ * is not finite counts as a step that did not raise G.  The loop ends when an
+ * accepted update changes G by a relative R < tol (the paper uses 1e-8), when
+ * the line search cannot raise G before R drops below tol, when the gradient
+ * is parallel to u0 (to rounding), or after max_iter accepted updates.  u0
+ * holds the last accepted perturbation.  gain_history (host, may be NULL)
+ * receives max_iter + 1 doubles: G of the start and after each accepted
+ * update (entries beyond stats->iterations are left unchanged).  stats (host)
+ * may be NULL.  Each trial point costs one checkpointed forward sweep;
+ * accepted points add the reverse sweep.  Uses two more device fields of the
+ * context and the projection factors on first call. */
+int pnop_optimise(pnop_ctx* ctx, void* u0, double E0, double horizon, int max_iter, double tol,
+                  double* gain_history, pnop_opt_stats* stats);
+
 /* Operators of the step, applied to device fields (for testing and for
  * users who compose their own schemes; layout as above, all FP64 in/out):
  *   PNOP_OP_CURL       out = curl a                              (Eq. 2.5)
@@ -159,6 +235,11 @@ int pnop_gradient_stats(const pnop_ctx* ctx, long long* advances, long long* adj
  *   PNOP_OP_NONLINEAR_T out = (dN/da at a, t)^T b
  *   PNOP_OP_STAGE_T_U  out = (dS/da)^T a      (b unused)
  *   PNOP_OP_STAGE_T_F  out = (dS/db)^T a      (b unused)
+ *   PNOP_OP_PROJECT    out = P a: orthogonal projection, in the energy inner
+ *                      product, onto admissible fields (Hermitian k = 0 plane,
+ *                      zero at the wall, discrete divergence zero at every
+ *                      r_j, mean mode with u_r = 0 and zero flux; the
+ *                      constraints of Section 2.2)  (b unused)
  * Transposes act on Euclidean cotangents of the stored real and imaginary
  * parts.  out must not alias a or b. */
 enum {
@@ -167,7 +248,8 @@ enum {
     PNOP_OP_STAGE = 2,
     PNOP_OP_NONLINEAR_T = 3,
     PNOP_OP_STAGE_T_U = 4,
-    PNOP_OP_STAGE_T_F = 5
+    PNOP_OP_STAGE_T_F = 5,
+    PNOP_OP_PROJECT = 6
 };
 int pnop_apply(pnop_ctx* ctx, int op, const void* a, const void* b, void* out, double t);
 

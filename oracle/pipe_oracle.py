@@ -301,7 +301,7 @@ class Oracle:
         fh = np.einsum('jmb,bk->jmk', x, np.conj(self.Ez)) * self.ck[None, None, :]
         return self._herm(fh)
 
-    # ---------------- nonlinear forcing (Eq. 2.5, rotational form) ----------------
+    # ---------------- nonlinear forcing (Eq. 2.5: quadratic term rotational, base-flow terms advective) ----------------
     def base(self, t: float):
         p = self.p
         if not p.base:
@@ -310,18 +310,19 @@ class Oracle:
         return womersley(self.r, t, p.Re, p.Wo, p.A)
 
     def nonlinear(self, u: np.ndarray, t: float) -> np.ndarray:
-        """N = u x w + (U e_z) x w + u x (-dU/dr e_theta), w = curl u."""
+        """N = u x w - U du/dz - u_r dU/dr e_z, w = curl u: the quadratic term in
+        rotational form, the base-flow terms in advective form (they differ from
+        (U e_z) x w + u x (-dU/dr e_theta) by grad(U u_z), which the discrete
+        projection does not remove exactly)."""
         w = self.curl(u)
         up = np.stack([self.synth(c) for c in u])
         wp = np.stack([self.synth(c) for c in w])
         cr = np.cross(up, wp, axis=0)
         n = np.stack([self.analysis(c) for c in cr])
         U, dU = self.base(t)
-        U = U[:, None, None]
-        dU = dU[:, None, None]
-        n[0] += -U * w[1] + dU * u[2]
-        n[1] += U * w[0]
-        n[2] += -dU * u[0]
+        a = -1j * self.kz[None, None, :] * U[:, None, None]  # -U d/dz
+        n += a[None] * u
+        n[2] += -dU[:, None, None] * u[0]
         return n
 
     def nonlinearT(self, u: np.ndarray, t: float, nb: np.ndarray) -> np.ndarray:
@@ -335,12 +336,9 @@ class Oracle:
         ub = np.stack([self.synthT(c) for c in upb])
         wb = np.stack([self.synthT(c) for c in wpb])
         U, dU = self.base(t)
-        U = U[:, None, None]
-        dU = dU[:, None, None]
-        wb[1] += -U * nb[0]
-        ub[2] += dU * nb[0]
-        wb[0] += U * nb[1]
-        ub[0] += -dU * nb[2]
+        a = -1j * self.kz[None, None, :] * U[:, None, None]
+        ub += np.conj(a)[None] * nb          # y = a x  ->  x_bar = conj(a) y_bar
+        ub[0] += -dU[:, None, None] * nb[2]
         return ub + self.curlT(wb)
 
     # ---------------- linear stage map S(u, F) (Section 2.4) ----------------
@@ -482,11 +480,9 @@ class Oracle:
         p = self.p
 
         def forcing(v, tt):
-            full = np.zeros((3, p.nr, 2 * p.M + 1, p.K + 1), np.complex128)
-            full[:, :, m + p.M, k] = v
-            w = self.curl(full)[:, :, m + p.M, k]
             U, dU = self.base(tt)
-            return np.stack([-U * w[1] + dU * v[2], U * w[0], -dU * v[0]])
+            a = -1j * self.kz[k] * U
+            return np.stack([a * v[0], a * v[1], a * v[2] - dU * v[0]])
 
         Su, SF = self.mode_maps(m, k)
         n0 = forcing(um, t)
@@ -500,6 +496,15 @@ class Oracle:
         imr = 1j * self.m[None, :, None] / self.r[:, None, None]
         ikz = 1j * self.kz[None, None, :]
         return self.apply_d1(ur, 1) + ur / self.r[:, None, None] + imr * ut + ikz * uz
+
+    def mode_energy(self, u: np.ndarray) -> np.ndarray:
+        """Energy of each stored mode (m, k >= 0) with the weights of Eq. 2.1, split
+        into the cross-section part (u_r, u_theta) [0] and the axial part (u_z) [1];
+        shape (2, 2M+1, K+1), summing to `energy`."""
+        w = 0.5 * self.What
+        a = np.sum(w * (np.abs(u[0]) ** 2 + np.abs(u[1]) ** 2), axis=0)
+        b = np.sum(w * np.abs(u[2]) ** 2, axis=0)
+        return np.stack([a, b])
 
     def scale_to(self, u: np.ndarray, E0: float) -> np.ndarray:
         return u * math.sqrt(E0 / self.energy(u))

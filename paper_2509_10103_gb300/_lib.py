@@ -19,12 +19,16 @@ PNOP_FP64 = 0
 PNOP_MIXED = 1
 KCLASSES = ("synth_theta", "zpass_fwd", "zpass_adj", "anal_theta", "spectral", "radial_band", "radial_solve",
             "elementwise", "reduce")
-OP_CURL, OP_NONLINEAR, OP_STAGE, OP_NONLINEAR_T, OP_STAGE_T_U, OP_STAGE_T_F = range(6)
+OP_CURL, OP_NONLINEAR, OP_STAGE, OP_NONLINEAR_T, OP_STAGE_T_U, OP_STAGE_T_F, OP_PROJECT = range(7)
 
 EXPORTS = (
     "pnop_create", "pnop_set_base_flow", "pnop_dims", "pnop_grid_points", "pnop_step_forward",
-    "pnop_step_adjoint", "pnop_gradient", "pnop_gradient_forward", "pnop_gradient_backward", "pnop_gradient_host", "pnop_gradient_stats", "pnop_energy",
-    "pnop_inner", "pnop_apply", "pnop_set_timeout", "pnop_sync", "pnop_profile", "pnop_profile_read", "pnop_revolve_counts", "pnop_context_bytes", "pnop_energy_noalloc", "pnop_last_error", "pnop_error_string", "pnop_destroy",
+    "pnop_step_adjoint", "pnop_gradient", "pnop_gradient_forward", "pnop_gradient_backward", "pnop_gradient_host",
+    "pnop_gradient_stats", "pnop_optimise", "pnop_set_host_tier", "pnop_host_tier_stats", "pnop_two_level_counts",
+    "pnop_check_conversions", "pnop_mode_energy",
+    "pnop_energy", "pnop_inner", "pnop_apply", "pnop_set_timeout",
+    "pnop_sync", "pnop_profile", "pnop_profile_read", "pnop_revolve_counts", "pnop_context_bytes",
+    "pnop_energy_noalloc", "pnop_last_error", "pnop_error_string", "pnop_destroy",
 )
 
 
@@ -35,6 +39,11 @@ class pnop_grid(ctypes.Structure):
 class pnop_params(ctypes.Structure):
     _fields_ = [("Re", c_double), ("Wo", c_double), ("A", c_double), ("dt", c_double), ("tau0", c_double),
                 ("precision", c_int), ("snap_budget", c_int), ("hbm_budget", c_size_t)]
+
+
+class pnop_opt_stats(ctypes.Structure):
+    _fields_ = [("iterations", c_int), ("gradients", c_int), ("forward_evals", c_int), ("converged", c_int),
+                ("gain", c_double), ("rel_change", c_double)]
 
 
 def _load():
@@ -53,6 +62,15 @@ def _load():
         "pnop_gradient_backward": (c_int, [c_void_p, c_double, c_int, c_void_p]),
         "pnop_gradient_host": (c_int, [c_void_p, c_void_p, c_double, c_double, c_void_p, POINTER(c_double)]),
         "pnop_gradient_stats": (c_int, [c_void_p, POINTER(c_longlong), POINTER(c_longlong), POINTER(c_longlong)]),
+        "pnop_optimise": (c_int, [c_void_p, c_void_p, c_double, c_double, c_int, c_double, POINTER(c_double),
+                                  POINTER(pnop_opt_stats)]),
+        "pnop_set_host_tier": (c_int, [c_void_p, c_longlong, c_double]),
+        "pnop_check_conversions": (c_int, [c_longlong, POINTER(c_longlong)]),
+        "pnop_mode_energy": (c_int, [c_void_p, c_void_p, POINTER(c_double)]),
+        "pnop_host_tier_stats": (c_int, [c_void_p, POINTER(c_int), POINTER(c_longlong), POINTER(c_longlong),
+                                         POINTER(c_double)]),
+        "pnop_two_level_counts": (c_int, [c_longlong, c_int, c_longlong, c_double, POINTER(c_int),
+                                          POINTER(c_longlong)]),
         "pnop_energy": (c_int, [c_void_p, c_void_p, POINTER(c_double)]),
         "pnop_inner": (c_int, [c_void_p, c_void_p, c_void_p, POINTER(c_double)]),
         "pnop_apply": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_void_p, c_double]),
@@ -100,6 +118,24 @@ def pnop_revolve_counts(nsteps: int, snaps: int):
     if rc != PNOP_OK:
         raise PnopError(rc, "revolve_counts")
     return a.value, s.value
+
+
+def pnop_check_conversions(n):
+    """Disagreements of the integer-pipe FP64<->FP32 conversions with the hardware ones."""
+    bad = c_longlong()
+    rc = lib.pnop_check_conversions(n, byref(bad))
+    if rc != PNOP_OK:
+        raise PnopError(rc, "check_conversions")
+    return bad.value
+
+
+def pnop_two_level_counts(nsteps, snaps, max_host_slots, io_ratio):
+    """(host checkpoints, forward steps) of the two-level schedule (host only)."""
+    nf, adv = c_int(), c_longlong()
+    rc = lib.pnop_two_level_counts(nsteps, snaps, max_host_slots, io_ratio, byref(nf), byref(adv))
+    if rc != PNOP_OK:
+        raise PnopError(rc, "two_level_counts")
+    return nf.value, adv.value
 
 
 def pnop_context_bytes(nr, ntheta, nz, Lz, precision, snaps):
@@ -202,6 +238,32 @@ class Context:
         a, b, c = c_longlong(), c_longlong(), c_longlong()
         self._check(lib.pnop_gradient_stats(self._h, byref(a), byref(b), byref(c)), "gradient_stats")
         return a.value, b.value, c.value
+
+    def pnop_optimise(self, u0, E0, horizon, max_iter, tol=1e-8):
+        """Adjoint looping on u0 (device, in/out); returns (stats dict, gain history list)."""
+        hist = (c_double * (max_iter + 1))()
+        st = pnop_opt_stats()
+        self._check(lib.pnop_optimise(self._h, c_void_p(_ptr(u0)), E0, horizon, max_iter, tol, hist, byref(st)),
+                    "optimise")
+        stats = {name: getattr(st, name) for name, _ in pnop_opt_stats._fields_}
+        return stats, list(hist[: st.iterations + 1])
+
+    def pnop_mode_energy(self, u):
+        """Per-mode energy, shape (2, 2M+1, K+1): cross-section and axial parts."""
+        import numpy as np
+        nm, nk = self.shape[2], self.shape[3]
+        out = np.zeros((2, nm, nk), np.float64)
+        self._check(lib.pnop_mode_energy(self._h, c_void_p(_ptr(u)), out.ctypes.data_as(POINTER(c_double))),
+                    "mode_energy")
+        return out
+
+    def pnop_set_host_tier(self, max_host_slots, io_ratio=-1.0):
+        self._check(lib.pnop_set_host_tier(self._h, max_host_slots, io_ratio), "set_host_tier")
+
+    def pnop_host_tier_stats(self):
+        nf, st, ld, r = c_int(), c_longlong(), c_longlong(), c_double()
+        self._check(lib.pnop_host_tier_stats(self._h, byref(nf), byref(st), byref(ld), byref(r)), "host_tier_stats")
+        return {"host_checkpoints": nf.value, "host_stores": st.value, "host_loads": ld.value, "io_ratio": r.value}
 
     def pnop_apply(self, op, a, b, out, t=0.0):
         bp = c_void_p(_ptr(b)) if b is not None else c_void_p(0)

@@ -111,39 +111,42 @@ __device__ __forceinline__ void base_at(const Geo& g, int j, double c, double s,
     dU = -2.0 * r + (b.x * c - b.y * s);
 }
 
-// N += (U e_z) x w + u x (-dU/dr e_theta)
-__global__ void k_base_add(Geo g, const double2* __restrict__ u, const double2* __restrict__ w, double2* __restrict__ N,
-                           double c, double s) {
+// N += -U du/dz - u_r dU/dr e_z: the base-flow terms in advective form.  The
+// rotational form (U e_z) x w + u x (-dU/dr e_theta) differs from it by
+// grad(U u_z), which the discrete pressure projection does not remove exactly;
+// the remainder couples u_z back into (u_r, u_theta) and makes k = 0 modes of
+// steady pipe flow grow at high Re.
+__global__ void k_base_add(Geo g, const double2* __restrict__ u, double2* __restrict__ N, double c, double s) {
     Idx d;
     if (!decode(g, d)) return;
     double U, dU;
     base_at(g, d.j, c, s, U, dU);
     const size_t o = sidx(g, d.j, d.im, d.k), S = d.S;
-    const double2 ur = u[o], uz = u[o + 2 * S], wr = w[o], wt = w[o + S];
+    const double a = d.k * g.kz0 * U;  // -U d/dz = -i a
+    const double2 ur = u[o], ut = u[o + S], uz = u[o + 2 * S];
     double2 x = N[o];
-    N[o] = make_double2(x.x - U * wt.x + dU * uz.x, x.y - U * wt.y + dU * uz.y);
+    N[o] = make_double2(x.x + a * ur.y, x.y - a * ur.x);
     x = N[o + S];
-    N[o + S] = make_double2(x.x + U * wr.x, x.y + U * wr.y);
+    N[o + S] = make_double2(x.x + a * ut.y, x.y - a * ut.x);
     x = N[o + 2 * S];
-    N[o + 2 * S] = make_double2(x.x - dU * ur.x, x.y - dU * ur.y);
+    N[o + 2 * S] = make_double2(x.x + a * uz.y - dU * ur.x, x.y - a * uz.x - dU * ur.y);
 }
 
-__global__ void k_baseT_acc(Geo g, const double2* __restrict__ nb, double2* __restrict__ ub, double2* __restrict__ wb,
-                            double c, double s) {
+// transpose (Euclidean cotangents): ub += conj(-i a) nb = i a nb; ub_r -= dU nb_z
+__global__ void k_baseT_acc(Geo g, const double2* __restrict__ nb, double2* __restrict__ ub, double c, double s) {
     Idx d;
     if (!decode(g, d)) return;
     double U, dU;
     base_at(g, d.j, c, s, U, dU);
     const size_t o = sidx(g, d.j, d.im, d.k), S = d.S;
+    const double a = d.k * g.kz0 * U;
     const double2 nr_ = nb[o], nt = nb[o + S], nz = nb[o + 2 * S];
-    double2 x = wb[o + S];
-    wb[o + S] = make_double2(x.x - U * nr_.x, x.y - U * nr_.y);
+    double2 x = ub[o];
+    ub[o] = make_double2(x.x - a * nr_.y - dU * nz.x, x.y + a * nr_.x - dU * nz.y);
+    x = ub[o + S];
+    ub[o + S] = make_double2(x.x - a * nt.y, x.y + a * nt.x);
     x = ub[o + 2 * S];
-    ub[o + 2 * S] = make_double2(x.x + dU * nr_.x, x.y + dU * nr_.y);
-    x = wb[o];
-    wb[o] = make_double2(x.x + U * nt.x, x.y + U * nt.y);
-    x = ub[o];
-    ub[o] = make_double2(x.x - dU * nz.x, x.y - dU * nz.y);
+    ub[o + 2 * S] = make_double2(x.x - a * nz.y, x.y + a * nz.x);
 }
 
 // ------------------------------------------------------------------ radial stage (forward)
@@ -555,6 +558,135 @@ __global__ void k_stageT_div(Geo g, const double2* __restrict__ z, double2* __re
     Fb[o + 2 * S] = make_double2(x.x - kz * zj.y, x.y + kz * zj.x);
 }
 
+// ------------------------------------------------------------------ admissible projection
+// Orthogonal projection onto admissible fields in the energy inner product:
+// Hermitian k = 0 plane, no slip, discrete divergence zero at every r_j, and
+// for the mean mode u_r = 0 with zero flux.  Per mode (m, k) != (0, 0):
+// y = C x (wall values removed), solve S z = y (S = C W^-1 C^H, real SPD,
+// banded Cholesky factors), x -= W^-1 C^H z.
+
+// u(m, 0) and u(-m, 0) <- their Hermitian average; one thread per (c, j, m >= 0)
+__global__ void k_proj_herm(Geo g, double2* __restrict__ u) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= 3 * g.nr * (g.M + 1)) return;
+    const int m = t % (g.M + 1), cj = t / (g.M + 1);
+    const size_t S = (size_t)g.nr * g.nm * g.nk;
+    const int c = cj / g.nr, j = cj % g.nr;
+    double2* a = u + c * S + sidx(g, j, g.M + m, 0);
+    double2* b = u + c * S + sidx(g, j, g.M - m, 0);
+    const double2 p = *a, q = *b;
+    const double2 h = make_double2(0.5 * (p.x + q.x), 0.5 * (p.y - q.y));
+    *a = h;
+    *b = make_double2(h.x, -h.y);
+}
+
+// y_j = sum_{c >= 1} D1[j][c] u_r[c] + u_r[j] / r_j + (i m / r_j) u_theta[j] + i k_z u_z[j]  (wall values excluded)
+__global__ void k_proj_div(Geo g, const double2* __restrict__ u, double2* __restrict__ y) {
+    Idx d;
+    if (!decode(g, d)) return;
+    const size_t o = sidx(g, d.j, d.im, d.k), S = d.S;
+    if (d.m == 0 && d.k == 0) {
+        y[o] = make_double2(0, 0);
+        return;
+    }
+    const double* B = g.D1 + ((size_t)par_idx(d.m + 1) * g.nr + d.j) * kB;
+    double2 acc = make_double2(0, 0);
+    for (int s = 0; s < kB; ++s) {
+        const int c = d.j - 4 + s;
+        if (c >= 1 && c < g.nr) acc = dfma(__ldg(B + s), u[sidx(g, c, d.im, d.k)], acc);
+    }
+    if (d.j >= 1) {
+        const double ir = g.invr[d.j], mr = d.m * ir, kz = d.k * g.kz0;
+        const double2 a = u[o], b = u[o + S], c = u[o + 2 * S];
+        acc.x += ir * a.x - mr * b.y - kz * c.y;
+        acc.y += ir * a.y + mr * b.x + kz * c.x;
+    }
+    y[o] = acc;
+}
+
+// S z = y in place per mode (one thread per mode and real/imaginary part); the
+// mean-mode threads store the W-weighted mean of u_z over j >= 1 in y(0, mean).
+__global__ void k_proj_solve(Geo g, const double* __restrict__ L, const double2* __restrict__ u,
+                             double2* __restrict__ y) {
+    constexpr int B = 12, W1 = B + 1;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= 2 * g.nm * g.nk) return;
+    const int part = t / (g.nm * g.nk), mode = t % (g.nm * g.nk);
+    const int im = mode / g.nk, k = mode % g.nk, m = im - g.M;
+    double* Y = reinterpret_cast<double*>(y) + part;
+    auto at = [&](int j) -> double& { return Y[2 * sidx(g, j, im, k)]; };
+    if (m == 0 && k == 0) {
+        const double* uz = reinterpret_cast<const double*>(u + 2 * (size_t)g.nr * g.nm * g.nk) + part;
+        double num = 0, den = 0;
+        for (int j = 1; j < g.nr; ++j) {
+            num += g.W[j] * uz[2 * sidx(g, j, im, k)];
+            den += g.W[j];
+        }
+        at(0) = num / den;
+        return;
+    }
+    const double* F = L + (((size_t)abs(m) * g.nk + k) * g.nr) * W1;
+    for (int j = 0; j < g.nr; ++j) {  // L w = y
+        double v = at(j);
+        for (int i = max(0, j - B); i < j; ++i) v -= F[j * W1 + (i - j + B)] * at(i);
+        at(j) = v * F[j * W1 + B];
+    }
+    for (int j = g.nr - 1; j >= 0; --j) {  // L^T z = w
+        double v = at(j);
+        for (int i = j + 1; i <= min(g.nr - 1, j + B); ++i) v -= F[i * W1 + (j - i + B)] * at(i);
+        at(j) = v * F[j * W1 + B];
+    }
+}
+
+// u -= W^-1 C^H z; wall values zero; mean mode: u_r = 0, u_z -= its weighted mean
+__global__ void k_proj_update(Geo g, double2* __restrict__ u, const double2* __restrict__ z) {
+    Idx d;
+    if (!decode(g, d)) return;
+    const size_t o = sidx(g, d.j, d.im, d.k), S = d.S;
+    if (d.j == 0) {
+        u[o] = u[o + S] = u[o + 2 * S] = make_double2(0, 0);
+        return;
+    }
+    if (d.m == 0 && d.k == 0) {
+        const double2 mu = z[sidx(g, 0, d.im, d.k)];
+        u[o] = make_double2(0, 0);
+        const double2 c = u[o + 2 * S];
+        u[o + 2 * S] = make_double2(c.x - mu.x, c.y - mu.y);
+        return;
+    }
+    const double ir = g.invr[d.j], mr = d.m * ir, kz = d.k * g.kz0, wi = 1.0 / g.W[d.j];
+    const double2 zj = z[o];
+    double2 dr = band_col(g, g.D1 + (size_t)par_idx(d.m + 1) * g.nr * kB, z, d.j, d.im, d.k);
+    dr.x += ir * zj.x;
+    dr.y += ir * zj.y;
+    const double2 a = u[o], b = u[o + S], c = u[o + 2 * S];
+    u[o] = make_double2(a.x - wi * dr.x, a.y - wi * dr.y);
+    u[o + S] = make_double2(b.x - wi * mr * zj.y, b.y + wi * mr * zj.x);
+    u[o + 2 * S] = make_double2(c.x - wi * kz * zj.y, c.y + wi * kz * zj.x);
+}
+
+// ------------------------------------------------------------------ diagnostics
+// Energy of every Fourier mode, split into the cross-section (u_r, u_theta)
+// and axial (u_z) parts: E[0][im][k], E[1][im][k] with the weights of the
+// energy inner product (2 pi Lz W_j c_k / 2).  One thread per mode, fixed
+// summation order.
+__global__ void k_mode_energy(Geo g, const double2* __restrict__ u, double* __restrict__ E) {
+    const int mode = blockIdx.x * blockDim.x + threadIdx.x;
+    if (mode >= g.nm * g.nk) return;
+    const int im = mode / g.nk, k = mode % g.nk;
+    const size_t S = (size_t)g.nr * g.nm * g.nk;
+    double a = 0, b = 0;
+    for (int j = 0; j < g.nr; ++j) {
+        const size_t o = sidx(g, j, im, k);
+        const double2 p = u[o], q = u[o + S], c = u[o + 2 * S];
+        a += g.W[j] * (p.x * p.x + p.y * p.y + q.x * q.x + q.y * q.y);
+        b += g.W[j] * (c.x * c.x + c.y * c.y);
+    }
+    const double w = 0.5 * g.ewt * (k == 0 ? 1.0 : 2.0);
+    E[mode] = w * a;
+    E[g.nm * g.nk + mode] = w * b;
+}
+
 // ------------------------------------------------------------------ elementwise / reductions
 __global__ void k_axpby(size_t n, double a, const double2* __restrict__ x, double b, const double2* __restrict__ y,
                         double2* __restrict__ out) {
@@ -630,12 +762,12 @@ void launch_curlT_acc(const Geo& g, const double2* wb, double2* ub, cudaStream_t
     k_curlT_acc<<<spec_grid(g), spec_bx(g), 0, s>>>(g, wb, ub);
     check_launch("curlT");
 }
-void launch_base_add(const Geo& g, const double2* u, const double2* w, double2* N, double c, double sn, cudaStream_t s) {
-    k_base_add<<<spec_grid(g), spec_bx(g), 0, s>>>(g, u, w, N, c, sn);
+void launch_base_add(const Geo& g, const double2* u, double2* N, double c, double sn, cudaStream_t s) {
+    k_base_add<<<spec_grid(g), spec_bx(g), 0, s>>>(g, u, N, c, sn);
     check_launch("base_add");
 }
-void launch_baseT_acc(const Geo& g, const double2* nb, double2* ub, double2* wb, double c, double sn, cudaStream_t s) {
-    k_baseT_acc<<<spec_grid(g), spec_bx(g), 0, s>>>(g, nb, ub, wb, c, sn);
+void launch_baseT_acc(const Geo& g, const double2* nb, double2* ub, double c, double sn, cudaStream_t s) {
+    k_baseT_acc<<<spec_grid(g), spec_bx(g), 0, s>>>(g, nb, ub, c, sn);
     check_launch("baseT");
 }
 
@@ -713,6 +845,19 @@ void launch_stageT_psolve(const Geo& g, double2* q, cudaStream_t s) {
 void launch_stageT_div(const Geo& g, const double2* z, double2* Fb, cudaStream_t s) {
     k_stageT_div<<<spec_grid(g), spec_bx(g), 0, s>>>(g, z, Fb);
     check_launch("stageT_div");
+}
+
+void launch_mode_energy(const Geo& g, const double2* u, double* E, cudaStream_t s) {
+    k_mode_energy<<<nblk((size_t)g.nm * g.nk, 128), 128, 0, s>>>(g, u, E);
+    check_launch("mode_energy");
+}
+
+void launch_project(const Geo& g, double2* u, double2* y, const double* L, cudaStream_t s) {
+    k_proj_herm<<<nblk((size_t)3 * g.nr * (g.M + 1), 128), 128, 0, s>>>(g, u);
+    k_proj_div<<<spec_grid(g), spec_bx(g), 0, s>>>(g, u, y);
+    k_proj_solve<<<nblk((size_t)2 * g.nm * g.nk, 64), 64, 0, s>>>(g, L, u, y);
+    k_proj_update<<<spec_grid(g), spec_bx(g), 0, s>>>(g, u, y);
+    check_launch("project");
 }
 
 void launch_axpby(size_t n, double a, const double2* x, double b, const double2* y, double2* out, cudaStream_t s) {

@@ -38,10 +38,16 @@ void ck(cudaError_t e, const char* what) {
 // Binomial schedule (Section 2.5) as a list of actions: advance n steps from
 // the state in a slot (into another slot, or into the scratch state when dst
 // is -1), or take the adjoint step of step n from a slot / the scratch state.
+// One entry of a checkpointing plan.  kAdv: advance n steps from snapshot
+// `slot` (result into snapshot `dst`, or left as the current state when
+// dst < 0); kAdj: the adjoint step `start` from snapshot `slot` (or the
+// current state); kStore / kLoad: copy snapshot `slot` to / from host slot
+// `host` (the second level of the two-level schedule).
+enum ActionKind { kAdv = 0, kAdj = 1, kStore = 2, kLoad = 3 };
 struct Action {
-    bool adjoint;
+    int kind;
     long long start, n;
-    int slot, dst;
+    int slot, dst, host;
 };
 
 bool smooth_size(int n) {
@@ -64,6 +70,8 @@ struct pnop_ctx {
     double *d_r = nullptr, *d_invr = nullptr, *d_W = nullptr, *d_D1 = nullptr, *d_Lb = nullptr;
     double *d_facH = nullptr, *d_facP = nullptr, *d_infl = nullptr, *d_fluxg = nullptr;
     double *d_facHT = nullptr, *d_facPT = nullptr;
+    double* d_projL = nullptr;  // admissible-projection factors, built on first use
+    double* d_spec = nullptr;   // per-mode energies [2][nm][nk]
     double2 *d_Uh = nullptr, *d_dUh = nullptr;
     pnop::Twiddles tw{};
     // workspace
@@ -85,6 +93,7 @@ struct pnop_ctx {
     cudaEvent_t ev_fork = nullptr, ev_bu = nullptr, ev_t = nullptr;
     double2 *tmpA = nullptr, *tmpB = nullptr, *lamA = nullptr, *lamB = nullptr;
     void* Y = nullptr;
+    void* Y2 = nullptr;  // theta synthesis of u and curl u kept from N(u) for N'(u)^T in the adjoint step
     void* Z = nullptr;
     double* partial = nullptr;
     double* dscal = nullptr;  // [4] device scalars
@@ -96,6 +105,17 @@ struct pnop_ctx {
     size_t plan_pos = 0;
     const double2* cur = nullptr;
     double2* uN = nullptr;
+    double2 *opt_g = nullptr, *opt_u = nullptr;  // adjoint looping: gradient, trial point
+    // second checkpoint level in pinned host memory (two-level schedule)
+    long long host_max = 0;            // host slots allowed (0: single level)
+    double host_ratio = 0;             // T_io / T_step of Eq. 2.21 (store + load of one field)
+    std::vector<void*> host;           // pinned host slots, allocated on demand
+    double2* hstage = nullptr;         // device staging field for the copies
+    cudaStream_t copy = nullptr;       // copy stream (host traffic overlaps the steps)
+    cudaEvent_t ev_copy = nullptr, ev_staged = nullptr;
+    int pref_host = -1;                // host slot prefetched into hstage (-1: none)
+    int st_nf = 0;
+    long long st_hstore = 0, st_hload = 0;
     bool pending = false;
     int st_slots = 0;
     double timeout_s = 0;  // host limit on waits for device work (0: none)
@@ -323,6 +343,17 @@ void stageT(pnop_ctx* c, const double2* ubn, double2* ub, int acc, double2* Fb) 
     if (Fb) stageT_proj(c, Fb, c->q, c->stream);
 }
 
+// u <- P u, the energy-orthogonal projection onto admissible fields (scratch q)
+void project(pnop_ctx* c, double2* u) {
+    if (!c->d_projL) {
+        std::vector<double> L;
+        std::string err;
+        if (!pnop::build_projection(c->h, L, err)) throw Status(PNOP_ERR_UNSUPPORTED, err);
+        c->d_projL = c->upload(L);
+    }
+    run(c, PNOP_K_RADIAL_SOLVE, 4, nmodes(c), [&] { pnop::launch_project(c->geo, u, c->q, c->d_projL, c->stream); });
+}
+
 void axpby(pnop_ctx* c, double a, const double2* x, double b, const double2* y, double2* out) {
     const size_t n = 3 * c->S();
     run(c, PNOP_K_ELEMENTWISE, 1, (double)n, [&] { pnop::launch_axpby(n, a, x, b, y, out, c->stream); });
@@ -334,26 +365,37 @@ void inner_dev(pnop_ctx* c, const double2* a, const double2* b, double* dst) {
     run(c, PNOP_K_REDUCE, 2, 3.0 * c->S(), [&] { pnop::launch_inner(c->geo, a, b, c->partial, dst, c->stream); });
 }
 
-// theta synthesis / z pass / theta analysis in the context's transform precision
-void transforms(pnop_ctx* c, const pnop::FieldPtrs& f, int nin, int nout, int zmode, const pnop::ZScales& sc) {
+// theta synthesis / z pass / theta analysis in the context's transform
+// precision, through the physical scratch Y.  Fields [0, cached) are already
+// synthesised in Y and are not redone.
+void transforms(pnop_ctx* c, const pnop::FieldPtrs& f, int nin, int nout, int zmode, const pnop::ZScales& sc, void* Y,
+                int cached) {
     const Geo& g = c->geo;
     cudaStream_t s = c->stream;
     const double cols = (double)g.nr * g.nk, rows = (double)g.nr * g.nt;
     const int zk = zmode == pnop::ZFWD ? PNOP_K_ZPASS_FWD : PNOP_K_ZPASS_ADJ;
+    pnop::FieldPtrs fs = f;
+    for (int i = 0; i + cached < nin; ++i) fs.in[i] = f.in[cached + i];
+    const int ns = nin - cached;
+    const size_t plane = (size_t)g.nr * g.nt * g.nk;
     if (mixed(c)) {
-        run(c, PNOP_K_SYNTH_THETA, 1, nin * cols, [&] { pnop::launch_synth_theta<float2>(g, f, nin, (float2*)c->Y, c->tw, s); });
-        run(c, zk, 1, rows, [&] { pnop::launch_zpass<float2>(g, zmode, (const float2*)c->Y, (float2*)c->Z, sc, c->tw, s); });
+        float2* Yf = (float2*)Y;
+        run(c, PNOP_K_SYNTH_THETA, 1, ns * cols, [&] { pnop::launch_synth_theta<float2>(g, fs, ns, Yf + cached * plane, c->tw, s); });
+        run(c, zk, 1, rows, [&] { pnop::launch_zpass<float2>(g, zmode, Yf, (float2*)c->Z, sc, c->tw, s); });
         run(c, PNOP_K_ANAL_THETA, 1, nout * cols, [&] { pnop::launch_anal_theta<float2>(g, f, nout, (const float2*)c->Z, c->tw, s); });
     } else {
-        run(c, PNOP_K_SYNTH_THETA, 1, nin * cols, [&] { pnop::launch_synth_theta<double2>(g, f, nin, (double2*)c->Y, c->tw, s); });
-        run(c, zk, 1, rows, [&] { pnop::launch_zpass<double2>(g, zmode, (const double2*)c->Y, (double2*)c->Z, sc, c->tw, s); });
+        double2* Yd = (double2*)Y;
+        run(c, PNOP_K_SYNTH_THETA, 1, ns * cols, [&] { pnop::launch_synth_theta<double2>(g, fs, ns, Yd + cached * plane, c->tw, s); });
+        run(c, zk, 1, rows, [&] { pnop::launch_zpass<double2>(g, zmode, Yd, (double2*)c->Z, sc, c->tw, s); });
         run(c, PNOP_K_ANAL_THETA, 1, nout * cols, [&] { pnop::launch_anal_theta<double2>(g, f, nout, (const double2*)c->Z, c->tw, s); });
     }
 }
 
 // ------------------------------------------------------------------ nonlinear term
-// N = P[I(u) x I(w)] + (U e_z) x w + u x (-dU/dr e_theta), w = curl u  (Eq. 2.5)
-void nonlinear(pnop_ctx* c, const double2* u, double t, double2* N) {
+// N = P[I(u) x I(w)] - U du/dz - u_r dU/dr e_z, w = curl u  (Eq. 2.5; base-flow
+// terms in advective form)
+// The physical u and w are left in Y (fields 0..5).
+void nonlinear(pnop_ctx* c, const double2* u, double t, double2* N, void* Y) {
     const Geo& g = c->geo;
     const size_t S = c->S();
     cudaStream_t s = c->stream;
@@ -368,17 +410,18 @@ void nonlinear(pnop_ctx* c, const double2* u, double t, double2* N) {
     const double inv_n = 1.0 / ((double)g.nt * g.nzp);
     for (int i = 0; i < 6; ++i) sc.h0[i] = sc.hk[i] = 1.0;
     for (int i = 0; i < 3; ++i) sc.o0[i] = sc.ok[i] = inv_n;
-    transforms(c, f, 6, 3, pnop::ZFWD, sc);
+    transforms(c, f, 6, 3, pnop::ZFWD, sc, Y, 0);
     const double ph = c->h.omega * t;
-    run(c, PNOP_K_SPECTRAL, 1, flops::base * S, [&] { pnop::launch_base_add(g, u, c->omega, N, std::cos(ph), std::sin(ph), s); });
+    run(c, PNOP_K_SPECTRAL, 1, flops::base * S, [&] { pnop::launch_base_add(g, u, N, std::cos(ph), std::sin(ph), s); });
 }
 
-// ub = (dN/du at u)^T nb  (Euclidean cotangents)
-void nonlinearT(pnop_ctx* c, const double2* u, double t, const double2* nb, double2* ub) {
+// ub = (dN/du at u)^T nb  (Euclidean cotangents).  With cached, Y already
+// holds the physical u and curl u of this u (fields 0..5, left by nonlinear).
+void nonlinearT(pnop_ctx* c, const double2* u, double t, const double2* nb, double2* ub, void* Y, bool cached) {
     const Geo& g = c->geo;
     const size_t S = c->S();
     cudaStream_t s = c->stream;
-    run(c, PNOP_K_SPECTRAL, 1, flops::curl * S, [&] { pnop::launch_curl(g, u, c->omega, s); });
+    if (!cached) run(c, PNOP_K_SPECTRAL, 1, flops::curl * S, [&] { pnop::launch_curl(g, u, c->omega, s); });
     pnop::FieldPtrs f{};
     for (int i = 0; i < 3; ++i) {
         f.in[i] = u + i * S;
@@ -400,9 +443,9 @@ void nonlinearT(pnop_ctx* c, const double2* u, double t, const double2* nb, doub
         sc.o0[i] = 1.0;
         sc.ok[i] = 2.0;
     }
-    transforms(c, f, 9, 6, pnop::ZADJ, sc);
+    transforms(c, f, 9, 6, pnop::ZADJ, sc, Y, cached ? 6 : 0);
     const double ph = c->h.omega * t;
-    run(c, PNOP_K_SPECTRAL, 1, flops::base * S, [&] { pnop::launch_baseT_acc(g, nb, ub, c->wb, std::cos(ph), std::sin(ph), s); });
+    run(c, PNOP_K_SPECTRAL, 1, flops::base * S, [&] { pnop::launch_baseT_acc(g, nb, ub, std::cos(ph), std::sin(ph), s); });
     run(c, PNOP_K_SPECTRAL, 1, flops::curlT * S, [&] { pnop::launch_curlT_acc(g, c->wb, ub, s); });
 }
 
@@ -414,9 +457,9 @@ void fwd_step(pnop_ctx* c, const double2* u, double2* out, double t) {
     fork_side(c);
     stage_bu(c, u, c->RB, c->side);
     ck(cudaEventRecord(c->ev_bu, c->side), "record");
-    nonlinear(c, u, t, c->N0);
+    nonlinear(c, u, t, c->N0, c->Y);
     stage(c, c->RB, c->N0, c->us, nullptr, c->ev_bu);
-    nonlinear(c, c->us, t + c->h.ph.dt, c->N1);
+    nonlinear(c, c->us, t + c->h.ph.dt, c->N1, c->Y);
     axpby(c, 0.5, c->N1, -0.5, c->N0, c->N1);
     stage(c, nullptr, c->N1, out, c->us, nullptr);
 }
@@ -426,9 +469,10 @@ void fwd_step(pnop_ctx* c, const double2* u, double2* out, double t) {
 //   Fb = S_F^H lin, ub* = N*'^T (Fb/2),
 //   ubar = S_u^H (lin + ub*) + N0'^T S_F^H (lin/2 + ub*).
 // S_u^H and S_F^H share their front part (Rl for lin, R for ub*), so the
-// transposed viscous matvec runs once, on Rl + R (added by the second solve).  B u and everything that
-// depends on lin alone (Rl, S_F^H lin) run on the side stream while the
-// predictor is re-run on the context stream.
+// transposed viscous matvec runs once, on Rl + R (added by the second solve).
+// B u and everything that depends on lin alone (Rl, S_F^H lin) run on the
+// side stream while the predictor is re-run on the context stream.  N(u) and
+// N'(u)^T share the physical u and curl u (scratch Y2).
 void adj_step(pnop_ctx* c, const double2* u, double t, const double2* lin, double2* lout) {
     const Geo& g = c->geo;
     fork_side(c);
@@ -440,15 +484,15 @@ void adj_step(pnop_ctx* c, const double2* u, double t, const double2* lin, doubl
         c->side);
     stageT_proj(c, c->Nb, c->q2, c->side);  // Nb = S_F^H lin / 2
     ck(cudaEventRecord(c->ev_t, c->side), "record");
-    nonlinear(c, u, t, c->N0);
+    nonlinear(c, u, t, c->N0, c->Y2);  // physical u, curl u stay in Y2 for N'(u)^T below
     stage(c, c->RB, c->N0, c->us, nullptr, c->ev_bu);
     join_side(c, c->ev_t);
-    nonlinearT(c, c->us, t + c->h.ph.dt, c->Nb, c->ubs);
+    nonlinearT(c, c->us, t + c->h.ph.dt, c->Nb, c->ubs, c->Y, false);
     stageT_front(c, c->ubs, c->R, c->stream, c->Rl);  // R = front(ub*) + front(lin)
     run(c, PNOP_K_RADIAL_BAND, 1, (flops::trhs_u + flops::trhs_f) * c->S(),
         [&] { pnop::launch_stageT_rhs(g, c->R, c->Rl, 1.0, -0.5, c->ua, 0, c->Nb, c->stream); });
     stageT_proj(c, c->Nb, c->q, c->stream);  // Nb = S_F^H (lin/2 + ub*)
-    nonlinearT(c, u, t, c->Nb, c->ubs);
+    nonlinearT(c, u, t, c->Nb, c->ubs, c->Y2, true);
     axpby(c, 1.0, c->ua, 1.0, c->ubs, lout);
 }
 
@@ -477,31 +521,147 @@ const double2* advance(pnop_ctx* c, const double2* src, long long start, long lo
 void plan_reverse(std::vector<Action>& P, long long start, long long l, int slot, int s) {
     if (l <= 0) return;
     if (l == 1) {
-        P.push_back({true, start, 1, slot, 0});
+        P.push_back({kAdj, start, 1, slot, 0, -1});
         return;
     }
     if (s == 1) {
         for (long long i = l - 1; i >= 0; --i) {
-            if (i > 0) P.push_back({false, start, i, slot, -1});
-            P.push_back({true, start + i, 1, i > 0 ? -1 : slot, 0});
+            if (i > 0) P.push_back({kAdv, start, i, slot, -1, -1});
+            P.push_back({kAdj, start + i, 1, i > 0 ? -1 : slot, 0, -1});
         }
         return;
     }
     const int r = pnop::revolve_repetitions(l, s);
     long long m = std::max<long long>(1, std::max(pnop::binom_beta(s, r - 2), l - pnop::binom_beta(s - 1, r)));
     m = std::min(m, l - 1);
-    P.push_back({false, start, m, slot, slot + 1});
+    P.push_back({kAdv, start, m, slot, slot + 1, -1});
     plan_reverse(P, start + m, l - m, slot + 1, s - 1);
     plan_reverse(P, start, m, slot, s);
 }
 
+// Two-level schedule (Section 2.5): nf >= 1 host checkpoints hold the starts
+// b_0 = 0, ..., b_{nf-1} of the first nf of nf + 1 near-equal intervals
+// (b_i = floor(i N / (nf + 1))); the last interval starts in snapshot 0.  The
+// forward phase stores u0, advances interval by interval storing each start,
+// then runs the binomial schedule of the last interval; the reverse phase
+// loads each earlier start from the host and runs that interval's schedule.
+long long interval_start(long long N, int nf, int i) { return (long long)((__int128)i * N / (nf + 1)); }
+
+void plan_two_level(std::vector<Action>& P, long long N, int s, int nf) {
+    P.push_back({kStore, 0, 0, 0, -1, 0});
+    for (int i = 1; i <= nf; ++i) {
+        const long long b0 = interval_start(N, nf, i - 1), b1 = interval_start(N, nf, i);
+        P.push_back({kAdv, b0, b1 - b0, 0, 0, -1});
+        if (i < nf) P.push_back({kStore, b1, 0, 0, -1, i});
+    }
+    const long long bl = interval_start(N, nf, nf);
+    plan_reverse(P, bl, N - bl, 0, s);
+    for (int i = nf - 1; i >= 0; --i) {
+        const long long b0 = interval_start(N, nf, i), b1 = interval_start(N, nf, i + 1);
+        P.push_back({kLoad, b0, 0, 0, -1, i});
+        plan_reverse(P, b0, b1 - b0, 0, s);
+    }
+}
+
+// Forward steps of the whole sweep (the terminal step included) with nf host
+// checkpoints: the forward phase to the last interval, then each interval's
+// binomial recomputation (Eq. 2.18); nf = 0 is the single-level schedule.
+double two_level_steps(long long N, int s, int nf) {
+    if (nf == 0) return (double)pnop::revolve_advances(N, s) + 1.0;
+    const long long L = N / (nf + 1), q = N % (nf + 1);  // q intervals of L + 1, the rest of L
+    const double inner = (double)(nf + 1 - q) * (double)pnop::revolve_advances(L, s) +
+                         (double)q * (double)pnop::revolve_advances(L + 1, s);
+    return (double)interval_start(N, nf, nf) + inner + 1.0;
+}
+
+// Number of host checkpoints minimising the recovery time of Eq. 2.21,
+// nf T_io + (forward steps) T_step, in units of T_step (ratio = T_io / T_step).
+int choose_host_checkpoints(long long N, int s, long long host_max, double ratio) {
+    const long long kmax = std::min<long long>(host_max, N - 1);
+    int best = 0;
+    double best_cost = two_level_steps(N, s, 0);
+    for (long long k = 1; k <= kmax; ++k) {
+        const double cost = (double)k * ratio + two_level_steps(N, s, (int)k);
+        if (cost < best_cost) {
+            best_cost = cost;
+            best = (int)k;
+        }
+    }
+    return best;
+}
+
 // Runs actions [from, to) of the plan; returns the index of the first adjoint
 // action reached when stop_at_adjoint (its state pointer in *state).
+// ---- second checkpoint level: pinned host memory over the host link
+// The staging field hstage carries every host copy; ev_staged marks the last
+// context-stream use of it, ev_copy the last copy-stream transfer.
+void ensure_host_tier(pnop_ctx* c, int slots) {
+    if (!c->copy) {
+        ck(cudaStreamCreateWithFlags(&c->copy, cudaStreamNonBlocking), "copy stream");
+        ck(cudaEventCreateWithFlags(&c->ev_copy, cudaEventDisableTiming), "event");
+        ck(cudaEventCreateWithFlags(&c->ev_staged, cudaEventDisableTiming), "event");
+        ck(cudaEventRecord(c->ev_copy, c->copy), "event");
+        ck(cudaEventRecord(c->ev_staged, c->stream), "event");
+    }
+    if (!c->hstage) c->hstage = c->field();
+    while ((int)c->host.size() < slots) {
+        void* p = nullptr;
+        cudaError_t e = cudaMallocHost(&p, c->field_bytes());
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            throw Status(PNOP_ERR_OOM, std::string("pinned host slot: ") + cudaGetErrorString(e));
+        }
+        c->host.push_back(p);
+    }
+}
+
+void host_store(pnop_ctx* c, const double2* src, int h) {
+    const size_t fb = c->field_bytes();
+    ck(cudaStreamWaitEvent(c->stream, c->ev_copy, 0), "wait copy");  // hstage free
+    ck(cudaMemcpyAsync(c->hstage, src, fb, cudaMemcpyDeviceToDevice, c->stream), "stage");
+    ck(cudaEventRecord(c->ev_staged, c->stream), "event");
+    ck(cudaStreamWaitEvent(c->copy, c->ev_staged, 0), "wait stage");
+    ck(cudaMemcpyAsync(c->host[h], c->hstage, fb, cudaMemcpyDeviceToHost, c->copy), "d2h");
+    ck(cudaEventRecord(c->ev_copy, c->copy), "event");
+    c->pref_host = -1;
+    ++c->st_hstore;
+}
+
+void host_prefetch(pnop_ctx* c, int h) {
+    ck(cudaStreamWaitEvent(c->copy, c->ev_staged, 0), "wait stage");  // hstage no longer read
+    ck(cudaMemcpyAsync(c->hstage, c->host[h], c->field_bytes(), cudaMemcpyHostToDevice, c->copy), "h2d");
+    ck(cudaEventRecord(c->ev_copy, c->copy), "event");
+    c->pref_host = h;
+}
+
+// host slot h -> dst, then start the transfer of the plan's next load
+void host_load(pnop_ctx* c, int h, double2* dst, size_t plan_index) {
+    if (c->pref_host != h) host_prefetch(c, h);
+    ck(cudaStreamWaitEvent(c->stream, c->ev_copy, 0), "wait h2d");
+    ck(cudaMemcpyAsync(dst, c->hstage, c->field_bytes(), cudaMemcpyDeviceToDevice, c->stream), "unstage");
+    ck(cudaEventRecord(c->ev_staged, c->stream), "event");
+    c->pref_host = -1;
+    ++c->st_hload;
+    for (size_t i = plan_index + 1; i < c->plan.size(); ++i)
+        if (c->plan[i].kind == kLoad) {
+            host_prefetch(c, c->plan[i].host);
+            break;
+        }
+}
+
 size_t run_plan(pnop_ctx* c, size_t from, bool stop_at_adjoint, const double2** state) {
     const auto& P = c->plan;
     for (size_t i = from; i < P.size(); ++i) {
         const Action& a = P[i];
-        if (!a.adjoint) {
+        if (a.kind == kStore) {
+            host_store(c, c->snaps[a.slot], a.host);
+            continue;
+        }
+        if (a.kind == kLoad) {
+            host_load(c, a.host, c->snaps[a.slot], i);
+            continue;
+        }
+        if (a.kind == kAdv) {
             const double2* r = advance(c, c->snaps[a.slot], a.start, a.n, a.dst >= 0 ? c->snaps[a.dst] : nullptr);
             if (a.dst >= 0) ++c->st_store;
             else c->cur = r;
@@ -575,6 +735,30 @@ int snapshot_slots(pnop_ctx* c, long long N) {
     return (int)s;
 }
 
+// T_io / T_step of Eq. 2.21 on this device: one store and one load of a field
+// through pinned host memory against one forward step, timed with events.
+double measure_io_ratio(pnop_ctx* c) {
+    ensure_host_tier(c, 1);
+    const size_t fb = c->field_bytes();
+    cudaEvent_t e[3];
+    for (auto& x : e) ck(cudaEventCreate(&x), "event");
+    ck(cudaMemsetAsync(c->tmpB, 0, fb, c->stream), "memset");
+    float io = 0, step = 0;
+    for (int rep = 0; rep < 2; ++rep) {  // the first round warms up
+        ck(cudaEventRecord(e[0], c->stream), "event");
+        ck(cudaMemcpyAsync(c->host[0], c->tmpB, fb, cudaMemcpyDeviceToHost, c->stream), "d2h");
+        ck(cudaMemcpyAsync(c->hstage, c->host[0], fb, cudaMemcpyHostToDevice, c->stream), "h2d");
+        ck(cudaEventRecord(e[1], c->stream), "event");
+        fwd_step(c, c->tmpB, c->tmpA, c->h.ph.tau0);
+        ck(cudaEventRecord(e[2], c->stream), "event");
+        ck(cudaEventSynchronize(e[2]), "sync");
+        ck(cudaEventElapsedTime(&io, e[0], e[1]), "elapsed");
+        ck(cudaEventElapsedTime(&step, e[1], e[2]), "elapsed");
+    }
+    for (auto& x : e) cudaEventDestroy(x);
+    return step > 0 ? (double)io / (double)step : 1.0;
+}
+
 // Forward part of the gradient sweep: copies (and rescales) u0, runs the
 // schedule up to its first adjoint step, computes u_N and E(T).  The sweep
 // state stays in the context for gradient_backward.
@@ -599,7 +783,15 @@ void gradient_forward(pnop_ctx* c, const double2* u0, double E0, double horizon,
     c->st_adv = c->st_adj = c->st_store = 0;
     c->st_slots = s;
     c->plan.clear();
-    plan_reverse(c->plan, 0, N, 0, s);
+    const int nf = (c->host_max > 0 && N > 1) ? choose_host_checkpoints(N, s, c->host_max, c->host_ratio) : 0;
+    c->st_nf = nf;
+    c->st_hstore = c->st_hload = 0;
+    if (nf > 0) {
+        ensure_host_tier(c, nf);
+        plan_two_level(c->plan, N, s, nf);
+    } else {
+        plan_reverse(c->plan, 0, N, 0, s);
+    }
     const double2* st = nullptr;
     c->plan_pos = run_plan(c, 0, true, &st);
     if (c->plan_pos >= c->plan.size() || c->plan[c->plan_pos].start != N - 1)
@@ -611,6 +803,11 @@ void gradient_forward(pnop_ctx* c, const double2* u0, double E0, double horizon,
     if (!std::isfinite(ET2)) throw Status(PNOP_ERR_NONFINITE, "final energy is not finite");
     *ET = 0.5 * ET2;
     if (Einit_out) *Einit_out = Einit;
+    for (size_t i = c->plan_pos; i < c->plan.size(); ++i)  // start the first host load early
+        if (c->plan[i].kind == kLoad) {
+            host_prefetch(c, c->plan[i].host);
+            break;
+        }
     c->pending = true;
 }
 
@@ -634,6 +831,81 @@ int gradient_impl(pnop_ctx* c, const double2* u0, double E0, double horizon, dou
     gradient_backward(c, 1.0, false, grad);
     if (gain) *gain = ET / Einit;
     return PNOP_OK;
+}
+
+// Adjoint looping (Section 2.3).  With u_dagger = -g (g the Riesz gradient of
+// E(T)), the update (1 + lambda alpha) u - alpha u_dagger = (1 + lambda alpha) u
+// + alpha g keeps E = E0 for lambda = lambda_+ of Eq. 2.14 (C0 = <u, u_dagger>,
+// E0_dagger = <u_dagger, u_dagger>/2), real for 0 < alpha <= alpha_max
+// (Eq. 2.15).  A trial point costs the checkpointed forward sweep; when it
+// raises G the reverse sweep of that same sweep gives the next gradient.
+void optimise_impl(pnop_ctx* c, double2* u, double E0, double horizon, int max_iter, double tol, double* hist,
+                   pnop_opt_stats* st) {
+    constexpr int kMaxHalvings = 60;
+    if (!c->opt_g) c->opt_g = c->field();
+    if (!c->opt_u) c->opt_u = c->field();
+    double2 *g = c->opt_g, *trial = c->opt_u;
+    project(c, u);
+    const double E = 0.5 * inner_sync(c, u, u);
+    if (!(E > 0) || !std::isfinite(E)) throw Status(PNOP_ERR_NONFINITE, "initial field has no finite energy");
+    axpby(c, std::sqrt(E0 / E), u, 0.0, nullptr, u);
+    double ET = 0, Eu = 0;
+    gradient_forward(c, u, -1.0, horizon, &ET, &Eu);
+    gradient_backward(c, 1.0, false, g);
+    project(c, g);
+    double G = ET / Eu;
+    *st = pnop_opt_stats{0, 1, 1, 0, G, std::nan("")};
+    if (hist) hist[0] = G;
+    for (int it = 0; it < max_iter && !st->converged; ++it) {
+        const double E0d = 0.5 * inner_sync(c, g, g);  // |u_dagger| = |g|
+        const double C0 = -inner_sync(c, u, g);
+        const double d = E0d / E0 - C0 * C0 / (4.0 * E0 * E0);
+        if (!std::isfinite(d)) throw Status(PNOP_ERR_NONFINITE, "gradient is not finite");
+        if (d <= 1e-12 * (E0d / E0)) {  // u_dagger parallel to u: the optimality condition
+            st->converged = 1;
+            break;
+        }
+        double alpha = 1.0 / std::sqrt(d);
+        bool accepted = false;
+        double Gn = G, R = 0;
+        for (int h = 0; h < kMaxHalvings; ++h) {
+            const double b = (alpha * C0 - 2.0 * E0) / (2.0 * alpha * E0);
+            const double lam = b + std::sqrt(std::max(0.0, b * b - (alpha * E0d - C0) / (alpha * E0)));
+            axpby(c, 1.0 + lam * alpha, u, alpha, g, trial);
+            bool finite = true;
+            try {
+                gradient_forward(c, trial, -1.0, horizon, &ET, &Eu);
+            } catch (const Status& e) {
+                if (e.code != PNOP_ERR_NONFINITE) throw;
+                finite = false;  // the trial blew up: treat as no growth
+            }
+            ++st->forward_evals;
+            Gn = finite ? ET / Eu : std::nan("");
+            R = std::isfinite(Gn) ? std::fabs(Gn - G) / std::fabs(Gn) : INFINITY;
+            if (std::isfinite(Gn) && Gn > G) {
+                accepted = true;
+                break;
+            }
+            if (R < tol) break;
+            alpha *= 0.5;
+        }
+        if (!accepted) {
+            st->converged = 1;
+            break;
+        }
+        gradient_backward(c, 1.0, false, g);
+        project(c, g);
+        ++st->gradients;
+        ck(cudaMemcpyAsync(u, trial, c->field_bytes(), cudaMemcpyDeviceToDevice, c->stream), "accept");
+        G = Gn;
+        st->iterations = it + 1;
+        st->gain = G;
+        st->rel_change = R;
+        if (hist) hist[it + 1] = G;
+        if (R < tol) st->converged = 1;
+    }
+    c->pending = false;  // the last trial's sweep is not the caller's
+    wait_stream(c, "optimise sync");
 }
 
 }  // namespace
@@ -663,11 +935,22 @@ int pnop_context_bytes(const pnop_grid* grid, const pnop_params* params, int sna
     const size_t nm = 2 * M + 1, nk = K + 1, nkp = (nk + pnop::kTileK - 1) / pnop::kTileK * pnop::kTileK, nt = 3 * (M + 1);
     const size_t S = nr * nm * nk, field = 3 * S * 16;
     const size_t cz = params->precision == PNOP_MIXED ? 8 : 16;
-    size_t b = (17 + (size_t)snaps) * field + 2 * S * 16;              // work fields, u_N, checkpoints, q, q2
-    b += 15 * nr * nt * nk * cz;                                         // transform scratch Y, Z
+    size_t b = (20 + (size_t)snaps) * field + 2 * S * 16;              // work fields, u_N, optimiser, host staging, checkpoints, q, q2
+    b += 24 * nr * nt * nk * cz;                                         // transform scratch Y, Y2, Z
     b += 2 * ((M + 2) + (M + 1)) * nr * 13 * nkp * 8;                    // LU factors and transposed rows
     b += (M + 2) * nr * 13 * 8 + 2 * nr * 13 * 8 + nm * nk * 3 * nr * 8; // bands, D1, influence
     *bytes = b + (1 << 20) + (40 + (size_t)snaps) * (2 << 20);        // tables, reductions, allocation rounding
+    return PNOP_OK;
+}
+
+int pnop_two_level_counts(long long nsteps, int snaps, long long max_host_slots, double io_ratio,
+                          int* host_checkpoints, long long* advances) {
+    if (nsteps < 1 || snaps < 1 || max_host_slots < 0 || !(io_ratio >= 0) || !std::isfinite(io_ratio))
+        return PNOP_ERR_INVALID_ARG;
+    const int s = (int)std::min<long long>(snaps, nsteps);
+    const int nf = nsteps > 1 ? choose_host_checkpoints(nsteps, s, max_host_slots, io_ratio) : 0;
+    if (host_checkpoints) *host_checkpoints = nf;
+    if (advances) *advances = (long long)std::llround(two_level_steps(nsteps, s, nf));
     return PNOP_OK;
 }
 
@@ -686,6 +969,13 @@ void pnop_destroy(pnop_ctx* ctx) {
     for (cudaEvent_t e : {ctx->ev_fork, ctx->ev_bu, ctx->ev_t})
         if (e) cudaEventDestroy(e);
     if (ctx->side) cudaStreamDestroy(ctx->side);
+    if (ctx->copy) {
+        cudaStreamSynchronize(ctx->copy);
+        cudaStreamDestroy(ctx->copy);
+    }
+    for (cudaEvent_t e : {ctx->ev_copy, ctx->ev_staged})
+        if (e) cudaEventDestroy(e);
+    for (void* p : ctx->host) cudaFreeHost(p);
     for (void* p : ctx->allocs) cudaFree(p);
     delete ctx;
 }
@@ -757,6 +1047,7 @@ int pnop_create(const pnop_grid* grid, const pnop_params* params, void* cuda_str
         const size_t cz = mixed(c) ? sizeof(float2) : sizeof(double2);
         const size_t plane = (size_t)d.nr * d.nth * d.nk * cz;
         c->Y = c->dalloc(9 * plane);
+        c->Y2 = c->dalloc(9 * plane);
         c->Z = c->dalloc(6 * plane);
         c->partial = (double*)c->dalloc(pnop::inner_partials(g) * sizeof(double));
         c->dscal = (double*)c->dalloc(4 * sizeof(double));
@@ -871,9 +1162,76 @@ int pnop_gradient_host(pnop_ctx* ctx, const double* u0_host, double E0, double h
     });
 }
 
+int pnop_optimise(pnop_ctx* ctx, void* u0, double E0, double horizon, int max_iter, double tol,
+                  double* gain_history, pnop_opt_stats* stats) {
+    return guarded(ctx, [&]() -> int {
+        if (!u0 || !(E0 > 0) || max_iter < 0 || !(tol >= 0)) throw Status(PNOP_ERR_INVALID_ARG, "bad arguments");
+        pnop_opt_stats st{};
+        optimise_impl(ctx, (double2*)u0, E0, horizon, max_iter, tol, gain_history, &st);
+        if (stats) *stats = st;
+        return PNOP_OK;
+    });
+}
+
+int pnop_mode_energy(pnop_ctx* ctx, const void* u, double* spectrum) {
+    return guarded(ctx, [&]() -> int {
+        if (!u || !spectrum) throw Status(PNOP_ERR_INVALID_ARG, "bad arguments");
+        const size_t n = 2 * (size_t)ctx->geo.nm * ctx->geo.nk;
+        if (!ctx->d_spec) ctx->d_spec = (double*)ctx->dalloc(n * sizeof(double));
+        run(ctx, PNOP_K_REDUCE, 1, 3.0 * ctx->S(),
+            [&] { pnop::launch_mode_energy(ctx->geo, (const double2*)u, ctx->d_spec, ctx->stream); });
+        ck(cudaMemcpyAsync(spectrum, ctx->d_spec, n * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream), "copy");
+        wait_stream(ctx, "mode energy");
+        return PNOP_OK;
+    });
+}
+
+int pnop_check_conversions(long long n, long long* mismatches) {
+    if (n < 0 || !mismatches) return PNOP_ERR_INVALID_ARG;
+    unsigned long long* d = nullptr;
+    if (cudaMalloc(&d, sizeof(unsigned long long)) != cudaSuccess) {
+        cudaGetLastError();
+        return PNOP_ERR_OOM;
+    }
+    unsigned long long h = 0;
+    cudaError_t e = cudaMemset(d, 0, sizeof h);
+    if (e == cudaSuccess) {
+        try {
+            pnop::launch_conversion_check((unsigned long long)n, 0x5eedull, d, 0);
+        } catch (const std::runtime_error&) {
+            e = cudaErrorLaunchFailure;
+        }
+    }
+    if (e == cudaSuccess) e = cudaMemcpy(&h, d, sizeof h, cudaMemcpyDeviceToHost);
+    cudaFree(d);
+    if (e != cudaSuccess) return PNOP_ERR_CUDA;
+    *mismatches = (long long)h;
+    return PNOP_OK;
+}
+
+int pnop_set_host_tier(pnop_ctx* ctx, long long max_host_slots, double io_ratio) {
+    return guarded(ctx, [&]() -> int {
+        if (max_host_slots < 0 || !std::isfinite(io_ratio) || max_host_slots > (1LL << 30))
+            throw Status(PNOP_ERR_INVALID_ARG, "bad arguments");
+        ctx->pending = false;  // measuring uses the sweep buffers
+        ctx->host_max = max_host_slots;
+        ctx->host_ratio = io_ratio >= 0 ? io_ratio : (max_host_slots > 0 ? measure_io_ratio(ctx) : 0.0);
+        return PNOP_OK;
+    });
+}
+
+int pnop_host_tier_stats(const pnop_ctx* ctx, int* host_checkpoints, long long* host_stores, long long* host_loads,
+                         double* io_ratio) {
+    if (!ctx) return PNOP_ERR_INVALID_ARG;
+    if (host_checkpoints) *host_checkpoints = ctx->st_nf;
+    if (host_stores) *host_stores = ctx->st_hstore;
+    if (host_loads) *host_loads = ctx->st_hload;
+    if (io_ratio) *io_ratio = ctx->host_ratio;
+    return PNOP_OK;
+}
+
 int pnop_gradient_stats(const pnop_ctx* ctx, long long* advances, long long* adjoint_steps, long long* stores) {
     if (!ctx) return PNOP_ERR_INVALID_ARG;
-    if (stores) *stores = ctx->st_store;
     if (advances) *advances = ctx->st_adv;
     if (adjoint_steps) *adjoint_steps = ctx->st_adj;
     if (stores) *stores = ctx->st_store;
@@ -890,17 +1248,21 @@ int pnop_apply(pnop_ctx* ctx, int op, const void* a, const void* b, void* out, d
         const Geo& g = ctx->geo;
         switch (op) {
             case PNOP_OP_CURL: run(ctx, PNOP_K_SPECTRAL, 1, flops::curl * ctx->S(), [&] { pnop::launch_curl(g, A, O, ctx->stream); }); break;
-            case PNOP_OP_NONLINEAR: nonlinear(ctx, A, t, O); break;
+            case PNOP_OP_NONLINEAR: nonlinear(ctx, A, t, O, ctx->Y); break;
             case PNOP_OP_STAGE:
                 if (!B) throw Status(PNOP_ERR_INVALID_ARG, "stage needs a forcing field");
                 stage_u(ctx, A, B, O);
                 break;
             case PNOP_OP_NONLINEAR_T:
                 if (!B) throw Status(PNOP_ERR_INVALID_ARG, "transpose needs a cotangent field");
-                nonlinearT(ctx, A, t, B, O);
+                nonlinearT(ctx, A, t, B, O, ctx->Y, false);
                 break;
             case PNOP_OP_STAGE_T_U: stageT(ctx, A, O, 0, ctx->Fb); break;
             case PNOP_OP_STAGE_T_F: stageT(ctx, A, ctx->ua, 0, O); break;
+            case PNOP_OP_PROJECT:
+                ck(cudaMemcpyAsync(O, A, ctx->field_bytes(), cudaMemcpyDeviceToDevice, ctx->stream), "copy");
+                project(ctx, O);
+                break;
             default: throw Status(PNOP_ERR_INVALID_ARG, "unknown operator");
         }
         wait_stream(ctx, "apply");

@@ -467,13 +467,72 @@ bool build_operators(HostOps& h, std::string& err) {
 // ---------------------------------------------------------------- checkpoint counts
 long long binom_beta(int s, long long t) {
     if (t < 0) return 0;
-    // C(s + t, s) with saturation
+    // C(s + t, s) = C(s + t, t) with saturation, over the shorter product
+    const long long a = std::max<long long>(s, t), b = std::min<long long>(s, t);
     long double v = 1;
-    for (int i = 1; i <= s; ++i) {
-        v = v * (long double)(t + i) / (long double)i;
+    for (long long i = 1; i <= b; ++i) {
+        v = v * (long double)(a + i) / (long double)i;
         if (v > 4.0e18L) return (long long)4e18;
     }
     return (long long)(v + 0.5L);
+}
+
+bool build_projection(const HostOps& h, std::vector<double>& L, std::string& err) {
+    const int nr = h.d.nr, M = h.d.M, nk = h.d.nk, B = kProjBand, W1 = B + 1;
+    // A_par = D_r W^-1 D_r^T over the columns i >= 1, banded, for both parities
+    std::vector<double> A[2];
+    for (int par = 0; par < 2; ++par) {
+        A[par].assign((size_t)nr * W1, 0.0);  // A[j][j' - j + B] for j' in [j - B, j]
+        std::vector<std::vector<std::pair<int, double>>> col(nr);  // column i: (row j, D_r(j, i))
+        for (int j = 0; j < nr; ++j)
+            for (int e = 0; e < kBand; ++e) {
+                const int i = j - kLo + e;
+                if (i < 1 || i >= nr) continue;
+                double v = h.D1[((size_t)par * nr + j) * kBand + e];
+                if (i == j) v += h.invr[j];
+                if (v != 0.0) col[i].push_back({j, v});
+            }
+        for (int i = 1; i < nr; ++i)
+            for (auto& a : col[i])
+                for (auto& b : col[i]) {
+                    if (b.first > a.first) continue;
+                    if (a.first - b.first > B) {
+                        err = "admissible projection: divergence stencil wider than the factor band";
+                        return false;
+                    }
+                    A[par][(size_t)a.first * W1 + (b.first - a.first + B)] += a.second * b.second / h.W[i];
+                }
+    }
+    L.assign((size_t)(M + 1) * nk * nr * W1, 0.0);
+    std::vector<double> S((size_t)nr * W1);
+    for (int ma = 0; ma <= M; ++ma) {
+        const int par = parity_index(ma + 1);
+        for (int k = 0; k < nk; ++k) {
+            if (ma == 0 && k == 0) continue;  // mean mode: diagonal constraints, no factor
+            const double kz = 2.0 * M_PI * k / h.d.Lz;
+            S = A[par];
+            for (int j = 1; j < nr; ++j)
+                S[(size_t)j * W1 + B] += ((double)ma * ma * h.invr[j] * h.invr[j] + kz * kz) / h.W[j];
+            double* F = &L[(((size_t)ma * nk + k) * nr) * W1];
+            for (int j = 0; j < nr; ++j) {
+                for (int i = std::max(0, j - B); i <= j; ++i) {
+                    double v = S[(size_t)j * W1 + (i - j + B)];
+                    for (int q = std::max(0, j - B); q < i; ++q)
+                        if (q >= i - B) v -= F[(size_t)j * W1 + (q - j + B)] * F[(size_t)i * W1 + (q - i + B)];
+                    if (i < j) {
+                        F[(size_t)j * W1 + (i - j + B)] = v * F[(size_t)i * W1 + B];
+                    } else {
+                        if (!(v > 0) || !std::isfinite(v)) {
+                            err = "admissible projection: constraint system is not positive definite";
+                            return false;
+                        }
+                        F[(size_t)j * W1 + B] = 1.0 / std::sqrt(v);
+                    }
+                }
+            }
+        }
+    }
+    return true;
 }
 
 int revolve_repetitions(long long nsteps, int snaps) {

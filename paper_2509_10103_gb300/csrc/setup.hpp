@@ -73,6 +73,19 @@ bool build_operators(HostOps& h, std::string& err);
 // Bessel J_nu of complex argument by its power series.
 std::complex<double> bessel_j(int nu, std::complex<double> z);
 
+// Factors for the orthogonal projection onto admissible fields (no slip,
+// discretely solenoidal; Section 2.2 constraints) in the energy inner product.
+// For mode (m, k) != (0, 0), with the wall values removed, the constraint
+// C x = D_r x_r + (i m / r) x_theta + i k_z x_z = 0 at every r_j gives the
+// real symmetric positive definite system
+//   S = D_r W^-1 D_r^T + diag((m^2 / r^2 + k_z^2) / W)  (rows j >= 1 for the diagonal),
+// D_r = D1 (parity of m + 1) + 1/r over the columns j >= 1, banded with
+// half-bandwidth kProjBand.  L holds its banded Cholesky factor per (|m|, k):
+// [|m| = 0..M][k][j][e], e = i - j + kProjBand for i = j - kProjBand .. j - 1,
+// and e = kProjBand holding 1 / L_jj.
+constexpr int kProjBand = 12;
+bool build_projection(const HostOps& h, std::vector<double>& L, std::string& err);
+
 // Binomial checkpointing (Section 2.5).
 long long binom_beta(int s, long long t);
 int revolve_repetitions(long long nsteps, int snaps);

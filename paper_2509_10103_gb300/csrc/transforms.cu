@@ -597,6 +597,44 @@ __global__ void k_zpass2(Geo g, const T2* __restrict__ Y, T2* __restrict__ Z, ZS
         }
 }
 
+// ------------------------------------------------------------------ conversion self-check
+// d2f_rn / f2d_exact against the hardware conversions on pseudo-random bit
+// patterns (SplitMix64) and on constructed edge cases (signed zeros,
+// infinities, NaNs, the largest and smallest normals, exact halfway cases).
+// Counts disagreements (NaN payloads aside).
+__device__ __forceinline__ unsigned long long splitmix64(unsigned long long z) {
+    z += 0x9e3779b97f4a7c15ull;
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+    return z ^ (z >> 31);
+}
+__global__ void k_conv_check(unsigned long long n, unsigned long long seed, unsigned long long* bad) {
+    const unsigned long long edge[] = {
+        0x0000000000000000ull, 0x8000000000000000ull, 0x7ff0000000000000ull, 0xfff0000000000000ull,
+        0x7ff8000000000000ull, 0x7ff0000000000001ull, 0x47efffffe0000000ull, 0x47effffff0000000ull,
+        0x3810000000000000ull, 0x380fffffffffffffull, 0x3ff0000010000000ull, 0x3ff0000030000000ull,
+        0x3ff00000f0000000ull, 0x3ff0000010000001ull, 0xbff0000030000000ull, 0x3fefffffffffffffull};
+    constexpr int kEdge = sizeof(edge) / sizeof(edge[0]);
+    for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < n + kEdge;
+         i += (unsigned long long)gridDim.x * blockDim.x) {
+        unsigned long long bits = i < kEdge ? edge[i] : splitmix64(seed + i);
+        if (i >= kEdge && (i & 1))  // half of the patterns inside the float exponent range
+            bits = (bits & 0x800fffffffffffffull) | ((897ull + ((bits >> 52) & 0x7ffull) % 254ull) << 52);
+        const double x = __longlong_as_double((long long)bits);
+        const float a = d2f_rn(x), b = (float)x;
+        if (!(isnan(a) && isnan(b)) && __float_as_uint(a) != __float_as_uint(b)) atomicAdd(bad, 1ull);
+        const float f = __uint_as_float((unsigned)(bits >> 17));
+        const double c = f2d_exact(f), d = (double)f;
+        if (!(isnan(c) && isnan(d)) && __double_as_longlong(c) != __double_as_longlong(d)) atomicAdd(bad, 1ull);
+    }
+}
+
+void launch_conversion_check(unsigned long long n, unsigned long long seed, unsigned long long* bad,
+                             cudaStream_t s) {
+    k_conv_check<<<1024, 256, 0, s>>>(n, seed, bad);
+    check_launch("conversion check");
+}
+
 // ------------------------------------------------------------------ launchers
 template <class T2> static const T2* tw_theta(const Twiddles& t);
 template <> const double2* tw_theta<double2>(const Twiddles& t) { return t.th_d; }

@@ -77,3 +77,31 @@ def test_revolve_plan_large_horizons(L):
         adv, _ = L.pnop_revolve_counts(n, s)
         assert adv == po.revolve_advances(n, s)
     assert L.pnop_revolve_counts(4000, 32)[0] == 11405
+
+
+def _two_level_model(N, s, k, C):
+    """Forward steps of the two-level schedule by construction: the forward
+    phase reaches the start of the last of k + 1 near-equal intervals, then
+    each interval costs its optimal binomial recomputation (brute-force table
+    C), plus the terminal step."""
+    if k == 0:
+        return C[N, s] + 1
+    b = [i * N // (k + 1) for i in range(k + 2)]
+    return b[k] + sum(C[b[i + 1] - b[i], s] for i in range(k + 1)) + 1
+
+
+def test_two_level_schedule_minimises_eq_2_21(L):
+    C = po.revolve_advances_dp(120, 8)
+    for N, s, H, r in ((30, 2, 10, 0.0), (100, 4, 40, 0.3), (120, 8, 119, 0.0), (60, 3, 5, 2.0), (50, 8, 0, 0.0),
+                       (97, 2, 96, 0.05)):
+        nf, adv = L.pnop_two_level_counts(N, s, H, r)
+        costs = [k * r + _two_level_model(N, s, k, C) for k in range(0, min(H, N - 1) + 1)]
+        best = min(costs)
+        assert abs(nf * r + adv - best) < 1e-9, (N, s, H, r)
+        assert costs.index(best) == nf
+        assert adv == _two_level_model(N, s, nf, C)
+    # enough host slots: each state is computed once (ties go to fewer host slots)
+    nf, adv = L.pnop_two_level_counts(100, 2, 99, 0.0)
+    assert adv == 100 and nf >= 98
+    # no host slots: the single-level schedule (Eq. 2.18 + the terminal step)
+    assert L.pnop_two_level_counts(100, 4, 0, 0.0) == (0, po.revolve_advances(100, 4) + 1)

@@ -1,0 +1,85 @@
+"""GPU adjoint looping (pnop_optimise, Section 2.3) against the oracle loop
+and, on a linear problem, against the exact optimum (largest squared singular
+value of the weighted N-step Jacobian, assembled by the oracle)."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import adjoint_looping as al
+from oracle import pipe_oracle as po
+from paper_2509_10103_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def L():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2509_10103_gb300 import build
+    build.build()
+    from paper_2509_10103_gb300 import _lib
+    return _lib
+
+
+def dev(x):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(x, dtype=np.complex128)).to("cuda")
+
+
+def run_both(L, prm, N, E0, max_iter, tol, seed, precision=0, snaps=3):
+    o = po.Oracle(po.Params(**prm))
+    p = o.p
+    ctx = L.Context(p.nr, 2 * (p.M + 1), 2 * (p.K + 1), p.Lz, p.Re, p.dt, p.Wo, p.A, 0.0, precision, snaps)
+    u0 = synth.random_field(o.r, p.M, p.K, p.Lz, seed=seed)
+    x = dev(u0)
+    stats, hist = ctx.pnop_optimise(x, E0, N * p.dt, max_iter, tol)
+    u_ref, hist_ref, info = al.optimise(o, u0, 0.0, N, E0, max_iter, tol)
+    got = x.cpu().numpy()
+    ctx.close()
+    return o, stats, hist, got, u_ref, hist_ref, info
+
+
+def test_optimiser_linear_problem_matches_oracle_and_exact_optimum(L):
+    prm = dict(nr=9, M=1, K=1, Lz=4.0, Re=500.0, dt=0.25, Wo=8.0, A=0.0)
+    N, E0 = 20, 1e-20
+    o, stats, hist, got, u_ref, hist_ref, info = run_both(L, prm, N, E0, 12, 1e-10, seed=1)
+    n = min(len(hist), len(hist_ref))
+    assert n >= 6
+    np.testing.assert_allclose(hist[:n], hist_ref[:n], rtol=1e-9)
+    assert stats["gradients"] == stats["iterations"] + 1
+    assert abs(o.energy(got) / E0 - 1) < 1e-12
+    if len(hist) == len(hist_ref):
+        assert np.abs(got - u_ref).max() <= 1e-7 * np.abs(u_ref).max()
+    # exact optimum of the linear map (the oracle pins the same quantity on the CPU)
+    from tests.test_oracle_optimiser import exact_linear_optimum
+    assert abs(hist[-1] / exact_linear_optimum(o, N) - 1) < 1e-5
+
+
+def test_optimiser_nonlinear_iterations_match_oracle(L):
+    prm = dict(nr=12, M=3, K=5, Lz=10.0, Re=2000.0, dt=0.01, Wo=8.0, A=1.0)
+    o, stats, hist, got, u_ref, hist_ref, info = run_both(L, prm, 20, 1e-3, 3, 1e-8, seed=4)
+    assert len(hist) == len(hist_ref) == 4
+    # the iterates inherit the gradient's 1e-10 agreement, amplified by the alpha_max steps
+    np.testing.assert_allclose(hist, hist_ref, rtol=1e-6)
+    assert stats["forward_evals"] == info["forward_evals"] + 1  # the library counts the start's sweep
+    assert np.abs(got - u_ref).max() <= 1e-6 * np.abs(u_ref).max()
+    assert all(b > a for a, b in zip(hist, hist[1:]))
+
+
+def test_optimiser_mixed_precision_tracks_fp64(L):
+    prm = dict(nr=12, M=3, K=5, Lz=10.0, Re=2000.0, dt=0.01, Wo=8.0, A=1.0)
+    o = po.Oracle(po.Params(**prm))
+    p = o.p
+    u0 = synth.random_field(o.r, p.M, p.K, p.Lz, seed=4)
+    out = {}
+    for prec in (0, 1):
+        ctx = L.Context(p.nr, 2 * (p.M + 1), 2 * (p.K + 1), p.Lz, p.Re, p.dt, p.Wo, p.A, 0.0, prec, 3)
+        x = dev(u0)
+        out[prec] = ctx.pnop_optimise(x, 1e-3, 20 * p.dt, 3, 1e-8)
+        ctx.close()
+    (s0, h0), (s1, h1) = out[0], out[1]
+    assert len(h0) == len(h1)
+    np.testing.assert_allclose(h1, h0, rtol=1e-5)

@@ -193,6 +193,28 @@ def test_stage_transposes(case, request, L):
 
 
 @pytest.mark.parametrize("case", ["small", "ragged"])
+def test_mode_energy_spectrum(case, request):
+    c = request.getfixturevalue(case)
+    u = c.field(15, 1e-3)
+    got = c.ctx.pnop_mode_energy(dev(u))
+    ref = c.o.mode_energy(u)
+    assert np.abs(got - ref).max() <= 1e-13 * ref.sum()
+
+
+@pytest.mark.parametrize("case", ["small", "ragged"])
+def test_admissible_projection(case, request, L):
+    from oracle import adjoint_looping as al
+    c = request.getfixturevalue(case)
+    rng = np.random.default_rng(13)
+    g = c.field(14, 1.0) + 0.1 * (rng.standard_normal(c.ctx.shape) + 1j * rng.standard_normal(c.ctx.shape))
+    out = c.zeros()
+    c.ctx.pnop_apply(L.OP_PROJECT, dev(g), None, out)
+    ref = al.project_admissible(c.o, g)
+    assert rel(host(out), ref) < 1e-9
+    assert np.abs(c.o.divergence(host(out))).max() < 1e-8 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("case", ["small", "ragged"])
 def test_forward_steps(case, request):
     c = request.getfixturevalue(case)
     u0 = c.field(10, 1e-2)
@@ -310,3 +332,8 @@ def test_mixed_precision_error_budget(L):
     cos = c.o.inner(gh, gref) / math.sqrt(c.o.inner(gh, gh) * c.o.inner(gref, gref))
     assert abs(gain / G - 1) <= 1e-5
     assert cos >= 0.99999
+
+
+def test_integer_pipe_conversions_match_the_hardware(L):
+    # the mixed-precision transforms convert FP64 <-> FP32 on the integer pipes
+    assert L.pnop_check_conversions(1 << 24) == 0

@@ -222,7 +222,8 @@ def test_divergence_converges_under_refinement():
 def test_energy_budget_production_minus_dissipation():
     res = []
     for dt in (0.004, 0.002):
-        o = _oracle(nr=24, M=2, K=2, Re=100.0, dt=dt)
+        # nr = 32: the spatial floor of the discrete budget (~1e-6) stays below the O(dt^2) time error
+        o = _oracle(nr=32, M=2, K=2, Re=100.0, dt=dt)
         ns = int(round(0.2 / dt))
         u = o.forward(_field(o, 2, 1e-3), 0.0, ns)
         t = ns * dt
@@ -366,3 +367,46 @@ def test_planted_missing_hermitian_factor_breaks_library_transform(monkeypatch):
     monkeypatch.setattr(po.Oracle, "synth", bad_synth)
     with pytest.raises(AssertionError):
         test_synth_matches_library_irfft()
+
+
+def test_mode_energy_and_resolution_measures_follow_their_definitions():
+    """Per-mode energies sum to the energy; e_M, e_K from the stored half
+    spectrum equal the paper's sums over the full spectrum (Section 2.4),
+    evaluated here from the Hermitian extension f(-m, -k) = conj f(m, k)."""
+    from paper_2509_10103_gb300 import diagnostics, synth
+    p = po.Params(nr=10, M=3, K=4, Lz=7.0, Re=1000.0, dt=0.01)
+    o = po.Oracle(p)
+    u = synth.random_field(o.r, p.M, p.K, p.Lz, seed=5, decay=1.5)
+    spec = o.mode_energy(u)
+    E = o.energy(u)
+    assert abs(spec.sum() / E - 1) < 1e-13
+    # full spectrum over k = -K..K
+    W = 0.5 * (2 * math.pi * p.Lz) * o.W
+    def e_full(m, k):
+        f = u[:, :, m + p.M, k] if k >= 0 else np.conj(u[:, :, -m + p.M, -k])
+        return float(np.sum(W * np.sum(np.abs(f) ** 2, axis=0)))
+    total = sum(e_full(m, k) for m in range(-p.M, p.M + 1) for k in range(-p.K, p.K + 1))
+    assert abs(total / E - 1) < 1e-12
+    eM = sum(e_full(p.M, k) for k in range(-p.K, p.K + 1)) / E
+    eK = sum(e_full(m, p.K) for m in range(-p.M, p.M + 1)) / E
+    gM, gK = diagnostics.resolution_measures(spec, E)
+    assert abs(gM / eM - 1) < 1e-12 and abs(gK / eK - 1) < 1e-12
+    Grt, Gz = diagnostics.component_gains(spec, E)
+    assert abs(Grt + Gz - 1) < 1e-13
+    assert abs(Gz - float(np.sum(0.5 * o.What * np.abs(u[2]) ** 2)) / E) < 1e-13
+
+
+def test_linear_step_of_steady_pipe_flow_has_no_growing_mode():
+    """Hagen-Poiseuille flow is linearly stable: the per-mode step map at
+    Re = 1750 has every eigenvalue inside the unit circle (the rotational form
+    of the base-flow terms fails this: a pair near 1.0016 at nr = 38)."""
+    o = _oracle(nr=24, M=2, K=1, Lz=math.pi, Re=1750.0, dt=0.01, A=0.0)
+    n = 3 * o.p.nr
+    for m in range(0, 3):
+        for k in range(0, 2):
+            J = np.zeros((n, n), complex)
+            for i in range(n):
+                e = np.zeros(n, complex)
+                e[i] = 1.0
+                J[:, i] = o.linear_mode_step(e.reshape(3, o.p.nr), m, k, 0.0).ravel()
+            assert np.abs(np.linalg.eigvals(J)).max() < 1.0, (m, k)
