@@ -186,12 +186,6 @@ int pnop_two_level_counts(long long nsteps, int snaps, long long max_host_slots,
  * energy traces. */
 int pnop_mode_energy(pnop_ctx* ctx, const void* u, double* spectrum);
 
-/* Self-check of the FP64 <-> FP32 conversions the mixed-precision transforms
- * perform on the integer pipes: runs them against the hardware conversions on
- * n pseudo-random bit patterns plus edge cases on the current device and
- * writes the number of disagreements (NaN payloads aside) to *mismatches. */
-int pnop_check_conversions(long long n, long long* mismatches);
-
 /* Counters and result of pnop_optimise. */
 typedef struct {
     int iterations;    /* accepted updates */

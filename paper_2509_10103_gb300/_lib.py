@@ -25,7 +25,7 @@ EXPORTS = (
     "pnop_create", "pnop_set_base_flow", "pnop_dims", "pnop_grid_points", "pnop_step_forward",
     "pnop_step_adjoint", "pnop_gradient", "pnop_gradient_forward", "pnop_gradient_backward", "pnop_gradient_host",
     "pnop_gradient_stats", "pnop_optimise", "pnop_set_host_tier", "pnop_host_tier_stats", "pnop_two_level_counts",
-    "pnop_check_conversions", "pnop_mode_energy",
+    "pnop_mode_energy",
     "pnop_energy", "pnop_inner", "pnop_apply", "pnop_set_timeout",
     "pnop_sync", "pnop_profile", "pnop_profile_read", "pnop_revolve_counts", "pnop_context_bytes",
     "pnop_energy_noalloc", "pnop_last_error", "pnop_error_string", "pnop_destroy",
@@ -65,7 +65,6 @@ def _load():
         "pnop_optimise": (c_int, [c_void_p, c_void_p, c_double, c_double, c_int, c_double, POINTER(c_double),
                                   POINTER(pnop_opt_stats)]),
         "pnop_set_host_tier": (c_int, [c_void_p, c_longlong, c_double]),
-        "pnop_check_conversions": (c_int, [c_longlong, POINTER(c_longlong)]),
         "pnop_mode_energy": (c_int, [c_void_p, c_void_p, POINTER(c_double)]),
         "pnop_host_tier_stats": (c_int, [c_void_p, POINTER(c_int), POINTER(c_longlong), POINTER(c_longlong),
                                          POINTER(c_double)]),
@@ -118,15 +117,6 @@ def pnop_revolve_counts(nsteps: int, snaps: int):
     if rc != PNOP_OK:
         raise PnopError(rc, "revolve_counts")
     return a.value, s.value
-
-
-def pnop_check_conversions(n):
-    """Disagreements of the integer-pipe FP64<->FP32 conversions with the hardware ones."""
-    bad = c_longlong()
-    rc = lib.pnop_check_conversions(n, byref(bad))
-    if rc != PNOP_OK:
-        raise PnopError(rc, "check_conversions")
-    return bad.value
 
 
 def pnop_two_level_counts(nsteps, snaps, max_host_slots, io_ratio):

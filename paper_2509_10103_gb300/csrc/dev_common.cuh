@@ -35,40 +35,10 @@ __device__ __forceinline__ double2 dfma(double s, double2 a, double2 acc) {
     return make_double2(fma(s, a.x, acc.x), fma(s, a.y, acc.y));
 }
 
-// FP64 <-> FP32 conversions on the integer pipes, from the IEEE-754 binary64
-// and binary32 layouts: the FP64 pipe of this GPU issues two lanes per SM per
-// cycle, so the conversion instructions it would execute dominate the FP32
-// transform kernels.  Round to nearest even, infinities and NaNs kept; the
-// rare values below the smallest normal float (|x| < 2^-126) take the
-// hardware conversion.
-__device__ __forceinline__ float d2f_rn(double x) {
-    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
-    const unsigned hi = (unsigned)(b >> 32), lo = (unsigned)b;
-    const unsigned sign = hi & 0x80000000u;
-    const int e = (int)((hi >> 20) & 0x7ffu);
-    const unsigned m = ((hi & 0xfffffu) << 3) | (lo >> 29);  // upper 23 of the 52 fraction bits
-    const unsigned rest = lo & 0x1fffffffu;                   // the 29 bits dropped
-    const int fe = e - 1023 + 127;
-    if (e == 0x7ff) return __uint_as_float(sign | 0x7f800000u | m | ((m | rest) ? 0x400000u : 0u));
-    if (fe >= 255) return __uint_as_float(sign | 0x7f800000u);
-    if (fe <= 0) return (float)x;
-    unsigned r = sign | ((unsigned)fe << 23) | m;
-    if (rest > 0x10000000u || (rest == 0x10000000u && (m & 1u))) r += 1u;  // carries into the exponent as it should
-    return __uint_as_float(r);
-}
-__device__ __forceinline__ double f2d_exact(float f) {
-    const unsigned u = __float_as_uint(f);
-    const unsigned sign = u & 0x80000000u, e = (u >> 23) & 0xffu, m = u & 0x7fffffu;
-    if (e == 0) return (double)f;
-    const unsigned de = e == 0xffu ? 0x7ffu : e + 896u;  // rebias 127 -> 1023
-    return __hiloint2double((int)(sign | (de << 20) | (m >> 3)), (int)(m << 29));
-}
-
 template <class T2> __device__ __forceinline__ T2 from_d(double2 v);
 template <> __device__ __forceinline__ double2 from_d<double2>(double2 v) { return v; }
-template <> __device__ __forceinline__ float2 from_d<float2>(double2 v) { return make_float2(d2f_rn(v.x), d2f_rn(v.y)); }
-__device__ __forceinline__ double2 to_d(double2 v) { return v; }
-__device__ __forceinline__ double2 to_d(float2 v) { return make_double2(f2d_exact(v.x), f2d_exact(v.y)); }
+template <> __device__ __forceinline__ float2 from_d<float2>(double2 v) { return make_float2((float)v.x, (float)v.y); }
+template <class T2> __device__ __forceinline__ double2 to_d(T2 v) { return make_double2((double)v.x, (double)v.y); }
 
 __device__ __forceinline__ int par_idx(int m) { return m & 1; }  // 0 even, 1 odd (two's complement)
 

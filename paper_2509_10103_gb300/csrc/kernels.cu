@@ -111,12 +111,12 @@ __device__ __forceinline__ void base_at(const Geo& g, int j, double c, double s,
     dU = -2.0 * r + (b.x * c - b.y * s);
 }
 
-// N += -U du/dz - u_r dU/dr e_z: the base-flow terms in advective form.  The
+// N = -U du/dz - u_r dU/dr e_z: the base-flow terms in advective form.  The
 // rotational form (U e_z) x w + u x (-dU/dr e_theta) differs from it by
 // grad(U u_z), which the discrete pressure projection does not remove exactly;
 // the remainder couples u_z back into (u_r, u_theta) and makes k = 0 modes of
 // steady pipe flow grow at high Re.
-__global__ void k_base_add(Geo g, const double2* __restrict__ u, double2* __restrict__ N, double c, double s) {
+__global__ void k_base(Geo g, const double2* __restrict__ u, double2* __restrict__ N, double c, double s) {
     Idx d;
     if (!decode(g, d)) return;
     double U, dU;
@@ -124,16 +124,13 @@ __global__ void k_base_add(Geo g, const double2* __restrict__ u, double2* __rest
     const size_t o = sidx(g, d.j, d.im, d.k), S = d.S;
     const double a = d.k * g.kz0 * U;  // -U d/dz = -i a
     const double2 ur = u[o], ut = u[o + S], uz = u[o + 2 * S];
-    double2 x = N[o];
-    N[o] = make_double2(x.x + a * ur.y, x.y - a * ur.x);
-    x = N[o + S];
-    N[o + S] = make_double2(x.x + a * ut.y, x.y - a * ut.x);
-    x = N[o + 2 * S];
-    N[o + 2 * S] = make_double2(x.x + a * uz.y - dU * ur.x, x.y - a * uz.x - dU * ur.y);
+    N[o] = make_double2(a * ur.y, -a * ur.x);
+    N[o + S] = make_double2(a * ut.y, -a * ut.x);
+    N[o + 2 * S] = make_double2(a * uz.y - dU * ur.x, -a * uz.x - dU * ur.y);
 }
 
-// transpose (Euclidean cotangents): ub += conj(-i a) nb = i a nb; ub_r -= dU nb_z
-__global__ void k_baseT_acc(Geo g, const double2* __restrict__ nb, double2* __restrict__ ub, double c, double s) {
+// transpose (Euclidean cotangents): ub = conj(-i a) nb = i a nb; ub_r -= dU nb_z
+__global__ void k_baseT(Geo g, const double2* __restrict__ nb, double2* __restrict__ ub, double c, double s) {
     Idx d;
     if (!decode(g, d)) return;
     double U, dU;
@@ -141,12 +138,9 @@ __global__ void k_baseT_acc(Geo g, const double2* __restrict__ nb, double2* __re
     const size_t o = sidx(g, d.j, d.im, d.k), S = d.S;
     const double a = d.k * g.kz0 * U;
     const double2 nr_ = nb[o], nt = nb[o + S], nz = nb[o + 2 * S];
-    double2 x = ub[o];
-    ub[o] = make_double2(x.x - a * nr_.y - dU * nz.x, x.y + a * nr_.x - dU * nz.y);
-    x = ub[o + S];
-    ub[o + S] = make_double2(x.x - a * nt.y, x.y + a * nt.x);
-    x = ub[o + 2 * S];
-    ub[o + 2 * S] = make_double2(x.x - a * nz.y, x.y + a * nz.x);
+    ub[o] = make_double2(-a * nr_.y - dU * nz.x, a * nr_.x - dU * nz.y);
+    ub[o + S] = make_double2(-a * nt.y, a * nt.x);
+    ub[o + 2 * S] = make_double2(-a * nz.y, a * nz.x);
 }
 
 // ------------------------------------------------------------------ radial stage (forward)
@@ -762,12 +756,12 @@ void launch_curlT_acc(const Geo& g, const double2* wb, double2* ub, cudaStream_t
     k_curlT_acc<<<spec_grid(g), spec_bx(g), 0, s>>>(g, wb, ub);
     check_launch("curlT");
 }
-void launch_base_add(const Geo& g, const double2* u, double2* N, double c, double sn, cudaStream_t s) {
-    k_base_add<<<spec_grid(g), spec_bx(g), 0, s>>>(g, u, N, c, sn);
-    check_launch("base_add");
+void launch_base(const Geo& g, const double2* u, double2* N, double c, double sn, cudaStream_t s) {
+    k_base<<<spec_grid(g), spec_bx(g), 0, s>>>(g, u, N, c, sn);
+    check_launch("base");
 }
-void launch_baseT_acc(const Geo& g, const double2* nb, double2* ub, double c, double sn, cudaStream_t s) {
-    k_baseT_acc<<<spec_grid(g), spec_bx(g), 0, s>>>(g, nb, ub, c, sn);
+void launch_baseT(const Geo& g, const double2* nb, double2* ub, double c, double sn, cudaStream_t s) {
+    k_baseT<<<spec_grid(g), spec_bx(g), 0, s>>>(g, nb, ub, c, sn);
     check_launch("baseT");
 }
 

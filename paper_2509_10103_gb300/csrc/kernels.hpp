@@ -33,10 +33,12 @@ struct Geo {
     double ewt;          // 2 pi Lz (energy weight prefactor)
 };
 
-// Up to 9 input / 6 output spectral component planes for the transforms.
+// Up to 9 input / 6 output spectral component planes for the transforms; the
+// analysis adds add[i] (when not null) to output i.
 struct FieldPtrs {
     const double2* in[9];
     double2* out[6];
+    const double2* add[6];
 };
 
 // Per-field multipliers applied when forming the Hermitian z spectrum:
@@ -60,9 +62,10 @@ enum ZMode { ZFWD = 0, ZADJ = 1 };
 // ---- spectral FP64 kernels ----
 void launch_curl(const Geo& g, const double2* u, double2* w, cudaStream_t s);
 void launch_curlT_acc(const Geo& g, const double2* wb, double2* ub, cudaStream_t s);
-// base-flow terms in advective form: N += -U du/dz - u_r dU/dr e_z (and the transpose into ub)
-void launch_base_add(const Geo& g, const double2* u, double2* N, double c, double sn, cudaStream_t s);
-void launch_baseT_acc(const Geo& g, const double2* nb, double2* ub, double c, double sn, cudaStream_t s);
+// base-flow terms in advective form: N = -U du/dz - u_r dU/dr e_z, and their
+// transpose ub = (dN/du)^T nb (both written, not accumulated)
+void launch_base(const Geo& g, const double2* u, double2* N, double c, double sn, cudaStream_t s);
+void launch_baseT(const Geo& g, const double2* nb, double2* ub, double c, double sn, cudaStream_t s);
 
 // ---- transforms (T = double for FP64, float for mixed) ----
 template <class T2>
@@ -95,10 +98,6 @@ void launch_stageT_rhs(const Geo& g, const double2* X, const double2* Y, double 
 void launch_stageT_qbar(const Geo& g, const double2* Fb, double2* q, cudaStream_t s);
 void launch_stageT_psolve(const Geo& g, double2* q, cudaStream_t s);
 void launch_stageT_div(const Geo& g, const double2* z, double2* Fb, cudaStream_t s);
-
-// ---- self-check of the integer-pipe FP64 <-> FP32 conversions: n random
-// patterns plus edge cases, disagreements added to *bad (device counter) ----
-void launch_conversion_check(unsigned long long n, unsigned long long seed, unsigned long long* bad, cudaStream_t s);
 
 // ---- diagnostics: per-mode energy, E[0] cross-section and E[1] axial parts, [2][nm][nk] ----
 void launch_mode_energy(const Geo& g, const double2* u, double* E, cudaStream_t s);

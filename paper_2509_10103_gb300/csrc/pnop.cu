@@ -90,7 +90,8 @@ struct pnop_ctx {
     double2* q = nullptr;
     double2* q2 = nullptr;  // pressure scratch of the side stream
     cudaStream_t side = nullptr;  // second stream for independent work within a step
-    cudaEvent_t ev_fork = nullptr, ev_bu = nullptr, ev_t = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_bu = nullptr, ev_t = nullptr, ev_base = nullptr;
+    double2* Nbase = nullptr;  // base-flow terms (or their transpose), added by the analysis
     double2 *tmpA = nullptr, *tmpB = nullptr, *lamA = nullptr, *lamB = nullptr;
     void* Y = nullptr;
     void* Y2 = nullptr;  // theta synthesis of u and curl u kept from N(u) for N'(u)^T in the adjoint step
@@ -369,7 +370,7 @@ void inner_dev(pnop_ctx* c, const double2* a, const double2* b, double* dst) {
 // precision, through the physical scratch Y.  Fields [0, cached) are already
 // synthesised in Y and are not redone.
 void transforms(pnop_ctx* c, const pnop::FieldPtrs& f, int nin, int nout, int zmode, const pnop::ZScales& sc, void* Y,
-                int cached) {
+                int cached, cudaEvent_t before_analysis) {
     const Geo& g = c->geo;
     cudaStream_t s = c->stream;
     const double cols = (double)g.nr * g.nk, rows = (double)g.nr * g.nt;
@@ -382,45 +383,66 @@ void transforms(pnop_ctx* c, const pnop::FieldPtrs& f, int nin, int nout, int zm
         float2* Yf = (float2*)Y;
         run(c, PNOP_K_SYNTH_THETA, 1, ns * cols, [&] { pnop::launch_synth_theta<float2>(g, fs, ns, Yf + cached * plane, c->tw, s); });
         run(c, zk, 1, rows, [&] { pnop::launch_zpass<float2>(g, zmode, Yf, (float2*)c->Z, sc, c->tw, s); });
+        if (before_analysis) join_side(c, before_analysis);
         run(c, PNOP_K_ANAL_THETA, 1, nout * cols, [&] { pnop::launch_anal_theta<float2>(g, f, nout, (const float2*)c->Z, c->tw, s); });
     } else {
         double2* Yd = (double2*)Y;
         run(c, PNOP_K_SYNTH_THETA, 1, ns * cols, [&] { pnop::launch_synth_theta<double2>(g, fs, ns, Yd + cached * plane, c->tw, s); });
         run(c, zk, 1, rows, [&] { pnop::launch_zpass<double2>(g, zmode, Yd, (double2*)c->Z, sc, c->tw, s); });
+        if (before_analysis) join_side(c, before_analysis);
         run(c, PNOP_K_ANAL_THETA, 1, nout * cols, [&] { pnop::launch_anal_theta<double2>(g, f, nout, (const double2*)c->Z, c->tw, s); });
     }
 }
 
 // ------------------------------------------------------------------ nonlinear term
+// Base-flow terms of N(u) at time t into Nbase on the side stream (the caller
+// has forked it); the analysis of the transforms adds them after ev_base.
+void queue_base(pnop_ctx* c, const double2* u, double t) {
+    const double ph = c->h.omega * t;
+    run(c, PNOP_K_SPECTRAL, 1, flops::base * c->S(),
+        [&] { pnop::launch_base(c->geo, u, c->Nbase, std::cos(ph), std::sin(ph), c->side); }, c->side);
+    ck(cudaEventRecord(c->ev_base, c->side), "record");
+}
+
 // N = P[I(u) x I(w)] - U du/dz - u_r dU/dr e_z, w = curl u  (Eq. 2.5; base-flow
-// terms in advective form)
-// The physical u and w are left in Y (fields 0..5).
-void nonlinear(pnop_ctx* c, const double2* u, double t, double2* N, void* Y) {
+// terms in advective form, computed on the side stream while the curl and the
+// transforms run).  The physical u and w are left in Y (fields 0..5).  With
+// base_queued the caller has already queued the base terms of this u.
+void nonlinear(pnop_ctx* c, const double2* u, double t, double2* N, void* Y, bool base_queued = false) {
     const Geo& g = c->geo;
     const size_t S = c->S();
     cudaStream_t s = c->stream;
+    if (!base_queued) {
+        fork_side(c);
+        queue_base(c, u, t);
+    }
     run(c, PNOP_K_SPECTRAL, 1, flops::curl * S, [&] { pnop::launch_curl(g, u, c->omega, s); });
     pnop::FieldPtrs f{};
     for (int i = 0; i < 3; ++i) {
         f.in[i] = u + i * S;
         f.in[3 + i] = c->omega + i * S;
         f.out[i] = N + i * S;
+        f.add[i] = c->Nbase + i * S;
     }
     pnop::ZScales sc{};
     const double inv_n = 1.0 / ((double)g.nt * g.nzp);
     for (int i = 0; i < 6; ++i) sc.h0[i] = sc.hk[i] = 1.0;
     for (int i = 0; i < 3; ++i) sc.o0[i] = sc.ok[i] = inv_n;
-    transforms(c, f, 6, 3, pnop::ZFWD, sc, Y, 0);
-    const double ph = c->h.omega * t;
-    run(c, PNOP_K_SPECTRAL, 1, flops::base * S, [&] { pnop::launch_base_add(g, u, N, std::cos(ph), std::sin(ph), s); });
+    transforms(c, f, 6, 3, pnop::ZFWD, sc, Y, 0, c->ev_base);
 }
 
 // ub = (dN/du at u)^T nb  (Euclidean cotangents).  With cached, Y already
 // holds the physical u and curl u of this u (fields 0..5, left by nonlinear).
+// The base-flow transpose runs on the side stream and is added by the analysis.
 void nonlinearT(pnop_ctx* c, const double2* u, double t, const double2* nb, double2* ub, void* Y, bool cached) {
     const Geo& g = c->geo;
     const size_t S = c->S();
     cudaStream_t s = c->stream;
+    fork_side(c);
+    const double ph = c->h.omega * t;
+    run(c, PNOP_K_SPECTRAL, 1, flops::base * S,
+        [&] { pnop::launch_baseT(g, nb, c->Nbase, std::cos(ph), std::sin(ph), c->side); }, c->side);
+    ck(cudaEventRecord(c->ev_base, c->side), "record");
     if (!cached) run(c, PNOP_K_SPECTRAL, 1, flops::curl * S, [&] { pnop::launch_curl(g, u, c->omega, s); });
     pnop::FieldPtrs f{};
     for (int i = 0; i < 3; ++i) {
@@ -429,6 +451,7 @@ void nonlinearT(pnop_ctx* c, const double2* u, double t, const double2* nb, doub
         f.in[6 + i] = nb + i * S;
         f.out[i] = ub + i * S;
         f.out[3 + i] = c->wb + i * S;
+        f.add[i] = c->Nbase + i * S;
     }
     pnop::ZScales sc{};
     const double inv_n = 1.0 / ((double)g.nt * g.nzp);
@@ -443,9 +466,7 @@ void nonlinearT(pnop_ctx* c, const double2* u, double t, const double2* nb, doub
         sc.o0[i] = 1.0;
         sc.ok[i] = 2.0;
     }
-    transforms(c, f, 9, 6, pnop::ZADJ, sc, Y, cached ? 6 : 0);
-    const double ph = c->h.omega * t;
-    run(c, PNOP_K_SPECTRAL, 1, flops::base * S, [&] { pnop::launch_baseT_acc(g, nb, ub, std::cos(ph), std::sin(ph), s); });
+    transforms(c, f, 9, 6, pnop::ZADJ, sc, Y, cached ? 6 : 0, c->ev_base);
     run(c, PNOP_K_SPECTRAL, 1, flops::curlT * S, [&] { pnop::launch_curlT_acc(g, c->wb, ub, s); });
 }
 
@@ -455,9 +476,10 @@ void nonlinearT(pnop_ctx* c, const double2* u, double t, const double2* nb, doub
 // depends on u only and runs on the side stream while N(u) is transformed.
 void fwd_step(pnop_ctx* c, const double2* u, double2* out, double t) {
     fork_side(c);
+    queue_base(c, u, t);
     stage_bu(c, u, c->RB, c->side);
     ck(cudaEventRecord(c->ev_bu, c->side), "record");
-    nonlinear(c, u, t, c->N0, c->Y);
+    nonlinear(c, u, t, c->N0, c->Y, true);
     stage(c, c->RB, c->N0, c->us, nullptr, c->ev_bu);
     nonlinear(c, c->us, t + c->h.ph.dt, c->N1, c->Y);
     axpby(c, 0.5, c->N1, -0.5, c->N0, c->N1);
@@ -476,6 +498,7 @@ void fwd_step(pnop_ctx* c, const double2* u, double2* out, double t) {
 void adj_step(pnop_ctx* c, const double2* u, double t, const double2* lin, double2* lout) {
     const Geo& g = c->geo;
     fork_side(c);
+    queue_base(c, u, t);
     stage_bu(c, u, c->RB, c->side);
     ck(cudaEventRecord(c->ev_bu, c->side), "record");
     stageT_front(c, lin, c->Rl, c->side);
@@ -484,7 +507,7 @@ void adj_step(pnop_ctx* c, const double2* u, double t, const double2* lin, doubl
         c->side);
     stageT_proj(c, c->Nb, c->q2, c->side);  // Nb = S_F^H lin / 2
     ck(cudaEventRecord(c->ev_t, c->side), "record");
-    nonlinear(c, u, t, c->N0, c->Y2);  // physical u, curl u stay in Y2 for N'(u)^T below
+    nonlinear(c, u, t, c->N0, c->Y2, true);  // physical u, curl u stay in Y2 for N'(u)^T below
     stage(c, c->RB, c->N0, c->us, nullptr, c->ev_bu);
     join_side(c, c->ev_t);
     nonlinearT(c, c->us, t + c->h.ph.dt, c->Nb, c->ubs, c->Y, false);
@@ -935,7 +958,7 @@ int pnop_context_bytes(const pnop_grid* grid, const pnop_params* params, int sna
     const size_t nm = 2 * M + 1, nk = K + 1, nkp = (nk + pnop::kTileK - 1) / pnop::kTileK * pnop::kTileK, nt = 3 * (M + 1);
     const size_t S = nr * nm * nk, field = 3 * S * 16;
     const size_t cz = params->precision == PNOP_MIXED ? 8 : 16;
-    size_t b = (20 + (size_t)snaps) * field + 2 * S * 16;              // work fields, u_N, optimiser, host staging, checkpoints, q, q2
+    size_t b = (21 + (size_t)snaps) * field + 2 * S * 16;              // work fields, u_N, optimiser, host staging, checkpoints, q, q2
     b += 24 * nr * nt * nk * cz;                                         // transform scratch Y, Y2, Z
     b += 2 * ((M + 2) + (M + 1)) * nr * 13 * nkp * 8;                    // LU factors and transposed rows
     b += (M + 2) * nr * 13 * 8 + 2 * nr * 13 * 8 + nm * nk * 3 * nr * 8; // bands, D1, influence
@@ -966,7 +989,7 @@ int pnop_revolve_counts(int nsteps, int snaps, long long* advances, long long* s
 void pnop_destroy(pnop_ctx* ctx) {
     if (!ctx) return;
     for (auto e : ctx->ev) cudaEventDestroy(e);
-    for (cudaEvent_t e : {ctx->ev_fork, ctx->ev_bu, ctx->ev_t})
+    for (cudaEvent_t e : {ctx->ev_fork, ctx->ev_bu, ctx->ev_t, ctx->ev_base})
         if (e) cudaEventDestroy(e);
     if (ctx->side) cudaStreamDestroy(ctx->side);
     if (ctx->copy) {
@@ -1037,12 +1060,12 @@ int pnop_create(const pnop_grid* grid, const pnop_params* params, void* cuda_str
         c->tw.th_f = c->upload(thf);
         c->tw.z_f = c->upload(zf);
         for (double2** b : {&c->omega, &c->N0, &c->N1, &c->us, &c->ua, &c->Fb, &c->Nb, &c->ubs, &c->wb, &c->R,
-                            &c->Rl, &c->RB, &c->tmpA, &c->tmpB, &c->lamA, &c->lamB})
+                            &c->Rl, &c->RB, &c->tmpA, &c->tmpB, &c->lamA, &c->lamB, &c->Nbase})
             *b = c->field();
         c->q = (double2*)c->dalloc(c->S() * sizeof(double2));
         c->q2 = (double2*)c->dalloc(c->S() * sizeof(double2));
         ck(cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking), "side stream");
-        for (cudaEvent_t* e : {&c->ev_fork, &c->ev_bu, &c->ev_t})
+        for (cudaEvent_t* e : {&c->ev_fork, &c->ev_bu, &c->ev_t, &c->ev_base})
             ck(cudaEventCreateWithFlags(e, cudaEventDisableTiming), "event");
         const size_t cz = mixed(c) ? sizeof(float2) : sizeof(double2);
         const size_t plane = (size_t)d.nr * d.nth * d.nk * cz;
@@ -1184,29 +1207,6 @@ int pnop_mode_energy(pnop_ctx* ctx, const void* u, double* spectrum) {
         wait_stream(ctx, "mode energy");
         return PNOP_OK;
     });
-}
-
-int pnop_check_conversions(long long n, long long* mismatches) {
-    if (n < 0 || !mismatches) return PNOP_ERR_INVALID_ARG;
-    unsigned long long* d = nullptr;
-    if (cudaMalloc(&d, sizeof(unsigned long long)) != cudaSuccess) {
-        cudaGetLastError();
-        return PNOP_ERR_OOM;
-    }
-    unsigned long long h = 0;
-    cudaError_t e = cudaMemset(d, 0, sizeof h);
-    if (e == cudaSuccess) {
-        try {
-            pnop::launch_conversion_check((unsigned long long)n, 0x5eedull, d, 0);
-        } catch (const std::runtime_error&) {
-            e = cudaErrorLaunchFailure;
-        }
-    }
-    if (e == cudaSuccess) e = cudaMemcpy(&h, d, sizeof h, cudaMemcpyDeviceToHost);
-    cudaFree(d);
-    if (e != cudaSuccess) return PNOP_ERR_CUDA;
-    *mismatches = (long long)h;
-    return PNOP_OK;
 }
 
 int pnop_set_host_tier(pnop_ctx* ctx, long long max_host_slots, double io_ratio) {

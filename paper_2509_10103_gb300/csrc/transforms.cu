@@ -247,6 +247,7 @@ __global__ void k_anal_theta(Geo g, FieldPtrs f, const T2* __restrict__ Z, const
     __syncthreads();
     T2* res = fft_cols<T2, KB, KB, -1>(buf0, buf1, g.nt, tw);
     double2* dst = f.out[fi] + (size_t)j * g.nm * g.nk;
+    const double2* add = f.add[fi] ? f.add[fi] + (size_t)j * g.nm * g.nk : nullptr;
     for (int i = threadIdx.x; i < g.nm * KB; i += blockDim.x) {
         const int im = i / KB, kk = i % KB;
         if (kk >= kw) continue;
@@ -256,7 +257,9 @@ __global__ void k_anal_theta(Geo g, FieldPtrs f, const T2* __restrict__ Z, const
             double2 vm = to_d(res[(m > 0 ? g.nt - m : -m) * KB + kk]);
             v = make_double2(0.5 * (v.x + vm.x), 0.5 * (v.y - vm.y));
         }
-        dst[(size_t)im * g.nk + k0 + kk] = v;
+        const size_t o = (size_t)im * g.nk + k0 + kk;
+        if (add) v = make_double2(v.x + add[o].x, v.y + add[o].y);
+        dst[o] = v;
     }
 }
 
@@ -453,6 +456,7 @@ __global__ void __launch_bounds__(128) k_anal2(Geo g, FieldPtrs f, const T2* __r
     }
     __syncthreads();
     double2* dst = f.out[fi] + (size_t)j * g.nm * g.nk;
+    const double2* add = f.add[fi] ? f.add[fi] + (size_t)j * g.nm * g.nk : nullptr;
     for (int t = threadIdx.x; t < KB * N2; t += blockDim.x) {
         const int kk = t % KB, m2 = t / KB, k = k0 + kk;
         T2 v[N1];
@@ -464,8 +468,14 @@ __global__ void __launch_bounds__(128) k_anal2(Geo g, FieldPtrs f, const T2* __r
             const int n = m2 + N2 * m1;
             const int m = n <= g.M ? n : n - N;
             if (k < g.nk && m >= -g.M) {
-                if (k == 0) buf[n * KB + kk] = v[m1];
-                else dst[(size_t)(m + g.M) * g.nk + k] = to_d(v[m1]);
+                if (k == 0) {
+                    buf[n * KB + kk] = v[m1];
+                } else {
+                    const size_t o = (size_t)(m + g.M) * g.nk + k;
+                    double2 x = to_d(v[m1]);
+                    if (add) x = make_double2(x.x + add[o].x, x.y + add[o].y);
+                    dst[o] = x;
+                }
             }
         }
     }
@@ -475,7 +485,9 @@ __global__ void __launch_bounds__(128) k_anal2(Geo g, FieldPtrs f, const T2* __r
             const int m = im - g.M;
             const double2 v = to_d(buf[(m < 0 ? m + N : m) * KB]);
             const double2 vm = to_d(buf[(m > 0 ? N - m : -m) * KB]);
-            dst[(size_t)im * g.nk] = make_double2(0.5 * (v.x + vm.x), 0.5 * (v.y - vm.y));
+            double2 x = make_double2(0.5 * (v.x + vm.x), 0.5 * (v.y - vm.y));
+            if (add) x = make_double2(x.x + add[(size_t)im * g.nk].x, x.y + add[(size_t)im * g.nk].y);
+            dst[(size_t)im * g.nk] = x;
         }
     }
 }
@@ -595,44 +607,6 @@ __global__ void k_zpass2(Geo g, const T2* __restrict__ Y, T2* __restrict__ Z, ZS
                     mk<T2>((T)0.5 * (P.y + Pm.y) * s2, (T)-0.5 * (P.x - Pm.x) * s2);
             }
         }
-}
-
-// ------------------------------------------------------------------ conversion self-check
-// d2f_rn / f2d_exact against the hardware conversions on pseudo-random bit
-// patterns (SplitMix64) and on constructed edge cases (signed zeros,
-// infinities, NaNs, the largest and smallest normals, exact halfway cases).
-// Counts disagreements (NaN payloads aside).
-__device__ __forceinline__ unsigned long long splitmix64(unsigned long long z) {
-    z += 0x9e3779b97f4a7c15ull;
-    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
-    z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
-    return z ^ (z >> 31);
-}
-__global__ void k_conv_check(unsigned long long n, unsigned long long seed, unsigned long long* bad) {
-    const unsigned long long edge[] = {
-        0x0000000000000000ull, 0x8000000000000000ull, 0x7ff0000000000000ull, 0xfff0000000000000ull,
-        0x7ff8000000000000ull, 0x7ff0000000000001ull, 0x47efffffe0000000ull, 0x47effffff0000000ull,
-        0x3810000000000000ull, 0x380fffffffffffffull, 0x3ff0000010000000ull, 0x3ff0000030000000ull,
-        0x3ff00000f0000000ull, 0x3ff0000010000001ull, 0xbff0000030000000ull, 0x3fefffffffffffffull};
-    constexpr int kEdge = sizeof(edge) / sizeof(edge[0]);
-    for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < n + kEdge;
-         i += (unsigned long long)gridDim.x * blockDim.x) {
-        unsigned long long bits = i < kEdge ? edge[i] : splitmix64(seed + i);
-        if (i >= kEdge && (i & 1))  // half of the patterns inside the float exponent range
-            bits = (bits & 0x800fffffffffffffull) | ((897ull + ((bits >> 52) & 0x7ffull) % 254ull) << 52);
-        const double x = __longlong_as_double((long long)bits);
-        const float a = d2f_rn(x), b = (float)x;
-        if (!(isnan(a) && isnan(b)) && __float_as_uint(a) != __float_as_uint(b)) atomicAdd(bad, 1ull);
-        const float f = __uint_as_float((unsigned)(bits >> 17));
-        const double c = f2d_exact(f), d = (double)f;
-        if (!(isnan(c) && isnan(d)) && __double_as_longlong(c) != __double_as_longlong(d)) atomicAdd(bad, 1ull);
-    }
-}
-
-void launch_conversion_check(unsigned long long n, unsigned long long seed, unsigned long long* bad,
-                             cudaStream_t s) {
-    k_conv_check<<<1024, 256, 0, s>>>(n, seed, bad);
-    check_launch("conversion check");
 }
 
 // ------------------------------------------------------------------ launchers

@@ -333,7 +333,3 @@ def test_mixed_precision_error_budget(L):
     assert abs(gain / G - 1) <= 1e-5
     assert cos >= 0.99999
 
-
-def test_integer_pipe_conversions_match_the_hardware(L):
-    # the mixed-precision transforms convert FP64 <-> FP32 on the integer pipes
-    assert L.pnop_check_conversions(1 << 24) == 0
