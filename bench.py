@@ -273,6 +273,35 @@ def budget_sweep(L, torch, precision, H, budgets=(10, 57, 100), steps=2):
     return out
 
 
+def continuous_adjoint_report(L, torch, precision, H, snaps, steps=2):
+    """The gradient through the continuous adjoint (pnop_gradient_continuous) on
+    the same workload, and its agreement with the exact discrete gradient
+    (both projected onto admissible fields)."""
+    import numpy as np
+    ctx = L.Context(NR, NTHETA, NZ, LZ, RE, DT, WO, AMP, TAU0, precision, snaps)
+    r = np.array(ctx.pnop_grid_points())
+    u0 = torch.from_numpy(make_u0(r)).to("cuda")
+    gc, gd = torch.zeros_like(u0), torch.zeros_like(u0)
+    horizon = H * DT
+    ctx.pnop_gradient_continuous(u0, E0, horizon, gc)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        ctx.pnop_gradient_continuous(u0, E0, horizon, gc)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    ctx.pnop_gradient(u0, E0, horizon, gd)
+    pc, pd = torch.zeros_like(u0), torch.zeros_like(u0)
+    ctx.pnop_apply(L.OP_PROJECT, gc, None, pc)
+    ctx.pnop_apply(L.OP_PROJECT, gd, None, pd)
+    cos = ctx.pnop_inner(pc, pd) / math.sqrt(ctx.pnop_inner(pc, pc) * ctx.pnop_inner(pd, pd))
+    ctx.close()
+    return {"steps_per_s": H * steps / (ms / 1e3), "snap_budget": snaps,
+            "cosine_with_discrete_gradient_projected": cos}
+
+
 def host_tier_report(L, torch, precision, H, snaps=10, steps=2):
     """The same gradient with `snaps` HBM checkpoint slots plus up to H - 1 pinned
     host slots (two-level schedule, Eq. 2.21, io ratio measured)."""
@@ -558,6 +587,7 @@ def main():
                               "fp64": time_single_steps(L, torch, L.PNOP_FP64)}
         out["budget_sweep_mixed"] = budget_sweep(L, torch, L.PNOP_MIXED, H)
         out["host_tier_mixed"] = host_tier_report(L, torch, L.PNOP_MIXED, H)
+        out["continuous_adjoint_mixed"] = continuous_adjoint_report(L, torch, L.PNOP_MIXED, H, s)
     if not args.no_serving and ws == 1:
         out["serving"] = serving_report(L)
     if not args.no_cpu_baseline and ws == 1:

@@ -120,6 +120,19 @@ int pnop_step_adjoint(pnop_ctx* ctx, const void* u_n, void* lam, double t_n);
  * a whole number of time steps (to 1e-9 relative). */
 int pnop_gradient(pnop_ctx* ctx, const void* u0, double E0, double horizon, void* grad_out, double* gain_out);
 
+/* Gradient from the continuous adjoint equations (Eq. 2.9-2.11), the form the
+ * paper integrates: the same checkpointed forward sweep, then w = -u_dagger
+ * from w(T) = u(T) (Eq. 2.8) backward to tau0 with the predictor-corrector of
+ * the forward step and the adjoint forcing (PNOP_OP_NONLINEAR_ADJ), taken at
+ * the stored forward states of both ends of each step.  grad_out receives
+ * w(tau0), the gradient in the energy inner product; it approximates the exact
+ * discrete gradient of pnop_gradient to discretisation error.  Other
+ * arguments as pnop_gradient.  Allocates on first use physical scratch for 18
+ * fields and four more device fields (counted against hbm_budget; not in
+ * pnop_context_bytes). */
+int pnop_gradient_continuous(pnop_ctx* ctx, const void* u0, double E0, double horizon, void* grad_out,
+                             double* gain_out);
+
 /* pnop_gradient in two halves, for reverse-mode drivers (an autograd
  * backward): pnop_gradient_forward copies u0 (rescaled to E0 when E0 > 0),
  * runs the checkpointed forward sweep up to the terminal state u_N and
@@ -229,6 +242,10 @@ int pnop_optimise(pnop_ctx* ctx, void* u0, double E0, double horizon, int max_it
  *   PNOP_OP_NONLINEAR_T out = (dN/da at a, t)^T b
  *   PNOP_OP_STAGE_T_U  out = (dS/da)^T a      (b unused)
  *   PNOP_OP_STAGE_T_F  out = (dS/db)^T a      (b unused)
+ *   PNOP_OP_NONLINEAR_ADJ out = N_adj(b; a, t): forcing of the continuous adjoint
+ *                      equation for the adjoint field b (w = -u_dagger) about the
+ *                      forward state a, in backward time (Eq. 2.9):
+ *                      U db/dz - b_z U' e_r + P[-a x curl b - 2 (grad a) . b]
  *   PNOP_OP_PROJECT    out = P a: orthogonal projection, in the energy inner
  *                      product, onto admissible fields (Hermitian k = 0 plane,
  *                      zero at the wall, discrete divergence zero at every
@@ -243,7 +260,8 @@ enum {
     PNOP_OP_NONLINEAR_T = 3,
     PNOP_OP_STAGE_T_U = 4,
     PNOP_OP_STAGE_T_F = 5,
-    PNOP_OP_PROJECT = 6
+    PNOP_OP_PROJECT = 6,
+    PNOP_OP_NONLINEAR_ADJ = 7
 };
 int pnop_apply(pnop_ctx* ctx, int op, const void* a, const void* b, void* out, double t);
 

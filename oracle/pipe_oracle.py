@@ -497,6 +497,61 @@ class Oracle:
         ikz = 1j * self.kz[None, None, :]
         return self.apply_d1(ur, 1) + ur / self.r[:, None, None] + imr * ut + ikz * uz
 
+    # ---------------- continuous adjoint (Eq. 2.9-2.11), the paper's own form ----------------
+    def grad_u(self, u: np.ndarray):
+        """Velocity-gradient tensor G[i][j] = (grad u)_ij in cylindrical components
+        (i the derivative direction r, theta, z; j the velocity component), spectral:
+        (d_r u_j), ((d_theta u_r - u_theta)/r, (d_theta u_theta + u_r)/r, d_theta u_z / r),
+        (d_z u_j)."""
+        ur, ut, uz = u
+        ir = 1.0 / self.r[:, None, None]
+        im = 1j * self.m[None, :, None]
+        ikz = 1j * self.kz[None, None, :]
+        return [[self.apply_d1(ur, 1), self.apply_d1(ut, 1), self.apply_d1(uz, 0)],
+                [(im * ur - ut) * ir, (im * ut + ur) * ir, im * uz * ir],
+                [ikz * ur, ikz * ut, ikz * uz]]
+
+    def nonlinear_adj(self, w: np.ndarray, u: np.ndarray, t: float) -> np.ndarray:
+        """Forcing of the adjoint equation (Eq. 2.9) in backward time tau = T - t:
+        dw/dtau = Re^-1 lap w + N_adj(w; u) - grad p_dagger, with
+        N_adj = ((U + u).grad) w - (grad(U + u)) . w
+              = U dw/dz - w_z dU/dr e_r  +  P[-u x curl w - 2 (grad u) . w],
+        the gradient part grad(u . w) of the perturbation term going into the adjoint
+        pressure, the base-flow part in advective form (as in `nonlinear`)."""
+        om = self.curl(w)
+        up = np.stack([self.synth(c) for c in u])
+        wp = np.stack([self.synth(c) for c in w])
+        omp = np.stack([self.synth(c) for c in om])
+        G = self.grad_u(u)
+        Gp = [[self.synth(G[i][j]) for j in range(3)] for i in range(3)]
+        Gw = np.stack([sum(Gp[i][j] * wp[j] for j in range(3)) for i in range(3)])
+        n = np.stack([self.analysis(c) for c in (-np.cross(up, omp, axis=0) - 2.0 * Gw)])
+        U, dU = self.base(t)
+        n += (1j * self.kz[None, None, :] * U[:, None, None])[None] * w
+        n[0] += -dU[:, None, None] * w[2]
+        return n
+
+    def adjoint_step_continuous(self, u_next: np.ndarray, t_next: float, u_now: np.ndarray, t_now: float,
+                                w: np.ndarray) -> np.ndarray:
+        """w(t_now) from w(t_next), t_next = t_now + dt: the predictor-corrector of
+        `step` run backward in time with the adjoint forcing, taken at (u_next,
+        t_next) for the predictor and at (u_now, t_now) for the corrector."""
+        n0 = self.nonlinear_adj(w, u_next, t_next)
+        ws = self.stage(w, n0)
+        n1 = self.nonlinear_adj(ws, u_now, t_now)
+        return self.stage(w, 0.5 * (n0 + n1))
+
+    def gradient_continuous(self, u0: np.ndarray, t0: float, nsteps: int):
+        """E(T) and the gradient from the continuous adjoint: w(T) = u(T) (the
+        compatibility condition Eq. 2.8 with w = -u_dagger), integrated back to t0;
+        w(t0) is the gradient in the energy inner product (w = -u_dagger, Eq. 2.12)."""
+        uN, states = self.forward(u0, t0, nsteps, keep=True)
+        w = uN.copy()
+        for n in range(nsteps - 1, -1, -1):
+            w = self.adjoint_step_continuous(states[n + 1], t0 + (n + 1) * self.p.dt, states[n],
+                                             t0 + n * self.p.dt, w)
+        return self.energy(uN), w
+
     def mode_energy(self, u: np.ndarray) -> np.ndarray:
         """Energy of each stored mode (m, k >= 0) with the weights of Eq. 2.1, split
         into the cross-section part (u_r, u_theta) [0] and the axial part (u_z) [1];

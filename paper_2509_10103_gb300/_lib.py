@@ -19,14 +19,13 @@ PNOP_FP64 = 0
 PNOP_MIXED = 1
 KCLASSES = ("synth_theta", "zpass_fwd", "zpass_adj", "anal_theta", "spectral", "radial_band", "radial_solve",
             "elementwise", "reduce")
-OP_CURL, OP_NONLINEAR, OP_STAGE, OP_NONLINEAR_T, OP_STAGE_T_U, OP_STAGE_T_F, OP_PROJECT = range(7)
+OP_CURL, OP_NONLINEAR, OP_STAGE, OP_NONLINEAR_T, OP_STAGE_T_U, OP_STAGE_T_F, OP_PROJECT, OP_NONLINEAR_ADJ = range(8)
 
 EXPORTS = (
-    "pnop_create", "pnop_set_base_flow", "pnop_dims", "pnop_grid_points", "pnop_step_forward",
-    "pnop_step_adjoint", "pnop_gradient", "pnop_gradient_forward", "pnop_gradient_backward", "pnop_gradient_host",
-    "pnop_gradient_stats", "pnop_optimise", "pnop_set_host_tier", "pnop_host_tier_stats", "pnop_two_level_counts",
-    "pnop_mode_energy",
-    "pnop_energy", "pnop_inner", "pnop_apply", "pnop_set_timeout",
+    "pnop_create", "pnop_set_base_flow", "pnop_dims", "pnop_grid_points", "pnop_step_forward", "pnop_step_adjoint",
+    "pnop_gradient", "pnop_gradient_continuous", "pnop_gradient_forward", "pnop_gradient_backward",
+    "pnop_gradient_host", "pnop_gradient_stats", "pnop_optimise", "pnop_set_host_tier", "pnop_host_tier_stats",
+    "pnop_two_level_counts", "pnop_mode_energy", "pnop_energy", "pnop_inner", "pnop_apply", "pnop_set_timeout",
     "pnop_sync", "pnop_profile", "pnop_profile_read", "pnop_revolve_counts", "pnop_context_bytes",
     "pnop_energy_noalloc", "pnop_last_error", "pnop_error_string", "pnop_destroy",
 )
@@ -58,6 +57,7 @@ def _load():
         "pnop_step_forward": (c_int, [c_void_p, c_void_p, c_double, c_int]),
         "pnop_step_adjoint": (c_int, [c_void_p, c_void_p, c_void_p, c_double]),
         "pnop_gradient": (c_int, [c_void_p, c_void_p, c_double, c_double, c_void_p, POINTER(c_double)]),
+        "pnop_gradient_continuous": (c_int, [c_void_p, c_void_p, c_double, c_double, c_void_p, POINTER(c_double)]),
         "pnop_gradient_forward": (c_int, [c_void_p, c_void_p, c_double, c_double, POINTER(c_double), POINTER(c_double)]),
         "pnop_gradient_backward": (c_int, [c_void_p, c_double, c_int, c_void_p]),
         "pnop_gradient_host": (c_int, [c_void_p, c_void_p, c_double, c_double, c_void_p, POINTER(c_double)]),
@@ -200,6 +200,12 @@ class Context:
         gain = c_double()
         self._check(lib.pnop_gradient(self._h, c_void_p(_ptr(u0)), E0, horizon, c_void_p(_ptr(grad_out)),
                                       byref(gain)), "gradient")
+        return gain.value
+
+    def pnop_gradient_continuous(self, u0, E0, horizon, grad_out):
+        gain = c_double()
+        self._check(lib.pnop_gradient_continuous(self._h, c_void_p(_ptr(u0)), E0, horizon,
+                                                 c_void_p(_ptr(grad_out)), byref(gain)), "gradient_continuous")
         return gain.value
 
     def pnop_gradient_forward(self, u0, E0, horizon):

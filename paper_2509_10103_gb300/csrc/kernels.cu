@@ -143,6 +143,41 @@ __global__ void k_baseT(Geo g, const double2* __restrict__ nb, double2* __restri
     ub[o + 2 * S] = make_double2(-a * nz.y, a * nz.x);
 }
 
+// Velocity-gradient tensor in cylindrical components, G[3 i + j] = (grad u)_ij:
+// (d_r u_j), ((im u_r - u_theta)/r, (im u_theta + u_r)/r, im u_z / r), (i k_z u_j).
+__global__ void k_grad_u(Geo g, const double2* __restrict__ u, double2* __restrict__ G) {
+    Idx d;
+    if (!decode(g, d)) return;
+    const size_t o = sidx(g, d.j, d.im, d.k), S = d.S;
+    const double ir = g.invr[d.j], mr = d.m * ir, kz = d.k * g.kz0;
+    const double2 a = u[o], b = u[o + S], c = u[o + 2 * S];
+    const double* Bv = g.D1 + ((size_t)par_idx(d.m + 1) * g.nr + d.j) * kB;
+    const double* Bz = g.D1 + ((size_t)par_idx(d.m) * g.nr + d.j) * kB;
+    G[o] = band_row(g, Bv, u, d.j, d.im, d.k);
+    G[o + S] = band_row(g, Bv, u + S, d.j, d.im, d.k);
+    G[o + 2 * S] = band_row(g, Bz, u + 2 * S, d.j, d.im, d.k);
+    G[o + 3 * S] = make_double2(-mr * a.y - ir * b.x, mr * a.x - ir * b.y);
+    G[o + 4 * S] = make_double2(-mr * b.y + ir * a.x, mr * b.x + ir * a.y);
+    G[o + 5 * S] = make_double2(-mr * c.y, mr * c.x);
+    G[o + 6 * S] = make_double2(-kz * a.y, kz * a.x);
+    G[o + 7 * S] = make_double2(-kz * b.y, kz * b.x);
+    G[o + 8 * S] = make_double2(-kz * c.y, kz * c.x);
+}
+
+// Base-flow part of the continuous-adjoint forcing: N = U dw/dz - w_z dU/dr e_r
+__global__ void k_base_adj(Geo g, const double2* __restrict__ w, double2* __restrict__ N, double c, double s) {
+    Idx d;
+    if (!decode(g, d)) return;
+    double U, dU;
+    base_at(g, d.j, c, s, U, dU);
+    const size_t o = sidx(g, d.j, d.im, d.k), S = d.S;
+    const double a = d.k * g.kz0 * U;  // U d/dz = i a
+    const double2 wr = w[o], wt = w[o + S], wz = w[o + 2 * S];
+    N[o] = make_double2(-a * wr.y - dU * wz.x, a * wr.x - dU * wz.y);
+    N[o + S] = make_double2(-a * wt.y, a * wt.x);
+    N[o + 2 * S] = make_double2(-a * wz.y, a * wz.x);
+}
+
 // ------------------------------------------------------------------ radial stage (forward)
 // q = div F (rows j >= 1; q_0 = 0 is the tentative Neumann datum)
 __global__ void k_stage_div(Geo g, const double2* __restrict__ F, double2* __restrict__ q) {
@@ -755,6 +790,14 @@ void launch_curl(const Geo& g, const double2* u, double2* w, cudaStream_t s) {
 void launch_curlT_acc(const Geo& g, const double2* wb, double2* ub, cudaStream_t s) {
     k_curlT_acc<<<spec_grid(g), spec_bx(g), 0, s>>>(g, wb, ub);
     check_launch("curlT");
+}
+void launch_grad_u(const Geo& g, const double2* u, double2* G, cudaStream_t s) {
+    k_grad_u<<<spec_grid(g), spec_bx(g), 0, s>>>(g, u, G);
+    check_launch("grad_u");
+}
+void launch_base_adj(const Geo& g, const double2* w, double2* N, double c, double sn, cudaStream_t s) {
+    k_base_adj<<<spec_grid(g), spec_bx(g), 0, s>>>(g, w, N, c, sn);
+    check_launch("base_adj");
 }
 void launch_base(const Geo& g, const double2* u, double2* N, double c, double sn, cudaStream_t s) {
     k_base<<<spec_grid(g), spec_bx(g), 0, s>>>(g, u, N, c, sn);

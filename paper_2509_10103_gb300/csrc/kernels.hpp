@@ -33,10 +33,11 @@ struct Geo {
     double ewt;          // 2 pi Lz (energy weight prefactor)
 };
 
-// Up to 9 input / 6 output spectral component planes for the transforms; the
+// Up to 18 input / 6 output spectral component planes for the transforms; the
 // analysis adds add[i] (when not null) to output i.
+constexpr int kMaxIn = 18;
 struct FieldPtrs {
-    const double2* in[9];
+    const double2* in[kMaxIn];
     double2* out[6];
     const double2* add[6];
 };
@@ -44,9 +45,9 @@ struct FieldPtrs {
 // Per-field multipliers applied when forming the Hermitian z spectrum:
 // H_0 = h0 * Re(Y_0), H_k = hk * Y_k (k >= 1); per-output k-scales o0, ok.
 struct ZScales {
-    double h0[9], hk[9];
+    double h0[kMaxIn], hk[kMaxIn];
     double o0[6], ok[6];
-    float fh0[9], fhk[9], fo0[6], fok[6];  // FP32 copies, filled by launch_zpass
+    float fh0[kMaxIn], fhk[kMaxIn], fo0[6], fok[6];  // FP32 copies, filled by launch_zpass
 };
 
 // Twiddle tables e^{-2 pi i n / N} for N = nt and N = nzp, FP64 and FP32.
@@ -57,11 +58,19 @@ struct Twiddles {
     const float2* z_f;
 };
 
-enum ZMode { ZFWD = 0, ZADJ = 1 };
+// ZFWD: u, w -> u x w (6 -> 3 fields); ZADJ: u, w, g -> w x g, g x u (9 -> 6),
+// the transpose; ZCADJ: u, curl w, w, grad u -> -u x curl w - 2 (grad u) . w
+// (18 -> 3), the perturbation forcing of the continuous adjoint.
+enum ZMode { ZFWD = 0, ZADJ = 1, ZCADJ = 2 };
 
 // ---- spectral FP64 kernels ----
 void launch_curl(const Geo& g, const double2* u, double2* w, cudaStream_t s);
 void launch_curlT_acc(const Geo& g, const double2* wb, double2* ub, cudaStream_t s);
+// continuous adjoint: G[3 i + j] = (grad u)_ij (9 component planes, i the
+// derivative direction), and the base-flow part of its forcing
+// Nb = U dw/dz - w_z dU/dr e_r (written)
+void launch_grad_u(const Geo& g, const double2* u, double2* G, cudaStream_t s);
+void launch_base_adj(const Geo& g, const double2* w, double2* N, double c, double sn, cudaStream_t s);
 // base-flow terms in advective form: N = -U du/dz - u_r dU/dr e_z, and their
 // transpose ub = (dN/du)^T nb (both written, not accumulated)
 void launch_base(const Geo& g, const double2* u, double2* N, double c, double sn, cudaStream_t s);

@@ -107,6 +107,11 @@ struct pnop_ctx {
     const double2* cur = nullptr;
     double2* uN = nullptr;
     double2 *opt_g = nullptr, *opt_u = nullptr;  // adjoint looping: gradient, trial point
+    // continuous adjoint (allocated on first use): physical scratch for 18 fields,
+    // grad u (9 component planes), the later forward state u^{n+1}
+    void* Y3 = nullptr;
+    double2 *Gu = nullptr, *cprev = nullptr;
+    bool continuous = false;  // run_plan takes the continuous adjoint step
     // second checkpoint level in pinned host memory (two-level schedule)
     long long host_max = 0;            // host slots allowed (0: single level)
     double host_ratio = 0;             // T_io / T_step of Eq. 2.21 (store + load of one field)
@@ -287,7 +292,7 @@ void wait_stream(pnop_ctx* c, const char* what) {
 namespace flops {
 constexpr double div = 36 + 12, bu = 3 * 36 + 24, rhs = 36 + 12 + 8, a0_mode = 72, finish = 20;
 constexpr double tfinish = 36, trhs_u = 3 * 36 + 30, trhs_f = 8, qbar = 36 + 8, tdiv = 36 + 12;
-constexpr double curl = 2 * 36 + 16, curlT = 2 * 36 + 20, base = 12;
+constexpr double curl = 2 * 36 + 16, curlT = 2 * 36 + 20, base = 12, grad_u = 3 * 36 + 24;
 }  // namespace flops
 
 // RB = explicit Crank-Nicolson half B u (old velocity only) on stream st
@@ -468,6 +473,65 @@ void nonlinearT(pnop_ctx* c, const double2* u, double t, const double2* nb, doub
     }
     transforms(c, f, 9, 6, pnop::ZADJ, sc, Y, cached ? 6 : 0, c->ev_base);
     run(c, PNOP_K_SPECTRAL, 1, flops::curlT * S, [&] { pnop::launch_curlT_acc(g, c->wb, ub, s); });
+}
+
+// ------------------------------------------------------------------ continuous adjoint
+// Forcing of the adjoint equation in backward time (Eq. 2.9, with w = -u_dagger):
+// N_adj(w; u, t) = U dw/dz - w_z dU/dr e_r + P[-u x curl w - 2 (grad u) . w];
+// the base-flow part on the side stream (queued by the caller when
+// base_queued), added by the analysis.
+void queue_base_adj(pnop_ctx* c, const double2* w, double t) {
+    const double ph = c->h.omega * t;
+    run(c, PNOP_K_SPECTRAL, 1, flops::base * c->S(),
+        [&] { pnop::launch_base_adj(c->geo, w, c->Nbase, std::cos(ph), std::sin(ph), c->side); }, c->side);
+    ck(cudaEventRecord(c->ev_base, c->side), "record");
+}
+
+void nonlinear_adj(pnop_ctx* c, const double2* w, const double2* u, double t, double2* N, bool base_queued = false) {
+    const Geo& g = c->geo;
+    const size_t S = c->S();
+    cudaStream_t s = c->stream;
+    if (!c->Y3) {
+        const size_t cz = mixed(c) ? sizeof(float2) : sizeof(double2);
+        c->Y3 = c->dalloc(18 * (size_t)g.nr * g.nt * g.nk * cz);
+    }
+    if (!c->Gu) c->Gu = (double2*)c->dalloc(9 * S * sizeof(double2));
+    if (!base_queued) {
+        fork_side(c);
+        queue_base_adj(c, w, t);
+    }
+    run(c, PNOP_K_SPECTRAL, 1, flops::curl * S, [&] { pnop::launch_curl(g, w, c->omega, s); });
+    run(c, PNOP_K_SPECTRAL, 1, flops::grad_u * S, [&] { pnop::launch_grad_u(g, u, c->Gu, s); });
+    pnop::FieldPtrs f{};
+    for (int i = 0; i < 3; ++i) {
+        f.in[i] = u + i * S;
+        f.in[3 + i] = c->omega + i * S;
+        f.in[6 + i] = w + i * S;
+        f.out[i] = N + i * S;
+        f.add[i] = c->Nbase + i * S;
+    }
+    for (int i = 0; i < 9; ++i) f.in[9 + i] = c->Gu + i * S;
+    pnop::ZScales sc{};
+    const double inv_n = 1.0 / ((double)g.nt * g.nzp);
+    for (int i = 0; i < 18; ++i) sc.h0[i] = sc.hk[i] = 1.0;
+    for (int i = 0; i < 3; ++i) sc.o0[i] = sc.ok[i] = inv_n;
+    transforms(c, f, 18, 3, pnop::ZCADJ, sc, c->Y3, 0, c->ev_base);
+}
+
+// w(t_now) from w(t_next = t_now + dt): the predictor-corrector of the forward
+// step run backward in time, forcing N_adj at (u_next, t_next) for the
+// predictor and at (u_now, t_now) for the corrector; S is the same stage map.
+void cadj_step(pnop_ctx* c, const double2* u_next, double t_next, const double2* u_now, double t_now,
+               const double2* w, double2* out) {
+    fork_side(c);
+    queue_base_adj(c, w, t_next);
+    stage_bu(c, w, c->RB, c->side);
+    ck(cudaEventRecord(c->ev_bu, c->side), "record");
+    nonlinear_adj(c, w, u_next, t_next, c->N0, true);
+    stage(c, c->RB, c->N0, c->us, nullptr, c->ev_bu);
+    nonlinear_adj(c, c->us, u_now, t_now, c->N1);
+    axpby(c, 0.5, c->N1, -0.5, c->N0, c->N1);
+    stage(c, nullptr, c->N1, out, c->us, nullptr);
 }
 
 // ------------------------------------------------------------------ steps
@@ -695,7 +759,13 @@ size_t run_plan(pnop_ctx* c, size_t from, bool stop_at_adjoint, const double2** 
             *state = st;
             return i;
         }
-        adj_step(c, st, c->h.ph.tau0 + a.start * c->h.ph.dt, c->lamA, c->lamB);
+        const double tn = c->h.ph.tau0 + a.start * c->h.ph.dt;
+        if (c->continuous) {
+            cadj_step(c, c->cprev, tn + c->h.ph.dt, st, tn, c->lamA, c->lamB);
+            ck(cudaMemcpyAsync(c->cprev, st, c->field_bytes(), cudaMemcpyDeviceToDevice, c->stream), "keep state");
+        } else {
+            adj_step(c, st, tn, c->lamA, c->lamB);
+        }
         std::swap(c->lamA, c->lamB);
         ++c->st_adj;
     }
@@ -845,6 +915,29 @@ void gradient_backward(pnop_ctx* c, double gE, bool euclidean, double2* grad) {
     run_plan(c, c->plan_pos, false, &st);
     if (euclidean) ck(cudaMemcpyAsync(grad, c->lamA, c->field_bytes(), cudaMemcpyDeviceToDevice, c->stream), "copy");
     else weight(c, c->lamA, grad, 1);
+    wait_stream(c, "gradient sync");
+}
+
+// Backward part with the continuous adjoint: w(T) = u_N (compatibility
+// condition Eq. 2.8, w = -u_dagger), integrated back over the same schedule;
+// w(tau0) is the gradient in the energy inner product.
+void gradient_backward_continuous(pnop_ctx* c, double2* grad) {
+    if (!c->pending) throw Status(PNOP_ERR_INVALID_ARG, "no pending gradient forward on this context");
+    c->pending = false;
+    if (!c->cprev) c->cprev = c->field();
+    const size_t fb = c->field_bytes();
+    ck(cudaMemcpyAsync(c->lamA, c->uN, fb, cudaMemcpyDeviceToDevice, c->stream), "terminal");
+    ck(cudaMemcpyAsync(c->cprev, c->uN, fb, cudaMemcpyDeviceToDevice, c->stream), "terminal state");
+    const double2* st = nullptr;
+    c->continuous = true;
+    try {
+        run_plan(c, c->plan_pos, false, &st);
+    } catch (...) {
+        c->continuous = false;
+        throw;
+    }
+    c->continuous = false;
+    ck(cudaMemcpyAsync(grad, c->lamA, fb, cudaMemcpyDeviceToDevice, c->stream), "copy");
     wait_stream(c, "gradient sync");
 }
 
@@ -1153,6 +1246,18 @@ int pnop_gradient(pnop_ctx* ctx, const void* u0, double E0, double horizon, void
     });
 }
 
+int pnop_gradient_continuous(pnop_ctx* ctx, const void* u0, double E0, double horizon, void* grad_out,
+                             double* gain_out) {
+    return guarded(ctx, [&]() -> int {
+        if (!u0 || !grad_out) throw Status(PNOP_ERR_INVALID_ARG, "bad arguments");
+        double ET = 0, Einit = 0;
+        gradient_forward(ctx, (const double2*)u0, E0, horizon, &ET, &Einit);
+        gradient_backward_continuous(ctx, (double2*)grad_out);
+        if (gain_out) *gain_out = ET / Einit;
+        return PNOP_OK;
+    });
+}
+
 int pnop_gradient_forward(pnop_ctx* ctx, const void* u0, double E0, double horizon, double* ET_out, double* E0_out) {
     return guarded(ctx, [&]() -> int {
         if (!u0 || !ET_out) throw Status(PNOP_ERR_INVALID_ARG, "bad arguments");
@@ -1259,6 +1364,10 @@ int pnop_apply(pnop_ctx* ctx, int op, const void* a, const void* b, void* out, d
                 break;
             case PNOP_OP_STAGE_T_U: stageT(ctx, A, O, 0, ctx->Fb); break;
             case PNOP_OP_STAGE_T_F: stageT(ctx, A, ctx->ua, 0, O); break;
+            case PNOP_OP_NONLINEAR_ADJ:
+                if (!B) throw Status(PNOP_ERR_INVALID_ARG, "b (the adjoint field) is required");
+                nonlinear_adj(ctx, B, A, t, O);
+                break;
             case PNOP_OP_PROJECT:
                 ck(cudaMemcpyAsync(O, A, ctx->field_bytes(), cudaMemcpyDeviceToDevice, ctx->stream), "copy");
                 project(ctx, O);

@@ -142,6 +142,27 @@ __global__ void k_synth_theta(Geo g, FieldPtrs f, T2* __restrict__ Y, const T2* 
     }
 }
 
+// Products of the continuous-adjoint forcing at one physical point from the
+// packed columns (u_r, u_theta), (u_z, o_r), (o_theta, o_z), (w_r, w_theta),
+// (w_z, G_rr), (G_rtheta, G_rz), (G_thetar, G_thetatheta), (G_thetaz, G_zr),
+// (G_ztheta, G_zz), o = curl w, G = grad u:
+//   P = -u x o - 2 G . w,  (G . w)_i = sum_j G_ij w_j;  out: (P_r, P_theta), (P_z, 0)
+template <class T2>
+__device__ __forceinline__ void cadj_products(const T2* row, T2* out) {
+    using T = typename RealOf<T2>::T;
+    const T ur = row[0].x, ut = row[0].y, uz = row[1].x;
+    const T orr = row[1].y, ot = row[2].x, oz = row[2].y;
+    const T wr = row[3].x, wt = row[3].y, wz = row[4].x;
+    const T Grr = row[4].y, Grt = row[5].x, Grz = row[5].y;
+    const T Gtr = row[6].x, Gtt = row[6].y, Gtz = row[7].x;
+    const T Gzr = row[7].y, Gzt = row[8].x, Gzz = row[8].y;
+    const T pr = -(ut * oz - uz * ot) - (T)2 * (Grr * wr + Grt * wt + Grz * wz);
+    const T pt = -(uz * orr - ur * oz) - (T)2 * (Gtr * wr + Gtt * wt + Gtz * wz);
+    const T pz = -(ur * ot - ut * orr) - (T)2 * (Gzr * wr + Gzt * wt + Gzz * wz);
+    out[0] = mk<T2>(pr, pt);
+    out[1] = mk<T2>(pz, 0);
+}
+
 // ------------------------------------------------------------------ z pass + products
 // One block per (j, theta_a) row.  The Hermitian z spectra of two real fields
 // are packed into one complex inverse FFT; the pointwise products of the
@@ -152,9 +173,9 @@ __global__ void k_synth_theta(Geo g, FieldPtrs f, T2* __restrict__ Y, const T2* 
 template <class T2, int MODE>
 __global__ void k_zpass(Geo g, const T2* __restrict__ Y, T2* __restrict__ Z, ZScales sc, const T2* __restrict__ twg) {
     using T = typename RealOf<T2>::T;
-    constexpr int NIN = MODE == ZFWD ? 6 : 9;
+    constexpr int NIN = MODE == ZFWD ? 6 : (MODE == ZADJ ? 9 : 18);
     constexpr int NPI = (NIN + 1) / 2;
-    constexpr int NOUT = MODE == ZFWD ? 3 : 6;
+    constexpr int NOUT = MODE == ZADJ ? 6 : 3;
     constexpr int NPO = (NOUT + 1) / 2;
     constexpr int LD = NPI;  // NPI >= NPO
     extern __shared__ __align__(16) unsigned char smem[];
@@ -199,6 +220,8 @@ __global__ void k_zpass(Geo g, const T2* __restrict__ Y, T2* __restrict__ Z, ZSc
         if (MODE == ZFWD) {
             o[0] = mk<T2>(ut * wz - uz * wt, uz * wr - ur * wz);
             o[1] = mk<T2>(ur * wt - ut * wr, 0);
+        } else if (MODE == ZCADJ) {
+            cadj_products<T2>(row, o);
         } else {
             const T gr = row[3].x, gt = row[3].y, gz = row[4].x;
             // w x g
@@ -499,9 +522,9 @@ template <class T2, int MODE, int N1, int N2>
 __global__ void k_zpass2(Geo g, const T2* __restrict__ Y, T2* __restrict__ Z, ZScales sc, const T2* __restrict__ twg) {
     using T = typename RealOf<T2>::T;
     constexpr int N = N1 * N2, NP = N + N1;
-    constexpr int NIN = MODE == ZFWD ? 6 : 9;
+    constexpr int NIN = MODE == ZFWD ? 6 : (MODE == ZADJ ? 9 : 18);
     constexpr int NPI = (NIN + 1) / 2;
-    constexpr int NOUT = MODE == ZFWD ? 3 : 6;
+    constexpr int NOUT = MODE == ZADJ ? 6 : 3;
     constexpr int NPO = (NOUT + 1) / 2;
     extern __shared__ __align__(16) unsigned char smem[];
     T2* col = reinterpret_cast<T2*>(smem);  // [NPI][NP]
@@ -556,6 +579,15 @@ __global__ void k_zpass2(Geo g, const T2* __restrict__ Y, T2* __restrict__ Z, ZS
     // pointwise products, in place (each slot read and written by one thread)
     for (int s = threadIdx.x; s < N; s += blockDim.x) {
         const int o = at(s);
+        if constexpr (MODE == ZCADJ) {
+            T2 row[NPI], res[2];
+#pragma unroll
+            for (int p = 0; p < NPI; ++p) row[p] = col[p * NP + o];
+            cadj_products<T2>(row, res);
+            col[o] = res[0];
+            col[NP + o] = res[1];
+            continue;
+        }
         const T2 c0 = col[o], c1 = col[NP + o], c2 = col[2 * NP + o];
         const T ur = c0.x, ut = c0.y, uz = c1.x;
         const T wr = c1.y, wt = c2.x, wz = c2.y;
@@ -716,7 +748,7 @@ static unsigned zpass_threads(const Geo& g) {
 
 template <class T2, int MODE, int N1, int N2>
 static void zpass2(const Geo& g, const T2* Y, T2* Z, const ZScales& sc, const T2* tw, cudaStream_t s) {
-    constexpr int NPI = MODE == ZFWD ? 3 : 5;
+    constexpr int NPI = MODE == ZFWD ? 3 : (MODE == ZADJ ? 5 : 9);
     const size_t sm = (size_t)(NPI * (N1 * N2 + N1) + N1 * N2) * sizeof(T2);
     static bool attr = false;
     if (!attr) {
@@ -735,10 +767,22 @@ static bool zpass2_any(const Geo& g, const T2* Y, T2* Z, const ZScales& sc, cons
     }
 }
 
+template <class T2, int MODE>
+static void zpass_stockham(const Geo& g, const T2* Y, T2* Z, const ZScales& sc, const T2* tw, cudaStream_t s) {
+    constexpr int LD = MODE == ZFWD ? 3 : (MODE == ZADJ ? 5 : 9);
+    const size_t sm = (size_t)(2 * g.nzp * LD + g.nzp) * sizeof(T2);
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_zpass<T2, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        attr = true;
+    }
+    k_zpass<T2, MODE><<<dim3(g.nt, g.nr), zpass_threads(g), sm, s>>>(g, Y, Z, sc, tw);
+}
+
 template <class T2>
 void launch_zpass(const Geo& g, int mode, const T2* Y, T2* Z, const ZScales& sc_in, const Twiddles& tw, cudaStream_t s) {
     ZScales sc = sc_in;
-    for (int i = 0; i < 9; ++i) {
+    for (int i = 0; i < kMaxIn; ++i) {
         sc.fh0[i] = (float)sc.h0[i];
         sc.fhk[i] = (float)sc.hk[i];
     }
@@ -746,33 +790,18 @@ void launch_zpass(const Geo& g, int mode, const T2* Y, T2* Z, const ZScales& sc_
         sc.fo0[i] = (float)sc.o0[i];
         sc.fok[i] = (float)sc.ok[i];
     }
+    const T2* t = tw_z<T2>(tw);
     // FP64 z passes stay on the Stockham kernel: they are bound by the FP64
     // pipe, where the register kernel's lower occupancy measured slower.
     bool done = false;
     if constexpr (std::is_same<T2, float2>::value)
-        done = mode == ZFWD ? zpass2_any<T2, ZFWD>(g, Y, Z, sc, tw_z<T2>(tw), s)
-                            : zpass2_any<T2, ZADJ>(g, Y, Z, sc, tw_z<T2>(tw), s);
-    if (done) {
-        check_launch("zpass");
-        return;
-    }
-    const int ld = mode == ZFWD ? 3 : 5;
-    const size_t sm = (size_t)(2 * g.nzp * ld + g.nzp) * sizeof(T2);
-    dim3 grid(g.nt, g.nr);
-    if (mode == ZFWD) {
-        static bool attr = false;
-        if (!attr) {
-            cudaFuncSetAttribute(k_zpass<T2, ZFWD>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-            attr = true;
-        }
-        k_zpass<T2, ZFWD><<<grid, zpass_threads(g), sm, s>>>(g, Y, Z, sc, tw_z<T2>(tw));
-    } else {
-        static bool attr = false;
-        if (!attr) {
-            cudaFuncSetAttribute(k_zpass<T2, ZADJ>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-            attr = true;
-        }
-        k_zpass<T2, ZADJ><<<grid, zpass_threads(g), sm, s>>>(g, Y, Z, sc, tw_z<T2>(tw));
+        done = mode == ZFWD ? zpass2_any<T2, ZFWD>(g, Y, Z, sc, t, s)
+                            : (mode == ZADJ ? zpass2_any<T2, ZADJ>(g, Y, Z, sc, t, s)
+                                            : zpass2_any<T2, ZCADJ>(g, Y, Z, sc, t, s));
+    if (!done) {
+        if (mode == ZFWD) zpass_stockham<T2, ZFWD>(g, Y, Z, sc, t, s);
+        else if (mode == ZADJ) zpass_stockham<T2, ZADJ>(g, Y, Z, sc, t, s);
+        else zpass_stockham<T2, ZCADJ>(g, Y, Z, sc, t, s);
     }
     check_launch("zpass");
 }

@@ -333,3 +333,51 @@ def test_mixed_precision_error_budget(L):
     assert abs(gain / G - 1) <= 1e-5
     assert cos >= 0.99999
 
+
+
+@pytest.mark.parametrize("case", ["small", "ragged"])
+def test_continuous_adjoint_forcing(case, request, L):
+    c = request.getfixturevalue(case)
+    u = c.field(31, 1e-2)
+    w = c.field(32, 1.0)
+    t = c.tau0 + 0.23
+    out = c.zeros()
+    c.ctx.pnop_apply(L.OP_NONLINEAR_ADJ, dev(u), dev(w), out, t)
+    assert rel(host(out), c.o.nonlinear_adj(w, u, t)) < 1e-12
+
+
+def test_continuous_adjoint_forcing_two_pass(two_pass, two_pass_mixed, L):
+    c = two_pass
+    u = c.field(33, 1e-2)
+    w = c.field(34, 1.0)
+    t = c.tau0 + 0.41
+    ref = c.o.nonlinear_adj(w, u, t)
+    for cc, tol in ((c, 1e-12), (two_pass_mixed, 1e-5)):
+        out = cc.zeros()
+        cc.ctx.pnop_apply(L.OP_NONLINEAR_ADJ, dev(u), dev(w), out, t)
+        assert rel(host(out), ref) < tol
+
+
+@pytest.mark.parametrize("case", ["small", "ragged"])
+def test_continuous_adjoint_gradient(case, request, L):
+    c = request.getfixturevalue(case)
+    u0 = c.field(35, 1e-2)
+    n = 8
+    ET, gref = c.o.gradient_continuous(u0, c.tau0, n)
+    g = c.zeros()
+    gain = c.ctx.pnop_gradient_continuous(dev(u0), -1.0, n * c.o.p.dt, g)
+    assert abs(gain / (ET / c.o.energy(u0)) - 1) < TOL
+    assert rel(host(g), gref) < TOL
+
+
+def test_continuous_adjoint_gradient_mixed_precision(L):
+    c = Case(L, nr=32, M=7, K=15, Lz=10.0, Re=2000.0, dt=0.01, precision=1)
+    u0 = c.field(0, 1e-6)
+    n = 30
+    ET, gref = c.o.gradient_continuous(u0, 0.0, n)
+    g = c.zeros()
+    gain = c.ctx.pnop_gradient_continuous(dev(u0), -1.0, n * 0.01, g)
+    gh = host(g)
+    cos = c.o.inner(gh, gref) / math.sqrt(c.o.inner(gh, gh) * c.o.inner(gref, gref))
+    assert abs(gain / (ET / c.o.energy(u0)) - 1) <= 1e-5
+    assert cos >= 0.99999
