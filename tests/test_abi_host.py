@@ -105,3 +105,16 @@ def test_two_level_schedule_minimises_eq_2_21(L):
     assert adv == 100 and nf >= 98
     # no host slots: the single-level schedule (Eq. 2.18 + the terminal step)
     assert L.pnop_two_level_counts(100, 4, 0, 0.0) == (0, po.revolve_advances(100, 4) + 1)
+
+
+def test_new_entry_points_reject_bad_arguments_without_a_device(L):
+    import ctypes
+    st = L.pnop_opt_stats()
+    assert L.lib.pnop_optimise(None, None, 1e-3, 1.0, 5, 1e-8, None, ctypes.byref(st)) == -1
+    assert L.lib.pnop_set_host_tier(None, 4, 0.0) == -1
+    assert L.lib.pnop_host_tier_stats(None, None, None, None, None) == -1
+    assert L.lib.pnop_mode_energy(None, None, None) == -1
+    assert L.lib.pnop_gradient_continuous(None, None, 1e-3, 1.0, None, None) == -1
+    nf, adv = ctypes.c_int(), ctypes.c_longlong()
+    for args in ((0, 2, 4, 0.0), (10, 0, 4, 0.0), (10, 2, -1, 0.0), (10, 2, 4, -1.0), (10, 2, 4, float("nan"))):
+        assert L.lib.pnop_two_level_counts(*args, ctypes.byref(nf), ctypes.byref(adv)) == -1
