@@ -5,7 +5,10 @@
 #include <cuda_runtime.h>
 
 #include <cstdio>
+#include <mutex>
+#include <set>
 #include <stdexcept>
+#include <utility>
 
 namespace pnop {
 
@@ -56,5 +59,18 @@ static inline void check_launch(const char* what) {
     }
 }
 static inline unsigned nblk(size_t n, int bs) { return (unsigned)((n + bs - 1) / bs); }
+
+// Raises the dynamic shared-memory limit of a kernel to 200 KB once per
+// (kernel, device): the attribute is per device, and launches come from
+// several host threads (the serving layer) and several devices.
+inline void smem_limit(const void* kernel) {
+    static std::mutex mu;
+    static std::set<std::pair<const void*, int>> done;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lock(mu);
+    if (done.insert({kernel, dev}).second)
+        cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+}
 
 }  // namespace pnop

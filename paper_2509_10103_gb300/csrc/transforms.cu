@@ -658,11 +658,7 @@ template <class T2> static int theta_kb(const Geo& g) {
 template <class T2, int KB>
 static void synth_theta_kb(const Geo& g, const FieldPtrs& f, int nfield, T2* Y, const T2* tw, cudaStream_t s) {
     const size_t sm = (size_t)(2 * g.nt * KB + g.nt) * sizeof(T2);
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(k_synth_theta<T2, KB>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        attr = true;
-    }
+    smem_limit((const void*)k_synth_theta<T2, KB>);
     dim3 grid((g.nk + KB - 1) / KB, g.nr, nfield);
     k_synth_theta<T2, KB><<<grid, 256, sm, s>>>(g, f, Y, tw);
 }
@@ -670,11 +666,7 @@ static void synth_theta_kb(const Geo& g, const FieldPtrs& f, int nfield, T2* Y, 
 template <class T2, int KB>
 static void anal_theta_kb(const Geo& g, const FieldPtrs& f, int nfield, const T2* Z, const T2* tw, cudaStream_t s) {
     const size_t sm = (size_t)(2 * g.nt * KB + g.nt) * sizeof(T2);
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(k_anal_theta<T2, KB>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        attr = true;
-    }
+    smem_limit((const void*)k_anal_theta<T2, KB>);
     dim3 grid((g.nk + KB - 1) / KB, g.nr, nfield);
     k_anal_theta<T2, KB><<<grid, 256, sm, s>>>(g, f, Z, tw);
 }
@@ -685,22 +677,14 @@ static void anal_theta_kb(const Geo& g, const FieldPtrs& f, int nfield, const T2
 template <class T2, int KB, int N1, int N2>
 static void synth2(const Geo& g, const FieldPtrs& f, int nfield, T2* Y, const T2* tw, cudaStream_t s) {
     const size_t sm = (size_t)(N1 * N2 * KB + N1 * N2) * sizeof(T2);
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(k_synth2<T2, KB, N1, N2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        attr = true;
-    }
+    smem_limit((const void*)k_synth2<T2, KB, N1, N2>);
     dim3 grid((g.nk + KB - 1) / KB, g.nr, nfield);
     k_synth2<T2, KB, N1, N2><<<grid, 128, sm, s>>>(g, f, Y, tw);
 }
 template <class T2, int KB, int N1, int N2>
 static void anal2(const Geo& g, const FieldPtrs& f, int nfield, const T2* Z, const T2* tw, cudaStream_t s) {
     const size_t sm = (size_t)(N1 * N2 * KB + N1 * N2) * sizeof(T2);
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(k_anal2<T2, KB, N1, N2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        attr = true;
-    }
+    smem_limit((const void*)k_anal2<T2, KB, N1, N2>);
     dim3 grid((g.nk + KB - 1) / KB, g.nr, nfield);
     k_anal2<T2, KB, N1, N2><<<grid, 128, sm, s>>>(g, f, Z, tw);
 }
@@ -750,11 +734,7 @@ template <class T2, int MODE, int N1, int N2>
 static void zpass2(const Geo& g, const T2* Y, T2* Z, const ZScales& sc, const T2* tw, cudaStream_t s) {
     constexpr int NPI = MODE == ZFWD ? 3 : (MODE == ZADJ ? 5 : 9);
     const size_t sm = (size_t)(NPI * (N1 * N2 + N1) + N1 * N2) * sizeof(T2);
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(k_zpass2<T2, MODE, N1, N2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        attr = true;
-    }
+    smem_limit((const void*)k_zpass2<T2, MODE, N1, N2>);
     k_zpass2<T2, MODE, N1, N2><<<dim3(g.nt, g.nr), zpass_threads(g), sm, s>>>(g, Y, Z, sc, tw);
 }
 template <class T2, int MODE>
@@ -771,11 +751,7 @@ template <class T2, int MODE>
 static void zpass_stockham(const Geo& g, const T2* Y, T2* Z, const ZScales& sc, const T2* tw, cudaStream_t s) {
     constexpr int LD = MODE == ZFWD ? 3 : (MODE == ZADJ ? 5 : 9);
     const size_t sm = (size_t)(2 * g.nzp * LD + g.nzp) * sizeof(T2);
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(k_zpass<T2, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        attr = true;
-    }
+    smem_limit((const void*)k_zpass<T2, MODE>);
     k_zpass<T2, MODE><<<dim3(g.nt, g.nr), zpass_threads(g), sm, s>>>(g, Y, Z, sc, tw);
 }
 
