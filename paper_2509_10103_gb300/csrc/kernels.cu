@@ -77,7 +77,7 @@ __global__ void k_curl(Geo g, const double2* __restrict__ u, double2* __restrict
     Idx d;
     if (!decode(g, d)) return;
     const double2 *ur = u, *ut = u + d.S, *uz = u + 2 * d.S;
-    const double kz = d.k * g.kz0, ir = g.invr[d.j], mr = d.m * ir;
+    const double kz = __ldg(g.kzt + d.k), ir = g.invr[d.j], mr = __ldg(g.mrt + (size_t)d.im * g.nr + d.j);
     const size_t o = sidx(g, d.j, d.im, d.k);
     const double2 dz = band_row(g, g.D1 + ((size_t)par_idx(d.m) * g.nr + d.j) * kB, uz, d.j, d.im, d.k);
     const double2 dt = band_row(g, g.D1 + ((size_t)par_idx(d.m + 1) * g.nr + d.j) * kB, ut, d.j, d.im, d.k);
@@ -91,7 +91,7 @@ __global__ void k_curlT_acc(Geo g, const double2* __restrict__ wb, double2* __re
     Idx d;
     if (!decode(g, d)) return;
     const double2 *wr = wb, *wt = wb + d.S, *wz = wb + 2 * d.S;
-    const double kz = d.k * g.kz0, ir = g.invr[d.j], mr = d.m * ir;
+    const double kz = __ldg(g.kzt + d.k), ir = g.invr[d.j], mr = __ldg(g.mrt + (size_t)d.im * g.nr + d.j);
     const size_t o = sidx(g, d.j, d.im, d.k);
     const double2 sT = band_col(g, g.D1 + (size_t)par_idx(d.m + 1) * g.nr * kB, wz, d.j, d.im, d.k);
     const double2 sP = band_col(g, g.D1 + (size_t)par_idx(d.m) * g.nr * kB, wt, d.j, d.im, d.k);
@@ -122,7 +122,7 @@ __global__ void k_base(Geo g, const double2* __restrict__ u, double2* __restrict
     double U, dU;
     base_at(g, d.j, c, s, U, dU);
     const size_t o = sidx(g, d.j, d.im, d.k), S = d.S;
-    const double a = d.k * g.kz0 * U;  // -U d/dz = -i a
+    const double a = __ldg(g.kzt + d.k) * U;  // -U d/dz = -i a
     const double2 ur = u[o], ut = u[o + S], uz = u[o + 2 * S];
     N[o] = make_double2(a * ur.y, -a * ur.x);
     N[o + S] = make_double2(a * ut.y, -a * ut.x);
@@ -136,7 +136,7 @@ __global__ void k_baseT(Geo g, const double2* __restrict__ nb, double2* __restri
     double U, dU;
     base_at(g, d.j, c, s, U, dU);
     const size_t o = sidx(g, d.j, d.im, d.k), S = d.S;
-    const double a = d.k * g.kz0 * U;
+    const double a = __ldg(g.kzt + d.k) * U;
     const double2 nr_ = nb[o], nt = nb[o + S], nz = nb[o + 2 * S];
     ub[o] = make_double2(-a * nr_.y - dU * nz.x, a * nr_.x - dU * nz.y);
     ub[o + S] = make_double2(-a * nt.y, a * nt.x);
@@ -149,7 +149,7 @@ __global__ void k_grad_u(Geo g, const double2* __restrict__ u, double2* __restri
     Idx d;
     if (!decode(g, d)) return;
     const size_t o = sidx(g, d.j, d.im, d.k), S = d.S;
-    const double ir = g.invr[d.j], mr = d.m * ir, kz = d.k * g.kz0;
+    const double ir = g.invr[d.j], mr = __ldg(g.mrt + (size_t)d.im * g.nr + d.j), kz = __ldg(g.kzt + d.k);
     const double2 a = u[o], b = u[o + S], c = u[o + 2 * S];
     const double* Bv = g.D1 + ((size_t)par_idx(d.m + 1) * g.nr + d.j) * kB;
     const double* Bz = g.D1 + ((size_t)par_idx(d.m) * g.nr + d.j) * kB;
@@ -171,7 +171,7 @@ __global__ void k_base_adj(Geo g, const double2* __restrict__ w, double2* __rest
     double U, dU;
     base_at(g, d.j, c, s, U, dU);
     const size_t o = sidx(g, d.j, d.im, d.k), S = d.S;
-    const double a = d.k * g.kz0 * U;  // U d/dz = i a
+    const double a = __ldg(g.kzt + d.k) * U;  // U d/dz = i a
     const double2 wr = w[o], wt = w[o + S], wz = w[o + 2 * S];
     N[o] = make_double2(-a * wr.y - dU * wz.x, a * wr.x - dU * wz.y);
     N[o + S] = make_double2(-a * wt.y, a * wt.x);
@@ -188,7 +188,7 @@ __global__ void k_stage_div(Geo g, const double2* __restrict__ F, double2* __res
         q[o] = make_double2(0, 0);
         return;
     }
-    const double kz = d.k * g.kz0, ir = g.invr[d.j], mr = d.m * ir;
+    const double kz = __ldg(g.kzt + d.k), ir = g.invr[d.j], mr = __ldg(g.mrt + (size_t)d.im * g.nr + d.j);
     double2 acc = band_row(g, g.D1 + ((size_t)par_idx(d.m + 1) * g.nr + d.j) * kB, F, d.j, d.im, d.k);
     const double2 fr = F[o], ft = F[o + S], fz = F[o + 2 * S];
     acc.x += ir * fr.x - mr * ft.y - kz * fz.y;
@@ -338,7 +338,7 @@ __global__ void k_stage_bu(Geo g, const double2* __restrict__ u, double2* __rest
         RB[o] = RB[o + S] = RB[o + 2 * S] = make_double2(0, 0);
         return;
     }
-    const double kz = d.k * g.kz0, ir = g.invr[d.j];
+    const double ir = g.invr[d.j];
     const double* Lp = g.Lb + ((size_t)abs(d.m + 1) * g.nr + d.j) * kB;
     const double* Lz = g.Lb + ((size_t)abs(d.m) * g.nr + d.j) * kB;
     double2 tr = make_double2(0, 0), tt = make_double2(0, 0), sz = make_double2(0, 0);
@@ -355,11 +355,11 @@ __global__ void k_stage_bu(Geo g, const double2* __restrict__ u, double2* __rest
         tt = dfma(lp, ut[oc], tt);
         sz = dfma(__ldg(Lz + s), uz[oc], sz);
     }
-    const double dg = g.inv_dt - kz * kz * g.inv_2re;
+    const double dg = __ldg(g.dgt + d.k);
     const double2 a = ur[o], b = ut[o], c = uz[o];
     const double2 up = make_double2(a.x - b.y, a.y + b.x);
     const double2 um = make_double2(a.x + b.y, a.y - b.x);
-    const double fm = 4.0 * d.m * ir * ir;
+    const double fm = 4.0 * __ldg(g.mrt + (size_t)d.im * g.nr + d.j) * ir;
     const double2 sp = make_double2(tr.x - tt.y, tr.y + tt.x);
     const double2 sm = make_double2(tr.x + tt.y + fm * um.x, tr.y - tt.x + fm * um.y);
     RB[o] = make_double2(dg * up.x + g.inv_2re * sp.x, dg * up.y + g.inv_2re * sp.y);
@@ -377,7 +377,7 @@ __global__ void k_stage_rhs(Geo g, const double2* __restrict__ RB, const double2
         R[o] = R[o + S] = R[o + 2 * S] = make_double2(0, 0);
         return;
     }
-    const double kz = d.k * g.kz0, ir = g.invr[d.j], mr = d.m * ir;
+    const double kz = __ldg(g.kzt + d.k), mr = __ldg(g.mrt + (size_t)d.im * g.nr + d.j);
     const double2 dp = band_row(g, g.D1 + ((size_t)par_idx(d.m) * g.nr + d.j) * kB, p, d.j, d.im, d.k);
     const double2 pj = p[o], fr0 = F[o], ft0 = F[o + S], fz0 = F[o + 2 * S];
     const double2 fr = make_double2(fr0.x - dp.x, fr0.y - dp.y);
@@ -517,8 +517,7 @@ __global__ void k_stageT_rhs(Geo g, const double2* __restrict__ X, const double2
     const size_t o = sidx(g, d.j, d.im, d.k), S = d.S;
     const double2 rp = X[o], rm = X[o + S], rz = X[o + 2 * S];
     if (ub) {
-        const double kz = d.k * g.kz0;
-        const double dg = g.inv_dt - kz * kz * g.inv_2re;
+        const double dg = __ldg(g.dgt + d.k);
         const double2 bp0 = band_col(g, g.Lb + (size_t)abs(d.m + 1) * g.nr * kB, X, d.j, d.im, d.k);
         const double2 bm0 = band_col(g, g.Lb + (size_t)abs(d.m - 1) * g.nr * kB, X + S, d.j, d.im, d.k);
         const double2 bz0 = band_col(g, g.Lb + (size_t)abs(d.m) * g.nr * kB, X + 2 * S, d.j, d.im, d.k);
@@ -562,7 +561,7 @@ __global__ void k_stageT_qbar(Geo g, const double2* __restrict__ Fb, double2* __
         q[o] = make_double2(0, 0);
         return;
     }
-    const double kz = d.k * g.kz0, mr = d.m * g.invr[d.j];
+    const double kz = __ldg(g.kzt + d.k), mr = __ldg(g.mrt + (size_t)d.im * g.nr + d.j);
     double2 acc = band_col(g, g.D1 + (size_t)par_idx(d.m) * g.nr * kB, Fb, d.j, d.im, d.k);
     const double2 ft = Fb[o + S], fz = Fb[o + 2 * S];
     acc.x += mr * ft.y + kz * fz.y;
@@ -576,7 +575,7 @@ __global__ void k_stageT_div(Geo g, const double2* __restrict__ z, double2* __re
     if (!decode(g, d)) return;
     if (d.m == 0 && d.k == 0) return;
     const size_t o = sidx(g, d.j, d.im, d.k), S = d.S;
-    const double kz = d.k * g.kz0, ir = g.invr[d.j], mr = d.m * ir;
+    const double kz = __ldg(g.kzt + d.k), ir = g.invr[d.j], mr = __ldg(g.mrt + (size_t)d.im * g.nr + d.j);
     const double2 dz = band_col(g, g.D1 + (size_t)par_idx(d.m + 1) * g.nr * kB, z, d.j, d.im, d.k);
     const double2 zj = z[o];
     double2 x = Fb[o];
@@ -625,7 +624,7 @@ __global__ void k_proj_div(Geo g, const double2* __restrict__ u, double2* __rest
         if (c >= 1 && c < g.nr) acc = dfma(__ldg(B + s), u[sidx(g, c, d.im, d.k)], acc);
     }
     if (d.j >= 1) {
-        const double ir = g.invr[d.j], mr = d.m * ir, kz = d.k * g.kz0;
+        const double ir = g.invr[d.j], mr = __ldg(g.mrt + (size_t)d.im * g.nr + d.j), kz = __ldg(g.kzt + d.k);
         const double2 a = u[o], b = u[o + S], c = u[o + 2 * S];
         acc.x += ir * a.x - mr * b.y - kz * c.y;
         acc.y += ir * a.y + mr * b.x + kz * c.x;
@@ -683,7 +682,7 @@ __global__ void k_proj_update(Geo g, double2* __restrict__ u, const double2* __r
         u[o + 2 * S] = make_double2(c.x - mu.x, c.y - mu.y);
         return;
     }
-    const double ir = g.invr[d.j], mr = d.m * ir, kz = d.k * g.kz0, wi = 1.0 / g.W[d.j];
+    const double ir = g.invr[d.j], mr = __ldg(g.mrt + (size_t)d.im * g.nr + d.j), kz = __ldg(g.kzt + d.k), wi = 1.0 / g.W[d.j];
     const double2 zj = z[o];
     double2 dr = band_col(g, g.D1 + (size_t)par_idx(d.m + 1) * g.nr * kB, z, d.j, d.im, d.k);
     dr.x += ir * zj.x;
@@ -814,18 +813,10 @@ static void launch_band_solve(const Geo& g, const double* fac, double2* X, const
     const unsigned nblocks = (unsigned)((helm ? 3 : 1) * g.nm * g.ntile);
     const size_t sm = (size_t)g.nr * kSK * sizeof(double2) + 2 * (size_t)kRC * 9 * kSK * sizeof(double);
     if (!zero_row0) {
-        static bool attr = false;
-        if (!attr) {
-            cudaFuncSetAttribute(k_band_solve<4, 8, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-            attr = true;
-        }
+        smem_limit((const void*)k_band_solve<4, 8, false>);
         k_band_solve<4, 8, false><<<nblocks, 2 * kSK, sm, s>>>(g, fac, X, add, helm, 0);
     } else {
-        static bool attr = false;
-        if (!attr) {
-            cudaFuncSetAttribute(k_band_solve<8, 4, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-            attr = true;
-        }
+        smem_limit((const void*)k_band_solve<8, 4, true>);
         k_band_solve<8, 4, true><<<nblocks, 2 * kSK, sm, s>>>(g, fac, X, add, helm, 1);
     }
 }

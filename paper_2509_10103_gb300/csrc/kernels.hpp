@@ -7,7 +7,7 @@ namespace pnop {
 
 // Systems per banded-solver block: consecutive k of one (component, m).  The
 // factor tables are tiled in k by the same count.
-constexpr int kSK = 16;
+constexpr int kSK = 32;
 
 // Read-only geometry and operators, passed to kernels by value.
 struct Geo {
@@ -31,6 +31,12 @@ struct Geo {
     const double2* Uh;   // [nr]
     const double2* dUh;  // [nr]
     double ewt;          // 2 pi Lz (energy weight prefactor)
+    // per-mode constants as tables, so that spectral kernels spend no FP64
+    // instruction on integer conversions: k_z = k kz0 [nk], m / r_j [nm][nr],
+    // 1/dt - k_z^2 / (2 Re) (the explicit Crank-Nicolson diagonal) [nk]
+    const double* kzt;
+    const double* mrt;
+    const double* dgt;
 };
 
 // Up to 18 input / 6 output spectral component planes for the transforms; the

@@ -71,6 +71,7 @@ struct pnop_ctx {
     double *d_facH = nullptr, *d_facP = nullptr, *d_infl = nullptr, *d_fluxg = nullptr;
     double *d_facHT = nullptr, *d_facPT = nullptr;
     double* d_projL = nullptr;  // admissible-projection factors, built on first use
+    double* d_dgt = nullptr;    // 1/dt - k_z^2/(2 Re) per k (depends on dt and Re)
     double* d_spec = nullptr;   // per-mode energies [2][nm][nk]
     double2 *d_Uh = nullptr, *d_dUh = nullptr;
     pnop::Twiddles tw{};
@@ -185,6 +186,14 @@ void upload_operators(pnop_ctx* c) {
         else ck(cudaMemcpy(dst, v.data(), v.size() * sizeof(double), cudaMemcpyHostToDevice), "upload");
     };
     put(c->d_Lb, h.Lb);
+    {
+        std::vector<double> dg(h.d.nk);
+        for (int k = 0; k < h.d.nk; ++k) {
+            const double kz = 2.0 * M_PI * k / h.d.Lz;
+            dg[k] = 1.0 / h.ph.dt - kz * kz / (2.0 * h.ph.Re);
+        }
+        put(c->d_dgt, dg);
+    }
     put(c->d_facH, h.facH);
     put(c->d_facP, h.facP);
     put(c->d_facHT, h.facHT);
@@ -203,6 +212,7 @@ void upload_operators(pnop_ctx* c) {
     g.inv_dt = 1.0 / h.ph.dt;
     g.inv_2re = 1.0 / (2.0 * h.ph.Re);
     g.Lb = c->d_Lb;
+    g.dgt = c->d_dgt;
     g.facH = c->d_facH;
     g.facP = c->d_facP;
     g.facHT = c->d_facHT;
@@ -1145,6 +1155,14 @@ int pnop_create(const pnop_grid* grid, const pnop_params* params, void* cuda_str
         g.invr = c->d_invr;
         g.W = c->d_W;
         g.D1 = c->d_D1;
+        {
+            std::vector<double> kz(d.nk), mr((size_t)d.nm * d.nr);
+            for (int k = 0; k < d.nk; ++k) kz[k] = k * g.kz0;
+            for (int im = 0; im < d.nm; ++im)
+                for (int j = 0; j < d.nr; ++j) mr[(size_t)im * d.nr + j] = (im - M) * c->h.invr[j];
+            g.kzt = c->upload(kz);
+            g.mrt = c->upload(mr);
+        }
         upload_operators(c);
         auto thd = twiddle_table<double2>(d.nth), zd = twiddle_table<double2>(d.nzp);
         auto thf = twiddle_table<float2>(d.nth), zf = twiddle_table<float2>(d.nzp);

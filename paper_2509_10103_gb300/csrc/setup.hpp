@@ -32,7 +32,7 @@ struct Physics {
 // every row come first, then the backward-sweep columns [nc1, kBand):
 //   table[mat][tile][part 0: j][e < nc1][kk] , [part 1: j][e - nc1][kk]
 // so a run of consecutive rows of one sweep is one contiguous piece.
-constexpr int kTileK = 16;
+constexpr int kTileK = 32;
 inline size_t fac_index(int mat, int k, int j, int e, int nr, int ntile, int nc1) {
     const size_t tile = ((size_t)mat * ntile + k / kTileK) * (size_t)nr * kBand * kTileK;
     const size_t in = e < nc1 ? ((size_t)j * nc1 + e) * kTileK
