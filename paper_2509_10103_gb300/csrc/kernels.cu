@@ -359,12 +359,13 @@ __global__ void k_stage_bu(Geo g, const double2* __restrict__ u, double2* __rest
     const double2 a = ur[o], b = ut[o], c = uz[o];
     const double2 up = make_double2(a.x - b.y, a.y + b.x);
     const double2 um = make_double2(a.x + b.y, a.y - b.x);
-    const double fm = 4.0 * __ldg(g.mrt + (size_t)d.im * g.nr + d.j) * ir;
+    // the bands hold L / (2 Re), so the 4m/r^2 diagonal difference carries the same factor
+    const double fm = 4.0 * g.inv_2re * __ldg(g.mrt + (size_t)d.im * g.nr + d.j) * ir;
     const double2 sp = make_double2(tr.x - tt.y, tr.y + tt.x);
     const double2 sm = make_double2(tr.x + tt.y + fm * um.x, tr.y - tt.x + fm * um.y);
-    RB[o] = make_double2(dg * up.x + g.inv_2re * sp.x, dg * up.y + g.inv_2re * sp.y);
-    RB[o + S] = make_double2(dg * um.x + g.inv_2re * sm.x, dg * um.y + g.inv_2re * sm.y);
-    RB[o + 2 * S] = make_double2(dg * c.x + g.inv_2re * sz.x, dg * c.y + g.inv_2re * sz.y);
+    RB[o] = make_double2(fma(dg, up.x, sp.x), fma(dg, up.y, sp.y));
+    RB[o + S] = make_double2(fma(dg, um.x, sm.x), fma(dg, um.y, sm.y));
+    RB[o + 2 * S] = make_double2(fma(dg, c.x, sz.x), fma(dg, c.y, sz.y));
 }
 
 // R_v = [RB_v +] F'_v for v = +, -, z (rows j >= 1), F' = F - grad p
@@ -521,9 +522,9 @@ __global__ void k_stageT_rhs(Geo g, const double2* __restrict__ X, const double2
         const double2 bp0 = band_col(g, g.Lb + (size_t)abs(d.m + 1) * g.nr * kB, X, d.j, d.im, d.k);
         const double2 bm0 = band_col(g, g.Lb + (size_t)abs(d.m - 1) * g.nr * kB, X + S, d.j, d.im, d.k);
         const double2 bz0 = band_col(g, g.Lb + (size_t)abs(d.m) * g.nr * kB, X + 2 * S, d.j, d.im, d.k);
-        const double2 bp = make_double2(dg * rp.x + g.inv_2re * bp0.x, dg * rp.y + g.inv_2re * bp0.y);
-        const double2 bm = make_double2(dg * rm.x + g.inv_2re * bm0.x, dg * rm.y + g.inv_2re * bm0.y);
-        const double2 bz = make_double2(dg * rz.x + g.inv_2re * bz0.x, dg * rz.y + g.inv_2re * bz0.y);
+        const double2 bp = make_double2(fma(dg, rp.x, bp0.x), fma(dg, rp.y, bp0.y));  // bands hold L / (2 Re)
+        const double2 bm = make_double2(fma(dg, rm.x, bm0.x), fma(dg, rm.y, bm0.y));
+        const double2 bz = make_double2(fma(dg, rz.x, bz0.x), fma(dg, rz.y, bz0.y));
         double2 vr = make_double2(bp.x + bm.x, bp.y + bm.y);
         double2 vt = make_double2(bp.y - bm.y, -bp.x + bm.x);
         double2 vz = bz;

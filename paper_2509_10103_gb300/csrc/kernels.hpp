@@ -19,7 +19,7 @@ struct Geo {
     const double* invr;
     const double* W;
     const double* D1;    // [2][nr][13]
-    const double* Lb;    // [M+2][nr][13]
+    const double* Lb;    // [M+2][nr][13]  L_m / (2 Re), no k_z^2 (that sits in dgt)
     int ntile;           // k tiles of kSK values in the factor tables
     const double* facH;  // M+2 Helmholtz matrices, A x = b rows, tiled (4 forward | 9 backward columns)
     const double* facP;  // M+1 pressure matrices, same layout

@@ -185,7 +185,12 @@ void upload_operators(pnop_ctx* c) {
         if (!dst) dst = c->upload(v);
         else ck(cudaMemcpy(dst, v.data(), v.size() * sizeof(double), cudaMemcpyHostToDevice), "upload");
     };
-    put(c->d_Lb, h.Lb);
+    {
+        // device bands hold L_m / (2 Re): the explicit Crank-Nicolson half B = 1/dt + L/(2 Re)
+        std::vector<double> lb(h.Lb);
+        for (double& x : lb) x /= 2.0 * h.ph.Re;
+        put(c->d_Lb, lb);
+    }
     {
         std::vector<double> dg(h.d.nk);
         for (int k = 0; k < h.d.nk; ++k) {
@@ -843,8 +848,15 @@ int snapshot_slots(pnop_ctx* c, long long N) {
 double measure_io_ratio(pnop_ctx* c) {
     ensure_host_tier(c, 1);
     const size_t fb = c->field_bytes();
-    cudaEvent_t e[3];
-    for (auto& x : e) ck(cudaEventCreate(&x), "event");
+    struct Events {  // destroyed on every exit path
+        cudaEvent_t e[3] = {nullptr, nullptr, nullptr};
+        ~Events() {
+            for (auto x : e)
+                if (x) cudaEventDestroy(x);
+        }
+    } ev;
+    cudaEvent_t* e = ev.e;
+    for (int i = 0; i < 3; ++i) ck(cudaEventCreate(&e[i]), "event");
     ck(cudaMemsetAsync(c->tmpB, 0, fb, c->stream), "memset");
     float io = 0, step = 0;
     for (int rep = 0; rep < 2; ++rep) {  // the first round warms up
@@ -858,7 +870,6 @@ double measure_io_ratio(pnop_ctx* c) {
         ck(cudaEventElapsedTime(&io, e[0], e[1]), "elapsed");
         ck(cudaEventElapsedTime(&step, e[1], e[2]), "elapsed");
     }
-    for (auto& x : e) cudaEventDestroy(x);
     return step > 0 ? (double)io / (double)step : 1.0;
 }
 
