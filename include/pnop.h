@@ -6,7 +6,9 @@
  * (Keuchel & Avila, "Nonlinear optimal perturbation growth in pulsatile pipe
  * flow": Section 2, Eq. 2.1–2.12 for the equations, Section 2.4 for the
  * discretisation and the predictor–corrector step, Section 2.5 and
- * Eq. 2.18–2.20 for the binomial checkpointing).
+ * Eq. 2.18–2.21 for the binomial and two-level checkpointing), with the
+ * adjoint-looping optimisation of Section 2.3 and the continuous adjoint
+ * equations Eq. 2.9–2.11 on top.
  *
  * C ABI, one CUDA device, plain pointers.  Every entry point returns an int
  * status (PNOP_OK = 0, negative on error) unless stated otherwise; no
@@ -27,10 +29,12 @@
  * frees them and keeps no pointer to them after a call returns.  The context
  * owns its operators, workspace and checkpoint pool (device memory).
  *
- * Streams: all device work of a context is ordered on the stream given to
- * pnop_create (NULL = legacy default stream).  Calls that return host scalars
- * (energy, inner, gradient) synchronise that stream.  A context must not be
- * used from two host threads at once.
+ * Streams: the device work of a call is ordered after earlier work on the
+ * stream given to pnop_create (NULL = legacy default stream) and before later
+ * work on it; inside a call the context also runs work on its own side and
+ * copy streams, forked from and joined back to that stream with events.
+ * Calls that return host scalars (energy, inner, gradient) synchronise that
+ * stream.  A context must not be used from two host threads at once.
  */
 #ifndef PNOP_H
 #define PNOP_H
