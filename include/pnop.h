@@ -234,6 +234,14 @@ typedef struct {
 int pnop_optimise(pnop_ctx* ctx, void* u0, double E0, double horizon, int max_iter, double tol,
                   double* gain_history, pnop_opt_stats* stats);
 
+/* pnop_optimise with the choice of adjoint: PNOP_ADJOINT_DISCRETE (the exact
+ * gradient of pnop_gradient, the default of pnop_optimise) or
+ * PNOP_ADJOINT_CONTINUOUS (the paper's continuous adjoint equations, as in
+ * pnop_gradient_continuous). */
+enum { PNOP_ADJOINT_DISCRETE = 0, PNOP_ADJOINT_CONTINUOUS = 1 };
+int pnop_optimise_ex(pnop_ctx* ctx, void* u0, double E0, double horizon, int max_iter, double tol, int adjoint,
+                     double* gain_history, pnop_opt_stats* stats);
+
 /* Operators of the step, applied to device fields (for testing and for
  * users who compose their own schemes; layout as above, all FP64 in/out):
  *   PNOP_OP_CURL       out = curl a                              (Eq. 2.5)

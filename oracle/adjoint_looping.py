@@ -106,12 +106,14 @@ def project_admissible(o, g: np.ndarray) -> np.ndarray:
 
 
 def optimise(o, u0: np.ndarray, t0: float, nsteps: int, E0: float, max_iter: int, tol: float = 1e-8,
-             max_halvings: int = 60):
+             max_halvings: int = 60, continuous: bool = False):
     """Adjoint looping from u0 (rescaled to E0).  Returns (u, history, info):
     history[s] is G after s accepted updates; info counts gradients (forward +
-    adjoint sweeps) and forward-only gain evaluations of the line search."""
+    adjoint sweeps) and forward-only gain evaluations of the line search.  With
+    continuous, the gradients come from the continuous adjoint equations."""
+    grad = o.gradient_continuous if continuous else o.gradient
     u = o.scale_to(project_admissible(o, u0), E0)
-    ET, g = o.gradient(u, t0, nsteps)
+    ET, g = grad(u, t0, nsteps)
     g = project_admissible(o, g)
     G = ET / o.energy(u)
     hist = [G]
@@ -142,7 +144,7 @@ def optimise(o, u0: np.ndarray, t0: float, nsteps: int, E0: float, max_iter: int
             info["converged"] = True
             break
         u, Gn, R = accepted
-        ET, g = o.gradient(u, t0, nsteps)
+        ET, g = grad(u, t0, nsteps)
         g = project_admissible(o, g)
         info["gradients"] += 1
         G = ET / o.energy(u)

@@ -24,7 +24,7 @@ OP_CURL, OP_NONLINEAR, OP_STAGE, OP_NONLINEAR_T, OP_STAGE_T_U, OP_STAGE_T_F, OP_
 EXPORTS = (
     "pnop_create", "pnop_set_base_flow", "pnop_dims", "pnop_grid_points", "pnop_step_forward", "pnop_step_adjoint",
     "pnop_gradient", "pnop_gradient_continuous", "pnop_gradient_forward", "pnop_gradient_backward",
-    "pnop_gradient_host", "pnop_gradient_stats", "pnop_optimise", "pnop_set_host_tier", "pnop_host_tier_stats",
+    "pnop_gradient_host", "pnop_gradient_stats", "pnop_optimise", "pnop_optimise_ex", "pnop_set_host_tier", "pnop_host_tier_stats",
     "pnop_two_level_counts", "pnop_mode_energy", "pnop_energy", "pnop_inner", "pnop_apply", "pnop_set_timeout",
     "pnop_sync", "pnop_profile", "pnop_profile_read", "pnop_revolve_counts", "pnop_context_bytes",
     "pnop_energy_noalloc", "pnop_last_error", "pnop_error_string", "pnop_destroy",
@@ -64,6 +64,8 @@ def _load():
         "pnop_gradient_stats": (c_int, [c_void_p, POINTER(c_longlong), POINTER(c_longlong), POINTER(c_longlong)]),
         "pnop_optimise": (c_int, [c_void_p, c_void_p, c_double, c_double, c_int, c_double, POINTER(c_double),
                                   POINTER(pnop_opt_stats)]),
+        "pnop_optimise_ex": (c_int, [c_void_p, c_void_p, c_double, c_double, c_int, c_double, c_int,
+                                     POINTER(c_double), POINTER(pnop_opt_stats)]),
         "pnop_set_host_tier": (c_int, [c_void_p, c_longlong, c_double]),
         "pnop_mode_energy": (c_int, [c_void_p, c_void_p, POINTER(c_double)]),
         "pnop_host_tier_stats": (c_int, [c_void_p, POINTER(c_int), POINTER(c_longlong), POINTER(c_longlong),
@@ -235,12 +237,13 @@ class Context:
         self._check(lib.pnop_gradient_stats(self._h, byref(a), byref(b), byref(c)), "gradient_stats")
         return a.value, b.value, c.value
 
-    def pnop_optimise(self, u0, E0, horizon, max_iter, tol=1e-8):
-        """Adjoint looping on u0 (device, in/out); returns (stats dict, gain history list)."""
+    def pnop_optimise(self, u0, E0, horizon, max_iter, tol=1e-8, continuous=False):
+        """Adjoint looping on u0 (device, in/out); returns (stats dict, gain history list).
+        continuous selects the continuous adjoint for the gradients."""
         hist = (c_double * (max_iter + 1))()
         st = pnop_opt_stats()
-        self._check(lib.pnop_optimise(self._h, c_void_p(_ptr(u0)), E0, horizon, max_iter, tol, hist, byref(st)),
-                    "optimise")
+        self._check(lib.pnop_optimise_ex(self._h, c_void_p(_ptr(u0)), E0, horizon, max_iter, tol, int(bool(continuous)),
+                                         hist, byref(st)), "optimise")
         stats = {name: getattr(st, name) for name, _ in pnop_opt_stats._fields_}
         return stats, list(hist[: st.iterations + 1])
 

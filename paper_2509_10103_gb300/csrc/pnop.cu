@@ -976,8 +976,8 @@ int gradient_impl(pnop_ctx* c, const double2* u0, double E0, double horizon, dou
 // E0_dagger = <u_dagger, u_dagger>/2), real for 0 < alpha <= alpha_max
 // (Eq. 2.15).  A trial point costs the checkpointed forward sweep; when it
 // raises G the reverse sweep of that same sweep gives the next gradient.
-void optimise_impl(pnop_ctx* c, double2* u, double E0, double horizon, int max_iter, double tol, double* hist,
-                   pnop_opt_stats* st) {
+void optimise_impl(pnop_ctx* c, double2* u, double E0, double horizon, int max_iter, double tol, bool continuous,
+                   double* hist, pnop_opt_stats* st) {
     constexpr int kMaxHalvings = 60;
     if (!c->opt_g) c->opt_g = c->field();
     if (!c->opt_u) c->opt_u = c->field();
@@ -987,9 +987,13 @@ void optimise_impl(pnop_ctx* c, double2* u, double E0, double horizon, int max_i
     if (!(E > 0) || !std::isfinite(E)) throw Status(PNOP_ERR_NONFINITE, "initial field has no finite energy");
     axpby(c, std::sqrt(E0 / E), u, 0.0, nullptr, u);
     double ET = 0, Eu = 0;
+    auto backward = [&] {
+        if (continuous) gradient_backward_continuous(c, g);
+        else gradient_backward(c, 1.0, false, g);
+        project(c, g);
+    };
     gradient_forward(c, u, -1.0, horizon, &ET, &Eu);
-    gradient_backward(c, 1.0, false, g);
-    project(c, g);
+    backward();
     double G = ET / Eu;
     *st = pnop_opt_stats{0, 1, 1, 0, G, std::nan("")};
     if (hist) hist[0] = G;
@@ -1030,8 +1034,7 @@ void optimise_impl(pnop_ctx* c, double2* u, double E0, double horizon, int max_i
             st->converged = 1;
             break;
         }
-        gradient_backward(c, 1.0, false, g);
-        project(c, g);
+        backward();
         ++st->gradients;
         ck(cudaMemcpyAsync(u, trial, c->field_bytes(), cudaMemcpyDeviceToDevice, c->stream), "accept");
         G = Gn;
@@ -1319,15 +1322,23 @@ int pnop_gradient_host(pnop_ctx* ctx, const double* u0_host, double E0, double h
     });
 }
 
-int pnop_optimise(pnop_ctx* ctx, void* u0, double E0, double horizon, int max_iter, double tol,
-                  double* gain_history, pnop_opt_stats* stats) {
+int pnop_optimise_ex(pnop_ctx* ctx, void* u0, double E0, double horizon, int max_iter, double tol, int adjoint,
+                     double* gain_history, pnop_opt_stats* stats) {
     return guarded(ctx, [&]() -> int {
-        if (!u0 || !(E0 > 0) || max_iter < 0 || !(tol >= 0)) throw Status(PNOP_ERR_INVALID_ARG, "bad arguments");
+        if (!u0 || !(E0 > 0) || max_iter < 0 || !(tol >= 0) ||
+            (adjoint != PNOP_ADJOINT_DISCRETE && adjoint != PNOP_ADJOINT_CONTINUOUS))
+            throw Status(PNOP_ERR_INVALID_ARG, "bad arguments");
         pnop_opt_stats st{};
-        optimise_impl(ctx, (double2*)u0, E0, horizon, max_iter, tol, gain_history, &st);
+        optimise_impl(ctx, (double2*)u0, E0, horizon, max_iter, tol, adjoint == PNOP_ADJOINT_CONTINUOUS,
+                      gain_history, &st);
         if (stats) *stats = st;
         return PNOP_OK;
     });
+}
+
+int pnop_optimise(pnop_ctx* ctx, void* u0, double E0, double horizon, int max_iter, double tol,
+                  double* gain_history, pnop_opt_stats* stats) {
+    return pnop_optimise_ex(ctx, u0, E0, horizon, max_iter, tol, PNOP_ADJOINT_DISCRETE, gain_history, stats);
 }
 
 int pnop_mode_energy(pnop_ctx* ctx, const void* u, double* spectrum) {

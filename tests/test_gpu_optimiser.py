@@ -29,14 +29,14 @@ def dev(x):
     return torch.from_numpy(np.ascontiguousarray(x, dtype=np.complex128)).to("cuda")
 
 
-def run_both(L, prm, N, E0, max_iter, tol, seed, precision=0, snaps=3):
+def run_both(L, prm, N, E0, max_iter, tol, seed, precision=0, snaps=3, continuous=False):
     o = po.Oracle(po.Params(**prm))
     p = o.p
     ctx = L.Context(p.nr, 2 * (p.M + 1), 2 * (p.K + 1), p.Lz, p.Re, p.dt, p.Wo, p.A, 0.0, precision, snaps)
     u0 = synth.random_field(o.r, p.M, p.K, p.Lz, seed=seed)
     x = dev(u0)
-    stats, hist = ctx.pnop_optimise(x, E0, N * p.dt, max_iter, tol)
-    u_ref, hist_ref, info = al.optimise(o, u0, 0.0, N, E0, max_iter, tol)
+    stats, hist = ctx.pnop_optimise(x, E0, N * p.dt, max_iter, tol, continuous=continuous)
+    u_ref, hist_ref, info = al.optimise(o, u0, 0.0, N, E0, max_iter, tol, continuous=continuous)
     got = x.cpu().numpy()
     ctx.close()
     return o, stats, hist, got, u_ref, hist_ref, info
@@ -68,6 +68,16 @@ def test_optimiser_nonlinear_iterations_match_oracle(L):
     # the iterates inherit the gradient's 1e-10 agreement, amplified by the alpha_max steps
     np.testing.assert_allclose(hist, hist_ref, rtol=1e-6)
     assert stats["forward_evals"] == info["forward_evals"] + 1  # the library counts the start's sweep
+    assert np.abs(got - u_ref).max() <= 1e-6 * np.abs(u_ref).max()
+    assert all(b > a for a, b in zip(hist, hist[1:]))
+
+
+def test_optimiser_with_continuous_adjoint_matches_oracle(L):
+    prm = dict(nr=12, M=3, K=5, Lz=10.0, Re=2000.0, dt=0.01, Wo=8.0, A=1.0)
+    o, stats, hist, got, u_ref, hist_ref, info = run_both(L, prm, 20, 1e-3, 3, 1e-8, seed=4, continuous=True)
+    assert len(hist) == len(hist_ref) >= 2
+    np.testing.assert_allclose(hist, hist_ref, rtol=1e-6)
+    assert stats["gradients"] == info["gradients"]
     assert np.abs(got - u_ref).max() <= 1e-6 * np.abs(u_ref).max()
     assert all(b > a for a, b in zip(hist, hist[1:]))
 
