@@ -111,16 +111,28 @@ __device__ __forceinline__ void base_at(const Geo& g, int j, double c, double s,
     dU = -2.0 * r + (b.x * c - b.y * s);
 }
 
+// U and dU/dr at the block's radius (a spectral block covers one j): one
+// thread evaluates them and the block shares the pair, instead of every
+// thread repeating the same FP64 arithmetic.  Called by all threads of the
+// block before any of them returns.
+__device__ __forceinline__ void base_block(const Geo& g, double c, double s, double& U, double& dU) {
+    __shared__ double sh[2];
+    if (threadIdx.x == 0) base_at(g, blockIdx.z, c, s, sh[0], sh[1]);
+    __syncthreads();
+    U = sh[0];
+    dU = sh[1];
+}
+
 // N = -U du/dz - u_r dU/dr e_z: the base-flow terms in advective form.  The
 // rotational form (U e_z) x w + u x (-dU/dr e_theta) differs from it by
 // grad(U u_z), which the discrete pressure projection does not remove exactly;
 // the remainder couples u_z back into (u_r, u_theta) and makes k = 0 modes of
 // steady pipe flow grow at high Re.
 __global__ void k_base(Geo g, const double2* __restrict__ u, double2* __restrict__ N, double c, double s) {
+    double U, dU;
+    base_block(g, c, s, U, dU);
     Idx d;
     if (!decode(g, d)) return;
-    double U, dU;
-    base_at(g, d.j, c, s, U, dU);
     const size_t o = sidx(g, d.j, d.im, d.k), S = d.S;
     const double a = __ldg(g.kzt + d.k) * U;  // -U d/dz = -i a
     const double2 ur = u[o], ut = u[o + S], uz = u[o + 2 * S];
@@ -131,10 +143,10 @@ __global__ void k_base(Geo g, const double2* __restrict__ u, double2* __restrict
 
 // transpose (Euclidean cotangents): ub = conj(-i a) nb = i a nb; ub_r -= dU nb_z
 __global__ void k_baseT(Geo g, const double2* __restrict__ nb, double2* __restrict__ ub, double c, double s) {
+    double U, dU;
+    base_block(g, c, s, U, dU);
     Idx d;
     if (!decode(g, d)) return;
-    double U, dU;
-    base_at(g, d.j, c, s, U, dU);
     const size_t o = sidx(g, d.j, d.im, d.k), S = d.S;
     const double a = __ldg(g.kzt + d.k) * U;
     const double2 nr_ = nb[o], nt = nb[o + S], nz = nb[o + 2 * S];
@@ -166,10 +178,10 @@ __global__ void k_grad_u(Geo g, const double2* __restrict__ u, double2* __restri
 
 // Base-flow part of the continuous-adjoint forcing: N = U dw/dz - w_z dU/dr e_r
 __global__ void k_base_adj(Geo g, const double2* __restrict__ w, double2* __restrict__ N, double c, double s) {
+    double U, dU;
+    base_block(g, c, s, U, dU);
     Idx d;
     if (!decode(g, d)) return;
-    double U, dU;
-    base_at(g, d.j, c, s, U, dU);
     const size_t o = sidx(g, d.j, d.im, d.k), S = d.S;
     const double a = __ldg(g.kzt + d.k) * U;  // U d/dz = i a
     const double2 wr = w[o], wt = w[o + S], wz = w[o + 2 * S];
