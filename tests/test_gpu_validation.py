@@ -66,7 +66,7 @@ def test_linear_optimum_pulsatile_wo2_peaks_at_0029T():
     ctx = L.Context(nr, 2 * (M + 1), 2 * (K + 1), Lz, Re, dt, Wo, A, tau0, L.PNOP_FP64, 200)
     r = np.array(ctx.pnop_grid_points())
     u = torch.from_numpy(synth.random_field(r, M, K, Lz, seed=3)).to("cuda")
-    stats, hist = ctx.pnop_optimise(u, 1e-20, nsteps * dt, 12, 1e-5)
+    stats, hist = ctx.pnop_optimise(u, 1e-20, nsteps * dt, 25, 1e-6)
     print("optimise", stats, hist)
     x = u.clone()
     E0 = ctx.pnop_energy(x)
