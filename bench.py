@@ -387,24 +387,26 @@ def _serving_requests(L, nreq, seed, arrivals):
     return reqs
 
 
-def serving_report(L, nreq=256, probe=48, load=0.7, seed=0, budget=40 << 30, max_active=8):
+def serving_report(L, nreq=256, probe=48, load=0.7, seed=0, budget=40 << 30, max_active=8, batched=False):
     """Capacity probe, then a Poisson stream at `load` x that capacity.
 
     The probe submits `probe` requests at once and takes completed / wall as
     the capacity (requests/s).  The stream then offers `nreq` requests with
     exponential gaps of mean 1 / (load x capacity) and reports p50/p99
-    latency (arrival to result on the host) and throughput."""
+    latency (arrival to result on the host) and throughput.  batched: the
+    BatchServer (max_active slots per batch of one resolution, shared
+    launches) instead of one context and stream per request."""
     import numpy as np
     from paper_2509_10103_gb300 import serving
     reqs = _serving_requests(L, probe, seed + 1, np.zeros(probe))
     t0 = time.perf_counter()
-    res, _ = serving.serve_stream(reqs, hbm_budget=budget, max_active=max_active)
+    res, _ = serving.serve_stream(reqs, hbm_budget=budget, max_active=max_active, batched=batched)
     cap = sum(r.error is None for r in res) / (time.perf_counter() - t0)
     rate = load * cap
     gaps = np.random.default_rng(seed + 2).exponential(1.0 / rate, nreq)
     reqs = _serving_requests(L, nreq, seed, np.cumsum(gaps))
     t0 = time.perf_counter()
-    res, srv = serving.serve_stream(reqs, hbm_budget=budget, max_active=max_active)
+    res, srv = serving.serve_stream(reqs, hbm_budget=budget, max_active=max_active, batched=batched)
     wall = time.perf_counter() - t0
     ok = [r for r in res if r.error is None]
     steps = sum(int(round(q.horizon / q.dt)) for q, r in zip(reqs, res) if r.error is None)
@@ -416,7 +418,64 @@ def serving_report(L, nreq=256, probe=48, load=0.7, seed=0, budget=40 << 30, max
             "steps_per_s": steps / wall, "p50_latency_s": lat["p50_s"], "p99_latency_s": lat["p99_s"],
             "mean_latency_s": lat.get("mean_s"), "peak_active": srv.peak_active,
             "peak_admitted_gb": srv.peak_bytes / 2 ** 30, "hbm_budget_gb": budget / 2 ** 30, "wall_s": wall,
-            "horizons": "10-50 steps of dt=0.005", "arrivals": f"Poisson at {load} x measured capacity"}
+            "horizons": "10-50 steps of dt=0.005", "arrivals": f"Poisson at {load} x measured capacity",
+            "server": "batched launches per resolution (BatchServer)" if batched else "one context and stream per request",
+            "peak_requests_in_one_batch": getattr(srv, "peak_batch", None)}
+
+
+def batch_report(L, torch, nsteps=20, snaps=8, seed=7):
+    """Batched gradients (pnop_batch) against the same requests one after
+    another on single contexts, per serving resolution: B requests of seeded
+    physics (as the serving stream), nsteps steps of dt = 0.005 each.
+    Operator set-up (host) is outside both timings; the batched time runs
+    from the first queued step to the last fetched gradient."""
+    import numpy as np
+    from paper_2509_10103_gb300 import synth
+    rng = np.random.default_rng(seed)
+    out = {}
+    cases = [(res, L.PNOP_MIXED, 16 if res[0] < 64 else 8) for res in SERVE_RES] + [(SERVE_RES[0], L.PNOP_FP64, 16)]
+    for (nr, nth, nz, lz), prec, B in cases:
+        ctx = L.Context(nr, nth, nz, lz, 2000.0, 0.005, 8.0, 1.0, 0.0, prec, 1)
+        r = np.array(ctx.pnop_grid_points())
+        ctx.close()
+        u = torch.from_numpy(synth.random_field(r, nth // 2 - 1, nz // 2 - 1, lz, seed=seed + nr)).to("cuda")
+        phys = [(float(rng.uniform(1500, 3000)), float(rng.uniform(4, 18)), float(rng.uniform(0.5, 1.5)),
+                 float(rng.uniform(0, 100)), float(10 ** rng.uniform(-7, -4))) for _ in range(B)]
+        H = nsteps * 0.005
+        g = torch.empty_like(u)
+        # batched
+        b = L.Batch(nr, nth, nz, lz, B, prec, snaps)
+        for rep in range(2):  # the first pass warms up
+            ids = [b.pnop_batch_submit(u, E0, H, Re, 0.005, Wo, A, t0) for Re, Wo, A, t0, E0 in phys]
+            torch.cuda.synchronize()
+            st0 = b.pnop_batch_stats()
+            t0 = time.perf_counter()
+            b.pnop_batch_run(1 << 30)
+            for i in ids:
+                b.pnop_batch_result(i, g)
+            torch.cuda.synchronize()
+            tb = time.perf_counter() - t0
+            st = b.pnop_batch_stats()
+        b.close()
+        # one after another on single contexts
+        ctxs = [L.Context(nr, nth, nz, lz, Re, 0.005, Wo, A, t0, prec, snaps) for Re, Wo, A, t0, E0 in phys]
+        ctxs[0].pnop_gradient(u, phys[0][4], H, g)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for c, (Re, Wo, A, tt, E0) in zip(ctxs, phys):
+            c.pnop_gradient(u, E0, H, g)
+        torch.cuda.synchronize()
+        ts = time.perf_counter() - t0
+        for c in ctxs:
+            c.close()
+        ticks = st["ticks"] - st0["ticks"]
+        key = f"{nr}x{nth}x{nz}_{'mixed' if prec == L.PNOP_MIXED else 'fp64'}"
+        out[key] = {"requests": B, "steps_each": nsteps, "snap_budget": snaps,
+                    "batched_steps_per_s": B * nsteps / tb, "single_steps_per_s": B * nsteps / ts,
+                    "speedup": ts / tb, "batched_ticks": ticks,
+                    "mean_requests_per_launch": (st["entries"] - st0["entries"]) / max(1, ticks),
+                    "kernel_launches_batched": st["launches"] - st0["launches"]}
+    return out
 
 
 # ------------------------------------------------------------------ CPU oracle (baseline / reference arm)
@@ -588,8 +647,11 @@ def main():
         out["budget_sweep_mixed"] = budget_sweep(L, torch, L.PNOP_MIXED, H)
         out["host_tier_mixed"] = host_tier_report(L, torch, L.PNOP_MIXED, H)
         out["continuous_adjoint_mixed"] = continuous_adjoint_report(L, torch, L.PNOP_MIXED, H, s)
+    if ws == 1 and not args.no_extras:
+        out["batched_gradients"] = batch_report(L, torch)
     if not args.no_serving and ws == 1:
         out["serving"] = serving_report(L)
+        out["serving_batched"] = serving_report(L, batched=True)
     if not args.no_cpu_baseline and ws == 1:
         planes, modes = 16, 64
         smp = oracle_sample(planes, modes)

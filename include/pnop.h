@@ -365,6 +365,69 @@ const char* pnop_error_string(int status);
 /* Free the context and everything it owns.  NULL is allowed. */
 void pnop_destroy(pnop_ctx* ctx);
 
+/* ---------------------------------------------------------------------------
+ * Batched gradients (a serving form; the paper has no counterpart).  A batch
+ * holds up to `capacity` (1..PNOP_MAX_BATCH) gradient requests of one grid,
+ * each with its own Re, Wo, A, dt, tau0, E0 and horizon, and runs them
+ * together: every kernel of a forward or adjoint step is launched once for
+ * all requests that take that kind of step next (the requests' fields sit in
+ * per-request slots of shared buffers).  Each request follows its own
+ * binomial checkpoint schedule (Section 2.5, snap_budget slots of its own)
+ * and gets bitwise the gradient and gain pnop_gradient returns for it on a
+ * single context with the same snap_budget and precision.  Requests can be
+ * submitted while others run (continuous batching).
+ *
+ * Use: pnop_batch_create; pnop_batch_submit per request (copies u0 in, the
+ * slot is taken until its result is fetched); pnop_batch_run to queue steps;
+ * pnop_batch_poll to see whether a request is finished without blocking;
+ * pnop_batch_result to fetch its gradient (same semantics as pnop_gradient's
+ * grad_out) and gain and free its slot.  All device work is ordered on the
+ * stream given at creation; submit, run and poll do not wait for the device,
+ * result waits for the request's own work. */
+#define PNOP_MAX_BATCH 16
+typedef struct pnop_batch pnop_batch;
+
+/* grid: as for pnop_create.  params: precision, snap_budget (>= 1,
+ * checkpoint slots per request) and hbm_budget (0 = no limit) apply to every
+ * request; Re, Wo, A, dt and tau0 must be valid but are replaced by each
+ * request's own.  Device memory for all slots is allocated here (about
+ * capacity times a single context's workspace plus snap_budget fields). */
+int pnop_batch_create(const pnop_grid* grid, const pnop_params* params, int capacity, void* cuda_stream,
+                      pnop_batch** out);
+
+/* Admit one request: physics from request->Re, Wo, A, dt, tau0 (the other
+ * fields are ignored), u0 (device, layout above, read during the call's
+ * stream-ordered copy), E0 > 0 rescales u0 to energy E0 (E0 <= 0 keeps it),
+ * horizon a positive whole number of steps of request->dt.  *id_out receives
+ * the request id.  PNOP_ERR_OOM when no slot is free, PNOP_ERR_INVALID_ARG
+ * for bad parameters; builds the request's operators on the host. */
+int pnop_batch_submit(pnop_batch* batch, const pnop_params* request, const void* u0, double E0, double horizon,
+                      int* id_out);
+
+/* Queue up to max_ticks batched steps (one tick: every request's pending
+ * checkpoint copies, then one batched forward, terminal or adjoint step for
+ * the requests whose next step is of the most common kind).  *ticks_out:
+ * ticks queued (fewer when all requests are finished); *running_out:
+ * requests still unfinished after them.  Either pointer may be NULL. */
+int pnop_batch_run(pnop_batch* batch, int max_ticks, int* ticks_out, int* running_out);
+
+/* *done_out = 1 when request id has been fully queued and its device work
+ * has completed, else 0.  PNOP_ERR_INVALID_ARG for an unknown id. */
+int pnop_batch_poll(pnop_batch* batch, int id, int* done_out);
+
+/* Gradient (device, may be NULL) and gain of a finished request; frees its
+ * slot.  PNOP_ERR_INVALID_ARG when the request has not been fully queued
+ * yet (run more ticks), PNOP_ERR_NONFINITE when its energies are not finite
+ * (the slot is freed all the same). */
+int pnop_batch_result(pnop_batch* batch, int id, void* grad_out, double* gain_out);
+
+/* Batched steps launched (ticks), the requests they covered in total
+ * (entries / ticks = mean batch size) and the kernels launched. */
+int pnop_batch_stats(const pnop_batch* batch, long long* ticks, long long* entries, long long* launches);
+
+const char* pnop_batch_last_error(const pnop_batch* batch);
+void pnop_batch_destroy(pnop_batch* batch);
+
 #ifdef __cplusplus
 }
 #endif

@@ -28,6 +28,8 @@ EXPORTS = (
     "pnop_two_level_counts", "pnop_mode_energy", "pnop_energy", "pnop_inner", "pnop_apply", "pnop_set_timeout",
     "pnop_sync", "pnop_profile", "pnop_profile_read", "pnop_revolve_counts", "pnop_context_bytes",
     "pnop_energy_noalloc", "pnop_last_error", "pnop_error_string", "pnop_destroy",
+    "pnop_batch_create", "pnop_batch_submit", "pnop_batch_run", "pnop_batch_poll", "pnop_batch_result",
+    "pnop_batch_stats", "pnop_batch_last_error", "pnop_batch_destroy",
 )
 
 
@@ -86,6 +88,14 @@ def _load():
         "pnop_last_error": (c_char_p, [c_void_p]),
         "pnop_error_string": (c_char_p, [c_int]),
         "pnop_destroy": (None, [c_void_p]),
+        "pnop_batch_create": (c_int, [POINTER(pnop_grid), POINTER(pnop_params), c_int, c_void_p, POINTER(c_void_p)]),
+        "pnop_batch_submit": (c_int, [c_void_p, POINTER(pnop_params), c_void_p, c_double, c_double, POINTER(c_int)]),
+        "pnop_batch_run": (c_int, [c_void_p, c_int, POINTER(c_int), POINTER(c_int)]),
+        "pnop_batch_poll": (c_int, [c_void_p, c_int, POINTER(c_int)]),
+        "pnop_batch_result": (c_int, [c_void_p, c_int, c_void_p, POINTER(c_double)]),
+        "pnop_batch_stats": (c_int, [c_void_p, POINTER(c_longlong), POINTER(c_longlong), POINTER(c_longlong)]),
+        "pnop_batch_last_error": (c_char_p, [c_void_p]),
+        "pnop_batch_destroy": (None, [c_void_p]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -292,3 +302,66 @@ class Context:
         e = c_double()
         self._check(lib.pnop_inner(self._h, c_void_p(_ptr(a)), c_void_p(_ptr(b)), byref(e)), "inner")
         return e.value
+
+
+PNOP_MAX_BATCH = 16
+
+
+class Batch:
+    """Batched gradients of up to `capacity` requests of one grid (pnop_batch):
+    one kernel launch per step kind covers every request taking that step."""
+
+    def __init__(self, nr, ntheta, nz, Lz, capacity, precision=PNOP_FP64, snap_budget=8, hbm_budget=0,
+                 stretch=0.0, stream=0):
+        g = pnop_grid(nr, ntheta, nz, Lz, stretch)
+        p = pnop_params(2000.0, 8.0, 1.0, 0.01, 0.0, precision, snap_budget, hbm_budget)
+        h = c_void_p()
+        rc = lib.pnop_batch_create(byref(g), byref(p), capacity, c_void_p(stream), byref(h))
+        if rc != PNOP_OK:
+            raise PnopError(rc, "pnop_batch_create")
+        self._h = h
+        self.capacity = capacity
+        self.M, self.K = ntheta // 2 - 1, nz // 2 - 1
+        self.shape = (3, nr, 2 * self.M + 1, self.K + 1)
+
+    def _check(self, rc, what):
+        if rc != PNOP_OK:
+            raise PnopError(rc, f"{what}: {lib.pnop_batch_last_error(self._h).decode()}")
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib.pnop_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        self.close()
+
+    def pnop_batch_submit(self, u0, E0, horizon, Re, dt, Wo=8.0, A=1.0, tau0=0.0):
+        """Admit one request; returns its id (u0 is copied in stream order)."""
+        p = pnop_params(Re, Wo, A, dt, tau0, 0, 0, 0)
+        i = c_int()
+        self._check(lib.pnop_batch_submit(self._h, byref(p), c_void_p(_ptr(u0)), E0, horizon, byref(i)), "submit")
+        return i.value
+
+    def pnop_batch_run(self, max_ticks):
+        """Queue up to max_ticks batched steps; returns (ticks, requests still running)."""
+        t, r = c_int(), c_int()
+        self._check(lib.pnop_batch_run(self._h, max_ticks, byref(t), byref(r)), "run")
+        return t.value, r.value
+
+    def pnop_batch_poll(self, rid):
+        d = c_int()
+        self._check(lib.pnop_batch_poll(self._h, rid, byref(d)), "poll")
+        return bool(d.value)
+
+    def pnop_batch_result(self, rid, grad_out=None):
+        """(gain) of a finished request; its gradient into grad_out (device) when given."""
+        gain = c_double()
+        self._check(lib.pnop_batch_result(self._h, rid, c_void_p(_ptr(grad_out)) if grad_out is not None else None,
+                                          byref(gain)), "result")
+        return gain.value
+
+    def pnop_batch_stats(self):
+        t, e, la = c_longlong(), c_longlong(), c_longlong()
+        self._check(lib.pnop_batch_stats(self._h, byref(t), byref(e), byref(la)), "stats")
+        return {"ticks": t.value, "entries": e.value, "launches": la.value}

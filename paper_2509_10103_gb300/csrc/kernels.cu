@@ -10,24 +10,35 @@
 #include "kernels.hpp"
 
 #include <algorithm>
+#include <string>
 
 namespace pnop {
 
 // ------------------------------------------------------------------ spectral FP64 kernels
 struct Idx {
-    int j, im, k, m;
-    size_t S;
+    int j, im, k, m, b, slot;
+    size_t S, off;  // off: element offset of the entry's slot in every spectral buffer
 };
 // Spectral kernels run on a 3-D grid: x covers k, y the azimuthal index, z
-// the radial index, so no thread divides to find its (j, m, k).
+// the radial index and the batch entry (z = b nr + j), so no thread divides
+// to find its (j, m, k).
 __device__ __forceinline__ bool decode(const Geo& g, Idx& d) {
     d.S = (size_t)g.nr * g.nm * g.nk;
     d.k = blockIdx.x * blockDim.x + threadIdx.x;
     d.im = blockIdx.y;
-    d.j = blockIdx.z;
+    d.b = blockIdx.z / g.nr;
+    d.j = blockIdx.z - d.b * g.nr;
+    d.slot = g.slot[d.b];
+    d.off = (size_t)d.slot * g.fs;
     d.m = d.im - g.M;
     return d.k < g.nk;
 }
+// Per-slot operator tables of a batched context (stride 0 tables are shared).
+__device__ __forceinline__ const double* slot_Lb(const Geo& g, int slot) { return g.Lb + (size_t)slot * g.sLb; }
+__device__ __forceinline__ const double* slot_dgt(const Geo& g, int slot) { return g.dgt + (size_t)slot * g.sNk; }
+__device__ __forceinline__ const double* slot_infl(const Geo& g, int slot) { return g.infl + (size_t)slot * g.sInfl; }
+__device__ __forceinline__ const double* slot_fluxg(const Geo& g, int slot) { return g.fluxg + (size_t)slot * g.sNr; }
+template <class P> __device__ __forceinline__ P moved(P p, size_t off) { return p ? p + off : p; }
 __device__ __forceinline__ size_t sidx(const Geo& g, int j, int im, int k) {
     return ((size_t)j * g.nm + im) * g.nk + k;
 }
@@ -76,6 +87,8 @@ __device__ __forceinline__ double2 band_col(const Geo& g, const double* B0, cons
 __global__ void k_curl(Geo g, const double2* __restrict__ u, double2* __restrict__ w) {
     Idx d;
     if (!decode(g, d)) return;
+    u += d.off;
+    w += d.off;
     const double2 *ur = u, *ut = u + d.S, *uz = u + 2 * d.S;
     const double kz = __ldg(g.kzt + d.k), ir = g.invr[d.j], mr = __ldg(g.mrt + (size_t)d.im * g.nr + d.j);
     const size_t o = sidx(g, d.j, d.im, d.k);
@@ -90,6 +103,8 @@ __global__ void k_curl(Geo g, const double2* __restrict__ u, double2* __restrict
 __global__ void k_curlT_acc(Geo g, const double2* __restrict__ wb, double2* __restrict__ ub) {
     Idx d;
     if (!decode(g, d)) return;
+    wb += d.off;
+    ub += d.off;
     const double2 *wr = wb, *wt = wb + d.S, *wz = wb + 2 * d.S;
     const double kz = __ldg(g.kzt + d.k), ir = g.invr[d.j], mr = __ldg(g.mrt + (size_t)d.im * g.nr + d.j);
     const size_t o = sidx(g, d.j, d.im, d.k);
@@ -104,20 +119,24 @@ __global__ void k_curlT_acc(Geo g, const double2* __restrict__ wb, double2* __re
     ub[o + 2 * d.S] = make_double2(x.x + mr * a.y - sP.x, x.y - mr * a.x - sP.y);
 }
 
-__device__ __forceinline__ void base_at(const Geo& g, int j, double c, double s, double& U, double& dU) {
+__device__ __forceinline__ void base_at(const Geo& g, int slot, int j, double c, double s, double& U, double& dU) {
     const double r = g.r[j];
-    const double2 a = g.Uh[j], b = g.dUh[j];
+    const double2 a = g.Uh[(size_t)slot * g.sNr + j], b = g.dUh[(size_t)slot * g.sNr + j];
     U = 1.0 - r * r + (a.x * c - a.y * s);
     dU = -2.0 * r + (b.x * c - b.y * s);
 }
 
-// U and dU/dr at the block's radius (a spectral block covers one j): one
-// thread evaluates them and the block shares the pair, instead of every
-// thread repeating the same FP64 arithmetic.  Called by all threads of the
-// block before any of them returns.
-__device__ __forceinline__ void base_block(const Geo& g, double c, double s, double& U, double& dU) {
+// U and dU/dr at the block's radius and batch entry (a spectral block covers
+// one j of one entry), at that entry's phase ph: one thread evaluates them and
+// the block shares the pair, instead of every thread repeating the same FP64
+// arithmetic.  Called by all threads of the block before any of them returns.
+__device__ __forceinline__ void base_block(const Geo& g, int ph, double& U, double& dU) {
     __shared__ double sh[2];
-    if (threadIdx.x == 0) base_at(g, blockIdx.z, c, s, sh[0], sh[1]);
+    if (threadIdx.x == 0) {
+        const int b = blockIdx.z / g.nr, j = blockIdx.z - b * g.nr;
+        const double2 cs = g.cs[ph][b];
+        base_at(g, g.slot[b], j, cs.x, cs.y, sh[0], sh[1]);
+    }
     __syncthreads();
     U = sh[0];
     dU = sh[1];
@@ -128,11 +147,13 @@ __device__ __forceinline__ void base_block(const Geo& g, double c, double s, dou
 // grad(U u_z), which the discrete pressure projection does not remove exactly;
 // the remainder couples u_z back into (u_r, u_theta) and makes k = 0 modes of
 // steady pipe flow grow at high Re.
-__global__ void k_base(Geo g, const double2* __restrict__ u, double2* __restrict__ N, double c, double s) {
+__global__ void k_base(Geo g, const double2* __restrict__ u, double2* __restrict__ N, int ph) {
     double U, dU;
-    base_block(g, c, s, U, dU);
+    base_block(g, ph, U, dU);
     Idx d;
     if (!decode(g, d)) return;
+    u += d.off;
+    N += d.off;
     const size_t o = sidx(g, d.j, d.im, d.k), S = d.S;
     const double a = __ldg(g.kzt + d.k) * U;  // -U d/dz = -i a
     const double2 ur = u[o], ut = u[o + S], uz = u[o + 2 * S];
@@ -142,11 +163,13 @@ __global__ void k_base(Geo g, const double2* __restrict__ u, double2* __restrict
 }
 
 // transpose (Euclidean cotangents): ub = conj(-i a) nb = i a nb; ub_r -= dU nb_z
-__global__ void k_baseT(Geo g, const double2* __restrict__ nb, double2* __restrict__ ub, double c, double s) {
+__global__ void k_baseT(Geo g, const double2* __restrict__ nb, double2* __restrict__ ub, int ph) {
     double U, dU;
-    base_block(g, c, s, U, dU);
+    base_block(g, ph, U, dU);
     Idx d;
     if (!decode(g, d)) return;
+    nb += d.off;
+    ub += d.off;
     const size_t o = sidx(g, d.j, d.im, d.k), S = d.S;
     const double a = __ldg(g.kzt + d.k) * U;
     const double2 nr_ = nb[o], nt = nb[o + S], nz = nb[o + 2 * S];
@@ -159,7 +182,7 @@ __global__ void k_baseT(Geo g, const double2* __restrict__ nb, double2* __restri
 // (d_r u_j), ((im u_r - u_theta)/r, (im u_theta + u_r)/r, im u_z / r), (i k_z u_j).
 __global__ void k_grad_u(Geo g, const double2* __restrict__ u, double2* __restrict__ G) {
     Idx d;
-    if (!decode(g, d)) return;
+    if (!decode(g, d)) return;  // single-request launches only (the launcher checks)
     const size_t o = sidx(g, d.j, d.im, d.k), S = d.S;
     const double ir = g.invr[d.j], mr = __ldg(g.mrt + (size_t)d.im * g.nr + d.j), kz = __ldg(g.kzt + d.k);
     const double2 a = u[o], b = u[o + S], c = u[o + 2 * S];
@@ -177,11 +200,13 @@ __global__ void k_grad_u(Geo g, const double2* __restrict__ u, double2* __restri
 }
 
 // Base-flow part of the continuous-adjoint forcing: N = U dw/dz - w_z dU/dr e_r
-__global__ void k_base_adj(Geo g, const double2* __restrict__ w, double2* __restrict__ N, double c, double s) {
+__global__ void k_base_adj(Geo g, const double2* __restrict__ w, double2* __restrict__ N, int ph) {
     double U, dU;
-    base_block(g, c, s, U, dU);
+    base_block(g, ph, U, dU);
     Idx d;
     if (!decode(g, d)) return;
+    w += d.off;
+    N += d.off;
     const size_t o = sidx(g, d.j, d.im, d.k), S = d.S;
     const double a = __ldg(g.kzt + d.k) * U;  // U d/dz = i a
     const double2 wr = w[o], wt = w[o + S], wz = w[o + 2 * S];
@@ -195,6 +220,8 @@ __global__ void k_base_adj(Geo g, const double2* __restrict__ w, double2* __rest
 __global__ void k_stage_div(Geo g, const double2* __restrict__ F, double2* __restrict__ q) {
     Idx d;
     if (!decode(g, d)) return;
+    F += d.off;
+    q += d.off;
     const size_t o = sidx(g, d.j, d.im, d.k), S = d.S;
     if (d.j == 0 || (d.m == 0 && d.k == 0)) {
         q[o] = make_double2(0, 0);
@@ -231,9 +258,12 @@ __device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_g
 // NL lower coefficients (oldest first) for the forward sweep, diagonal in the
 // forward sweep when DIAG1 (else in the backward sweep), NU upper coefficients
 // (nearest first) for the backward sweep.  X = A^{-1} X [+ add].
+// Batch entry blockIdx.y; its factor table sits at fac + slot * fac_stride
+// (stride 0: a table shared by all slots).
 template <int NL, int NU, bool DIAG1>
-__global__ void __launch_bounds__(2 * kSK) k_band_solve(Geo g, const double* __restrict__ fac, double2* __restrict__ X,
-                                                  const double2* __restrict__ add, int helm, int zero_row0) {
+__global__ void __launch_bounds__(2 * kSK) k_band_solve(Geo g, const double* __restrict__ fac, size_t fac_stride,
+                                                  double2* __restrict__ X, const double2* __restrict__ add, int helm,
+                                                  int zero_row0) {
     constexpr int NC1 = NL + (DIAG1 ? 1 : 0);  // forward sweep: columns [0, NC1)
     constexpr int NC2 = kB - NC1;               // backward sweep: columns [NC1, 13)
     constexpr int NCM = NC1 > NC2 ? NC1 : NC2;
@@ -249,6 +279,11 @@ __global__ void __launch_bounds__(2 * kSK) k_band_solve(Geo g, const double* __r
     const int mv = helm ? (v == 0 ? m + 1 : (v == 1 ? m - 1 : m)) : m;
     const int k0 = kb * kSK;
     const size_t S = (size_t)g.nr * g.nm * g.nk;
+    const int slot = g.slot[blockIdx.y];
+    const size_t off = (size_t)slot * g.fs;
+    fac += (size_t)slot * fac_stride;
+    X += off;
+    add = moved(add, off);
     double2* x = X + (size_t)v * S;  // v = 0 for the pressure
     const double* T1 = fac + ((size_t)abs(mv) * g.ntile + kb) * (size_t)g.nr * kB * kSK;  // [nr][NC1][kSK]
     const double* T2 = T1 + (size_t)g.nr * NC1 * kSK;                                    // [nr][NC2][kSK]
@@ -345,14 +380,17 @@ __global__ void __launch_bounds__(2 * kSK) k_band_solve(Geo g, const double* __r
 __global__ void k_stage_bu(Geo g, const double2* __restrict__ u, double2* __restrict__ RB) {
     Idx d;
     if (!decode(g, d)) return;
+    u += d.off;
+    RB += d.off;
     const size_t o = sidx(g, d.j, d.im, d.k), S = d.S;
     if (d.j == 0) {
         RB[o] = RB[o + S] = RB[o + 2 * S] = make_double2(0, 0);
         return;
     }
     const double ir = g.invr[d.j];
-    const double* Lp = g.Lb + ((size_t)abs(d.m + 1) * g.nr + d.j) * kB;
-    const double* Lz = g.Lb + ((size_t)abs(d.m) * g.nr + d.j) * kB;
+    const double* Lb = slot_Lb(g, d.slot);
+    const double* Lp = Lb + ((size_t)abs(d.m + 1) * g.nr + d.j) * kB;
+    const double* Lz = Lb + ((size_t)abs(d.m) * g.nr + d.j) * kB;
     double2 tr = make_double2(0, 0), tt = make_double2(0, 0), sz = make_double2(0, 0);
     const double2 *ur = u, *ut = u + S, *uz = u + 2 * S;
     // rows j >= 4 touch columns j-4..j+4 only (9 entries), wall rows columns 0..8
@@ -367,12 +405,12 @@ __global__ void k_stage_bu(Geo g, const double2* __restrict__ u, double2* __rest
         tt = dfma(lp, ut[oc], tt);
         sz = dfma(__ldg(Lz + s), uz[oc], sz);
     }
-    const double dg = __ldg(g.dgt + d.k);
+    const double dg = __ldg(slot_dgt(g, d.slot) + d.k);
     const double2 a = ur[o], b = ut[o], c = uz[o];
     const double2 up = make_double2(a.x - b.y, a.y + b.x);
     const double2 um = make_double2(a.x + b.y, a.y - b.x);
     // the bands hold L / (2 Re), so the 4m/r^2 diagonal difference carries the same factor
-    const double fm = 4.0 * g.inv_2re * __ldg(g.mrt + (size_t)d.im * g.nr + d.j) * ir;
+    const double fm = 4.0 * g.inv_2re[d.slot] * __ldg(g.mrt + (size_t)d.im * g.nr + d.j) * ir;
     const double2 sp = make_double2(tr.x - tt.y, tr.y + tt.x);
     const double2 sm = make_double2(tr.x + tt.y + fm * um.x, tr.y - tt.x + fm * um.y);
     RB[o] = make_double2(fma(dg, up.x, sp.x), fma(dg, up.y, sp.y));
@@ -385,6 +423,10 @@ __global__ void k_stage_rhs(Geo g, const double2* __restrict__ RB, const double2
                             const double2* __restrict__ p, double2* __restrict__ R) {
     Idx d;
     if (!decode(g, d)) return;
+    RB = moved(RB, d.off);
+    F += d.off;
+    p += d.off;
+    R += d.off;
     const size_t o = sidx(g, d.j, d.im, d.k), S = d.S;
     if (d.j == 0) {
         R[o] = R[o + S] = R[o + 2 * S] = make_double2(0, 0);
@@ -426,6 +468,11 @@ __global__ void __launch_bounds__(kFK* kFJ) k_stage_finish(Geo g, const double2*
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int k = blockIdx.x * kFK + tx, im = blockIdx.y, m = im - g.M;
     const size_t S = (size_t)g.nr * g.nm * g.nk;
+    const int slot = g.slot[blockIdx.z];  // batch entry blockIdx.z
+    const size_t off = (size_t)slot * g.fs;
+    R += off;
+    addto = moved(addto, off);
+    out += off;
     const bool on = k < g.nk, mean = (m == 0 && k == 0);
     double2 part = make_double2(0, 0);
     if (on) {
@@ -446,7 +493,8 @@ __global__ void __launch_bounds__(kFK* kFJ) k_stage_finish(Geo g, const double2*
     double2 a0 = red[0][tx];
 #pragma unroll
     for (int i = 1; i < kFJ; ++i) a0 = make_double2(a0.x + red[i][tx].x, a0.y + red[i][tx].y);
-    const double* h = g.infl + ((size_t)im * g.nk + k) * 3 * g.nr;
+    const double* h = slot_infl(g, slot) + ((size_t)im * g.nk + k) * 3 * g.nr;
+    const double* fg = slot_fluxg(g, slot);
     for (int j = ty; j < g.nr; j += kFJ) {
         const size_t o = sidx(g, j, im, k);
         const double2 xp = R[o], xm = R[o + S];
@@ -454,7 +502,7 @@ __global__ void __launch_bounds__(kFK* kFJ) k_stage_finish(Geo g, const double2*
         double2 ut = make_double2(0.5 * (xp.y - xm.y), -0.5 * (xp.x - xm.x));
         double2 uz = R[o + 2 * S];
         if (mean) {
-            uz = dfma(g.fluxg[j] * (-g.flux_inv), a0, uz);
+            uz = dfma(fg[j] * (-g.flux_inv[slot]), a0, uz);
             ur = make_double2(0, 0);
         } else {
             const double h0 = h[j], h1 = h[g.nr + j], h2 = h[2 * g.nr + j];
@@ -482,14 +530,19 @@ __global__ void __launch_bounds__(kFK* kFJ) k_stageT_finish(Geo g, const double2
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int k = blockIdx.x * kFK + tx, im = blockIdx.y, m = im - g.M;
     const size_t S = (size_t)g.nr * g.nm * g.nk;
+    const int slot = g.slot[blockIdx.z];  // batch entry blockIdx.z
+    const size_t off = (size_t)slot * g.fs;
+    un += off;
+    R += off;
     const bool on = k < g.nk, mean = (m == 0 && k == 0);
-    const double* h = g.infl + ((size_t)im * g.nk + (on ? k : 0)) * 3 * g.nr;
+    const double* h = slot_infl(g, slot) + ((size_t)im * g.nk + (on ? k : 0)) * 3 * g.nr;
+    const double* fg = slot_fluxg(g, slot);
     double2 part = make_double2(0, 0);
     if (on) {
         for (int j = ty; j < g.nr; j += kFJ) {
             const size_t o = sidx(g, j, im, k);
             if (mean) {
-                part = dfma(g.fluxg[j], un[o + 2 * S], part);
+                part = dfma(fg[j], un[o + 2 * S], part);
             } else {
                 const double2 a = un[o], b = un[o + S], c = un[o + 2 * S];
                 // infl0 a - i infl1 b - i infl2 c
@@ -510,7 +563,7 @@ __global__ void __launch_bounds__(kFK* kFJ) k_stageT_finish(Geo g, const double2
         double2 yr = un[o], yt = un[o + S], yz = un[o + 2 * S];
         if (mean) {
             yr = make_double2(0, 0);
-            yz = dfma(-g.flux_inv * g.W[j], acc, yz);
+            yz = dfma(-g.flux_inv[slot] * g.W[j], acc, yz);
         } else if (j <= 8) {
             yr = dfma(__ldg(d0 + 4 + j), acc, yr);
         }
@@ -527,13 +580,18 @@ __global__ void k_stageT_rhs(Geo g, const double2* __restrict__ X, const double2
                              double cf2, double2* __restrict__ ub, int acc, double2* __restrict__ Fb) {
     Idx d;
     if (!decode(g, d)) return;
+    X += d.off;
+    Y = moved(Y, d.off);
+    ub = moved(ub, d.off);
+    Fb = moved(Fb, d.off);
     const size_t o = sidx(g, d.j, d.im, d.k), S = d.S;
     const double2 rp = X[o], rm = X[o + S], rz = X[o + 2 * S];
     if (ub) {
-        const double dg = __ldg(g.dgt + d.k);
-        const double2 bp0 = band_col(g, g.Lb + (size_t)abs(d.m + 1) * g.nr * kB, X, d.j, d.im, d.k);
-        const double2 bm0 = band_col(g, g.Lb + (size_t)abs(d.m - 1) * g.nr * kB, X + S, d.j, d.im, d.k);
-        const double2 bz0 = band_col(g, g.Lb + (size_t)abs(d.m) * g.nr * kB, X + 2 * S, d.j, d.im, d.k);
+        const double dg = __ldg(slot_dgt(g, d.slot) + d.k);
+        const double* Lb = slot_Lb(g, d.slot);
+        const double2 bp0 = band_col(g, Lb + (size_t)abs(d.m + 1) * g.nr * kB, X, d.j, d.im, d.k);
+        const double2 bm0 = band_col(g, Lb + (size_t)abs(d.m - 1) * g.nr * kB, X + S, d.j, d.im, d.k);
+        const double2 bz0 = band_col(g, Lb + (size_t)abs(d.m) * g.nr * kB, X + 2 * S, d.j, d.im, d.k);
         const double2 bp = make_double2(fma(dg, rp.x, bp0.x), fma(dg, rp.y, bp0.y));  // bands hold L / (2 Re)
         const double2 bm = make_double2(fma(dg, rm.x, bm0.x), fma(dg, rm.y, bm0.y));
         const double2 bz = make_double2(fma(dg, rz.x, bz0.x), fma(dg, rz.y, bz0.y));
@@ -569,6 +627,8 @@ __global__ void k_stageT_rhs(Geo g, const double2* __restrict__ X, const double2
 __global__ void k_stageT_qbar(Geo g, const double2* __restrict__ Fb, double2* __restrict__ q) {
     Idx d;
     if (!decode(g, d)) return;
+    Fb += d.off;
+    q += d.off;
     const size_t o = sidx(g, d.j, d.im, d.k), S = d.S;
     if (d.m == 0 && d.k == 0) {
         q[o] = make_double2(0, 0);
@@ -586,6 +646,8 @@ __global__ void k_stageT_qbar(Geo g, const double2* __restrict__ Fb, double2* __
 __global__ void k_stageT_div(Geo g, const double2* __restrict__ z, double2* __restrict__ Fb) {
     Idx d;
     if (!decode(g, d)) return;
+    z += d.off;
+    Fb += d.off;
     if (d.m == 0 && d.k == 0) return;
     const size_t o = sidx(g, d.j, d.im, d.k), S = d.S;
     const double kz = __ldg(g.kzt + d.k), ir = g.invr[d.j], mr = __ldg(g.mrt + (size_t)d.im * g.nr + d.j);
@@ -729,10 +791,15 @@ __global__ void k_mode_energy(Geo g, const double2* __restrict__ u, double* __re
 }
 
 // ------------------------------------------------------------------ elementwise / reductions
-__global__ void k_axpby(size_t n, double a, const double2* __restrict__ x, double b, const double2* __restrict__ y,
-                        double2* __restrict__ out) {
+// n values of batch entry blockIdx.y
+__global__ void k_axpby(Geo g, size_t n, double a, const double2* __restrict__ x, double b,
+                        const double2* __restrict__ y, double2* __restrict__ out) {
     const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
+    const size_t off = (size_t)g.slot[blockIdx.y] * g.fs;
+    x += off;
+    y = moved(y, off);
+    out += off;
     const double2 p = x[i];
     double2 r = make_double2(a * p.x, a * p.y);
     if (y) {
@@ -746,6 +813,8 @@ __global__ void k_axpby(size_t n, double a, const double2* __restrict__ x, doubl
 __global__ void k_weight(Geo g, const double2* __restrict__ x, double2* __restrict__ out, int divide) {
     Idx d;
     if (!decode(g, d)) return;
+    x += d.off;
+    out += d.off;
     const double w = g.ewt * g.W[d.j] * (d.k == 0 ? 1.0 : 2.0);
     const double f = divide ? 1.0 / w : w;
     for (int c = 0; c < 3; ++c) {
@@ -761,6 +830,8 @@ __global__ void k_inner_partial(Geo g, const double2* __restrict__ a, const doub
     Idx d;
     double acc = 0;
     if (decode(g, d)) {
+        a += d.off;
+        b += d.off;
         const double w = g.W[d.j] * (d.k == 0 ? 1.0 : 2.0);
         for (int c = 0; c < 3; ++c) {
             const size_t i = c * d.S + sidx(g, d.j, d.im, d.k);
@@ -777,9 +848,12 @@ __global__ void k_inner_partial(Geo g, const double2* __restrict__ a, const doub
     if (threadIdx.x == 0) partial[((size_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x] = red[0];
 }
 
-__global__ void k_inner_final(const double* __restrict__ partial, int np, double scale, double* __restrict__ out) {
+// Block b sums the np partials of batch entry b into out[slot[b]].
+__global__ void k_inner_final(Geo g, const double* __restrict__ partial, int np, double scale,
+                              double* __restrict__ out) {
     __shared__ double red[1024];
     double acc = 0;
+    partial += (size_t)blockIdx.x * np;
     for (int i = threadIdx.x; i < np; i += blockDim.x) acc += partial[i];
     red[threadIdx.x] = acc;
     __syncthreads();
@@ -787,13 +861,32 @@ __global__ void k_inner_final(const double* __restrict__ partial, int np, double
         if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
         __syncthreads();
     }
-    if (threadIdx.x == 0) out[0] = red[0] * scale;
+    if (threadIdx.x == 0) out[g.slot[blockIdx.x]] = red[0] * scale;
+}
+
+// x *= sqrt(E0 / (scale e2[slot])) over the 3 S values of batch entry blockIdx.y
+__global__ void k_scale_energy(Geo g, size_t n, double2* __restrict__ x, double E0, double scale,
+                               const double* __restrict__ e2) {
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int slot = g.slot[blockIdx.y];
+    const double f = sqrt(E0 / (scale * e2[slot]));
+    x += (size_t)slot * g.fs;
+    x[i] = make_double2(f * x[i].x, f * x[i].y);
 }
 
 // ------------------------------------------------------------------ launchers
 // block and grid of the 3-D spectral launches (x: k, y: m, z: r)
 static inline unsigned spec_bx(const Geo& g) { return g.nk <= 32 ? 32u : (g.nk <= 64 ? 64u : 128u); }
-static inline dim3 spec_grid(const Geo& g) { return dim3((g.nk + spec_bx(g) - 1) / spec_bx(g), g.nm, g.nr); }
+static inline dim3 spec_grid(const Geo& g) {
+    return dim3((g.nk + spec_bx(g) - 1) / spec_bx(g), g.nm, g.nr * g.nb);
+}
+// Operators that only single-request contexts use (continuous adjoint,
+// projection, diagnostics) index no slot: refuse a batched geometry.
+static void single_only(const Geo& g, const char* what) {
+    if (g.nb != 1 || g.slot[0] != 0)
+        throw std::runtime_error(std::string(what) + ": not available on batched launches");
+}
 
 void launch_curl(const Geo& g, const double2* u, double2* w, cudaStream_t s) {
     k_curl<<<spec_grid(g), spec_bx(g), 0, s>>>(g, u, w);
@@ -804,33 +897,34 @@ void launch_curlT_acc(const Geo& g, const double2* wb, double2* ub, cudaStream_t
     check_launch("curlT");
 }
 void launch_grad_u(const Geo& g, const double2* u, double2* G, cudaStream_t s) {
+    single_only(g, "grad_u");
     k_grad_u<<<spec_grid(g), spec_bx(g), 0, s>>>(g, u, G);
     check_launch("grad_u");
 }
-void launch_base_adj(const Geo& g, const double2* w, double2* N, double c, double sn, cudaStream_t s) {
-    k_base_adj<<<spec_grid(g), spec_bx(g), 0, s>>>(g, w, N, c, sn);
+void launch_base_adj(const Geo& g, const double2* w, double2* N, int ph, cudaStream_t s) {
+    k_base_adj<<<spec_grid(g), spec_bx(g), 0, s>>>(g, w, N, ph);
     check_launch("base_adj");
 }
-void launch_base(const Geo& g, const double2* u, double2* N, double c, double sn, cudaStream_t s) {
-    k_base<<<spec_grid(g), spec_bx(g), 0, s>>>(g, u, N, c, sn);
+void launch_base(const Geo& g, const double2* u, double2* N, int ph, cudaStream_t s) {
+    k_base<<<spec_grid(g), spec_bx(g), 0, s>>>(g, u, N, ph);
     check_launch("base");
 }
-void launch_baseT(const Geo& g, const double2* nb, double2* ub, double c, double sn, cudaStream_t s) {
-    k_baseT<<<spec_grid(g), spec_bx(g), 0, s>>>(g, nb, ub, c, sn);
+void launch_baseT(const Geo& g, const double2* nb, double2* ub, int ph, cudaStream_t s) {
+    k_baseT<<<spec_grid(g), spec_bx(g), 0, s>>>(g, nb, ub, ph);
     check_launch("baseT");
 }
 
 // trans (zero_row0 == 1) selects the transposed coefficient layout
-static void launch_band_solve(const Geo& g, const double* fac, double2* X, const double2* add, int helm, int zero_row0,
-                              cudaStream_t s) {
-    const unsigned nblocks = (unsigned)((helm ? 3 : 1) * g.nm * g.ntile);
+static void launch_band_solve(const Geo& g, const double* fac, size_t fac_stride, double2* X, const double2* add,
+                              int helm, int zero_row0, cudaStream_t s) {
+    const dim3 nblocks((unsigned)((helm ? 3 : 1) * g.nm * g.ntile), (unsigned)g.nb);
     const size_t sm = (size_t)g.nr * kSK * sizeof(double2) + 2 * (size_t)kRC * 9 * kSK * sizeof(double);
     if (!zero_row0) {
         smem_limit((const void*)k_band_solve<4, 8, false>);
-        k_band_solve<4, 8, false><<<nblocks, 2 * kSK, sm, s>>>(g, fac, X, add, helm, 0);
+        k_band_solve<4, 8, false><<<nblocks, 2 * kSK, sm, s>>>(g, fac, fac_stride, X, add, helm, 0);
     } else {
         smem_limit((const void*)k_band_solve<8, 4, true>);
-        k_band_solve<8, 4, true><<<nblocks, 2 * kSK, sm, s>>>(g, fac, X, add, helm, 1);
+        k_band_solve<8, 4, true><<<nblocks, 2 * kSK, sm, s>>>(g, fac, fac_stride, X, add, helm, 1);
     }
 }
 
@@ -839,7 +933,7 @@ void launch_stage_div(const Geo& g, const double2* F, double2* q, cudaStream_t s
     check_launch("stage_div");
 }
 void launch_stage_psolve(const Geo& g, double2* q, cudaStream_t s) {
-    launch_band_solve(g, g.facP, q, nullptr, 0, 0, s);
+    launch_band_solve(g, g.facP, 0, q, nullptr, 0, 0, s);
     check_launch("stage_psolve");
 }
 void launch_stage_bu(const Geo& g, const double2* u, double2* RB, cudaStream_t s) {
@@ -851,10 +945,10 @@ void launch_stage_rhs(const Geo& g, const double2* RB, const double2* F, const d
     check_launch("stage_rhs");
 }
 void launch_stage_hsolve(const Geo& g, double2* R, cudaStream_t s) {
-    launch_band_solve(g, g.facH, R, nullptr, 1, 0, s);
+    launch_band_solve(g, g.facH, g.sFacH, R, nullptr, 1, 0, s);
     check_launch("stage_hsolve");
 }
-static inline dim3 mode_grid(const Geo& g) { return dim3((g.nk + kFK - 1) / kFK, g.nm); }
+static inline dim3 mode_grid(const Geo& g) { return dim3((g.nk + kFK - 1) / kFK, g.nm, g.nb); }
 void launch_stage_finish(const Geo& g, const double2* R, const double2* addto, double2* out, cudaStream_t s) {
     k_stage_finish<<<mode_grid(g), dim3(kFK, kFJ), 0, s>>>(g, R, addto, out);
     check_launch("stage_finish");
@@ -864,7 +958,7 @@ void launch_stageT_finish(const Geo& g, const double2* ubn, double2* R, cudaStre
     check_launch("stageT_finish");
 }
 void launch_stageT_hsolve(const Geo& g, double2* R, const double2* add, cudaStream_t s) {
-    launch_band_solve(g, g.facHT, R, add, 1, 1, s);
+    launch_band_solve(g, g.facHT, g.sFacH, R, add, 1, 1, s);
     check_launch("stageT_hsolve");
 }
 void launch_stageT_rhs(const Geo& g, const double2* X, const double2* Y, double cf1, double cf2, double2* ub, int acc,
@@ -880,7 +974,7 @@ void launch_stageT_qbar(const Geo& g, const double2* Fb, double2* q, cudaStream_
     check_launch("stageT_qbar");
 }
 void launch_stageT_psolve(const Geo& g, double2* q, cudaStream_t s) {
-    launch_band_solve(g, g.facPT, q, nullptr, 0, 1, s);
+    launch_band_solve(g, g.facPT, 0, q, nullptr, 0, 1, s);
     check_launch("stageT_psolve");
 }
 void launch_stageT_div(const Geo& g, const double2* z, double2* Fb, cudaStream_t s) {
@@ -889,11 +983,13 @@ void launch_stageT_div(const Geo& g, const double2* z, double2* Fb, cudaStream_t
 }
 
 void launch_mode_energy(const Geo& g, const double2* u, double* E, cudaStream_t s) {
+    single_only(g, "mode_energy");
     k_mode_energy<<<nblk((size_t)g.nm * g.nk, 128), 128, 0, s>>>(g, u, E);
     check_launch("mode_energy");
 }
 
 void launch_project(const Geo& g, double2* u, double2* y, const double* L, cudaStream_t s) {
+    single_only(g, "project");
     k_proj_herm<<<nblk((size_t)3 * g.nr * (g.M + 1), 128), 128, 0, s>>>(g, u);
     k_proj_div<<<spec_grid(g), spec_bx(g), 0, s>>>(g, u, y);
     k_proj_solve<<<nblk((size_t)2 * g.nm * g.nk, 64), 64, 0, s>>>(g, L, u, y);
@@ -901,8 +997,9 @@ void launch_project(const Geo& g, double2* u, double2* y, const double* L, cudaS
     check_launch("project");
 }
 
-void launch_axpby(size_t n, double a, const double2* x, double b, const double2* y, double2* out, cudaStream_t s) {
-    k_axpby<<<nblk(n, 256), 256, 0, s>>>(n, a, x, b, y, out);
+void launch_axpby(const Geo& g, size_t n, double a, const double2* x, double b, const double2* y, double2* out,
+                  cudaStream_t s) {
+    k_axpby<<<dim3(nblk(n, 256), g.nb), 256, 0, s>>>(g, n, a, x, b, y, out);
     check_launch("axpby");
 }
 void launch_weight(const Geo& g, const double2* x, double2* out, int divide, cudaStream_t s) {
@@ -916,8 +1013,13 @@ size_t inner_partials(const Geo& g) {
 void launch_inner(const Geo& g, const double2* a, const double2* b, double* partial, double* dev_out, cudaStream_t s) {
     const dim3 grid = spec_grid(g);
     k_inner_partial<<<grid, spec_bx(g), 0, s>>>(g, a, b, partial);
-    k_inner_final<<<1, 1024, 0, s>>>(partial, (int)(grid.x * grid.y * grid.z), g.ewt, dev_out);
+    k_inner_final<<<g.nb, 1024, 0, s>>>(g, partial, (int)(grid.x * grid.y * (grid.z / g.nb)), g.ewt, dev_out);
     check_launch("inner");
+}
+void launch_scale_energy(const Geo& g, double2* x, double E0, double scale, const double* e2, cudaStream_t s) {
+    const size_t n = 3 * (size_t)g.nr * g.nm * g.nk;
+    k_scale_energy<<<dim3(nblk(n, 256), g.nb), 256, 0, s>>>(g, n, x, E0, scale, e2);
+    check_launch("scale_energy");
 }
 
 }  // namespace pnop

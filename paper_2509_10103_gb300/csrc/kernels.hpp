@@ -9,12 +9,13 @@ namespace pnop {
 // factor tables are tiled in k by the same count.
 constexpr int kSK = 32;
 
+// Most requests one batched launch covers (one storage slot each).
+constexpr int kMaxBatch = 16;
+
 // Read-only geometry and operators, passed to kernels by value.
 struct Geo {
     int nr, M, K, nm, nk, nt, nzp;
     double kz0;      // 2 pi / Lz
-    double inv_dt;   // 1 / dt
-    double inv_2re;  // 1 / (2 Re)
     const double* r;
     const double* invr;
     const double* W;
@@ -27,7 +28,6 @@ struct Geo {
     const double* facPT;
     const double* infl;  // [nm][nk][3][nr]
     const double* fluxg; // [nr]
-    double flux_inv;
     const double2* Uh;   // [nr]
     const double2* dUh;  // [nr]
     double ewt;          // 2 pi Lz (energy weight prefactor)
@@ -37,6 +37,21 @@ struct Geo {
     const double* kzt;
     const double* mrt;
     const double* dgt;
+    // Batched launches.  A launch covers nb requests; entry b works on storage
+    // slot slot[b].  Every spectral buffer holds one field per slot, slot s at
+    // element s * fs; every physical scratch buffer one set of planes per slot
+    // at s * ps.  The tables that depend on the request's Re, dt, Wo and A
+    // (Lb, facH, facHT, infl, fluxg, Uh, dUh, dgt) hold one copy per slot at
+    // the strides below; r, W, D1, facP, facPT, kzt, mrt and the twiddles
+    // depend on the grid only and are shared.  A single-request context has
+    // nb = 1 and slot[0] = 0, so no pointer moves.
+    int nb;
+    int slot[kMaxBatch];
+    size_t fs, ps;
+    size_t sLb, sFacH, sInfl, sNr, sNk;
+    double inv_2re[kMaxBatch];   // 1 / (2 Re) per slot
+    double flux_inv[kMaxBatch];  // flux normalisation per slot
+    double2 cs[2][kMaxBatch];    // (cos, sin) of the pulsation phase of entry b at the step's two stage times
 };
 
 // Up to 18 input / 6 output spectral component planes for the transforms; the
@@ -76,11 +91,12 @@ void launch_curlT_acc(const Geo& g, const double2* wb, double2* ub, cudaStream_t
 // derivative direction), and the base-flow part of its forcing
 // Nb = U dw/dz - w_z dU/dr e_r (written)
 void launch_grad_u(const Geo& g, const double2* u, double2* G, cudaStream_t s);
-void launch_base_adj(const Geo& g, const double2* w, double2* N, double c, double sn, cudaStream_t s);
+void launch_base_adj(const Geo& g, const double2* w, double2* N, int ph, cudaStream_t s);
 // base-flow terms in advective form: N = -U du/dz - u_r dU/dr e_z, and their
-// transpose ub = (dN/du)^T nb (both written, not accumulated)
-void launch_base(const Geo& g, const double2* u, double2* N, double c, double sn, cudaStream_t s);
-void launch_baseT(const Geo& g, const double2* nb, double2* ub, double c, double sn, cudaStream_t s);
+// transpose ub = (dN/du)^T nb (both written, not accumulated), at the phase
+// g.cs[ph][b] of each batch entry
+void launch_base(const Geo& g, const double2* u, double2* N, int ph, cudaStream_t s);
+void launch_baseT(const Geo& g, const double2* nb, double2* ub, int ph, cudaStream_t s);
 
 // ---- transforms (T = double for FP64, float for mixed) ----
 template <class T2>
@@ -122,11 +138,16 @@ void launch_mode_energy(const Geo& g, const double2* u, double* E, cudaStream_t 
 void launch_project(const Geo& g, double2* u, double2* y, const double* L, cudaStream_t s);
 
 // ---- elementwise / reductions ----
-void launch_axpby(size_t n, double a, const double2* x, double b, const double2* y, double2* out, cudaStream_t s);
+// out = a x + b y over n values per batch entry (y may be null)
+void launch_axpby(const Geo& g, size_t n, double a, const double2* x, double b, const double2* y, double2* out,
+                  cudaStream_t s);
 void launch_weight(const Geo& g, const double2* x, double2* out, int divide, cudaStream_t s);
-// Deterministic weighted inner product sum W_hat Re(conj(a) b); result to dev_out[0].
-// partial must hold inner_partials(g) doubles (one per block, fixed order).
+// Deterministic weighted inner product sum W_hat Re(conj(a) b); the result of
+// batch entry b to dev_out[slot[b]].  partial must hold inner_partials(g)
+// doubles (one per block, fixed order).
 void launch_inner(const Geo& g, const double2* a, const double2* b, double* partial, double* dev_out, cudaStream_t s);
 size_t inner_partials(const Geo& g);
+// x *= sqrt(E0 / (scale * e2[slot])) for every batch entry (e2 from launch_inner)
+void launch_scale_energy(const Geo& g, double2* x, double E0, double scale, const double* e2, cudaStream_t s);
 
 }  // namespace pnop

@@ -50,6 +50,25 @@ struct Action {
     int slot, dst, host;
 };
 
+// One request of a batched context, as a queue of per-slot operations: copies
+// between the slot's state and its checkpoints, forward steps, the terminal
+// step, adjoint steps and the final Riesz map.
+enum OpKind { kOpRestore = 0, kOpStore = 1, kOpFwd = 2, kOpTerm = 3, kOpAdj = 4, kOpFinish = 5 };
+struct Op {
+    int kind;
+    long long n;  // step index (kOpFwd, kOpTerm, kOpAdj)
+    int snap;     // checkpoint index (kOpRestore, kOpStore)
+};
+struct BatchReq {
+    bool active = false, done = false, fetched = true;
+    int id = -1;
+    double Re = 0, Wo = 0, A = 0, dt = 0, tau0 = 0, omega = 0, E0 = 0;
+    long long N = 0;
+    std::vector<Op> ops;
+    size_t pos = 0;
+    cudaEvent_t ev_done = nullptr;
+};
+
 bool smooth_size(int n) {
     if (n < 2) return false;
     while (n % 2 == 0) n /= 2;
@@ -134,6 +153,17 @@ struct pnop_ctx {
     double prof_ms[PNOP_K_NCLASS] = {};
     long long launches[PNOP_K_NCLASS] = {};
     double units[PNOP_K_NCLASS] = {};
+    // batched context: nslot storage slots, one request each; every spectral
+    // buffer (fields, checkpoints, scratch) holds nslot fields at stride 3 S
+    int nslot = 1;
+    bool batched = false;
+    double bt[pnop::kMaxBatch] = {};  // step start time of each entry of the current batched launch
+    std::vector<BatchReq> breq;       // per slot
+    int next_id = 0;
+    double2* bcur = nullptr;          // per-slot current state
+    double2* blam = nullptr;          // per-slot cotangent
+    double *d_e0 = nullptr, *d_eT = nullptr;  // per-slot 2 E(0) and 2 E(T) (inner products)
+    long long b_ticks = 0, b_launch_entries = 0;
 
     size_t S() const { return (size_t)h.d.nr * h.d.nm * h.d.nk; }
     size_t field_bytes() const { return 3 * S() * sizeof(double2); }
@@ -157,7 +187,7 @@ struct pnop_ctx {
         if (!v.empty()) ck(cudaMemcpy(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice), "upload");
         return p;
     }
-    double2* field() { return (double2*)dalloc(field_bytes()); }
+    double2* field() { return (double2*)dalloc((size_t)nslot * field_bytes()); }
 };
 
 namespace {
@@ -178,18 +208,21 @@ template <class T2> std::vector<T2> twiddle_table(int N) {
     return t;
 }
 
-void upload_operators(pnop_ctx* c) {
-    // operator tables that depend on Re/dt/Wo/A are re-uploaded on change
-    const auto& h = c->h;
-    auto put = [&](double*& dst, const std::vector<double>& v) {
-        if (!dst) dst = c->upload(v);
-        else ck(cudaMemcpy(dst, v.data(), v.size() * sizeof(double), cudaMemcpyHostToDevice), "upload");
+// Tables of slot `slot` from the operators h was built with (Re, dt, Wo and
+// A of that slot's request).  The per-slot tables are allocated for all slots
+// on first use; the grid-only tables (pressure factors) are written once.
+void upload_slot_operators(pnop_ctx* c, int slot, const pnop::HostOps& h) {
+    const size_t ns = (size_t)c->nslot;
+    auto put = [&](double*& dst, const std::vector<double>& v, size_t slots, size_t at) {
+        if (!dst) dst = (double*)c->dalloc(std::max<size_t>(1, v.size()) * slots * sizeof(double));
+        ck(cudaMemcpy(dst + at * v.size(), v.data(), v.size() * sizeof(double), cudaMemcpyHostToDevice), "upload");
     };
     {
         // device bands hold L_m / (2 Re): the explicit Crank-Nicolson half B = 1/dt + L/(2 Re)
         std::vector<double> lb(h.Lb);
         for (double& x : lb) x /= 2.0 * h.ph.Re;
-        put(c->d_Lb, lb);
+        put(c->d_Lb, lb, ns, slot);
+        c->geo.sLb = lb.size();
     }
     {
         std::vector<double> dg(h.d.nk);
@@ -197,25 +230,31 @@ void upload_operators(pnop_ctx* c) {
             const double kz = 2.0 * M_PI * k / h.d.Lz;
             dg[k] = 1.0 / h.ph.dt - kz * kz / (2.0 * h.ph.Re);
         }
-        put(c->d_dgt, dg);
+        put(c->d_dgt, dg, ns, slot);
+        c->geo.sNk = dg.size();
     }
-    put(c->d_facH, h.facH);
-    put(c->d_facP, h.facP);
-    put(c->d_facHT, h.facHT);
-    put(c->d_facPT, h.facPT);
-    put(c->d_infl, h.infl);
-    put(c->d_fluxg, h.fluxg);
+    put(c->d_facH, h.facH, ns, slot);
+    put(c->d_facHT, h.facHT, ns, slot);
+    c->geo.sFacH = h.facH.size();
+    if (!c->d_facP) {
+        put(c->d_facP, h.facP, 1, 0);
+        put(c->d_facPT, h.facPT, 1, 0);
+    }
+    put(c->d_infl, h.infl, ns, slot);
+    c->geo.sInfl = h.infl.size();
+    put(c->d_fluxg, h.fluxg, ns, slot);
+    c->geo.sNr = h.fluxg.size();
     auto uh = cvec(h.Uh), duh = cvec(h.dUh);
     if (!c->d_Uh) {
-        c->d_Uh = c->upload(uh);
-        c->d_dUh = c->upload(duh);
-    } else {
-        ck(cudaMemcpy(c->d_Uh, uh.data(), uh.size() * sizeof(double2), cudaMemcpyHostToDevice), "upload");
-        ck(cudaMemcpy(c->d_dUh, duh.data(), duh.size() * sizeof(double2), cudaMemcpyHostToDevice), "upload");
+        c->d_Uh = (double2*)c->dalloc(uh.size() * ns * sizeof(double2));
+        c->d_dUh = (double2*)c->dalloc(duh.size() * ns * sizeof(double2));
     }
+    ck(cudaMemcpy(c->d_Uh + slot * uh.size(), uh.data(), uh.size() * sizeof(double2), cudaMemcpyHostToDevice), "upload");
+    ck(cudaMemcpy(c->d_dUh + slot * duh.size(), duh.data(), duh.size() * sizeof(double2), cudaMemcpyHostToDevice),
+       "upload");
     Geo& g = c->geo;
-    g.inv_dt = 1.0 / h.ph.dt;
-    g.inv_2re = 1.0 / (2.0 * h.ph.Re);
+    g.inv_2re[slot] = 1.0 / (2.0 * h.ph.Re);
+    g.flux_inv[slot] = h.flux_inv;
     g.Lb = c->d_Lb;
     g.dgt = c->d_dgt;
     g.facH = c->d_facH;
@@ -225,10 +264,12 @@ void upload_operators(pnop_ctx* c) {
     g.ntile = h.ntile;
     g.infl = c->d_infl;
     g.fluxg = c->d_fluxg;
-    g.flux_inv = h.flux_inv;
     g.Uh = c->d_Uh;
     g.dUh = c->d_dUh;
 }
+
+// operator tables that depend on Re/dt/Wo/A are re-uploaded on change
+void upload_operators(pnop_ctx* c) { upload_slot_operators(c, 0, c->h); }
 
 bool mixed(const pnop_ctx* c) { return c->prm.precision == PNOP_MIXED; }
 
@@ -243,12 +284,12 @@ void prof_flush(pnop_ctx* c) {
     c->ev_used = 0;
 }
 
-// Launch `nk` kernels of class `cls` doing `units` work units on stream `st`
-// (the context stream by default); bracket them with CUDA events on that
-// stream when the class is being timed.
+// Launch `nk` kernels of class `cls` doing `units` work units per batch entry
+// on stream `st` (the context stream by default); bracket them with CUDA
+// events on that stream when the class is being timed.
 template <class F> void run(pnop_ctx* c, int cls, int nk, double units, F&& f, cudaStream_t st) {
     c->launches[cls] += nk;
-    c->units[cls] += units;
+    c->units[cls] += units * c->geo.nb;
     if (!(c->prof_mask & (1u << cls))) {
         f();
         return;
@@ -377,7 +418,7 @@ void project(pnop_ctx* c, double2* u) {
 
 void axpby(pnop_ctx* c, double a, const double2* x, double b, const double2* y, double2* out) {
     const size_t n = 3 * c->S();
-    run(c, PNOP_K_ELEMENTWISE, 1, (double)n, [&] { pnop::launch_axpby(n, a, x, b, y, out, c->stream); });
+    run(c, PNOP_K_ELEMENTWISE, 1, (double)n, [&] { pnop::launch_axpby(c->geo, n, a, x, b, y, out, c->stream); });
 }
 void weight(pnop_ctx* c, const double2* x, double2* out, int divide) {
     run(c, PNOP_K_ELEMENTWISE, 1, 3.0 * c->S(), [&] { pnop::launch_weight(c->geo, x, out, divide, c->stream); });
@@ -415,12 +456,30 @@ void transforms(pnop_ctx* c, const pnop::FieldPtrs& f, int nin, int nout, int zm
 }
 
 // ------------------------------------------------------------------ nonlinear term
+// Pulsation phase (cos, sin of omega t) of every batch entry into geo.cs[0]
+// for the next launches.  A single-request context takes t itself; a batched
+// context reads t as a step offset (0: the entry's step start, 1: its end)
+// and adds it to the entry's own start time with its own dt and omega.
+void set_phase(pnop_ctx* c, double t) {
+    Geo& g = c->geo;
+    if (!c->batched) {
+        const double ph = c->h.omega * t;
+        g.cs[0][0] = make_double2(std::cos(ph), std::sin(ph));
+        return;
+    }
+    for (int b = 0; b < g.nb; ++b) {
+        const BatchReq& r = c->breq[g.slot[b]];
+        const double ph = r.omega * (c->bt[b] + t * r.dt);
+        g.cs[0][b] = make_double2(std::cos(ph), std::sin(ph));
+    }
+}
+
 // Base-flow terms of N(u) at time t into Nbase on the side stream (the caller
 // has forked it); the analysis of the transforms adds them after ev_base.
 void queue_base(pnop_ctx* c, const double2* u, double t) {
-    const double ph = c->h.omega * t;
-    run(c, PNOP_K_SPECTRAL, 1, flops::base * c->S(),
-        [&] { pnop::launch_base(c->geo, u, c->Nbase, std::cos(ph), std::sin(ph), c->side); }, c->side);
+    set_phase(c, t);
+    run(c, PNOP_K_SPECTRAL, 1, flops::base * c->S(), [&] { pnop::launch_base(c->geo, u, c->Nbase, 0, c->side); },
+        c->side);
     ck(cudaEventRecord(c->ev_base, c->side), "record");
 }
 
@@ -459,9 +518,8 @@ void nonlinearT(pnop_ctx* c, const double2* u, double t, const double2* nb, doub
     const size_t S = c->S();
     cudaStream_t s = c->stream;
     fork_side(c);
-    const double ph = c->h.omega * t;
-    run(c, PNOP_K_SPECTRAL, 1, flops::base * S,
-        [&] { pnop::launch_baseT(g, nb, c->Nbase, std::cos(ph), std::sin(ph), c->side); }, c->side);
+    set_phase(c, t);
+    run(c, PNOP_K_SPECTRAL, 1, flops::base * S, [&] { pnop::launch_baseT(g, nb, c->Nbase, 0, c->side); }, c->side);
     ck(cudaEventRecord(c->ev_base, c->side), "record");
     if (!cached) run(c, PNOP_K_SPECTRAL, 1, flops::curl * S, [&] { pnop::launch_curl(g, u, c->omega, s); });
     pnop::FieldPtrs f{};
@@ -496,9 +554,9 @@ void nonlinearT(pnop_ctx* c, const double2* u, double t, const double2* nb, doub
 // the base-flow part on the side stream (queued by the caller when
 // base_queued), added by the analysis.
 void queue_base_adj(pnop_ctx* c, const double2* w, double t) {
-    const double ph = c->h.omega * t;
-    run(c, PNOP_K_SPECTRAL, 1, flops::base * c->S(),
-        [&] { pnop::launch_base_adj(c->geo, w, c->Nbase, std::cos(ph), std::sin(ph), c->side); }, c->side);
+    set_phase(c, t);
+    run(c, PNOP_K_SPECTRAL, 1, flops::base * c->S(), [&] { pnop::launch_base_adj(c->geo, w, c->Nbase, 0, c->side); },
+        c->side);
     ck(cudaEventRecord(c->ev_base, c->side), "record");
 }
 
@@ -1048,6 +1106,174 @@ void optimise_impl(pnop_ctx* c, double2* u, double E0, double horizon, int max_i
     wait_stream(c, "optimise sync");
 }
 
+// ------------------------------------------------------------------ batched gradients
+// A batched context runs the checkpointed gradient of up to nslot requests of
+// one grid, each with its own Re, Wo, A, dt, tau0, E0 and horizon.  Each
+// request turns its binomial schedule (Section 2.5) into a queue of per-slot
+// operations; a tick takes every request to its next step and launches one
+// batched forward, terminal or adjoint step for all requests whose next step
+// is of the kind most of them wait for.  The steps are the same
+// predictor-corrector step and its exact transpose as the single-request
+// path, in place on the slot's state and cotangent, so every request gets
+// bitwise the gradient it gets alone.
+
+// Active batch entries of the next launches: geo.nb and geo.slot.
+void batch_select(pnop_ctx* c, const std::vector<int>& slots) {
+    Geo& g = c->geo;
+    g.nb = (int)slots.size();
+    for (int b = 0; b < g.nb; ++b) g.slot[b] = slots[b];
+}
+void batch_reset(pnop_ctx* c) {
+    c->geo.nb = 1;
+    c->geo.slot[0] = 0;
+}
+
+double2* slot_ptr(pnop_ctx* c, double2* base, int slot) { return base + (size_t)slot * 3 * c->S(); }
+
+// Queue of operations of one request from its binomial plan: the first
+// adjoint step (N - 1) is preceded by the terminal step u_{N-1} -> u_N.
+void batch_ops(BatchReq& r, const std::vector<Action>& P) {
+    r.ops.clear();
+    bool first_adj = true;
+    for (const Action& a : P) {
+        if (a.kind == kAdv) {
+            r.ops.push_back({kOpRestore, 0, a.slot});
+            for (long long i = 0; i < a.n; ++i) r.ops.push_back({kOpFwd, a.start + i, -1});
+            if (a.dst >= 0) r.ops.push_back({kOpStore, 0, a.dst});
+        } else if (a.kind == kAdj) {
+            if (a.slot >= 0) r.ops.push_back({kOpRestore, 0, a.slot});
+            if (first_adj) {
+                if (a.start != r.N - 1) throw Status(PNOP_ERR_INVALID_ARG, "checkpoint schedule out of order");
+                r.ops.push_back({kOpTerm, r.N - 1, -1});
+                first_adj = false;
+            }
+            r.ops.push_back({kOpAdj, a.start, -1});
+        } else {
+            throw Status(PNOP_ERR_UNSUPPORTED, "host checkpoints are not used by batched contexts");
+        }
+    }
+    r.ops.push_back({kOpFinish, 0, -1});
+    r.pos = 0;
+}
+
+int batch_submit(pnop_ctx* c, const pnop_params* p, const double2* u0, double E0, double horizon) {
+    if (!p || !u0 || !(p->Re > 0) || !(p->dt > 0) || !(p->A >= 0) || !(p->Wo > 0 || p->A == 0))
+        throw Status(PNOP_ERR_INVALID_ARG, "bad request parameters");
+    const double nd = horizon / p->dt;
+    const long long N = (long long)std::llround(nd);
+    if (!(horizon > 0) || N < 1 || std::fabs(nd - (double)N) > 1e-9 * std::max(1.0, nd))
+        throw Status(PNOP_ERR_INVALID_ARG, "horizon must be a positive whole number of time steps");
+    int slot = -1;
+    for (int i = 0; i < c->nslot; ++i)
+        if (!c->breq[i].active && c->breq[i].fetched) {
+            slot = i;
+            break;
+        }
+    if (slot < 0) throw Status(PNOP_ERR_OOM, "no free slot in the batch");
+    // operators of this request's physics into the slot's tables (the slot
+    // is idle: no queued launch reads them)
+    pnop::HostOps hs = c->h;
+    hs.ph = {p->Re, p->Wo, p->A, p->dt, p->tau0};
+    std::string err;
+    if (!pnop::build_operators(hs, err)) throw Status(PNOP_ERR_UNSUPPORTED, err);
+    upload_slot_operators(c, slot, hs);
+    const int s = (int)std::max<long long>(1, std::min<long long>(c->prm.snap_budget, N));
+    while ((int)c->snaps.size() < s) c->snaps.push_back(c->field());
+    BatchReq& r = c->breq[slot];
+    r.Re = p->Re;
+    r.Wo = p->Wo;
+    r.A = p->A;
+    r.dt = p->dt;
+    r.tau0 = p->tau0;
+    r.omega = hs.omega;
+    r.E0 = E0;
+    r.N = N;
+    std::vector<Action> P;
+    plan_reverse(P, 0, N, 0, s);
+    batch_ops(r, P);
+    if (!r.ev_done) ck(cudaEventCreateWithFlags(&r.ev_done, cudaEventDisableTiming), "event");
+    // u0 into checkpoint 0, scaled to E0 on the device (as the single path does on the host)
+    double2* s0 = slot_ptr(c, c->snaps[0], slot);
+    ck(cudaMemcpyAsync(s0, u0, c->field_bytes(), cudaMemcpyDeviceToDevice, c->stream), "copy u0");
+    batch_select(c, {slot});
+    inner_dev(c, c->snaps[0], c->snaps[0], c->d_e0);
+    if (E0 > 0) {
+        run(c, PNOP_K_ELEMENTWISE, 1, 3.0 * c->S(),
+            [&] { pnop::launch_scale_energy(c->geo, c->snaps[0], E0, 0.5, c->d_e0, c->stream); });
+        inner_dev(c, c->snaps[0], c->snaps[0], c->d_e0);
+    }
+    batch_reset(c);
+    r.id = c->next_id++;
+    r.active = true;
+    r.done = false;
+    r.fetched = false;
+    return r.id;
+}
+
+// One tick: copies and finished requests first, then one batched step.
+// Returns false when no request has work left.
+bool batch_tick(pnop_ctx* c) {
+    std::vector<int> lists[3], fin;  // kOpFwd, kOpTerm, kOpAdj
+    const size_t fb = c->field_bytes();
+    for (int i = 0; i < c->nslot; ++i) {
+        BatchReq& r = c->breq[i];
+        if (!r.active || r.done) continue;
+        while (r.pos < r.ops.size() && (r.ops[r.pos].kind == kOpRestore || r.ops[r.pos].kind == kOpStore)) {
+            const Op& o = r.ops[r.pos++];
+            double2* st = slot_ptr(c, c->bcur, i);
+            double2* ck_ = slot_ptr(c, c->snaps[o.snap], i);
+            if (o.kind == kOpRestore) ck(cudaMemcpyAsync(st, ck_, fb, cudaMemcpyDeviceToDevice, c->stream), "restore");
+            else ck(cudaMemcpyAsync(ck_, st, fb, cudaMemcpyDeviceToDevice, c->stream), "store");
+        }
+        const int k = r.ops[r.pos].kind;
+        if (k == kOpFinish) fin.push_back(i);
+        else lists[k - kOpFwd].push_back(i);
+    }
+    if (!fin.empty()) {  // gradient = W_hat^-1 cotangent (Riesz), into the slot's result field
+        batch_select(c, fin);
+        weight(c, c->blam, c->uN, 1);
+        batch_reset(c);
+        for (int i : fin) {
+            BatchReq& r = c->breq[i];
+            ck(cudaEventRecord(r.ev_done, c->stream), "record");
+            r.done = true;
+            ++r.pos;
+        }
+    }
+    // the kind with most waiting requests (ties: adjoint, forward, terminal)
+    int kind = -1;
+    size_t best = 0;
+    for (int k : {2, 0, 1})
+        if (lists[k].size() > best) {
+            best = lists[k].size();
+            kind = k;
+        }
+    if (kind < 0) return !fin.empty();
+    const std::vector<int>& sel = lists[kind];
+    batch_select(c, sel);
+    for (int b = 0; b < (int)sel.size(); ++b) {
+        const BatchReq& r = c->breq[sel[b]];
+        c->bt[b] = r.tau0 + r.ops[r.pos].n * r.dt;
+    }
+    if (kind == 0) {
+        fwd_step(c, c->bcur, c->bcur, 0.0);
+        c->st_adv += (long long)sel.size();
+    } else if (kind == 1) {  // terminal step, its energy, and the terminal cotangent W_hat u_N
+        fwd_step(c, c->bcur, c->uN, 0.0);
+        inner_dev(c, c->uN, c->uN, c->d_eT);
+        weight(c, c->uN, c->blam, 0);
+        c->st_adv += (long long)sel.size();
+    } else {
+        adj_step(c, c->bcur, 0.0, c->blam, c->blam);
+        c->st_adj += (long long)sel.size();
+    }
+    batch_reset(c);
+    for (int i : sel) ++c->breq[i].pos;
+    ++c->b_ticks;
+    c->b_launch_entries += (long long)sel.size();
+    return true;
+}
+
 }  // namespace
 
 // ====================================================================== C ABI
@@ -1116,14 +1342,22 @@ void pnop_destroy(pnop_ctx* ctx) {
     for (cudaEvent_t e : {ctx->ev_copy, ctx->ev_staged})
         if (e) cudaEventDestroy(e);
     for (void* p : ctx->host) cudaFreeHost(p);
+    for (auto& r : ctx->breq)
+        if (r.ev_done) cudaEventDestroy(r.ev_done);
     for (void* p : ctx->allocs) cudaFree(p);
     delete ctx;
 }
 
-int pnop_create(const pnop_grid* grid, const pnop_params* params, void* cuda_stream, pnop_ctx** out) {
+}  // extern "C"
+
+namespace {
+// A context with nslot storage slots (1: the single-request context of
+// pnop_create; batched: pnop_batch_create, one request per slot).
+int create_impl(const pnop_grid* grid, const pnop_params* params, void* cuda_stream, int nslot, bool batched,
+                pnop_ctx** out) {
     if (!out) return PNOP_ERR_INVALID_ARG;
     *out = nullptr;
-    if (!grid || !params) return PNOP_ERR_INVALID_ARG;
+    if (!grid || !params || nslot < 1 || nslot > pnop::kMaxBatch) return PNOP_ERR_INVALID_ARG;
     if (grid->nr < 9 || grid->ntheta < 4 || grid->nz < 4 || (grid->ntheta & 1) || (grid->nz & 1) ||
         !(grid->Lz > 0) || !(grid->stretch >= 0 && grid->stretch < 1))
         return PNOP_ERR_INVALID_ARG;
@@ -1136,6 +1370,8 @@ int pnop_create(const pnop_grid* grid, const pnop_params* params, void* cuda_str
     pnop_ctx* c = new pnop_ctx();
     c->prm = *params;
     c->stream = (cudaStream_t)cuda_stream;
+    c->nslot = nslot;
+    c->batched = batched;
     pnop::Dims& d = c->h.d;
     d.nr = grid->nr;
     d.M = M;
@@ -1161,6 +1397,9 @@ int pnop_create(const pnop_grid* grid, const pnop_params* params, void* cuda_str
         g.nzp = d.nzp;
         g.kz0 = 2.0 * M_PI / d.Lz;
         g.ewt = 2.0 * M_PI * d.Lz;
+        g.nb = 1;
+        g.slot[0] = 0;
+        g.fs = 3 * c->S();
         c->d_r = c->upload(c->h.r);
         c->d_invr = c->upload(c->h.invr);
         c->d_W = c->upload(c->h.W);
@@ -1185,20 +1424,33 @@ int pnop_create(const pnop_grid* grid, const pnop_params* params, void* cuda_str
         c->tw.th_f = c->upload(thf);
         c->tw.z_f = c->upload(zf);
         for (double2** b : {&c->omega, &c->N0, &c->N1, &c->us, &c->ua, &c->Fb, &c->Nb, &c->ubs, &c->wb, &c->R,
-                            &c->Rl, &c->RB, &c->tmpA, &c->tmpB, &c->lamA, &c->lamB, &c->Nbase})
+                            &c->Rl, &c->RB, &c->Nbase})
             *b = c->field();
-        c->q = (double2*)c->dalloc(c->S() * sizeof(double2));
-        c->q2 = (double2*)c->dalloc(c->S() * sizeof(double2));
+        if (batched) {  // per-slot state, cotangent and energies replace the sweep buffers
+            c->bcur = c->field();
+            c->blam = c->field();
+            c->uN = c->field();  // terminal state, then the finished gradient
+            c->d_e0 = (double*)c->dalloc(nslot * sizeof(double));
+            c->d_eT = (double*)c->dalloc(nslot * sizeof(double));
+            c->breq.resize(nslot);
+        } else {
+            for (double2** b : {&c->tmpA, &c->tmpB, &c->lamA, &c->lamB}) *b = c->field();
+        }
+        // one-component scratch: a full field per slot when batched (the slot stride is 3 S)
+        c->q = batched ? c->field() : (double2*)c->dalloc(c->S() * sizeof(double2));
+        c->q2 = batched ? c->field() : (double2*)c->dalloc(c->S() * sizeof(double2));
         ck(cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking), "side stream");
         for (cudaEvent_t* e : {&c->ev_fork, &c->ev_bu, &c->ev_t, &c->ev_base})
             ck(cudaEventCreateWithFlags(e, cudaEventDisableTiming), "event");
         const size_t cz = mixed(c) ? sizeof(float2) : sizeof(double2);
         const size_t plane = (size_t)d.nr * d.nth * d.nk * cz;
-        c->Y = c->dalloc(9 * plane);
-        c->Y2 = c->dalloc(9 * plane);
-        c->Z = c->dalloc(6 * plane);
-        c->partial = (double*)c->dalloc(pnop::inner_partials(g) * sizeof(double));
+        g.ps = 9 * (size_t)d.nr * d.nth * d.nk;  // physical planes per slot (elements)
+        c->Y = c->dalloc(nslot * 9 * plane);
+        c->Y2 = c->dalloc(nslot * 9 * plane);
+        c->Z = c->dalloc((batched ? nslot * 9 : 6) * plane);
+        c->partial = (double*)c->dalloc(nslot * pnop::inner_partials(g) * sizeof(double));
         c->dscal = (double*)c->dalloc(4 * sizeof(double));
+        if (batched) c->h.ph.dt = 1.0;  // batched steps take times as step offsets (set_phase)
         ck(cudaDeviceSynchronize(), "create");
         return PNOP_OK;
     });
@@ -1208,6 +1460,13 @@ int pnop_create(const pnop_grid* grid, const pnop_params* params, void* cuda_str
     }
     *out = c;
     return PNOP_OK;
+}
+}  // namespace
+
+extern "C" {
+
+int pnop_create(const pnop_grid* grid, const pnop_params* params, void* cuda_stream, pnop_ctx** out) {
+    return create_impl(grid, params, cuda_stream, 1, false, out);
 }
 
 int pnop_set_base_flow(pnop_ctx* ctx, double Re, double Wo, double A, double tau0) {
@@ -1465,6 +1724,121 @@ int pnop_energy(pnop_ctx* ctx, const void* u, double* E_out) {
         return PNOP_OK;
     });
 }
+
+// ---------------------------------------------------------------- batched gradients
+static pnop_ctx* bctx(pnop_batch* b) { return reinterpret_cast<pnop_ctx*>(b); }
+static const pnop_ctx* bctx_c(const pnop_batch* b) { return reinterpret_cast<const pnop_ctx*>(b); }
+
+int pnop_batch_create(const pnop_grid* grid, const pnop_params* params, int capacity, void* cuda_stream,
+                      pnop_batch** out) {
+    if (!out) return PNOP_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!params || params->snap_budget < 1 || capacity < 1 || capacity > pnop::kMaxBatch) return PNOP_ERR_INVALID_ARG;
+    pnop_ctx* c = nullptr;
+    int rc = create_impl(grid, params, cuda_stream, capacity, true, &c);
+    if (rc != PNOP_OK) return rc;
+    rc = guarded(c, [&]() -> int {  // the checkpoints of every slot, so that admission allocates nothing
+        while ((int)c->snaps.size() < params->snap_budget) c->snaps.push_back(c->field());
+        return PNOP_OK;
+    });
+    if (rc != PNOP_OK) {
+        pnop_destroy(c);
+        return rc;
+    }
+    *out = reinterpret_cast<pnop_batch*>(c);
+    return PNOP_OK;
+}
+
+int pnop_batch_submit(pnop_batch* batch, const pnop_params* request, const void* u0, double E0, double horizon,
+                      int* id_out) {
+    pnop_ctx* c = bctx(batch);
+    return guarded(c, [&]() -> int {
+        const int id = batch_submit(c, request, (const double2*)u0, E0, horizon);
+        if (id_out) *id_out = id;
+        return PNOP_OK;
+    });
+}
+
+int pnop_batch_run(pnop_batch* batch, int max_ticks, int* ticks_out, int* running_out) {
+    pnop_ctx* c = bctx(batch);
+    return guarded(c, [&]() -> int {
+        if (max_ticks < 0) throw Status(PNOP_ERR_INVALID_ARG, "max_ticks must be >= 0");
+        int t = 0;
+        while (t < max_ticks && batch_tick(c)) ++t;
+        int running = 0;
+        for (const BatchReq& r : c->breq) running += (r.active && !r.done) ? 1 : 0;
+        if (ticks_out) *ticks_out = t;
+        if (running_out) *running_out = running;
+        return PNOP_OK;
+    });
+}
+
+static BatchReq* find_req(pnop_ctx* c, int id, int* slot) {
+    for (int i = 0; i < c->nslot; ++i)
+        if (c->breq[i].active && c->breq[i].id == id) {
+            if (slot) *slot = i;
+            return &c->breq[i];
+        }
+    throw Status(PNOP_ERR_INVALID_ARG, "no such request in the batch");
+}
+
+int pnop_batch_poll(pnop_batch* batch, int id, int* done_out) {
+    pnop_ctx* c = bctx(batch);
+    return guarded(c, [&]() -> int {
+        BatchReq* r = find_req(c, id, nullptr);
+        int done = 0;
+        if (r->done) {
+            const cudaError_t e = cudaEventQuery(r->ev_done);
+            if (e == cudaSuccess) done = 1;
+            else if (e != cudaErrorNotReady) ck(e, "poll");
+        }
+        if (done_out) *done_out = done;
+        return PNOP_OK;
+    });
+}
+
+int pnop_batch_result(pnop_batch* batch, int id, void* grad_out, double* gain_out) {
+    pnop_ctx* c = bctx(batch);
+    return guarded(c, [&]() -> int {
+        int slot = -1;
+        BatchReq* r = find_req(c, id, &slot);
+        if (!r->done) throw Status(PNOP_ERR_INVALID_ARG, "request not finished: run more ticks");
+        // the copies wait for this request's own completion only (not for the
+        // steps of other requests queued after it): they run on the copy stream
+        if (!c->copy) ck(cudaStreamCreateWithFlags(&c->copy, cudaStreamNonBlocking), "copy stream");
+        ck(cudaStreamWaitEvent(c->copy, r->ev_done, 0), "wait request");
+        double e0 = 0, eT = 0;
+        ck(cudaMemcpyAsync(&e0, c->d_e0 + slot, sizeof(double), cudaMemcpyDeviceToHost, c->copy), "energy copy");
+        ck(cudaMemcpyAsync(&eT, c->d_eT + slot, sizeof(double), cudaMemcpyDeviceToHost, c->copy), "energy copy");
+        if (grad_out)
+            ck(cudaMemcpyAsync(grad_out, slot_ptr(c, c->uN, slot), c->field_bytes(), cudaMemcpyDeviceToDevice,
+                               c->copy), "gradient copy");
+        ck(cudaStreamSynchronize(c->copy), "result sync");
+        r->active = false;  // the slot is free again
+        r->fetched = true;
+        if (gain_out) *gain_out = eT / e0;
+        if (!(e0 > 0) || !std::isfinite(e0)) throw Status(PNOP_ERR_NONFINITE, "initial field has no finite energy");
+        if (!std::isfinite(eT)) throw Status(PNOP_ERR_NONFINITE, "final energy is not finite");
+        return PNOP_OK;
+    });
+}
+
+int pnop_batch_stats(const pnop_batch* batch, long long* ticks, long long* entries, long long* launches) {
+    const pnop_ctx* c = bctx_c(batch);
+    if (!c) return PNOP_ERR_INVALID_ARG;
+    if (ticks) *ticks = c->b_ticks;
+    if (entries) *entries = c->b_launch_entries;
+    if (launches) {
+        long long n = 0;
+        for (int i = 0; i < PNOP_K_NCLASS; ++i) n += c->launches[i];
+        *launches = n;
+    }
+    return PNOP_OK;
+}
+
+const char* pnop_batch_last_error(const pnop_batch* batch) { return pnop_last_error(bctx_c(batch)); }
+
+void pnop_batch_destroy(pnop_batch* batch) { pnop_destroy(bctx(batch)); }
 
 int pnop_inner(pnop_ctx* ctx, const void* a, const void* b, double* out) {
     return guarded(ctx, [&]() -> int {

@@ -119,12 +119,14 @@ __global__ void k_synth_theta(Geo g, FieldPtrs f, T2* __restrict__ Y, const T2* 
     T2* buf0 = reinterpret_cast<T2*>(smem);
     T2* buf1 = buf0 + g.nt * KB;
     T2* tw = buf1 + g.nt * KB;
-    const int k0 = blockIdx.x * KB, j = blockIdx.y, fi = blockIdx.z;
+    const int k0 = blockIdx.x * KB, j = blockIdx.y;
+    const int nf = gridDim.z / g.nb, b = blockIdx.z / nf, fi = blockIdx.z - b * nf, slot = g.slot[b];
+    Y += (size_t)slot * g.ps;
     const int kw = min(KB, g.nk - k0);
     for (int i = threadIdx.x; i < g.nt; i += blockDim.x) tw[i] = twg[i];
     for (int i = threadIdx.x; i < g.nt * KB; i += blockDim.x) buf0[i] = mk<T2>(0, 0);
     __syncthreads();
-    const double2* src = f.in[fi] + (size_t)j * g.nm * g.nk;
+    const double2* src = f.in[fi] + (size_t)slot * g.fs + (size_t)j * g.nm * g.nk;
     for (int i = threadIdx.x; i < g.nm * KB; i += blockDim.x) {
         const int im = i / KB, kk = i % KB;
         if (kk < kw) {
@@ -184,6 +186,9 @@ __global__ void k_zpass(Geo g, const T2* __restrict__ Y, T2* __restrict__ Z, ZSc
     T2* bufB = bufA + N * LD;
     T2* tw = bufB + N * LD;
     const int a = blockIdx.x, j = blockIdx.y;
+    const size_t poff = (size_t)g.slot[blockIdx.z] * g.ps;  // batch entry blockIdx.z
+    Y += poff;
+    Z += poff;
     for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = twg[i];
     // Hermitian-extended spectra, two fields per column
     for (int p = 0; p < NPI; ++p)
@@ -259,7 +264,10 @@ __global__ void k_anal_theta(Geo g, FieldPtrs f, const T2* __restrict__ Z, const
     T2* buf0 = reinterpret_cast<T2*>(smem);
     T2* buf1 = buf0 + g.nt * KB;
     T2* tw = buf1 + g.nt * KB;
-    const int k0 = blockIdx.x * KB, j = blockIdx.y, fi = blockIdx.z;
+    const int k0 = blockIdx.x * KB, j = blockIdx.y;
+    const int nf = gridDim.z / g.nb, b = blockIdx.z / nf, fi = blockIdx.z - b * nf, slot = g.slot[b];
+    const size_t off = (size_t)slot * g.fs;
+    Z += (size_t)slot * g.ps;
     const int kw = min(KB, g.nk - k0);
     for (int i = threadIdx.x; i < g.nt; i += blockDim.x) tw[i] = twg[i];
     const T2* src = Z + ((size_t)(fi * g.nr + j) * g.nt) * g.nk;
@@ -269,8 +277,8 @@ __global__ void k_anal_theta(Geo g, FieldPtrs f, const T2* __restrict__ Z, const
     }
     __syncthreads();
     T2* res = fft_cols<T2, KB, KB, -1>(buf0, buf1, g.nt, tw);
-    double2* dst = f.out[fi] + (size_t)j * g.nm * g.nk;
-    const double2* add = f.add[fi] ? f.add[fi] + (size_t)j * g.nm * g.nk : nullptr;
+    double2* dst = f.out[fi] + off + (size_t)j * g.nm * g.nk;
+    const double2* add = f.add[fi] ? f.add[fi] + off + (size_t)j * g.nm * g.nk : nullptr;
     for (int i = threadIdx.x; i < g.nm * KB; i += blockDim.x) {
         const int im = i / KB, kk = i % KB;
         if (kk >= kw) continue;
@@ -423,10 +431,12 @@ __global__ void __launch_bounds__(128) k_synth2(Geo g, FieldPtrs f, T2* __restri
     extern __shared__ __align__(16) unsigned char smem[];
     T2* buf = reinterpret_cast<T2*>(smem);  // [N][KB]
     T2* tw = buf + N * KB;                   // [N]
-    const int k0 = blockIdx.x * KB, j = blockIdx.y, fi = blockIdx.z;
+    const int k0 = blockIdx.x * KB, j = blockIdx.y;
+    const int nf = gridDim.z / g.nb, b = blockIdx.z / nf, fi = blockIdx.z - b * nf, slot = g.slot[b];
+    Y += (size_t)slot * g.ps;
     for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = twg[i];
     __syncthreads();
-    const double2* src = f.in[fi] + (size_t)j * g.nm * g.nk;
+    const double2* src = f.in[fi] + (size_t)slot * g.fs + (size_t)j * g.nm * g.nk;
     for (int t = threadIdx.x; t < KB * N2; t += blockDim.x) {
         const int kk = t % KB, n2 = t / KB, k = k0 + kk;
         T2 v[N1];
@@ -464,7 +474,10 @@ __global__ void __launch_bounds__(128) k_anal2(Geo g, FieldPtrs f, const T2* __r
     extern __shared__ __align__(16) unsigned char smem[];
     T2* buf = reinterpret_cast<T2*>(smem);  // [N][KB]
     T2* tw = buf + N * KB;                   // [N]
-    const int k0 = blockIdx.x * KB, j = blockIdx.y, fi = blockIdx.z;
+    const int k0 = blockIdx.x * KB, j = blockIdx.y;
+    const int nf = gridDim.z / g.nb, b = blockIdx.z / nf, fi = blockIdx.z - b * nf, slot = g.slot[b];
+    const size_t off = (size_t)slot * g.fs;
+    Z += (size_t)slot * g.ps;
     for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = twg[i];
     __syncthreads();
     const T2* src = Z + ((size_t)(fi * g.nr + j) * N) * g.nk;
@@ -478,8 +491,8 @@ __global__ void __launch_bounds__(128) k_anal2(Geo g, FieldPtrs f, const T2* __r
         for (int m2 = 0; m2 < N2; ++m2) buf[(N2 * k1 + m2) * KB + kk] = twr<T2, -1>(v[m2], tw, k1 * m2);
     }
     __syncthreads();
-    double2* dst = f.out[fi] + (size_t)j * g.nm * g.nk;
-    const double2* add = f.add[fi] ? f.add[fi] + (size_t)j * g.nm * g.nk : nullptr;
+    double2* dst = f.out[fi] + off + (size_t)j * g.nm * g.nk;
+    const double2* add = f.add[fi] ? f.add[fi] + off + (size_t)j * g.nm * g.nk : nullptr;
     for (int t = threadIdx.x; t < KB * N2; t += blockDim.x) {
         const int kk = t % KB, m2 = t / KB, k = k0 + kk;
         T2 v[N1];
@@ -530,6 +543,9 @@ __global__ void k_zpass2(Geo g, const T2* __restrict__ Y, T2* __restrict__ Z, ZS
     T2* col = reinterpret_cast<T2*>(smem);  // [NPI][NP]
     T2* tw = col + NPI * NP;                 // [N]
     const int K = g.K, nk = g.nk, a = blockIdx.x, j = blockIdx.y;
+    const size_t poff = (size_t)g.slot[blockIdx.z] * g.ps;  // batch entry blockIdx.z
+    Y += poff;
+    Z += poff;
     auto at = [](int s) { return s + s / N2; };
     for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = twg[i];
     __syncthreads();
@@ -659,7 +675,7 @@ template <class T2, int KB>
 static void synth_theta_kb(const Geo& g, const FieldPtrs& f, int nfield, T2* Y, const T2* tw, cudaStream_t s) {
     const size_t sm = (size_t)(2 * g.nt * KB + g.nt) * sizeof(T2);
     smem_limit((const void*)k_synth_theta<T2, KB>);
-    dim3 grid((g.nk + KB - 1) / KB, g.nr, nfield);
+    dim3 grid((g.nk + KB - 1) / KB, g.nr, nfield * g.nb);
     k_synth_theta<T2, KB><<<grid, 256, sm, s>>>(g, f, Y, tw);
 }
 
@@ -667,7 +683,7 @@ template <class T2, int KB>
 static void anal_theta_kb(const Geo& g, const FieldPtrs& f, int nfield, const T2* Z, const T2* tw, cudaStream_t s) {
     const size_t sm = (size_t)(2 * g.nt * KB + g.nt) * sizeof(T2);
     smem_limit((const void*)k_anal_theta<T2, KB>);
-    dim3 grid((g.nk + KB - 1) / KB, g.nr, nfield);
+    dim3 grid((g.nk + KB - 1) / KB, g.nr, nfield * g.nb);
     k_anal_theta<T2, KB><<<grid, 256, sm, s>>>(g, f, Z, tw);
 }
 
@@ -678,14 +694,14 @@ template <class T2, int KB, int N1, int N2>
 static void synth2(const Geo& g, const FieldPtrs& f, int nfield, T2* Y, const T2* tw, cudaStream_t s) {
     const size_t sm = (size_t)(N1 * N2 * KB + N1 * N2) * sizeof(T2);
     smem_limit((const void*)k_synth2<T2, KB, N1, N2>);
-    dim3 grid((g.nk + KB - 1) / KB, g.nr, nfield);
+    dim3 grid((g.nk + KB - 1) / KB, g.nr, nfield * g.nb);
     k_synth2<T2, KB, N1, N2><<<grid, 128, sm, s>>>(g, f, Y, tw);
 }
 template <class T2, int KB, int N1, int N2>
 static void anal2(const Geo& g, const FieldPtrs& f, int nfield, const T2* Z, const T2* tw, cudaStream_t s) {
     const size_t sm = (size_t)(N1 * N2 * KB + N1 * N2) * sizeof(T2);
     smem_limit((const void*)k_anal2<T2, KB, N1, N2>);
-    dim3 grid((g.nk + KB - 1) / KB, g.nr, nfield);
+    dim3 grid((g.nk + KB - 1) / KB, g.nr, nfield * g.nb);
     k_anal2<T2, KB, N1, N2><<<grid, 128, sm, s>>>(g, f, Z, tw);
 }
 
@@ -735,7 +751,7 @@ static void zpass2(const Geo& g, const T2* Y, T2* Z, const ZScales& sc, const T2
     constexpr int NPI = MODE == ZFWD ? 3 : (MODE == ZADJ ? 5 : 9);
     const size_t sm = (size_t)(NPI * (N1 * N2 + N1) + N1 * N2) * sizeof(T2);
     smem_limit((const void*)k_zpass2<T2, MODE, N1, N2>);
-    k_zpass2<T2, MODE, N1, N2><<<dim3(g.nt, g.nr), zpass_threads(g), sm, s>>>(g, Y, Z, sc, tw);
+    k_zpass2<T2, MODE, N1, N2><<<dim3(g.nt, g.nr, g.nb), zpass_threads(g), sm, s>>>(g, Y, Z, sc, tw);
 }
 template <class T2, int MODE>
 static bool zpass2_any(const Geo& g, const T2* Y, T2* Z, const ZScales& sc, const T2* tw, cudaStream_t s) {
@@ -752,7 +768,7 @@ static void zpass_stockham(const Geo& g, const T2* Y, T2* Z, const ZScales& sc, 
     constexpr int LD = MODE == ZFWD ? 3 : (MODE == ZADJ ? 5 : 9);
     const size_t sm = (size_t)(2 * g.nzp * LD + g.nzp) * sizeof(T2);
     smem_limit((const void*)k_zpass<T2, MODE>);
-    k_zpass<T2, MODE><<<dim3(g.nt, g.nr), zpass_threads(g), sm, s>>>(g, Y, Z, sc, tw);
+    k_zpass<T2, MODE><<<dim3(g.nt, g.nr, g.nb), zpass_threads(g), sm, s>>>(g, Y, Z, sc, tw);
 }
 
 template <class T2>

@@ -1,4 +1,4 @@
-"""Continuous-batching server for gradient requests of mixed parameters.
+"""Continuous-batching servers for gradient requests of mixed parameters.
 
 A request asks for the checkpointed gradient dE(T)/du0 and the gain G of one
 initial perturbation (Eq. 2.1, 2.8, 2.12) at its own (Re, Wo, A, tau0, E0,
@@ -11,6 +11,9 @@ the device until it completes) and a CUDA stream; its host thread drives the
 library (ctypes releases the GIL), so kernels of different requests overlap on
 the GPU.  Each request's arithmetic is independent of the others and
 deterministic, so its result is the same alone and in the mix.
+
+BatchServer goes further: requests of one grid share a pnop_batch, so each
+kernel of a step is launched once for all of them (see its docstring).
 
 The library has no counterpart in the paper: this is the serving layer named
 in the workload list (continuous batching, HBM admission, p50/p99 latency).
@@ -162,12 +165,226 @@ class Server:
                 self.lock.wait(timeout=min(left, 1.0))
 
 
-def serve_stream(requests, hbm_budget: int, max_active: int = 8, device: int = 0, runner=None, sizer=None):
+class BatchServer:
+    """Continuous batching with shared launches.
+
+    Requests of one (grid, precision, checkpoint slots) share a pnop_batch of
+    `slots` request slots: every kernel of a step runs once for all requests
+    of that batch taking that kind of step.  A driver thread admits queued
+    requests into free slots (first come, first served per batch), queues
+    `ticks` batched steps per batch per round (at most two rounds in flight
+    per batch, so that new arrivals join within a few steps), and collects
+    finished requests.  A batch's device memory (about `slots` contexts) is
+    allocated when the first request of its kind arrives and counted against
+    the HBM budget; a batch with no request left is released when another
+    kind needs the memory.  Each request gets bitwise the result it gets
+    alone (the batched steps are the single-request steps per slot)."""
+
+    def __init__(self, hbm_budget: int, slots: int = 8, ticks: int = 4, device: int = 0, batch_factory=None,
+                 sizer=None):
+        """batch_factory(request, slots, stream) -> batch object (pnop_batch_submit / run / poll / result /
+        close, as _lib.Batch) and sizer(request, slots) -> bytes replace the GPU batch and the library
+        estimate (host-side tests)."""
+        self.hbm_budget = int(hbm_budget)
+        self.slots = slots
+        self.ticks = ticks
+        self.device = device
+        self.factory = batch_factory
+        self.sizer = sizer
+        self.queue: deque = deque()
+        self.results: dict = {}
+        self.lock = threading.Condition()
+        self.t0 = time.perf_counter()
+        self.batches: dict = {}     # key -> dict(batch, stream, bytes, running {bid: (request, admitted)}, rounds)
+        self.bytes_in_use = 0
+        self.peak_bytes = 0
+        self.active = 0
+        self.peak_active = 0
+        self.peak_batch = 0
+        self.closed = False
+        self.error: Optional[str] = None
+        self.driver = threading.Thread(target=self._drive, daemon=True)
+        self.driver.start()
+
+    def now(self) -> float:
+        return time.perf_counter() - self.t0
+
+    @staticmethod
+    def key(r: Request):
+        return (r.nr, r.ntheta, r.nz, r.Lz, r.precision, r.snaps)
+
+    def batch_bytes(self, r: Request) -> int:
+        if self.sizer is not None:
+            return int(self.sizer(r, self.slots))
+        return self.slots * _lib.pnop_context_bytes(r.nr, r.ntheta, r.nz, r.Lz, r.precision, r.snaps)
+
+    def submit(self, r: Request) -> None:
+        if self.batch_bytes(r) > self.hbm_budget:
+            raise ValueError(f"request {r.rid}: a batch of its kind needs more than the whole budget")
+        with self.lock:
+            self.queue.append(r)
+            self.lock.notify_all()
+
+    # ---- driver thread
+    def _new_batch(self, r: Request):
+        if self.factory is not None:
+            return self.factory(r, self.slots, None), None
+        import torch
+        stream = torch.cuda.Stream(device=self.device)
+        b = _lib.Batch(r.nr, r.ntheta, r.nz, r.Lz, self.slots, r.precision, r.snaps, stream=stream.cuda_stream)
+        return b, stream
+
+    def _get_batch(self, r: Request):
+        k = self.key(r)
+        if k in self.batches:
+            return self.batches[k]
+        need = self.batch_bytes(r)
+        if self.bytes_in_use + need > self.hbm_budget:  # release idle batches of other kinds
+            for kk in [kk for kk, e in self.batches.items() if not e["running"]]:
+                e = self.batches.pop(kk)
+                e["batch"].close()
+                self.bytes_in_use -= e["bytes"]
+                if self.bytes_in_use + need <= self.hbm_budget:
+                    break
+        if self.bytes_in_use + need > self.hbm_budget:
+            return None
+        b, stream = self._new_batch(r)
+        e = {"batch": b, "stream": stream, "bytes": need, "running": {}, "rounds": deque()}
+        self.batches[k] = e
+        self.bytes_in_use += need
+        self.peak_bytes = max(self.peak_bytes, self.bytes_in_use)
+        return e
+
+    def _admit(self, pending: deque) -> None:
+        keep = deque()
+        while pending:
+            r = pending.popleft()
+            e = self._get_batch(r)
+            if e is None or len(e["running"]) >= self.slots:
+                keep.append(r)
+                continue
+            try:
+                bid = self._submit_one(e, r)
+            except Exception as ex:  # reported per request
+                self._finish(r, self.now(), float("nan"), None, f"{type(ex).__name__}: {ex}")
+                continue
+            e["running"][bid] = (r, self.now())
+            self.active += 1
+            self.peak_active = max(self.peak_active, self.active)
+            self.peak_batch = max(self.peak_batch, len(e["running"]))
+        pending.extend(keep)
+
+    def _submit_one(self, e, r: Request) -> int:
+        b = e["batch"]
+        if self.factory is not None:
+            return b.pnop_batch_submit(r.u0, r.E0, r.horizon, r.Re, r.dt, r.Wo, r.A, r.tau0)
+        import torch
+        with torch.cuda.stream(e["stream"]):
+            u0 = torch.from_numpy(np.ascontiguousarray(r.u0)).to(f"cuda:{self.device}", non_blocking=False)
+        return b.pnop_batch_submit(u0, r.E0, r.horizon, r.Re, r.dt, r.Wo, r.A, r.tau0)
+
+    def _collect(self, e) -> None:
+        b = e["batch"]
+        for bid in list(e["running"]):
+            if not b.pnop_batch_poll(bid):
+                continue
+            r, admitted = e["running"].pop(bid)
+            self.active -= 1
+            err, gain, grad = None, float("nan"), None
+            try:
+                if self.factory is not None:
+                    gain, grad = b.pnop_batch_result(bid)
+                else:
+                    import torch
+                    with torch.cuda.stream(e["stream"]):
+                        g = torch.empty(b.shape, dtype=torch.complex128, device=f"cuda:{self.device}")
+                    gain = b.pnop_batch_result(bid, g)
+                    grad = g.cpu().numpy()
+            except Exception as ex:
+                err = f"{type(ex).__name__}: {ex}"
+            self._finish(r, admitted, gain, grad, err)
+
+    def _finish(self, r, admitted, gain, grad, err) -> None:
+        with self.lock:
+            self.results[r.rid] = Result(r.rid, gain, grad, r.arrival, admitted, self.now(), 0, err)
+            self.lock.notify_all()
+
+    def _drive(self) -> None:
+        if self.factory is None:
+            import torch
+            torch.cuda.set_device(self.device)
+        pending: deque = deque()
+        try:
+            while True:
+                with self.lock:
+                    if self.closed and not self.queue and not pending and not self.active:
+                        return
+                    if not self.queue and not pending and not self.active:
+                        self.lock.wait(timeout=0.05)
+                    pending.extend(self.queue)
+                    self.queue.clear()
+                self._admit(pending)
+                for e in self.batches.values():
+                    if not e["running"]:
+                        continue
+                    rounds = e["rounds"]
+                    if len(rounds) >= 2:  # at most two rounds in flight per batch
+                        rounds.popleft().synchronize()
+                    e["batch"].pnop_batch_run(self.ticks)
+                    if e["stream"] is not None:
+                        import torch
+                        ev = torch.cuda.Event()
+                        ev.record(e["stream"])
+                        rounds.append(ev)
+                for e in self.batches.values():
+                    self._collect(e)
+        except Exception as ex:  # the driver stops; waiters see the error
+            with self.lock:
+                self.error = f"{type(ex).__name__}: {ex}"
+                self.lock.notify_all()
+
+    def wait(self, n: int, timeout: float = 3600.0) -> None:
+        end = time.perf_counter() + timeout
+        with self.lock:
+            while len(self.results) < n:
+                if self.error:
+                    raise RuntimeError(f"serving driver failed: {self.error}")
+                left = end - time.perf_counter()
+                if left <= 0:
+                    raise TimeoutError(f"{len(self.results)} of {n} requests finished")
+                self.lock.wait(timeout=min(left, 0.05))
+
+    def close(self) -> None:
+        with self.lock:
+            self.closed = True
+            self.lock.notify_all()
+        self.driver.join(timeout=60)
+        for e in self.batches.values():
+            e["batch"].close()
+        self.batches.clear()
+
+
+def serve_stream(requests, hbm_budget: int, max_active: int = 8, device: int = 0, runner=None, sizer=None,
+                 batched: bool = False, ticks: int = 4, batch_factory=None):
     """Submit requests at their arrival times (seconds after start) and wait.
 
     Returns (results sorted by id, server).  Arrival times are honoured on the
     host clock; a request arriving while others run is admitted as soon as
-    memory and a slot are free."""
+    memory and a slot are free.  batched selects the BatchServer (max_active
+    slots per batch of one kind) instead of one context and stream per
+    request."""
+    if batched:
+        srv = BatchServer(hbm_budget, max_active, ticks, device, batch_factory, sizer)
+        try:
+            for r in sorted(requests, key=lambda q: q.arrival):
+                delay = r.arrival - srv.now()
+                if delay > 0:
+                    time.sleep(delay)
+                srv.submit(r)
+            srv.wait(len(requests))
+        finally:
+            srv.close()
+        return [srv.results[r.rid] for r in sorted(requests, key=lambda q: q.rid)], srv
     srv = Server(hbm_budget, max_active, device, runner, sizer)
     for r in sorted(requests, key=lambda q: q.arrival):
         delay = r.arrival - srv.now()

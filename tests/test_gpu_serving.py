@@ -73,3 +73,16 @@ def test_admission_budget_serialises_when_memory_is_short(mods):
     res, srv = serving.serve_stream(reqs, hbm_budget=need, max_active=8)
     assert all(r.error is None for r in res)
     assert srv.peak_active == 1
+
+
+def test_batched_server_gives_each_request_its_alone_result(mods):
+    L, serving = mods
+    reqs = _requests(L, serving)
+    mix, srv = serving.serve_stream(reqs, hbm_budget=8 << 30, max_active=4, batched=True, ticks=3)
+    assert all(r.error is None for r in mix), [r.error for r in mix]
+    assert srv.peak_batch >= 2  # requests of one kind shared launches
+    for r in reqs:
+        alone, _ = serving.serve_stream([r], hbm_budget=8 << 30, max_active=1)
+        a, m = alone[0], mix[r.rid]
+        assert a.gain == m.gain
+        assert np.array_equal(a.grad, m.grad)

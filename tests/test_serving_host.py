@@ -70,3 +70,78 @@ def test_latency_summary():
     rs = [serving.Result(i, 1.0, None, 0.0, 0.0, float(i + 1), 0) for i in range(100)]
     s = serving.latency_summary(rs)
     assert abs(s["p50_s"] - 50.5) < 1e-9 and s["p99_s"] > 99.0 and s["n"] == 100
+
+
+class FakeBatch:
+    """Stands in for a pnop_batch: a request finishes after as many ticks as
+    its horizon has steps; each tick covers every unfinished request."""
+    made = []
+
+    def __init__(self, r, slots, stream):
+        self.slots = slots
+        self.left = {}
+        self.gain = {}
+        self.next = 0
+        self.max_live = 0
+        self.closed = False
+        FakeBatch.made.append(self)
+
+    def pnop_batch_submit(self, u0, E0, horizon, Re, dt, Wo, A, tau0):
+        assert len(self.left) < self.slots
+        if Re < 0:
+            raise RuntimeError("planted failure")
+        bid = self.next
+        self.next += 1
+        self.left[bid] = int(round(horizon / dt))
+        self.gain[bid] = Re
+        return bid
+
+    def pnop_batch_run(self, ticks):
+        for _ in range(ticks):
+            live = [b for b, n in self.left.items() if n > 0]
+            self.max_live = max(self.max_live, len(live))
+            for b in live:
+                self.left[b] -= 1
+        return ticks, sum(1 for n in self.left.values() if n > 0)
+
+    def pnop_batch_poll(self, bid):
+        return self.left[bid] == 0
+
+    def pnop_batch_result(self, bid):
+        del self.left[bid]
+        return self.gain.pop(bid), np.full(3, bid)
+
+    def close(self):
+        self.closed = True
+
+
+def _breq(i, kind, steps, arrival=0.0, Re=None):
+    r = _req(i, arrival, size=kind)
+    r.horizon = float(steps)
+    r.Re = float(i) if Re is None else Re
+    return r
+
+
+def test_batch_server_shares_steps_and_respects_slots():
+    FakeBatch.made.clear()
+    reqs = [_breq(i, 1 + i % 2, 3 + i % 5) for i in range(14)]
+    res, srv = serving.serve_stream(reqs, hbm_budget=10, max_active=3, batched=True, ticks=1,
+                                    batch_factory=FakeBatch, sizer=lambda r, slots: 1)
+    assert all(x.error is None for x in res), [x.error for x in res]
+    assert [x.gain for x in res] == [float(i) for i in range(14)]
+    assert len(FakeBatch.made) == 2  # one batch per kind of request
+    assert all(b.max_live <= 3 for b in FakeBatch.made)  # slot limit
+    assert max(b.max_live for b in FakeBatch.made) >= 2  # requests shared ticks
+    assert srv.peak_batch <= 3 and srv.active == 0
+
+
+def test_batch_server_budget_releases_idle_batches_and_reports_errors():
+    FakeBatch.made.clear()
+    reqs = [_breq(0, 1, 4), _breq(1, 2, 4, arrival=0.05), _breq(2, 1, 2, arrival=0.1, Re=-1.0)]
+    # room for one batch at a time: kind 2 waits for kind 1's batch to go idle
+    res, srv = serving.serve_stream(reqs, hbm_budget=1, max_active=2, batched=True, ticks=1,
+                                    batch_factory=FakeBatch, sizer=lambda r, slots: 1)
+    assert res[0].error is None and res[1].error is None
+    assert res[2].error is not None and "planted" in res[2].error
+    assert srv.peak_bytes <= 1
+    assert len(FakeBatch.made) == 3 and FakeBatch.made[0].closed
