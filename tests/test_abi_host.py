@@ -118,3 +118,22 @@ def test_new_entry_points_reject_bad_arguments_without_a_device(L):
     nf, adv = ctypes.c_int(), ctypes.c_longlong()
     for args in ((0, 2, 4, 0.0), (10, 0, 4, 0.0), (10, 2, -1, 0.0), (10, 2, 4, -1.0), (10, 2, 4, float("nan"))):
         assert L.lib.pnop_two_level_counts(*args, ctypes.byref(nf), ctypes.byref(adv)) == -1
+
+
+def test_batch_entry_points_reject_bad_arguments_without_a_device(L):
+    import ctypes
+    g = L.pnop_grid(12, 8, 12, 6.0, 0.0)
+    h = ctypes.c_void_p()
+    for cap, snaps in ((0, 2), (L.PNOP_MAX_BATCH + 1, 2), (4, 0)):
+        p = L.pnop_params(2000.0, 8.0, 1.0, 0.01, 0.0, 0, snaps, 0)
+        assert L.lib.pnop_batch_create(ctypes.byref(g), ctypes.byref(p), cap, None, ctypes.byref(h)) == -1
+        assert h.value is None
+    p = L.pnop_params(2000.0, 8.0, 1.0, 0.01, 0.0, 0, 2, 0)
+    assert L.lib.pnop_batch_create(None, ctypes.byref(p), 2, None, ctypes.byref(h)) == -1
+    i, t = ctypes.c_int(), ctypes.c_longlong()
+    assert L.lib.pnop_batch_submit(None, ctypes.byref(p), None, 1e-3, 1.0, ctypes.byref(i)) == -1
+    assert L.lib.pnop_batch_run(None, 4, None, None) == -1
+    assert L.lib.pnop_batch_poll(None, 0, ctypes.byref(i)) == -1
+    assert L.lib.pnop_batch_result(None, 0, None, None) == -1
+    assert L.lib.pnop_batch_stats(None, ctypes.byref(t), None, None) == -1
+    L.lib.pnop_batch_destroy(None)
