@@ -404,6 +404,21 @@ int pnop_batch_create(const pnop_grid* grid, const pnop_params* params, int capa
 int pnop_batch_submit(pnop_batch* batch, const pnop_params* request, const void* u0, double E0, double horizon,
                       int* id_out);
 
+/* The host part of a submission, split off so that it can run beside the
+ * device work: pnop_batch_prepare builds the operators of one request's
+ * physics (Re, Wo, A, dt, tau0 of *request) on the host.  It reads only the
+ * batch's grid tables, which never change after creation, records no error
+ * text, and may run on any number of host threads at once, concurrently with
+ * every other call on the batch.  pnop_batch_submit_prepared then admits a
+ * request with them (same arguments and errors as pnop_batch_submit; ops
+ * stays owned by the caller and may be used again); pnop_ops_free releases
+ * them (NULL allowed).  pnop_batch_submit is prepare + submit_prepared. */
+typedef struct pnop_ops pnop_ops;
+int pnop_batch_prepare(const pnop_batch* batch, const pnop_params* request, pnop_ops** out);
+int pnop_batch_submit_prepared(pnop_batch* batch, const pnop_ops* ops, const void* u0, double E0, double horizon,
+                               int* id_out);
+void pnop_ops_free(pnop_ops* ops);
+
 /* Queue up to max_ticks batched steps (one tick: every request's pending
  * checkpoint copies, then one batched forward, terminal or adjoint step for
  * the requests whose next step is of the most common kind).  *ticks_out:

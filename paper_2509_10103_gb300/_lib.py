@@ -29,7 +29,8 @@ EXPORTS = (
     "pnop_sync", "pnop_profile", "pnop_profile_read", "pnop_revolve_counts", "pnop_context_bytes",
     "pnop_energy_noalloc", "pnop_last_error", "pnop_error_string", "pnop_destroy",
     "pnop_batch_create", "pnop_batch_submit", "pnop_batch_run", "pnop_batch_poll", "pnop_batch_result",
-    "pnop_batch_stats", "pnop_batch_last_error", "pnop_batch_destroy",
+    "pnop_batch_stats", "pnop_batch_last_error", "pnop_batch_destroy", "pnop_batch_prepare",
+    "pnop_batch_submit_prepared", "pnop_ops_free",
 )
 
 
@@ -96,6 +97,9 @@ def _load():
         "pnop_batch_stats": (c_int, [c_void_p, POINTER(c_longlong), POINTER(c_longlong), POINTER(c_longlong)]),
         "pnop_batch_last_error": (c_char_p, [c_void_p]),
         "pnop_batch_destroy": (None, [c_void_p]),
+        "pnop_batch_prepare": (c_int, [c_void_p, POINTER(pnop_params), POINTER(c_void_p)]),
+        "pnop_batch_submit_prepared": (c_int, [c_void_p, c_void_p, c_void_p, c_double, c_double, POINTER(c_int)]),
+        "pnop_ops_free": (None, [c_void_p]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -342,6 +346,26 @@ class Batch:
         i = c_int()
         self._check(lib.pnop_batch_submit(self._h, byref(p), c_void_p(_ptr(u0)), E0, horizon, byref(i)), "submit")
         return i.value
+
+    def pnop_batch_prepare(self, Re, dt, Wo=8.0, A=1.0, tau0=0.0):
+        """Host operators of one request (thread-safe; see pnop.h).  Returns an
+        opaque handle for pnop_batch_submit_prepared; free it with pnop_ops_free."""
+        p = pnop_params(Re, Wo, A, dt, tau0, 0, 0, 0)
+        o = c_void_p()
+        rc = lib.pnop_batch_prepare(self._h, byref(p), byref(o))
+        if rc != PNOP_OK:
+            raise PnopError(rc, "prepare")
+        return o
+
+    def pnop_batch_submit_prepared(self, ops, u0, E0, horizon):
+        i = c_int()
+        self._check(lib.pnop_batch_submit_prepared(self._h, ops, c_void_p(_ptr(u0)), E0, horizon, byref(i)),
+                    "submit_prepared")
+        return i.value
+
+    @staticmethod
+    def pnop_ops_free(ops):
+        lib.pnop_ops_free(ops)
 
     def pnop_batch_run(self, max_ticks):
         """Queue up to max_ticks batched steps; returns (ticks, requests still running)."""

@@ -60,7 +60,7 @@ def build(verbose: bool = False, force: bool = False, ptxas_info: bool = False) 
             if ptxas_info:
                 cmd += ["-Xptxas", "-v"]
         else:
-            cmd = ["g++", "-O2", "-std=c++17", "-fPIC", "-c", src, "-o", obj]
+            cmd = ["g++", "-O2", "-std=c++17", "-fPIC", "-pthread", "-c", src, "-o", obj]
         jobs.append(cmd)
     with ThreadPoolExecutor(max_workers=len(jobs)) as ex:
         logs = list(ex.map(_run, jobs))
@@ -69,7 +69,7 @@ def build(verbose: bool = False, force: bool = False, ptxas_info: bool = False) 
             if log.strip():
                 print(log)
     tmp = OUT + ".tmp"
-    _run([nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"])
+    _run([nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart", "-Xcompiler", "-pthread"])
     os.replace(tmp, OUT)
     return OUT
 

@@ -1156,9 +1156,33 @@ void batch_ops(BatchReq& r, const std::vector<Action>& P) {
     r.pos = 0;
 }
 
-int batch_submit(pnop_ctx* c, const pnop_params* p, const double2* u0, double E0, double horizon) {
-    if (!p || !u0 || !(p->Re > 0) || !(p->dt > 0) || !(p->A >= 0) || !(p->Wo > 0 || p->A == 0))
+// Host operators of one request's physics on the batch's grid.  Reads only the
+// batch's grid tables and pressure factors (fixed after creation), so any
+// number of these can run at once, beside the batch's other calls.
+pnop::HostOps batch_prepare(const pnop_ctx* c, const pnop_params* p) {
+    if (!p || !(p->Re > 0) || !(p->dt > 0) || !(p->A >= 0) || !(p->Wo > 0 || p->A == 0))
         throw Status(PNOP_ERR_INVALID_ARG, "bad request parameters");
+    pnop::HostOps hs;
+    hs.d = c->h.d;
+    hs.r = c->h.r;
+    hs.invr = c->h.invr;
+    hs.W = c->h.W;
+    hs.D1 = c->h.D1;
+    hs.D2 = c->h.D2;
+    hs.facP = c->h.facP;
+    hs.facPT = c->h.facPT;
+    hs.ph = {p->Re, p->Wo, p->A, p->dt, p->tau0};
+    std::string err;
+    if (!pnop::build_operators(hs, err, true)) throw Status(PNOP_ERR_UNSUPPORTED, err);
+    return hs;
+}
+
+int batch_submit(pnop_ctx* c, const pnop::HostOps& hs, const double2* u0, double E0, double horizon) {
+    const pnop::Physics* p = &hs.ph;
+    if (!u0) throw Status(PNOP_ERR_INVALID_ARG, "u0 is NULL");
+    if (hs.d.nr != c->h.d.nr || hs.d.M != c->h.d.M || hs.d.K != c->h.d.K || hs.d.Lz != c->h.d.Lz ||
+        hs.d.stretch != c->h.d.stretch)
+        throw Status(PNOP_ERR_INVALID_ARG, "operators prepared for another grid");
     const double nd = horizon / p->dt;
     const long long N = (long long)std::llround(nd);
     if (!(horizon > 0) || N < 1 || std::fabs(nd - (double)N) > 1e-9 * std::max(1.0, nd))
@@ -1172,10 +1196,6 @@ int batch_submit(pnop_ctx* c, const pnop_params* p, const double2* u0, double E0
     if (slot < 0) throw Status(PNOP_ERR_OOM, "no free slot in the batch");
     // operators of this request's physics into the slot's tables (the slot
     // is idle: no queued launch reads them)
-    pnop::HostOps hs = c->h;
-    hs.ph = {p->Re, p->Wo, p->A, p->dt, p->tau0};
-    std::string err;
-    if (!pnop::build_operators(hs, err)) throw Status(PNOP_ERR_UNSUPPORTED, err);
     upload_slot_operators(c, slot, hs);
     const int s = (int)std::max<long long>(1, std::min<long long>(c->prm.snap_budget, N));
     while ((int)c->snaps.size() < s) c->snaps.push_back(c->field());
@@ -1749,11 +1769,53 @@ int pnop_batch_create(const pnop_grid* grid, const pnop_params* params, int capa
     return PNOP_OK;
 }
 
+struct pnop_ops {
+    pnop::HostOps h;
+};
+
+int pnop_batch_prepare(const pnop_batch* batch, const pnop_params* request, pnop_ops** out) {
+    if (!out) return PNOP_ERR_INVALID_ARG;
+    *out = nullptr;
+    const pnop_ctx* c = bctx_c(batch);
+    if (!c) return PNOP_ERR_INVALID_ARG;
+    try {  // records no error text: the batch may be in use by another thread
+        pnop_ops* o = new pnop_ops();
+        try {
+            o->h = batch_prepare(c, request);
+        } catch (...) {
+            delete o;
+            throw;
+        }
+        *out = o;
+        return PNOP_OK;
+    } catch (const Status& s) {
+        return s.code;
+    } catch (const std::bad_alloc&) {
+        return PNOP_ERR_OOM;
+    } catch (...) {
+        return PNOP_ERR_UNSUPPORTED;
+    }
+}
+
+void pnop_ops_free(pnop_ops* ops) { delete ops; }
+
+int pnop_batch_submit_prepared(pnop_batch* batch, const pnop_ops* ops, const void* u0, double E0, double horizon,
+                               int* id_out) {
+    pnop_ctx* c = bctx(batch);
+    return guarded(c, [&]() -> int {
+        if (!ops) throw Status(PNOP_ERR_INVALID_ARG, "ops is NULL");
+        const int id = batch_submit(c, ops->h, (const double2*)u0, E0, horizon);
+        if (id_out) *id_out = id;
+        return PNOP_OK;
+    });
+}
+
 int pnop_batch_submit(pnop_batch* batch, const pnop_params* request, const void* u0, double E0, double horizon,
                       int* id_out) {
     pnop_ctx* c = bctx(batch);
     return guarded(c, [&]() -> int {
-        const int id = batch_submit(c, request, (const double2*)u0, E0, horizon);
+        const pnop::HostOps hs = batch_prepare(c, request);
+        const int id = batch_submit(c, hs, (const double2*)u0, E0, horizon);
         if (id_out) *id_out = id;
         return PNOP_OK;
     });

@@ -11,6 +11,8 @@
 #include <cmath>
 #include <cstdio>
 #include <random>
+#include <thread>
+#include <vector>
 
 namespace pnop {
 
@@ -332,7 +334,22 @@ static Band pressure_band(const HostOps& h, int mabs, double kz) {
     return A;
 }
 
-bool build_operators(HostOps& h, std::string& err) {
+// fn(k) for k = 0..n-1 on up to 16 host threads; fn touches only data of its own k.
+template <class F> static void parallel_k(int n, F&& fn) {
+    const int T = std::max(1, std::min<int>({n, 16, (int)std::max(1u, std::thread::hardware_concurrency())}));
+    if (T == 1) {
+        for (int k = 0; k < n; ++k) fn(k, 0);
+        return;
+    }
+    std::vector<std::thread> th;
+    for (int t = 0; t < T; ++t)
+        th.emplace_back([&, t] {
+            for (int k = t; k < n; k += T) fn(k, t);
+        });
+    for (auto& x : th) x.join();
+}
+
+bool build_operators(HostOps& h, std::string& err, bool reuse_pressure) {
     const Dims& d = h.d;
     const int nr = d.nr, nk = d.nk, M = d.M;
     if (!(h.ph.Re > 0) || !(h.ph.dt > 0)) {
@@ -354,24 +371,34 @@ bool build_operators(HostOps& h, std::string& err) {
     }
     const int nt = h.ntile = (nk + kTileK - 1) / kTileK;
     const int D = kNc1Direct, T = kNc1Transposed;
+    const size_t pressure_size = (size_t)(M + 1) * nt * nr * kBand * kTileK;
+    // the pressure factors depend on the grid only: a caller that built them
+    // for this grid before may keep them
+    const bool pressure = !(reuse_pressure && h.facP.size() == pressure_size && h.facPT.size() == pressure_size);
     h.facH.assign((size_t)(M + 2) * nt * nr * kBand * kTileK, 0.0);
     h.facHT.assign(h.facH.size(), 0.0);
-    h.facP.assign((size_t)(M + 1) * nt * nr * kBand * kTileK, 0.0);
-    h.facPT.assign(h.facP.size(), 0.0);
-    std::vector<double> f;
-    double worst = 0, growth = 0;
-    for (int k = 0; k < nk; ++k) {
+    if (pressure) {
+        h.facP.assign(pressure_size, 0.0);
+        h.facPT.assign(pressure_size, 0.0);
+    }
+    // every k owns its own factor entries, so the k loop runs on host threads
+    std::vector<double> worst_t(16, 0.0);
+    std::vector<int> fail_t(16, 0);
+    parallel_k(nk, [&](int k, int t) {
+        std::vector<double> f;
+        double growth = 0;
         const double kz = 2.0 * M_PI * k / d.Lz;
         for (int ma = 0; ma <= M + 1; ++ma) {
             Band A = helmholtz_band(h, ma, kz);
             if (!band_lu(A, f, growth)) {
-                err = "Helmholtz band LU failed";
-                return false;
+                fail_t[t] = 1;
+                return;
             }
-            worst = std::max(worst, band_backward_error(A, f, 1234u + ma * 977u + k));
+            worst_t[t] = std::max(worst_t[t], band_backward_error(A, f, 1234u + ma * 977u + k));
             scatter_factors(h.facH, ma, k, nr, nt, D, f);
             scatter_factors(h.facHT, ma, k, nr, nt, T, transpose_factors(nr, f));
         }
+        if (!pressure) return;
         for (int ma = 0; ma <= M; ++ma) {
             if (ma == 0 && k == 0) {
                 // singular Neumann problem of the mean mode: never used (p = 0)
@@ -383,14 +410,24 @@ bool build_operators(HostOps& h, std::string& err) {
             }
             Band A = pressure_band(h, ma, kz);
             if (!band_lu(A, f, growth)) {
-                err = "pressure band LU failed";
-                return false;
+                fail_t[t] = 2;
+                return;
             }
-            worst = std::max(worst, band_backward_error(A, f, 4321u + ma * 131u + k));
+            worst_t[t] = std::max(worst_t[t], band_backward_error(A, f, 4321u + ma * 131u + k));
             scatter_factors(h.facP, ma, k, nr, nt, D, f);
             scatter_factors(h.facPT, ma, k, nr, nt, T, transpose_factors(nr, f));
         }
+    });
+    double worst = 0;
+    for (int t = 0; t < 16; ++t) {
+        if (fail_t[t]) {
+            err = fail_t[t] == 1 ? "Helmholtz band LU failed" : "pressure band LU failed";
+            return false;
+        }
+        worst = std::max(worst, worst_t[t]);
     }
+    std::vector<double> f, fac_tmp;
+    double growth = 0;
     if (!(worst < 1e-12)) {
         char buf[160];
         std::snprintf(buf, sizeof buf, "banded LU without pivoting is unstable here (backward error %.3g)", worst);
@@ -401,8 +438,9 @@ bool build_operators(HostOps& h, std::string& err) {
     // datum, h the Helmholtz response to -grad(phi) with u = 0 at the wall;
     // stored scaled by -1/delta, delta = d/dr(h_r) at the wall.
     h.infl.assign((size_t)d.nm * nk * 3 * nr, 0.0);
-    std::vector<double> fac_tmp;
-    for (int k = 0; k < nk; ++k) {
+    std::vector<int> zero_t(16, 0);
+    parallel_k(nk, [&](int k, int t) {
+        std::vector<double> f, fac_tmp;
         const double kz = 2.0 * M_PI * k / d.Lz;
         for (int im = 0; im < d.nm; ++im) {
             const int m = im - M;
@@ -439,8 +477,8 @@ bool build_operators(HostOps& h, std::string& err) {
             double delta = 0;
             for (int c = 0; c <= kUp && c < nr; ++c) delta += h.D1[((size_t)pv * nr + 0) * kBand + (c + kLo)] * hr[c];
             if (!(std::fabs(delta) > 1e-300) || !std::isfinite(delta)) {
-                err = "influence response has zero wall divergence";
-                return false;
+                zero_t[t] = 1;
+                return;
             }
             double* out = &h.infl[(((size_t)im * nk + k) * 3) * nr];
             for (int j = 0; j < nr; ++j) {
@@ -449,7 +487,12 @@ bool build_operators(HostOps& h, std::string& err) {
                 out[2 * nr + j] = -fz[j] / delta;
             }
         }
-    }
+    });
+    for (int t = 0; t < 16; ++t)
+        if (zero_t[t]) {
+            err = "influence response has zero wall divergence";
+            return false;
+        }
     // flux response of mode (0,0): Helmholtz of u_z with unit forcing
     {
         Band Hz = helmholtz_band(h, 0, 0.0);

@@ -68,7 +68,9 @@ int parity_index(int m);  // 0 when m is even, 1 when odd
 // Builds grid, weights and finite differences (Re-independent part).
 bool build_grid(HostOps& h, std::string& err);
 // Builds base flow, banded LU factors, influence and flux vectors.
-bool build_operators(HostOps& h, std::string& err);
+// reuse_pressure: keep h.facP / h.facPT when they already have this grid's
+// size (they depend on the grid only, not on Re or dt).
+bool build_operators(HostOps& h, std::string& err, bool reuse_pressure = false);
 
 // Bessel J_nu of complex argument by its power series.
 std::complex<double> bessel_j(int nu, std::complex<double> z);

@@ -170,32 +170,37 @@ class BatchServer:
 
     Requests of one (grid, precision, checkpoint slots) share a pnop_batch of
     `slots` request slots: every kernel of a step runs once for all requests
-    of that batch taking that kind of step.  A driver thread admits queued
-    requests into free slots (first come, first served per batch), queues
-    `ticks` batched steps per batch per round (at most two rounds in flight
-    per batch, so that new arrivals join within a few steps), and collects
-    finished requests.  A batch's device memory (about `slots` contexts) is
-    allocated when the first request of its kind arrives and counted against
-    the HBM budget; a batch with no request left is released when another
-    kind needs the memory.  Each request gets bitwise the result it gets
-    alone (the batched steps are the single-request steps per slot)."""
+    of that batch taking that kind of step.  A driver thread takes arrivals in
+    order, has their host operators built on a small thread pool
+    (pnop_batch_prepare, which may run beside the device work), admits
+    prepared requests into free slots (first come, first served per batch),
+    keeps up to `rounds` rounds of `ticks` batched steps queued per batch
+    (without blocking on the device), and collects finished requests.  A
+    batch's device memory (about `slots` contexts) is allocated when the first
+    request of its kind arrives and counted against the HBM budget; a batch
+    with no request left is released when another kind needs the memory.
+    Each request gets bitwise the result it gets alone (the batched steps are
+    the single-request steps per slot)."""
 
     def __init__(self, hbm_budget: int, slots: int = 8, ticks: int = 4, device: int = 0, batch_factory=None,
-                 sizer=None):
-        """batch_factory(request, slots, stream) -> batch object (pnop_batch_submit / run / poll / result /
-        close, as _lib.Batch) and sizer(request, slots) -> bytes replace the GPU batch and the library
-        estimate (host-side tests)."""
+                 sizer=None, rounds: int = 3, workers: int = 4):
+        """batch_factory(request, slots, stream) -> batch object (pnop_batch_prepare / submit_prepared /
+        run / poll / result / close, as _lib.Batch) and sizer(request, slots) -> bytes replace the GPU
+        batch and the library estimate (host-side tests)."""
+        from concurrent.futures import ThreadPoolExecutor
         self.hbm_budget = int(hbm_budget)
         self.slots = slots
         self.ticks = ticks
+        self.max_rounds = rounds
         self.device = device
         self.factory = batch_factory
         self.sizer = sizer
+        self.pool = ThreadPoolExecutor(max_workers=workers)
         self.queue: deque = deque()
         self.results: dict = {}
         self.lock = threading.Condition()
         self.t0 = time.perf_counter()
-        self.batches: dict = {}     # key -> dict(batch, stream, bytes, running {bid: (request, admitted)}, rounds)
+        self.batches: dict = {}  # key -> dict(batch, stream, bytes, running {bid: (request, admitted)}, rounds)
         self.bytes_in_use = 0
         self.peak_bytes = 0
         self.active = 0
@@ -240,7 +245,7 @@ class BatchServer:
             return self.batches[k]
         need = self.batch_bytes(r)
         if self.bytes_in_use + need > self.hbm_budget:  # release idle batches of other kinds
-            for kk in [kk for kk, e in self.batches.items() if not e["running"]]:
+            for kk in [kk for kk, e in self.batches.items() if not e["running"] and not e["prepared"]]:
                 e = self.batches.pop(kk)
                 e["batch"].close()
                 self.bytes_in_use -= e["bytes"]
@@ -249,47 +254,84 @@ class BatchServer:
         if self.bytes_in_use + need > self.hbm_budget:
             return None
         b, stream = self._new_batch(r)
-        e = {"batch": b, "stream": stream, "bytes": need, "running": {}, "rounds": deque()}
+        e = {"batch": b, "stream": stream, "bytes": need, "running": {}, "rounds": deque(), "prepared": deque()}
         self.batches[k] = e
         self.bytes_in_use += need
         self.peak_bytes = max(self.peak_bytes, self.bytes_in_use)
         return e
 
-    def _admit(self, pending: deque) -> None:
+    def _route(self, pending: deque) -> None:
+        """Arrivals to their batch's preparation queue (in order), at most
+        `slots` prepared or preparing requests waiting per batch."""
         keep = deque()
         while pending:
             r = pending.popleft()
             e = self._get_batch(r)
-            if e is None or len(e["running"]) >= self.slots:
+            if e is None or len(e["prepared"]) >= self.slots:
                 keep.append(r)
                 continue
+            fut = self.pool.submit(e["batch"].pnop_batch_prepare, r.Re, r.dt, r.Wo, r.A, r.tau0)
+            e["prepared"].append((r, fut))
+        pending.extend(keep)
+
+    def _admit(self, e) -> bool:
+        did = False
+        b = e["batch"]
+        while e["prepared"] and len(e["running"]) < self.slots and e["prepared"][0][1].done():
+            r, fut = e["prepared"].popleft()
+            ops = None
             try:
-                bid = self._submit_one(e, r)
+                ops = fut.result()
+                bid = self._submit_one(e, r, ops)
             except Exception as ex:  # reported per request
                 self._finish(r, self.now(), float("nan"), None, f"{type(ex).__name__}: {ex}")
                 continue
+            finally:
+                if ops is not None:
+                    b.pnop_ops_free(ops)
             e["running"][bid] = (r, self.now())
             self.active += 1
             self.peak_active = max(self.peak_active, self.active)
             self.peak_batch = max(self.peak_batch, len(e["running"]))
-        pending.extend(keep)
+            did = True
+        return did
 
-    def _submit_one(self, e, r: Request) -> int:
+    def _submit_one(self, e, r: Request, ops) -> int:
         b = e["batch"]
         if self.factory is not None:
-            return b.pnop_batch_submit(r.u0, r.E0, r.horizon, r.Re, r.dt, r.Wo, r.A, r.tau0)
+            return b.pnop_batch_submit_prepared(ops, r.u0, r.E0, r.horizon)
         import torch
         with torch.cuda.stream(e["stream"]):
             u0 = torch.from_numpy(np.ascontiguousarray(r.u0)).to(f"cuda:{self.device}", non_blocking=False)
-        return b.pnop_batch_submit(u0, r.E0, r.horizon, r.Re, r.dt, r.Wo, r.A, r.tau0)
+        return b.pnop_batch_submit_prepared(ops, u0, r.E0, r.horizon)
 
-    def _collect(self, e) -> None:
+    def _queue_rounds(self, e) -> bool:
+        rounds = e["rounds"]
+        while rounds and (rounds[0] is None or rounds[0].query()):
+            rounds.popleft()
+        did = False
+        while e["running"] and len(rounds) < self.max_rounds:
+            _, running = e["batch"].pnop_batch_run(self.ticks)
+            ev = None
+            if e["stream"] is not None:
+                import torch
+                ev = torch.cuda.Event()
+                ev.record(e["stream"])
+            rounds.append(ev)
+            did = True
+            if running == 0:
+                break
+        return did
+
+    def _collect(self, e) -> bool:
         b = e["batch"]
+        did = False
         for bid in list(e["running"]):
             if not b.pnop_batch_poll(bid):
                 continue
             r, admitted = e["running"].pop(bid)
             self.active -= 1
+            did = True
             err, gain, grad = None, float("nan"), None
             try:
                 if self.factory is not None:
@@ -303,6 +345,7 @@ class BatchServer:
             except Exception as ex:
                 err = f"{type(ex).__name__}: {ex}"
             self._finish(r, admitted, gain, grad, err)
+        return did
 
     def _finish(self, r, admitted, gain, grad, err) -> None:
         with self.lock:
@@ -317,27 +360,21 @@ class BatchServer:
         try:
             while True:
                 with self.lock:
-                    if self.closed and not self.queue and not pending and not self.active:
+                    waiting = pending or any(e["prepared"] for e in self.batches.values())
+                    if self.closed and not self.queue and not waiting and not self.active:
                         return
-                    if not self.queue and not pending and not self.active:
+                    if not self.queue and not waiting and not self.active:
                         self.lock.wait(timeout=0.05)
                     pending.extend(self.queue)
                     self.queue.clear()
-                self._admit(pending)
-                for e in self.batches.values():
-                    if not e["running"]:
-                        continue
-                    rounds = e["rounds"]
-                    if len(rounds) >= 2:  # at most two rounds in flight per batch
-                        rounds.popleft().synchronize()
-                    e["batch"].pnop_batch_run(self.ticks)
-                    if e["stream"] is not None:
-                        import torch
-                        ev = torch.cuda.Event()
-                        ev.record(e["stream"])
-                        rounds.append(ev)
-                for e in self.batches.values():
-                    self._collect(e)
+                self._route(pending)
+                did = False
+                for e in list(self.batches.values()):
+                    did |= self._admit(e)
+                    did |= self._queue_rounds(e)
+                    did |= self._collect(e)
+                if not did:
+                    time.sleep(0.0002)
         except Exception as ex:  # the driver stops; waiters see the error
             with self.lock:
                 self.error = f"{type(ex).__name__}: {ex}"
@@ -359,7 +396,13 @@ class BatchServer:
             self.closed = True
             self.lock.notify_all()
         self.driver.join(timeout=60)
+        self.pool.shutdown(wait=True)
         for e in self.batches.values():
+            for _, fut in e["prepared"]:
+                try:
+                    e["batch"].pnop_ops_free(fut.result())
+                except Exception:
+                    pass
             e["batch"].close()
         self.batches.clear()
 

@@ -136,4 +136,8 @@ def test_batch_entry_points_reject_bad_arguments_without_a_device(L):
     assert L.lib.pnop_batch_poll(None, 0, ctypes.byref(i)) == -1
     assert L.lib.pnop_batch_result(None, 0, None, None) == -1
     assert L.lib.pnop_batch_stats(None, ctypes.byref(t), None, None) == -1
+    o = ctypes.c_void_p()
+    assert L.lib.pnop_batch_prepare(None, ctypes.byref(p), ctypes.byref(o)) == -1 and o.value is None
+    assert L.lib.pnop_batch_submit_prepared(None, None, None, 1e-3, 1.0, ctypes.byref(i)) == -1
+    L.lib.pnop_ops_free(None)
     L.lib.pnop_batch_destroy(None)

@@ -86,10 +86,18 @@ class FakeBatch:
         self.closed = False
         FakeBatch.made.append(self)
 
-    def pnop_batch_submit(self, u0, E0, horizon, Re, dt, Wo, A, tau0):
-        assert len(self.left) < self.slots
+    def pnop_batch_prepare(self, Re, dt, Wo, A, tau0):
         if Re < 0:
             raise RuntimeError("planted failure")
+        return (Re, dt)
+
+    @staticmethod
+    def pnop_ops_free(ops):
+        pass
+
+    def pnop_batch_submit_prepared(self, ops, u0, E0, horizon):
+        assert len(self.left) < self.slots
+        Re, dt = ops
         bid = self.next
         self.next += 1
         self.left[bid] = int(round(horizon / dt))
