@@ -423,7 +423,7 @@ def serving_report(L, nreq=256, probe=48, load=0.7, seed=0, budget=40 << 30, max
             "peak_requests_in_one_batch": getattr(srv, "peak_batch", None)}
 
 
-def batch_report(L, torch, nsteps=20, snaps=8, seed=7):
+def batch_report(L, torch, nsteps=20, snaps=8, seed=7, only=None):
     """Batched gradients (pnop_batch) against the same requests one after
     another on single contexts, per serving resolution: B requests of seeded
     physics (as the serving stream), nsteps steps of dt = 0.005 each.
@@ -434,6 +434,8 @@ def batch_report(L, torch, nsteps=20, snaps=8, seed=7):
     rng = np.random.default_rng(seed)
     out = {}
     cases = [(res, L.PNOP_MIXED, 16 if res[0] < 64 else 8) for res in SERVE_RES] + [(SERVE_RES[0], L.PNOP_FP64, 16)]
+    if only is not None:  # one resolution (mixed) only
+        cases = [c for c in cases if c[0][:3] == tuple(only) and c[1] == L.PNOP_MIXED]
     for (nr, nth, nz, lz), prec, B in cases:
         ctx = L.Context(nr, nth, nz, lz, 2000.0, 0.005, 8.0, 1.0, 0.0, prec, 1)
         r = np.array(ctx.pnop_grid_points())
@@ -585,6 +587,8 @@ def main():
                     help="skip the single-step timings and the budget sweep (profiling runs)")
     ap.add_argument("--precision", default="both", choices=["both", "mixed", "fp64"],
                     help="which path(s) to time; 'fp64' reports the FP64 path as the main line")
+    ap.add_argument("--only-batched", default=None, metavar="RES",
+                    help="print only the batched-gradient comparison at one serving resolution (e.g. 32x32x64)")
     args = ap.parse_args()
     if args.impl == "reference":
         return reference_main(args)
@@ -600,6 +604,10 @@ def main():
     barrier(ws)
     from paper_2509_10103_gb300 import _lib as L
 
+    if args.only_batched:
+        res = tuple(int(x) for x in args.only_batched.split("x"))
+        print(json.dumps(batch_report(L, torch, only=res)))
+        return 0
     peaks, pk_src = load_peaks()
     H, s = args.horizon_steps, args.snaps
     sampler = ClockSampler(local) if rank == 0 else None
