@@ -78,6 +78,8 @@ def test_admission_budget_serialises_when_memory_is_short(mods):
 def test_batched_server_gives_each_request_its_alone_result(mods):
     L, serving = mods
     reqs = _requests(L, serving)
+    for r in reqs:  # all at once, so that requests of one kind certainly share a batch
+        r.arrival = 0.0
     mix, srv = serving.serve_stream(reqs, hbm_budget=8 << 30, max_active=4, batched=True, ticks=3)
     assert all(r.error is None for r in mix), [r.error for r in mix]
     assert srv.peak_batch >= 2  # requests of one kind shared launches
