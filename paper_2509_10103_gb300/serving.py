@@ -49,10 +49,16 @@ class Request:
     precision: int = _lib.PNOP_MIXED
     snaps: int = 8
     arrival: float = 0.0                 # seconds after the server start
+    kind: str = "gradient"               # "gradient", or "optimise": adjoint looping (Section 2.3) from u0
+    max_iter: int = 10                   # optimise: iterations at most
+    tol: float = 1e-8                    # optimise: relative change of G that stops the loop
 
 
 @dataclass
 class Result:
+    """gain: G = E(T)/E0 (for "optimise", G of the optimum found); grad: the
+    gradient (for "optimise", the optimised initial perturbation, energy E0);
+    history: the gains of the accepted iterates ("optimise" only)."""
     rid: int
     gain: float
     grad: np.ndarray
@@ -61,6 +67,7 @@ class Result:
     done: float
     device_bytes: int
     error: Optional[str] = None
+    history: Optional[list] = None
 
     @property
     def latency(self) -> float:
@@ -132,6 +139,14 @@ class Server:
                 u0 = torch.from_numpy(np.ascontiguousarray(r.u0)).to(dev)
                 g = torch.zeros(ctx.shape, dtype=torch.complex128, device=dev)
             stream.synchronize()
+            if r.kind == "optimise":  # u0 becomes the optimum, in place
+                stats, hist = ctx.pnop_optimise(u0, r.E0, r.horizon, r.max_iter, r.tol)
+                with torch.cuda.stream(stream):
+                    u = u0.cpu()
+                stream.synchronize()
+                return stats["gain"], u.numpy(), hist
+            if r.kind != "gradient":
+                raise ValueError(f"unknown request kind {r.kind!r}")
             gain = ctx.pnop_gradient(u0, r.E0, r.horizon, g)
             with torch.cuda.stream(stream):
                 grad = g.cpu()
@@ -141,14 +156,16 @@ class Server:
             ctx.close()
 
     def _run(self, r: Request, need: int, admitted: float) -> None:
-        err, gain, grad = None, float("nan"), None
+        err, gain, grad, hist = None, float("nan"), None, None
         try:
-            gain, grad = self.runner(r, need)
+            out = self.runner(r, need)
+            gain, grad = out[0], out[1]
+            hist = out[2] if len(out) > 2 else None
         except Exception as e:  # reported per request; the server keeps running
             err = f"{type(e).__name__}: {e}"
         done = self.now()
         with self.lock:
-            self.results[r.rid] = Result(r.rid, gain, grad, r.arrival, admitted, done, need, err)
+            self.results[r.rid] = Result(r.rid, gain, grad, r.arrival, admitted, done, need, err, hist)
             self.active -= 1
             self.bytes_in_use -= need
             self._admit_locked()
@@ -180,10 +197,16 @@ class BatchServer:
     request of its kind arrives and counted against the HBM budget; a batch
     with no request left is released when another kind needs the memory.
     Each request gets bitwise the result it gets alone (the batched steps are
-    the single-request steps per slot)."""
+    the single-request steps per slot).
+
+    Optimisation requests (adjoint looping) run one context each on an inner
+    Server, at most `opt_active` at a time within a quarter of the HBM
+    budget: their line search needs forward-only sweeps of one request,
+    which a batch does not run."""
 
     def __init__(self, hbm_budget: int, slots: int = 8, ticks: int = 4, device: int = 0, batch_factory=None,
-                 sizer=None, rounds: int = 3, workers: int = 4):
+                 sizer=None, rounds: int = 3, workers: int = 4, opt_active: int = 2, opt_runner=None,
+                 opt_sizer=None):
         """batch_factory(request, slots, stream) -> batch object (pnop_batch_prepare / submit_prepared /
         run / poll / result / close, as _lib.Batch) and sizer(request, slots) -> bytes replace the GPU
         batch and the library estimate (host-side tests)."""
@@ -208,6 +231,10 @@ class BatchServer:
         self.peak_batch = 0
         self.closed = False
         self.error: Optional[str] = None
+        self.opt_active = opt_active
+        self.opt_runner = opt_runner
+        self.opt_sizer = opt_sizer
+        self.opt_server: Optional[Server] = None
         self.driver = threading.Thread(target=self._drive, daemon=True)
         self.driver.start()
 
@@ -224,6 +251,15 @@ class BatchServer:
         return self.slots * _lib.pnop_context_bytes(r.nr, r.ntheta, r.nz, r.Lz, r.precision, r.snaps)
 
     def submit(self, r: Request) -> None:
+        if r.kind == "optimise":
+            if self.opt_server is None:
+                self.opt_server = Server(self.hbm_budget // 4, self.opt_active, self.device, self.opt_runner,
+                                         self.opt_sizer)
+                self.opt_server.t0 = self.t0
+            self.opt_server.submit(r)
+            return
+        if r.kind != "gradient":
+            raise ValueError(f"unknown request kind {r.kind!r}")
         if self.batch_bytes(r) > self.hbm_budget:
             raise ValueError(f"request {r.rid}: a batch of its kind needs more than the whole budget")
         with self.lock:
@@ -382,14 +418,20 @@ class BatchServer:
 
     def wait(self, n: int, timeout: float = 3600.0) -> None:
         end = time.perf_counter() + timeout
+
+        def count():
+            return len(self.results) + (len(self.opt_server.results) if self.opt_server else 0)
+
         with self.lock:
-            while len(self.results) < n:
+            while count() < n:
                 if self.error:
                     raise RuntimeError(f"serving driver failed: {self.error}")
                 left = end - time.perf_counter()
                 if left <= 0:
-                    raise TimeoutError(f"{len(self.results)} of {n} requests finished")
+                    raise TimeoutError(f"{count()} of {n} requests finished")
                 self.lock.wait(timeout=min(left, 0.05))
+            if self.opt_server:
+                self.results.update(self.opt_server.results)
 
     def close(self) -> None:
         with self.lock:

@@ -88,3 +88,27 @@ def test_batched_server_gives_each_request_its_alone_result(mods):
         a, m = alone[0], mix[r.rid]
         assert a.gain == m.gain
         assert np.array_equal(a.grad, m.grad)
+
+
+def test_optimisation_request_served_beside_gradients_matches_alone(mods):
+    L, serving = mods
+    import torch
+    reqs = _requests(L, serving)[:3]
+    for r in reqs:
+        r.arrival = 0.0
+    opt = reqs[1]
+    opt.kind, opt.max_iter = "optimise", 2
+    mix, srv = serving.serve_stream(reqs, hbm_budget=8 << 30, max_active=4, batched=True, ticks=3)
+    assert all(r.error is None for r in mix), [r.error for r in mix]
+    m = mix[opt.rid]
+    assert m.history is not None and len(m.history) >= 2 and m.gain == m.history[-1]
+    ctx = L.Context(opt.nr, opt.ntheta, opt.nz, opt.Lz, opt.Re, opt.dt, opt.Wo, opt.A, opt.tau0, opt.precision,
+                    opt.snaps)
+    u = torch.from_numpy(np.ascontiguousarray(opt.u0)).to("cuda")
+    stats, hist = ctx.pnop_optimise(u, opt.E0, opt.horizon, opt.max_iter, opt.tol)
+    ctx.close()
+    assert m.gain == stats["gain"] and list(m.history) == list(hist)
+    assert np.array_equal(m.grad, u.cpu().numpy())
+    for r in (reqs[0], reqs[2]):
+        alone, _ = serving.serve_stream([r], hbm_budget=8 << 30, max_active=1)
+        assert alone[0].gain == mix[r.rid].gain and np.array_equal(alone[0].grad, mix[r.rid].grad)

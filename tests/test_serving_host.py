@@ -153,3 +153,37 @@ def test_batch_server_budget_releases_idle_batches_and_reports_errors():
     assert res[2].error is not None and "planted" in res[2].error
     assert srv.peak_bytes <= 1
     assert len(FakeBatch.made) == 3 and FakeBatch.made[0].closed
+
+
+def test_batch_server_runs_optimisation_requests_on_contexts():
+    FakeBatch.made.clear()
+    seen = []
+
+    def opt_runner(r, need):
+        seen.append(r.rid)
+        time.sleep(0.02)
+        return 100.0 + r.rid, np.full(3, -r.rid), [1.0, 50.0, 100.0 + r.rid]
+
+    srv = serving.BatchServer(hbm_budget=8, slots=2, ticks=1, batch_factory=FakeBatch,
+                              sizer=lambda r, slots: 1, opt_runner=opt_runner, opt_sizer=lambda r: 1)
+    reqs = [_breq(i, 1, 3) for i in range(6)]
+    for r in reqs[::2]:
+        r.kind = "optimise"
+    try:
+        for r in reqs:
+            srv.submit(r)
+        srv.wait(len(reqs))
+    finally:
+        srv.close()
+    res = srv.results
+    assert sorted(seen) == [0, 2, 4]
+    for i in range(6):
+        assert res[i].error is None
+        if i % 2 == 0:
+            assert res[i].gain == 100.0 + i and res[i].history[-1] == res[i].gain
+        else:
+            assert res[i].gain == float(i) and res[i].history is None
+    with pytest.raises(ValueError):
+        bad = _breq(9, 1, 3)
+        bad.kind = "bogus"
+        srv.submit(bad)
