@@ -120,3 +120,24 @@ def test_batch_at_full_size_matches_alone(L):
         assert gain == gain1
         assert torch.equal(g, g1)
     b.close()
+
+
+def test_batched_fp64_requests_match_the_oracle(L):
+    """Two FP64 requests of different physics in one batch against the oracle
+    gradient (relative 1e-10, as the single-request parity tests)."""
+    import torch
+    reqs = [REQS[0], REQS[1]]
+    us = seeds(L, 2)
+    b = L.Batch(GRID["nr"], GRID["ntheta"], GRID["nz"], GRID["Lz"], capacity=2, precision=0, snap_budget=3)
+    ids = [b.pnop_batch_submit(u, r[5], r[6] * r[3], r[0], r[3], r[1], r[2], r[4]) for r, u in zip(reqs, us)]
+    b.pnop_batch_run(10000)
+    M, K = GRID["ntheta"] // 2 - 1, GRID["nz"] // 2 - 1
+    for rid, (Re, Wo, A, dt, tau0, E0, n), u in zip(ids, reqs, us):
+        g = torch.empty_like(u)
+        gain = b.pnop_batch_result(rid, g)
+        o = po.Oracle(po.Params(nr=GRID["nr"], M=M, K=K, Lz=GRID["Lz"], Re=Re, dt=dt, Wo=Wo, A=A))
+        u0 = o.scale_to(u.cpu().numpy(), E0)
+        ET, gref = o.gradient(u0, tau0, n)
+        assert abs(gain / (ET / o.energy(u0)) - 1) < 1e-10
+        assert np.abs(g.cpu().numpy() - gref).max() <= 1e-10 * np.abs(gref).max()
+    b.close()
