@@ -537,6 +537,21 @@ def oracle_sample(planes=4, modes=16):
     return json.loads(p.stdout.strip().splitlines()[-1])
 
 
+def oracle_sample_parallel(planes=16, modes=64, procs=None):
+    """The same one-thread oracle sample in `procs` processes at once (all host
+    cores by default): the sample's planes and modes are independent, so
+    procs / (wall time) samples per second is the oracle's all-core rate."""
+    procs = procs or os.cpu_count() or 1
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    ps = [subprocess.Popen([sys.executable, "-c", ORACLE_SAMPLE_CODE, ROOT, str(planes), str(modes)],
+                           stdout=subprocess.PIPE, stderr=subprocess.PIPE, text=True, env=env) for _ in range(procs)]
+    outs = [p.communicate(timeout=1800) for p in ps]
+    if any(p.returncode != 0 for p in ps):
+        raise RuntimeError("parallel oracle sample failed")
+    # each process times its own sample while all cores are busy
+    return procs, [json.loads(o.strip().splitlines()[-1])["per_step_s"] for o, _ in outs]
+
+
 def oracle_sample_desc(planes, modes):
     return (f"FP64 numpy oracle, 1 thread: curl + 3/2-padded transforms/products on {planes} of {NR} radial planes"
             f" (x{NR // planes}), stage maps applied on {modes} random (m,k) modes (x{(2 * M + 1) * (K + 1) // modes}),"
@@ -665,6 +680,12 @@ def main():
         smp = oracle_sample(planes, modes)
         out["cpu_baseline"] = {"value": 1.0 / smp["per_step_s"], "unit": "steps/s", "cores": 1, "kind": "oracle",
                                "sample": oracle_sample_desc(planes, modes)}
+        if not args.no_extras:
+            procs, per_step = oracle_sample_parallel(planes, modes)
+            # every process extrapolates one step from its share of the cores
+            out["cpu_baseline_all_cores"] = {
+                "value": sum(1.0 / x for x in per_step), "unit": "steps/s", "cores": procs, "kind": "oracle",
+                "sample": oracle_sample_desc(planes, modes) + f"; {procs} such samples at once, one per core"}
     print(json.dumps(out))
     return 0
 
