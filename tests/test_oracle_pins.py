@@ -410,3 +410,31 @@ def test_linear_step_of_steady_pipe_flow_has_no_growing_mode():
                 e[i] = 1.0
                 J[:, i] = o.linear_mode_step(e.reshape(3, o.p.nr), m, k, 0.0).ravel()
             assert np.abs(np.linalg.eigvals(J)).max() < 1.0, (m, k)
+
+
+def test_uniform_base_flow_only_translates_a_mode():
+    """The advective base-flow term -U du/dz (Eq. 2.5) for a plug flow U = U0:
+    advection by a uniform velocity is a translation, so every Fourier mode of
+    the solution without base flow turns by exp(-i k_z U0 t) (the factor is a
+    scalar per mode and commutes with the viscous operator and the wall
+    conditions).  The discrete pressure projection sees the forcing -i k_z U0 u
+    through its discrete divergence, which vanishes only to finite-difference
+    order, so the gap is a spatial discretisation error: it falls under radial
+    refinement.  A wrong sign or a dropped k_z leaves an O(1) gap.  (The
+    energy budget does not see this term: it is energy-neutral.)"""
+    U0, T, m, k, dt = 0.7, 1.0, 1, 2, 0.01
+    gaps = {}
+    for nr in (12, 24):
+        prm = dict(nr=nr, M=2, K=3, Lz=6.0, Re=1000.0, dt=dt, Wo=8.0, A=0.0, base=False)
+        still = po.Oracle(po.Params(**prm))
+        plug = po.Oracle(po.Params(**prm))
+        plug.base = lambda t, o=plug: (np.full_like(o.r, U0), np.zeros_like(o.r))
+        u = synth.random_field(still.r, 2, 3, 6.0, seed=9)[:, :, m + 2, k]
+        a, b = u.copy(), u.copy()
+        for s in range(int(round(T / dt))):
+            a = still.linear_mode_step(a, m, k, s * dt)
+            b = plug.linear_mode_step(b, m, k, s * dt)
+        turn = np.exp(-1j * still.kz[k] * U0 * T)
+        gaps[nr] = np.abs(b - a * turn).max() / np.abs(a).max()
+        assert np.abs(b - a * np.conj(turn)).max() / np.abs(a).max() > 0.5  # the other direction is far off
+    assert gaps[24] < 1e-4 and gaps[12] > 10 * gaps[24]
