@@ -348,8 +348,11 @@ def roofline(L, res, mixed, peaks, pk_src):
             "traffic": tt}
     if frac_f >= frac_b:
         base.update({"bound": "alu", "achieved": ach_f, "peak": fp_peak, "unit": "TFLOP/s", "frac": frac_f,
-                     "peak_source": f"derived: {N_SM} SMs x {FP32_FLOPS_PER_CLK_SM if fp_peak > 10 else FP64_FLOPS_PER_CLK_SM} flop/clk x {smx:g} MHz",
-                     "hbm_frac": frac_b})
+                     "peak_source": f"derived: {N_SM} SMs x {FP32_FLOPS_PER_CLK_SM if fp_peak > 10 else FP64_FLOPS_PER_CLK_SM} flop/clk x {smx:g} MHz"})
+        if by is not None:
+            base["hbm_frac"] = frac_b
+        elif tt:  # the class counts flops only: its HBM use from the measured DRAM traffic per launch
+            base["hbm_frac_of_measured_traffic"] = tt / (t / launches) / 1e9 / hbm
     else:
         base.update({"bound": "hbm", "achieved": ach_b, "peak": hbm, "unit": "GB/s", "frac": frac_b,
                      "peak_source": f"{pk_src} (MEASURED_PEAKS.json hbm_gbs)" if pk_src == "measured" else "fallback",
