@@ -440,6 +440,12 @@ int pnop_batch_result(pnop_batch* batch, int id, void* grad_out, double* gain_ou
  * (entries / ticks = mean batch size) and the kernels launched. */
 int pnop_batch_stats(const pnop_batch* batch, long long* ticks, long long* entries, long long* launches);
 
+/* Device bytes pnop_batch_create allocates for this grid, precision
+ * (params->precision), checkpoint slots (params->snap_budget) and capacity (an
+ * upper estimate, for admission control by an HBM budget).  Host only; needs
+ * no device. */
+int pnop_batch_bytes(const pnop_grid* grid, const pnop_params* params, int capacity, size_t* bytes);
+
 const char* pnop_batch_last_error(const pnop_batch* batch);
 void pnop_batch_destroy(pnop_batch* batch);
 

@@ -30,7 +30,7 @@ EXPORTS = (
     "pnop_energy_noalloc", "pnop_last_error", "pnop_error_string", "pnop_destroy",
     "pnop_batch_create", "pnop_batch_submit", "pnop_batch_run", "pnop_batch_poll", "pnop_batch_result",
     "pnop_batch_stats", "pnop_batch_last_error", "pnop_batch_destroy", "pnop_batch_prepare",
-    "pnop_batch_submit_prepared", "pnop_ops_free",
+    "pnop_batch_submit_prepared", "pnop_ops_free", "pnop_batch_bytes",
 )
 
 
@@ -100,6 +100,7 @@ def _load():
         "pnop_batch_prepare": (c_int, [c_void_p, POINTER(pnop_params), POINTER(c_void_p)]),
         "pnop_batch_submit_prepared": (c_int, [c_void_p, c_void_p, c_void_p, c_double, c_double, POINTER(c_int)]),
         "pnop_ops_free": (None, [c_void_p]),
+        "pnop_batch_bytes": (c_int, [POINTER(pnop_grid), POINTER(pnop_params), c_int, POINTER(c_size_t)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -152,6 +153,17 @@ def pnop_context_bytes(nr, ntheta, nz, Lz, precision, snaps):
     rc = lib.pnop_context_bytes(byref(g), byref(p), snaps, byref(out))
     if rc != PNOP_OK:
         raise PnopError(rc, "context_bytes")
+    return out.value
+
+
+def pnop_batch_bytes(nr, ntheta, nz, Lz, precision, snaps, capacity):
+    """Upper estimate of the device bytes of a batch (host only)."""
+    g = pnop_grid(nr, ntheta, nz, Lz, 0.0)
+    p = pnop_params(1.0, 1.0, 0.0, 1.0, 0.0, precision, snaps, 0)
+    out = c_size_t()
+    rc = lib.pnop_batch_bytes(byref(g), byref(p), capacity, byref(out))
+    if rc != PNOP_OK:
+        raise PnopError(rc, "batch_bytes")
     return out.value
 
 

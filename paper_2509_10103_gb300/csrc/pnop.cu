@@ -1329,6 +1329,22 @@ int pnop_context_bytes(const pnop_grid* grid, const pnop_params* params, int sna
     return PNOP_OK;
 }
 
+int pnop_batch_bytes(const pnop_grid* grid, const pnop_params* params, int capacity, size_t* bytes) {
+    if (!grid || !params || !bytes || params->snap_budget < 1 || capacity < 1 || capacity > pnop::kMaxBatch ||
+        grid->nr < 1 || grid->ntheta < 4 || grid->nz < 4)
+        return PNOP_ERR_INVALID_ARG;
+    const size_t nr = grid->nr, M = grid->ntheta / 2 - 1, K = grid->nz / 2 - 1, C = capacity;
+    const size_t nm = 2 * M + 1, nk = K + 1, nkp = (nk + pnop::kTileK - 1) / pnop::kTileK * pnop::kTileK, nt = 3 * (M + 1);
+    const size_t S = nr * nm * nk, field = 3 * S * 16, snaps = (size_t)params->snap_budget;
+    const size_t cz = params->precision == PNOP_MIXED ? 8 : 16;
+    size_t b = C * (18 + snaps) * field;                                 // work fields, state, cotangent, result, q, q2, checkpoints
+    b += C * 27 * nr * nt * nk * cz;                                     // transform scratch Y, Y2, Z (9 planes each)
+    b += C * 2 * (M + 2) * nr * 13 * nkp * 8 + 2 * (M + 1) * nr * 13 * nkp * 8;  // Helmholtz factors per slot, pressure shared
+    b += C * ((M + 2) * nr * 13 * 8 + nm * nk * 3 * nr * 8 + nk * 8 + 5 * nr * 8) + 2 * nr * 13 * 8;  // bands, influence
+    *bytes = b + (1 << 20) + C * (40 + snaps) * (2 << 20);              // tables, reductions, allocation rounding
+    return PNOP_OK;
+}
+
 int pnop_two_level_counts(long long nsteps, int snaps, long long max_host_slots, double io_ratio,
                           int* host_checkpoints, long long* advances) {
     if (nsteps < 1 || snaps < 1 || max_host_slots < 0 || !(io_ratio >= 0) || !std::isfinite(io_ratio))

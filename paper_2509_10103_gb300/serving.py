@@ -193,9 +193,10 @@ class BatchServer:
     prepared requests into free slots (first come, first served per batch),
     keeps up to `rounds` rounds of `ticks` batched steps queued per batch
     (without blocking on the device), and collects finished requests.  A
-    batch's device memory (about `slots` contexts) is allocated when the first
-    request of its kind arrives and counted against the HBM budget; a batch
-    with no request left is released when another kind needs the memory.
+    batch's device memory (about `slots` contexts, pnop_batch_bytes) is
+    allocated when the first request of its kind arrives and counted against
+    the HBM budget; a batch with no request left is released when another
+    kind needs the memory.
     Each request gets bitwise the result it gets alone (the batched steps are
     the single-request steps per slot).
 
@@ -248,7 +249,7 @@ class BatchServer:
     def batch_bytes(self, r: Request) -> int:
         if self.sizer is not None:
             return int(self.sizer(r, self.slots))
-        return self.slots * _lib.pnop_context_bytes(r.nr, r.ntheta, r.nz, r.Lz, r.precision, r.snaps)
+        return _lib.pnop_batch_bytes(r.nr, r.ntheta, r.nz, r.Lz, r.precision, r.snaps, self.slots)
 
     def submit(self, r: Request) -> None:
         if r.kind == "optimise":

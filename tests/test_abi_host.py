@@ -141,3 +141,18 @@ def test_batch_entry_points_reject_bad_arguments_without_a_device(L):
     assert L.lib.pnop_batch_submit_prepared(None, None, None, 1e-3, 1.0, ctypes.byref(i)) == -1
     L.lib.pnop_ops_free(None)
     L.lib.pnop_batch_destroy(None)
+
+
+def test_batch_bytes_estimate_grows_with_capacity_and_checkpoints(L):
+    b = {c: L.pnop_batch_bytes(64, 64, 256, 100.0, L.PNOP_MIXED, 8, c) for c in (1, 2, 8)}
+    assert b[1] < b[2] < b[8] and b[8] > 7 * (b[2] - b[1])
+    assert L.pnop_batch_bytes(64, 64, 256, 100.0, L.PNOP_MIXED, 16, 2) > b[2]
+    assert L.pnop_batch_bytes(64, 64, 256, 100.0, L.PNOP_FP64, 8, 2) > b[2]
+    field = 3 * 64 * 63 * 128 * 16
+    assert b[2] > 2 * (18 + 8) * field  # at least the per-slot fields
+    import ctypes
+    g = L.pnop_grid(64, 64, 256, 100.0, 0.0)
+    out = ctypes.c_size_t()
+    for cap, snaps in ((0, 8), (17, 8), (2, 0)):
+        p = L.pnop_params(1.0, 1.0, 0.0, 1.0, 0.0, 1, snaps, 0)
+        assert L.lib.pnop_batch_bytes(ctypes.byref(g), ctypes.byref(p), cap, ctypes.byref(out)) == -1

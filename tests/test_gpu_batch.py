@@ -141,3 +141,16 @@ def test_batched_fp64_requests_match_the_oracle(L):
         assert abs(gain / (ET / o.energy(u0)) - 1) < 1e-10
         assert np.abs(g.cpu().numpy() - gref).max() <= 1e-10 * np.abs(gref).max()
     b.close()
+
+
+def test_batch_bytes_bounds_what_a_batch_allocates(L):
+    import torch
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    b = L.Batch(32, 32, 64, 10.0, capacity=4, precision=1, snap_budget=4)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    b.close()
+    used = free0 - free1
+    est = L.pnop_batch_bytes(32, 32, 64, 10.0, 1, 4, 4)
+    assert 0 < used <= est
