@@ -2,6 +2,7 @@
 // predictor-corrector step (Section 2.4), its exact transpose, and the
 // binomially checkpointed gradient sweep (Section 2.5, Eq. 2.18-2.20).
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <chrono>
@@ -34,6 +35,15 @@ struct Status : std::runtime_error {
 void ck(cudaError_t e, const char* what) {
     if (e != cudaSuccess) throw CudaError(std::string(what) + ": " + cudaGetErrorString(e));
 }
+
+// NVTX range over a scope (step, stage, sweep), for timeline tools and for
+// ncu --nvtx filters; a no-op when no tool is attached.
+struct Range {
+    explicit Range(const char* name) { nvtxRangePushA(name); }
+    ~Range() { nvtxRangePop(); }
+    Range(const Range&) = delete;
+    Range& operator=(const Range&) = delete;
+};
 
 // Binomial schedule (Section 2.5) as a list of actions: advance n steps from
 // the state in a slot (into another slot, or into the scratch state when dst
@@ -361,6 +371,7 @@ void stage_bu(pnop_ctx* c, const double2* u, double2* RB, cudaStream_t st) {
 // rb_ready is given the context stream waits for it before using RB.
 void stage(pnop_ctx* c, const double2* RB, const double2* F, double2* out, const double2* addto,
            cudaEvent_t rb_ready) {
+    Range nvtx_range("pnop:stage");
     const Geo& g = c->geo;
     cudaStream_t s = c->stream;
     const double S = (double)c->S();
@@ -398,6 +409,7 @@ void stageT_proj(pnop_ctx* c, double2* Fb, double2* q, cudaStream_t s) {
 
 // ub (=, or += when acc) S_u^H ubn ; Fb = S_F^H ubn  (either may be null)
 void stageT(pnop_ctx* c, const double2* ubn, double2* ub, int acc, double2* Fb) {
+    Range nvtx_range("pnop:stageT");
     const Geo& g = c->geo;
     stageT_front(c, ubn, c->R, c->stream);
     run(c, PNOP_K_RADIAL_BAND, 1, ((ub ? flops::trhs_u : 0) + (Fb ? flops::trhs_f : 0)) * c->S(),
@@ -488,6 +500,7 @@ void queue_base(pnop_ctx* c, const double2* u, double t) {
 // transforms run).  The physical u and w are left in Y (fields 0..5).  With
 // base_queued the caller has already queued the base terms of this u.
 void nonlinear(pnop_ctx* c, const double2* u, double t, double2* N, void* Y, bool base_queued = false) {
+    Range nvtx_range("pnop:nonlinear");
     const Geo& g = c->geo;
     const size_t S = c->S();
     cudaStream_t s = c->stream;
@@ -514,6 +527,7 @@ void nonlinear(pnop_ctx* c, const double2* u, double t, double2* N, void* Y, boo
 // holds the physical u and curl u of this u (fields 0..5, left by nonlinear).
 // The base-flow transpose runs on the side stream and is added by the analysis.
 void nonlinearT(pnop_ctx* c, const double2* u, double t, const double2* nb, double2* ub, void* Y, bool cached) {
+    Range nvtx_range("pnop:nonlinearT");
     const Geo& g = c->geo;
     const size_t S = c->S();
     cudaStream_t s = c->stream;
@@ -561,6 +575,7 @@ void queue_base_adj(pnop_ctx* c, const double2* w, double t) {
 }
 
 void nonlinear_adj(pnop_ctx* c, const double2* w, const double2* u, double t, double2* N, bool base_queued = false) {
+    Range nvtx_range("pnop:nonlinear_adj");
     const Geo& g = c->geo;
     const size_t S = c->S();
     cudaStream_t s = c->stream;
@@ -596,6 +611,7 @@ void nonlinear_adj(pnop_ctx* c, const double2* w, const double2* u, double t, do
 // predictor and at (u_now, t_now) for the corrector; S is the same stage map.
 void cadj_step(pnop_ctx* c, const double2* u_next, double t_next, const double2* u_now, double t_now,
                const double2* w, double2* out) {
+    Range nvtx_range("pnop:cadj_step");
     fork_side(c);
     queue_base_adj(c, w, t_next);
     stage_bu(c, w, c->RB, c->side);
@@ -612,6 +628,7 @@ void cadj_step(pnop_ctx* c, const double2* u_next, double t_next, const double2*
 // (S is linear), so the corrector skips the explicit viscous matvec.  B u
 // depends on u only and runs on the side stream while N(u) is transformed.
 void fwd_step(pnop_ctx* c, const double2* u, double2* out, double t) {
+    Range nvtx_range("pnop:fwd_step");
     fork_side(c);
     queue_base(c, u, t);
     stage_bu(c, u, c->RB, c->side);
@@ -633,6 +650,7 @@ void fwd_step(pnop_ctx* c, const double2* u, double2* out, double t) {
 // side stream while the predictor is re-run on the context stream.  N(u) and
 // N'(u)^T share the physical u and curl u (scratch Y2).
 void adj_step(pnop_ctx* c, const double2* u, double t, const double2* lin, double2* lout) {
+    Range nvtx_range("pnop:adj_step");
     const Geo& g = c->geo;
     fork_side(c);
     queue_base(c, u, t);
@@ -935,6 +953,7 @@ double measure_io_ratio(pnop_ctx* c) {
 // schedule up to its first adjoint step, computes u_N and E(T).  The sweep
 // state stays in the context for gradient_backward.
 void gradient_forward(pnop_ctx* c, const double2* u0, double E0, double horizon, double* ET, double* Einit_out) {
+    Range nvtx_range("pnop:gradient_forward");
     const double dt = c->h.ph.dt;
     const double nd = horizon / dt;
     const long long N = (long long)std::llround(nd);
@@ -986,6 +1005,7 @@ void gradient_forward(pnop_ctx* c, const double2* u0, double E0, double horizon,
 // Backward part: terminal cotangent gE * W_hat u_N, the remaining schedule,
 // then grad = cotangent / W_hat (Riesz) or the Euclidean cotangent itself.
 void gradient_backward(pnop_ctx* c, double gE, bool euclidean, double2* grad) {
+    Range nvtx_range("pnop:gradient_backward");
     if (!c->pending) throw Status(PNOP_ERR_INVALID_ARG, "no pending gradient forward on this context");
     c->pending = false;
     weight(c, c->uN, c->lamA, 0);
@@ -1233,6 +1253,7 @@ int batch_submit(pnop_ctx* c, const pnop::HostOps& hs, const double2* u0, double
 // One tick: copies and finished requests first, then one batched step.
 // Returns false when no request has work left.
 bool batch_tick(pnop_ctx* c) {
+    Range nvtx_range("pnop:batch_tick");
     std::vector<int> lists[3], fin;  // kOpFwd, kOpTerm, kOpAdj
     const size_t fb = c->field_bytes();
     for (int i = 0; i < c->nslot; ++i) {
