@@ -52,6 +52,7 @@ class Request:
     kind: str = "gradient"               # "gradient", or "optimise": adjoint looping (Section 2.3) from u0
     max_iter: int = 10                   # optimise: iterations at most
     tol: float = 1e-8                    # optimise: relative change of G that stops the loop
+    deadline: Optional[float] = None     # seconds after arrival by which it must be admitted, else dropped
 
 
 @dataclass
@@ -74,8 +75,17 @@ class Result:
         return self.done - self.arrival
 
 
+CANCELLED = "cancelled"
+EXPIRED = "deadline exceeded before admission"
+
+
 class Server:
-    """Admits requests by HBM budget and slot count; runs each on its own stream."""
+    """Admits requests by HBM budget and slot count; runs each on its own stream.
+
+    cancel(rid) drops a queued request at once; a running one finishes its
+    device work (launched kernels are never interrupted) and its result is
+    discarded.  A request with a deadline that is still queued when it passes
+    is dropped.  Both are reported as the request's error."""
 
     def __init__(self, hbm_budget: int, max_active: int = 8, device: int = 0, runner=None, sizer=None):
         """runner(request, budget_bytes) -> (gain, grad) replaces the GPU runner
@@ -94,9 +104,33 @@ class Server:
         self.lock = threading.Condition()
         self.t0 = time.perf_counter()
         self.threads = []
+        self.cancelled: set = set()
 
     def now(self) -> float:
         return time.perf_counter() - self.t0
+
+    def _drop_locked(self, r: Request, why: str) -> None:
+        self.results[r.rid] = Result(r.rid, float("nan"), None, r.arrival, float("nan"), self.now(), 0, why)
+        self.lock.notify_all()
+
+    def cancel(self, rid: int) -> bool:
+        """Cancel a queued or running request; False when it is unknown or done."""
+        with self.lock:
+            for i, (r, _) in enumerate(self.queue):
+                if r.rid == rid:
+                    del self.queue[i]
+                    self._drop_locked(r, CANCELLED)
+                    return True
+            if rid in self.results:
+                return False
+            self.cancelled.add(rid)
+            return True
+
+    def _expire_locked(self) -> None:
+        now = self.now()
+        for r, need in [q for q in self.queue if q[0].deadline is not None and now - q[0].arrival > q[0].deadline]:
+            self.queue.remove((r, need))
+            self._drop_locked(r, EXPIRED)
 
     def request_bytes(self, r: Request) -> int:
         if self.sizer is not None:
@@ -112,6 +146,7 @@ class Server:
             self._admit_locked()
 
     def _admit_locked(self) -> None:
+        self._expire_locked()
         # first come, first served: the head waits until its memory fits
         while self.queue and self.active < self.max_active:
             r, need = self.queue[0]
@@ -165,6 +200,8 @@ class Server:
             err = f"{type(e).__name__}: {e}"
         done = self.now()
         with self.lock:
+            if r.rid in self.cancelled:
+                gain, grad, hist, err = float("nan"), None, None, CANCELLED
             self.results[r.rid] = Result(r.rid, gain, grad, r.arrival, admitted, done, need, err, hist)
             self.active -= 1
             self.bytes_in_use -= need
@@ -176,10 +213,13 @@ class Server:
         end = time.perf_counter() + timeout
         with self.lock:
             while len(self.results) < n:
+                self._expire_locked()
+                if len(self.results) >= n:
+                    break
                 left = end - time.perf_counter()
                 if left <= 0:
                     raise TimeoutError(f"{len(self.results)} of {n} requests finished")
-                self.lock.wait(timeout=min(left, 1.0))
+                self.lock.wait(timeout=min(left, 0.05))
 
 
 class BatchServer:
@@ -203,7 +243,11 @@ class BatchServer:
     Optimisation requests (adjoint looping) run one context each on an inner
     Server, at most `opt_active` at a time within a quarter of the HBM
     budget: their line search needs forward-only sweeps of one request,
-    which a batch does not run."""
+    which a batch does not run.
+
+    cancel(rid) and deadlines behave as in Server: a request not yet in a
+    slot is dropped; one in a slot runs to its end (its steps are shared
+    launches) and its result is discarded."""
 
     def __init__(self, hbm_budget: int, slots: int = 8, ticks: int = 4, device: int = 0, batch_factory=None,
                  sizer=None, rounds: int = 3, workers: int = 4, opt_active: int = 2, opt_runner=None,
@@ -236,6 +280,8 @@ class BatchServer:
         self.opt_runner = opt_runner
         self.opt_sizer = opt_sizer
         self.opt_server: Optional[Server] = None
+        self.opt_rids: set = set()
+        self.cancelled: set = set()
         self.driver = threading.Thread(target=self._drive, daemon=True)
         self.driver.start()
 
@@ -251,8 +297,34 @@ class BatchServer:
             return int(self.sizer(r, self.slots))
         return _lib.pnop_batch_bytes(r.nr, r.ntheta, r.nz, r.Lz, r.precision, r.snaps, self.slots)
 
+    def cancel(self, rid: int) -> bool:
+        """Cancel a request (see the class note); False when it is unknown or done."""
+        if rid in self.opt_rids:
+            return self.opt_server.cancel(rid)
+        with self.lock:
+            for r in list(self.queue):
+                if r.rid == rid:
+                    self.queue.remove(r)
+                    self.results[r.rid] = Result(r.rid, float("nan"), None, r.arrival, float("nan"), self.now(), 0,
+                                                 CANCELLED)
+                    self.lock.notify_all()
+                    return True
+            if rid in self.results:
+                return False
+            self.cancelled.add(rid)
+            return True
+
+    def _dropped(self, r: Request) -> Optional[str]:
+        """Why a request not yet in a slot is dropped (None: keep it)."""
+        if r.rid in self.cancelled:
+            return CANCELLED
+        if r.deadline is not None and self.now() - r.arrival > r.deadline:
+            return EXPIRED
+        return None
+
     def submit(self, r: Request) -> None:
         if r.kind == "optimise":
+            self.opt_rids.add(r.rid)
             if self.opt_server is None:
                 self.opt_server = Server(self.hbm_budget // 4, self.opt_active, self.device, self.opt_runner,
                                          self.opt_sizer)
@@ -303,6 +375,10 @@ class BatchServer:
         keep = deque()
         while pending:
             r = pending.popleft()
+            why = self._dropped(r)
+            if why:
+                self._finish(r, float("nan"), float("nan"), None, why)
+                continue
             e = self._get_batch(r)
             if e is None or len(e["prepared"]) >= self.slots:
                 keep.append(r)
@@ -314,6 +390,15 @@ class BatchServer:
     def _admit(self, e) -> bool:
         did = False
         b = e["batch"]
+        for item in [x for x in e["prepared"] if x[1].done() and self._dropped(x[0])]:
+            e["prepared"].remove(item)
+            r, fut = item
+            try:
+                b.pnop_ops_free(fut.result())
+            except Exception:
+                pass
+            self._finish(r, float("nan"), float("nan"), None, self._dropped(r))
+            did = True
         while e["prepared"] and len(e["running"]) < self.slots and e["prepared"][0][1].done():
             r, fut = e["prepared"].popleft()
             ops = None
@@ -381,6 +466,8 @@ class BatchServer:
                     grad = g.cpu().numpy()
             except Exception as ex:
                 err = f"{type(ex).__name__}: {ex}"
+            if r.rid in self.cancelled:
+                gain, grad, err = float("nan"), None, CANCELLED
             self._finish(r, admitted, gain, grad, err)
         return did
 

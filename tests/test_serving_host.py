@@ -187,3 +187,50 @@ def test_batch_server_runs_optimisation_requests_on_contexts():
         bad = _breq(9, 1, 3)
         bad.kind = "bogus"
         srv.submit(bad)
+
+
+def test_context_server_cancels_and_expires_requests():
+    gpu = FakeGPU(dur=0.2)
+    srv = serving.Server(hbm_budget=1, max_active=1, runner=gpu, sizer=lambda r: 1)
+    reqs = [_req(0), _req(1), _req(2), _req(3)]
+    reqs[3].deadline = 0.05            # waits behind request 0 and 2 for longer than 50 ms
+    for r in reqs:
+        srv.submit(r)
+    assert srv.cancel(1)               # queued: dropped at once
+    assert srv.cancel(0)               # running: finishes, result discarded
+    srv.wait(4)
+    res = srv.results
+    assert res[0].error == serving.CANCELLED and res[0].grad is None
+    assert res[1].error == serving.CANCELLED and res[1].rid not in gpu.start
+    assert res[2].error is None and res[2].gain == 2.0
+    assert res[3].error == serving.EXPIRED and 3 not in gpu.start
+    assert not srv.cancel(2)           # already done
+
+
+class SlowBatch(FakeBatch):
+    """FakeBatch whose ticks take real time, so that requests wait for slots."""
+
+    def pnop_batch_run(self, ticks):
+        time.sleep(0.01 * ticks)
+        return super().pnop_batch_run(ticks)
+
+
+def test_batch_server_cancels_and_expires_requests():
+    FakeBatch.made.clear()
+    srv = serving.BatchServer(hbm_budget=8, slots=1, ticks=1, batch_factory=SlowBatch, sizer=lambda r, slots: 1)
+    reqs = [_breq(0, 1, 20), _breq(1, 1, 3), _breq(2, 1, 3), _breq(3, 1, 3)]
+    reqs[3].deadline = 0.05            # one slot, busy with request 0 for ~0.2 s
+    try:
+        for r in reqs:
+            srv.submit(r)
+        time.sleep(0.02)
+        assert srv.cancel(0)           # in its slot: runs to the end, result discarded
+        assert srv.cancel(1)           # waiting for the slot: dropped
+        srv.wait(4)
+    finally:
+        srv.close()
+    res = srv.results
+    assert res[0].error == serving.CANCELLED and res[0].grad is None
+    assert res[1].error == serving.CANCELLED
+    assert res[2].error is None and res[2].gain == 2.0
+    assert res[3].error == serving.EXPIRED
