@@ -230,7 +230,9 @@ typedef struct {
  * update (entries beyond stats->iterations are left unchanged).  stats (host)
  * may be NULL.  Each trial point costs one checkpointed forward sweep;
  * accepted points add the reverse sweep.  Uses two more device fields of the
- * context and the projection factors on first call. */
+ * context and the projection factors on first call.  The loop keeps no state
+ * between calls besides u0: calling again with the returned u0 resumes it
+ * (the first iterate is then the last accepted one). */
 int pnop_optimise(pnop_ctx* ctx, void* u0, double E0, double horizon, int max_iter, double tol,
                   double* gain_history, pnop_opt_stats* stats);
 
