@@ -18,6 +18,8 @@ import pytest
 
 from paper_2509_10103_gb300 import synth
 
+from tests.test_oracle_pins import paper_numbers
+
 pytestmark = [pytest.mark.gpu, pytest.mark.slow,
               pytest.mark.skipif(os.environ.get("PNOP_VALIDATION") != "1", reason="set PNOP_VALIDATION=1")]
 
@@ -48,8 +50,9 @@ def test_linear_optimum_steady_pipe_re1750():
     energy_by_mode = [float((u[:, :, i, k].abs() ** 2).sum()) for i in range(2 * M + 1) for k in range(K + 1)]
     dominant = int(np.argmax(energy_by_mode))
     assert dominant // (K + 1) in (M - 1, M + 1) and dominant % (K + 1) == 0  # m = +-1, k = 0
-    assert abs(best / 219.0 - 1) < 0.02
-    assert abs(tbest - 85.05) < 2.0
+    P = paper_numbers()
+    assert abs(best / P["steady_re1750_lzpi_tau80_Gmax"] - 1) < 0.02
+    assert abs(tbest - P["steady_re1750_lzpi_tau80_tmax"]) < 2.0
     ctx.close()
 
 
@@ -80,6 +83,8 @@ def test_linear_optimum_pulsatile_wo2_peaks_at_0029T():
     e = ctx.pnop_mode_energy(u).sum(axis=0)
     e = e / e.sum()
     assert e[M - 1, 0] + e[M + 1, 0] > 0.99  # streamwise vortices: m = +-1, k = 0
-    assert abs(tbest - 90.0) < 3.0 and abs(tbest / T - 0.029) < 0.001
+    P = paper_numbers()
+    assert abs(tbest - P["wo2_re2000_a1_lz10_tpeak"]) < 3.0
+    assert abs(tbest / T - P["wo2_re2000_a1_lz10_tpeak_over_T"]) < 0.001
     assert stats["gain"] < best  # the growth goes on past the optimisation time
     ctx.close()

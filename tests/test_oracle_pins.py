@@ -438,3 +438,34 @@ def test_uniform_base_flow_only_translates_a_mode():
         gaps[nr] = np.abs(b - a * turn).max() / np.abs(a).max()
         assert np.abs(b - a * np.conj(turn)).max() / np.abs(a).max() > 0.5  # the other direction is far off
     assert gaps[24] < 1e-4 and gaps[12] > 10 * gaps[24]
+
+
+def paper_numbers():
+    """Key -> value of tests/golden/paper_appendix_a.txt (numbers the paper prints)."""
+    out = {}
+    with open(os.path.join(GOLDEN, "paper_appendix_a.txt")) as f:
+        for line in f:
+            if line.strip() and not line.startswith("#"):
+                key, val = line.split()[:2]
+                out[key] = float(val)
+    return out
+
+
+def test_printed_wo2_peak_fixes_the_time_unit():
+    """App. A.2 prints the Wo = 2 growth peak both as t ~ 90 and as 0.029 T.
+    With lengths in R and velocities in 2 U_bar the period is 2 pi Re / Wo^2
+    (= 3141.6 at Re = 2000, Wo = 2) and 0.029 T = 91; the formula printed in
+    the paper's introduction, pi Re / (2 Wo^2), would put the peak at 23.  The
+    library and the oracle take the first (design reading 1)."""
+    P = paper_numbers()
+    Re, Wo = 2000.0, 2.0
+    T_units = 2 * math.pi * Re / Wo ** 2
+    T_printed = math.pi * Re / (2 * Wo ** 2)
+    assert abs(P["wo2_re2000_a1_lz10_tpeak_over_T"] * T_units - P["wo2_re2000_a1_lz10_tpeak"]) < 2.0
+    assert abs(P["wo2_re2000_a1_lz10_tpeak_over_T"] * T_printed - P["wo2_re2000_a1_lz10_tpeak"]) > 50.0
+    o = po.Oracle(po.Params(nr=9, M=1, K=1, Lz=4.0, Re=Re, dt=0.01, Wo=Wo, A=1.0))
+    # the oracle's base flow repeats after T_units: the bulk velocity u_b(t) = (1 + A sin(2 pi t / T)) / 2
+    U0, _ = o.base(0.3)
+    U1, _ = o.base(0.3 + T_units)
+    Uh, _ = o.base(0.3 + 0.5 * T_units)
+    assert np.abs(U1 - U0).max() < 1e-12 and np.abs(Uh - U0).max() > 1e-2  # T is the period, not a multiple
