@@ -127,14 +127,14 @@ __device__ __forceinline__ void base_at(const Geo& g, int slot, int j, double c,
 }
 
 // U and dU/dr at the block's radius and batch entry (a spectral block covers
-// one j of one entry), at that entry's phase ph: one thread evaluates them and
+// one j of one entry), at that entry's phase g.cs[b]: one thread evaluates them and
 // the block shares the pair, instead of every thread repeating the same FP64
 // arithmetic.  Called by all threads of the block before any of them returns.
-__device__ __forceinline__ void base_block(const Geo& g, int ph, double& U, double& dU) {
+__device__ __forceinline__ void base_block(const Geo& g, double& U, double& dU) {
     __shared__ double sh[2];
     if (threadIdx.x == 0) {
         const int b = blockIdx.z / g.nr, j = blockIdx.z - b * g.nr;
-        const double2 cs = g.cs[ph][b];
+        const double2 cs = g.cs[b];
         base_at(g, g.slot[b], j, cs.x, cs.y, sh[0], sh[1]);
     }
     __syncthreads();
@@ -147,9 +147,9 @@ __device__ __forceinline__ void base_block(const Geo& g, int ph, double& U, doub
 // grad(U u_z), which the discrete pressure projection does not remove exactly;
 // the remainder couples u_z back into (u_r, u_theta) and makes k = 0 modes of
 // steady pipe flow grow at high Re.
-__global__ void k_base(Geo g, const double2* __restrict__ u, double2* __restrict__ N, int ph) {
+__global__ void k_base(Geo g, const double2* __restrict__ u, double2* __restrict__ N) {
     double U, dU;
-    base_block(g, ph, U, dU);
+    base_block(g, U, dU);
     Idx d;
     if (!decode(g, d)) return;
     u += d.off;
@@ -163,9 +163,9 @@ __global__ void k_base(Geo g, const double2* __restrict__ u, double2* __restrict
 }
 
 // transpose (Euclidean cotangents): ub = conj(-i a) nb = i a nb; ub_r -= dU nb_z
-__global__ void k_baseT(Geo g, const double2* __restrict__ nb, double2* __restrict__ ub, int ph) {
+__global__ void k_baseT(Geo g, const double2* __restrict__ nb, double2* __restrict__ ub) {
     double U, dU;
-    base_block(g, ph, U, dU);
+    base_block(g, U, dU);
     Idx d;
     if (!decode(g, d)) return;
     nb += d.off;
@@ -200,9 +200,9 @@ __global__ void k_grad_u(Geo g, const double2* __restrict__ u, double2* __restri
 }
 
 // Base-flow part of the continuous-adjoint forcing: N = U dw/dz - w_z dU/dr e_r
-__global__ void k_base_adj(Geo g, const double2* __restrict__ w, double2* __restrict__ N, int ph) {
+__global__ void k_base_adj(Geo g, const double2* __restrict__ w, double2* __restrict__ N) {
     double U, dU;
-    base_block(g, ph, U, dU);
+    base_block(g, U, dU);
     Idx d;
     if (!decode(g, d)) return;
     w += d.off;
@@ -901,16 +901,16 @@ void launch_grad_u(const Geo& g, const double2* u, double2* G, cudaStream_t s) {
     k_grad_u<<<spec_grid(g), spec_bx(g), 0, s>>>(g, u, G);
     check_launch("grad_u");
 }
-void launch_base_adj(const Geo& g, const double2* w, double2* N, int ph, cudaStream_t s) {
-    k_base_adj<<<spec_grid(g), spec_bx(g), 0, s>>>(g, w, N, ph);
+void launch_base_adj(const Geo& g, const double2* w, double2* N, cudaStream_t s) {
+    k_base_adj<<<spec_grid(g), spec_bx(g), 0, s>>>(g, w, N);
     check_launch("base_adj");
 }
-void launch_base(const Geo& g, const double2* u, double2* N, int ph, cudaStream_t s) {
-    k_base<<<spec_grid(g), spec_bx(g), 0, s>>>(g, u, N, ph);
+void launch_base(const Geo& g, const double2* u, double2* N, cudaStream_t s) {
+    k_base<<<spec_grid(g), spec_bx(g), 0, s>>>(g, u, N);
     check_launch("base");
 }
-void launch_baseT(const Geo& g, const double2* nb, double2* ub, int ph, cudaStream_t s) {
-    k_baseT<<<spec_grid(g), spec_bx(g), 0, s>>>(g, nb, ub, ph);
+void launch_baseT(const Geo& g, const double2* nb, double2* ub, cudaStream_t s) {
+    k_baseT<<<spec_grid(g), spec_bx(g), 0, s>>>(g, nb, ub);
     check_launch("baseT");
 }
 

@@ -51,7 +51,7 @@ struct Geo {
     size_t sLb, sFacH, sInfl, sNr, sNk;
     double inv_2re[kMaxBatch];   // 1 / (2 Re) per slot
     double flux_inv[kMaxBatch];  // flux normalisation per slot
-    double2 cs[2][kMaxBatch];    // (cos, sin) of the pulsation phase of entry b at the step's two stage times
+    double2 cs[kMaxBatch];       // (cos, sin) of the pulsation phase of entry b at the launch's time
 };
 
 // Up to 18 input / 6 output spectral component planes for the transforms; the
@@ -91,12 +91,12 @@ void launch_curlT_acc(const Geo& g, const double2* wb, double2* ub, cudaStream_t
 // derivative direction), and the base-flow part of its forcing
 // Nb = U dw/dz - w_z dU/dr e_r (written)
 void launch_grad_u(const Geo& g, const double2* u, double2* G, cudaStream_t s);
-void launch_base_adj(const Geo& g, const double2* w, double2* N, int ph, cudaStream_t s);
+void launch_base_adj(const Geo& g, const double2* w, double2* N, cudaStream_t s);
 // base-flow terms in advective form: N = -U du/dz - u_r dU/dr e_z, and their
 // transpose ub = (dN/du)^T nb (both written, not accumulated), at the phase
-// g.cs[ph][b] of each batch entry
-void launch_base(const Geo& g, const double2* u, double2* N, int ph, cudaStream_t s);
-void launch_baseT(const Geo& g, const double2* nb, double2* ub, int ph, cudaStream_t s);
+// g.cs[b] of each batch entry
+void launch_base(const Geo& g, const double2* u, double2* N, cudaStream_t s);
+void launch_baseT(const Geo& g, const double2* nb, double2* ub, cudaStream_t s);
 
 // ---- transforms (T = double for FP64, float for mixed) ----
 template <class T2>

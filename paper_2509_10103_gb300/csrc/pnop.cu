@@ -468,7 +468,7 @@ void transforms(pnop_ctx* c, const pnop::FieldPtrs& f, int nin, int nout, int zm
 }
 
 // ------------------------------------------------------------------ nonlinear term
-// Pulsation phase (cos, sin of omega t) of every batch entry into geo.cs[0]
+// Pulsation phase (cos, sin of omega t) of every batch entry into geo.cs
 // for the next launches.  A single-request context takes t itself; a batched
 // context reads t as a step offset (0: the entry's step start, 1: its end)
 // and adds it to the entry's own start time with its own dt and omega.
@@ -476,13 +476,13 @@ void set_phase(pnop_ctx* c, double t) {
     Geo& g = c->geo;
     if (!c->batched) {
         const double ph = c->h.omega * t;
-        g.cs[0][0] = make_double2(std::cos(ph), std::sin(ph));
+        g.cs[0] = make_double2(std::cos(ph), std::sin(ph));
         return;
     }
     for (int b = 0; b < g.nb; ++b) {
         const BatchReq& r = c->breq[g.slot[b]];
         const double ph = r.omega * (c->bt[b] + t * r.dt);
-        g.cs[0][b] = make_double2(std::cos(ph), std::sin(ph));
+        g.cs[b] = make_double2(std::cos(ph), std::sin(ph));
     }
 }
 
@@ -490,7 +490,7 @@ void set_phase(pnop_ctx* c, double t) {
 // has forked it); the analysis of the transforms adds them after ev_base.
 void queue_base(pnop_ctx* c, const double2* u, double t) {
     set_phase(c, t);
-    run(c, PNOP_K_SPECTRAL, 1, flops::base * c->S(), [&] { pnop::launch_base(c->geo, u, c->Nbase, 0, c->side); },
+    run(c, PNOP_K_SPECTRAL, 1, flops::base * c->S(), [&] { pnop::launch_base(c->geo, u, c->Nbase, c->side); },
         c->side);
     ck(cudaEventRecord(c->ev_base, c->side), "record");
 }
@@ -533,7 +533,7 @@ void nonlinearT(pnop_ctx* c, const double2* u, double t, const double2* nb, doub
     cudaStream_t s = c->stream;
     fork_side(c);
     set_phase(c, t);
-    run(c, PNOP_K_SPECTRAL, 1, flops::base * S, [&] { pnop::launch_baseT(g, nb, c->Nbase, 0, c->side); }, c->side);
+    run(c, PNOP_K_SPECTRAL, 1, flops::base * S, [&] { pnop::launch_baseT(g, nb, c->Nbase, c->side); }, c->side);
     ck(cudaEventRecord(c->ev_base, c->side), "record");
     if (!cached) run(c, PNOP_K_SPECTRAL, 1, flops::curl * S, [&] { pnop::launch_curl(g, u, c->omega, s); });
     pnop::FieldPtrs f{};
@@ -569,7 +569,7 @@ void nonlinearT(pnop_ctx* c, const double2* u, double t, const double2* nb, doub
 // base_queued), added by the analysis.
 void queue_base_adj(pnop_ctx* c, const double2* w, double t) {
     set_phase(c, t);
-    run(c, PNOP_K_SPECTRAL, 1, flops::base * c->S(), [&] { pnop::launch_base_adj(c->geo, w, c->Nbase, 0, c->side); },
+    run(c, PNOP_K_SPECTRAL, 1, flops::base * c->S(), [&] { pnop::launch_base_adj(c->geo, w, c->Nbase, c->side); },
         c->side);
     ck(cudaEventRecord(c->ev_base, c->side), "record");
 }
