@@ -667,28 +667,41 @@ def main():
         "gpu_launches": launches,
         "clocks": mix["clocks"],
     }
+
+    def extra(key, fn):
+        """A secondary report: its failure is recorded under its key and never costs the main line."""
+        try:
+            out[key] = fn()
+        except Exception as e:  # noqa: BLE001 - reported in the JSON line
+            out[key] = {"error": f"{type(e).__name__}: {e}"[:500]}
+
     if ws == 1 and not args.no_extras:
-        out["single_step"] = {"mixed": time_single_steps(L, torch, L.PNOP_MIXED),
-                              "fp64": time_single_steps(L, torch, L.PNOP_FP64)}
-        out["budget_sweep_mixed"] = budget_sweep(L, torch, L.PNOP_MIXED, H)
-        out["host_tier_mixed"] = host_tier_report(L, torch, L.PNOP_MIXED, H)
-        out["continuous_adjoint_mixed"] = continuous_adjoint_report(L, torch, L.PNOP_MIXED, H, s)
-    if ws == 1 and not args.no_extras:
-        out["batched_gradients"] = batch_report(L, torch)
+        extra("single_step", lambda: {"mixed": time_single_steps(L, torch, L.PNOP_MIXED),
+                                      "fp64": time_single_steps(L, torch, L.PNOP_FP64)})
+        extra("budget_sweep_mixed", lambda: budget_sweep(L, torch, L.PNOP_MIXED, H))
+        extra("host_tier_mixed", lambda: host_tier_report(L, torch, L.PNOP_MIXED, H))
+        extra("continuous_adjoint_mixed", lambda: continuous_adjoint_report(L, torch, L.PNOP_MIXED, H, s))
+        extra("batched_gradients", lambda: batch_report(L, torch))
     if not args.no_serving and ws == 1:
-        out["serving"] = serving_report(L)
-        out["serving_batched"] = serving_report(L, batched=True)
+        extra("serving", lambda: serving_report(L))
+        extra("serving_batched", lambda: serving_report(L, batched=True))
     if not args.no_cpu_baseline and ws == 1:
         planes, modes = 16, 64
-        smp = oracle_sample(planes, modes)
-        out["cpu_baseline"] = {"value": 1.0 / smp["per_step_s"], "unit": "steps/s", "cores": 1, "kind": "oracle",
-                               "sample": oracle_sample_desc(planes, modes)}
-        if not args.no_extras:
+
+        def one_core():
+            smp = oracle_sample(planes, modes)
+            return {"value": 1.0 / smp["per_step_s"], "unit": "steps/s", "cores": 1, "kind": "oracle",
+                    "sample": oracle_sample_desc(planes, modes)}
+
+        def all_cores():
             procs, per_step = oracle_sample_parallel(planes, modes)
             # every process extrapolates one step from its share of the cores
-            out["cpu_baseline_all_cores"] = {
-                "value": sum(1.0 / x for x in per_step), "unit": "steps/s", "cores": procs, "kind": "oracle",
-                "sample": oracle_sample_desc(planes, modes) + f"; {procs} such samples at once, one per core"}
+            return {"value": sum(1.0 / x for x in per_step), "unit": "steps/s", "cores": procs, "kind": "oracle",
+                    "sample": oracle_sample_desc(planes, modes) + f"; {procs} such samples at once, one per core"}
+
+        extra("cpu_baseline", one_core)
+        if not args.no_extras:
+            extra("cpu_baseline_all_cores", all_cores)
     print(json.dumps(out))
     return 0
 
