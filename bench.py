@@ -16,7 +16,8 @@ mixed path (FP32 transforms and products, FP64 radial solves and inner
 products) as `value`, and for the plain FP64 path under "fp64".
 
 --impl reference times the FP64 CPU oracle on a bounded sample of the same
-workload on the host cores (the baseline of this build).
+workload on the host cores (the oracle is the reference arm: the method has
+no other implementation to run).
 """
 from __future__ import annotations
 
