@@ -5,7 +5,9 @@
 // Spectral fields are FP64 complex, layout [c][j][m + M][k].  Everything here
 // is FP64: the curl and base-flow terms, and everything radial (banded
 // matvecs, banded LU solves, influence and flux corrections).  The theta/z
-// transforms are in transforms.cu.
+// transforms are in transforms.cu.  Every kernel also serves batched launches:
+// it finds its batch entry in one grid dimension and offsets its field
+// pointers and per-request tables by that entry's slot (see Geo).
 #include "dev_common.cuh"
 #include "kernels.hpp"
 

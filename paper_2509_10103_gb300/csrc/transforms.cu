@@ -1,7 +1,9 @@
 // Spectral <-> physical transforms of the pseudo-spectral pipe-flow step
 // (Keuchel & Avila, Section 2.4): theta synthesis, the z pass with the
 // pointwise products of the nonlinear term, theta analysis.  3/2-padded grids,
-// hand-written shared-memory FFTs templated on FP64 or FP32.
+// hand-written shared-memory FFTs templated on FP64 or FP32.  Batched launches
+// carry the batch entry in the grid's z dimension (with the field index for
+// the theta kernels) and offset spectral and physical buffers by its slot.
 #include "dev_common.cuh"
 #include "kernels.hpp"
 
