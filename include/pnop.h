@@ -337,8 +337,8 @@ int pnop_revolve_counts(int nsteps, int snaps, long long* advances, long long* s
  * synchronise the device and stall other streams.  Such callers cannot create
  * a context, so none is needed: pass the field u (device, layout above, nr,
  * M, K as for a context), the radial quadrature weights W (device, nr
- * doubles: sum_j W_j f(r_j) = int_0^1 f r dr, the same weights as the
- * context's inner product, Eq. 2.2) and the pipe length Lz; *E_out (host)
+ * doubles: sum_j W_j f(r_j) = int_0^1 f r dr, the same radial quadrature as
+ * the context's inner product uses) and the pipe length Lz; *E_out (host)
  * receives (1/2) <u, u>, as pnop_energy would.  The work is ordered on
  * cuda_stream (NULL = legacy default stream) and the call synchronises it.
  *
@@ -348,7 +348,10 @@ int pnop_revolve_counts(int nsteps, int snaps, long long* advances, long long* s
  * array's device address (with the device current) and should therefore come
  * before any stream capture on that device.  All calls share the array:
  * calls whose device work overlaps (concurrent streams or host threads)
- * race on it and must be serialised by the caller.  Each call clears the part it uses before writing.
+ * race on it and must be serialised by the caller.  Each call writes every
+ * part of the array it reads before reading it, so nothing a previous call left
+ * there reaches the result.  The cached address is only valid while the
+ * device's primary context lives: do not call cudaDeviceReset between calls.
  *
  * Limits and errors: 3 * nr * (2M+1) * (K+1) may be at most
  * PNOP_NOALLOC_MAX_VALUES complex values; larger fields, NULL pointers or bad

@@ -78,6 +78,9 @@ __global__ void k_energy_final_noalloc(double* __restrict__ scratch, int nb, dou
 
 // Resolves (once per device, with that device current) the device address of
 // the scratch array; host code may not use the symbol itself as an address.
+// The address is cached for the life of the process: a cudaDeviceReset (or a
+// reset of the primary context) unloads the module, after which the cached
+// address is stale, so callers of this entry point must not reset the device.
 int scratch_for_current_device(double** out) {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return PNOP_ERR_CUDA;
@@ -99,18 +102,21 @@ int scratch_for_current_device(double** out) {
 extern "C" int pnop_energy_noalloc(const void* u, const double* W, int nr, int M, int K, double Lz, double* E_out,
                                    void* cuda_stream) {
     if (!u || !W || !E_out || nr < 1 || M < 0 || K < 0 || !(Lz > 0)) return PNOP_ERR_INVALID_ARG;
-    const long long n = 3LL * nr * (2LL * M + 1) * (K + 1);
-    if (n > PNOP_NOALLOC_MAX_VALUES) return PNOP_ERR_INVALID_ARG;  // larger than the fixed scratch serves
+    // 3 nr (2M+1) (K+1) <= max, checked one factor at a time so that no
+    // product can overflow before the comparison
+    const long long cap = PNOP_NOALLOC_MAX_VALUES;
+    const long long f1 = 3LL * nr, f2 = 2LL * M + 1, f3 = (long long)K + 1;
+    if (f1 > cap || f2 > cap / f1 || f3 > cap / (f1 * f2)) return PNOP_ERR_INVALID_ARG;
+    const long long n = f1 * f2 * f3;
     double* scratch = nullptr;
     int rc = scratch_for_current_device(&scratch);
     if (rc != PNOP_OK) return rc;
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
     const int nb = (int)((n + kPerBlock - 1) / kPerBlock);
-    // clear the partials this call reads and the result slot (the array keeps
-    // whatever the previous call left there)
-    if (cudaMemsetAsync(scratch, 0, (size_t)nb * sizeof(double), s) != cudaSuccess ||
-        cudaMemsetAsync(scratch + kMaxBlocks, 0, sizeof(double), s) != cudaSuccess)
-        return PNOP_ERR_CUDA;
+    // The array keeps whatever the previous call left there.  Nothing needs
+    // clearing: block b of the first kernel writes partial b for every b < nb,
+    // the second kernel reads exactly those nb partials and writes the result
+    // slot, and the copy below reads that slot after it in stream order.
     k_energy_partial_noalloc<<<nb, kThreads, 0, s>>>(static_cast<const double2*>(u), W, nr, 2 * M + 1, K + 1, n,
                                                      scratch);
     k_energy_final_noalloc<<<1, 1024, 0, s>>>(scratch, nb, 0.5 * 2.0 * M_PI * Lz);

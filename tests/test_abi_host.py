@@ -156,3 +156,24 @@ def test_batch_bytes_estimate_grows_with_capacity_and_checkpoints(L):
     for cap, snaps in ((0, 8), (17, 8), (2, 0)):
         p = L.pnop_params(1.0, 1.0, 0.0, 1.0, 0.0, 1, snaps, 0)
         assert L.lib.pnop_batch_bytes(ctypes.byref(g), ctypes.byref(p), cap, ctypes.byref(out)) == -1
+
+
+def test_noalloc_energy_rejects_oversized_fields_without_a_device(L):
+    """pnop_energy_noalloc checks 3 nr (2M+1) (K+1) against its fixed scratch
+    before any CUDA call, one factor at a time, so sizes whose product would
+    overflow 64 bits are rejected too.  Non-null dummy pointers are never
+    dereferenced on these paths."""
+    import ctypes
+    dummy = ctypes.c_void_p(16)
+    e = ctypes.c_double()
+    INT_MAX = 2 ** 31 - 1
+    cases = [
+        (INT_MAX, INT_MAX // 2, INT_MAX - 1),      # product far beyond 2^63
+        (INT_MAX, 0, 0),                           # first factor alone too large
+        (64, 0, 87381),                            # 3*64*87382 = 2^24 + 128: one step past the limit
+        (512, 127, 255),
+    ]
+    for nr, M, K in cases:
+        rc = L.lib.pnop_energy_noalloc(dummy, ctypes.cast(dummy, ctypes.POINTER(ctypes.c_double)), nr, M, K, 10.0,
+                                       ctypes.byref(e), None)
+        assert rc == -1, (nr, M, K)

@@ -65,3 +65,26 @@ def test_noalloc_energy_rejects_fields_beyond_its_scratch(L):
     with pytest.raises(L.PnopError) as e:
         L.pnop_energy_noalloc(u, W, 512, 127, 255, 10.0)
     assert e.value.code == -1
+
+
+def test_noalloc_energy_at_its_largest_size_on_a_side_stream(L):
+    # 3 * 64 * 1 * 87381 = 2^24 - 64 complex values: the largest field of this
+    # shape the fixed scratch serves (one more k is rejected, see the host
+    # ABI tests), reduced on a non-default stream and checked against numpy
+    import torch
+    nr, M, K, Lz = 64, 0, 87380, 7.0
+    gen = torch.Generator(device="cpu").manual_seed(11)
+    u_h = torch.randn((3, nr, 2 * M + 1, K + 1, 2), generator=gen, dtype=torch.float64)
+    W_h = torch.rand(nr, generator=gen, dtype=torch.float64) + 0.1
+    uc = u_h[..., 0].numpy() + 1j * u_h[..., 1].numpy()
+    ck = np.full(K + 1, 2.0)
+    ck[0] = 1.0
+    ref = 0.5 * 2 * np.pi * Lz * np.sum(W_h.numpy()[None, :, None, None] * ck * np.abs(uc) ** 2)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        u = torch.view_as_complex(u_h.to("cuda", non_blocking=False)).contiguous()
+        W = W_h.to("cuda")
+    s.synchronize()
+    for _ in range(2):
+        e = L.pnop_energy_noalloc(u, W, nr, M, K, Lz, stream=s.cuda_stream)
+        assert abs(e / ref - 1) < TOL
