@@ -94,21 +94,42 @@ def class_work(cls, units, mixed):
         return units * fl, units * (nin + nout) * (K + 1) * cz
     if cls in ("radial_band", "spectral"):  # the library counts algorithmic FP64 flops as units
         return units, None
-    if cls == "radial_solve":  # one system: nr rows, 4 + up to 8 off-diagonals + scale, complex rhs
-        fl = NR * (4 + 8 + 1) * 4.0
-        by = NR * (13 * 8 + 4 * 16)
+    if cls == "radial_solve":
+        # one banded system with a real matrix and a complex right-hand side:
+        # nonzeros of the factors are 4 nr - 10 below the diagonal (4 per row,
+        # fewer in rows 0..3) and 4 nr + 6 above it (8 in the wall rows 0..3,
+        # 4 in the interior, fewer in the last rows), plus one scaling by the
+        # inverse diagonal per row: 8 nr - 4 FMAs and nr multiplies per real part
+        fl = 2.0 * (2.0 * (8 * NR - 4) + NR)
+        by = NR * (13 * 8 + 2 * 16)  # factor rows (stored band) + read and write of the complex value
         return units * fl, units * by
     return None, None
 
 
+KERNEL_SOURCES = ("kernels.cu", "transforms.cu", "kernels.hpp", "dev_common.cuh")
+
+
+def kernel_digest():
+    """Digest of the kernel sources, recorded beside every committed ncu traffic figure."""
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2509_10103_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
 def traffic_table():
-    """Measured DRAM bytes per launch from the committed ncu summaries."""
+    """DRAM bytes per launch from the committed ncu capture, per (class,
+    precision), kept only when the capture was taken of the kernel sources as
+    they are now (its digest matches): a figure of an older kernel is null."""
     out = {}
     p = os.path.join(ROOT, "profiles", "dram_traffic_per_launch.txt")
     if os.path.exists(p):
+        dig = kernel_digest()
         for line in open(p):
             parts = line.split()
-            if len(parts) == 4 and parts[0] == "traffic":
+            if len(parts) == 5 and parts[0] == "traffic" and parts[4] == dig:
                 out[(parts[1], parts[2])] = float(parts[3])
     return out
 
@@ -200,7 +221,8 @@ def aggregate_value(horizon_steps, steps, ws, ms_max):
 
 
 # ------------------------------------------------------------------ GPU arm
-def time_gradient(L, torch, precision, steps, warmup, H, snaps, ws, rank, sampler=None, host_slots=0):
+def time_gradient(L, torch, precision, steps, warmup, H, snaps, ws, rank, sampler=None, host_slots=0,
+                  profile_pass=True):
     ctx = L.Context(NR, NTHETA, NZ, LZ, RE, DT, WO, AMP, TAU0, precision, snaps)
     if host_slots:
         ctx.pnop_set_host_tier(host_slots, -1.0)  # io ratio measured on this device
@@ -216,7 +238,8 @@ def time_gradient(L, torch, precision, steps, warmup, H, snaps, ws, rank, sample
     for _ in range(max(0, warmup - 1)):
         gain = ctx.pnop_gradient(u0, E0, horizon, g)
     dom = max(prof, key=lambda k: prof[k][0])
-    ctx.pnop_profile(1 << L.KCLASSES.index(dom))
+    # the timed region runs with per-launch event timing off (counters only)
+    ctx.pnop_profile(0)
     barrier(ws)
     torch.cuda.synchronize()
     if sampler:
@@ -230,11 +253,22 @@ def time_gradient(L, torch, precision, steps, warmup, H, snaps, ws, rank, sample
     clocks = sampler.stop() if sampler else None
     barrier(ws)
     ms = e0.elapsed_time(e1)
-    tprof = ctx.pnop_profile_read()
+    counts = ctx.pnop_profile_read()
+    # the same steps once more with CUDA events around every launch of the
+    # dominant class, on the stream each launch goes to: its average launch
+    # duration for the roofline (this pass is not part of `value`)
+    tprof = None
+    if profile_pass:
+        ctx.pnop_profile(1 << L.KCLASSES.index(dom))
+        for _ in range(steps):
+            ctx.pnop_gradient(u0, E0, horizon, g)
+        torch.cuda.synchronize()
+        tprof = ctx.pnop_profile_read()
     adv, nadj, stores = ctx.pnop_gradient_stats()
     host = ctx.pnop_host_tier_stats() if host_slots else None
     ctx.close()
-    return {"ms": ms, "gain": gain, "warm_profile": prof, "timed_profile": tprof, "dominant": dom,
+    return {"ms": ms, "gain": gain, "warm_profile": prof, "timed_profile": tprof, "timed_counts": counts,
+            "dominant": dom,
             "advances": adv, "adjoint_steps": nadj, "stores": stores, "clocks": clocks, "host": host}
 
 
@@ -269,7 +303,7 @@ def budget_sweep(L, torch, precision, H, budgets=(10, 57, 100), steps=2):
     """fwd+adj steps/s of the same gradient at several checkpoint budgets (recompute vs store)."""
     out = {}
     for s in budgets:
-        res = time_gradient(L, torch, precision, steps, 1, H, s, 1, 0, None)
+        res = time_gradient(L, torch, precision, steps, 1, H, s, 1, 0, None, profile_pass=False)
         out[str(s)] = {"steps_per_s": H * steps / (res["ms"] / 1e3), "advances": res["advances"]}
     return out
 
@@ -306,7 +340,7 @@ def continuous_adjoint_report(L, torch, precision, H, snaps, steps=2):
 def host_tier_report(L, torch, precision, H, snaps=10, steps=2):
     """The same gradient with `snaps` HBM checkpoint slots plus up to H - 1 pinned
     host slots (two-level schedule, Eq. 2.21, io ratio measured)."""
-    res = time_gradient(L, torch, precision, steps, 1, H, snaps, 1, 0, None, host_slots=H - 1)
+    res = time_gradient(L, torch, precision, steps, 1, H, snaps, 1, 0, None, host_slots=H - 1, profile_pass=False)
     return {"hbm_slots": snaps, "max_host_slots": H - 1, "steps_per_s": H * steps / (res["ms"] / 1e3),
             "advances": res["advances"], **res["host"]}
 
@@ -329,7 +363,11 @@ def time_e2e(L, torch, precision, steps, warmup, H, snaps):
     return s
 
 
-def roofline(L, res, mixed, peaks, pk_src):
+def roofline(L, res, mixed, peaks, pk_src, alu_measured=None):
+    """Roofline of the dominant class.  alu_measured: {"fp64": T, "fp32": T}
+    from the library's FMA probe on this device (TFLOP/s); the ALU peak is
+    the measured figure when given, the derived one (SMs x lanes x clock)
+    otherwise, and both are reported."""
     cls = res["dominant"]
     ms, launches, units = res["timed_profile"][cls]
     fl, by = class_work(cls, units, mixed)
@@ -337,8 +375,11 @@ def roofline(L, res, mixed, peaks, pk_src):
     smx = peaks.get("sm_max_mhz", 2070.0)
     if fl is None or launches == 0 or ms <= 0:
         return None
-    fp_peak = alu_peak_tflops(FP32_FLOPS_PER_CLK_SM if (mixed and cls not in ("radial_solve", "radial_band", "spectral")) else
-                              FP64_FLOPS_PER_CLK_SM, smx)
+    fp32 = mixed and cls not in ("radial_solve", "radial_band", "spectral")
+    per_clk = FP32_FLOPS_PER_CLK_SM if fp32 else FP64_FLOPS_PER_CLK_SM
+    derived = alu_peak_tflops(per_clk, smx)
+    meas = (alu_measured or {}).get("fp32" if fp32 else "fp64")
+    fp_peak = meas if meas else derived
     t = ms / 1e3
     ach_f = fl / t / 1e12
     ach_b = by / t / 1e9 if by is not None else None
@@ -346,10 +387,14 @@ def roofline(L, res, mixed, peaks, pk_src):
     frac_b = ach_b / hbm if by is not None else 0.0
     tt = traffic_table().get((cls, "mixed" if mixed else "fp64"))
     base = {"kernel": cls, "launches": launches, "avg_launch_us": ms * 1e3 / launches,
-            "traffic": tt}
+            "traffic": tt,
+            "traffic_note": "ncu DRAM bytes per launch of the current kernel sources (profiles/), null when the"
+                            " committed capture predates them"}
     if frac_f >= frac_b:
+        src = (f"measured: {'FP32' if fp32 else 'FP64'} FMA probe pnop_measure_fma_peak on this GPU" if meas else
+               f"derived: {N_SM} SMs x {per_clk} flop/clk x {smx:g} MHz")
         base.update({"bound": "alu", "achieved": ach_f, "peak": fp_peak, "unit": "TFLOP/s", "frac": frac_f,
-                     "peak_source": f"derived: {N_SM} SMs x {FP32_FLOPS_PER_CLK_SM if fp_peak > 10 else FP64_FLOPS_PER_CLK_SM} flop/clk x {smx:g} MHz"})
+                     "peak_source": src, "peak_derived": derived, "frac_of_derived": ach_f / derived})
         if by is not None:
             base["hbm_frac"] = frac_b
         elif tt:  # the class counts flops only: its HBM use from the measured DRAM traffic per launch
@@ -557,7 +602,8 @@ def oracle_sample_parallel(planes=16, modes=64, procs=None):
 
 
 def oracle_sample_desc(planes, modes):
-    return (f"FP64 numpy oracle, 1 thread: curl + 3/2-padded transforms/products on {planes} of {NR} radial planes"
+    return (f"extrapolated from a bounded sample: "
+            f"FP64 numpy oracle, 1 thread: curl + 3/2-padded transforms/products on {planes} of {NR} radial planes"
             f" (x{NR // planes}), stage maps applied on {modes} random (m,k) modes (x{(2 * M + 1) * (K + 1) // modes}),"
             f" combined as 3 N + 2 N^T + 3 S + 2 S^T per fwd+adj step (store-all sweep); map construction excluded")
 
@@ -628,6 +674,7 @@ def main():
         print(json.dumps(batch_report(L, torch, only=res)))
         return 0
     peaks, pk_src = load_peaks()
+    alu = {"fp64": L.pnop_measure_fma_peak(L.PNOP_FP64, 0.05), "fp32": L.pnop_measure_fma_peak(L.PNOP_MIXED, 0.05)}
     H, s = args.horizon_steps, args.snaps
     sampler = ClockSampler(local) if rank == 0 else None
     if args.precision == "fp64":
@@ -641,13 +688,13 @@ def main():
         f = time_gradient(L, torch, L.PNOP_FP64, args.steps, args.warmup, H, s, ws, rank, None)
         fms = max_over_ranks(f["ms"], ws)
         fp64 = {"value": H * args.steps * ws / (fms / 1e3), "unit": "steps/s", "ms_per_step": fms / args.steps,
-                "gain": f["gain"], "dtype": "f64", "roofline": roofline(L, f, False, peaks, pk_src),
+                "gain": f["gain"], "dtype": "f64", "roofline": roofline(L, f, False, peaks, pk_src, alu),
                 "kernels_ms_per_step": {k: v[0] for k, v in f["warm_profile"].items()}}
     e2e_s = time_e2e(L, torch, main_prec, args.steps, args.warmup, H, s)
     e2e_s = max_over_ranks(e2e_s, ws)
     if rank != 0:
         return 0
-    launches = sum(v[1] for v in mix["timed_profile"].values())
+    launches = sum(v[1] for v in mix["timed_counts"].values())
     out = {
         "metric": "fwd+adj steps/s at 64x64x256, mixed vs FP64 on 1 GB300; serving p50/p99 latency",
         "value": value, "unit": "steps/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
@@ -659,7 +706,8 @@ def main():
                    "l2": f"inputs and working set > L2 (state {FIELD_BYTES / 2**20:.1f} MiB x >20 buffers + transform"
                          " scratch); no flush"},
         "gain": mix["gain"],
-        "roofline": roofline(L, mix, main_prec == L.PNOP_MIXED, peaks, pk_src),
+        "roofline": roofline(L, mix, main_prec == L.PNOP_MIXED, peaks, pk_src, alu),
+        "alu_peaks_measured_tflops": alu,
         "kernels_ms_per_step": {k: v[0] for k, v in mix["warm_profile"].items()},
         "fp64": fp64,
         "speedup_mixed_over_fp64": (value / fp64["value"]) if fp64 else None,

@@ -203,6 +203,20 @@ int pnop_two_level_counts(long long nsteps, int snaps, long long max_host_slots,
  * energy traces. */
 int pnop_mode_energy(pnop_ctx* ctx, const void* u, double* spectrum);
 
+/* Resolution measures of Section 2.4, reduced on the device from the field u
+ * (device, layout above): *e_M = the energy of the highest azimuthal mode
+ * m = M summed over the full axial spectrum k = -K..K, and *e_K = the energy
+ * of the highest axial mode k = K summed over m = -M..M, each over E0 (the
+ * paper keeps both below 1e-8 when it chooses M and K).  The printed formulas
+ * are garbled (their prefactors and the summation index of e_K); this reads
+ * them as energy fractions of those mode shells, with the energy of Eq. 2.1.
+ * The full-spectrum energies follow from the stored half by the Hermitian
+ * symmetry f(-m, -k) = conj f(m, k).  E0 <= 0 takes the energy of u itself.
+ * Host outputs; the call synchronises the context's stream.  Single-request
+ * contexts only.  Errors: PNOP_ERR_INVALID_ARG for NULL pointers or a
+ * non-finite E0, PNOP_ERR_NONFINITE when the result is not finite. */
+int pnop_resolution(pnop_ctx* ctx, const void* u, double E0, double* e_M, double* e_K);
+
 /* Counters and result of pnop_optimise. */
 typedef struct {
     int iterations;    /* accepted updates */
@@ -308,6 +322,18 @@ enum {
  * class_mask = 0 counts launches without timing. */
 int pnop_profile(pnop_ctx* ctx, unsigned class_mask);
 
+/* Measured fused-multiply-add throughput of the current device, in TFLOP/s
+ * (2 flops per FMA): precision PNOP_FP64 times FP64 FMAs, PNOP_MIXED FP32
+ * FMAs.  This is the denominator of the ALU roofline of the library's
+ * FP64-bound kernels (the paper gives no performance figures; this is a
+ * measurement utility).  Every SM runs independent FMA chains for about
+ * `seconds` (0 < seconds <= 10) per launch; the best of three launches is
+ * returned in *tflops (host).  The work is ordered on cuda_stream (NULL =
+ * legacy default stream) and the call synchronises it.  No device memory is
+ * allocated.  Bad arguments return PNOP_ERR_INVALID_ARG, CUDA failures
+ * PNOP_ERR_CUDA. */
+int pnop_measure_fma_peak(int precision, double seconds, void* cuda_stream, double* tflops);
+
 /* Read the counters since pnop_profile: per class device milliseconds (timed
  * classes only), kernel launches and work units (arrays of PNOP_K_NCLASS;
  * any may be NULL).  Synchronises the stream. */
@@ -323,6 +349,14 @@ int pnop_inner(pnop_ctx* ctx, const void* a, const void* b, double* out);
  * checkpoint slots (an upper estimate, for admission control by an HBM
  * budget).  Host only; needs no device. */
 int pnop_context_bytes(const pnop_grid* grid, const pnop_params* params, int snaps, size_t* bytes);
+
+/* Device bytes the context holds right now (operators, workspace, checkpoint
+ * slots, host-tier staging; buffers allocated on first use are included once
+ * they exist).  The checkpoint pool grows to the largest slot count a sweep
+ * has used and is kept until pnop_destroy, so this is the memory cost of the
+ * snapshot budget of Section 2.5 as run.  Host only: reads a counter, issues
+ * no device work.  NULL arguments return PNOP_ERR_INVALID_ARG. */
+int pnop_device_bytes(const pnop_ctx* ctx, size_t* bytes);
 
 /* Binomial checkpoint plan (Section 2.5) for nsteps steps and snaps slots,
  * computed on the host: minimal forward recomputations (Eq. 2.18), stores.

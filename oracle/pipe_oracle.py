@@ -561,6 +561,26 @@ class Oracle:
         b = np.sum(w * np.abs(u[2]) ** 2, axis=0)
         return np.stack([a, b])
 
+    def full_spectrum(self, u: np.ndarray) -> np.ndarray:
+        """Coefficients of every mode k = -K..K (axis 3, index k + K) from the
+        stored half by the Hermitian symmetry f(-m, -k) = conj f(m, k) (Eq. 2.16)."""
+        K = self.p.K
+        neg = np.conj(u[:, :, ::-1, :0:-1])      # (m, -k) = conj(-m, k), k = K..1
+        return np.concatenate([neg, u], axis=3)
+
+    def resolution(self, u: np.ndarray, E0: float):
+        """Resolution measures of Section 2.4: the energy in the highest
+        azimuthal mode m = M summed over k = -K..K, and in the highest axial
+        mode k = K summed over m = -M..M, each over E0.  (The printed formulas
+        are garbled; they are read as energy fractions of these mode shells,
+        with the energy of Eq. 2.1 and each mode of the full spectrum counted
+        once.)"""
+        p = self.p
+        f = self.full_spectrum(u)
+        w = 0.5 * (2.0 * np.pi * p.Lz) * self.W            # per radial point, one full-spectrum mode
+        e = np.einsum('j,cjmk->mk', w, np.abs(f) ** 2)      # energy of every (m, k), k = -K..K
+        return float(e[2 * p.M, :].sum() / E0), float(e[:, 2 * p.K].sum() / E0)
+
     def scale_to(self, u: np.ndarray, E0: float) -> np.ndarray:
         return u * math.sqrt(E0 / self.energy(u))
 

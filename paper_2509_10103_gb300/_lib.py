@@ -25,9 +25,9 @@ EXPORTS = (
     "pnop_create", "pnop_set_base_flow", "pnop_dims", "pnop_grid_points", "pnop_step_forward", "pnop_step_adjoint",
     "pnop_gradient", "pnop_gradient_continuous", "pnop_gradient_forward", "pnop_gradient_backward",
     "pnop_gradient_host", "pnop_gradient_stats", "pnop_optimise", "pnop_optimise_ex", "pnop_set_host_tier", "pnop_host_tier_stats",
-    "pnop_two_level_counts", "pnop_mode_energy", "pnop_energy", "pnop_inner", "pnop_apply", "pnop_set_timeout",
-    "pnop_sync", "pnop_profile", "pnop_profile_read", "pnop_revolve_counts", "pnop_context_bytes",
-    "pnop_energy_noalloc", "pnop_last_error", "pnop_error_string", "pnop_destroy",
+    "pnop_two_level_counts", "pnop_mode_energy", "pnop_resolution", "pnop_energy", "pnop_inner", "pnop_apply", "pnop_set_timeout",
+    "pnop_sync", "pnop_profile", "pnop_profile_read", "pnop_revolve_counts", "pnop_context_bytes", "pnop_device_bytes",
+    "pnop_energy_noalloc", "pnop_measure_fma_peak", "pnop_last_error", "pnop_error_string", "pnop_destroy",
     "pnop_batch_create", "pnop_batch_submit", "pnop_batch_run", "pnop_batch_poll", "pnop_batch_result",
     "pnop_batch_stats", "pnop_batch_last_error", "pnop_batch_destroy", "pnop_batch_prepare",
     "pnop_batch_submit_prepared", "pnop_ops_free", "pnop_batch_bytes",
@@ -71,6 +71,7 @@ def _load():
                                      POINTER(c_double), POINTER(pnop_opt_stats)]),
         "pnop_set_host_tier": (c_int, [c_void_p, c_longlong, c_double]),
         "pnop_mode_energy": (c_int, [c_void_p, c_void_p, POINTER(c_double)]),
+        "pnop_resolution": (c_int, [c_void_p, c_void_p, c_double, POINTER(c_double), POINTER(c_double)]),
         "pnop_host_tier_stats": (c_int, [c_void_p, POINTER(c_int), POINTER(c_longlong), POINTER(c_longlong),
                                          POINTER(c_double)]),
         "pnop_two_level_counts": (c_int, [c_longlong, c_int, c_longlong, c_double, POINTER(c_int),
@@ -84,8 +85,10 @@ def _load():
         "pnop_profile_read": (c_int, [c_void_p, POINTER(c_double), POINTER(c_longlong), POINTER(c_double)]),
         "pnop_context_bytes": (c_int, [POINTER(pnop_grid), POINTER(pnop_params), c_int, POINTER(c_size_t)]),
         "pnop_revolve_counts": (c_int, [c_int, c_int, POINTER(c_longlong), POINTER(c_longlong)]),
+        "pnop_device_bytes": (c_int, [c_void_p, POINTER(c_size_t)]),
         "pnop_energy_noalloc": (c_int, [c_void_p, c_void_p, c_int, c_int, c_int, c_double, POINTER(c_double),
                                         c_void_p]),
+        "pnop_measure_fma_peak": (c_int, [c_int, c_double, c_void_p, POINTER(c_double)]),
         "pnop_last_error": (c_char_p, [c_void_p]),
         "pnop_error_string": (c_char_p, [c_int]),
         "pnop_destroy": (None, [c_void_p]),
@@ -177,6 +180,15 @@ def pnop_energy_noalloc(u, W, nr, M, K, Lz, stream=0):
     if rc != PNOP_OK:
         raise PnopError(rc, "energy_noalloc")
     return e.value
+
+
+def pnop_measure_fma_peak(precision=PNOP_FP64, seconds=0.05, stream=0):
+    """Measured FMA throughput (TFLOP/s) of the current device, FP64 or FP32."""
+    t = c_double()
+    rc = lib.pnop_measure_fma_peak(precision, seconds, c_void_p(stream), byref(t))
+    if rc != PNOP_OK:
+        raise PnopError(rc, "measure_fma_peak")
+    return t.value
 
 
 class Context:
@@ -281,6 +293,18 @@ class Context:
         self._check(lib.pnop_mode_energy(self._h, c_void_p(_ptr(u)), out.ctypes.data_as(POINTER(c_double))),
                     "mode_energy")
         return out
+
+    def pnop_device_bytes(self):
+        """Device bytes the context holds now (checkpoint slots included)."""
+        b = c_size_t()
+        self._check(lib.pnop_device_bytes(self._h, byref(b)), "device_bytes")
+        return b.value
+
+    def pnop_resolution(self, u, E0=-1.0):
+        """(e_M, e_K): energy of the highest azimuthal / axial mode over E0 (E0 <= 0: the field's energy)."""
+        a, b = c_double(), c_double()
+        self._check(lib.pnop_resolution(self._h, c_void_p(_ptr(u)), E0, byref(a), byref(b)), "resolution")
+        return a.value, b.value
 
     def pnop_set_host_tier(self, max_host_slots, io_ratio=-1.0):
         self._check(lib.pnop_set_host_tier(self._h, max_host_slots, io_ratio), "set_host_tier")

@@ -1,6 +1,6 @@
 """Build libpnop.so in-tree for sm_103a (GB300).
 
-Five translation units are compiled in parallel (four CUDA, one host C++) and
+Six translation units are compiled in parallel (five CUDA, one host C++) and
 linked into paper_2509_10103_gb300/libpnop.so.  No cmake; nvcc and g++ only.
 """
 from __future__ import annotations
@@ -32,7 +32,7 @@ def _run(cmd):
 
 
 def sources():
-    return [os.path.join(CSRC, f) for f in ("kernels.cu", "transforms.cu", "pnop.cu", "noalloc.cu", "setup.cpp")]
+    return [os.path.join(CSRC, f) for f in ("kernels.cu", "transforms.cu", "pnop.cu", "noalloc.cu", "probe.cu", "setup.cpp")]
 
 
 def up_to_date() -> bool:

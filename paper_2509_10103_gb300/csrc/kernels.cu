@@ -374,64 +374,30 @@ __global__ void __launch_bounds__(2 * kSK) k_band_solve(Geo g, const double* __r
     }
 }
 
-// RB_v = B_v u_v for v = +, -, z (rows j >= 1; row 0 is the Dirichlet row):
-// the explicit Crank-Nicolson half [1/dt + L_v/(2 Re)] u_v, which depends on
-// the old velocity only.  L_{m+1} and L_{m-1} share parity and differ only on
-// the diagonal (L_{m-1} = L_{m+1} + 4m/r^2), so L_{m+1} is applied to u_r and
-// u_theta and combined: L+ u+ = Lp u_r + i Lp u_t, L- u- = Lp u_r - i Lp u_t + 4m/r^2 u-.
-__global__ void k_stage_bu(Geo g, const double2* __restrict__ u, double2* __restrict__ RB) {
-    Idx d;
-    if (!decode(g, d)) return;
-    u += d.off;
-    RB += d.off;
-    const size_t o = sidx(g, d.j, d.im, d.k), S = d.S;
-    if (d.j == 0) {
-        RB[o] = RB[o + S] = RB[o + 2 * S] = make_double2(0, 0);
-        return;
-    }
-    const double ir = g.invr[d.j];
-    const double* Lb = slot_Lb(g, d.slot);
-    const double* Lp = Lb + ((size_t)abs(d.m + 1) * g.nr + d.j) * kB;
-    const double* Lz = Lb + ((size_t)abs(d.m) * g.nr + d.j) * kB;
-    double2 tr = make_double2(0, 0), tt = make_double2(0, 0), sz = make_double2(0, 0);
-    const double2 *ur = u, *ut = u + S, *uz = u + 2 * S;
-    // rows j >= 4 touch columns j-4..j+4 only (9 entries), wall rows columns 0..8
-    const int s0 = d.j >= 4 ? 0 : 4 - d.j, s1 = d.j >= 4 ? 8 : 12 - d.j;
-#pragma unroll
-    for (int s = 0; s < kB; ++s) {
-        const int c = d.j - 4 + s;
-        if (s < s0 || s > s1 || c >= g.nr) continue;
-        const size_t oc = sidx(g, c, d.im, d.k);
-        const double lp = __ldg(Lp + s);
-        tr = dfma(lp, ur[oc], tr);
-        tt = dfma(lp, ut[oc], tt);
-        sz = dfma(__ldg(Lz + s), uz[oc], sz);
-    }
-    const double dg = __ldg(slot_dgt(g, d.slot) + d.k);
-    const double2 a = ur[o], b = ut[o], c = uz[o];
-    const double2 up = make_double2(a.x - b.y, a.y + b.x);
-    const double2 um = make_double2(a.x + b.y, a.y - b.x);
-    // the bands hold L / (2 Re), so the 4m/r^2 diagonal difference carries the same factor
-    const double fm = 4.0 * g.inv_2re[d.slot] * __ldg(g.mrt + (size_t)d.im * g.nr + d.j) * ir;
-    const double2 sp = make_double2(tr.x - tt.y, tr.y + tt.x);
-    const double2 sm = make_double2(tr.x + tt.y + fm * um.x, tr.y - tt.x + fm * um.y);
-    RB[o] = make_double2(fma(dg, up.x, sp.x), fma(dg, up.y, sp.y));
-    RB[o + S] = make_double2(fma(dg, um.x, sm.x), fma(dg, um.y, sm.y));
-    RB[o + 2 * S] = make_double2(fma(dg, c.x, sz.x), fma(dg, c.y, sz.y));
-}
-
-// R_v = [RB_v +] F'_v for v = +, -, z (rows j >= 1), F' = F - grad p
-__global__ void k_stage_rhs(Geo g, const double2* __restrict__ RB, const double2* __restrict__ F,
+// R_v = F'_v [+ (2/dt) (T u)_v] for v = +, -, z (rows j >= 1), F' = F - grad p;
+// wall row R_v = (T u)_v (0 without u).  T u: u+ = u_r + i u_theta,
+// u- = u_r - i u_theta, u_z.  With A_v + B_v = 2 I / dt this right-hand side
+// gives A_v^{-1} E (B_v T u + F') + T u.
+__global__ void k_stage_rhs(Geo g, const double2* __restrict__ u, const double2* __restrict__ F,
                             const double2* __restrict__ p, double2* __restrict__ R) {
     Idx d;
     if (!decode(g, d)) return;
-    RB = moved(RB, d.off);
+    u = moved(u, d.off);
     F += d.off;
     p += d.off;
     R += d.off;
     const size_t o = sidx(g, d.j, d.im, d.k), S = d.S;
+    double2 tp = make_double2(0, 0), tm = tp, tz = tp;
+    if (u) {
+        const double2 a = u[o], b = u[o + S], c = u[o + 2 * S];
+        tp = make_double2(a.x - b.y, a.y + b.x);
+        tm = make_double2(a.x + b.y, a.y - b.x);
+        tz = c;
+    }
     if (d.j == 0) {
-        R[o] = R[o + S] = R[o + 2 * S] = make_double2(0, 0);
+        R[o] = tp;
+        R[o + S] = tm;
+        R[o + 2 * S] = tz;
         return;
     }
     const double kz = __ldg(g.kzt + d.k), mr = __ldg(g.mrt + (size_t)d.im * g.nr + d.j);
@@ -441,11 +407,11 @@ __global__ void k_stage_rhs(Geo g, const double2* __restrict__ RB, const double2
     const double2 ft = make_double2(ft0.x + mr * pj.y, ft0.y - mr * pj.x);
     const double2 fz = make_double2(fz0.x + kz * pj.y, fz0.y - kz * pj.x);
     double2 rp = make_double2(fr.x - ft.y, fr.y + ft.x), rm = make_double2(fr.x + ft.y, fr.y - ft.x), rz = fz;
-    if (RB) {
-        const double2 a = RB[o], b = RB[o + S], c = RB[o + 2 * S];
-        rp.x += a.x; rp.y += a.y;
-        rm.x += b.x; rm.y += b.y;
-        rz.x += c.x; rz.y += c.y;
+    if (u) {
+        const double f = g.two_dt[d.slot];
+        rp = dfma(f, tp, rp);
+        rm = dfma(f, tm, rm);
+        rz = dfma(f, tz, rz);
     }
     R[o] = rp;
     R[o + S] = rm;
@@ -458,13 +424,14 @@ __global__ void k_stage_rhs(Geo g, const double2* __restrict__ RB, const double2
 // applies it to its rows j = y, y + kFJ, ...
 constexpr int kFK = 16, kFJ = 16;
 
-// out = [addto +] back to (r, theta, z) with the influence correction
-// (div u = 0 at the wall) or, for mode (0,0), flux correction and u_r = 0.
-// The wall coefficient a0 = d/dr u_r at the wall of the tentative velocity
-// (u_r = (x+ + x-)/2), or for mode (0,0) the flux sum_j W_j x_z, is reduced
-// first.
+// out = [addto +] back to (r, theta, z) [- usub] with the influence
+// correction (div u = 0 at the wall) or, for mode (0,0), flux correction and
+// u_r = 0.  The wall coefficient a0 = d/dr u_r at the wall of the tentative
+// velocity (u_r = (x+ + x-)/2 [- usub_r]), or for mode (0,0) the flux
+// sum_j W_j (x_z [- usub_z]), is reduced first.
 __global__ void __launch_bounds__(kFK* kFJ) k_stage_finish(Geo g, const double2* __restrict__ R,
                                                           const double2* __restrict__ addto,
+                                                          const double2* __restrict__ usub,
                                                           double2* __restrict__ out) {
     __shared__ double2 red[kFJ][kFK];
     const int tx = threadIdx.x, ty = threadIdx.y;
@@ -474,18 +441,26 @@ __global__ void __launch_bounds__(kFK* kFJ) k_stage_finish(Geo g, const double2*
     const size_t off = (size_t)slot * g.fs;
     R += off;
     addto = moved(addto, off);
+    usub = moved(usub, off);
     out += off;
     const bool on = k < g.nk, mean = (m == 0 && k == 0);
     double2 part = make_double2(0, 0);
     if (on) {
         if (mean) {
-            for (int j = ty; j < g.nr; j += kFJ) part = dfma(g.W[j], R[sidx(g, j, im, k) + 2 * S], part);
+            for (int j = ty; j < g.nr; j += kFJ) {
+                const size_t o = sidx(g, j, im, k) + 2 * S;
+                double2 x = R[o];
+                if (usub) x = make_double2(x.x - usub[o].x, x.y - usub[o].y);
+                part = dfma(g.W[j], x, part);
+            }
         } else {
             const double* d0 = g.D1 + (size_t)par_idx(m + 1) * g.nr * kB;  // row 0 of D1 (u_r parity)
             for (int c = ty; c <= 8 && c < g.nr; c += kFJ) {
                 const size_t oc = sidx(g, c, im, k);
                 const double2 p = R[oc], q = R[oc + S];
-                part = dfma(0.5 * __ldg(d0 + 4 + c), make_double2(p.x + q.x, p.y + q.y), part);
+                double2 x = make_double2(0.5 * (p.x + q.x), 0.5 * (p.y + q.y));
+                if (usub) x = make_double2(x.x - usub[oc].x, x.y - usub[oc].y);
+                part = dfma(__ldg(d0 + 4 + c), x, part);
             }
         }
     }
@@ -503,6 +478,12 @@ __global__ void __launch_bounds__(kFK* kFJ) k_stage_finish(Geo g, const double2*
         double2 ur = make_double2(0.5 * (xp.x + xm.x), 0.5 * (xp.y + xm.y));
         double2 ut = make_double2(0.5 * (xp.y - xm.y), -0.5 * (xp.x - xm.x));
         double2 uz = R[o + 2 * S];
+        if (usub) {
+            const double2 a = usub[o], b = usub[o + S], c = usub[o + 2 * S];
+            ur.x -= a.x; ur.y -= a.y;
+            ut.x -= b.x; ut.y -= b.y;
+            uz.x -= c.x; uz.y -= c.y;
+        }
         if (mean) {
             uz = dfma(fg[j] * (-g.flux_inv[slot]), a0, uz);
             ur = make_double2(0, 0);
@@ -526,8 +507,11 @@ __global__ void __launch_bounds__(kFK* kFJ) k_stage_finish(Geo g, const double2*
 
 // ------------------------------------------------------------------ radial stage (transpose)
 // Per mode: ybar = Fin^H ubar_new (a reduction over j), then xbar = Ti^H ybar.
+// The mode's coefficient acc of Fin^H goes to ac (added to it when ac_add), so
+// that Fin^H can be applied again later without the reduction.
 __global__ void __launch_bounds__(kFK* kFJ) k_stageT_finish(Geo g, const double2* __restrict__ un,
-                                                           double2* __restrict__ R) {
+                                                           double2* __restrict__ R, double2* __restrict__ ac,
+                                                           int ac_add) {
     __shared__ double2 red[kFJ][kFK];
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int k = blockIdx.x * kFK + tx, im = blockIdx.y, m = im - g.M;
@@ -559,6 +543,15 @@ __global__ void __launch_bounds__(kFK* kFJ) k_stageT_finish(Geo g, const double2
     double2 acc = red[0][tx];
 #pragma unroll
     for (int i = 1; i < kFJ; ++i) acc = make_double2(acc.x + red[i][tx].x, acc.y + red[i][tx].y);
+    if (ty == 0) {
+        double2* a = ac + ((size_t)slot * g.nm + im) * g.nk + k;
+        if (ac_add) {
+            const double2 prev = *a;
+            *a = make_double2(prev.x + acc.x, prev.y + acc.y);
+        } else {
+            *a = acc;
+        }
+    }
     const double* d0 = g.D1 + (size_t)par_idx(m + 1) * g.nr * kB;
     for (int j = ty; j < g.nr; j += kFJ) {
         const size_t o = sidx(g, j, im, k);
@@ -575,31 +568,51 @@ __global__ void __launch_bounds__(kFK* kFJ) k_stageT_finish(Geo g, const double2
     }
 }
 
-// ub (=, or += when acc) T^H B^T X when ub is given; Fb = T^H (cf1 X + cf2 Y)
-// when Fb is given (Y is read only when TWO).
+// With X = Z = A^{-T} T^-H Fin^H v (wall row kept) and E the projection on
+// rows j >= 1:
+//   ub (=, or += when acc) T^H ((2/dt) E Z + e0 Z_0) - Fin^H v  when ub is given,
+//     v = V1 [+ V2], Fin^H v from the stored per-mode coefficients ac
+//     (u_r rows 0..8 gain d0_j ac; mode (0,0): u_r = 0, u_z gains
+//     -flux_inv W_j ac): the transpose of the velocity part of the stage;
+//   Fb = T^H E (cf1 X + cf2 Y)  when Fb is given (Y is read only when TWO).
 template <bool TWO>
 __global__ void k_stageT_rhs(Geo g, const double2* __restrict__ X, const double2* __restrict__ Y, double cf1,
-                             double cf2, double2* __restrict__ ub, int acc, double2* __restrict__ Fb) {
+                             double cf2, double2* __restrict__ ub, int acc, double2* __restrict__ Fb,
+                             const double2* __restrict__ V1, const double2* __restrict__ V2,
+                             const double2* __restrict__ ac) {
     Idx d;
     if (!decode(g, d)) return;
     X += d.off;
     Y = moved(Y, d.off);
     ub = moved(ub, d.off);
     Fb = moved(Fb, d.off);
+    V1 = moved(V1, d.off);
+    V2 = moved(V2, d.off);
     const size_t o = sidx(g, d.j, d.im, d.k), S = d.S;
     const double2 rp = X[o], rm = X[o + S], rz = X[o + 2 * S];
     if (ub) {
-        const double dg = __ldg(slot_dgt(g, d.slot) + d.k);
-        const double* Lb = slot_Lb(g, d.slot);
-        const double2 bp0 = band_col(g, Lb + (size_t)abs(d.m + 1) * g.nr * kB, X, d.j, d.im, d.k);
-        const double2 bm0 = band_col(g, Lb + (size_t)abs(d.m - 1) * g.nr * kB, X + S, d.j, d.im, d.k);
-        const double2 bz0 = band_col(g, Lb + (size_t)abs(d.m) * g.nr * kB, X + 2 * S, d.j, d.im, d.k);
-        const double2 bp = make_double2(fma(dg, rp.x, bp0.x), fma(dg, rp.y, bp0.y));  // bands hold L / (2 Re)
-        const double2 bm = make_double2(fma(dg, rm.x, bm0.x), fma(dg, rm.y, bm0.y));
-        const double2 bz = make_double2(fma(dg, rz.x, bz0.x), fma(dg, rz.y, bz0.y));
+        const double f = d.j == 0 ? 1.0 : g.two_dt[d.slot];
+        const double2 bp = dscale(rp, f), bm = dscale(rm, f), bz = dscale(rz, f);
         double2 vr = make_double2(bp.x + bm.x, bp.y + bm.y);
         double2 vt = make_double2(bp.y - bm.y, -bp.x + bm.x);
         double2 vz = bz;
+        double2 mr = V1[o], mt = V1[o + S], mz = V1[o + 2 * S];
+        if (V2) {
+            const double2 a = V2[o], b = V2[o + S], c = V2[o + 2 * S];
+            mr.x += a.x; mr.y += a.y;
+            mt.x += b.x; mt.y += b.y;
+            mz.x += c.x; mz.y += c.y;
+        }
+        const double2 cm = ac[((size_t)d.slot * g.nm + d.im) * g.nk + d.k];
+        if (d.m == 0 && d.k == 0) {
+            mr = make_double2(0, 0);
+            mz = dfma(-g.flux_inv[d.slot] * g.W[d.j], cm, mz);
+        } else if (d.j <= 8) {
+            mr = dfma(__ldg(g.D1 + (size_t)par_idx(d.m + 1) * g.nr * kB + 4 + d.j), cm, mr);
+        }
+        vr.x -= mr.x; vr.y -= mr.y;
+        vt.x -= mt.x; vt.y -= mt.y;
+        vz.x -= mz.x; vz.y -= mz.y;
         if (acc) {
             const double2 a = ub[o], b = ub[o + S], c = ub[o + 2 * S];
             vr.x += a.x; vr.y += a.y;
@@ -611,6 +624,10 @@ __global__ void k_stageT_rhs(Geo g, const double2* __restrict__ X, const double2
         ub[o + 2 * S] = vz;
     }
     if (Fb) {
+        if (d.j == 0) {
+            Fb[o] = Fb[o + S] = Fb[o + 2 * S] = make_double2(0, 0);
+            return;
+        }
         double2 p = make_double2(cf1 * rp.x, cf1 * rp.y), q = make_double2(cf1 * rm.x, cf1 * rm.y),
                 z = make_double2(cf1 * rz.x, cf1 * rz.y);
         if (TWO) {
@@ -792,6 +809,51 @@ __global__ void k_mode_energy(Geo g, const double2* __restrict__ u, double* __re
     E[g.nm * g.nk + mode] = w * b;
 }
 
+// Resolution measures of Section 2.4 in one block, fixed summation order:
+// out[0] = energy of the azimuthal mode m = M over the full spectrum
+// k = -K..K, out[1] = energy of the axial mode k = K over m = -M..M.  A
+// stored mode (m, k > 0) holds e(m, k) + e(-m, -k), so the full-spectrum
+// energy of (M, k) is half of stored (M, k) and that of (M, -k) half of
+// stored (-M, k); (M, 0) counts once.  For K = 0 the axial mode is k = 0 and
+// every stored (m, 0) counts once.
+__global__ void __launch_bounds__(1024) k_resolution(Geo g, const double2* __restrict__ u, double* __restrict__ out) {
+    __shared__ double red[2][1024];
+    const size_t S = (size_t)g.nr * g.nm * g.nk;
+    const double w0 = 0.5 * g.ewt;
+    double aM = 0, aK = 0;
+    const int nM = 2 * 3 * g.nr * g.nk;  // (side, c, j, k) with side 0: m = M, side 1: m = -M
+    for (int i = threadIdx.x; i < nM; i += blockDim.x) {
+        const int k = i % g.nk, rest = i / g.nk, j = rest % g.nr, c = (rest / g.nr) % 3, side = rest / (3 * g.nr);
+        // full-spectrum weight: w0 W_j for (M, k >= 0) from side 0 and for
+        // (M, -k), k > 0, from side 1 (half the stored weight 2 w0 W_j of a
+        // k > 0 mode); stored (-M, 0) is (M, 0)'s conjugate, already counted
+        if (side && k == 0) continue;
+        const int im = side ? 0 : 2 * g.M;
+        const double2 v = u[c * S + sidx(g, j, im, k)];
+        aM += w0 * g.W[j] * (v.x * v.x + v.y * v.y);
+    }
+    const int nK = 3 * g.nr * g.nm;  // (c, j, m) at k = K: full-spectrum weight w0 W_j, K = 0 or not
+    for (int i = threadIdx.x; i < nK; i += blockDim.x) {
+        const int im = i % g.nm, rest = i / g.nm, j = rest % g.nr, c = rest / g.nr;
+        const double2 v = u[c * S + sidx(g, j, im, g.K)];
+        aK += w0 * g.W[j] * (v.x * v.x + v.y * v.y);
+    }
+    red[0][threadIdx.x] = aM;
+    red[1][threadIdx.x] = aK;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) {
+            red[0][threadIdx.x] += red[0][threadIdx.x + s];
+            red[1][threadIdx.x] += red[1][threadIdx.x + s];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        out[0] = red[0][0];
+        out[1] = red[1][0];
+    }
+}
+
 // ------------------------------------------------------------------ elementwise / reductions
 // n values of batch entry blockIdx.y
 __global__ void k_axpby(Geo g, size_t n, double a, const double2* __restrict__ x, double b,
@@ -916,17 +978,18 @@ void launch_baseT(const Geo& g, const double2* nb, double2* ub, cudaStream_t s) 
     check_launch("baseT");
 }
 
-// trans (zero_row0 == 1) selects the transposed coefficient layout
+// trans selects the transposed coefficient layout; zero_row0 writes 0 to the
+// wall row of the solution
 static void launch_band_solve(const Geo& g, const double* fac, size_t fac_stride, double2* X, const double2* add,
-                              int helm, int zero_row0, cudaStream_t s) {
+                              int helm, int trans, int zero_row0, cudaStream_t s) {
     const dim3 nblocks((unsigned)((helm ? 3 : 1) * g.nm * g.ntile), (unsigned)g.nb);
     const size_t sm = (size_t)g.nr * kSK * sizeof(double2) + 2 * (size_t)kRC * 9 * kSK * sizeof(double);
-    if (!zero_row0) {
+    if (!trans) {
         smem_limit((const void*)k_band_solve<4, 8, false>);
-        k_band_solve<4, 8, false><<<nblocks, 2 * kSK, sm, s>>>(g, fac, fac_stride, X, add, helm, 0);
+        k_band_solve<4, 8, false><<<nblocks, 2 * kSK, sm, s>>>(g, fac, fac_stride, X, add, helm, zero_row0);
     } else {
         smem_limit((const void*)k_band_solve<8, 4, true>);
-        k_band_solve<8, 4, true><<<nblocks, 2 * kSK, sm, s>>>(g, fac, fac_stride, X, add, helm, 1);
+        k_band_solve<8, 4, true><<<nblocks, 2 * kSK, sm, s>>>(g, fac, fac_stride, X, add, helm, zero_row0);
     }
 }
 
@@ -935,40 +998,38 @@ void launch_stage_div(const Geo& g, const double2* F, double2* q, cudaStream_t s
     check_launch("stage_div");
 }
 void launch_stage_psolve(const Geo& g, double2* q, cudaStream_t s) {
-    launch_band_solve(g, g.facP, 0, q, nullptr, 0, 0, s);
+    launch_band_solve(g, g.facP, 0, q, nullptr, 0, 0, 0, s);
     check_launch("stage_psolve");
 }
-void launch_stage_bu(const Geo& g, const double2* u, double2* RB, cudaStream_t s) {
-    k_stage_bu<<<spec_grid(g), spec_bx(g), 0, s>>>(g, u, RB);
-    check_launch("stage_bu");
-}
-void launch_stage_rhs(const Geo& g, const double2* RB, const double2* F, const double2* p, double2* R, cudaStream_t s) {
-    k_stage_rhs<<<spec_grid(g), spec_bx(g), 0, s>>>(g, RB, F, p, R);
+void launch_stage_rhs(const Geo& g, const double2* u, const double2* F, const double2* p, double2* R, cudaStream_t s) {
+    k_stage_rhs<<<spec_grid(g), spec_bx(g), 0, s>>>(g, u, F, p, R);
     check_launch("stage_rhs");
 }
 void launch_stage_hsolve(const Geo& g, double2* R, cudaStream_t s) {
-    launch_band_solve(g, g.facH, g.sFacH, R, nullptr, 1, 0, s);
+    launch_band_solve(g, g.facH, g.sFacH, R, nullptr, 1, 0, 0, s);
     check_launch("stage_hsolve");
 }
 static inline dim3 mode_grid(const Geo& g) { return dim3((g.nk + kFK - 1) / kFK, g.nm, g.nb); }
-void launch_stage_finish(const Geo& g, const double2* R, const double2* addto, double2* out, cudaStream_t s) {
-    k_stage_finish<<<mode_grid(g), dim3(kFK, kFJ), 0, s>>>(g, R, addto, out);
+void launch_stage_finish(const Geo& g, const double2* R, const double2* addto, const double2* usub, double2* out,
+                         cudaStream_t s) {
+    k_stage_finish<<<mode_grid(g), dim3(kFK, kFJ), 0, s>>>(g, R, addto, usub, out);
     check_launch("stage_finish");
 }
-void launch_stageT_finish(const Geo& g, const double2* ubn, double2* R, cudaStream_t s) {
-    k_stageT_finish<<<mode_grid(g), dim3(kFK, kFJ), 0, s>>>(g, ubn, R);
+void launch_stageT_finish(const Geo& g, const double2* ubn, double2* R, double2* ac, int ac_add, cudaStream_t s) {
+    k_stageT_finish<<<mode_grid(g), dim3(kFK, kFJ), 0, s>>>(g, ubn, R, ac, ac_add);
     check_launch("stageT_finish");
 }
 void launch_stageT_hsolve(const Geo& g, double2* R, const double2* add, cudaStream_t s) {
-    launch_band_solve(g, g.facHT, g.sFacH, R, add, 1, 1, s);
+    launch_band_solve(g, g.facHT, g.sFacH, R, add, 1, 1, 0, s);
     check_launch("stageT_hsolve");
 }
 void launch_stageT_rhs(const Geo& g, const double2* X, const double2* Y, double cf1, double cf2, double2* ub, int acc,
-                       double2* Fb, cudaStream_t s) {
+                       double2* Fb, const double2* V1, const double2* V2, const double2* ac, cudaStream_t s) {
+    if (ub && (!V1 || !ac)) throw std::runtime_error("stageT_rhs: the velocity part needs its input and coefficients");
     if (Y)
-        k_stageT_rhs<true><<<spec_grid(g), spec_bx(g), 0, s>>>(g, X, Y, cf1, cf2, ub, acc, Fb);
+        k_stageT_rhs<true><<<spec_grid(g), spec_bx(g), 0, s>>>(g, X, Y, cf1, cf2, ub, acc, Fb, V1, V2, ac);
     else
-        k_stageT_rhs<false><<<spec_grid(g), spec_bx(g), 0, s>>>(g, X, Y, cf1, cf2, ub, acc, Fb);
+        k_stageT_rhs<false><<<spec_grid(g), spec_bx(g), 0, s>>>(g, X, Y, cf1, cf2, ub, acc, Fb, V1, V2, ac);
     check_launch("stageT_rhs");
 }
 void launch_stageT_qbar(const Geo& g, const double2* Fb, double2* q, cudaStream_t s) {
@@ -976,7 +1037,7 @@ void launch_stageT_qbar(const Geo& g, const double2* Fb, double2* q, cudaStream_
     check_launch("stageT_qbar");
 }
 void launch_stageT_psolve(const Geo& g, double2* q, cudaStream_t s) {
-    launch_band_solve(g, g.facPT, 0, q, nullptr, 0, 1, s);
+    launch_band_solve(g, g.facPT, 0, q, nullptr, 0, 1, 1, s);
     check_launch("stageT_psolve");
 }
 void launch_stageT_div(const Geo& g, const double2* z, double2* Fb, cudaStream_t s) {
@@ -988,6 +1049,12 @@ void launch_mode_energy(const Geo& g, const double2* u, double* E, cudaStream_t 
     single_only(g, "mode_energy");
     k_mode_energy<<<nblk((size_t)g.nm * g.nk, 128), 128, 0, s>>>(g, u, E);
     check_launch("mode_energy");
+}
+
+void launch_resolution(const Geo& g, const double2* u, double* out, cudaStream_t s) {
+    single_only(g, "resolution");
+    k_resolution<<<1, 1024, 0, s>>>(g, u, out);
+    check_launch("resolution");
 }
 
 void launch_project(const Geo& g, double2* u, double2* y, const double* L, cudaStream_t s) {

@@ -49,7 +49,7 @@ struct Geo {
     int slot[kMaxBatch];
     size_t fs, ps;
     size_t sLb, sFacH, sInfl, sNr, sNk;
-    double inv_2re[kMaxBatch];   // 1 / (2 Re) per slot
+    double two_dt[kMaxBatch];    // 2 / dt per slot (A + B = 2 I / dt of the Crank-Nicolson pair)
     double flux_inv[kMaxBatch];  // flux normalisation per slot
     double2 cs[kMaxBatch];       // (cos, sin) of the pulsation phase of entry b at the launch's time
 };
@@ -107,31 +107,42 @@ template <class T2>
 void launch_anal_theta(const Geo& g, const FieldPtrs& f, int nfield, const T2* Z, const Twiddles& tw, cudaStream_t s);
 
 // ---- radial stage (forward): out = S(u, F) ----
-// q = div F; p = A_p^{-1} q; R = B u_pm + (F - grad p)_pm; R = A_v^{-1} R;
-// out = back to (r, theta, z) + influence / flux corrections (Section 2.4).
+// q = div F; p = A_p^{-1} q; R = (F - grad p)_pm [+ (2/dt) T u, wall row T u];
+// R = A_v^{-1} R; out = back to (r, theta, z) [- u] + influence / flux
+// corrections (Section 2.4).  The explicit Crank-Nicolson half enters through
+// A + B = 2 I / dt: A^{-1} E (B u + F) = A^{-1} (2 E u / dt + e0 u_0 + E F) - u,
+// so no banded product with the old velocity is formed.
 void launch_stage_div(const Geo& g, const double2* F, double2* q, cudaStream_t s);
 void launch_stage_psolve(const Geo& g, double2* q, cudaStream_t s);
-// RB = explicit Crank-Nicolson half B_v u_v (depends on the old velocity only)
-void launch_stage_bu(const Geo& g, const double2* u, double2* RB, cudaStream_t s);
-// R = [RB +] (F - grad p) in the +/- basis; RB may be null (forcing-only stage S(0, F))
-void launch_stage_rhs(const Geo& g, const double2* RB, const double2* F, const double2* p, double2* R, cudaStream_t s);
+// R = (F - grad p) in the +/- basis, plus (2/dt) T u (rows j >= 1) and T u
+// (wall row) when u is given (u null: forcing-only stage S(0, F))
+void launch_stage_rhs(const Geo& g, const double2* u, const double2* F, const double2* p, double2* R, cudaStream_t s);
 void launch_stage_hsolve(const Geo& g, double2* R, cudaStream_t s);
-// out = [addto +] finished stage (addto may be null): the per-mode wall coefficient
-// (influence) or flux sum (mode (0,0)) and the correction it drives, in one launch
-void launch_stage_finish(const Geo& g, const double2* R, const double2* addto, double2* out, cudaStream_t s);
+// out = [addto +] finished stage (addto may be null), with the old velocity
+// usub subtracted from the tentative velocity when given: the per-mode wall
+// coefficient (influence) or flux sum (mode (0,0)) and the correction it
+// drives, in one launch
+void launch_stage_finish(const Geo& g, const double2* R, const double2* addto, const double2* usub, double2* out,
+                         cudaStream_t s);
 // ---- radial stage (transpose): ub (=, or += when acc) S_u^H ubn, Fb = S_F^H ubn ----
-void launch_stageT_finish(const Geo& g, const double2* ubn, double2* R, cudaStream_t s);
-// R = A^{-T} R [+ add] (add may be null)
+// R = T^-H Fin^H ubn; the per-mode coefficient of Fin^H to ac[slot][m][k]
+// (added to what ac holds when ac_add)
+void launch_stageT_finish(const Geo& g, const double2* ubn, double2* R, double2* ac, int ac_add, cudaStream_t s);
+// R = A^{-T} R [+ add] (add may be null); the wall row is kept
 void launch_stageT_hsolve(const Geo& g, double2* R, const double2* add, cudaStream_t s);
-// ub (+)= T^H B^T X if ub;  Fb = T^H (cf1 X + cf2 Y) if Fb (Y may be null)
+// with Z = A^{-T} T^-H Fin^H v (X, the transposed solve's output, E: rows j >= 1):
+// ub (=, or += when acc) T^H ((2/dt) E Z + e0 Z_0) - Fin^H v if ub, v = V1 [+ V2]
+// (Fin^H from the coefficients ac);  Fb = T^H E (cf1 X + cf2 Y) if Fb (Y may be null)
 void launch_stageT_rhs(const Geo& g, const double2* X, const double2* Y, double cf1, double cf2, double2* ub, int acc,
-                       double2* Fb, cudaStream_t s);
+                       double2* Fb, const double2* V1, const double2* V2, const double2* ac, cudaStream_t s);
 void launch_stageT_qbar(const Geo& g, const double2* Fb, double2* q, cudaStream_t s);
 void launch_stageT_psolve(const Geo& g, double2* q, cudaStream_t s);
 void launch_stageT_div(const Geo& g, const double2* z, double2* Fb, cudaStream_t s);
 
 // ---- diagnostics: per-mode energy, E[0] cross-section and E[1] axial parts, [2][nm][nk] ----
 void launch_mode_energy(const Geo& g, const double2* u, double* E, cudaStream_t s);
+// ---- resolution measures: out[0] energy of m = M (all k), out[1] energy of k = K (all m), full spectrum ----
+void launch_resolution(const Geo& g, const double2* u, double* out, cudaStream_t s);
 
 // ---- admissible projection (energy-orthogonal, Section 2.2 constraints) ----
 // u <- P u in place; y: one-component scratch field; L: factors of build_projection

@@ -116,11 +116,11 @@ struct pnop_ctx {
     double2* wb = nullptr;
     double2* R = nullptr;
     double2* Rl = nullptr;  // front part of the transposed stage for the incoming cotangent
-    double2* RB = nullptr;  // explicit viscous half B u
+    double2* ac = nullptr;  // per-mode coefficients of the transposed influence correction [slot][m][k]
     double2* q = nullptr;
     double2* q2 = nullptr;  // pressure scratch of the side stream
     cudaStream_t side = nullptr;  // second stream for independent work within a step
-    cudaEvent_t ev_fork = nullptr, ev_bu = nullptr, ev_t = nullptr, ev_base = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_t = nullptr, ev_base = nullptr;
     double2* Nbase = nullptr;  // base-flow terms (or their transpose), added by the analysis
     double2 *tmpA = nullptr, *tmpB = nullptr, *lamA = nullptr, *lamB = nullptr;
     void* Y = nullptr;
@@ -263,7 +263,7 @@ void upload_slot_operators(pnop_ctx* c, int slot, const pnop::HostOps& h) {
     ck(cudaMemcpy(c->d_dUh + slot * duh.size(), duh.data(), duh.size() * sizeof(double2), cudaMemcpyHostToDevice),
        "upload");
     Geo& g = c->geo;
-    g.inv_2re[slot] = 1.0 / (2.0 * h.ph.Re);
+    g.two_dt[slot] = 2.0 / h.ph.dt;
     g.flux_inv[slot] = h.flux_inv;
     g.Lb = c->d_Lb;
     g.dgt = c->d_dgt;
@@ -356,45 +356,41 @@ void wait_stream(pnop_ctx* c, const char* what) {
 // of the RADIAL_BAND and SPECTRAL classes): a 9-entry band row on a complex
 // value is 36 flops; the remaining terms are counted as written.
 namespace flops {
-constexpr double div = 36 + 12, bu = 3 * 36 + 24, rhs = 36 + 12 + 8, a0_mode = 72, finish = 20;
-constexpr double tfinish = 36, trhs_u = 3 * 36 + 30, trhs_f = 8, qbar = 36 + 8, tdiv = 36 + 12;
+constexpr double div = 36 + 12, rhs = 36 + 12 + 8, rhs_u = 6 + 12, a0_mode = 72, finish = 20, finish_u = 6;
+constexpr double tfinish = 36, trhs_u = 12 + 12, trhs_f = 8, qbar = 36 + 8, tdiv = 36 + 12;
 constexpr double curl = 2 * 36 + 16, curlT = 2 * 36 + 20, base = 12, grad_u = 3 * 36 + 24;
 }  // namespace flops
 
-// RB = explicit Crank-Nicolson half B u (old velocity only) on stream st
-void stage_bu(pnop_ctx* c, const double2* u, double2* RB, cudaStream_t st) {
-    run(c, PNOP_K_RADIAL_BAND, 1, flops::bu * c->S(), [&] { pnop::launch_stage_bu(c->geo, u, RB, st); }, st);
-}
-
-// out = [addto +] S(u, F), one predictor-corrector stage (Section 2.4), where
-// the velocity enters through RB = B u (null: forcing only, S(0, F)).  When
-// rb_ready is given the context stream waits for it before using RB.
-void stage(pnop_ctx* c, const double2* RB, const double2* F, double2* out, const double2* addto,
-           cudaEvent_t rb_ready) {
+// out = [addto +] S(u, F), one predictor-corrector stage (Section 2.4); u
+// null: forcing only, S(0, F).  The old velocity enters the Helmholtz
+// right-hand side as (2/dt) T u and is subtracted after the solve, which
+// equals the explicit Crank-Nicolson half B u because A + B = 2 I / dt.
+void stage(pnop_ctx* c, const double2* u, const double2* F, double2* out, const double2* addto) {
     Range nvtx_range("pnop:stage");
     const Geo& g = c->geo;
     cudaStream_t s = c->stream;
     const double S = (double)c->S();
     run(c, PNOP_K_RADIAL_BAND, 1, flops::div * S, [&] { pnop::launch_stage_div(g, F, c->q, s); });
     run(c, PNOP_K_RADIAL_SOLVE, 1, nmodes(c), [&] { pnop::launch_stage_psolve(g, c->q, s); });
-    if (rb_ready) join_side(c, rb_ready);
-    run(c, PNOP_K_RADIAL_BAND, 1, flops::rhs * S, [&] { pnop::launch_stage_rhs(g, RB, F, c->q, c->R, s); });
+    run(c, PNOP_K_RADIAL_BAND, 1, (flops::rhs + (u ? flops::rhs_u : 0)) * S,
+        [&] { pnop::launch_stage_rhs(g, u, F, c->q, c->R, s); });
     run(c, PNOP_K_RADIAL_SOLVE, 1, 3 * nmodes(c), [&] { pnop::launch_stage_hsolve(g, c->R, s); });
-    run(c, PNOP_K_RADIAL_BAND, 1, flops::finish * S + flops::a0_mode * nmodes(c),
-        [&] { pnop::launch_stage_finish(g, c->R, addto, out, s); });
+    run(c, PNOP_K_RADIAL_BAND, 1, (flops::finish + (u ? flops::finish_u : 0)) * S + flops::a0_mode * nmodes(c),
+        [&] { pnop::launch_stage_finish(g, c->R, addto, u, out, s); });
 }
 
 // out = S(u, F) on the context stream alone (operator access)
-void stage_u(pnop_ctx* c, const double2* u, const double2* F, double2* out) {
-    if (u) stage_bu(c, u, c->RB, c->stream);
-    stage(c, u ? c->RB : nullptr, F, out, nullptr, nullptr);
-}
+void stage_u(pnop_ctx* c, const double2* u, const double2* F, double2* out) { stage(c, u, F, out, nullptr); }
 
-// Rb = E A^{-T} Ti^H Fin^H ubn [+ add]: the part of the transposed stage
-// shared by its velocity and forcing cotangents.
-void stageT_front(pnop_ctx* c, const double2* ubn, double2* Rb, cudaStream_t s, const double2* add = nullptr) {
+// Rb = A^{-T} Ti^H Fin^H ubn [+ add]: the part of the transposed stage shared
+// by its velocity and forcing cotangents.  The per-mode coefficients of
+// Fin^H go to c->ac (added to what it holds when ac_add), for the velocity
+// part of stageT_rhs.
+void stageT_front(pnop_ctx* c, const double2* ubn, double2* Rb, cudaStream_t s, const double2* add = nullptr,
+                  int ac_add = 0) {
     const Geo& g = c->geo;
-    run(c, PNOP_K_RADIAL_BAND, 1, flops::tfinish * c->S(), [&] { pnop::launch_stageT_finish(g, ubn, Rb, s); }, s);
+    run(c, PNOP_K_RADIAL_BAND, 1, flops::tfinish * c->S(),
+        [&] { pnop::launch_stageT_finish(g, ubn, Rb, c->ac, ac_add, s); }, s);
     run(c, PNOP_K_RADIAL_SOLVE, 1, 3 * nmodes(c), [&] { pnop::launch_stageT_hsolve(g, Rb, add, s); }, s);
 }
 
@@ -413,7 +409,7 @@ void stageT(pnop_ctx* c, const double2* ubn, double2* ub, int acc, double2* Fb) 
     const Geo& g = c->geo;
     stageT_front(c, ubn, c->R, c->stream);
     run(c, PNOP_K_RADIAL_BAND, 1, ((ub ? flops::trhs_u : 0) + (Fb ? flops::trhs_f : 0)) * c->S(),
-        [&] { pnop::launch_stageT_rhs(g, c->R, nullptr, 1.0, 0.0, ub, acc, Fb, c->stream); });
+        [&] { pnop::launch_stageT_rhs(g, c->R, nullptr, 1.0, 0.0, ub, acc, Fb, ubn, nullptr, c->ac, c->stream); });
     if (Fb) stageT_proj(c, Fb, c->q, c->stream);
 }
 
@@ -614,30 +610,25 @@ void cadj_step(pnop_ctx* c, const double2* u_next, double t_next, const double2*
     Range nvtx_range("pnop:cadj_step");
     fork_side(c);
     queue_base_adj(c, w, t_next);
-    stage_bu(c, w, c->RB, c->side);
-    ck(cudaEventRecord(c->ev_bu, c->side), "record");
     nonlinear_adj(c, w, u_next, t_next, c->N0, true);
-    stage(c, c->RB, c->N0, c->us, nullptr, c->ev_bu);
+    stage(c, w, c->N0, c->us, nullptr);
     nonlinear_adj(c, c->us, u_now, t_now, c->N1);
     axpby(c, 0.5, c->N1, -0.5, c->N0, c->N1);
-    stage(c, nullptr, c->N1, out, c->us, nullptr);
+    stage(c, nullptr, c->N1, out, c->us);
 }
 
 // ------------------------------------------------------------------ steps
 // Predictor u* = S(u, N0), corrector S(u, (N0 + N*)/2) = u* + S(0, (N* - N0)/2)
-// (S is linear), so the corrector skips the explicit viscous matvec.  B u
-// depends on u only and runs on the side stream while N(u) is transformed.
+// (S is linear), so the corrector has no velocity part.
 void fwd_step(pnop_ctx* c, const double2* u, double2* out, double t) {
     Range nvtx_range("pnop:fwd_step");
     fork_side(c);
     queue_base(c, u, t);
-    stage_bu(c, u, c->RB, c->side);
-    ck(cudaEventRecord(c->ev_bu, c->side), "record");
     nonlinear(c, u, t, c->N0, c->Y, true);
-    stage(c, c->RB, c->N0, c->us, nullptr, c->ev_bu);
+    stage(c, u, c->N0, c->us, nullptr);
     nonlinear(c, c->us, t + c->h.ph.dt, c->N1, c->Y);
     axpby(c, 0.5, c->N1, -0.5, c->N0, c->N1);
-    stage(c, nullptr, c->N1, out, c->us, nullptr);
+    stage(c, nullptr, c->N1, out, c->us);
 }
 
 // lout = J^T lin (Euclidean cotangents) for the step from state u at time t.
@@ -645,30 +636,30 @@ void fwd_step(pnop_ctx* c, const double2* u, double2* out, double t) {
 //   Fb = S_F^H lin, ub* = N*'^T (Fb/2),
 //   ubar = S_u^H (lin + ub*) + N0'^T S_F^H (lin/2 + ub*).
 // S_u^H and S_F^H share their front part (Rl for lin, R for ub*), so the
-// transposed viscous matvec runs once, on Rl + R (added by the second solve).
-// B u and everything that depends on lin alone (Rl, S_F^H lin) run on the
-// side stream while the predictor is re-run on the context stream.  N(u) and
+// velocity part of the transposed stage runs once, on lin + ub* (the second
+// solve adds Rl, the second front adds its Fin^H coefficients to lin's).
+// Everything that depends on lin alone (Rl, S_F^H lin) runs on the side
+// stream while the predictor is re-run on the context stream.  N(u) and
 // N'(u)^T share the physical u and curl u (scratch Y2).
 void adj_step(pnop_ctx* c, const double2* u, double t, const double2* lin, double2* lout) {
     Range nvtx_range("pnop:adj_step");
     const Geo& g = c->geo;
     fork_side(c);
     queue_base(c, u, t);
-    stage_bu(c, u, c->RB, c->side);
-    ck(cudaEventRecord(c->ev_bu, c->side), "record");
     stageT_front(c, lin, c->Rl, c->side);
     run(c, PNOP_K_RADIAL_BAND, 1, flops::trhs_f * c->S(),
-        [&] { pnop::launch_stageT_rhs(g, c->Rl, nullptr, 0.5, 0.0, nullptr, 0, c->Nb, c->side); },
+        [&] { pnop::launch_stageT_rhs(g, c->Rl, nullptr, 0.5, 0.0, nullptr, 0, c->Nb, nullptr, nullptr, nullptr,
+                                      c->side); },
         c->side);
     stageT_proj(c, c->Nb, c->q2, c->side);  // Nb = S_F^H lin / 2
     ck(cudaEventRecord(c->ev_t, c->side), "record");
     nonlinear(c, u, t, c->N0, c->Y2, true);  // physical u, curl u stay in Y2 for N'(u)^T below
-    stage(c, c->RB, c->N0, c->us, nullptr, c->ev_bu);
+    stage(c, u, c->N0, c->us, nullptr);
     join_side(c, c->ev_t);
     nonlinearT(c, c->us, t + c->h.ph.dt, c->Nb, c->ubs, c->Y, false);
-    stageT_front(c, c->ubs, c->R, c->stream, c->Rl);  // R = front(ub*) + front(lin)
+    stageT_front(c, c->ubs, c->R, c->stream, c->Rl, 1);  // R = front(ub*) + front(lin)
     run(c, PNOP_K_RADIAL_BAND, 1, (flops::trhs_u + flops::trhs_f) * c->S(),
-        [&] { pnop::launch_stageT_rhs(g, c->R, c->Rl, 1.0, -0.5, c->ua, 0, c->Nb, c->stream); });
+        [&] { pnop::launch_stageT_rhs(g, c->R, c->Rl, 1.0, -0.5, c->ua, 0, c->Nb, lin, c->ubs, c->ac, c->stream); });
     stageT_proj(c, c->Nb, c->q, c->stream);  // Nb = S_F^H (lin/2 + ub*)
     nonlinearT(c, u, t, c->Nb, c->ubs, c->Y2, true);
     axpby(c, 1.0, c->ua, 1.0, c->ubs, lout);
@@ -1350,6 +1341,12 @@ int pnop_context_bytes(const pnop_grid* grid, const pnop_params* params, int sna
     return PNOP_OK;
 }
 
+int pnop_device_bytes(const pnop_ctx* ctx, size_t* bytes) {
+    if (!ctx || !bytes) return PNOP_ERR_INVALID_ARG;
+    *bytes = ctx->bytes;
+    return PNOP_OK;
+}
+
 int pnop_batch_bytes(const pnop_grid* grid, const pnop_params* params, int capacity, size_t* bytes) {
     if (!grid || !params || !bytes || params->snap_budget < 1 || capacity < 1 || capacity > pnop::kMaxBatch ||
         grid->nr < 1 || grid->ntheta < 4 || grid->nz < 4)
@@ -1389,7 +1386,7 @@ int pnop_revolve_counts(int nsteps, int snaps, long long* advances, long long* s
 void pnop_destroy(pnop_ctx* ctx) {
     if (!ctx) return;
     for (auto e : ctx->ev) cudaEventDestroy(e);
-    for (cudaEvent_t e : {ctx->ev_fork, ctx->ev_bu, ctx->ev_t, ctx->ev_base})
+    for (cudaEvent_t e : {ctx->ev_fork, ctx->ev_t, ctx->ev_base})
         if (e) cudaEventDestroy(e);
     if (ctx->side) cudaStreamDestroy(ctx->side);
     if (ctx->copy) {
@@ -1481,8 +1478,9 @@ int create_impl(const pnop_grid* grid, const pnop_params* params, void* cuda_str
         c->tw.th_f = c->upload(thf);
         c->tw.z_f = c->upload(zf);
         for (double2** b : {&c->omega, &c->N0, &c->N1, &c->us, &c->ua, &c->Fb, &c->Nb, &c->ubs, &c->wb, &c->R,
-                            &c->Rl, &c->RB, &c->Nbase})
+                            &c->Rl, &c->Nbase})
             *b = c->field();
+        c->ac = (double2*)c->dalloc((size_t)nslot * d.nm * d.nk * sizeof(double2));
         if (batched) {  // per-slot state, cotangent and energies replace the sweep buffers
             c->bcur = c->field();
             c->blam = c->field();
@@ -1497,7 +1495,7 @@ int create_impl(const pnop_grid* grid, const pnop_params* params, void* cuda_str
         c->q = batched ? c->field() : (double2*)c->dalloc(c->S() * sizeof(double2));
         c->q2 = batched ? c->field() : (double2*)c->dalloc(c->S() * sizeof(double2));
         ck(cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking), "side stream");
-        for (cudaEvent_t* e : {&c->ev_fork, &c->ev_bu, &c->ev_t, &c->ev_base})
+        for (cudaEvent_t* e : {&c->ev_fork, &c->ev_t, &c->ev_base})
             ck(cudaEventCreateWithFlags(e, cudaEventDisableTiming), "event");
         const size_t cz = mixed(c) ? sizeof(float2) : sizeof(double2);
         const size_t plane = (size_t)d.nr * d.nth * d.nk * cz;
@@ -1666,6 +1664,30 @@ int pnop_mode_energy(pnop_ctx* ctx, const void* u, double* spectrum) {
             [&] { pnop::launch_mode_energy(ctx->geo, (const double2*)u, ctx->d_spec, ctx->stream); });
         ck(cudaMemcpyAsync(spectrum, ctx->d_spec, n * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream), "copy");
         wait_stream(ctx, "mode energy");
+        return PNOP_OK;
+    });
+}
+
+int pnop_resolution(pnop_ctx* ctx, const void* u, double E0, double* e_M, double* e_K) {
+    return guarded(ctx, [&]() -> int {
+        if (!u || !e_M || !e_K || !std::isfinite(E0)) throw Status(PNOP_ERR_INVALID_ARG, "bad arguments");
+        if (!ctx->d_spec) ctx->d_spec = (double*)ctx->dalloc(2 * (size_t)ctx->geo.nm * ctx->geo.nk * sizeof(double));
+        const double2* f = (const double2*)u;
+        run(ctx, PNOP_K_REDUCE, 1, 3.0 * ctx->h.d.nr * (2.0 * ctx->geo.nk + ctx->geo.nm),
+            [&] { pnop::launch_resolution(ctx->geo, f, ctx->d_spec, ctx->stream); });
+        double ref = E0;
+        if (!(E0 > 0)) {
+            inner_dev(ctx, f, f, ctx->dscal);
+            ck(cudaMemcpyAsync(&ref, ctx->dscal, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream), "copy");
+        }
+        double e[2] = {0, 0};
+        ck(cudaMemcpyAsync(e, ctx->d_spec, 2 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream), "copy");
+        wait_stream(ctx, "resolution");
+        if (!(E0 > 0)) ref *= 0.5;
+        if (!(ref > 0) || !std::isfinite(ref) || !std::isfinite(e[0]) || !std::isfinite(e[1]))
+            throw Status(PNOP_ERR_NONFINITE, "resolution: no finite positive reference energy");
+        *e_M = e[0] / ref;
+        *e_K = e[1] / ref;
         return PNOP_OK;
     });
 }

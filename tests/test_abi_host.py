@@ -177,3 +177,11 @@ def test_noalloc_energy_rejects_oversized_fields_without_a_device(L):
         rc = L.lib.pnop_energy_noalloc(dummy, ctypes.cast(dummy, ctypes.POINTER(ctypes.c_double)), nr, M, K, 10.0,
                                        ctypes.byref(e), None)
         assert rc == -1, (nr, M, K)
+
+
+def test_fma_probe_rejects_bad_arguments_without_a_device(L):
+    import ctypes
+    t = ctypes.c_double()
+    for prec, secs in ((0, 0.0), (0, -1.0), (0, 11.0), (7, 0.1)):
+        assert L.lib.pnop_measure_fma_peak(prec, secs, None, ctypes.byref(t)) == -1
+    assert L.lib.pnop_measure_fma_peak(0, 0.1, None, None) == -1

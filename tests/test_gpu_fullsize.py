@@ -143,3 +143,35 @@ def test_gradient_bitwise_across_budgets_and_mixed_error_budget(env, fields):
     cos = ip(gm3[1], gd[1]) / math.sqrt(ip(gm3[1], gm3[1]) * ip(gd[1], gd[1]))
     assert abs(gm3[0] / gd[0] - 1) <= 1e-5
     assert cos >= 0.99999
+
+
+@pytest.fixture(scope="module")
+def nonlinear_ref(env, fields):
+    """The oracle's N(u) and N'(u)^T nb at the full grid (a few einsums over the
+    exact DFT matrices: seconds in numpy), u and nb with every mode excited."""
+    torch, L = env
+    r, _, v, w = fields
+    o = po.Oracle(po.Params(nr=NR, M=M, K=K, Lz=LZ, Re=RE, dt=DT, Wo=WO, A=A))
+    u = o.scale_to(v, 1.0)
+    nb = o.scale_to(w, 1.0)
+    t = TAU0 + 0.37
+    return u, nb, t, o.nonlinear(u, t), o.nonlinearT(u, t, nb)
+
+
+@pytest.mark.parametrize("precision,tol", [(0, 1e-10), (1, 1e-5)])
+def test_nonlinear_term_and_transpose_match_the_oracle_at_full_size(env, nonlinear_ref, precision, tol):
+    """OP_NONLINEAR and OP_NONLINEAR_T through the two-pass 96- and 384-point
+    transform kernels the bench times, element by element against the oracle
+    (max-norm relative).  FP64: 1e-10.  Mixed: FP32 transforms of lengths 96
+    and 384 round each of their ~log2 N butterfly levels at 2^-24, about 1e-6
+    of the largest value; 1e-5 leaves a factor 10 over that."""
+    torch, L = env
+    u, nb, t, ref, refT = nonlinear_ref
+    ctx = ctx_for(L, precision)
+    out = torch.zeros(ctx.shape, dtype=torch.complex128, device="cuda")
+    ctx.pnop_apply(L.OP_NONLINEAR, dev(torch, u), None, out, t)
+    e1 = np.abs(out.cpu().numpy() - ref).max() / np.abs(ref).max()
+    ctx.pnop_apply(L.OP_NONLINEAR_T, dev(torch, u), dev(torch, nb), out, t)
+    e2 = np.abs(out.cpu().numpy() - refT).max() / np.abs(refT).max()
+    ctx.close()
+    assert e1 < tol and e2 < tol, (e1, e2)

@@ -6,6 +6,7 @@ import math
 import numpy as np
 import pytest
 
+from oracle import pipe_oracle as po
 from paper_2509_10103_gb300 import synth
 
 pytestmark = pytest.mark.gpu
@@ -48,6 +49,26 @@ def test_host_tier_gradient_is_bitwise_single_level(L, precision):
     assert ht["host_stores"] == nf and ht["host_loads"] == nf
     assert st1[0] == adv < st0[0]           # fewer forward steps than the single level
     assert st1[1] == st0[1] == N            # one adjoint step per step
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_host_tier_gradient_matches_the_oracle(L, precision):
+    """The two-level sweep against the oracle's store-all gradient (not only
+    against the single-level GPU sweep): FP64 to 1e-10, mixed precision within
+    the mixed-precision budget (gain 1e-5, cosine 0.99999)."""
+    N, s, H, E0 = 30, 2, 10, 1e-4
+    (gain, g, st, ht) = grads(L, 12, 8, 12, 10.0, N, s, H, 0.0, precision)[1]
+    assert ht["host_checkpoints"] > 0
+    o = po.Oracle(po.Params(nr=12, M=3, K=5, Lz=10.0, Re=2000.0, dt=0.01, Wo=8.0, A=1.0))
+    u0 = o.scale_to(synth.random_field(o.r, 3, 5, 10.0, seed=0), E0)
+    ET, gref = o.gradient(u0, 0.0, N)
+    if precision == 0:
+        assert abs(gain / (ET / E0) - 1) < 1e-10
+        assert np.abs(g - gref).max() <= 1e-10 * np.abs(gref).max()
+    else:
+        cos = o.inner(g, gref) / math.sqrt(o.inner(g, g) * o.inner(gref, gref))
+        assert abs(gain / (ET / E0) - 1) <= 1e-5
+        assert cos >= 0.99999
 
 
 def test_host_tier_full_size_store_all_on_host(L):

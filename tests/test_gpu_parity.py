@@ -202,6 +202,20 @@ def test_mode_energy_spectrum(case, request):
 
 
 @pytest.mark.parametrize("case", ["small", "ragged"])
+def test_resolution_measures(case, request):
+    """pnop_resolution (device reduction) against Oracle.resolution: e_M and
+    e_K relative 1e-12, with a given E0 and with the field's own energy."""
+    c = request.getfixturevalue(case)
+    p = c.o.p
+    u = c.o.scale_to(synth.random_field(c.o.r, p.M, p.K, p.Lz, seed=19, decay=1.5), 2e-3)
+    for E0 in (1e-3, -1.0):
+        eM, eK = c.ctx.pnop_resolution(dev(u), E0)
+        rM, rK = c.o.resolution(u, E0 if E0 > 0 else c.o.energy(u))
+        assert rM > 0 and rK > 0
+        assert abs(eM / rM - 1) < 1e-12 and abs(eK / rK - 1) < 1e-12
+
+
+@pytest.mark.parametrize("case", ["small", "ragged"])
 def test_admissible_projection(case, request, L):
     from oracle import adjoint_looping as al
     c = request.getfixturevalue(case)

@@ -396,6 +396,41 @@ def test_mode_energy_and_resolution_measures_follow_their_definitions():
     assert abs(Gz - float(np.sum(0.5 * o.What * np.abs(u[2]) ** 2)) / E) < 1e-13
 
 
+def test_oracle_resolution_measures_on_fields_with_known_shells():
+    """Oracle.resolution against facts fixed by the definitions: the full
+    spectrum holds the whole energy; a field living only in the mode (M, k0)
+    shares it equally with the conjugate partner (-M, -k0), so e_M = 1/2 and
+    e_K = 0 for k0 < K; one only in (m0, K) has e_K = 1/2 likewise; removing
+    those shells gives zero; and the values match the brute-force sums over
+    the Hermitian extension."""
+    from paper_2509_10103_gb300 import synth
+    p = po.Params(nr=10, M=3, K=4, Lz=7.0, Re=1000.0, dt=0.01)
+    o = po.Oracle(p)
+    u = synth.random_field(o.r, p.M, p.K, p.Lz, seed=8, decay=1.5)
+    E = o.energy(u)
+    f = o.full_spectrum(u)
+    assert f.shape == (3, p.nr, 2 * p.M + 1, 2 * p.K + 1)
+    W = 0.5 * (2 * math.pi * p.Lz) * o.W
+    assert abs(np.einsum('j,cjmk->', W, np.abs(f) ** 2) / E - 1) < 1e-13
+    eM, eK = o.resolution(u, E)
+    bM = sum(float(np.sum(W * np.sum(np.abs(u[:, :, p.M + p.M, k] if k >= 0 else np.conj(u[:, :, 0, -k])) ** 2,
+                                         axis=0))) for k in range(-p.K, p.K + 1)) / E
+    assert abs(eM / bM - 1) < 1e-12
+    from paper_2509_10103_gb300 import diagnostics
+    assert abs(eK / diagnostics.resolution_measures(o.mode_energy(u), E)[1] - 1) < 1e-12
+    only = np.zeros_like(u)
+    only[:, :, 2 * p.M, 2] = u[:, :, 2 * p.M, 2]
+    assert o.resolution(only, o.energy(only)) == pytest.approx((0.5, 0.0), abs=1e-14)
+    only = np.zeros_like(u)
+    only[:, :, 1, p.K] = u[:, :, 1, p.K]
+    assert o.resolution(only, o.energy(only)) == pytest.approx((0.0, 0.5), abs=1e-14)
+    cut = u.copy()
+    cut[:, :, 0, :] = 0
+    cut[:, :, 2 * p.M, :] = 0
+    cut[:, :, :, p.K] = 0
+    assert o.resolution(cut, E) == (0.0, 0.0)
+
+
 def test_linear_step_of_steady_pipe_flow_has_no_growing_mode():
     """Hagen-Poiseuille flow is linearly stable: the per-mode step map at
     Re = 1750 has every eigenvalue inside the unit circle (the rotational form
