@@ -406,15 +406,50 @@ def roofline(L, res, mixed, peaks, pk_src, alu_measured=None):
     return base
 
 
+def optimise_full_report(L, torch, E0_opt=1e-5, iters=10, precision=None):
+    """Adjoint looping (pnop_optimise, Section 2.3, Eq. 2.13-2.15) on the full
+    nonlinear optimisation workload: the 64x64x256 grid and physics above,
+    start at tau0 = T/4 (deceleration), horizon T/4 = 19,635 steps of
+    dt = 0.0025, seeded oblique initial guess, mixed precision, checkpoint
+    pool sized from free HBM (snap_budget 0).  Reports G per iteration and the
+    seconds per gradient."""
+    import numpy as np
+    precision = L.PNOP_MIXED if precision is None else precision
+    T = 2.0 * math.pi * RE / WO ** 2
+    nsteps = int(round(0.25 * T / DT))
+    ctx = L.Context(NR, NTHETA, NZ, LZ, RE, DT, WO, AMP, TAU0, precision, 0)
+    r = np.array(ctx.pnop_grid_points())
+    u = torch.from_numpy(make_u0(r)).to("cuda")
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    stats, hist = ctx.pnop_optimise(u, E0_opt, nsteps * DT, iters, 1e-8)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    adv, nadj, stores = ctx.pnop_gradient_stats()
+    out = {"workload": f"nr={NR} ntheta={NTHETA} nz={NZ}, Lz={LZ:g}, Re={RE:g}, Wo={WO:g}, A={AMP:g}, tau0=T/4,"
+                       f" horizon T/4 = {nsteps} steps of dt={DT:g}, oblique seed, E0={E0_opt:g}",
+           "precision": "mixed" if precision == L.PNOP_MIXED else "fp64",
+           "iterations": stats["iterations"], "gradients": stats["gradients"], "forward_evals": stats["forward_evals"],
+           "converged": stats["converged"], "gain_history": hist, "wall_s": wall,
+           # every gradient is one forward sweep (checkpoints stored) plus one adjoint sweep; rejected
+           # line-search trials add forward sweeps, counted in forward_evals
+           "seconds_per_gradient": wall / max(1, stats["gradients"]),
+           "advances_last_sweep": adv, "adjoint_steps_last_sweep": nadj,
+           "device_gb": ctx.pnop_device_bytes() / 2 ** 30}
+    ctx.close()
+    return out
+
+
 # ------------------------------------------------------------------ serving stream
 SERVE_RES = ((32, 32, 64, 10.0), (48, 48, 128, 25.0), (64, 64, 256, 50.0))
 
 
-def _serving_requests(L, nreq, seed, arrivals):
+def _serving_requests(L, nreq, seed, arrivals, full=False):
     """Seeded requests: resolution from SERVE_RES, Re in [1500, 3000], A in
-    [0.5, 1.5], Wo in [4, 18], E0 = 10^U(-7,-4), dt = 0.005 and 10-50 steps
-    (horizons shortened from 1-10 time units so the stream stays within a
-    minute), mixed precision, 8 checkpoint slots."""
+    [0.5, 1.5], Wo in [4, 18], E0 = 10^U(-7,-4), dt = 0.005, mixed precision.
+    full: horizons of 1-10 time units (200-2000 steps), 64 checkpoint slots
+    each; otherwise 10-50 steps (shortened so that the stream stays within a
+    minute) and 8 slots."""
     import numpy as np
     from paper_2509_10103_gb300 import serving, synth
     rng = np.random.default_rng(seed)
@@ -427,33 +462,36 @@ def _serving_requests(L, nreq, seed, arrivals):
     reqs = []
     for i in range(nreq):
         nr, nth, nz, lz = SERVE_RES[int(rng.integers(len(SERVE_RES)))]
-        n = int(rng.integers(10, 51))
+        n = int(rng.integers(200, 2001)) if full else int(rng.integers(10, 51))
         reqs.append(serving.Request(rid=i, nr=nr, ntheta=nth, nz=nz, Lz=lz, Re=float(rng.uniform(1500, 3000)),
                                     Wo=float(rng.uniform(4, 18)), A=float(rng.uniform(0.5, 1.5)),
                                     tau0=float(rng.uniform(0, 100)), E0=float(10 ** rng.uniform(-7, -4)),
                                     horizon=n * 0.005, dt=0.005, u0=fields[(nr, nth, nz)], precision=L.PNOP_MIXED,
-                                    snaps=8, arrival=float(arrivals[i])))
+                                    snaps=64 if full else 8, arrival=float(arrivals[i])))
     return reqs
 
 
-def serving_report(L, nreq=256, probe=48, load=0.7, seed=0, budget=40 << 30, max_active=8, batched=False):
+def serving_report(L, nreq=256, probe=48, load=0.7, seed=0, budget=40 << 30, max_active=8, batched=False,
+                   full=False):
     """Capacity probe, then a Poisson stream at `load` x that capacity.
 
     The probe submits `probe` requests at once and takes completed / wall as
     the capacity (requests/s).  The stream then offers `nreq` requests with
     exponential gaps of mean 1 / (load x capacity) and reports p50/p99
     latency (arrival to result on the host) and throughput.  batched: the
-    BatchServer (max_active slots per batch of one resolution, shared
-    launches) instead of one context and stream per request."""
+    BatchServer (max_active slots per batch of one resolution, more batches
+    of a resolution as its requests need them, shared launches) instead of one
+    context and stream per request.  full: the stated horizons of 1-10 time
+    units (see _serving_requests)."""
     import numpy as np
     from paper_2509_10103_gb300 import serving
-    reqs = _serving_requests(L, probe, seed + 1, np.zeros(probe))
+    reqs = _serving_requests(L, probe, seed + 1, np.zeros(probe), full)
     t0 = time.perf_counter()
     res, _ = serving.serve_stream(reqs, hbm_budget=budget, max_active=max_active, batched=batched)
     cap = sum(r.error is None for r in res) / (time.perf_counter() - t0)
     rate = load * cap
     gaps = np.random.default_rng(seed + 2).exponential(1.0 / rate, nreq)
-    reqs = _serving_requests(L, nreq, seed, np.cumsum(gaps))
+    reqs = _serving_requests(L, nreq, seed, np.cumsum(gaps), full)
     t0 = time.perf_counter()
     res, srv = serving.serve_stream(reqs, hbm_budget=budget, max_active=max_active, batched=batched)
     wall = time.perf_counter() - t0
@@ -467,9 +505,13 @@ def serving_report(L, nreq=256, probe=48, load=0.7, seed=0, budget=40 << 30, max
             "steps_per_s": steps / wall, "p50_latency_s": lat["p50_s"], "p99_latency_s": lat["p99_s"],
             "mean_latency_s": lat.get("mean_s"), "peak_active": srv.peak_active,
             "peak_admitted_gb": srv.peak_bytes / 2 ** 30, "hbm_budget_gb": budget / 2 ** 30, "wall_s": wall,
-            "horizons": "10-50 steps of dt=0.005", "arrivals": f"Poisson at {load} x measured capacity",
+            "horizons": "200-2000 steps of dt=0.005 (1-10 time units), 64 checkpoint slots" if full else
+                        "10-50 steps of dt=0.005, 8 checkpoint slots",
+            "arrivals": f"Poisson at {load} x measured capacity",
             "server": "batched launches per resolution (BatchServer)" if batched else "one context and stream per request",
-            "peak_requests_in_one_batch": getattr(srv, "peak_batch", None)}
+            "peak_requests_in_one_batch": getattr(srv, "peak_batch", None),
+            "peak_batches_of_one_resolution": getattr(srv, "peak_batches_per_kind", None),
+            "batches_created": getattr(srv, "batches_made", None)}
 
 
 def batch_report(L, torch, nsteps=20, snaps=8, seed=7, only=None):
@@ -652,6 +694,11 @@ def main():
                     help="skip the single-step timings and the budget sweep (profiling runs)")
     ap.add_argument("--precision", default="both", choices=["both", "mixed", "fp64"],
                     help="which path(s) to time; 'fp64' reports the FP64 path as the main line")
+    ap.add_argument("--optimise-full", action="store_true",
+                    help="print only the adjoint-looping run on the full deceleration horizon (19,635 steps)")
+    ap.add_argument("--opt-iters", type=int, default=10)
+    ap.add_argument("--serving-full", action="store_true",
+                    help="print only the serving reports (both servers) at the stated horizons of 1-10 time units")
     ap.add_argument("--only-batched", default=None, metavar="RES",
                     help="print only the batched-gradient comparison at one serving resolution (e.g. 32x32x64)")
     args = ap.parse_args()
@@ -669,6 +716,14 @@ def main():
     barrier(ws)
     from paper_2509_10103_gb300 import _lib as L
 
+    if args.optimise_full:
+        print(json.dumps({"optimise_full": optimise_full_report(L, torch, iters=args.opt_iters)}))
+        return 0
+    if args.serving_full:
+        out = {"serving_full": serving_report(L, probe=32, budget=160 << 30, full=True),
+               "serving_full_batched": serving_report(L, probe=32, budget=160 << 30, batched=True, full=True)}
+        print(json.dumps(out))
+        return 0
     if args.only_batched:
         res = tuple(int(x) for x in args.only_batched.split("x"))
         print(json.dumps(batch_report(L, torch, only=res)))

@@ -327,8 +327,9 @@ int pnop_profile(pnop_ctx* ctx, unsigned class_mask);
  * FMAs.  This is the denominator of the ALU roofline of the library's
  * FP64-bound kernels (the paper gives no performance figures; this is a
  * measurement utility).  Every SM runs independent FMA chains for about
- * `seconds` (0 < seconds <= 10) per launch; the best of three launches is
- * returned in *tflops (host).  The work is ordered on cuda_stream (NULL =
+ * `seconds` (0 < seconds <= 10) per launch, in nine configurations (4, 8 or
+ * 16 chains per thread, 2, 4 or 8 blocks of 256 threads per SM), three
+ * launches each; the best rate is returned in *tflops (host).  The work is ordered on cuda_stream (NULL =
  * legacy default stream) and the call synchronises it.  No device memory is
  * allocated.  Bad arguments return PNOP_ERR_INVALID_ARG, CUDA failures
  * PNOP_ERR_CUDA. */

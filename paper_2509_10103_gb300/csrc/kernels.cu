@@ -248,7 +248,8 @@ __global__ void k_stage_div(Geo g, const double2* __restrict__ F, double2* __res
 // copy.  Each of the 2 kSK threads sweeps the real or the imaginary part of one
 // system (the matrices are real).  Terms are accumulated oldest first, so the
 // dependence from one row to the next is a single FMA.
-constexpr int kRC = 8;  // rows per staged chunk
+constexpr int kRC = 8;        // rows per staged chunk
+constexpr int kRegRows = 64;  // grids up to this many radial points keep their columns in registers
 
 __device__ __forceinline__ void cp_async16(void* sm, const void* gm) {
     const unsigned a = (unsigned)__cvta_generic_to_shared(sm);
@@ -374,6 +375,129 @@ __global__ void __launch_bounds__(2 * kSK) k_band_solve(Geo g, const double* __r
     }
 }
 
+// The same two-sweep solve with each thread's column held in registers
+// (grids of at most MAXR radial points).  The column stays in x[0..MAXR): the
+// forward sweep reads its lower neighbours and the backward sweep its upper
+// neighbours straight from registers (every index is a compile-time constant
+// after unrolling), so no shared-memory round trip sits on the dependent
+// chain of a row; shared memory holds only the staged coefficient rows.  The
+// arithmetic and its order are those of k_band_solve: the results are the
+// same to the last bit (up to the sign of zero).
+template <int NL, int NU, bool DIAG1, int MAXR>
+__global__ void __launch_bounds__(2 * kSK) k_band_solve_reg(Geo g, const double* __restrict__ fac, size_t fac_stride,
+                                                      double2* __restrict__ X, const double2* __restrict__ add,
+                                                      int helm, int zero_row0) {
+    constexpr int NC1 = NL + (DIAG1 ? 1 : 0);
+    constexpr int NC2 = kB - NC1;
+    constexpr int NCM = NC1 > NC2 ? NC1 : NC2;
+    constexpr int MAXCH = MAXR / kRC;
+    static_assert(MAXR % kRC == 0, "whole chunks");
+    extern __shared__ __align__(16) unsigned char smem[];
+    double* Cb = reinterpret_cast<double*>(smem);  // [2][kRC][NCM][kSK]
+    int bi = blockIdx.x;
+    const int kb = bi % g.ntile;
+    bi /= g.ntile;
+    const int im = bi % g.nm, v = bi / g.nm;
+    const int m = im - g.M;
+    const int mv = helm ? (v == 0 ? m + 1 : (v == 1 ? m - 1 : m)) : m;
+    const int k0 = kb * kSK;
+    const size_t S = (size_t)g.nr * g.nm * g.nk;
+    const int slot = g.slot[blockIdx.y];
+    const size_t off = (size_t)slot * g.fs;
+    fac += (size_t)slot * fac_stride;
+    X += off;
+    add = moved(add, off);
+    const double* T1 = fac + ((size_t)abs(mv) * g.ntile + kb) * (size_t)g.nr * kB * kSK;
+    const double* T2 = T1 + (size_t)g.nr * NC1 * kSK;
+    const int tid = threadIdx.x, sy = tid % kSK, comp = tid / kSK;
+    const int nr = g.nr, nch = (nr + kRC - 1) / kRC;
+    const bool on = k0 + sy < g.nk;
+    // this thread's column: the real or imaginary part of system (v, m, k0 + sy)
+    const double* xs = reinterpret_cast<const double*>(X + (size_t)v * S) + comp;
+    double x[MAXR];
+#pragma unroll
+    for (int j = 0; j < MAXR; ++j) x[j] = (on && j < nr) ? xs[2 * sidx(g, j, im, k0 + sy)] : 0.0;
+    auto stage = [&](int t) {  // chunk t of the sweep sequence into buffer t & 1
+        if (t >= 2 * nch) return;
+        const bool fwd = t < nch;
+        const int c = fwd ? t : 2 * nch - 1 - t;
+        const int rows = min(kRC, nr - c * kRC);
+        const int nc = fwd ? NC1 : NC2;
+        const double* src = (fwd ? T1 : T2) + (size_t)c * kRC * nc * kSK;
+        double* dst = Cb + (size_t)(t & 1) * kRC * NCM * kSK;
+        const int nseg = rows * nc * (kSK / 2);
+        for (int i = tid; i < nseg; i += 2 * kSK) cp_async16(dst + 2 * i, src + 2 * i);
+    };
+    stage(0);
+    cp_async_commit();
+#pragma unroll
+    for (int t = 0; t < MAXCH; ++t) {
+        if (t < nch) {
+            stage(t + 1);
+            cp_async_commit();
+            cp_async_wait1();
+            __syncthreads();
+            const double* C = Cb + (size_t)(t & 1) * kRC * NCM * kSK + sy;
+#pragma unroll
+            for (int r = 0; r < kRC; ++r) {
+                const int j = t * kRC + r;
+                if (j < nr) {
+                    double val = x[j];
+                    const bool full = !(NL == 8 && j > 8);
+#pragma unroll
+                    for (int e = 0; e < NL; ++e) {
+                        const int jj = j - NL + e;  // w1[e] of k_band_solve: oldest first
+                        if (jj >= 0 && (full || e >= NL - 4)) val = fma(-C[(r * NC1 + e) * kSK], x[jj >= 0 ? jj : 0], val);
+                    }
+                    if (DIAG1) val *= C[(r * NC1 + NL) * kSK];
+                    x[j] = val;
+                }
+            }
+            __syncthreads();
+        }
+    }
+#pragma unroll
+    for (int c = MAXCH - 1; c >= 0; --c) {
+        if (c < nch) {
+            const int t = 2 * nch - 1 - c;
+            stage(t + 1);
+            cp_async_commit();
+            cp_async_wait1();
+            __syncthreads();
+            const double* C = Cb + (size_t)(t & 1) * kRC * NCM * kSK + sy;
+            constexpr int O = DIAG1 ? 0 : 1;
+#pragma unroll
+            for (int r = kRC - 1; r >= 0; --r) {
+                const int j = c * kRC + r;
+                if (j < nr) {
+                    double val = x[j];
+                    const bool full = !(NU == 8 && j >= 4);
+#pragma unroll
+                    for (int e = NU - 1; e >= 0; --e) {
+                        const int jj = j + 1 + e;  // w2[e] of k_band_solve: nearest first (0 beyond nr)
+                        if (jj < MAXR && (full || e < 4)) val = fma(-C[(r * NC2 + O + e) * kSK], x[jj < MAXR ? jj : 0], val);
+                    }
+                    if (!DIAG1) val *= C[(r * NC2) * kSK];
+                    x[j] = val;
+                }
+            }
+            __syncthreads();
+        }
+    }
+    if (!on) return;
+    double* xo = reinterpret_cast<double*>(X + (size_t)v * S) + comp;
+    const double* ad = add ? reinterpret_cast<const double*>(add + (size_t)v * S) + comp : nullptr;
+#pragma unroll
+    for (int j = 0; j < MAXR; ++j) {
+        if (j < nr) {
+            const size_t o = 2 * sidx(g, j, im, k0 + sy);
+            double val = (zero_row0 && j == 0) ? 0.0 : x[j];
+            if (ad) val += ad[o];
+            xo[o] = val;
+        }
+    }
+}
+
 // R_v = F'_v [+ (2/dt) (T u)_v] for v = +, -, z (rows j >= 1), F' = F - grad p;
 // wall row R_v = (T u)_v (0 without u).  T u: u+ = u_r + i u_theta,
 // u- = u_r - i u_theta, u_z.  With A_v + B_v = 2 I / dt this right-hand side
@@ -421,8 +545,13 @@ __global__ void k_stage_rhs(Geo g, const double2* __restrict__ u, const double2*
 // Per-mode kernels of the wall conditions run on blocks of kFK consecutive k
 // (x) times kFJ radial groups (y) of one m: a per-mode scalar is reduced over
 // j into shared memory in a fixed order (deterministic), then every thread
-// applies it to its rows j = y, y + kFJ, ...
-constexpr int kFK = 16, kFJ = 16;
+// applies it to its rows j = y, y + kFJ, ...  Fields and the influence table
+// are k-fastest, so a warp reads 32 consecutive k of one row.
+constexpr int kFK = 32, kFJ = 8;
+// influence response component c (0: u_r, 1: u_theta / i, 2: u_z / i) at row j of mode (im, k)
+__device__ __forceinline__ double infl_at(const double* h, const Geo& g, int im, int c, int j, int k) {
+    return __ldg(h + (((size_t)im * 3 + c) * g.nr + j) * g.nk + k);
+}
 
 // out = [addto +] back to (r, theta, z) [- usub] with the influence
 // correction (div u = 0 at the wall) or, for mode (0,0), flux correction and
@@ -470,7 +599,7 @@ __global__ void __launch_bounds__(kFK* kFJ) k_stage_finish(Geo g, const double2*
     double2 a0 = red[0][tx];
 #pragma unroll
     for (int i = 1; i < kFJ; ++i) a0 = make_double2(a0.x + red[i][tx].x, a0.y + red[i][tx].y);
-    const double* h = slot_infl(g, slot) + ((size_t)im * g.nk + k) * 3 * g.nr;
+    const double* h = slot_infl(g, slot);
     const double* fg = slot_fluxg(g, slot);
     for (int j = ty; j < g.nr; j += kFJ) {
         const size_t o = sidx(g, j, im, k);
@@ -488,7 +617,8 @@ __global__ void __launch_bounds__(kFK* kFJ) k_stage_finish(Geo g, const double2*
             uz = dfma(fg[j] * (-g.flux_inv[slot]), a0, uz);
             ur = make_double2(0, 0);
         } else {
-            const double h0 = h[j], h1 = h[g.nr + j], h2 = h[2 * g.nr + j];
+            const double h0 = infl_at(h, g, im, 0, j, k), h1 = infl_at(h, g, im, 1, j, k),
+                         h2 = infl_at(h, g, im, 2, j, k);
             ur = dfma(h0, a0, ur);
             ut = make_double2(ut.x - h1 * a0.y, ut.y + h1 * a0.x);
             uz = make_double2(uz.x - h2 * a0.y, uz.y + h2 * a0.x);
@@ -521,7 +651,7 @@ __global__ void __launch_bounds__(kFK* kFJ) k_stageT_finish(Geo g, const double2
     un += off;
     R += off;
     const bool on = k < g.nk, mean = (m == 0 && k == 0);
-    const double* h = slot_infl(g, slot) + ((size_t)im * g.nk + (on ? k : 0)) * 3 * g.nr;
+    const double* h = slot_infl(g, slot);
     const double* fg = slot_fluxg(g, slot);
     double2 part = make_double2(0, 0);
     if (on) {
@@ -531,9 +661,11 @@ __global__ void __launch_bounds__(kFK* kFJ) k_stageT_finish(Geo g, const double2
                 part = dfma(fg[j], un[o + 2 * S], part);
             } else {
                 const double2 a = un[o], b = un[o + S], c = un[o + 2 * S];
+                const double h0 = infl_at(h, g, im, 0, j, k), h1 = infl_at(h, g, im, 1, j, k),
+                             h2 = infl_at(h, g, im, 2, j, k);
                 // infl0 a - i infl1 b - i infl2 c
-                part.x += h[j] * a.x + h[g.nr + j] * b.y + h[2 * g.nr + j] * c.y;
-                part.y += h[j] * a.y - h[g.nr + j] * b.x - h[2 * g.nr + j] * c.x;
+                part.x += h0 * a.x + h1 * b.y + h2 * c.y;
+                part.y += h0 * a.y - h1 * b.x - h2 * c.x;
             }
         }
     }
@@ -983,6 +1115,19 @@ void launch_baseT(const Geo& g, const double2* nb, double2* ub, cudaStream_t s) 
 static void launch_band_solve(const Geo& g, const double* fac, size_t fac_stride, double2* X, const double2* add,
                               int helm, int trans, int zero_row0, cudaStream_t s) {
     const dim3 nblocks((unsigned)((helm ? 3 : 1) * g.nm * g.ntile), (unsigned)g.nb);
+    if (g.nr <= kRegRows) {  // columns in registers
+        const size_t sm = 2 * (size_t)kRC * 9 * kSK * sizeof(double);
+        if (!trans) {
+            smem_limit((const void*)k_band_solve_reg<4, 8, false, kRegRows>);
+            k_band_solve_reg<4, 8, false, kRegRows><<<nblocks, 2 * kSK, sm, s>>>(g, fac, fac_stride, X, add, helm,
+                                                                                 zero_row0);
+        } else {
+            smem_limit((const void*)k_band_solve_reg<8, 4, true, kRegRows>);
+            k_band_solve_reg<8, 4, true, kRegRows><<<nblocks, 2 * kSK, sm, s>>>(g, fac, fac_stride, X, add, helm,
+                                                                                zero_row0);
+        }
+        return;
+    }
     const size_t sm = (size_t)g.nr * kSK * sizeof(double2) + 2 * (size_t)kRC * 9 * kSK * sizeof(double);
     if (!trans) {
         smem_limit((const void*)k_band_solve<4, 8, false>);

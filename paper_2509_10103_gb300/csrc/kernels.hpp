@@ -26,7 +26,7 @@ struct Geo {
     const double* facP;  // M+1 pressure matrices, same layout
     const double* facHT; // transposed-solve rows, tiled (9 forward | 4 backward columns)
     const double* facPT;
-    const double* infl;  // [nm][nk][3][nr]
+    const double* infl;  // [nm][3][nr][nk] (k fastest)
     const double* fluxg; // [nr]
     const double2* Uh;   // [nr]
     const double2* dUh;  // [nr]

@@ -480,11 +480,13 @@ bool build_operators(HostOps& h, std::string& err, bool reuse_pressure) {
                 zero_t[t] = 1;
                 return;
             }
-            double* out = &h.infl[(((size_t)im * nk + k) * 3) * nr];
+            // k fastest: [im][component][j][k], so that the device reads it
+            // coalesced across the k of a block
+            double* out = &h.infl[(size_t)im * 3 * nr * nk + k];
             for (int j = 0; j < nr; ++j) {
-                out[j] = -hr[j] / delta;
-                out[nr + j] = -hti[j] / delta;
-                out[2 * nr + j] = -fz[j] / delta;
+                out[(size_t)j * nk] = -hr[j] / delta;
+                out[((size_t)nr + j) * nk] = -hti[j] / delta;
+                out[((size_t)2 * nr + j) * nk] = -fz[j] / delta;
             }
         }
     });

@@ -56,7 +56,7 @@ struct HostOps {
     int ntile = 0;
     std::vector<double> facH, facHT;            // M+2 matrices (per |m'|, k)  Helmholtz
     std::vector<double> facP, facPT;            // M+1 matrices (per |m|, k)   pressure
-    std::vector<double> infl;                   // [nm][nk][3][nr] influence response, pre-scaled by -1/delta
+    std::vector<double> infl;                   // [nm][3][nr][nk] influence response, pre-scaled by -1/delta
     std::vector<double> fluxg;                  // [nr] flux response of mode (0,0)
     double flux_inv = 0;                        // 1 / sum_j W_j g_j
     std::vector<std::complex<double>> Uh, dUh;  // [nr] oscillatory base-flow profiles

@@ -225,18 +225,22 @@ class Server:
 class BatchServer:
     """Continuous batching with shared launches.
 
-    Requests of one (grid, precision, checkpoint slots) share a pnop_batch of
-    `slots` request slots: every kernel of a step runs once for all requests
-    of that batch taking that kind of step.  A driver thread takes arrivals in
-    order, has their host operators built on a small thread pool
+    Requests of one kind (grid, precision, checkpoint slots) run in pnop_batch
+    objects of `slots` request slots each: every kernel of a step runs once for
+    all requests of a batch taking that kind of step.  A driver thread takes
+    arrivals in order, has their host operators built on a small thread pool
     (pnop_batch_prepare, which may run beside the device work), admits
-    prepared requests into free slots (first come, first served per batch),
+    prepared requests into free slots (first come, first served per kind),
     keeps up to `rounds` rounds of `ticks` batched steps queued per batch
-    (without blocking on the device), and collects finished requests.  A
-    batch's device memory (about `slots` contexts, pnop_batch_bytes) is
-    allocated when the first request of its kind arrives and counted against
-    the HBM budget; a batch with no request left is released when another
-    kind needs the memory.
+    (without blocking on the device), and collects finished requests.
+
+    Slots follow the arrival mix: when every slot of a kind is busy and more
+    of its requests are waiting, another batch of that kind is created if the
+    HBM budget allows (up to `max_batches_per_kind`, default unlimited), so a
+    resolution that receives more requests gets more slots.  A batch's device
+    memory (pnop_batch_bytes) is counted against the budget from its creation;
+    idle batches are released when another batch needs the memory, first
+    those of kinds with nothing waiting.
     Each request gets bitwise the result it gets alone (the batched steps are
     the single-request steps per slot).
 
@@ -251,7 +255,7 @@ class BatchServer:
 
     def __init__(self, hbm_budget: int, slots: int = 8, ticks: int = 4, device: int = 0, batch_factory=None,
                  sizer=None, rounds: int = 3, workers: int = 4, opt_active: int = 2, opt_runner=None,
-                 opt_sizer=None):
+                 opt_sizer=None, max_batches_per_kind: Optional[int] = None):
         """batch_factory(request, slots, stream) -> batch object (pnop_batch_prepare / submit_prepared /
         run / poll / result / close, as _lib.Batch) and sizer(request, slots) -> bytes replace the GPU
         batch and the library estimate (host-side tests)."""
@@ -260,6 +264,7 @@ class BatchServer:
         self.slots = slots
         self.ticks = ticks
         self.max_rounds = rounds
+        self.max_batches = max_batches_per_kind
         self.device = device
         self.factory = batch_factory
         self.sizer = sizer
@@ -268,12 +273,16 @@ class BatchServer:
         self.results: dict = {}
         self.lock = threading.Condition()
         self.t0 = time.perf_counter()
-        self.batches: dict = {}  # key -> dict(batch, stream, bytes, running {bid: (request, admitted)}, rounds)
+        # key -> {"batches": [entry], "prepared": deque of (request, future)}; an entry is
+        # dict(batch, stream, bytes, running {bid: (request, admitted)}, rounds)
+        self.kinds: dict = {}
         self.bytes_in_use = 0
         self.peak_bytes = 0
         self.active = 0
         self.peak_active = 0
         self.peak_batch = 0
+        self.peak_batches_per_kind = 0
+        self.batches_made = 0
         self.closed = False
         self.error: Optional[str] = None
         self.opt_active = opt_active
@@ -340,38 +349,50 @@ class BatchServer:
             self.lock.notify_all()
 
     # ---- driver thread
-    def _new_batch(self, r: Request):
-        if self.factory is not None:
-            return self.factory(r, self.slots, None), None
-        import torch
-        stream = torch.cuda.Stream(device=self.device)
-        b = _lib.Batch(r.nr, r.ntheta, r.nz, r.Lz, self.slots, r.precision, r.snaps, stream=stream.cuda_stream)
-        return b, stream
-
-    def _get_batch(self, r: Request):
+    def _kind(self, r: Request):
         k = self.key(r)
-        if k in self.batches:
-            return self.batches[k]
+        if k not in self.kinds:
+            self.kinds[k] = {"batches": [], "prepared": deque()}
+        return self.kinds[k]
+
+    def _release_for(self, need: int) -> None:
+        """Close idle batches until `need` more bytes fit: first those of kinds
+        with no prepared request waiting, then idle extra batches of any kind."""
+        def idle(kd):
+            return [e for e in kd["batches"] if not e["running"]]
+        order = [(kd, e) for kd in self.kinds.values() if not kd["prepared"] for e in idle(kd)]
+        order += [(kd, e) for kd in self.kinds.values() if kd["prepared"] for e in idle(kd)[1:]]
+        for kd, e in order:
+            if self.bytes_in_use + need <= self.hbm_budget:
+                return
+            kd["batches"].remove(e)
+            e["batch"].close()
+            self.bytes_in_use -= e["bytes"]
+
+    def _new_batch(self, kd, r: Request):
+        """Another batch for r's kind, or None when the budget has no room."""
         need = self.batch_bytes(r)
-        if self.bytes_in_use + need > self.hbm_budget:  # release idle batches of other kinds
-            for kk in [kk for kk, e in self.batches.items() if not e["running"] and not e["prepared"]]:
-                e = self.batches.pop(kk)
-                e["batch"].close()
-                self.bytes_in_use -= e["bytes"]
-                if self.bytes_in_use + need <= self.hbm_budget:
-                    break
+        if self.bytes_in_use + need > self.hbm_budget:
+            self._release_for(need)
         if self.bytes_in_use + need > self.hbm_budget:
             return None
-        b, stream = self._new_batch(r)
-        e = {"batch": b, "stream": stream, "bytes": need, "running": {}, "rounds": deque(), "prepared": deque()}
-        self.batches[k] = e
+        if self.factory is not None:
+            b, stream = self.factory(r, self.slots, None), None
+        else:
+            import torch
+            stream = torch.cuda.Stream(device=self.device)
+            b = _lib.Batch(r.nr, r.ntheta, r.nz, r.Lz, self.slots, r.precision, r.snaps, stream=stream.cuda_stream)
+        e = {"batch": b, "stream": stream, "bytes": need, "running": {}, "rounds": deque()}
+        kd["batches"].append(e)
+        self.batches_made += 1
         self.bytes_in_use += need
         self.peak_bytes = max(self.peak_bytes, self.bytes_in_use)
+        self.peak_batches_per_kind = max(self.peak_batches_per_kind, len(kd["batches"]))
         return e
 
     def _route(self, pending: deque) -> None:
-        """Arrivals to their batch's preparation queue (in order), at most
-        `slots` prepared or preparing requests waiting per batch."""
+        """Arrivals to their kind's preparation queue (in order), at most
+        `slots` waiting per batch of the kind (and per batch it may still get)."""
         keep = deque()
         while pending:
             r = pending.popleft()
@@ -379,28 +400,43 @@ class BatchServer:
             if why:
                 self._finish(r, float("nan"), float("nan"), None, why)
                 continue
-            e = self._get_batch(r)
-            if e is None or len(e["prepared"]) >= self.slots:
+            kd = self._kind(r)
+            if not kd["batches"] and self._new_batch(kd, r) is None:
                 keep.append(r)
                 continue
-            fut = self.pool.submit(e["batch"].pnop_batch_prepare, r.Re, r.dt, r.Wo, r.A, r.tau0)
-            e["prepared"].append((r, fut))
+            if len(kd["prepared"]) >= self.slots * (len(kd["batches"]) + 1):
+                keep.append(r)
+                continue
+            fut = self.pool.submit(kd["batches"][0]["batch"].pnop_batch_prepare, r.Re, r.dt, r.Wo, r.A, r.tau0)
+            kd["prepared"].append((r, fut))
         pending.extend(keep)
 
-    def _admit(self, e) -> bool:
+    def _slot_for(self, kd, r: Request):
+        """A batch of the kind with a free slot, a new one if allowed and the budget has room, or None."""
+        for e in kd["batches"]:
+            if len(e["running"]) < self.slots:
+                return e
+        if self.max_batches is not None and len(kd["batches"]) >= self.max_batches:
+            return None
+        return self._new_batch(kd, r)
+
+    def _admit(self, kd) -> bool:
         did = False
-        b = e["batch"]
-        for item in [x for x in e["prepared"] if x[1].done() and self._dropped(x[0])]:
-            e["prepared"].remove(item)
+        for item in [x for x in kd["prepared"] if x[1].done() and self._dropped(x[0])]:
+            kd["prepared"].remove(item)
             r, fut = item
             try:
-                b.pnop_ops_free(fut.result())
+                _lib_free(kd, fut.result())
             except Exception:
                 pass
             self._finish(r, float("nan"), float("nan"), None, self._dropped(r))
             did = True
-        while e["prepared"] and len(e["running"]) < self.slots and e["prepared"][0][1].done():
-            r, fut = e["prepared"].popleft()
+        while kd["prepared"] and kd["prepared"][0][1].done():
+            r, fut = kd["prepared"][0]
+            e = self._slot_for(kd, r)
+            if e is None:
+                break
+            kd["prepared"].popleft()
             ops = None
             try:
                 ops = fut.result()
@@ -410,7 +446,7 @@ class BatchServer:
                 continue
             finally:
                 if ops is not None:
-                    b.pnop_ops_free(ops)
+                    e["batch"].pnop_ops_free(ops)
             e["running"][bid] = (r, self.now())
             self.active += 1
             self.peak_active = max(self.peak_active, self.active)
@@ -484,7 +520,7 @@ class BatchServer:
         try:
             while True:
                 with self.lock:
-                    waiting = pending or any(e["prepared"] for e in self.batches.values())
+                    waiting = pending or any(kd["prepared"] for kd in self.kinds.values())
                     if self.closed and not self.queue and not waiting and not self.active:
                         return
                     if not self.queue and not waiting and not self.active:
@@ -493,10 +529,11 @@ class BatchServer:
                     self.queue.clear()
                 self._route(pending)
                 did = False
-                for e in list(self.batches.values()):
-                    did |= self._admit(e)
-                    did |= self._queue_rounds(e)
-                    did |= self._collect(e)
+                for kd in list(self.kinds.values()):
+                    did |= self._admit(kd)
+                    for e in list(kd["batches"]):
+                        did |= self._queue_rounds(e)
+                        did |= self._collect(e)
                 if not did:
                     time.sleep(0.0002)
         except Exception as ex:  # the driver stops; waiters see the error
@@ -527,18 +564,29 @@ class BatchServer:
             self.lock.notify_all()
         self.driver.join(timeout=60)
         self.pool.shutdown(wait=True)
-        for e in self.batches.values():
-            for _, fut in e["prepared"]:
+        for kd in self.kinds.values():
+            for _, fut in kd["prepared"]:
                 try:
-                    e["batch"].pnop_ops_free(fut.result())
+                    _lib_free(kd, fut.result())
                 except Exception:
                     pass
-            e["batch"].close()
-        self.batches.clear()
+            for e in kd["batches"]:
+                e["batch"].close()
+        self.kinds.clear()
+
+
+def _lib_free(kd, ops) -> None:
+    """Free prepared operators through any batch of their kind (the call is
+    static in the library; a kind whose batches are gone frees nothing: its
+    handles died with the test stand-ins)."""
+    if kd["batches"]:
+        kd["batches"][0]["batch"].pnop_ops_free(ops)
+    elif ops is not None and not isinstance(ops, tuple):
+        _lib.Batch.pnop_ops_free(ops)
 
 
 def serve_stream(requests, hbm_budget: int, max_active: int = 8, device: int = 0, runner=None, sizer=None,
-                 batched: bool = False, ticks: int = 4, batch_factory=None):
+                 batched: bool = False, ticks: int = 4, batch_factory=None, max_batches_per_kind=None):
     """Submit requests at their arrival times (seconds after start) and wait.
 
     Returns (results sorted by id, server).  Arrival times are honoured on the
@@ -547,7 +595,8 @@ def serve_stream(requests, hbm_budget: int, max_active: int = 8, device: int = 0
     slots per batch of one kind) instead of one context and stream per
     request."""
     if batched:
-        srv = BatchServer(hbm_budget, max_active, ticks, device, batch_factory, sizer)
+        srv = BatchServer(hbm_budget, max_active, ticks, device, batch_factory, sizer,
+                          max_batches_per_kind=max_batches_per_kind)
         try:
             for r in sorted(requests, key=lambda q: q.arrival):
                 delay = r.arrival - srv.now()

@@ -12,7 +12,9 @@ localised seed (Gaussian envelope of width 3 in z), E0=1e-5.
   (tests/golden/cfg2_oracle_100steps.json, written by make_cfg2_oracle.py
   beside it, which calls only the oracle): the gain, the gradient's energy
   norm, its inner products with eight seeded directions and 320 sampled
-  coefficients.
+  coefficients.  The coefficients are held to 1e-10 of the largest, or to
+  twice the spread between two equally valid roundings of the oracle itself
+  where that is larger (it is about 1e-10 here).
 * The 4000-step sweep takes Eq. 2.18's number of forward steps plus one.
 """
 import json
@@ -94,6 +96,12 @@ def test_fp64_first_100_steps_match_the_oracle(env):
     for seed, dot in zip(ref["dir_seeds"], ref["grad_dot_dirs"]):
         v = synth.random_field(o.r, M, K, LZ, seed=seed)
         assert abs(o.inner(gh, v) - dot) <= 1e-10 * math.sqrt(n2 * o.inner(v, v)), seed
+    # coefficient by coefficient: 1e-10 of the largest value, or twice the
+    # spread of two equally valid oracle evaluations where that is larger (the
+    # rounding floor of this 100-step, nr = 48 problem, recorded by the generator)
     err = max(abs(gh[tuple(i)] - complex(*z)) for i, z in ref["samples"])
-    assert err <= 1e-10 * ref["grad_max"]
+    tol = max(1e-10, 2 * ref["oracle_spread"]["grad_maxnorm_rel"])
+    print(f"cfg2 100-step FP64 vs oracle: max-norm {err / ref['grad_max']:.3e}, oracle spread"
+          f" {ref['oracle_spread']['grad_maxnorm_rel']:.3e}")
+    assert err <= tol * ref["grad_max"]
     ctx.close()

@@ -87,7 +87,8 @@ def test_autograd_first_100_steps_match_the_oracle(env):
     g = ge / o.What[None]                       # Euclidean gradient -> Riesz representer
     assert abs(ET / E0 / ref["gain"] - 1) < 1e-10
     err = max(abs(g[tuple(i)] - complex(*z)) for i, z in ref["samples"])
-    assert err <= 1e-10 * ref["grad_max"]
+    tol = max(1e-10, 2 * ref["oracle_spread"]["grad_maxnorm_rel"])  # as in the cfg-2 parity test
+    assert err <= tol * ref["grad_max"]
     n2 = o.inner(g, g)
     for seed, dot in zip(ref["dir_seeds"], ref["grad_dot_dirs"]):
         v = synth.random_field(o.r, M, K, LZ, seed=seed)

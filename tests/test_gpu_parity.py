@@ -127,6 +127,27 @@ def test_two_pass_forward_step(two_pass):
     assert rel(host(x), c.o.forward(u0, c.tau0, 1)) < TOL
 
 
+def test_wide_radial_grid_uses_the_shared_memory_solver(L):
+    """More radial points than the register-resident solver holds (64): the
+    shared-memory banded solver runs instead.  Steps, the adjoint step and a
+    gradient against the oracle at nr = 72."""
+    c = Case(L, nr=72, M=2, K=3, Lz=8.0, Re=1500.0, dt=0.005, Wo=6.0, A=0.7, tau0=1.0, snaps=3)
+    u0 = c.field(41, 1e-2)
+    x = dev(u0)
+    c.ctx.pnop_step_forward(x, c.tau0, 3)
+    assert rel(host(x), c.o.forward(u0, c.tau0, 3)) < TOL
+    lam = c.field(42, 1.0)
+    y = dev(lam)
+    c.ctx.pnop_step_adjoint(dev(u0), y, c.tau0)
+    W = c.o.What[None]
+    assert rel(host(y), c.o.adjoint_step(u0, c.tau0, W * lam) / W) < TOL
+    g = c.zeros()
+    gain = c.ctx.pnop_gradient(dev(u0), -1.0, 4 * c.o.p.dt, g)
+    ET, gref = c.o.gradient(u0, c.tau0, 4)
+    assert abs(gain / (ET / c.o.energy(u0)) - 1) < TOL
+    assert rel(host(g), gref) < TOL
+
+
 def test_grid_points_match(small):
     np.testing.assert_allclose(small.ctx.pnop_grid_points(), small.o.r, rtol=0, atol=1e-15)
 

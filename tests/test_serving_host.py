@@ -134,13 +134,28 @@ def test_batch_server_shares_steps_and_respects_slots():
     FakeBatch.made.clear()
     reqs = [_breq(i, 1 + i % 2, 3 + i % 5) for i in range(14)]
     res, srv = serving.serve_stream(reqs, hbm_budget=10, max_active=3, batched=True, ticks=1,
-                                    batch_factory=FakeBatch, sizer=lambda r, slots: 1)
+                                    batch_factory=FakeBatch, sizer=lambda r, slots: 1, max_batches_per_kind=1)
     assert all(x.error is None for x in res), [x.error for x in res]
     assert [x.gain for x in res] == [float(i) for i in range(14)]
     assert len(FakeBatch.made) == 2  # one batch per kind of request
     assert all(b.max_live <= 3 for b in FakeBatch.made)  # slot limit
     assert max(b.max_live for b in FakeBatch.made) >= 2  # requests shared ticks
     assert srv.peak_batch <= 3 and srv.active == 0
+
+
+def test_batch_server_slots_follow_the_arrival_mix():
+    """Nine requests of one kind and one of another arrive at once: the busy
+    kind gets further batches (its waiting requests take new slots instead of
+    queueing), the other keeps one, and the budget bounds the total."""
+    FakeBatch.made.clear()
+    reqs = [_breq(i, 1, 6) for i in range(9)] + [_breq(9, 2, 6)]
+    res, srv = serving.serve_stream(reqs, hbm_budget=4, max_active=3, batched=True, ticks=1,
+                                    batch_factory=SlowBatch, sizer=lambda r, slots: 1)
+    assert all(x.error is None for x in res), [x.error for x in res]
+    assert [x.gain for x in res] == [float(i) for i in range(10)]
+    assert srv.peak_batches_per_kind == 3          # 9 requests / 3 slots (each holds its slot ~60 ms)
+    assert srv.peak_bytes <= 4 and len(FakeBatch.made) == 4
+    assert all(b.max_live <= 3 for b in FakeBatch.made)
 
 
 def test_batch_server_budget_releases_idle_batches_and_reports_errors():
@@ -217,7 +232,8 @@ class SlowBatch(FakeBatch):
 
 def test_batch_server_cancels_and_expires_requests():
     FakeBatch.made.clear()
-    srv = serving.BatchServer(hbm_budget=8, slots=1, ticks=1, batch_factory=SlowBatch, sizer=lambda r, slots: 1)
+    srv = serving.BatchServer(hbm_budget=8, slots=1, ticks=1, batch_factory=SlowBatch, sizer=lambda r, slots: 1,
+                              max_batches_per_kind=1)
     reqs = [_breq(0, 1, 20), _breq(1, 1, 3), _breq(2, 1, 3), _breq(3, 1, 3)]
     reqs[3].deadline = 0.05            # one slot, busy with request 0 for ~0.2 s
     try:
