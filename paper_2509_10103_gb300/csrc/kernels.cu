@@ -558,6 +558,12 @@ __device__ __forceinline__ double infl_at(const double* h, const Geo& g, int im,
 // u_r = 0.  The wall coefficient a0 = d/dr u_r at the wall of the tentative
 // velocity (u_r = (x+ + x-)/2 [- usub_r]), or for mode (0,0) the flux
 // sum_j W_j (x_z [- usub_z]), is reduced first.
+// Blocks of the forward finish split the rows of a mode into kFR-row chunks
+// (grid z = batch entry x chunk); each block reduces the wall coefficient
+// itself (rows 0..8, or every row for the mean mode's flux), which costs a
+// few redundant reads of those rows, so that the apply phase runs on four
+// times as many blocks.
+constexpr int kFR = 16;
 __global__ void __launch_bounds__(kFK* kFJ) k_stage_finish(Geo g, const double2* __restrict__ R,
                                                           const double2* __restrict__ addto,
                                                           const double2* __restrict__ usub,
@@ -566,7 +572,9 @@ __global__ void __launch_bounds__(kFK* kFJ) k_stage_finish(Geo g, const double2*
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int k = blockIdx.x * kFK + tx, im = blockIdx.y, m = im - g.M;
     const size_t S = (size_t)g.nr * g.nm * g.nk;
-    const int slot = g.slot[blockIdx.z];  // batch entry blockIdx.z
+    const int nchunk = (g.nr + kFR - 1) / kFR;
+    const int b = blockIdx.z / nchunk, j0 = (blockIdx.z - b * nchunk) * kFR, j1 = min(g.nr, j0 + kFR);
+    const int slot = g.slot[b];  // batch entry b
     const size_t off = (size_t)slot * g.fs;
     R += off;
     addto = moved(addto, off);
@@ -601,7 +609,7 @@ __global__ void __launch_bounds__(kFK* kFJ) k_stage_finish(Geo g, const double2*
     for (int i = 1; i < kFJ; ++i) a0 = make_double2(a0.x + red[i][tx].x, a0.y + red[i][tx].y);
     const double* h = slot_infl(g, slot);
     const double* fg = slot_fluxg(g, slot);
-    for (int j = ty; j < g.nr; j += kFJ) {
+    for (int j = j0 + ty; j < j1; j += kFJ) {
         const size_t o = sidx(g, j, im, k);
         const double2 xp = R[o], xm = R[o + S];
         double2 ur = make_double2(0.5 * (xp.x + xm.x), 0.5 * (xp.y + xm.y));
@@ -638,11 +646,13 @@ __global__ void __launch_bounds__(kFK* kFJ) k_stage_finish(Geo g, const double2*
 // ------------------------------------------------------------------ radial stage (transpose)
 // Per mode: ybar = Fin^H ubar_new (a reduction over j), then xbar = Ti^H ybar.
 // The mode's coefficient acc of Fin^H goes to ac (added to it when ac_add), so
-// that Fin^H can be applied again later without the reduction.
-__global__ void __launch_bounds__(kFK* kFJ) k_stageT_finish(Geo g, const double2* __restrict__ un,
+// that Fin^H can be applied again later without the reduction.  Its reduction
+// runs over every row, so the block has kTJ radial groups (more rows in flight).
+constexpr int kTJ = 16;
+__global__ void __launch_bounds__(kFK* kTJ) k_stageT_finish(Geo g, const double2* __restrict__ un,
                                                            double2* __restrict__ R, double2* __restrict__ ac,
                                                            int ac_add) {
-    __shared__ double2 red[kFJ][kFK];
+    __shared__ double2 red[kTJ][kFK];
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int k = blockIdx.x * kFK + tx, im = blockIdx.y, m = im - g.M;
     const size_t S = (size_t)g.nr * g.nm * g.nk;
@@ -655,7 +665,7 @@ __global__ void __launch_bounds__(kFK* kFJ) k_stageT_finish(Geo g, const double2
     const double* fg = slot_fluxg(g, slot);
     double2 part = make_double2(0, 0);
     if (on) {
-        for (int j = ty; j < g.nr; j += kFJ) {
+        for (int j = ty; j < g.nr; j += kTJ) {
             const size_t o = sidx(g, j, im, k);
             if (mean) {
                 part = dfma(fg[j], un[o + 2 * S], part);
@@ -674,7 +684,7 @@ __global__ void __launch_bounds__(kFK* kFJ) k_stageT_finish(Geo g, const double2
     if (!on) return;
     double2 acc = red[0][tx];
 #pragma unroll
-    for (int i = 1; i < kFJ; ++i) acc = make_double2(acc.x + red[i][tx].x, acc.y + red[i][tx].y);
+    for (int i = 1; i < kTJ; ++i) acc = make_double2(acc.x + red[i][tx].x, acc.y + red[i][tx].y);
     if (ty == 0) {
         double2* a = ac + ((size_t)slot * g.nm + im) * g.nk + k;
         if (ac_add) {
@@ -685,7 +695,7 @@ __global__ void __launch_bounds__(kFK* kFJ) k_stageT_finish(Geo g, const double2
         }
     }
     const double* d0 = g.D1 + (size_t)par_idx(m + 1) * g.nr * kB;
-    for (int j = ty; j < g.nr; j += kFJ) {
+    for (int j = ty; j < g.nr; j += kTJ) {
         const size_t o = sidx(g, j, im, k);
         double2 yr = un[o], yt = un[o + S], yz = un[o + 2 * S];
         if (mean) {
@@ -1115,7 +1125,11 @@ void launch_baseT(const Geo& g, const double2* nb, double2* ub, cudaStream_t s) 
 static void launch_band_solve(const Geo& g, const double* fac, size_t fac_stride, double2* X, const double2* add,
                               int helm, int trans, int zero_row0, cudaStream_t s) {
     const dim3 nblocks((unsigned)((helm ? 3 : 1) * g.nm * g.ntile), (unsigned)g.nb);
-    if (g.nr <= kRegRows) {  // columns in registers
+    // columns in registers for the Helmholtz solves (three systems per mode:
+    // several warps per scheduler hide the dependent chain); the pressure
+    // solve, one system per mode and about one warp per scheduler, keeps the
+    // shared-memory form, which measured faster there
+    if (helm && g.nr <= kRegRows) {
         const size_t sm = 2 * (size_t)kRC * 9 * kSK * sizeof(double);
         if (!trans) {
             smem_limit((const void*)k_band_solve_reg<4, 8, false, kRegRows>);
@@ -1157,11 +1171,12 @@ void launch_stage_hsolve(const Geo& g, double2* R, cudaStream_t s) {
 static inline dim3 mode_grid(const Geo& g) { return dim3((g.nk + kFK - 1) / kFK, g.nm, g.nb); }
 void launch_stage_finish(const Geo& g, const double2* R, const double2* addto, const double2* usub, double2* out,
                          cudaStream_t s) {
-    k_stage_finish<<<mode_grid(g), dim3(kFK, kFJ), 0, s>>>(g, R, addto, usub, out);
+    const unsigned nchunk = (unsigned)((g.nr + kFR - 1) / kFR);
+    k_stage_finish<<<dim3((g.nk + kFK - 1) / kFK, g.nm, g.nb * nchunk), dim3(kFK, kFJ), 0, s>>>(g, R, addto, usub, out);
     check_launch("stage_finish");
 }
 void launch_stageT_finish(const Geo& g, const double2* ubn, double2* R, double2* ac, int ac_add, cudaStream_t s) {
-    k_stageT_finish<<<mode_grid(g), dim3(kFK, kFJ), 0, s>>>(g, ubn, R, ac, ac_add);
+    k_stageT_finish<<<mode_grid(g), dim3(kFK, kTJ), 0, s>>>(g, ubn, R, ac, ac_add);
     check_launch("stageT_finish");
 }
 void launch_stageT_hsolve(const Geo& g, double2* R, const double2* add, cudaStream_t s) {

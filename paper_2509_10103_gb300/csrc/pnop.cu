@@ -155,6 +155,17 @@ struct pnop_ctx {
     bool pending = false;
     int st_slots = 0;
     double timeout_s = 0;  // host limit on waits for device work (0: none)
+    // recomputation beside the adjoint: a second workspace on its own streams
+    // that runs the reverse sweep's forward advances while the adjoint steps
+    // run on this context's stream (single-request contexts, discrete adjoint,
+    // single checkpoint level)
+    pnop_ctx* shadow = nullptr;
+    double2* ring[2] = {nullptr, nullptr};       // end states of advances to the scratch state
+    cudaEvent_t ev_ring_w[2] = {}, ev_ring_r[2] = {};  // ring buffer written (shadow) / last read (adjoint)
+    std::vector<cudaEvent_t> ev_slot_w, ev_slot_r;     // per checkpoint slot, created on first use
+    std::vector<char> slot_shadow;                     // slot written by the shadow in this sweep
+    cudaEvent_t ev_main = nullptr, ev_shadow = nullptr;
+    bool owns_stream = false;                          // the shadow created its stream
     // per-class launch counters, work units and optional event timing
     unsigned prof_mask = 0;
     std::vector<cudaEvent_t> ev;     // pairs (start, stop)
@@ -854,6 +865,143 @@ size_t run_plan(pnop_ctx* c, size_t from, bool stop_at_adjoint, const double2** 
     return P.size();
 }
 
+// ---- recomputation beside the adjoint
+// The shadow is a second workspace for forward steps: its own work fields,
+// physical scratch and streams, the context's operator tables.  It is created
+// before the checkpoint pool is sized, so its memory counts against the HBM
+// budget like the rest of the context.
+void ensure_shadow(pnop_ctx* c) {
+    if (c->shadow) return;
+    pnop_ctx* sh = new pnop_ctx();
+    try {
+        sh->prm = c->prm;
+        sh->prm.hbm_budget = c->prm.hbm_budget ? (c->prm.hbm_budget > c->bytes ? c->prm.hbm_budget - c->bytes : 1) : 0;
+        sh->h.d = c->h.d;
+        sh->nslot = 1;
+        ck(cudaStreamCreateWithFlags(&sh->stream, cudaStreamNonBlocking), "shadow stream");
+        sh->owns_stream = true;
+        ck(cudaStreamCreateWithFlags(&sh->side, cudaStreamNonBlocking), "shadow side stream");
+        for (cudaEvent_t* e : {&sh->ev_fork, &sh->ev_t, &sh->ev_base})
+            ck(cudaEventCreateWithFlags(e, cudaEventDisableTiming), "event");
+        for (double2** b : {&sh->omega, &sh->N0, &sh->N1, &sh->us, &sh->R, &sh->Nbase, &sh->tmpA, &sh->tmpB})
+            *b = sh->field();
+        sh->q = (double2*)sh->dalloc(c->S() * sizeof(double2));
+        const size_t cz = mixed(c) ? sizeof(float2) : sizeof(double2);
+        const size_t plane = (size_t)c->h.d.nr * c->h.d.nth * c->h.d.nk * cz;
+        sh->Y = sh->dalloc(9 * plane);
+        sh->Z = sh->dalloc(6 * plane);
+        for (int r = 0; r < 2; ++r) {
+            ck(cudaEventCreateWithFlags(&c->ev_ring_w[r], cudaEventDisableTiming), "event");
+            ck(cudaEventCreateWithFlags(&c->ev_ring_r[r], cudaEventDisableTiming), "event");
+        }
+        ck(cudaEventCreateWithFlags(&c->ev_main, cudaEventDisableTiming), "event");
+        ck(cudaEventCreateWithFlags(&c->ev_shadow, cudaEventDisableTiming), "event");
+    } catch (...) {
+        pnop_destroy(sh);
+        throw;
+    }
+    c->shadow = sh;
+    c->bytes += sh->bytes;
+    c->ring[0] = c->field();
+    c->ring[1] = c->field();
+}
+
+// The shadow's view of the context as it is now (operators, phase, dt, profiling).
+void sync_shadow(pnop_ctx* c) {
+    pnop_ctx* sh = c->shadow;
+    sh->geo = c->geo;
+    sh->tw = c->tw;
+    sh->h.ph = c->h.ph;
+    sh->h.omega = c->h.omega;
+    sh->prm.precision = c->prm.precision;
+    sh->prof_mask = c->prof_mask;
+}
+
+cudaEvent_t slot_event(std::vector<cudaEvent_t>& v, int slot) {
+    if ((int)v.size() <= slot) v.resize(slot + 1, nullptr);
+    if (!v[slot]) ck(cudaEventCreateWithFlags(&v[slot], cudaEventDisableTiming), "event");
+    return v[slot];
+}
+
+// Reverse part of a single-level plan with its forward advances on the
+// shadow, so that recomputing the states of the next adjoint steps runs on
+// the GPU beside the adjoint steps of the present ones.  Events order every
+// buffer: an adjoint step waits for the advance that wrote its state; an
+// advance into a checkpoint slot (or one of the two scratch end states)
+// waits for the adjoint steps that last read it.  The kernels and their
+// inputs are those of run_plan, so the gradient is bitwise the same.
+void run_plan_overlap(pnop_ctx* c, size_t from) {
+    Range nvtx_range("pnop:reverse_overlap");
+    pnop_ctx* sh = c->shadow;
+    sync_shadow(c);
+    const auto& P = c->plan;
+    const size_t ns = c->snaps.size();
+    std::vector<char> wrote(ns, 0), read(ns, 0);
+    bool ring_read[2] = {false, false};
+    int ring_next = 0, cur_ring = -1;
+    const double2* cur = c->cur;
+    ck(cudaEventRecord(c->ev_main, c->stream), "event");  // the shadow starts after the forward phase
+    ck(cudaStreamWaitEvent(sh->stream, c->ev_main, 0), "wait");
+    for (size_t i = from; i < P.size(); ++i) {
+        const Action& a = P[i];
+        if (a.kind == kAdv) {
+            double2* dst = nullptr;
+            int r = -1;
+            if (a.dst >= 0) {
+                if (read[a.dst]) ck(cudaStreamWaitEvent(sh->stream, slot_event(c->ev_slot_r, a.dst), 0), "wait");
+                dst = c->snaps[a.dst];
+            } else {
+                r = ring_next;
+                ring_next ^= 1;
+                if (ring_read[r]) ck(cudaStreamWaitEvent(sh->stream, c->ev_ring_r[r], 0), "wait");
+                dst = c->ring[r];
+            }
+            advance(sh, c->snaps[a.slot], a.start, a.n, dst);
+            c->st_adv += a.n;
+            if (a.dst >= 0) {
+                ck(cudaEventRecord(slot_event(c->ev_slot_w, a.dst), sh->stream), "event");
+                wrote[a.dst] = 1;
+                ++c->st_store;
+            } else {
+                ck(cudaEventRecord(c->ev_ring_w[r], sh->stream), "event");
+                cur = dst;
+                cur_ring = r;
+            }
+            continue;
+        }
+        if (a.kind != kAdj) throw Status(PNOP_ERR_INVALID_ARG, "overlapped sweep: host-level action in the plan");
+        const double2* st = cur;
+        if (a.slot >= 0) {
+            st = c->snaps[a.slot];
+            if (wrote[a.slot]) ck(cudaStreamWaitEvent(c->stream, slot_event(c->ev_slot_w, a.slot), 0), "wait");
+        } else if (cur_ring >= 0) {
+            ck(cudaStreamWaitEvent(c->stream, c->ev_ring_w[cur_ring], 0), "wait");
+        }
+        adj_step(c, st, c->h.ph.tau0 + a.start * c->h.ph.dt, c->lamA, c->lamB);
+        std::swap(c->lamA, c->lamB);
+        ++c->st_adj;
+        if (a.slot >= 0) {
+            ck(cudaEventRecord(slot_event(c->ev_slot_r, a.slot), c->stream), "event");
+            read[a.slot] = 1;
+        } else if (cur_ring >= 0) {
+            ck(cudaEventRecord(c->ev_ring_r[cur_ring], c->stream), "event");
+            ring_read[cur_ring] = true;
+        }
+    }
+    ck(cudaEventRecord(c->ev_shadow, sh->stream), "event");
+    ck(cudaStreamWaitEvent(c->stream, c->ev_shadow, 0), "wait");
+    // the shadow's launches belong to this context's counters
+    prof_flush(sh);
+    for (int k = 0; k < PNOP_K_NCLASS; ++k) {
+        c->launches[k] += sh->launches[k];
+        c->units[k] += sh->units[k];
+        c->prof_ms[k] += sh->prof_ms[k];
+        sh->launches[k] = 0;
+        sh->units[k] = 0;
+        sh->prof_ms[k] = 0;
+    }
+}
+
 // Count-only replay of the same schedule (host logic, no device work).
 void count_reverse(long long l, int s, long long& adv, long long& stores) {
     if (l <= 1) return;
@@ -951,6 +1099,12 @@ void gradient_forward(pnop_ctx* c, const double2* u0, double E0, double horizon,
     if (!(horizon > 0) || N < 1 || std::fabs(nd - (double)N) > 1e-9 * std::max(1.0, nd))
         throw Status(PNOP_ERR_INVALID_ARG, "horizon must be a positive whole number of time steps");
     c->pending = false;
+    if (!c->batched) {
+        ensure_shadow(c);
+        // work a failed earlier sweep may have left on the shadow comes first
+        ck(cudaEventRecord(c->ev_shadow, c->shadow->stream), "event");
+        ck(cudaStreamWaitEvent(c->stream, c->ev_shadow, 0), "wait");
+    }
     const int s = snapshot_slots(c, N);
     while ((int)c->snaps.size() < s) c->snaps.push_back(c->field());
     if (!c->uN) c->uN = c->field();
@@ -1002,7 +1156,8 @@ void gradient_backward(pnop_ctx* c, double gE, bool euclidean, double2* grad) {
     weight(c, c->uN, c->lamA, 0);
     if (gE != 1.0) axpby(c, gE, c->lamA, 0.0, nullptr, c->lamA);
     const double2* st = nullptr;
-    run_plan(c, c->plan_pos, false, &st);
+    if (c->shadow && c->st_nf == 0) run_plan_overlap(c, c->plan_pos);
+    else run_plan(c, c->plan_pos, false, &st);
     if (euclidean) ck(cudaMemcpyAsync(grad, c->lamA, c->field_bytes(), cudaMemcpyDeviceToDevice, c->stream), "copy");
     else weight(c, c->lamA, grad, 1);
     wait_stream(c, "gradient sync");
@@ -1335,6 +1490,7 @@ int pnop_context_bytes(const pnop_grid* grid, const pnop_params* params, int sna
     const size_t cz = params->precision == PNOP_MIXED ? 8 : 16;
     size_t b = (21 + (size_t)snaps) * field + 2 * S * 16;              // work fields, u_N, optimiser, host staging, checkpoints, q, q2
     b += 24 * nr * nt * nk * cz;                                         // transform scratch Y, Y2, Z
+    b += 10 * field + S * 16 + 15 * nr * nt * nk * cz;                   // recomputation workspace (shadow) and its scratch states
     b += 2 * ((M + 2) + (M + 1)) * nr * 13 * nkp * 8;                    // LU factors and transposed rows
     b += (M + 2) * nr * 13 * 8 + 2 * nr * 13 * 8 + nm * nk * 3 * nr * 8; // bands, D1, influence
     *bytes = b + (1 << 20) + (40 + (size_t)snaps) * (2 << 20);        // tables, reductions, allocation rounding
@@ -1385,6 +1541,17 @@ int pnop_revolve_counts(int nsteps, int snaps, long long* advances, long long* s
 
 void pnop_destroy(pnop_ctx* ctx) {
     if (!ctx) return;
+    if (ctx->shadow) {
+        cudaStreamSynchronize(ctx->shadow->stream);
+        pnop_destroy(ctx->shadow);
+    }
+    for (cudaEvent_t e : {ctx->ev_ring_w[0], ctx->ev_ring_w[1], ctx->ev_ring_r[0], ctx->ev_ring_r[1], ctx->ev_main,
+                          ctx->ev_shadow})
+        if (e) cudaEventDestroy(e);
+    for (auto e : ctx->ev_slot_w)
+        if (e) cudaEventDestroy(e);
+    for (auto e : ctx->ev_slot_r)
+        if (e) cudaEventDestroy(e);
     for (auto e : ctx->ev) cudaEventDestroy(e);
     for (cudaEvent_t e : {ctx->ev_fork, ctx->ev_t, ctx->ev_base})
         if (e) cudaEventDestroy(e);
@@ -1399,6 +1566,7 @@ void pnop_destroy(pnop_ctx* ctx) {
     for (auto& r : ctx->breq)
         if (r.ev_done) cudaEventDestroy(r.ev_done);
     for (void* p : ctx->allocs) cudaFree(p);
+    if (ctx->owns_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
     delete ctx;
 }
 
