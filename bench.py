@@ -272,6 +272,32 @@ def time_gradient(L, torch, precision, steps, warmup, H, snaps, ws, rank, sample
             "advances": adv, "adjoint_steps": nadj, "stores": stores, "clocks": clocks, "host": host}
 
 
+def accuracy_vs_fp64(L, torch, H, snaps, precisions):
+    """Gain relative error and gradient cosine (energy inner product) of each
+    precision's gradient against the FP64 gradient on the bench workload (the
+    FP64 path is pinned to the oracle by the parity tests)."""
+    import numpy as np
+    out, ref = {}, None
+    for prec in (L.PNOP_FP64,) + tuple(precisions):
+        ctx = L.Context(NR, NTHETA, NZ, LZ, RE, DT, WO, AMP, TAU0, prec, snaps)
+        r = np.array(ctx.pnop_grid_points())
+        u0 = torch.from_numpy(make_u0(r)).to("cuda")
+        g = torch.zeros_like(u0)
+        gain = ctx.pnop_gradient(u0, E0, H * DT, g)
+        if ref is None:
+            ref = (gain, g, ctx)
+            continue
+        c64 = ref[2]
+        cos = c64.pnop_inner(g, ref[1]) / math.sqrt(c64.pnop_inner(g, g) * c64.pnop_inner(ref[1], ref[1]))
+        out[PREC_NAMES[prec]] = {"gain_rel_err_vs_fp64": abs(gain / ref[0] - 1), "gradient_cosine_vs_fp64": cos}
+        ctx.close()
+    ref[2].close()
+    return out
+
+
+PREC_NAMES = {0: "fp64", 1: "mixed", 2: "df", 3: "mixed_df"}
+
+
 def time_single_steps(L, torch, precision, reps=20):
     """Raw device time of one forward step and of one adjoint step (no checkpointing)."""
     import numpy as np
@@ -745,6 +771,14 @@ def main():
         fp64 = {"value": H * args.steps * ws / (fms / 1e3), "unit": "steps/s", "ms_per_step": fms / args.steps,
                 "gain": f["gain"], "dtype": "f64", "roofline": roofline(L, f, False, peaks, pk_src, alu),
                 "kernels_ms_per_step": {k: v[0] for k, v in f["warm_profile"].items()}}
+    mixed_df = None
+    if args.precision == "both":
+        f = time_gradient(L, torch, L.PNOP_MIXED_DF, args.steps, args.warmup, H, s, ws, rank, None)
+        fms = max_over_ranks(f["ms"], ws)
+        mixed_df = {"value": H * args.steps * ws / (fms / 1e3), "unit": "steps/s", "ms_per_step": fms / args.steps,
+                    "gain": f["gain"], "dtype": "f32 transforms + double-f32 banded products + f64",
+                    "roofline": roofline(L, f, True, peaks, pk_src, alu),
+                    "kernels_ms_per_step": {k: v[0] for k, v in f["warm_profile"].items()}}
     e2e_s = time_e2e(L, torch, main_prec, args.steps, args.warmup, H, s)
     e2e_s = max_over_ranks(e2e_s, ws)
     if rank != 0:
@@ -766,6 +800,8 @@ def main():
         "kernels_ms_per_step": {k: v[0] for k, v in mix["warm_profile"].items()},
         "fp64": fp64,
         "speedup_mixed_over_fp64": (value / fp64["value"]) if fp64 else None,
+        "mixed_df": mixed_df,
+        "speedup_mixed_df_over_fp64": (mixed_df["value"] / fp64["value"]) if (fp64 and mixed_df) else None,
         "e2e": {"value": H * args.steps * ws / e2e_s, "unit": "steps/s", "h2d_bytes_per_step": FIELD_BYTES,
                 "d2h_bytes_per_step": FIELD_BYTES + 24},
         "gpu_launches": launches,
@@ -780,7 +816,9 @@ def main():
             out[key] = {"error": f"{type(e).__name__}: {e}"[:500]}
 
     if ws == 1 and not args.no_extras:
+        extra("accuracy", lambda: accuracy_vs_fp64(L, torch, H, s, (L.PNOP_MIXED, L.PNOP_MIXED_DF, L.PNOP_DF)))
         extra("single_step", lambda: {"mixed": time_single_steps(L, torch, L.PNOP_MIXED),
+                                      "mixed_df": time_single_steps(L, torch, L.PNOP_MIXED_DF),
                                       "fp64": time_single_steps(L, torch, L.PNOP_FP64)})
         extra("budget_sweep_mixed", lambda: budget_sweep(L, torch, L.PNOP_MIXED, H))
         extra("host_tier_mixed", lambda: host_tier_report(L, torch, L.PNOP_MIXED, H))

@@ -55,7 +55,17 @@ enum {
     PNOP_ERR_UNSUPPORTED = -6   /* grid/solver combination not supported */
 };
 
-enum { PNOP_FP64 = 0, PNOP_MIXED = 1 };
+/* Arithmetic of a context, two independent bits:
+ *   PNOP_MIXED (1): the theta/z transforms and the products u x w (and their
+ *     transposes) in FP32;
+ *   PNOP_DF (2): the explicit banded radial products (curl, divergence,
+ *     pressure gradient and their transposes) in double-FP32 arithmetic
+ *     (about 48 significant bits, Dekker 1971), since FP64 runs at 1/64 of
+ *     the FP32 rate on this GPU.
+ * Everything else (the radial banded solves, the influence and flux
+ * corrections, the base flow, the stage combinations, energies and inner
+ * products) stays FP64.  PNOP_FP64 (0) is FP64 throughout. */
+enum { PNOP_FP64 = 0, PNOP_MIXED = 1, PNOP_DF = 2, PNOP_MIXED_DF = 3 };
 
 /* Grid.  nr radial points (>= 9); ntheta, nz nominal azimuthal/axial sizes,
  * giving |m| <= M = ntheta/2 - 1 and 0 <= k <= K = nz/2 - 1; the physical
@@ -71,8 +81,8 @@ typedef struct {
 /* Physics and run parameters.  Re = D Ubar / nu (mean), Wo and A as in
  * Section 1 (Eq. 2.4); time unit R/(2 Ubar), so the pulsation period is
  * 2 pi Re / Wo^2.  dt is the fixed time step, tau0 the start time of the
- * perturbation.  precision: PNOP_FP64, or PNOP_MIXED (FP32 transforms and
- * products, FP64 everything else).  snap_budget: checkpoint slots for
+ * perturbation.  precision: PNOP_FP64, PNOP_MIXED, PNOP_DF or PNOP_MIXED_DF
+ * (see above).  snap_budget: checkpoint slots for
  * pnop_gradient including the initial state (>= 1; Section 2.5).
  * snap_budget <= 0 sizes the checkpoint pool from the HBM budget.
  * hbm_budget: bytes the context may allocate (0 = no limit). */

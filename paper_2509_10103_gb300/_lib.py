@@ -16,7 +16,9 @@ LIB_PATH = os.path.join(HERE, "libpnop.so")
 
 PNOP_OK = 0
 PNOP_FP64 = 0
-PNOP_MIXED = 1
+PNOP_MIXED = 1      # FP32 transforms and products
+PNOP_DF = 2         # double-FP32 explicit banded products
+PNOP_MIXED_DF = 3
 KCLASSES = ("synth_theta", "zpass_fwd", "zpass_adj", "anal_theta", "spectral", "radial_band", "radial_solve",
             "elementwise", "reduce")
 OP_CURL, OP_NONLINEAR, OP_STAGE, OP_NONLINEAR_T, OP_STAGE_T_U, OP_STAGE_T_F, OP_PROJECT, OP_NONLINEAR_ADJ = range(8)

@@ -9,6 +9,7 @@
 // it finds its batch entry in one grid dimension and offsets its field
 // pointers and per-request tables by that entry's slot (see Geo).
 #include "dev_common.cuh"
+#include "dev_df.cuh"
 #include "kernels.hpp"
 
 #include <algorithm>
@@ -217,6 +218,265 @@ __global__ void k_base_adj(Geo g, const double2* __restrict__ w, double2* __rest
     N[o + 2 * S] = make_double2(-a * wz.y, a * wz.x);
 }
 
+// ------------------------------------------------------------------ double-FP32 banded products
+// The same products as k_curl, k_curlT_acc, k_stage_div, k_stage_rhs,
+// k_stageT_qbar and k_stageT_div, with the band rows and every term carrying
+// cancellation accumulated in double-float arithmetic (dev_df.cuh) instead of
+// FP64; inputs are split and outputs joined without FP64 instructions but the
+// final additions.  Used when the context's precision has the PNOP_DF bit.
+struct dacc2 {
+    dacc re, im;
+};
+__device__ __forceinline__ dfl dff(float2 v) {
+    dfl r;
+    r.h = v.x;
+    r.l = v.y;
+    return r;
+}
+__device__ __forceinline__ dacc dacc_neg(dacc a) {
+    a.s = -a.s;
+    a.c = -a.c;
+    return a;
+}
+__device__ __forceinline__ void df_fma2(dacc2& a, dfl k, const dfc& x) {
+    df_fma(a.re, k, x.re);
+    df_fma(a.im, k, x.im);
+}
+// sum_s B[j][s] x[j-4+s] (rows as in band_row)
+__device__ __forceinline__ dacc2 band_row_df(const Geo& g, const float2* B, const double2* x, int j, int im, int k) {
+    dacc2 a{dacc0(), dacc0()};
+    if (j >= 4) {
+#pragma unroll
+        for (int s = 0; s < 9; ++s) {
+            const int c = j - 4 + s;
+            if (c < g.nr) df_fma2(a, dff(__ldg(B + s)), df_load(x + sidx(g, c, im, k)));
+        }
+    } else {
+#pragma unroll
+        for (int s = 0; s < kB; ++s) {
+            const int c = j - 4 + s;
+            if (c >= 0 && c <= 8) df_fma2(a, dff(__ldg(B + s)), df_load(x + sidx(g, c, im, k)));
+        }
+    }
+    return a;
+}
+// (B^T x)_j (columns as in band_col)
+__device__ __forceinline__ dacc2 band_col_df(const Geo& g, const float2* B0, const double2* x, int j, int im, int k) {
+    dacc2 a{dacc0(), dacc0()};
+    if (j > 8) {
+#pragma unroll
+        for (int t = -4; t <= 4; ++t) {
+            const int c = j + t;
+            if (c < g.nr) df_fma2(a, dff(__ldg(B0 + (size_t)c * kB + (4 - t))), df_load(x + sidx(g, c, im, k)));
+        }
+    } else {
+#pragma unroll
+        for (int t = -8; t <= 4; ++t) {
+            const int c = j + t;
+            if (c >= 0 && c < g.nr) df_fma2(a, dff(__ldg(B0 + (size_t)c * kB + (4 - t))), df_load(x + sidx(g, c, im, k)));
+        }
+    }
+    return a;
+}
+__device__ __forceinline__ double2 df_out(const dacc2& a) { return make_double2(df_result(a.re), df_result(a.im)); }
+
+__global__ void k_curl_df(Geo g, const double2* __restrict__ u, double2* __restrict__ w) {
+    Idx d;
+    if (!decode(g, d)) return;
+    u += d.off;
+    w += d.off;
+    const double2 *ur = u, *ut = u + d.S, *uz = u + 2 * d.S;
+    const dfl kz = dff(__ldg(g.kztf + d.k)), ir = dff(__ldg(g.invrf + d.j)),
+              mr = dff(__ldg(g.mrtf + (size_t)d.im * g.nr + d.j));
+    const size_t o = sidx(g, d.j, d.im, d.k);
+    const dacc2 dz = band_row_df(g, g.D1f + ((size_t)par_idx(d.m) * g.nr + d.j) * kB, uz, d.j, d.im, d.k);
+    const dacc2 dt = band_row_df(g, g.D1f + ((size_t)par_idx(d.m + 1) * g.nr + d.j) * kB, ut, d.j, d.im, d.k);
+    const dfc a = df_load(ur + o), b = df_load(ut + o), c = df_load(uz + o);
+    dacc2 wr{dacc0(), dacc0()};  // (-mr c.y + kz b.y, mr c.x - kz b.x)
+    df_fma(wr.re, df_neg(mr), c.im);
+    df_fma(wr.re, kz, b.im);
+    df_fma(wr.im, mr, c.re);
+    df_fma(wr.im, df_neg(kz), b.re);
+    dacc2 wt{dacc_neg(dz.re), dacc_neg(dz.im)};  // (-kz a.y - dz.x, kz a.x - dz.y)
+    df_fma(wt.re, df_neg(kz), a.im);
+    df_fma(wt.im, kz, a.re);
+    dacc2 wz = dt;  // (dt.x + ir b.x + mr a.y, dt.y + ir b.y - mr a.x)
+    df_fma(wz.re, ir, b.re);
+    df_fma(wz.re, mr, a.im);
+    df_fma(wz.im, ir, b.im);
+    df_fma(wz.im, df_neg(mr), a.re);
+    w[o] = df_out(wr);
+    w[o + d.S] = df_out(wt);
+    w[o + 2 * d.S] = df_out(wz);
+}
+
+__global__ void k_curlT_acc_df(Geo g, const double2* __restrict__ wb, double2* __restrict__ ub) {
+    Idx d;
+    if (!decode(g, d)) return;
+    wb += d.off;
+    ub += d.off;
+    const double2 *wr = wb, *wt = wb + d.S, *wz = wb + 2 * d.S;
+    const dfl kz = dff(__ldg(g.kztf + d.k)), ir = dff(__ldg(g.invrf + d.j)),
+              mr = dff(__ldg(g.mrtf + (size_t)d.im * g.nr + d.j));
+    const size_t o = sidx(g, d.j, d.im, d.k);
+    const dacc2 sT = band_col_df(g, g.D1f + (size_t)par_idx(d.m + 1) * g.nr * kB, wz, d.j, d.im, d.k);
+    const dacc2 sP = band_col_df(g, g.D1f + (size_t)par_idx(d.m) * g.nr * kB, wt, d.j, d.im, d.k);
+    const dfc a = df_load(wr + o), b = df_load(wt + o), c = df_load(wz + o);
+    dacc2 xr{dacc0(), dacc0()};  // += (kz b.y - mr c.y, -kz b.x + mr c.x)
+    df_fma(xr.re, kz, b.im);
+    df_fma(xr.re, df_neg(mr), c.im);
+    df_fma(xr.im, df_neg(kz), b.re);
+    df_fma(xr.im, mr, c.re);
+    dacc2 xt = sT;  // += (-kz a.y + sT.x + ir c.x, kz a.x + sT.y + ir c.y)
+    df_fma(xt.re, df_neg(kz), a.im);
+    df_fma(xt.re, ir, c.re);
+    df_fma(xt.im, kz, a.re);
+    df_fma(xt.im, ir, c.im);
+    dacc2 xz{dacc_neg(sP.re), dacc_neg(sP.im)};  // += (mr a.y - sP.x, -mr a.x - sP.y)
+    df_fma(xz.re, mr, a.im);
+    df_fma(xz.im, df_neg(mr), a.re);
+    double2 x = ub[o], v = df_out(xr);
+    ub[o] = make_double2(x.x + v.x, x.y + v.y);
+    x = ub[o + d.S];
+    v = df_out(xt);
+    ub[o + d.S] = make_double2(x.x + v.x, x.y + v.y);
+    x = ub[o + 2 * d.S];
+    v = df_out(xz);
+    ub[o + 2 * d.S] = make_double2(x.x + v.x, x.y + v.y);
+}
+
+__global__ void k_stage_div_df(Geo g, const double2* __restrict__ F, double2* __restrict__ q) {
+    Idx d;
+    if (!decode(g, d)) return;
+    F += d.off;
+    q += d.off;
+    const size_t o = sidx(g, d.j, d.im, d.k), S = d.S;
+    if (d.j == 0 || (d.m == 0 && d.k == 0)) {
+        q[o] = make_double2(0, 0);
+        return;
+    }
+    const dfl kz = dff(__ldg(g.kztf + d.k)), ir = dff(__ldg(g.invrf + d.j)),
+              mr = dff(__ldg(g.mrtf + (size_t)d.im * g.nr + d.j));
+    dacc2 acc = band_row_df(g, g.D1f + ((size_t)par_idx(d.m + 1) * g.nr + d.j) * kB, F, d.j, d.im, d.k);
+    const dfc fr = df_load(F + o), ft = df_load(F + o + S), fz = df_load(F + o + 2 * S);
+    df_fma(acc.re, ir, fr.re);  // + ir fr.x - mr ft.y - kz fz.y
+    df_fma(acc.re, df_neg(mr), ft.im);
+    df_fma(acc.re, df_neg(kz), fz.im);
+    df_fma(acc.im, ir, fr.im);  // + ir fr.y + mr ft.x + kz fz.x
+    df_fma(acc.im, mr, ft.re);
+    df_fma(acc.im, kz, fz.re);
+    q[o] = df_out(acc);
+}
+
+// k_stage_rhs with every term of R in double-float: R_+ = F_r - F_t i - D1 p
+// + (m/r) p ..., written out per real part below
+__global__ void k_stage_rhs_df(Geo g, const double2* __restrict__ u, const double2* __restrict__ F,
+                               const double2* __restrict__ p, double2* __restrict__ R) {
+    Idx d;
+    if (!decode(g, d)) return;
+    u = moved(u, d.off);
+    F += d.off;
+    p += d.off;
+    R += d.off;
+    const size_t o = sidx(g, d.j, d.im, d.k), S = d.S;
+    if (d.j == 0) {  // the wall row: T u (no arithmetic worth double-float)
+        double2 tp = make_double2(0, 0), tm = tp, tz = tp;
+        if (u) {
+            const double2 a = u[o], b = u[o + S], c = u[o + 2 * S];
+            tp = make_double2(a.x - b.y, a.y + b.x);
+            tm = make_double2(a.x + b.y, a.y - b.x);
+            tz = c;
+        }
+        R[o] = tp;
+        R[o + S] = tm;
+        R[o + 2 * S] = tz;
+        return;
+    }
+    const dfl kz = dff(__ldg(g.kztf + d.k)), mr = dff(__ldg(g.mrtf + (size_t)d.im * g.nr + d.j));
+    const dacc2 dp = band_row_df(g, g.D1f + ((size_t)par_idx(d.m) * g.nr + d.j) * kB, p, d.j, d.im, d.k);
+    const dfc pj = df_load(p + o), fr = df_load(F + o), ft = df_load(F + o + S), fz = df_load(F + o + 2 * S);
+    // rp = (Fr.x - Ft.y - dp.x + mr p.x, Fr.y + Ft.x - dp.y + mr p.y)
+    // rm = (Fr.x + Ft.y - dp.x - mr p.x, Fr.y - Ft.x - dp.y - mr p.y)
+    // rz = (Fz.x + kz p.y, Fz.y - kz p.x)
+    dacc2 rp{dacc_neg(dp.re), dacc_neg(dp.im)}, rm = rp, rz{dacc0(), dacc0()};
+    df_add(rp.re, fr.re);
+    df_add(rp.re, df_neg(ft.im));
+    df_fma(rp.re, mr, pj.re);
+    df_add(rp.im, fr.im);
+    df_add(rp.im, ft.re);
+    df_fma(rp.im, mr, pj.im);
+    df_add(rm.re, fr.re);
+    df_add(rm.re, ft.im);
+    df_fma(rm.re, df_neg(mr), pj.re);
+    df_add(rm.im, fr.im);
+    df_add(rm.im, df_neg(ft.re));
+    df_fma(rm.im, df_neg(mr), pj.im);
+    df_add(rz.re, fz.re);
+    df_fma(rz.re, kz, pj.im);
+    df_add(rz.im, fz.im);
+    df_fma(rz.im, df_neg(kz), pj.re);
+    if (u) {  // + (2/dt) T u: u+ = (a.x - b.y, a.y + b.x), u- = (a.x + b.y, a.y - b.x), u_z
+        const dfl f = dff(g.two_dtf[d.slot]);
+        const dfc a = df_load(u + o), b = df_load(u + o + S), c = df_load(u + o + 2 * S);
+        df_fma(rp.re, f, a.re);
+        df_fma(rp.re, df_neg(f), b.im);
+        df_fma(rp.im, f, a.im);
+        df_fma(rp.im, f, b.re);
+        df_fma(rm.re, f, a.re);
+        df_fma(rm.re, f, b.im);
+        df_fma(rm.im, f, a.im);
+        df_fma(rm.im, df_neg(f), b.re);
+        df_fma(rz.re, f, c.re);
+        df_fma(rz.im, f, c.im);
+    }
+    R[o] = df_out(rp);
+    R[o + S] = df_out(rm);
+    R[o + 2 * S] = df_out(rz);
+}
+
+__global__ void k_stageT_qbar_df(Geo g, const double2* __restrict__ Fb, double2* __restrict__ q) {
+    Idx d;
+    if (!decode(g, d)) return;
+    Fb += d.off;
+    q += d.off;
+    const size_t o = sidx(g, d.j, d.im, d.k), S = d.S;
+    if (d.m == 0 && d.k == 0) {
+        q[o] = make_double2(0, 0);
+        return;
+    }
+    const dfl kz = dff(__ldg(g.kztf + d.k)), mr = dff(__ldg(g.mrtf + (size_t)d.im * g.nr + d.j));
+    dacc2 acc = band_col_df(g, g.D1f + (size_t)par_idx(d.m) * g.nr * kB, Fb, d.j, d.im, d.k);
+    const dfc ft = df_load(Fb + o + S), fz = df_load(Fb + o + 2 * S);
+    df_fma(acc.re, mr, ft.im);  // + mr ft.y + kz fz.y
+    df_fma(acc.re, kz, fz.im);
+    df_fma(acc.im, df_neg(mr), ft.re);  // - mr ft.x - kz fz.x
+    df_fma(acc.im, df_neg(kz), fz.re);
+    q[o] = df_out(acc);
+}
+
+__global__ void k_stageT_div_df(Geo g, const double2* __restrict__ z, double2* __restrict__ Fb) {
+    Idx d;
+    if (!decode(g, d)) return;
+    z += d.off;
+    Fb += d.off;
+    if (d.m == 0 && d.k == 0) return;
+    const size_t o = sidx(g, d.j, d.im, d.k), S = d.S;
+    const double kz = __ldg(g.kzt + d.k), mr = __ldg(g.mrt + (size_t)d.im * g.nr + d.j);
+    const dfl ir = dff(__ldg(g.invrf + d.j));
+    dacc2 dz = band_col_df(g, g.D1f + (size_t)par_idx(d.m + 1) * g.nr * kB, z, d.j, d.im, d.k);
+    const double2 zj = z[o];
+    const dfc zd = df_load(z + o);
+    df_fma(dz.re, ir, zd.re);  // D1v^T z + z / r
+    df_fma(dz.im, ir, zd.im);
+    const double2 v = df_out(dz);
+    double2 x = Fb[o];
+    Fb[o] = make_double2(x.x - v.x, x.y - v.y);
+    x = Fb[o + S];
+    Fb[o + S] = make_double2(x.x - mr * zj.y, x.y + mr * zj.x);
+    x = Fb[o + 2 * S];
+    Fb[o + 2 * S] = make_double2(x.x - kz * zj.y, x.y + kz * zj.x);
+}
+
 // ------------------------------------------------------------------ radial stage (forward)
 // q = div F (rows j >= 1; q_0 = 0 is the tentative Neumann datum)
 __global__ void k_stage_div(Geo g, const double2* __restrict__ F, double2* __restrict__ q) {
@@ -266,7 +526,8 @@ __device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_g
 template <int NL, int NU, bool DIAG1>
 __global__ void __launch_bounds__(2 * kSK) k_band_solve(Geo g, const double* __restrict__ fac, size_t fac_stride,
                                                   double2* __restrict__ X, const double2* __restrict__ add, int helm,
-                                                  int zero_row0) {
+                                                  int zero_row0, double* __restrict__ pw,
+                                                  const double2* __restrict__ usub) {
     constexpr int NC1 = NL + (DIAG1 ? 1 : 0);  // forward sweep: columns [0, NC1)
     constexpr int NC2 = kB - NC1;               // backward sweep: columns [NC1, 13)
     constexpr int NCM = NC1 > NC2 ? NC1 : NC2;
@@ -361,6 +622,28 @@ __global__ void __launch_bounds__(2 * kSK) k_band_solve(Geo g, const double* __r
         }
         __syncthreads();
     }
+    if (pw && k0 + sy < g.nk) {  // wall partials of the tentative velocity (as in k_band_solve_reg)
+        usub = moved(usub, off);
+        const double* us = usub ? reinterpret_cast<const double*>(usub) + comp : nullptr;
+        double* P = pw + ((((size_t)slot * 3 + v) * g.nm + im) * g.nk + (k0 + sy)) * 2 + comp;
+        if (v < 2) {
+            const double* d0 = g.D1 + (size_t)par_idx(m + 1) * g.nr * kB + 4;
+            double acc = 0.0;
+            for (int c = 0; c <= 8 && c < g.nr; ++c) {
+                double xv = 0.5 * Yd[(c * kSK + sy) * 2 + comp];
+                if (v == 0 && us) xv -= us[2 * sidx(g, c, im, k0 + sy)];
+                acc = fma(__ldg(d0 + c), xv, acc);
+            }
+            *P = acc;
+        } else if (m == 0 && k0 + sy == 0) {
+            double acc = 0.0;
+            for (int j = 0; j < g.nr; ++j) {
+                const double xj = Yd[(j * kSK + sy) * 2 + comp];
+                acc = fma(g.W[j], us ? xj - us[2 * (2 * S + sidx(g, j, im, 0))] : xj, acc);
+            }
+            *P = acc;
+        }
+    }
     for (int i = tid; i < g.nr * kSK; i += 2 * kSK) {
         const int j = i / kSK, t = i % kSK;
         if (k0 + t >= g.nk) continue;
@@ -386,7 +669,8 @@ __global__ void __launch_bounds__(2 * kSK) k_band_solve(Geo g, const double* __r
 template <int NL, int NU, bool DIAG1, int MAXR>
 __global__ void __launch_bounds__(2 * kSK) k_band_solve_reg(Geo g, const double* __restrict__ fac, size_t fac_stride,
                                                       double2* __restrict__ X, const double2* __restrict__ add,
-                                                      int helm, int zero_row0) {
+                                                      int helm, int zero_row0, double* __restrict__ pw,
+                                                      const double2* __restrict__ usub) {
     constexpr int NC1 = NL + (DIAG1 ? 1 : 0);
     constexpr int NC2 = kB - NC1;
     constexpr int NCM = NC1 > NC2 ? NC1 : NC2;
@@ -485,6 +769,34 @@ __global__ void __launch_bounds__(2 * kSK) k_band_solve_reg(Geo g, const double*
         }
     }
     if (!on) return;
+    if (pw) {  // wall partials of the tentative velocity (see wall_partials_at)
+        usub = moved(usub, off);
+        const double* us = usub ? reinterpret_cast<const double*>(usub) + comp : nullptr;
+        double* P = pw + ((((size_t)slot * 3 + v) * g.nm + im) * g.nk + (k0 + sy)) * 2 + comp;
+        if (v < 2) {
+            const double* d0 = g.D1 + (size_t)par_idx(m + 1) * nr * kB + 4;
+            double acc = 0.0;
+#pragma unroll
+            for (int c = 0; c <= 8; ++c) {
+                if (c < nr) {
+                    double xv = 0.5 * x[c];
+                    if (v == 0 && us) xv -= us[2 * sidx(g, c, im, k0 + sy)];
+                    acc = fma(__ldg(d0 + c), xv, acc);
+                }
+            }
+            *P = acc;
+        } else if (m == 0 && k0 + sy == 0) {  // the mean mode's flux sum_j W_j (x_z - usub_z)
+            double acc = 0.0;
+#pragma unroll
+            for (int j = 0; j < MAXR; ++j) {
+                if (j < nr) {
+                    const double xv = us ? x[j] - us[2 * (2 * S + sidx(g, j, im, 0))] : x[j];
+                    acc = fma(g.W[j], xv, acc);
+                }
+            }
+            *P = acc;
+        }
+    }
     double* xo = reinterpret_cast<double*>(X + (size_t)v * S) + comp;
     const double* ad = add ? reinterpret_cast<const double*>(add + (size_t)v * S) + comp : nullptr;
 #pragma unroll
@@ -555,104 +867,70 @@ __device__ __forceinline__ double infl_at(const double* h, const Geo& g, int im,
 
 // out = [addto +] back to (r, theta, z) [- usub] with the influence
 // correction (div u = 0 at the wall) or, for mode (0,0), flux correction and
-// u_r = 0.  The wall coefficient a0 = d/dr u_r at the wall of the tentative
-// velocity (u_r = (x+ + x-)/2 [- usub_r]), or for mode (0,0) the flux
-// sum_j W_j (x_z [- usub_z]), is reduced first.
-// Blocks of the forward finish split the rows of a mode into kFR-row chunks
-// (grid z = batch entry x chunk); each block reduces the wall coefficient
-// itself (rows 0..8, or every row for the mean mode's flux), which costs a
-// few redundant reads of those rows, so that the apply phase runs on four
-// times as many blocks.
-constexpr int kFR = 16;
-__global__ void __launch_bounds__(kFK* kFJ) k_stage_finish(Geo g, const double2* __restrict__ R,
-                                                          const double2* __restrict__ addto,
-                                                          const double2* __restrict__ usub,
-                                                          double2* __restrict__ out) {
-    __shared__ double2 red[kFJ][kFK];
-    const int tx = threadIdx.x, ty = threadIdx.y;
-    const int k = blockIdx.x * kFK + tx, im = blockIdx.y, m = im - g.M;
-    const size_t S = (size_t)g.nr * g.nm * g.nk;
-    const int nchunk = (g.nr + kFR - 1) / kFR;
-    const int b = blockIdx.z / nchunk, j0 = (blockIdx.z - b * nchunk) * kFR, j1 = min(g.nr, j0 + kFR);
-    const int slot = g.slot[b];  // batch entry b
-    const size_t off = (size_t)slot * g.fs;
-    R += off;
-    addto = moved(addto, off);
-    usub = moved(usub, off);
-    out += off;
-    const bool on = k < g.nk, mean = (m == 0 && k == 0);
-    double2 part = make_double2(0, 0);
-    if (on) {
-        if (mean) {
-            for (int j = ty; j < g.nr; j += kFJ) {
-                const size_t o = sidx(g, j, im, k) + 2 * S;
-                double2 x = R[o];
-                if (usub) x = make_double2(x.x - usub[o].x, x.y - usub[o].y);
-                part = dfma(g.W[j], x, part);
-            }
-        } else {
-            const double* d0 = g.D1 + (size_t)par_idx(m + 1) * g.nr * kB;  // row 0 of D1 (u_r parity)
-            for (int c = ty; c <= 8 && c < g.nr; c += kFJ) {
-                const size_t oc = sidx(g, c, im, k);
-                const double2 p = R[oc], q = R[oc + S];
-                double2 x = make_double2(0.5 * (p.x + q.x), 0.5 * (p.y + q.y));
-                if (usub) x = make_double2(x.x - usub[oc].x, x.y - usub[oc].y);
-                part = dfma(__ldg(d0 + 4 + c), x, part);
-            }
-        }
+// u_r = 0, one value per thread.  The mode's coefficient comes from the wall
+// partials the Helmholtz solve left in pw ([slot][3][m][k]): a0 = pw[0] +
+// pw[1] = d/dr u_r at the wall of the tentative velocity
+// u_r = (x+ + x-)/2 [- usub_r], or for mode (0,0) pw[2] = sum_j W_j
+// (x_z [- usub_z]).
+__global__ void k_stage_finish(Geo g, const double2* __restrict__ R, const double2* __restrict__ addto,
+                               const double2* __restrict__ usub, const double2* __restrict__ pw,
+                               double2* __restrict__ out) {
+    Idx d;
+    if (!decode(g, d)) return;
+    R += d.off;
+    addto = moved(addto, d.off);
+    usub = moved(usub, d.off);
+    out += d.off;
+    const size_t o = sidx(g, d.j, d.im, d.k), S = d.S, nmk = (size_t)g.nm * g.nk;
+    const bool mean = d.m == 0 && d.k == 0;
+    const double2* P = pw + (size_t)d.slot * 3 * nmk + (size_t)d.im * g.nk + d.k;
+    double2 a0;
+    if (mean) {
+        a0 = P[2 * nmk];
+    } else {
+        const double2 p0 = P[0], p1 = P[nmk];
+        a0 = make_double2(p0.x + p1.x, p0.y + p1.y);
     }
-    red[ty][tx] = part;
-    __syncthreads();
-    if (!on) return;
-    double2 a0 = red[0][tx];
-#pragma unroll
-    for (int i = 1; i < kFJ; ++i) a0 = make_double2(a0.x + red[i][tx].x, a0.y + red[i][tx].y);
-    const double* h = slot_infl(g, slot);
-    const double* fg = slot_fluxg(g, slot);
-    for (int j = j0 + ty; j < j1; j += kFJ) {
-        const size_t o = sidx(g, j, im, k);
-        const double2 xp = R[o], xm = R[o + S];
-        double2 ur = make_double2(0.5 * (xp.x + xm.x), 0.5 * (xp.y + xm.y));
-        double2 ut = make_double2(0.5 * (xp.y - xm.y), -0.5 * (xp.x - xm.x));
-        double2 uz = R[o + 2 * S];
-        if (usub) {
-            const double2 a = usub[o], b = usub[o + S], c = usub[o + 2 * S];
-            ur.x -= a.x; ur.y -= a.y;
-            ut.x -= b.x; ut.y -= b.y;
-            uz.x -= c.x; uz.y -= c.y;
-        }
-        if (mean) {
-            uz = dfma(fg[j] * (-g.flux_inv[slot]), a0, uz);
-            ur = make_double2(0, 0);
-        } else {
-            const double h0 = infl_at(h, g, im, 0, j, k), h1 = infl_at(h, g, im, 1, j, k),
-                         h2 = infl_at(h, g, im, 2, j, k);
-            ur = dfma(h0, a0, ur);
-            ut = make_double2(ut.x - h1 * a0.y, ut.y + h1 * a0.x);
-            uz = make_double2(uz.x - h2 * a0.y, uz.y + h2 * a0.x);
-        }
-        if (addto) {
-            const double2 a = addto[o], b = addto[o + S], c = addto[o + 2 * S];
-            ur.x += a.x; ur.y += a.y;
-            ut.x += b.x; ut.y += b.y;
-            uz.x += c.x; uz.y += c.y;
-        }
-        out[o] = ur;
-        out[o + S] = ut;
-        out[o + 2 * S] = uz;
+    const double2 xp = R[o], xm = R[o + S];
+    double2 ur = make_double2(0.5 * (xp.x + xm.x), 0.5 * (xp.y + xm.y));
+    double2 ut = make_double2(0.5 * (xp.y - xm.y), -0.5 * (xp.x - xm.x));
+    double2 uz = R[o + 2 * S];
+    if (usub) {
+        const double2 a = usub[o], b = usub[o + S], c = usub[o + 2 * S];
+        ur.x -= a.x; ur.y -= a.y;
+        ut.x -= b.x; ut.y -= b.y;
+        uz.x -= c.x; uz.y -= c.y;
     }
+    if (mean) {
+        uz = dfma(slot_fluxg(g, d.slot)[d.j] * (-g.flux_inv[d.slot]), a0, uz);
+        ur = make_double2(0, 0);
+    } else {
+        const double* h = slot_infl(g, d.slot);
+        const double h0 = infl_at(h, g, d.im, 0, d.j, d.k), h1 = infl_at(h, g, d.im, 1, d.j, d.k),
+                     h2 = infl_at(h, g, d.im, 2, d.j, d.k);
+        ur = dfma(h0, a0, ur);
+        ut = make_double2(ut.x - h1 * a0.y, ut.y + h1 * a0.x);
+        uz = make_double2(uz.x - h2 * a0.y, uz.y + h2 * a0.x);
+    }
+    if (addto) {
+        const double2 a = addto[o], b = addto[o + S], c = addto[o + 2 * S];
+        ur.x += a.x; ur.y += a.y;
+        ut.x += b.x; ut.y += b.y;
+        uz.x += c.x; uz.y += c.y;
+    }
+    out[o] = ur;
+    out[o + S] = ut;
+    out[o + 2 * S] = uz;
 }
 
 // ------------------------------------------------------------------ radial stage (transpose)
 // Per mode: ybar = Fin^H ubar_new (a reduction over j), then xbar = Ti^H ybar.
 // The mode's coefficient acc of Fin^H goes to ac (added to it when ac_add), so
-// that Fin^H can be applied again later without the reduction.  Its reduction
-// runs over every row, so the block has kTJ radial groups (more rows in flight).
-constexpr int kTJ = 16;
-__global__ void __launch_bounds__(kFK* kTJ) k_stageT_finish(Geo g, const double2* __restrict__ un,
+// that Fin^H can be applied again later without the reduction.
+__global__ void __launch_bounds__(kFK* kFJ) k_stageT_finish(Geo g, const double2* __restrict__ un,
                                                            double2* __restrict__ R, double2* __restrict__ ac,
                                                            int ac_add) {
-    __shared__ double2 red[kTJ][kFK];
+    __shared__ double2 red[kFJ][kFK];
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int k = blockIdx.x * kFK + tx, im = blockIdx.y, m = im - g.M;
     const size_t S = (size_t)g.nr * g.nm * g.nk;
@@ -665,7 +943,7 @@ __global__ void __launch_bounds__(kFK* kTJ) k_stageT_finish(Geo g, const double2
     const double* fg = slot_fluxg(g, slot);
     double2 part = make_double2(0, 0);
     if (on) {
-        for (int j = ty; j < g.nr; j += kTJ) {
+        for (int j = ty; j < g.nr; j += kFJ) {
             const size_t o = sidx(g, j, im, k);
             if (mean) {
                 part = dfma(fg[j], un[o + 2 * S], part);
@@ -684,7 +962,7 @@ __global__ void __launch_bounds__(kFK* kTJ) k_stageT_finish(Geo g, const double2
     if (!on) return;
     double2 acc = red[0][tx];
 #pragma unroll
-    for (int i = 1; i < kTJ; ++i) acc = make_double2(acc.x + red[i][tx].x, acc.y + red[i][tx].y);
+    for (int i = 1; i < kFJ; ++i) acc = make_double2(acc.x + red[i][tx].x, acc.y + red[i][tx].y);
     if (ty == 0) {
         double2* a = ac + ((size_t)slot * g.nm + im) * g.nk + k;
         if (ac_add) {
@@ -695,7 +973,7 @@ __global__ void __launch_bounds__(kFK* kTJ) k_stageT_finish(Geo g, const double2
         }
     }
     const double* d0 = g.D1 + (size_t)par_idx(m + 1) * g.nr * kB;
-    for (int j = ty; j < g.nr; j += kTJ) {
+    for (int j = ty; j < g.nr; j += kFJ) {
         const size_t o = sidx(g, j, im, k);
         double2 yr = un[o], yt = un[o + S], yz = un[o + 2 * S];
         if (mean) {
@@ -1095,11 +1373,13 @@ static void single_only(const Geo& g, const char* what) {
 }
 
 void launch_curl(const Geo& g, const double2* u, double2* w, cudaStream_t s) {
-    k_curl<<<spec_grid(g), spec_bx(g), 0, s>>>(g, u, w);
+    if (g.df) k_curl_df<<<spec_grid(g), spec_bx(g), 0, s>>>(g, u, w);
+    else k_curl<<<spec_grid(g), spec_bx(g), 0, s>>>(g, u, w);
     check_launch("curl");
 }
 void launch_curlT_acc(const Geo& g, const double2* wb, double2* ub, cudaStream_t s) {
-    k_curlT_acc<<<spec_grid(g), spec_bx(g), 0, s>>>(g, wb, ub);
+    if (g.df) k_curlT_acc_df<<<spec_grid(g), spec_bx(g), 0, s>>>(g, wb, ub);
+    else k_curlT_acc<<<spec_grid(g), spec_bx(g), 0, s>>>(g, wb, ub);
     check_launch("curlT");
 }
 void launch_grad_u(const Geo& g, const double2* u, double2* G, cudaStream_t s) {
@@ -1121,9 +1401,11 @@ void launch_baseT(const Geo& g, const double2* nb, double2* ub, cudaStream_t s) 
 }
 
 // trans selects the transposed coefficient layout; zero_row0 writes 0 to the
-// wall row of the solution
+// wall row of the solution; pw (forward Helmholtz solves only) receives the
+// wall partials of the tentative velocity, with usub subtracted
 static void launch_band_solve(const Geo& g, const double* fac, size_t fac_stride, double2* X, const double2* add,
-                              int helm, int trans, int zero_row0, cudaStream_t s) {
+                              int helm, int trans, int zero_row0, cudaStream_t s, double* pw = nullptr,
+                              const double2* usub = nullptr) {
     const dim3 nblocks((unsigned)((helm ? 3 : 1) * g.nm * g.ntile), (unsigned)g.nb);
     // columns in registers for the Helmholtz solves (three systems per mode:
     // several warps per scheduler hide the dependent chain); the pressure
@@ -1134,26 +1416,28 @@ static void launch_band_solve(const Geo& g, const double* fac, size_t fac_stride
         if (!trans) {
             smem_limit((const void*)k_band_solve_reg<4, 8, false, kRegRows>);
             k_band_solve_reg<4, 8, false, kRegRows><<<nblocks, 2 * kSK, sm, s>>>(g, fac, fac_stride, X, add, helm,
-                                                                                 zero_row0);
+                                                                                 zero_row0, pw, usub);
         } else {
             smem_limit((const void*)k_band_solve_reg<8, 4, true, kRegRows>);
             k_band_solve_reg<8, 4, true, kRegRows><<<nblocks, 2 * kSK, sm, s>>>(g, fac, fac_stride, X, add, helm,
-                                                                                zero_row0);
+                                                                                zero_row0, nullptr, nullptr);
         }
         return;
     }
     const size_t sm = (size_t)g.nr * kSK * sizeof(double2) + 2 * (size_t)kRC * 9 * kSK * sizeof(double);
     if (!trans) {
         smem_limit((const void*)k_band_solve<4, 8, false>);
-        k_band_solve<4, 8, false><<<nblocks, 2 * kSK, sm, s>>>(g, fac, fac_stride, X, add, helm, zero_row0);
+        k_band_solve<4, 8, false><<<nblocks, 2 * kSK, sm, s>>>(g, fac, fac_stride, X, add, helm, zero_row0, pw, usub);
     } else {
         smem_limit((const void*)k_band_solve<8, 4, true>);
-        k_band_solve<8, 4, true><<<nblocks, 2 * kSK, sm, s>>>(g, fac, fac_stride, X, add, helm, zero_row0);
+        k_band_solve<8, 4, true><<<nblocks, 2 * kSK, sm, s>>>(g, fac, fac_stride, X, add, helm, zero_row0, nullptr,
+                                                              nullptr);
     }
 }
 
 void launch_stage_div(const Geo& g, const double2* F, double2* q, cudaStream_t s) {
-    k_stage_div<<<spec_grid(g), spec_bx(g), 0, s>>>(g, F, q);
+    if (g.df) k_stage_div_df<<<spec_grid(g), spec_bx(g), 0, s>>>(g, F, q);
+    else k_stage_div<<<spec_grid(g), spec_bx(g), 0, s>>>(g, F, q);
     check_launch("stage_div");
 }
 void launch_stage_psolve(const Geo& g, double2* q, cudaStream_t s) {
@@ -1161,22 +1445,22 @@ void launch_stage_psolve(const Geo& g, double2* q, cudaStream_t s) {
     check_launch("stage_psolve");
 }
 void launch_stage_rhs(const Geo& g, const double2* u, const double2* F, const double2* p, double2* R, cudaStream_t s) {
-    k_stage_rhs<<<spec_grid(g), spec_bx(g), 0, s>>>(g, u, F, p, R);
+    if (g.df) k_stage_rhs_df<<<spec_grid(g), spec_bx(g), 0, s>>>(g, u, F, p, R);
+    else k_stage_rhs<<<spec_grid(g), spec_bx(g), 0, s>>>(g, u, F, p, R);
     check_launch("stage_rhs");
 }
-void launch_stage_hsolve(const Geo& g, double2* R, cudaStream_t s) {
-    launch_band_solve(g, g.facH, g.sFacH, R, nullptr, 1, 0, 0, s);
+void launch_stage_hsolve(const Geo& g, double2* R, const double2* usub, double* pw, cudaStream_t s) {
+    launch_band_solve(g, g.facH, g.sFacH, R, nullptr, 1, 0, 0, s, pw, usub);
     check_launch("stage_hsolve");
 }
 static inline dim3 mode_grid(const Geo& g) { return dim3((g.nk + kFK - 1) / kFK, g.nm, g.nb); }
-void launch_stage_finish(const Geo& g, const double2* R, const double2* addto, const double2* usub, double2* out,
-                         cudaStream_t s) {
-    const unsigned nchunk = (unsigned)((g.nr + kFR - 1) / kFR);
-    k_stage_finish<<<dim3((g.nk + kFK - 1) / kFK, g.nm, g.nb * nchunk), dim3(kFK, kFJ), 0, s>>>(g, R, addto, usub, out);
+void launch_stage_finish(const Geo& g, const double2* R, const double2* addto, const double2* usub, const double* pw,
+                         double2* out, cudaStream_t s) {
+    k_stage_finish<<<spec_grid(g), spec_bx(g), 0, s>>>(g, R, addto, usub, reinterpret_cast<const double2*>(pw), out);
     check_launch("stage_finish");
 }
 void launch_stageT_finish(const Geo& g, const double2* ubn, double2* R, double2* ac, int ac_add, cudaStream_t s) {
-    k_stageT_finish<<<mode_grid(g), dim3(kFK, kTJ), 0, s>>>(g, ubn, R, ac, ac_add);
+    k_stageT_finish<<<mode_grid(g), dim3(kFK, kFJ), 0, s>>>(g, ubn, R, ac, ac_add);
     check_launch("stageT_finish");
 }
 void launch_stageT_hsolve(const Geo& g, double2* R, const double2* add, cudaStream_t s) {
@@ -1193,7 +1477,8 @@ void launch_stageT_rhs(const Geo& g, const double2* X, const double2* Y, double 
     check_launch("stageT_rhs");
 }
 void launch_stageT_qbar(const Geo& g, const double2* Fb, double2* q, cudaStream_t s) {
-    k_stageT_qbar<<<spec_grid(g), spec_bx(g), 0, s>>>(g, Fb, q);
+    if (g.df) k_stageT_qbar_df<<<spec_grid(g), spec_bx(g), 0, s>>>(g, Fb, q);
+    else k_stageT_qbar<<<spec_grid(g), spec_bx(g), 0, s>>>(g, Fb, q);
     check_launch("stageT_qbar");
 }
 void launch_stageT_psolve(const Geo& g, double2* q, cudaStream_t s) {
@@ -1201,7 +1486,8 @@ void launch_stageT_psolve(const Geo& g, double2* q, cudaStream_t s) {
     check_launch("stageT_psolve");
 }
 void launch_stageT_div(const Geo& g, const double2* z, double2* Fb, cudaStream_t s) {
-    k_stageT_div<<<spec_grid(g), spec_bx(g), 0, s>>>(g, z, Fb);
+    if (g.df) k_stageT_div_df<<<spec_grid(g), spec_bx(g), 0, s>>>(g, z, Fb);
+    else k_stageT_div<<<spec_grid(g), spec_bx(g), 0, s>>>(g, z, Fb);
     check_launch("stageT_div");
 }
 

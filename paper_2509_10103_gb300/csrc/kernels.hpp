@@ -52,6 +52,15 @@ struct Geo {
     double two_dt[kMaxBatch];    // 2 / dt per slot (A + B = 2 I / dt of the Crank-Nicolson pair)
     double flux_inv[kMaxBatch];  // flux normalisation per slot
     double2 cs[kMaxBatch];       // (cos, sin) of the pulsation phase of entry b at the launch's time
+    // double-FP32 arithmetic for the explicit banded products (df != 0): the
+    // tables as (hi, lo) float pairs, D1 [2][nr][13], 1/r [nr], k_z [nk],
+    // m/r [nm][nr], and 2/dt per slot
+    int df;
+    const float2* D1f;
+    const float2* invrf;
+    const float2* kztf;
+    const float2* mrtf;
+    float2 two_dtf[kMaxBatch];
 };
 
 // Up to 18 input / 6 output spectral component planes for the transforms; the
@@ -117,13 +126,16 @@ void launch_stage_psolve(const Geo& g, double2* q, cudaStream_t s);
 // R = (F - grad p) in the +/- basis, plus (2/dt) T u (rows j >= 1) and T u
 // (wall row) when u is given (u null: forcing-only stage S(0, F))
 void launch_stage_rhs(const Geo& g, const double2* u, const double2* F, const double2* p, double2* R, cudaStream_t s);
-void launch_stage_hsolve(const Geo& g, double2* R, cudaStream_t s);
+// R = A_v^{-1} R; its epilogue writes the wall partials of the tentative
+// velocity (R back to (r, theta, z), usub subtracted when given) to pw
+// ([slot][3][nm][nk] complex): pw[0] + pw[1] = d/dr u_r at the wall,
+// pw[2](m = 0, k = 0) = the flux sum_j W_j u_z
+void launch_stage_hsolve(const Geo& g, double2* R, const double2* usub, double* pw, cudaStream_t s);
 // out = [addto +] finished stage (addto may be null), with the old velocity
-// usub subtracted from the tentative velocity when given: the per-mode wall
-// coefficient (influence) or flux sum (mode (0,0)) and the correction it
-// drives, in one launch
-void launch_stage_finish(const Geo& g, const double2* R, const double2* addto, const double2* usub, double2* out,
-                         cudaStream_t s);
+// usub subtracted from the tentative velocity when given, and the influence
+// (or, for mode (0,0), flux) correction driven by the wall partials pw
+void launch_stage_finish(const Geo& g, const double2* R, const double2* addto, const double2* usub, const double* pw,
+                         double2* out, cudaStream_t s);
 // ---- radial stage (transpose): ub (=, or += when acc) S_u^H ubn, Fb = S_F^H ubn ----
 // R = T^-H Fin^H ubn; the per-mode coefficient of Fin^H to ac[slot][m][k]
 // (added to what ac holds when ac_add)

@@ -117,6 +117,7 @@ struct pnop_ctx {
     double2* R = nullptr;
     double2* Rl = nullptr;  // front part of the transposed stage for the incoming cotangent
     double2* ac = nullptr;  // per-mode coefficients of the transposed influence correction [slot][m][k]
+    double* pw = nullptr;   // wall partials of the forward Helmholtz solve [slot][3][m][k] complex
     double2* q = nullptr;
     double2* q2 = nullptr;  // pressure scratch of the side stream
     cudaStream_t side = nullptr;  // second stream for independent work within a step
@@ -219,6 +220,18 @@ std::vector<double2> cvec(const std::vector<std::complex<double>>& v) {
     return o;
 }
 
+// (hi, lo) float pairs of FP64 values: hi the nearest float, lo the nearest
+// float to the remainder (tables of the double-FP32 kernels)
+float2 split_pair(double x) {
+    const float h = (float)x;
+    return make_float2(h, (float)(x - (double)h));
+}
+std::vector<float2> split_pairs(const std::vector<double>& v) {
+    std::vector<float2> o(v.size());
+    for (size_t i = 0; i < v.size(); ++i) o[i] = split_pair(v[i]);
+    return o;
+}
+
 template <class T2> std::vector<T2> twiddle_table(int N) {
     std::vector<T2> t(N);
     for (int n = 0; n < N; ++n) {
@@ -275,6 +288,7 @@ void upload_slot_operators(pnop_ctx* c, int slot, const pnop::HostOps& h) {
        "upload");
     Geo& g = c->geo;
     g.two_dt[slot] = 2.0 / h.ph.dt;
+    g.two_dtf[slot] = split_pair(2.0 / h.ph.dt);
     g.flux_inv[slot] = h.flux_inv;
     g.Lb = c->d_Lb;
     g.dgt = c->d_dgt;
@@ -292,7 +306,7 @@ void upload_slot_operators(pnop_ctx* c, int slot, const pnop::HostOps& h) {
 // operator tables that depend on Re/dt/Wo/A are re-uploaded on change
 void upload_operators(pnop_ctx* c) { upload_slot_operators(c, 0, c->h); }
 
-bool mixed(const pnop_ctx* c) { return c->prm.precision == PNOP_MIXED; }
+bool mixed(const pnop_ctx* c) { return (c->prm.precision & PNOP_MIXED) != 0; }
 
 void prof_flush(pnop_ctx* c) {
     if (!c->ev_used) return;
@@ -385,9 +399,9 @@ void stage(pnop_ctx* c, const double2* u, const double2* F, double2* out, const 
     run(c, PNOP_K_RADIAL_SOLVE, 1, nmodes(c), [&] { pnop::launch_stage_psolve(g, c->q, s); });
     run(c, PNOP_K_RADIAL_BAND, 1, (flops::rhs + (u ? flops::rhs_u : 0)) * S,
         [&] { pnop::launch_stage_rhs(g, u, F, c->q, c->R, s); });
-    run(c, PNOP_K_RADIAL_SOLVE, 1, 3 * nmodes(c), [&] { pnop::launch_stage_hsolve(g, c->R, s); });
+    run(c, PNOP_K_RADIAL_SOLVE, 1, 3 * nmodes(c), [&] { pnop::launch_stage_hsolve(g, c->R, u, c->pw, s); });
     run(c, PNOP_K_RADIAL_BAND, 1, (flops::finish + (u ? flops::finish_u : 0)) * S + flops::a0_mode * nmodes(c),
-        [&] { pnop::launch_stage_finish(g, c->R, addto, u, out, s); });
+        [&] { pnop::launch_stage_finish(g, c->R, addto, u, c->pw, out, s); });
 }
 
 // out = S(u, F) on the context stream alone (operator access)
@@ -886,6 +900,7 @@ void ensure_shadow(pnop_ctx* c) {
         for (double2** b : {&sh->omega, &sh->N0, &sh->N1, &sh->us, &sh->R, &sh->Nbase, &sh->tmpA, &sh->tmpB})
             *b = sh->field();
         sh->q = (double2*)sh->dalloc(c->S() * sizeof(double2));
+        sh->pw = (double*)sh->dalloc((size_t)3 * c->h.d.nm * c->h.d.nk * sizeof(double2));
         const size_t cz = mixed(c) ? sizeof(float2) : sizeof(double2);
         const size_t plane = (size_t)c->h.d.nr * c->h.d.nth * c->h.d.nk * cz;
         sh->Y = sh->dalloc(9 * plane);
@@ -1487,7 +1502,7 @@ int pnop_context_bytes(const pnop_grid* grid, const pnop_params* params, int sna
     const size_t nr = grid->nr, M = grid->ntheta / 2 - 1, K = grid->nz / 2 - 1;
     const size_t nm = 2 * M + 1, nk = K + 1, nkp = (nk + pnop::kTileK - 1) / pnop::kTileK * pnop::kTileK, nt = 3 * (M + 1);
     const size_t S = nr * nm * nk, field = 3 * S * 16;
-    const size_t cz = params->precision == PNOP_MIXED ? 8 : 16;
+    const size_t cz = (params->precision & PNOP_MIXED) ? 8 : 16;
     size_t b = (21 + (size_t)snaps) * field + 2 * S * 16;              // work fields, u_N, optimiser, host staging, checkpoints, q, q2
     b += 24 * nr * nt * nk * cz;                                         // transform scratch Y, Y2, Z
     b += 10 * field + S * 16 + 15 * nr * nt * nk * cz;                   // recomputation workspace (shadow) and its scratch states
@@ -1510,7 +1525,7 @@ int pnop_batch_bytes(const pnop_grid* grid, const pnop_params* params, int capac
     const size_t nr = grid->nr, M = grid->ntheta / 2 - 1, K = grid->nz / 2 - 1, C = capacity;
     const size_t nm = 2 * M + 1, nk = K + 1, nkp = (nk + pnop::kTileK - 1) / pnop::kTileK * pnop::kTileK, nt = 3 * (M + 1);
     const size_t S = nr * nm * nk, field = 3 * S * 16, snaps = (size_t)params->snap_budget;
-    const size_t cz = params->precision == PNOP_MIXED ? 8 : 16;
+    const size_t cz = (params->precision & PNOP_MIXED) ? 8 : 16;
     size_t b = C * (18 + snaps) * field;                                 // work fields, state, cotangent, result, q, q2, checkpoints
     b += C * 27 * nr * nt * nk * cz;                                     // transform scratch Y, Y2, Z (9 planes each)
     b += C * 2 * (M + 2) * nr * 13 * nkp * 8 + 2 * (M + 1) * nr * 13 * nkp * 8;  // Helmholtz factors per slot, pressure shared
@@ -1584,7 +1599,7 @@ int create_impl(const pnop_grid* grid, const pnop_params* params, void* cuda_str
         !(grid->Lz > 0) || !(grid->stretch >= 0 && grid->stretch < 1))
         return PNOP_ERR_INVALID_ARG;
     if (!(params->Re > 0) || !(params->dt > 0) ||
-        (params->precision != PNOP_FP64 && params->precision != PNOP_MIXED) || !(params->A >= 0) ||
+        params->precision < PNOP_FP64 || params->precision > PNOP_MIXED_DF || !(params->A >= 0) ||
         !(params->Wo > 0 || params->A == 0))
         return PNOP_ERR_INVALID_ARG;
     const int M = grid->ntheta / 2 - 1, K = grid->nz / 2 - 1;
@@ -1637,6 +1652,13 @@ int create_impl(const pnop_grid* grid, const pnop_params* params, void* cuda_str
                 for (int j = 0; j < d.nr; ++j) mr[(size_t)im * d.nr + j] = (im - M) * c->h.invr[j];
             g.kzt = c->upload(kz);
             g.mrt = c->upload(mr);
+            g.df = (params->precision & PNOP_DF) ? 1 : 0;
+            if (g.df) {
+                g.D1f = c->upload(split_pairs(c->h.D1));
+                g.invrf = c->upload(split_pairs(c->h.invr));
+                g.kztf = c->upload(split_pairs(kz));
+                g.mrtf = c->upload(split_pairs(mr));
+            }
         }
         upload_operators(c);
         auto thd = twiddle_table<double2>(d.nth), zd = twiddle_table<double2>(d.nzp);
@@ -1649,6 +1671,7 @@ int create_impl(const pnop_grid* grid, const pnop_params* params, void* cuda_str
                             &c->Rl, &c->Nbase})
             *b = c->field();
         c->ac = (double2*)c->dalloc((size_t)nslot * d.nm * d.nk * sizeof(double2));
+        c->pw = (double*)c->dalloc((size_t)nslot * 3 * d.nm * d.nk * sizeof(double2));
         if (batched) {  // per-slot state, cotangent and energies replace the sweep buffers
             c->bcur = c->field();
             c->blam = c->field();
