@@ -296,6 +296,8 @@ def accuracy_vs_fp64(L, torch, H, snaps, precisions):
 
 
 PREC_NAMES = {0: "fp64", 1: "mixed", 2: "df", 3: "mixed_df"}
+DTYPES = {0: "f64", 1: "f32 transforms + f64", 2: "double-f32 banded products + f64",
+          3: "f32 transforms + double-f32 banded products + f64"}
 
 
 def time_single_steps(L, torch, precision, reps=20):
@@ -718,8 +720,9 @@ def main():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the single-step timings and the budget sweep (profiling runs)")
-    ap.add_argument("--precision", default="both", choices=["both", "mixed", "fp64"],
-                    help="which path(s) to time; 'fp64' reports the FP64 path as the main line")
+    ap.add_argument("--precision", default="both", choices=["both", "mixed_df", "mixed", "fp64"],
+                    help="which path(s) to time: 'both' times the mixed path with double-FP32 banded products as the"
+                         " main line and the FP64 and plain mixed paths beside it; the others time one path")
     ap.add_argument("--optimise-full", action="store_true",
                     help="print only the adjoint-looping run on the full deceleration horizon (19,635 steps)")
     ap.add_argument("--opt-iters", type=int, default=10)
@@ -760,25 +763,25 @@ def main():
     sampler = ClockSampler(local) if rank == 0 else None
     if args.precision == "fp64":
         args.no_fp64 = True
-    main_prec = L.PNOP_FP64 if args.precision == "fp64" else L.PNOP_MIXED
+    # the main line: the mixed-precision path (FP32 transforms and products,
+    # double-FP32 banded products, FP64 solves, corrections and inner
+    # products) unless one path is asked for; the others are reported beside it
+    main_prec = {"both": L.PNOP_MIXED_DF, "mixed_df": L.PNOP_MIXED_DF, "mixed": L.PNOP_MIXED,
+                 "fp64": L.PNOP_FP64}[args.precision]
     mix = time_gradient(L, torch, main_prec, args.steps, args.warmup, H, s, ws, rank, sampler)
     ms = max_over_ranks(mix["ms"], ws)
     value = aggregate_value(H, args.steps, ws, ms)
-    fp64 = None
-    if not args.no_fp64 and args.precision != "mixed":
-        f = time_gradient(L, torch, L.PNOP_FP64, args.steps, args.warmup, H, s, ws, rank, None)
+
+    def side_path(prec):
+        f = time_gradient(L, torch, prec, args.steps, args.warmup, H, s, ws, rank, None)
         fms = max_over_ranks(f["ms"], ws)
-        fp64 = {"value": H * args.steps * ws / (fms / 1e3), "unit": "steps/s", "ms_per_step": fms / args.steps,
-                "gain": f["gain"], "dtype": "f64", "roofline": roofline(L, f, False, peaks, pk_src, alu),
+        return {"value": H * args.steps * ws / (fms / 1e3), "unit": "steps/s", "ms_per_step": fms / args.steps,
+                "gain": f["gain"], "dtype": DTYPES[prec],
+                "roofline": roofline(L, f, (prec & L.PNOP_MIXED) != 0, peaks, pk_src, alu),
                 "kernels_ms_per_step": {k: v[0] for k, v in f["warm_profile"].items()}}
-    mixed_df = None
-    if args.precision == "both":
-        f = time_gradient(L, torch, L.PNOP_MIXED_DF, args.steps, args.warmup, H, s, ws, rank, None)
-        fms = max_over_ranks(f["ms"], ws)
-        mixed_df = {"value": H * args.steps * ws / (fms / 1e3), "unit": "steps/s", "ms_per_step": fms / args.steps,
-                    "gain": f["gain"], "dtype": "f32 transforms + double-f32 banded products + f64",
-                    "roofline": roofline(L, f, True, peaks, pk_src, alu),
-                    "kernels_ms_per_step": {k: v[0] for k, v in f["warm_profile"].items()}}
+
+    fp64 = side_path(L.PNOP_FP64) if (not args.no_fp64 and args.precision == "both") else None
+    mixed_plain = side_path(L.PNOP_MIXED) if args.precision == "both" else None
     e2e_s = time_e2e(L, torch, main_prec, args.steps, args.warmup, H, s)
     e2e_s = max_over_ranks(e2e_s, ws)
     if rank != 0:
@@ -788,20 +791,20 @@ def main():
         "metric": "fwd+adj steps/s at 64x64x256, mixed vs FP64 on 1 GB300; serving p50/p99 latency",
         "value": value, "unit": "steps/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64" if main_prec == L.PNOP_FP64 else "f32+f64", "data": "synthetic",
+        "dtype": DTYPES[main_prec], "precision": PREC_NAMES[main_prec], "data": "synthetic",
         "config": {"workload": workload_name(H, s), "horizon_steps": H, "snap_budget": s,
                    "advances_per_gradient": mix["advances"], "adjoint_steps_per_gradient": mix["adjoint_steps"],
                    "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
                    "l2": f"inputs and working set > L2 (state {FIELD_BYTES / 2**20:.1f} MiB x >20 buffers + transform"
                          " scratch); no flush"},
         "gain": mix["gain"],
-        "roofline": roofline(L, mix, main_prec == L.PNOP_MIXED, peaks, pk_src, alu),
+        "roofline": roofline(L, mix, (main_prec & L.PNOP_MIXED) != 0, peaks, pk_src, alu),
         "alu_peaks_measured_tflops": alu,
         "kernels_ms_per_step": {k: v[0] for k, v in mix["warm_profile"].items()},
         "fp64": fp64,
         "speedup_mixed_over_fp64": (value / fp64["value"]) if fp64 else None,
-        "mixed_df": mixed_df,
-        "speedup_mixed_df_over_fp64": (mixed_df["value"] / fp64["value"]) if (fp64 and mixed_df) else None,
+        "mixed_fp64_banded": mixed_plain,
+        "speedup_mixed_fp64_banded_over_fp64": (mixed_plain["value"] / fp64["value"]) if (fp64 and mixed_plain) else None,
         "e2e": {"value": H * args.steps * ws / e2e_s, "unit": "steps/s", "h2d_bytes_per_step": FIELD_BYTES,
                 "d2h_bytes_per_step": FIELD_BYTES + 24},
         "gpu_launches": launches,

@@ -1062,6 +1062,122 @@ __global__ void k_stageT_rhs(Geo g, const double2* __restrict__ X, const double2
     }
 }
 
+// k_stageT_rhs in double-float arithmetic (PNOP_DF): the same outputs with
+// every sum and scaling in double-FP32 and one FP64 addition per output part
+template <bool TWO>
+__global__ void k_stageT_rhs_df(Geo g, const double2* __restrict__ X, const double2* __restrict__ Y, double cf1,
+                                double cf2, double2* __restrict__ ub, int acc, double2* __restrict__ Fb,
+                                const double2* __restrict__ V1, const double2* __restrict__ V2,
+                                const double2* __restrict__ ac) {
+    Idx d;
+    if (!decode(g, d)) return;
+    X += d.off;
+    Y = moved(Y, d.off);
+    ub = moved(ub, d.off);
+    Fb = moved(Fb, d.off);
+    V1 = moved(V1, d.off);
+    V2 = moved(V2, d.off);
+    const size_t o = sidx(g, d.j, d.im, d.k), S = d.S;
+    const dfc rp = df_load(X + o), rm = df_load(X + o + S), rz = df_load(X + o + 2 * S);
+    if (ub) {
+        dfl f;
+        f.h = 1.f;
+        f.l = 0.f;
+        if (d.j != 0) f = dff(g.two_dtf[d.slot]);
+        // T^H (f rp, f rm, f rz) - Fin^H (V1 + V2): r = f (rp + rm), theta = f (i... ) as in k_stageT_rhs
+        dacc2 vr{dacc0(), dacc0()}, vt{dacc0(), dacc0()}, vz{dacc0(), dacc0()};
+        df_fma(vr.re, f, rp.re);
+        df_fma(vr.re, f, rm.re);
+        df_fma(vr.im, f, rp.im);
+        df_fma(vr.im, f, rm.im);
+        df_fma(vt.re, f, rp.im);
+        df_fma(vt.re, df_neg(f), rm.im);
+        df_fma(vt.im, df_neg(f), rp.re);
+        df_fma(vt.im, f, rm.re);
+        df_fma(vz.re, f, rz.re);
+        df_fma(vz.im, f, rz.im);
+        const dfc a = df_load(V1 + o), b = df_load(V1 + o + S), c = df_load(V1 + o + 2 * S);
+        const bool mean = d.m == 0 && d.k == 0;
+        if (!mean) {
+            df_add(vr.re, df_neg(a.re));
+            df_add(vr.im, df_neg(a.im));
+        }
+        df_add(vt.re, df_neg(b.re));
+        df_add(vt.im, df_neg(b.im));
+        df_add(vz.re, df_neg(c.re));
+        df_add(vz.im, df_neg(c.im));
+        if (V2) {
+            const dfc a2 = df_load(V2 + o), b2 = df_load(V2 + o + S), c2 = df_load(V2 + o + 2 * S);
+            if (!mean) {
+                df_add(vr.re, df_neg(a2.re));
+                df_add(vr.im, df_neg(a2.im));
+            }
+            df_add(vt.re, df_neg(b2.re));
+            df_add(vt.im, df_neg(b2.im));
+            df_add(vz.re, df_neg(c2.re));
+            df_add(vz.im, df_neg(c2.im));
+        }
+        const double2 cm = ac[((size_t)d.slot * g.nm + d.im) * g.nk + d.k];
+        if (mean) {  // Fin^H: u_r = 0, u_z gains -flux_inv W_j cm
+            const dfl kf = df_split(g.flux_inv[d.slot] * g.W[d.j]);
+            df_fma(vz.re, kf, df_split(cm.x));
+            df_fma(vz.im, kf, df_split(cm.y));
+        } else if (d.j <= 8) {  // Fin^H: u_r rows 0..8 gain d0_j cm
+            const dfl kd = df_split(__ldg(g.D1 + (size_t)par_idx(d.m + 1) * g.nr * kB + 4 + d.j));
+            df_fma(vr.re, df_neg(kd), df_split(cm.x));
+            df_fma(vr.im, df_neg(kd), df_split(cm.y));
+        }
+        double2 outr = df_out(vr), outt = df_out(vt), outz = df_out(vz);
+        if (acc) {
+            const double2 pa = ub[o], pb = ub[o + S], pc = ub[o + 2 * S];
+            outr = make_double2(outr.x + pa.x, outr.y + pa.y);
+            outt = make_double2(outt.x + pb.x, outt.y + pb.y);
+            outz = make_double2(outz.x + pc.x, outz.y + pc.y);
+        }
+        ub[o] = outr;
+        ub[o + S] = outt;
+        ub[o + 2 * S] = outz;
+    }
+    if (Fb) {
+        if (d.j == 0) {
+            Fb[o] = Fb[o + S] = Fb[o + 2 * S] = make_double2(0, 0);
+            return;
+        }
+        const dfl k1 = df_split(cf1);
+        dacc2 p{dacc0(), dacc0()}, q{dacc0(), dacc0()}, z{dacc0(), dacc0()};
+        df_fma(p.re, k1, rp.re);
+        df_fma(p.im, k1, rp.im);
+        df_fma(q.re, k1, rm.re);
+        df_fma(q.im, k1, rm.im);
+        df_fma(z.re, k1, rz.re);
+        df_fma(z.im, k1, rz.im);
+        if (TWO) {
+            const dfl k2 = df_split(cf2);
+            const dfc ya = df_load(Y + o), yb = df_load(Y + o + S), yc = df_load(Y + o + 2 * S);
+            df_fma(p.re, k2, ya.re);
+            df_fma(p.im, k2, ya.im);
+            df_fma(q.re, k2, yb.re);
+            df_fma(q.im, k2, yb.im);
+            df_fma(z.re, k2, yc.re);
+            df_fma(z.im, k2, yc.im);
+        }
+        // (p + q, (p.y - q.y, -p.x + q.x), z)
+        const dfl pr = df_val(p.re), pi = df_val(p.im), qr = df_val(q.re), qi = df_val(q.im);
+        dacc2 fr{dacc0(), dacc0()}, ft{dacc0(), dacc0()};
+        df_add(fr.re, pr);
+        df_add(fr.re, qr);
+        df_add(fr.im, pi);
+        df_add(fr.im, qi);
+        df_add(ft.re, pi);
+        df_add(ft.re, df_neg(qi));
+        df_add(ft.im, df_neg(pr));
+        df_add(ft.im, qr);
+        Fb[o] = df_out(fr);
+        Fb[o + S] = df_out(ft);
+        Fb[o + 2 * S] = df_out(z);
+    }
+}
+
 // qbar = G^H Fb' = D1p^T Fb'_r - i (m/r) Fb'_t - i kz Fb'_z
 __global__ void k_stageT_qbar(Geo g, const double2* __restrict__ Fb, double2* __restrict__ q) {
     Idx d;
@@ -1470,10 +1586,16 @@ void launch_stageT_hsolve(const Geo& g, double2* R, const double2* add, cudaStre
 void launch_stageT_rhs(const Geo& g, const double2* X, const double2* Y, double cf1, double cf2, double2* ub, int acc,
                        double2* Fb, const double2* V1, const double2* V2, const double2* ac, cudaStream_t s) {
     if (ub && (!V1 || !ac)) throw std::runtime_error("stageT_rhs: the velocity part needs its input and coefficients");
-    if (Y)
+    if (g.df) {
+        if (Y)
+            k_stageT_rhs_df<true><<<spec_grid(g), spec_bx(g), 0, s>>>(g, X, Y, cf1, cf2, ub, acc, Fb, V1, V2, ac);
+        else
+            k_stageT_rhs_df<false><<<spec_grid(g), spec_bx(g), 0, s>>>(g, X, Y, cf1, cf2, ub, acc, Fb, V1, V2, ac);
+    } else if (Y) {
         k_stageT_rhs<true><<<spec_grid(g), spec_bx(g), 0, s>>>(g, X, Y, cf1, cf2, ub, acc, Fb, V1, V2, ac);
-    else
+    } else {
         k_stageT_rhs<false><<<spec_grid(g), spec_bx(g), 0, s>>>(g, X, Y, cf1, cf2, ub, acc, Fb, V1, V2, ac);
+    }
     check_launch("stageT_rhs");
 }
 void launch_stageT_qbar(const Geo& g, const double2* Fb, double2* q, cudaStream_t s) {
