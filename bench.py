@@ -515,13 +515,17 @@ def serving_report(L, nreq=256, probe=48, load=0.7, seed=0, budget=40 << 30, max
     from paper_2509_10103_gb300 import serving
     reqs = _serving_requests(L, probe, seed + 1, np.zeros(probe), full)
     t0 = time.perf_counter()
-    res, _ = serving.serve_stream(reqs, hbm_budget=budget, max_active=max_active, batched=batched)
+    # both servers run at most max_active requests at once (the batched one over all its batches)
+    cap_total = max_active if batched else None
+    res, _ = serving.serve_stream(reqs, hbm_budget=budget, max_active=max_active, batched=batched,
+                                  max_active_total=cap_total)
     cap = sum(r.error is None for r in res) / (time.perf_counter() - t0)
     rate = load * cap
     gaps = np.random.default_rng(seed + 2).exponential(1.0 / rate, nreq)
     reqs = _serving_requests(L, nreq, seed, np.cumsum(gaps), full)
     t0 = time.perf_counter()
-    res, srv = serving.serve_stream(reqs, hbm_budget=budget, max_active=max_active, batched=batched)
+    res, srv = serving.serve_stream(reqs, hbm_budget=budget, max_active=max_active, batched=batched,
+                                    max_active_total=cap_total)
     wall = time.perf_counter() - t0
     ok = [r for r in res if r.error is None]
     steps = sum(int(round(q.horizon / q.dt)) for q, r in zip(reqs, res) if r.error is None)
@@ -536,7 +540,8 @@ def serving_report(L, nreq=256, probe=48, load=0.7, seed=0, budget=40 << 30, max
             "horizons": "200-2000 steps of dt=0.005 (1-10 time units), 64 checkpoint slots" if full else
                         "10-50 steps of dt=0.005, 8 checkpoint slots",
             "arrivals": f"Poisson at {load} x measured capacity",
-            "server": "batched launches per resolution (BatchServer)" if batched else "one context and stream per request",
+            "server": (f"batched launches per resolution (BatchServer), at most {max_active} requests running"
+                       if batched else f"one context and stream per request, at most {max_active} running"),
             "peak_requests_in_one_batch": getattr(srv, "peak_batch", None),
             "peak_batches_of_one_resolution": getattr(srv, "peak_batches_per_kind", None),
             "batches_created": getattr(srv, "batches_made", None)}

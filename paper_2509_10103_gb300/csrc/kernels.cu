@@ -523,7 +523,7 @@ __device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_g
 // (nearest first) for the backward sweep.  X = A^{-1} X [+ add].
 // Batch entry blockIdx.y; its factor table sits at fac + slot * fac_stride
 // (stride 0: a table shared by all slots).
-template <int NL, int NU, bool DIAG1>
+template <int NL, int NU, bool DIAG1, bool WALL>
 __global__ void __launch_bounds__(2 * kSK) k_band_solve(Geo g, const double* __restrict__ fac, size_t fac_stride,
                                                   double2* __restrict__ X, const double2* __restrict__ add, int helm,
                                                   int zero_row0, double* __restrict__ pw,
@@ -622,7 +622,7 @@ __global__ void __launch_bounds__(2 * kSK) k_band_solve(Geo g, const double* __r
         }
         __syncthreads();
     }
-    if (pw && k0 + sy < g.nk) {  // wall partials of the tentative velocity (as in k_band_solve_reg)
+    if (WALL && k0 + sy < g.nk) {  // wall partials of the tentative velocity (as in k_band_solve_reg)
         usub = moved(usub, off);
         const double* us = usub ? reinterpret_cast<const double*>(usub) + comp : nullptr;
         double* P = pw + ((((size_t)slot * 3 + v) * g.nm + im) * g.nk + (k0 + sy)) * 2 + comp;
@@ -666,7 +666,7 @@ __global__ void __launch_bounds__(2 * kSK) k_band_solve(Geo g, const double* __r
 // chain of a row; shared memory holds only the staged coefficient rows.  The
 // arithmetic and its order are those of k_band_solve: the results are the
 // same to the last bit (up to the sign of zero).
-template <int NL, int NU, bool DIAG1, int MAXR>
+template <int NL, int NU, bool DIAG1, int MAXR, bool WALL>
 __global__ void __launch_bounds__(2 * kSK) k_band_solve_reg(Geo g, const double* __restrict__ fac, size_t fac_stride,
                                                       double2* __restrict__ X, const double2* __restrict__ add,
                                                       int helm, int zero_row0, double* __restrict__ pw,
@@ -769,34 +769,6 @@ __global__ void __launch_bounds__(2 * kSK) k_band_solve_reg(Geo g, const double*
         }
     }
     if (!on) return;
-    if (pw) {  // wall partials of the tentative velocity (see wall_partials_at)
-        usub = moved(usub, off);
-        const double* us = usub ? reinterpret_cast<const double*>(usub) + comp : nullptr;
-        double* P = pw + ((((size_t)slot * 3 + v) * g.nm + im) * g.nk + (k0 + sy)) * 2 + comp;
-        if (v < 2) {
-            const double* d0 = g.D1 + (size_t)par_idx(m + 1) * nr * kB + 4;
-            double acc = 0.0;
-#pragma unroll
-            for (int c = 0; c <= 8; ++c) {
-                if (c < nr) {
-                    double xv = 0.5 * x[c];
-                    if (v == 0 && us) xv -= us[2 * sidx(g, c, im, k0 + sy)];
-                    acc = fma(__ldg(d0 + c), xv, acc);
-                }
-            }
-            *P = acc;
-        } else if (m == 0 && k0 + sy == 0) {  // the mean mode's flux sum_j W_j (x_z - usub_z)
-            double acc = 0.0;
-#pragma unroll
-            for (int j = 0; j < MAXR; ++j) {
-                if (j < nr) {
-                    const double xv = us ? x[j] - us[2 * (2 * S + sidx(g, j, im, 0))] : x[j];
-                    acc = fma(g.W[j], xv, acc);
-                }
-            }
-            *P = acc;
-        }
-    }
     double* xo = reinterpret_cast<double*>(X + (size_t)v * S) + comp;
     const double* ad = add ? reinterpret_cast<const double*>(add + (size_t)v * S) + comp : nullptr;
 #pragma unroll
@@ -806,6 +778,34 @@ __global__ void __launch_bounds__(2 * kSK) k_band_solve_reg(Geo g, const double*
             double val = (zero_row0 && j == 0) ? 0.0 : x[j];
             if (ad) val += ad[o];
             xo[o] = val;
+        }
+    }
+    // wall partials of the tentative velocity (forward Helmholtz solves), from
+    // the column just written (so that no register holds the column longer):
+    // the wall derivative part, rows 0..8, or the mean mode's flux
+    if (WALL) {
+        usub = moved(usub, off);
+        const double* us = usub ? reinterpret_cast<const double*>(usub) + comp : nullptr;
+        double* P = pw + ((((size_t)slot * 3 + v) * g.nm + im) * g.nk + (k0 + sy)) * 2 + comp;
+        if (v < 2) {
+            const double* d0 = g.D1 + (size_t)par_idx(m + 1) * nr * kB + 4;
+            double acc = 0.0;
+#pragma unroll 1
+            for (int c = 0; c <= 8 && c < nr; ++c) {
+                const size_t o = 2 * sidx(g, c, im, k0 + sy);
+                double xv = 0.5 * xo[o];
+                if (v == 0 && us) xv -= us[o];
+                acc = fma(__ldg(d0 + c), xv, acc);
+            }
+            *P = acc;
+        } else if (m == 0 && k0 + sy == 0) {  // sum_j W_j (x_z - usub_z)
+            double acc = 0.0;
+#pragma unroll 1
+            for (int j = 0; j < nr; ++j) {
+                const size_t o = 2 * sidx(g, j, im, 0);
+                acc = fma(g.W[j], us ? xo[o] - us[2 * 2 * S + o] : xo[o], acc);
+            }
+            *P = acc;
         }
     }
 }
@@ -921,6 +921,88 @@ __global__ void k_stage_finish(Geo g, const double2* __restrict__ R, const doubl
     out[o] = ur;
     out[o + S] = ut;
     out[o + 2 * S] = uz;
+}
+
+// k_stage_finish in double-float arithmetic (PNOP_DF): the same combination
+// with one FP64 addition per output part
+__global__ void k_stage_finish_df(Geo g, const double2* __restrict__ R, const double2* __restrict__ addto,
+                                  const double2* __restrict__ usub, const double2* __restrict__ pw,
+                                  double2* __restrict__ out) {
+    Idx d;
+    if (!decode(g, d)) return;
+    R += d.off;
+    addto = moved(addto, d.off);
+    usub = moved(usub, d.off);
+    out += d.off;
+    const size_t o = sidx(g, d.j, d.im, d.k), S = d.S, nmk = (size_t)g.nm * g.nk;
+    const bool mean = d.m == 0 && d.k == 0;
+    const double2* P = pw + (size_t)d.slot * 3 * nmk + (size_t)d.im * g.nk + d.k;
+    dfc a0;
+    if (mean) {
+        a0 = df_load(P + 2 * nmk);
+    } else {
+        const dfc p0 = df_load(P), p1 = df_load(P + nmk);
+        dacc s0 = dacc0(), s1 = dacc0();
+        df_add(s0, p0.re);
+        df_add(s0, p1.re);
+        df_add(s1, p0.im);
+        df_add(s1, p1.im);
+        a0.re = df_val(s0);
+        a0.im = df_val(s1);
+    }
+    const dfc xp = df_load(R + o), xm = df_load(R + o + S), xz = df_load(R + o + 2 * S);
+    dfl half;
+    half.h = 0.5f;
+    half.l = 0.f;
+    // u_r = (x+ + x-)/2, u_theta = (x+ - x-)/(2i), u_z
+    dacc2 ur{dacc0(), dacc0()}, ut{dacc0(), dacc0()}, uz{dacc0(), dacc0()};
+    df_fma(ur.re, half, xp.re);
+    df_fma(ur.re, half, xm.re);
+    df_fma(ur.im, half, xp.im);
+    df_fma(ur.im, half, xm.im);
+    df_fma(ut.re, half, xp.im);
+    df_fma(ut.re, df_neg(half), xm.im);
+    df_fma(ut.im, df_neg(half), xp.re);
+    df_fma(ut.im, half, xm.re);
+    df_add(uz.re, xz.re);
+    df_add(uz.im, xz.im);
+    if (usub) {
+        const dfc a = df_load(usub + o), b = df_load(usub + o + S), c = df_load(usub + o + 2 * S);
+        df_add(ur.re, df_neg(a.re));
+        df_add(ur.im, df_neg(a.im));
+        df_add(ut.re, df_neg(b.re));
+        df_add(ut.im, df_neg(b.im));
+        df_add(uz.re, df_neg(c.re));
+        df_add(uz.im, df_neg(c.im));
+    }
+    if (mean) {
+        const dfl f = df_split(slot_fluxg(g, d.slot)[d.j] * (-g.flux_inv[d.slot]));
+        df_fma(uz.re, f, a0.re);
+        df_fma(uz.im, f, a0.im);
+        ur = dacc2{dacc0(), dacc0()};
+    } else {
+        const double* h = slot_infl(g, d.slot);
+        const dfl h0 = df_split(infl_at(h, g, d.im, 0, d.j, d.k)), h1 = df_split(infl_at(h, g, d.im, 1, d.j, d.k)),
+                  h2 = df_split(infl_at(h, g, d.im, 2, d.j, d.k));
+        df_fma(ur.re, h0, a0.re);
+        df_fma(ur.im, h0, a0.im);
+        df_fma(ut.re, df_neg(h1), a0.im);  // ut += i h1 a0
+        df_fma(ut.im, h1, a0.re);
+        df_fma(uz.re, df_neg(h2), a0.im);
+        df_fma(uz.im, h2, a0.re);
+    }
+    if (addto) {
+        const dfc a = df_load(addto + o), b = df_load(addto + o + S), c = df_load(addto + o + 2 * S);
+        df_add(ur.re, a.re);
+        df_add(ur.im, a.im);
+        df_add(ut.re, b.re);
+        df_add(ut.im, b.im);
+        df_add(uz.re, c.re);
+        df_add(uz.im, c.im);
+    }
+    out[o] = df_out(ur);
+    out[o + S] = df_out(ut);
+    out[o + 2 * S] = df_out(uz);
 }
 
 // ------------------------------------------------------------------ radial stage (transpose)
@@ -1526,28 +1608,40 @@ static void launch_band_solve(const Geo& g, const double* fac, size_t fac_stride
     // columns in registers for the Helmholtz solves (three systems per mode:
     // several warps per scheduler hide the dependent chain); the pressure
     // solve, one system per mode and about one warp per scheduler, keeps the
-    // shared-memory form, which measured faster there
+    // shared-memory form, which measured faster there.  Only the forward
+    // Helmholtz instance carries the wall-partial epilogue (pw).
     if (helm && g.nr <= kRegRows) {
         const size_t sm = 2 * (size_t)kRC * 9 * kSK * sizeof(double);
-        if (!trans) {
-            smem_limit((const void*)k_band_solve_reg<4, 8, false, kRegRows>);
-            k_band_solve_reg<4, 8, false, kRegRows><<<nblocks, 2 * kSK, sm, s>>>(g, fac, fac_stride, X, add, helm,
-                                                                                 zero_row0, pw, usub);
+        if (!trans && pw) {
+            smem_limit((const void*)k_band_solve_reg<4, 8, false, kRegRows, true>);
+            k_band_solve_reg<4, 8, false, kRegRows, true><<<nblocks, 2 * kSK, sm, s>>>(g, fac, fac_stride, X, add,
+                                                                                       helm, zero_row0, pw, usub);
+        } else if (!trans) {
+            smem_limit((const void*)k_band_solve_reg<4, 8, false, kRegRows, false>);
+            k_band_solve_reg<4, 8, false, kRegRows, false><<<nblocks, 2 * kSK, sm, s>>>(g, fac, fac_stride, X, add,
+                                                                                        helm, zero_row0, nullptr,
+                                                                                        nullptr);
         } else {
-            smem_limit((const void*)k_band_solve_reg<8, 4, true, kRegRows>);
-            k_band_solve_reg<8, 4, true, kRegRows><<<nblocks, 2 * kSK, sm, s>>>(g, fac, fac_stride, X, add, helm,
-                                                                                zero_row0, nullptr, nullptr);
+            smem_limit((const void*)k_band_solve_reg<8, 4, true, kRegRows, false>);
+            k_band_solve_reg<8, 4, true, kRegRows, false><<<nblocks, 2 * kSK, sm, s>>>(g, fac, fac_stride, X, add,
+                                                                                       helm, zero_row0, nullptr,
+                                                                                       nullptr);
         }
         return;
     }
     const size_t sm = (size_t)g.nr * kSK * sizeof(double2) + 2 * (size_t)kRC * 9 * kSK * sizeof(double);
-    if (!trans) {
-        smem_limit((const void*)k_band_solve<4, 8, false>);
-        k_band_solve<4, 8, false><<<nblocks, 2 * kSK, sm, s>>>(g, fac, fac_stride, X, add, helm, zero_row0, pw, usub);
+    if (!trans && pw) {
+        smem_limit((const void*)k_band_solve<4, 8, false, true>);
+        k_band_solve<4, 8, false, true><<<nblocks, 2 * kSK, sm, s>>>(g, fac, fac_stride, X, add, helm, zero_row0, pw,
+                                                                     usub);
+    } else if (!trans) {
+        smem_limit((const void*)k_band_solve<4, 8, false, false>);
+        k_band_solve<4, 8, false, false><<<nblocks, 2 * kSK, sm, s>>>(g, fac, fac_stride, X, add, helm, zero_row0,
+                                                                      nullptr, nullptr);
     } else {
-        smem_limit((const void*)k_band_solve<8, 4, true>);
-        k_band_solve<8, 4, true><<<nblocks, 2 * kSK, sm, s>>>(g, fac, fac_stride, X, add, helm, zero_row0, nullptr,
-                                                              nullptr);
+        smem_limit((const void*)k_band_solve<8, 4, true, false>);
+        k_band_solve<8, 4, true, false><<<nblocks, 2 * kSK, sm, s>>>(g, fac, fac_stride, X, add, helm, zero_row0,
+                                                                     nullptr, nullptr);
     }
 }
 
@@ -1572,7 +1666,9 @@ void launch_stage_hsolve(const Geo& g, double2* R, const double2* usub, double* 
 static inline dim3 mode_grid(const Geo& g) { return dim3((g.nk + kFK - 1) / kFK, g.nm, g.nb); }
 void launch_stage_finish(const Geo& g, const double2* R, const double2* addto, const double2* usub, const double* pw,
                          double2* out, cudaStream_t s) {
-    k_stage_finish<<<spec_grid(g), spec_bx(g), 0, s>>>(g, R, addto, usub, reinterpret_cast<const double2*>(pw), out);
+    const double2* p2 = reinterpret_cast<const double2*>(pw);
+    if (g.df) k_stage_finish_df<<<spec_grid(g), spec_bx(g), 0, s>>>(g, R, addto, usub, p2, out);
+    else k_stage_finish<<<spec_grid(g), spec_bx(g), 0, s>>>(g, R, addto, usub, p2, out);
     check_launch("stage_finish");
 }
 void launch_stageT_finish(const Geo& g, const double2* ubn, double2* R, double2* ac, int ac_add, cudaStream_t s) {

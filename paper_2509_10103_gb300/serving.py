@@ -237,7 +237,11 @@ class BatchServer:
     Slots follow the arrival mix: when every slot of a kind is busy and more
     of its requests are waiting, another batch of that kind is created if the
     HBM budget allows (up to `max_batches_per_kind`, default unlimited), so a
-    resolution that receives more requests gets more slots.  A batch's device
+    resolution that receives more requests gets more slots.  Prepared requests
+    are admitted in arrival order across kinds, and `max_active_total` (default
+    unlimited) caps the requests running at once over all batches: more
+    concurrent requests add throughput only while the GPU has room, and beyond
+    that they lengthen every request's latency.  A batch's device
     memory (pnop_batch_bytes) is counted against the budget from its creation;
     idle batches are released when another batch needs the memory, first
     those of kinds with nothing waiting.
@@ -255,7 +259,8 @@ class BatchServer:
 
     def __init__(self, hbm_budget: int, slots: int = 8, ticks: int = 4, device: int = 0, batch_factory=None,
                  sizer=None, rounds: int = 3, workers: int = 4, opt_active: int = 2, opt_runner=None,
-                 opt_sizer=None, max_batches_per_kind: Optional[int] = None):
+                 opt_sizer=None, max_batches_per_kind: Optional[int] = None,
+                 max_active_total: Optional[int] = None):
         """batch_factory(request, slots, stream) -> batch object (pnop_batch_prepare / submit_prepared /
         run / poll / result / close, as _lib.Batch) and sizer(request, slots) -> bytes replace the GPU
         batch and the library estimate (host-side tests)."""
@@ -265,6 +270,7 @@ class BatchServer:
         self.ticks = ticks
         self.max_rounds = rounds
         self.max_batches = max_batches_per_kind
+        self.max_total = max_active_total
         self.device = device
         self.factory = batch_factory
         self.sizer = sizer
@@ -420,22 +426,39 @@ class BatchServer:
             return None
         return self._new_batch(kd, r)
 
-    def _admit(self, kd) -> bool:
+    def _admit_all(self) -> bool:
+        """Prepared requests into slots, oldest arrival first over all kinds."""
         did = False
-        for item in [x for x in kd["prepared"] if x[1].done() and self._dropped(x[0])]:
-            kd["prepared"].remove(item)
-            r, fut = item
-            try:
-                _lib_free(kd, fut.result())
-            except Exception:
-                pass
-            self._finish(r, float("nan"), float("nan"), None, self._dropped(r))
-            did = True
+        for kd in self.kinds.values():
+            for item in [x for x in kd["prepared"] if x[1].done() and self._dropped(x[0])]:
+                kd["prepared"].remove(item)
+                r, fut = item
+                try:
+                    _lib_free(kd, fut.result())
+                except Exception:
+                    pass
+                self._finish(r, float("nan"), float("nan"), None, self._dropped(r))
+                did = True
+        blocked = set()
+        while self.max_total is None or self.active < self.max_total:
+            cands = [(kd["prepared"][0][0].arrival, key) for key, kd in self.kinds.items()
+                     if key not in blocked and kd["prepared"] and kd["prepared"][0][1].done()]
+            if not cands:
+                break
+            key = min(cands)[1]
+            if self._admit_one(self.kinds[key]):
+                did = True
+            else:
+                blocked.add(key)
+        return did
+
+    def _admit_one(self, kd) -> bool:
+        """The head of the kind's prepared queue into a slot; False when no slot is free."""
         while kd["prepared"] and kd["prepared"][0][1].done():
             r, fut = kd["prepared"][0]
             e = self._slot_for(kd, r)
             if e is None:
-                break
+                return False
             kd["prepared"].popleft()
             ops = None
             try:
@@ -451,8 +474,8 @@ class BatchServer:
             self.active += 1
             self.peak_active = max(self.peak_active, self.active)
             self.peak_batch = max(self.peak_batch, len(e["running"]))
-            did = True
-        return did
+            return True
+        return False
 
     def _submit_one(self, e, r: Request, ops) -> int:
         b = e["batch"]
@@ -528,9 +551,8 @@ class BatchServer:
                     pending.extend(self.queue)
                     self.queue.clear()
                 self._route(pending)
-                did = False
+                did = self._admit_all()
                 for kd in list(self.kinds.values()):
-                    did |= self._admit(kd)
                     for e in list(kd["batches"]):
                         did |= self._queue_rounds(e)
                         did |= self._collect(e)
@@ -586,7 +608,8 @@ def _lib_free(kd, ops) -> None:
 
 
 def serve_stream(requests, hbm_budget: int, max_active: int = 8, device: int = 0, runner=None, sizer=None,
-                 batched: bool = False, ticks: int = 4, batch_factory=None, max_batches_per_kind=None):
+                 batched: bool = False, ticks: int = 4, batch_factory=None, max_batches_per_kind=None,
+                 max_active_total=None):
     """Submit requests at their arrival times (seconds after start) and wait.
 
     Returns (results sorted by id, server).  Arrival times are honoured on the
@@ -596,7 +619,7 @@ def serve_stream(requests, hbm_budget: int, max_active: int = 8, device: int = 0
     request."""
     if batched:
         srv = BatchServer(hbm_budget, max_active, ticks, device, batch_factory, sizer,
-                          max_batches_per_kind=max_batches_per_kind)
+                          max_batches_per_kind=max_batches_per_kind, max_active_total=max_active_total)
         try:
             for r in sorted(requests, key=lambda q: q.arrival):
                 delay = r.arrival - srv.now()

@@ -158,6 +158,19 @@ def test_batch_server_slots_follow_the_arrival_mix():
     assert all(b.max_live <= 3 for b in FakeBatch.made)
 
 
+def test_batch_server_caps_concurrency_and_admits_in_arrival_order():
+    """With max_active_total, at most that many requests run over all batches,
+    and waiting requests enter slots oldest first whatever their kind."""
+    FakeBatch.made.clear()
+    reqs = [_breq(i, 1 + (i % 2), 6, arrival=0.001 * i) for i in range(8)]
+    res, srv = serving.serve_stream(reqs, hbm_budget=8, max_active=4, batched=True, ticks=1,
+                                    batch_factory=SlowBatch, sizer=lambda r, slots: 1, max_active_total=2)
+    assert all(x.error is None for x in res), [x.error for x in res]
+    assert srv.peak_active == 2
+    admitted = sorted(range(8), key=lambda i: res[i].admitted)
+    assert admitted == list(range(8))
+
+
 def test_batch_server_budget_releases_idle_batches_and_reports_errors():
     FakeBatch.made.clear()
     reqs = [_breq(0, 1, 4), _breq(1, 2, 4, arrival=0.05), _breq(2, 1, 2, arrival=0.1, Re=-1.0)]
