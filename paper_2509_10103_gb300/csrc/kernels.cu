@@ -242,239 +242,331 @@ __device__ __forceinline__ void df_fma2(dacc2& a, dfl k, const dfc& x) {
     df_fma(a.re, k, x.re);
     df_fma(a.im, k, x.im);
 }
-// sum_s B[j][s] x[j-4+s] (rows as in band_row)
-__device__ __forceinline__ dacc2 band_row_df(const Geo& g, const float2* B, const double2* x, int j, int im, int k) {
+// The double-FP32 kernels work on tiles: a block owns kTK consecutive k of
+// one m and kTJ consecutive radial rows; it loads the banded input fields on
+// rows [j0 - 8, j0 + kTJ + 4) (clipped to the grid; this covers the one-sided
+// wall stencils and the transposed columns), splits every value once into
+// (hi, lo) pairs in shared memory, and each of its kTG radial groups then
+// computes rows j0 + y, j0 + y + kTG, ... from the tile.  A value is split
+// about 1.75 times instead of once per band entry that reads it.
+constexpr int kTK = 32, kTG = 8, kTJ = 16, kTR = kTJ + 12;
+struct TBlk {
+    int k, im, m, slot, j0, j1, lo, hi;
+    size_t S, off;
+    bool on;
+};
+__device__ __forceinline__ TBlk tdecode(const Geo& g) {
+    TBlk t;
+    t.S = (size_t)g.nr * g.nm * g.nk;
+    t.k = blockIdx.x * kTK + threadIdx.x;
+    t.im = blockIdx.y;
+    t.m = t.im - g.M;
+    const int ntj = (g.nr + kTJ - 1) / kTJ, b = blockIdx.z / ntj, tj = blockIdx.z - b * ntj;
+    t.slot = g.slot[b];
+    t.off = (size_t)t.slot * g.fs;
+    t.j0 = tj * kTJ;
+    t.j1 = min(g.nr, t.j0 + kTJ);
+    t.lo = max(0, t.j0 - 8);
+    t.hi = min(g.nr, t.j0 + kTJ + 4);
+    t.on = t.k < g.nk;
+    return t;
+}
+typedef float4 DfTile[kTR][kTK];  // (re.hi, re.lo, im.hi, im.lo) per (row - lo, k)
+__device__ __forceinline__ void tile_load(const Geo& g, const TBlk& t, const double2* f, DfTile& tl) {
+    for (int r = t.lo + (int)threadIdx.y; r < t.hi; r += kTG) {
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (t.on) {
+            const dfc x = df_load(f + sidx(g, r, t.im, t.k));
+            v = make_float4(x.re.h, x.re.l, x.im.h, x.im.l);
+        }
+        tl[r - t.lo][threadIdx.x] = v;
+    }
+}
+__device__ __forceinline__ dfc tile_at(const DfTile& tl, int lo, int r) {
+    const float4 v = tl[r - lo][threadIdx.x];
+    dfc x;
+    x.re.h = v.x;
+    x.re.l = v.y;
+    x.im.h = v.z;
+    x.im.l = v.w;
+    return x;
+}
+// sum_s B[j][s] x[j-4+s] from the tile (rows as in band_row)
+__device__ __forceinline__ dacc2 band_row_t(const Geo& g, const float2* B, const DfTile& tl, int lo, int j) {
     dacc2 a{dacc0(), dacc0()};
     if (j >= 4) {
 #pragma unroll
         for (int s = 0; s < 9; ++s) {
             const int c = j - 4 + s;
-            if (c < g.nr) df_fma2(a, dff(__ldg(B + s)), df_load(x + sidx(g, c, im, k)));
+            if (c < g.nr) df_fma2(a, dff(__ldg(B + s)), tile_at(tl, lo, c));
         }
     } else {
 #pragma unroll
         for (int s = 0; s < kB; ++s) {
             const int c = j - 4 + s;
-            if (c >= 0 && c <= 8) df_fma2(a, dff(__ldg(B + s)), df_load(x + sidx(g, c, im, k)));
+            if (c >= 0 && c <= 8) df_fma2(a, dff(__ldg(B + s)), tile_at(tl, lo, c));
         }
     }
     return a;
 }
-// (B^T x)_j (columns as in band_col)
-__device__ __forceinline__ dacc2 band_col_df(const Geo& g, const float2* B0, const double2* x, int j, int im, int k) {
+// (B^T x)_j from the tile (columns as in band_col)
+__device__ __forceinline__ dacc2 band_col_t(const Geo& g, const float2* B0, const DfTile& tl, int lo, int j) {
     dacc2 a{dacc0(), dacc0()};
     if (j > 8) {
 #pragma unroll
         for (int t = -4; t <= 4; ++t) {
             const int c = j + t;
-            if (c < g.nr) df_fma2(a, dff(__ldg(B0 + (size_t)c * kB + (4 - t))), df_load(x + sidx(g, c, im, k)));
+            if (c < g.nr) df_fma2(a, dff(__ldg(B0 + (size_t)c * kB + (4 - t))), tile_at(tl, lo, c));
         }
     } else {
 #pragma unroll
         for (int t = -8; t <= 4; ++t) {
             const int c = j + t;
-            if (c >= 0 && c < g.nr) df_fma2(a, dff(__ldg(B0 + (size_t)c * kB + (4 - t))), df_load(x + sidx(g, c, im, k)));
+            if (c >= 0 && c < g.nr) df_fma2(a, dff(__ldg(B0 + (size_t)c * kB + (4 - t))), tile_at(tl, lo, c));
         }
     }
     return a;
 }
 __device__ __forceinline__ double2 df_out(const dacc2& a) { return make_double2(df_result(a.re), df_result(a.im)); }
 
-__global__ void k_curl_df(Geo g, const double2* __restrict__ u, double2* __restrict__ w) {
-    Idx d;
-    if (!decode(g, d)) return;
-    u += d.off;
-    w += d.off;
-    const double2 *ur = u, *ut = u + d.S, *uz = u + 2 * d.S;
-    const dfl kz = dff(__ldg(g.kztf + d.k)), ir = dff(__ldg(g.invrf + d.j)),
-              mr = dff(__ldg(g.mrtf + (size_t)d.im * g.nr + d.j));
-    const size_t o = sidx(g, d.j, d.im, d.k);
-    const dacc2 dz = band_row_df(g, g.D1f + ((size_t)par_idx(d.m) * g.nr + d.j) * kB, uz, d.j, d.im, d.k);
-    const dacc2 dt = band_row_df(g, g.D1f + ((size_t)par_idx(d.m + 1) * g.nr + d.j) * kB, ut, d.j, d.im, d.k);
-    const dfc a = df_load(ur + o), b = df_load(ut + o), c = df_load(uz + o);
-    dacc2 wr{dacc0(), dacc0()};  // (-mr c.y + kz b.y, mr c.x - kz b.x)
-    df_fma(wr.re, df_neg(mr), c.im);
-    df_fma(wr.re, kz, b.im);
-    df_fma(wr.im, mr, c.re);
-    df_fma(wr.im, df_neg(kz), b.re);
-    dacc2 wt{dacc_neg(dz.re), dacc_neg(dz.im)};  // (-kz a.y - dz.x, kz a.x - dz.y)
-    df_fma(wt.re, df_neg(kz), a.im);
-    df_fma(wt.im, kz, a.re);
-    dacc2 wz = dt;  // (dt.x + ir b.x + mr a.y, dt.y + ir b.y - mr a.x)
-    df_fma(wz.re, ir, b.re);
-    df_fma(wz.re, mr, a.im);
-    df_fma(wz.im, ir, b.im);
-    df_fma(wz.im, df_neg(mr), a.re);
-    w[o] = df_out(wr);
-    w[o + d.S] = df_out(wt);
-    w[o + 2 * d.S] = df_out(wz);
-}
-
-__global__ void k_curlT_acc_df(Geo g, const double2* __restrict__ wb, double2* __restrict__ ub) {
-    Idx d;
-    if (!decode(g, d)) return;
-    wb += d.off;
-    ub += d.off;
-    const double2 *wr = wb, *wt = wb + d.S, *wz = wb + 2 * d.S;
-    const dfl kz = dff(__ldg(g.kztf + d.k)), ir = dff(__ldg(g.invrf + d.j)),
-              mr = dff(__ldg(g.mrtf + (size_t)d.im * g.nr + d.j));
-    const size_t o = sidx(g, d.j, d.im, d.k);
-    const dacc2 sT = band_col_df(g, g.D1f + (size_t)par_idx(d.m + 1) * g.nr * kB, wz, d.j, d.im, d.k);
-    const dacc2 sP = band_col_df(g, g.D1f + (size_t)par_idx(d.m) * g.nr * kB, wt, d.j, d.im, d.k);
-    const dfc a = df_load(wr + o), b = df_load(wt + o), c = df_load(wz + o);
-    dacc2 xr{dacc0(), dacc0()};  // += (kz b.y - mr c.y, -kz b.x + mr c.x)
-    df_fma(xr.re, kz, b.im);
-    df_fma(xr.re, df_neg(mr), c.im);
-    df_fma(xr.im, df_neg(kz), b.re);
-    df_fma(xr.im, mr, c.re);
-    dacc2 xt = sT;  // += (-kz a.y + sT.x + ir c.x, kz a.x + sT.y + ir c.y)
-    df_fma(xt.re, df_neg(kz), a.im);
-    df_fma(xt.re, ir, c.re);
-    df_fma(xt.im, kz, a.re);
-    df_fma(xt.im, ir, c.im);
-    dacc2 xz{dacc_neg(sP.re), dacc_neg(sP.im)};  // += (mr a.y - sP.x, -mr a.x - sP.y)
-    df_fma(xz.re, mr, a.im);
-    df_fma(xz.im, df_neg(mr), a.re);
-    double2 x = ub[o], v = df_out(xr);
-    ub[o] = make_double2(x.x + v.x, x.y + v.y);
-    x = ub[o + d.S];
-    v = df_out(xt);
-    ub[o + d.S] = make_double2(x.x + v.x, x.y + v.y);
-    x = ub[o + 2 * d.S];
-    v = df_out(xz);
-    ub[o + 2 * d.S] = make_double2(x.x + v.x, x.y + v.y);
-}
-
-__global__ void k_stage_div_df(Geo g, const double2* __restrict__ F, double2* __restrict__ q) {
-    Idx d;
-    if (!decode(g, d)) return;
-    F += d.off;
-    q += d.off;
-    const size_t o = sidx(g, d.j, d.im, d.k), S = d.S;
-    if (d.j == 0 || (d.m == 0 && d.k == 0)) {
-        q[o] = make_double2(0, 0);
-        return;
+__global__ void __launch_bounds__(kTK* kTG) k_curl_df(Geo g, const double2* __restrict__ u, double2* __restrict__ w) {
+    __shared__ DfTile tz, tt;
+    const TBlk t = tdecode(g);
+    u += t.off;
+    w += t.off;
+    const double2 *ur = u, *ut = u + t.S, *uz = u + 2 * t.S;
+    tile_load(g, t, uz, tz);
+    tile_load(g, t, ut, tt);
+    __syncthreads();
+    if (!t.on) return;
+    const dfl kz = dff(__ldg(g.kztf + t.k));
+    for (int j = t.j0 + threadIdx.y; j < t.j1; j += kTG) {
+        const dfl ir = dff(__ldg(g.invrf + j)), mr = dff(__ldg(g.mrtf + (size_t)t.im * g.nr + j));
+        const size_t o = sidx(g, j, t.im, t.k);
+        const dacc2 dz = band_row_t(g, g.D1f + ((size_t)par_idx(t.m) * g.nr + j) * kB, tz, t.lo, j);
+        const dacc2 dt = band_row_t(g, g.D1f + ((size_t)par_idx(t.m + 1) * g.nr + j) * kB, tt, t.lo, j);
+        const dfc a = df_load(ur + o), b = tile_at(tt, t.lo, j), c = tile_at(tz, t.lo, j);
+        dacc2 wr{dacc0(), dacc0()};  // (-mr c.y + kz b.y, mr c.x - kz b.x)
+        df_fma(wr.re, df_neg(mr), c.im);
+        df_fma(wr.re, kz, b.im);
+        df_fma(wr.im, mr, c.re);
+        df_fma(wr.im, df_neg(kz), b.re);
+        dacc2 wt{dacc_neg(dz.re), dacc_neg(dz.im)};  // (-kz a.y - dz.x, kz a.x - dz.y)
+        df_fma(wt.re, df_neg(kz), a.im);
+        df_fma(wt.im, kz, a.re);
+        dacc2 wz = dt;  // (dt.x + ir b.x + mr a.y, dt.y + ir b.y - mr a.x)
+        df_fma(wz.re, ir, b.re);
+        df_fma(wz.re, mr, a.im);
+        df_fma(wz.im, ir, b.im);
+        df_fma(wz.im, df_neg(mr), a.re);
+        w[o] = df_out(wr);
+        w[o + t.S] = df_out(wt);
+        w[o + 2 * t.S] = df_out(wz);
     }
-    const dfl kz = dff(__ldg(g.kztf + d.k)), ir = dff(__ldg(g.invrf + d.j)),
-              mr = dff(__ldg(g.mrtf + (size_t)d.im * g.nr + d.j));
-    dacc2 acc = band_row_df(g, g.D1f + ((size_t)par_idx(d.m + 1) * g.nr + d.j) * kB, F, d.j, d.im, d.k);
-    const dfc fr = df_load(F + o), ft = df_load(F + o + S), fz = df_load(F + o + 2 * S);
-    df_fma(acc.re, ir, fr.re);  // + ir fr.x - mr ft.y - kz fz.y
-    df_fma(acc.re, df_neg(mr), ft.im);
-    df_fma(acc.re, df_neg(kz), fz.im);
-    df_fma(acc.im, ir, fr.im);  // + ir fr.y + mr ft.x + kz fz.x
-    df_fma(acc.im, mr, ft.re);
-    df_fma(acc.im, kz, fz.re);
-    q[o] = df_out(acc);
+}
+
+__global__ void __launch_bounds__(kTK* kTG) k_curlT_acc_df(Geo g, const double2* __restrict__ wb,
+                                                         double2* __restrict__ ub) {
+    __shared__ DfTile tz, tt;
+    const TBlk t = tdecode(g);
+    wb += t.off;
+    ub += t.off;
+    const double2 *wr = wb, *wt = wb + t.S, *wz = wb + 2 * t.S;
+    tile_load(g, t, wz, tz);
+    tile_load(g, t, wt, tt);
+    __syncthreads();
+    if (!t.on) return;
+    const dfl kz = dff(__ldg(g.kztf + t.k));
+    for (int j = t.j0 + threadIdx.y; j < t.j1; j += kTG) {
+        const dfl ir = dff(__ldg(g.invrf + j)), mr = dff(__ldg(g.mrtf + (size_t)t.im * g.nr + j));
+        const size_t o = sidx(g, j, t.im, t.k);
+        const dacc2 sT = band_col_t(g, g.D1f + (size_t)par_idx(t.m + 1) * g.nr * kB, tz, t.lo, j);
+        const dacc2 sP = band_col_t(g, g.D1f + (size_t)par_idx(t.m) * g.nr * kB, tt, t.lo, j);
+        const dfc a = df_load(wr + o), b = tile_at(tt, t.lo, j), c = tile_at(tz, t.lo, j);
+        dacc2 xr{dacc0(), dacc0()};  // += (kz b.y - mr c.y, -kz b.x + mr c.x)
+        df_fma(xr.re, kz, b.im);
+        df_fma(xr.re, df_neg(mr), c.im);
+        df_fma(xr.im, df_neg(kz), b.re);
+        df_fma(xr.im, mr, c.re);
+        dacc2 xt = sT;  // += (-kz a.y + sT.x + ir c.x, kz a.x + sT.y + ir c.y)
+        df_fma(xt.re, df_neg(kz), a.im);
+        df_fma(xt.re, ir, c.re);
+        df_fma(xt.im, kz, a.re);
+        df_fma(xt.im, ir, c.im);
+        dacc2 xz{dacc_neg(sP.re), dacc_neg(sP.im)};  // += (mr a.y - sP.x, -mr a.x - sP.y)
+        df_fma(xz.re, mr, a.im);
+        df_fma(xz.im, df_neg(mr), a.re);
+        double2 x = ub[o], v = df_out(xr);
+        ub[o] = make_double2(x.x + v.x, x.y + v.y);
+        x = ub[o + t.S];
+        v = df_out(xt);
+        ub[o + t.S] = make_double2(x.x + v.x, x.y + v.y);
+        x = ub[o + 2 * t.S];
+        v = df_out(xz);
+        ub[o + 2 * t.S] = make_double2(x.x + v.x, x.y + v.y);
+    }
+}
+
+__global__ void __launch_bounds__(kTK* kTG) k_stage_div_df(Geo g, const double2* __restrict__ F,
+                                                         double2* __restrict__ q) {
+    __shared__ DfTile tr;
+    const TBlk t = tdecode(g);
+    F += t.off;
+    q += t.off;
+    tile_load(g, t, F, tr);
+    __syncthreads();
+    if (!t.on) return;
+    const size_t S = t.S;
+    const dfl kz = dff(__ldg(g.kztf + t.k));
+    for (int j = t.j0 + threadIdx.y; j < t.j1; j += kTG) {
+        const size_t o = sidx(g, j, t.im, t.k);
+        if (j == 0 || (t.m == 0 && t.k == 0)) {
+            q[o] = make_double2(0, 0);
+            continue;
+        }
+        const dfl ir = dff(__ldg(g.invrf + j)), mr = dff(__ldg(g.mrtf + (size_t)t.im * g.nr + j));
+        dacc2 acc = band_row_t(g, g.D1f + ((size_t)par_idx(t.m + 1) * g.nr + j) * kB, tr, t.lo, j);
+        const dfc fr = tile_at(tr, t.lo, j), ft = df_load(F + o + S), fz = df_load(F + o + 2 * S);
+        df_fma(acc.re, ir, fr.re);  // + ir fr.x - mr ft.y - kz fz.y
+        df_fma(acc.re, df_neg(mr), ft.im);
+        df_fma(acc.re, df_neg(kz), fz.im);
+        df_fma(acc.im, ir, fr.im);  // + ir fr.y + mr ft.x + kz fz.x
+        df_fma(acc.im, mr, ft.re);
+        df_fma(acc.im, kz, fz.re);
+        q[o] = df_out(acc);
+    }
 }
 
 // k_stage_rhs with every term of R in double-float: R_+ = F_r - F_t i - D1 p
 // + (m/r) p ..., written out per real part below
-__global__ void k_stage_rhs_df(Geo g, const double2* __restrict__ u, const double2* __restrict__ F,
-                               const double2* __restrict__ p, double2* __restrict__ R) {
-    Idx d;
-    if (!decode(g, d)) return;
-    u = moved(u, d.off);
-    F += d.off;
-    p += d.off;
-    R += d.off;
-    const size_t o = sidx(g, d.j, d.im, d.k), S = d.S;
-    if (d.j == 0) {  // the wall row: T u (no arithmetic worth double-float)
-        double2 tp = make_double2(0, 0), tm = tp, tz = tp;
-        if (u) {
-            const double2 a = u[o], b = u[o + S], c = u[o + 2 * S];
-            tp = make_double2(a.x - b.y, a.y + b.x);
-            tm = make_double2(a.x + b.y, a.y - b.x);
-            tz = c;
+__global__ void __launch_bounds__(kTK* kTG) k_stage_rhs_df(Geo g, const double2* __restrict__ u,
+                                                         const double2* __restrict__ F,
+                                                         const double2* __restrict__ p, double2* __restrict__ R) {
+    __shared__ DfTile tp;
+    const TBlk t = tdecode(g);
+    u = moved(u, t.off);
+    F += t.off;
+    p += t.off;
+    R += t.off;
+    tile_load(g, t, p, tp);
+    __syncthreads();
+    if (!t.on) return;
+    const size_t S = t.S;
+    const dfl kz = dff(__ldg(g.kztf + t.k));
+    for (int j = t.j0 + threadIdx.y; j < t.j1; j += kTG) {
+        const size_t o = sidx(g, j, t.im, t.k);
+        if (j == 0) {  // the wall row: T u (no arithmetic worth double-float)
+            double2 vp = make_double2(0, 0), vm = vp, vz = vp;
+            if (u) {
+                const double2 a = u[o], b = u[o + S], c = u[o + 2 * S];
+                vp = make_double2(a.x - b.y, a.y + b.x);
+                vm = make_double2(a.x + b.y, a.y - b.x);
+                vz = c;
+            }
+            R[o] = vp;
+            R[o + S] = vm;
+            R[o + 2 * S] = vz;
+            continue;
         }
-        R[o] = tp;
-        R[o + S] = tm;
-        R[o + 2 * S] = tz;
-        return;
+        const dfl mr = dff(__ldg(g.mrtf + (size_t)t.im * g.nr + j));
+        const dacc2 dp = band_row_t(g, g.D1f + ((size_t)par_idx(t.m) * g.nr + j) * kB, tp, t.lo, j);
+        const dfc pj = tile_at(tp, t.lo, j), fr = df_load(F + o), ft = df_load(F + o + S), fz = df_load(F + o + 2 * S);
+        // rp = (Fr.x - Ft.y - dp.x + mr p.x, Fr.y + Ft.x - dp.y + mr p.y)
+        // rm = (Fr.x + Ft.y - dp.x - mr p.x, Fr.y - Ft.x - dp.y - mr p.y)
+        // rz = (Fz.x + kz p.y, Fz.y - kz p.x)
+        dacc2 rp{dacc_neg(dp.re), dacc_neg(dp.im)}, rm = rp, rz{dacc0(), dacc0()};
+        df_add(rp.re, fr.re);
+        df_add(rp.re, df_neg(ft.im));
+        df_fma(rp.re, mr, pj.re);
+        df_add(rp.im, fr.im);
+        df_add(rp.im, ft.re);
+        df_fma(rp.im, mr, pj.im);
+        df_add(rm.re, fr.re);
+        df_add(rm.re, ft.im);
+        df_fma(rm.re, df_neg(mr), pj.re);
+        df_add(rm.im, fr.im);
+        df_add(rm.im, df_neg(ft.re));
+        df_fma(rm.im, df_neg(mr), pj.im);
+        df_add(rz.re, fz.re);
+        df_fma(rz.re, kz, pj.im);
+        df_add(rz.im, fz.im);
+        df_fma(rz.im, df_neg(kz), pj.re);
+        if (u) {  // + (2/dt) T u: u+ = (a.x - b.y, a.y + b.x), u- = (a.x + b.y, a.y - b.x), u_z
+            const dfl f = dff(g.two_dtf[t.slot]);
+            const dfc a = df_load(u + o), b = df_load(u + o + S), c = df_load(u + o + 2 * S);
+            df_fma(rp.re, f, a.re);
+            df_fma(rp.re, df_neg(f), b.im);
+            df_fma(rp.im, f, a.im);
+            df_fma(rp.im, f, b.re);
+            df_fma(rm.re, f, a.re);
+            df_fma(rm.re, f, b.im);
+            df_fma(rm.im, f, a.im);
+            df_fma(rm.im, df_neg(f), b.re);
+            df_fma(rz.re, f, c.re);
+            df_fma(rz.im, f, c.im);
+        }
+        R[o] = df_out(rp);
+        R[o + S] = df_out(rm);
+        R[o + 2 * S] = df_out(rz);
     }
-    const dfl kz = dff(__ldg(g.kztf + d.k)), mr = dff(__ldg(g.mrtf + (size_t)d.im * g.nr + d.j));
-    const dacc2 dp = band_row_df(g, g.D1f + ((size_t)par_idx(d.m) * g.nr + d.j) * kB, p, d.j, d.im, d.k);
-    const dfc pj = df_load(p + o), fr = df_load(F + o), ft = df_load(F + o + S), fz = df_load(F + o + 2 * S);
-    // rp = (Fr.x - Ft.y - dp.x + mr p.x, Fr.y + Ft.x - dp.y + mr p.y)
-    // rm = (Fr.x + Ft.y - dp.x - mr p.x, Fr.y - Ft.x - dp.y - mr p.y)
-    // rz = (Fz.x + kz p.y, Fz.y - kz p.x)
-    dacc2 rp{dacc_neg(dp.re), dacc_neg(dp.im)}, rm = rp, rz{dacc0(), dacc0()};
-    df_add(rp.re, fr.re);
-    df_add(rp.re, df_neg(ft.im));
-    df_fma(rp.re, mr, pj.re);
-    df_add(rp.im, fr.im);
-    df_add(rp.im, ft.re);
-    df_fma(rp.im, mr, pj.im);
-    df_add(rm.re, fr.re);
-    df_add(rm.re, ft.im);
-    df_fma(rm.re, df_neg(mr), pj.re);
-    df_add(rm.im, fr.im);
-    df_add(rm.im, df_neg(ft.re));
-    df_fma(rm.im, df_neg(mr), pj.im);
-    df_add(rz.re, fz.re);
-    df_fma(rz.re, kz, pj.im);
-    df_add(rz.im, fz.im);
-    df_fma(rz.im, df_neg(kz), pj.re);
-    if (u) {  // + (2/dt) T u: u+ = (a.x - b.y, a.y + b.x), u- = (a.x + b.y, a.y - b.x), u_z
-        const dfl f = dff(g.two_dtf[d.slot]);
-        const dfc a = df_load(u + o), b = df_load(u + o + S), c = df_load(u + o + 2 * S);
-        df_fma(rp.re, f, a.re);
-        df_fma(rp.re, df_neg(f), b.im);
-        df_fma(rp.im, f, a.im);
-        df_fma(rp.im, f, b.re);
-        df_fma(rm.re, f, a.re);
-        df_fma(rm.re, f, b.im);
-        df_fma(rm.im, f, a.im);
-        df_fma(rm.im, df_neg(f), b.re);
-        df_fma(rz.re, f, c.re);
-        df_fma(rz.im, f, c.im);
-    }
-    R[o] = df_out(rp);
-    R[o + S] = df_out(rm);
-    R[o + 2 * S] = df_out(rz);
 }
 
-__global__ void k_stageT_qbar_df(Geo g, const double2* __restrict__ Fb, double2* __restrict__ q) {
-    Idx d;
-    if (!decode(g, d)) return;
-    Fb += d.off;
-    q += d.off;
-    const size_t o = sidx(g, d.j, d.im, d.k), S = d.S;
-    if (d.m == 0 && d.k == 0) {
-        q[o] = make_double2(0, 0);
-        return;
+__global__ void __launch_bounds__(kTK* kTG) k_stageT_qbar_df(Geo g, const double2* __restrict__ Fb,
+                                                           double2* __restrict__ q) {
+    __shared__ DfTile tr;
+    const TBlk t = tdecode(g);
+    Fb += t.off;
+    q += t.off;
+    tile_load(g, t, Fb, tr);
+    __syncthreads();
+    if (!t.on) return;
+    const size_t S = t.S;
+    const dfl kz = dff(__ldg(g.kztf + t.k));
+    for (int j = t.j0 + threadIdx.y; j < t.j1; j += kTG) {
+        const size_t o = sidx(g, j, t.im, t.k);
+        if (t.m == 0 && t.k == 0) {
+            q[o] = make_double2(0, 0);
+            continue;
+        }
+        const dfl mr = dff(__ldg(g.mrtf + (size_t)t.im * g.nr + j));
+        dacc2 acc = band_col_t(g, g.D1f + (size_t)par_idx(t.m) * g.nr * kB, tr, t.lo, j);
+        const dfc ft = df_load(Fb + o + S), fz = df_load(Fb + o + 2 * S);
+        df_fma(acc.re, mr, ft.im);  // + mr ft.y + kz fz.y
+        df_fma(acc.re, kz, fz.im);
+        df_fma(acc.im, df_neg(mr), ft.re);  // - mr ft.x - kz fz.x
+        df_fma(acc.im, df_neg(kz), fz.re);
+        q[o] = df_out(acc);
     }
-    const dfl kz = dff(__ldg(g.kztf + d.k)), mr = dff(__ldg(g.mrtf + (size_t)d.im * g.nr + d.j));
-    dacc2 acc = band_col_df(g, g.D1f + (size_t)par_idx(d.m) * g.nr * kB, Fb, d.j, d.im, d.k);
-    const dfc ft = df_load(Fb + o + S), fz = df_load(Fb + o + 2 * S);
-    df_fma(acc.re, mr, ft.im);  // + mr ft.y + kz fz.y
-    df_fma(acc.re, kz, fz.im);
-    df_fma(acc.im, df_neg(mr), ft.re);  // - mr ft.x - kz fz.x
-    df_fma(acc.im, df_neg(kz), fz.re);
-    q[o] = df_out(acc);
 }
 
-__global__ void k_stageT_div_df(Geo g, const double2* __restrict__ z, double2* __restrict__ Fb) {
-    Idx d;
-    if (!decode(g, d)) return;
-    z += d.off;
-    Fb += d.off;
-    if (d.m == 0 && d.k == 0) return;
-    const size_t o = sidx(g, d.j, d.im, d.k), S = d.S;
-    const double kz = __ldg(g.kzt + d.k), mr = __ldg(g.mrt + (size_t)d.im * g.nr + d.j);
-    const dfl ir = dff(__ldg(g.invrf + d.j));
-    dacc2 dz = band_col_df(g, g.D1f + (size_t)par_idx(d.m + 1) * g.nr * kB, z, d.j, d.im, d.k);
-    const double2 zj = z[o];
-    const dfc zd = df_load(z + o);
-    df_fma(dz.re, ir, zd.re);  // D1v^T z + z / r
-    df_fma(dz.im, ir, zd.im);
-    const double2 v = df_out(dz);
-    double2 x = Fb[o];
-    Fb[o] = make_double2(x.x - v.x, x.y - v.y);
-    x = Fb[o + S];
-    Fb[o + S] = make_double2(x.x - mr * zj.y, x.y + mr * zj.x);
-    x = Fb[o + 2 * S];
-    Fb[o + 2 * S] = make_double2(x.x - kz * zj.y, x.y + kz * zj.x);
+__global__ void __launch_bounds__(kTK* kTG) k_stageT_div_df(Geo g, const double2* __restrict__ z,
+                                                          double2* __restrict__ Fb) {
+    __shared__ DfTile tz;
+    const TBlk t = tdecode(g);
+    z += t.off;
+    Fb += t.off;
+    tile_load(g, t, z, tz);
+    __syncthreads();
+    if (!t.on || (t.m == 0 && t.k == 0)) return;
+    const size_t S = t.S;
+    const double kz = __ldg(g.kzt + t.k);
+    for (int j = t.j0 + threadIdx.y; j < t.j1; j += kTG) {
+        const size_t o = sidx(g, j, t.im, t.k);
+        const double mr = __ldg(g.mrt + (size_t)t.im * g.nr + j);
+        const dfl ir = dff(__ldg(g.invrf + j));
+        dacc2 dz = band_col_t(g, g.D1f + (size_t)par_idx(t.m + 1) * g.nr * kB, tz, t.lo, j);
+        const double2 zj = z[o];
+        const dfc zd = tile_at(tz, t.lo, j);
+        df_fma(dz.re, ir, zd.re);  // D1v^T z + z / r
+        df_fma(dz.im, ir, zd.im);
+        const double2 v = df_out(dz);
+        double2 x = Fb[o];
+        Fb[o] = make_double2(x.x - v.x, x.y - v.y);
+        x = Fb[o + S];
+        Fb[o + S] = make_double2(x.x - mr * zj.y, x.y + mr * zj.x);
+        x = Fb[o + 2 * S];
+        Fb[o + 2 * S] = make_double2(x.x - kz * zj.y, x.y + kz * zj.x);
+    }
 }
 
 // ------------------------------------------------------------------ radial stage (forward)
@@ -1558,6 +1650,11 @@ __global__ void k_scale_energy(Geo g, size_t n, double2* __restrict__ x, double 
 }
 
 // ------------------------------------------------------------------ launchers
+// grid and block of the tiled double-FP32 kernels (x: k tiles, y: m, z: row tiles x batch entries)
+static inline dim3 tile_grid(const Geo& g) {
+    return dim3((g.nk + kTK - 1) / kTK, g.nm, ((g.nr + kTJ - 1) / kTJ) * g.nb);
+}
+static inline dim3 tile_block() { return dim3(kTK, kTG); }
 // block and grid of the 3-D spectral launches (x: k, y: m, z: r)
 static inline unsigned spec_bx(const Geo& g) { return g.nk <= 32 ? 32u : (g.nk <= 64 ? 64u : 128u); }
 static inline dim3 spec_grid(const Geo& g) {
@@ -1571,12 +1668,12 @@ static void single_only(const Geo& g, const char* what) {
 }
 
 void launch_curl(const Geo& g, const double2* u, double2* w, cudaStream_t s) {
-    if (g.df) k_curl_df<<<spec_grid(g), spec_bx(g), 0, s>>>(g, u, w);
+    if (g.df) k_curl_df<<<tile_grid(g), tile_block(), 0, s>>>(g, u, w);
     else k_curl<<<spec_grid(g), spec_bx(g), 0, s>>>(g, u, w);
     check_launch("curl");
 }
 void launch_curlT_acc(const Geo& g, const double2* wb, double2* ub, cudaStream_t s) {
-    if (g.df) k_curlT_acc_df<<<spec_grid(g), spec_bx(g), 0, s>>>(g, wb, ub);
+    if (g.df) k_curlT_acc_df<<<tile_grid(g), tile_block(), 0, s>>>(g, wb, ub);
     else k_curlT_acc<<<spec_grid(g), spec_bx(g), 0, s>>>(g, wb, ub);
     check_launch("curlT");
 }
@@ -1646,7 +1743,7 @@ static void launch_band_solve(const Geo& g, const double* fac, size_t fac_stride
 }
 
 void launch_stage_div(const Geo& g, const double2* F, double2* q, cudaStream_t s) {
-    if (g.df) k_stage_div_df<<<spec_grid(g), spec_bx(g), 0, s>>>(g, F, q);
+    if (g.df) k_stage_div_df<<<tile_grid(g), tile_block(), 0, s>>>(g, F, q);
     else k_stage_div<<<spec_grid(g), spec_bx(g), 0, s>>>(g, F, q);
     check_launch("stage_div");
 }
@@ -1655,7 +1752,7 @@ void launch_stage_psolve(const Geo& g, double2* q, cudaStream_t s) {
     check_launch("stage_psolve");
 }
 void launch_stage_rhs(const Geo& g, const double2* u, const double2* F, const double2* p, double2* R, cudaStream_t s) {
-    if (g.df) k_stage_rhs_df<<<spec_grid(g), spec_bx(g), 0, s>>>(g, u, F, p, R);
+    if (g.df) k_stage_rhs_df<<<tile_grid(g), tile_block(), 0, s>>>(g, u, F, p, R);
     else k_stage_rhs<<<spec_grid(g), spec_bx(g), 0, s>>>(g, u, F, p, R);
     check_launch("stage_rhs");
 }
@@ -1695,7 +1792,7 @@ void launch_stageT_rhs(const Geo& g, const double2* X, const double2* Y, double 
     check_launch("stageT_rhs");
 }
 void launch_stageT_qbar(const Geo& g, const double2* Fb, double2* q, cudaStream_t s) {
-    if (g.df) k_stageT_qbar_df<<<spec_grid(g), spec_bx(g), 0, s>>>(g, Fb, q);
+    if (g.df) k_stageT_qbar_df<<<tile_grid(g), tile_block(), 0, s>>>(g, Fb, q);
     else k_stageT_qbar<<<spec_grid(g), spec_bx(g), 0, s>>>(g, Fb, q);
     check_launch("stageT_qbar");
 }
@@ -1704,7 +1801,7 @@ void launch_stageT_psolve(const Geo& g, double2* q, cudaStream_t s) {
     check_launch("stageT_psolve");
 }
 void launch_stageT_div(const Geo& g, const double2* z, double2* Fb, cudaStream_t s) {
-    if (g.df) k_stageT_div_df<<<spec_grid(g), spec_bx(g), 0, s>>>(g, z, Fb);
+    if (g.df) k_stageT_div_df<<<tile_grid(g), tile_block(), 0, s>>>(g, z, Fb);
     else k_stageT_div<<<spec_grid(g), spec_bx(g), 0, s>>>(g, z, Fb);
     check_launch("stageT_div");
 }
