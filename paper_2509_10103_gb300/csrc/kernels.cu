@@ -751,7 +751,8 @@ __global__ void __launch_bounds__(2 * kSK) k_band_solve(Geo g, const double* __r
 }
 
 // The same two-sweep solve with each thread's column held in registers
-// (grids of at most MAXR radial points).  The column stays in x[0..MAXR): the
+// (grids of at most MAXR radial points; the launch bound of six blocks per SM
+// keeps the register count at 168, which holds the column without spills).  The column stays in x[0..MAXR): the
 // forward sweep reads its lower neighbours and the backward sweep its upper
 // neighbours straight from registers (every index is a compile-time constant
 // after unrolling), so no shared-memory round trip sits on the dependent
@@ -759,7 +760,7 @@ __global__ void __launch_bounds__(2 * kSK) k_band_solve(Geo g, const double* __r
 // arithmetic and its order are those of k_band_solve: the results are the
 // same to the last bit (up to the sign of zero).
 template <int NL, int NU, bool DIAG1, int MAXR, bool WALL>
-__global__ void __launch_bounds__(2 * kSK) k_band_solve_reg(Geo g, const double* __restrict__ fac, size_t fac_stride,
+__global__ void __launch_bounds__(2 * kSK, 6) k_band_solve_reg(Geo g, const double* __restrict__ fac, size_t fac_stride,
                                                       double2* __restrict__ X, const double2* __restrict__ add,
                                                       int helm, int zero_row0, double* __restrict__ pw,
                                                       const double2* __restrict__ usub) {
@@ -793,6 +794,23 @@ __global__ void __launch_bounds__(2 * kSK) k_band_solve_reg(Geo g, const double*
     double x[MAXR];
 #pragma unroll
     for (int j = 0; j < MAXR; ++j) x[j] = (on && j < nr) ? xs[2 * sidx(g, j, im, k0 + sy)] : 0.0;
+    // wall partials of the tentative velocity T^-1 x - usub (forward Helmholtz
+    // solves): the usub part now, the solution's part after the sweeps.
+    // v = 0, 1: d0 . (x/2) over rows 0..8 (d0 the wall row of D1 for u_r), minus
+    // d0 . usub_r on v = 0; the mean mode's u_z block: sum_j W_j (x - usub_z).
+    const bool mean_z = v == 2 && m == 0 && k0 + sy == 0;
+    double wall_u = 0.0;
+    if (WALL && on && usub) {
+        const double* us = reinterpret_cast<const double*>(usub + off) + comp;
+        if (v == 0) {
+            const double* d0 = g.D1 + (size_t)par_idx(m + 1) * nr * kB + 4;
+#pragma unroll 1
+            for (int c = 0; c <= 8 && c < nr; ++c) wall_u = fma(__ldg(d0 + c), us[2 * sidx(g, c, im, k0 + sy)], wall_u);
+        } else if (mean_z) {
+#pragma unroll 1
+            for (int j = 0; j < nr; ++j) wall_u = fma(g.W[j], us[2 * (2 * S + sidx(g, j, im, 0))], wall_u);
+        }
+    }
     auto stage = [&](int t) {  // chunk t of the sweep sequence into buffer t & 1
         if (t >= 2 * nch) return;
         const bool fwd = t < nch;
@@ -861,6 +879,23 @@ __global__ void __launch_bounds__(2 * kSK) k_band_solve_reg(Geo g, const double*
         }
     }
     if (!on) return;
+    if (WALL) {
+        double* P = pw + ((((size_t)slot * 3 + v) * g.nm + im) * g.nk + (k0 + sy)) * 2 + comp;
+        if (v < 2) {
+            const double* d0 = g.D1 + (size_t)par_idx(m + 1) * nr * kB + 4;
+            double acc = 0.0;
+#pragma unroll
+            for (int c = 0; c <= 8; ++c)
+                if (c < nr) acc = fma(__ldg(d0 + c), 0.5 * x[c], acc);
+            *P = acc - wall_u;
+        } else if (mean_z) {
+            double acc = 0.0;
+#pragma unroll
+            for (int j = 0; j < MAXR; ++j)
+                if (j < nr) acc = fma(g.W[j], x[j], acc);
+            *P = acc - wall_u;
+        }
+    }
     double* xo = reinterpret_cast<double*>(X + (size_t)v * S) + comp;
     const double* ad = add ? reinterpret_cast<const double*>(add + (size_t)v * S) + comp : nullptr;
 #pragma unroll
@@ -870,34 +905,6 @@ __global__ void __launch_bounds__(2 * kSK) k_band_solve_reg(Geo g, const double*
             double val = (zero_row0 && j == 0) ? 0.0 : x[j];
             if (ad) val += ad[o];
             xo[o] = val;
-        }
-    }
-    // wall partials of the tentative velocity (forward Helmholtz solves), from
-    // the column just written (so that no register holds the column longer):
-    // the wall derivative part, rows 0..8, or the mean mode's flux
-    if (WALL) {
-        usub = moved(usub, off);
-        const double* us = usub ? reinterpret_cast<const double*>(usub) + comp : nullptr;
-        double* P = pw + ((((size_t)slot * 3 + v) * g.nm + im) * g.nk + (k0 + sy)) * 2 + comp;
-        if (v < 2) {
-            const double* d0 = g.D1 + (size_t)par_idx(m + 1) * nr * kB + 4;
-            double acc = 0.0;
-#pragma unroll 1
-            for (int c = 0; c <= 8 && c < nr; ++c) {
-                const size_t o = 2 * sidx(g, c, im, k0 + sy);
-                double xv = 0.5 * xo[o];
-                if (v == 0 && us) xv -= us[o];
-                acc = fma(__ldg(d0 + c), xv, acc);
-            }
-            *P = acc;
-        } else if (m == 0 && k0 + sy == 0) {  // sum_j W_j (x_z - usub_z)
-            double acc = 0.0;
-#pragma unroll 1
-            for (int j = 0; j < nr; ++j) {
-                const size_t o = 2 * sidx(g, j, im, 0);
-                acc = fma(g.W[j], us ? xo[o] - us[2 * 2 * S + o] : xo[o], acc);
-            }
-            *P = acc;
         }
     }
 }
