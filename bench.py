@@ -106,7 +106,7 @@ def class_work(cls, units, mixed):
     return None, None
 
 
-KERNEL_SOURCES = ("kernels.cu", "transforms.cu", "kernels.hpp", "dev_common.cuh")
+KERNEL_SOURCES = ("kernels.cu", "transforms.cu", "kernels.hpp", "dev_common.cuh", "dev_df.cuh")
 
 
 def kernel_digest():
@@ -391,7 +391,7 @@ def time_e2e(L, torch, precision, steps, warmup, H, snaps):
     return s
 
 
-def roofline(L, res, mixed, peaks, pk_src, alu_measured=None):
+def roofline(L, res, mixed, peaks, pk_src, alu_measured=None, prec_name=None):
     """Roofline of the dominant class.  alu_measured: {"fp64": T, "fp32": T}
     from the library's FMA probe on this device (TFLOP/s); the ALU peak is
     the measured figure when given, the derived one (SMs x lanes x clock)
@@ -413,7 +413,7 @@ def roofline(L, res, mixed, peaks, pk_src, alu_measured=None):
     ach_b = by / t / 1e9 if by is not None else None
     frac_f = ach_f / fp_peak
     frac_b = ach_b / hbm if by is not None else 0.0
-    tt = traffic_table().get((cls, "mixed" if mixed else "fp64"))
+    tt = traffic_table().get((cls, prec_name or ("mixed" if mixed else "fp64")))
     base = {"kernel": cls, "launches": launches, "avg_launch_us": ms * 1e3 / launches,
             "traffic": tt,
             "traffic_note": "ncu DRAM bytes per launch of the current kernel sources (profiles/), null when the"
@@ -782,7 +782,7 @@ def main():
         fms = max_over_ranks(f["ms"], ws)
         return {"value": H * args.steps * ws / (fms / 1e3), "unit": "steps/s", "ms_per_step": fms / args.steps,
                 "gain": f["gain"], "dtype": DTYPES[prec],
-                "roofline": roofline(L, f, (prec & L.PNOP_MIXED) != 0, peaks, pk_src, alu),
+                "roofline": roofline(L, f, (prec & L.PNOP_MIXED) != 0, peaks, pk_src, alu, PREC_NAMES[prec]),
                 "kernels_ms_per_step": {k: v[0] for k, v in f["warm_profile"].items()}}
 
     fp64 = side_path(L.PNOP_FP64) if (not args.no_fp64 and args.precision == "both") else None
@@ -803,7 +803,7 @@ def main():
                    "l2": f"inputs and working set > L2 (state {FIELD_BYTES / 2**20:.1f} MiB x >20 buffers + transform"
                          " scratch); no flush"},
         "gain": mix["gain"],
-        "roofline": roofline(L, mix, (main_prec & L.PNOP_MIXED) != 0, peaks, pk_src, alu),
+        "roofline": roofline(L, mix, (main_prec & L.PNOP_MIXED) != 0, peaks, pk_src, alu, PREC_NAMES[main_prec]),
         "alu_peaks_measured_tflops": alu,
         "kernels_ms_per_step": {k: v[0] for k, v in mix["warm_profile"].items()},
         "fp64": fp64,
