@@ -150,10 +150,10 @@ def test_batch_server_slots_follow_the_arrival_mix():
     FakeBatch.made.clear()
     reqs = [_breq(i, 1, 6) for i in range(9)] + [_breq(9, 2, 6)]
     res, srv = serving.serve_stream(reqs, hbm_budget=4, max_active=3, batched=True, ticks=1,
-                                    batch_factory=SlowBatch, sizer=lambda r, slots: 1)
+                                    batch_factory=SlowerBatch, sizer=lambda r, slots: 1)
     assert all(x.error is None for x in res), [x.error for x in res]
     assert [x.gain for x in res] == [float(i) for i in range(10)]
-    assert srv.peak_batches_per_kind == 3          # 9 requests / 3 slots (each holds its slot ~60 ms)
+    assert srv.peak_batches_per_kind == 3          # 9 requests / 3 slots (each holds its slot ~0.3 s)
     assert srv.peak_bytes <= 4 and len(FakeBatch.made) == 4
     assert all(b.max_live <= 3 for b in FakeBatch.made)
 
@@ -240,6 +240,15 @@ class SlowBatch(FakeBatch):
 
     def pnop_batch_run(self, ticks):
         time.sleep(0.01 * ticks)
+        return super().pnop_batch_run(ticks)
+
+
+class SlowerBatch(FakeBatch):
+    """Ticks of 50 ms: every request of a burst is prepared long before the
+    first one could free its slot, even on a loaded host."""
+
+    def pnop_batch_run(self, ticks):
+        time.sleep(0.05 * ticks)
         return super().pnop_batch_run(ticks)
 
 
