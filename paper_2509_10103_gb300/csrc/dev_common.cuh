@@ -69,9 +69,12 @@ __device__ __forceinline__ double f64_of(float f) {
 
 template <class T2> __device__ __forceinline__ T2 from_d(double2 v);
 template <> __device__ __forceinline__ double2 from_d<double2>(double2 v) { return v; }
-template <> __device__ __forceinline__ float2 from_d<float2>(double2 v) { return make_float2(f32_of(v.x), f32_of(v.y)); }
+// A complex value's two parts take the two routes, the hardware conversion
+// (FP64 pipe) for the real part and the integer one for the imaginary part,
+// so that neither pipe carries all the conversions of a transform.
+template <> __device__ __forceinline__ float2 from_d<float2>(double2 v) { return make_float2((float)v.x, f32_of(v.y)); }
 __device__ __forceinline__ double2 to_d(double2 v) { return v; }
-__device__ __forceinline__ double2 to_d(float2 v) { return make_double2(f64_of(v.x), f64_of(v.y)); }
+__device__ __forceinline__ double2 to_d(float2 v) { return make_double2((double)v.x, f64_of(v.y)); }
 
 __device__ __forceinline__ int par_idx(int m) { return m & 1; }  // 0 even, 1 odd (two's complement)
 
