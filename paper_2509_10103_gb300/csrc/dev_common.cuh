@@ -38,26 +38,12 @@ __device__ __forceinline__ double2 dfma(double s, double2 a, double2 acc) {
     return make_double2(fma(s, a.x, acc.x), fma(s, a.y, acc.y));
 }
 
-// FP64 <-> FP32 conversions by integer operations on the bit patterns.  The
-// GB300's FP64 pipe, which also executes the hardware conversions, runs at
-// 1/64 of the FP32 rate, and the mixed-precision transforms convert every
-// spectral value on the way in and out; these take integer issue slots
-// instead.  Rounding is to nearest (ties away from zero) through a carry into
-// the exponent; magnitudes below 2^-126 become signed zero; infinities and
-// NaN stay infinite and NaN (so that a non-finite field is still detected).
-__device__ __forceinline__ float f32_of(double x) {
-    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
-    const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
-    const unsigned long long mag = b & 0x7FFFFFFFFFFFFFFFull;
-    if (mag >= 0x47F0000000000000ull) {  // |x| >= 2^128, infinities, NaN
-        const bool nan = mag > 0x7FF0000000000000ull;
-        return __uint_as_float(sign | 0x7F800000u | (nan ? 0x400000u : 0u));
-    }
-    const unsigned long long rnd = mag + (1ull << 28);  // half a unit of the 24-bit significand
-    const int e = (int)(rnd >> 52);
-    if (e <= 896) return __uint_as_float(sign);
-    return __uint_as_float(sign | ((unsigned)(e - 896) << 23) | ((unsigned)(rnd >> 29) & 0x7FFFFFu));
-}
+// FP32 -> FP64 conversion by integer operations on the bit pattern (exact).
+// The GB300's FP64 pipe, which also executes the hardware conversions, runs at
+// 1/64 of the FP32 rate, and the mixed-precision theta analysis converts every
+// spectral value it writes; this takes integer issue slots instead.  Zero and
+// subnormals become signed zero; infinities and NaN stay infinite and NaN (so
+// that a non-finite field is still detected).
 __device__ __forceinline__ double f64_of(float f) {
     const unsigned u = __float_as_uint(f);
     const unsigned long long sign = (unsigned long long)(u & 0x80000000u) << 32;
@@ -69,12 +55,13 @@ __device__ __forceinline__ double f64_of(float f) {
 
 template <class T2> __device__ __forceinline__ T2 from_d(double2 v);
 template <> __device__ __forceinline__ double2 from_d<double2>(double2 v) { return v; }
-// A complex value's two parts take the two routes, the hardware conversion
-// (FP64 pipe) for the real part and the integer one for the imaginary part,
-// so that neither pipe carries all the conversions of a transform.
-template <> __device__ __forceinline__ float2 from_d<float2>(double2 v) { return make_float2((float)v.x, f32_of(v.y)); }
+// The theta synthesis converts with the hardware (its FP64 pipe has room
+// between the loads), the theta analysis by integer operations (its FP64 pipe
+// also carries the additions of the base-flow terms): each measured fastest
+// that way on the 64x64x256 gradient.
+template <> __device__ __forceinline__ float2 from_d<float2>(double2 v) { return make_float2((float)v.x, (float)v.y); }
 __device__ __forceinline__ double2 to_d(double2 v) { return v; }
-__device__ __forceinline__ double2 to_d(float2 v) { return make_double2((double)v.x, f64_of(v.y)); }
+__device__ __forceinline__ double2 to_d(float2 v) { return make_double2(f64_of(v.x), f64_of(v.y)); }
 
 __device__ __forceinline__ int par_idx(int m) { return m & 1; }  // 0 even, 1 odd (two's complement)
 
