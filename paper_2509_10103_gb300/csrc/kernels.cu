@@ -145,6 +145,42 @@ __device__ __forceinline__ void base_block(const Geo& g, double& U, double& dU) 
     dU = sh[1];
 }
 
+// N = -U du/dz - u_r dU/dr e_z: the base-flow terms in advective form.  The
+// rotational form (U e_z) x w + u x (-dU/dr e_theta) differs from it by
+// grad(U u_z), which the discrete pressure projection does not remove exactly;
+// the remainder couples u_z back into (u_r, u_theta) and makes k = 0 modes of
+// steady pipe flow grow at high Re.
+__global__ void k_base(Geo g, const double2* __restrict__ u, double2* __restrict__ N) {
+    double U, dU;
+    base_block(g, U, dU);
+    Idx d;
+    if (!decode(g, d)) return;
+    u += d.off;
+    N += d.off;
+    const size_t o = sidx(g, d.j, d.im, d.k), S = d.S;
+    const double a = __ldg(g.kzt + d.k) * U;  // -U d/dz = -i a
+    const double2 ur = u[o], ut = u[o + S], uz = u[o + 2 * S];
+    N[o] = make_double2(a * ur.y, -a * ur.x);
+    N[o + S] = make_double2(a * ut.y, -a * ut.x);
+    N[o + 2 * S] = make_double2(a * uz.y - dU * ur.x, -a * uz.x - dU * ur.y);
+}
+
+// transpose (Euclidean cotangents): ub = conj(-i a) nb = i a nb; ub_r -= dU nb_z
+__global__ void k_baseT(Geo g, const double2* __restrict__ nb, double2* __restrict__ ub) {
+    double U, dU;
+    base_block(g, U, dU);
+    Idx d;
+    if (!decode(g, d)) return;
+    nb += d.off;
+    ub += d.off;
+    const size_t o = sidx(g, d.j, d.im, d.k), S = d.S;
+    const double a = __ldg(g.kzt + d.k) * U;
+    const double2 nr_ = nb[o], nt = nb[o + S], nz = nb[o + 2 * S];
+    ub[o] = make_double2(-a * nr_.y - dU * nz.x, a * nr_.x - dU * nz.y);
+    ub[o + S] = make_double2(-a * nt.y, a * nt.x);
+    ub[o + 2 * S] = make_double2(-a * nz.y, a * nz.x);
+}
+
 // Velocity-gradient tensor in cylindrical components, G[3 i + j] = (grad u)_ij:
 // (d_r u_j), ((im u_r - u_theta)/r, (im u_theta + u_r)/r, im u_z / r), (i k_z u_j).
 __global__ void k_grad_u(Geo g, const double2* __restrict__ u, double2* __restrict__ G) {
@@ -1656,6 +1692,14 @@ void launch_grad_u(const Geo& g, const double2* u, double2* G, cudaStream_t s) {
 void launch_base_adj(const Geo& g, const double2* w, double2* N, cudaStream_t s) {
     k_base_adj<<<spec_grid(g), spec_bx(g), 0, s>>>(g, w, N);
     check_launch("base_adj");
+}
+void launch_base(const Geo& g, const double2* u, double2* N, cudaStream_t s) {
+    k_base<<<spec_grid(g), spec_bx(g), 0, s>>>(g, u, N);
+    check_launch("base");
+}
+void launch_baseT(const Geo& g, const double2* nb, double2* ub, cudaStream_t s) {
+    k_baseT<<<spec_grid(g), spec_bx(g), 0, s>>>(g, nb, ub);
+    check_launch("baseT");
 }
 
 // trans selects the transposed coefficient layout; zero_row0 writes 0 to the

@@ -64,18 +64,12 @@ struct Geo {
 };
 
 // Up to 18 input / 6 output spectral component planes for the transforms; the
-// analysis adds add[i] (when not null) to output i.  With bmode != 0 it also
-// adds the base-flow terms of the spectral field bsrc (three components) to
-// outputs 0..2, in FP64 at the launch's phase: bmode 1 the terms of N(u),
-// -U du/dz - u_r dU/dr e_z; bmode 2 their transpose, ub = i k_z U nb, ub_r -=
-// dU/dr nb_z.
+// analysis adds add[i] (when not null) to output i.
 constexpr int kMaxIn = 18;
 struct FieldPtrs {
     const double2* in[kMaxIn];
     double2* out[6];
     const double2* add[6];
-    const double2* bsrc;
-    int bmode;
 };
 
 // Per-field multipliers applied when forming the Hermitian z spectrum:
@@ -99,41 +93,6 @@ struct Twiddles {
 // (18 -> 3), the perturbation forcing of the continuous adjoint.
 enum ZMode { ZFWD = 0, ZADJ = 1, ZCADJ = 2 };
 
-#ifdef __CUDACC__
-// U and dU/dr of the Womersley base flow at radial row j of batch entry b, at
-// that entry's pulsation phase g.cs[b] (Eq. 2.3-2.4; profiles from setup.cpp)
-__device__ __forceinline__ void base_flow_at(const Geo& g, int b, int j, double& U, double& dU) {
-    const double2 cs = g.cs[b];
-    const int slot = g.slot[b];
-    const double r = g.r[j];
-    const double2 a = g.Uh[(size_t)slot * g.sNr + j], c = g.dUh[(size_t)slot * g.sNr + j];
-    U = 1.0 - r * r + (a.x * cs.x - a.y * cs.y);
-    dU = -2.0 * r + (c.x * cs.x - c.y * cs.y);
-}
-// x += the base-flow term (FieldPtrs::bmode) of output field fi at spectral
-// index o of row j (bs: bsrc at the entry's slot and at row j)
-__device__ __forceinline__ double2 add_base_term(const Geo& g, const FieldPtrs& f, const double2* bs, int fi,
-                                                 size_t o, int k, double U, double dU, double2 x) {
-    const size_t S = (size_t)g.nr * g.nm * g.nk;
-    const double a = __ldg(g.kzt + k) * U;
-    const double2 v = bs[fi * S + o];
-    if (f.bmode == 1) {  // -i a u_fi, and -dU u_r on u_z
-        x = make_double2(fma(a, v.y, x.x), fma(-a, v.x, x.y));
-        if (fi == 2) {
-            const double2 t = bs[o];
-            x = make_double2(fma(-dU, t.x, x.x), fma(-dU, t.y, x.y));
-        }
-    } else {  // i a nb_fi, and -dU nb_z on u_r
-        x = make_double2(fma(-a, v.y, x.x), fma(a, v.x, x.y));
-        if (fi == 0) {
-            const double2 t = bs[2 * S + o];
-            x = make_double2(fma(-dU, t.x, x.x), fma(-dU, t.y, x.y));
-        }
-    }
-    return x;
-}
-#endif
-
 // ---- spectral FP64 kernels ----
 void launch_curl(const Geo& g, const double2* u, double2* w, cudaStream_t s);
 void launch_curlT_acc(const Geo& g, const double2* wb, double2* ub, cudaStream_t s);
@@ -142,6 +101,11 @@ void launch_curlT_acc(const Geo& g, const double2* wb, double2* ub, cudaStream_t
 // Nb = U dw/dz - w_z dU/dr e_r (written)
 void launch_grad_u(const Geo& g, const double2* u, double2* G, cudaStream_t s);
 void launch_base_adj(const Geo& g, const double2* w, double2* N, cudaStream_t s);
+// base-flow terms in advective form: N = -U du/dz - u_r dU/dr e_z, and their
+// transpose ub = (dN/du)^T nb (both written, not accumulated), at the phase
+// g.cs[b] of each batch entry
+void launch_base(const Geo& g, const double2* u, double2* N, cudaStream_t s);
+void launch_baseT(const Geo& g, const double2* nb, double2* ub, cudaStream_t s);
 
 // ---- transforms (T = double for FP64, float for mixed) ----
 template <class T2>

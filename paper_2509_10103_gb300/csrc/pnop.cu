@@ -507,40 +507,55 @@ void set_phase(pnop_ctx* c, double t) {
     }
 }
 
+// Base-flow terms of N(u) at time t into Nbase on the side stream (the caller
+// has forked it); the analysis of the transforms adds them after ev_base.
+void queue_base(pnop_ctx* c, const double2* u, double t) {
+    set_phase(c, t);
+    run(c, PNOP_K_SPECTRAL, 1, flops::base * c->S(), [&] { pnop::launch_base(c->geo, u, c->Nbase, c->side); },
+        c->side);
+    ck(cudaEventRecord(c->ev_base, c->side), "record");
+}
+
 // N = P[I(u) x I(w)] - U du/dz - u_r dU/dr e_z, w = curl u  (Eq. 2.5; base-flow
-// terms in advective form, added in FP64 by the theta analysis from u itself).
-// The physical u and w are left in Y (fields 0..5).
-void nonlinear(pnop_ctx* c, const double2* u, double t, double2* N, void* Y) {
+// terms in advective form, computed on the side stream while the curl and the
+// transforms run).  The physical u and w are left in Y (fields 0..5).  With
+// base_queued the caller has already queued the base terms of this u.
+void nonlinear(pnop_ctx* c, const double2* u, double t, double2* N, void* Y, bool base_queued = false) {
     Range nvtx_range("pnop:nonlinear");
     const Geo& g = c->geo;
     const size_t S = c->S();
     cudaStream_t s = c->stream;
-    set_phase(c, t);
+    if (!base_queued) {
+        fork_side(c);
+        queue_base(c, u, t);
+    }
     run(c, PNOP_K_SPECTRAL, 1, flops::curl * S, [&] { pnop::launch_curl(g, u, c->omega, s); });
     pnop::FieldPtrs f{};
     for (int i = 0; i < 3; ++i) {
         f.in[i] = u + i * S;
         f.in[3 + i] = c->omega + i * S;
         f.out[i] = N + i * S;
+        f.add[i] = c->Nbase + i * S;
     }
-    f.bsrc = u;
-    f.bmode = 1;
     pnop::ZScales sc{};
     const double inv_n = 1.0 / ((double)g.nt * g.nzp);
     for (int i = 0; i < 6; ++i) sc.h0[i] = sc.hk[i] = 1.0;
     for (int i = 0; i < 3; ++i) sc.o0[i] = sc.ok[i] = inv_n;
-    transforms(c, f, 6, 3, pnop::ZFWD, sc, Y, 0, nullptr);
+    transforms(c, f, 6, 3, pnop::ZFWD, sc, Y, 0, c->ev_base);
 }
 
 // ub = (dN/du at u)^T nb  (Euclidean cotangents).  With cached, Y already
 // holds the physical u and curl u of this u (fields 0..5, left by nonlinear).
-// The base-flow transpose is added in FP64 by the theta analysis from nb.
+// The base-flow transpose runs on the side stream and is added by the analysis.
 void nonlinearT(pnop_ctx* c, const double2* u, double t, const double2* nb, double2* ub, void* Y, bool cached) {
     Range nvtx_range("pnop:nonlinearT");
     const Geo& g = c->geo;
     const size_t S = c->S();
     cudaStream_t s = c->stream;
+    fork_side(c);
     set_phase(c, t);
+    run(c, PNOP_K_SPECTRAL, 1, flops::base * S, [&] { pnop::launch_baseT(g, nb, c->Nbase, c->side); }, c->side);
+    ck(cudaEventRecord(c->ev_base, c->side), "record");
     if (!cached) run(c, PNOP_K_SPECTRAL, 1, flops::curl * S, [&] { pnop::launch_curl(g, u, c->omega, s); });
     pnop::FieldPtrs f{};
     for (int i = 0; i < 3; ++i) {
@@ -549,9 +564,8 @@ void nonlinearT(pnop_ctx* c, const double2* u, double t, const double2* nb, doub
         f.in[6 + i] = nb + i * S;
         f.out[i] = ub + i * S;
         f.out[3 + i] = c->wb + i * S;
+        f.add[i] = c->Nbase + i * S;
     }
-    f.bsrc = nb;
-    f.bmode = 2;
     pnop::ZScales sc{};
     const double inv_n = 1.0 / ((double)g.nt * g.nzp);
     for (int i = 0; i < 6; ++i) sc.h0[i] = sc.hk[i] = 1.0;
@@ -565,7 +579,7 @@ void nonlinearT(pnop_ctx* c, const double2* u, double t, const double2* nb, doub
         sc.o0[i] = 1.0;
         sc.ok[i] = 2.0;
     }
-    transforms(c, f, 9, 6, pnop::ZADJ, sc, Y, cached ? 6 : 0, nullptr);
+    transforms(c, f, 9, 6, pnop::ZADJ, sc, Y, cached ? 6 : 0, c->ev_base);
     run(c, PNOP_K_SPECTRAL, 1, flops::curlT * S, [&] { pnop::launch_curlT_acc(g, c->wb, ub, s); });
 }
 
@@ -633,7 +647,9 @@ void cadj_step(pnop_ctx* c, const double2* u_next, double t_next, const double2*
 // (S is linear), so the corrector has no velocity part.
 void fwd_step(pnop_ctx* c, const double2* u, double2* out, double t) {
     Range nvtx_range("pnop:fwd_step");
-    nonlinear(c, u, t, c->N0, c->Y);
+    fork_side(c);
+    queue_base(c, u, t);
+    nonlinear(c, u, t, c->N0, c->Y, true);
     stage(c, u, c->N0, c->us, nullptr);
     nonlinear(c, c->us, t + c->h.ph.dt, c->N1, c->Y);
     axpby(c, 0.5, c->N1, -0.5, c->N0, c->N1);
@@ -654,6 +670,7 @@ void adj_step(pnop_ctx* c, const double2* u, double t, const double2* lin, doubl
     Range nvtx_range("pnop:adj_step");
     const Geo& g = c->geo;
     fork_side(c);
+    queue_base(c, u, t);
     stageT_front(c, lin, c->Rl, c->side);
     run(c, PNOP_K_RADIAL_BAND, 1, flops::trhs_f * c->S(),
         [&] { pnop::launch_stageT_rhs(g, c->Rl, nullptr, 0.5, 0.0, nullptr, 0, c->Nb, nullptr, nullptr, nullptr,
@@ -661,7 +678,7 @@ void adj_step(pnop_ctx* c, const double2* u, double t, const double2* lin, doubl
         c->side);
     stageT_proj(c, c->Nb, c->q2, c->side);  // Nb = S_F^H lin / 2
     ck(cudaEventRecord(c->ev_t, c->side), "record");
-    nonlinear(c, u, t, c->N0, c->Y2);  // physical u, curl u stay in Y2 for N'(u)^T below
+    nonlinear(c, u, t, c->N0, c->Y2, true);  // physical u, curl u stay in Y2 for N'(u)^T below
     stage(c, u, c->N0, c->us, nullptr);
     join_side(c, c->ev_t);
     nonlinearT(c, c->us, t + c->h.ph.dt, c->Nb, c->ubs, c->Y, false);
@@ -880,7 +897,7 @@ void ensure_shadow(pnop_ctx* c) {
         ck(cudaStreamCreateWithFlags(&sh->side, cudaStreamNonBlocking), "shadow side stream");
         for (cudaEvent_t* e : {&sh->ev_fork, &sh->ev_t, &sh->ev_base})
             ck(cudaEventCreateWithFlags(e, cudaEventDisableTiming), "event");
-        for (double2** b : {&sh->omega, &sh->N0, &sh->N1, &sh->us, &sh->R, &sh->tmpA, &sh->tmpB})
+        for (double2** b : {&sh->omega, &sh->N0, &sh->N1, &sh->us, &sh->R, &sh->Nbase, &sh->tmpA, &sh->tmpB})
             *b = sh->field();
         sh->q = (double2*)sh->dalloc(c->S() * sizeof(double2));
         sh->pw = (double*)sh->dalloc((size_t)3 * c->h.d.nm * c->h.d.nk * sizeof(double2));

@@ -281,10 +281,6 @@ __global__ void k_anal_theta(Geo g, FieldPtrs f, const T2* __restrict__ Z, const
     T2* res = fft_cols<T2, KB, KB, -1>(buf0, buf1, g.nt, tw);
     double2* dst = f.out[fi] + off + (size_t)j * g.nm * g.nk;
     const double2* add = f.add[fi] ? f.add[fi] + off + (size_t)j * g.nm * g.nk : nullptr;
-    const bool base = f.bmode && fi < 3;
-    const double2* bs = base ? f.bsrc + off + (size_t)j * g.nm * g.nk : nullptr;
-    double U = 0, dU = 0;
-    if (base) base_flow_at(g, b, j, U, dU);
     for (int i = threadIdx.x; i < g.nm * KB; i += blockDim.x) {
         const int im = i / KB, kk = i % KB;
         if (kk >= kw) continue;
@@ -296,7 +292,6 @@ __global__ void k_anal_theta(Geo g, FieldPtrs f, const T2* __restrict__ Z, const
         }
         const size_t o = (size_t)im * g.nk + k0 + kk;
         if (add) v = make_double2(v.x + add[o].x, v.y + add[o].y);
-        if (base) v = add_base_term(g, f, bs, fi, o, k0 + kk, U, dU, v);
         dst[o] = v;
     }
 }
@@ -500,10 +495,6 @@ __global__ void __launch_bounds__(128) k_anal2(Geo g, FieldPtrs f, const T2* __r
     __syncthreads();
     double2* dst = f.out[fi] + off + (size_t)j * g.nm * g.nk;
     const double2* add = f.add[fi] ? f.add[fi] + off + (size_t)j * g.nm * g.nk : nullptr;
-    const bool base = f.bmode && fi < 3;
-    const double2* bs = base ? f.bsrc + off + (size_t)j * g.nm * g.nk : nullptr;
-    double U = 0, dU = 0;
-    if (base) base_flow_at(g, b, j, U, dU);
     for (int t = threadIdx.x; t < KB * N2; t += blockDim.x) {
         const int kk = t % KB, m2 = t / KB, k = k0 + kk;
         T2 v[N1];
@@ -521,7 +512,6 @@ __global__ void __launch_bounds__(128) k_anal2(Geo g, FieldPtrs f, const T2* __r
                     const size_t o = (size_t)(m + g.M) * g.nk + k;
                     double2 x = to_d(v[m1]);
                     if (add) x = make_double2(x.x + add[o].x, x.y + add[o].y);
-                    if (base) x = add_base_term(g, f, bs, fi, o, k, U, dU, x);
                     dst[o] = x;
                 }
             }
@@ -535,7 +525,6 @@ __global__ void __launch_bounds__(128) k_anal2(Geo g, FieldPtrs f, const T2* __r
             const double2 vm = to_d(buf[(m > 0 ? N - m : -m) * KB]);
             double2 x = make_double2(0.5 * (v.x + vm.x), 0.5 * (v.y - vm.y));
             if (add) x = make_double2(x.x + add[(size_t)im * g.nk].x, x.y + add[(size_t)im * g.nk].y);
-            if (base) x = add_base_term(g, f, bs, fi, (size_t)im * g.nk, 0, U, dU, x);
             dst[(size_t)im * g.nk] = x;
         }
     }
