@@ -828,9 +828,10 @@ def main():
         extra("single_step", lambda: {"mixed": time_single_steps(L, torch, L.PNOP_MIXED),
                                       "mixed_df": time_single_steps(L, torch, L.PNOP_MIXED_DF),
                                       "fp64": time_single_steps(L, torch, L.PNOP_FP64)})
-        extra("budget_sweep_mixed", lambda: budget_sweep(L, torch, L.PNOP_MIXED, H))
-        extra("host_tier_mixed", lambda: host_tier_report(L, torch, L.PNOP_MIXED, H))
-        extra("continuous_adjoint_mixed", lambda: continuous_adjoint_report(L, torch, L.PNOP_MIXED, H, s))
+        # the side reports run the main line's path
+        extra("budget_sweep", lambda: budget_sweep(L, torch, main_prec, H))
+        extra("host_tier", lambda: host_tier_report(L, torch, main_prec, H))
+        extra("continuous_adjoint", lambda: continuous_adjoint_report(L, torch, main_prec, H, s))
         extra("batched_gradients", lambda: batch_report(L, torch))
     if not args.no_serving and ws == 1:
         extra("serving", lambda: serving_report(L))
