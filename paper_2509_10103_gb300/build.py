@@ -39,7 +39,7 @@ def up_to_date() -> bool:
     if not os.path.exists(OUT):
         return False
     t = os.path.getmtime(OUT)
-    deps = sources() + [os.path.join(CSRC, f) for f in ("kernels.hpp", "setup.hpp", "dev_common.cuh")]
+    deps = sources() + [os.path.join(CSRC, f) for f in ("kernels.hpp", "setup.hpp", "dev_common.cuh", "dev_df.cuh")]
     deps.append(os.path.join(os.path.dirname(HERE), "include", "pnop.h"))
     return all(os.path.getmtime(d) <= t for d in deps)
 

@@ -80,6 +80,48 @@ static inline void check_launch(const char* what) {
 }
 static inline unsigned nblk(size_t n, int bs) { return (unsigned)((n + bs - 1) / bs); }
 
+// ------------------------------------------------------------------ launches
+// Programmatic dependent launch.  Every kernel of the library starts with
+// grid_dep_sync(): it waits until the grids it depends on have completed and
+// their writes are visible, then allows the next grid on the stream to be
+// launched at once.  A kernel launched with launch_pdl can thus be scheduled
+// while its predecessor is still in its last wave, and starts work the moment
+// the predecessor ends, instead of after a full launch round trip; it never
+// reads or writes memory before the wait, so stream order is kept.
+// launch_serial launches without that relaxation: the single-wave kernels
+// whose time depends on an even spread of their blocks over the SMs (the
+// banded solves) use it, so that all their blocks are placed on an idle GPU.
+__device__ __forceinline__ void grid_dep_sync() {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+template <class... KArgs, class... Args>
+inline void launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, Args&&... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
+
+template <class... KArgs, class... Args>
+inline void launch_serial(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                          Args&&... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
+
 // Raises the dynamic shared-memory limit of a kernel to 200 KB once per
 // (kernel, device): the attribute is per device, and launches come from
 // several host threads (the serving layer) and several devices.

@@ -88,6 +88,7 @@ __device__ __forceinline__ double2 band_col(const Geo& g, const double* B0, cons
 }
 
 __global__ void k_curl(Geo g, const double2* __restrict__ u, double2* __restrict__ w) {
+    grid_dep_sync();
     Idx d;
     if (!decode(g, d)) return;
     u += d.off;
@@ -104,6 +105,7 @@ __global__ void k_curl(Geo g, const double2* __restrict__ u, double2* __restrict
 }
 
 __global__ void k_curlT_acc(Geo g, const double2* __restrict__ wb, double2* __restrict__ ub) {
+    grid_dep_sync();
     Idx d;
     if (!decode(g, d)) return;
     wb += d.off;
@@ -151,6 +153,7 @@ __device__ __forceinline__ void base_block(const Geo& g, double& U, double& dU) 
 // the remainder couples u_z back into (u_r, u_theta) and makes k = 0 modes of
 // steady pipe flow grow at high Re.
 __global__ void k_base(Geo g, const double2* __restrict__ u, double2* __restrict__ N) {
+    grid_dep_sync();
     double U, dU;
     base_block(g, U, dU);
     Idx d;
@@ -167,6 +170,7 @@ __global__ void k_base(Geo g, const double2* __restrict__ u, double2* __restrict
 
 // transpose (Euclidean cotangents): ub = conj(-i a) nb = i a nb; ub_r -= dU nb_z
 __global__ void k_baseT(Geo g, const double2* __restrict__ nb, double2* __restrict__ ub) {
+    grid_dep_sync();
     double U, dU;
     base_block(g, U, dU);
     Idx d;
@@ -184,6 +188,7 @@ __global__ void k_baseT(Geo g, const double2* __restrict__ nb, double2* __restri
 // Velocity-gradient tensor in cylindrical components, G[3 i + j] = (grad u)_ij:
 // (d_r u_j), ((im u_r - u_theta)/r, (im u_theta + u_r)/r, im u_z / r), (i k_z u_j).
 __global__ void k_grad_u(Geo g, const double2* __restrict__ u, double2* __restrict__ G) {
+    grid_dep_sync();
     Idx d;
     if (!decode(g, d)) return;  // single-request launches only (the launcher checks)
     const size_t o = sidx(g, d.j, d.im, d.k), S = d.S;
@@ -204,6 +209,7 @@ __global__ void k_grad_u(Geo g, const double2* __restrict__ u, double2* __restri
 
 // Base-flow part of the continuous-adjoint forcing: N = U dw/dz - w_z dU/dr e_r
 __global__ void k_base_adj(Geo g, const double2* __restrict__ w, double2* __restrict__ N) {
+    grid_dep_sync();
     double U, dU;
     base_block(g, U, dU);
     Idx d;
@@ -330,6 +336,7 @@ __device__ __forceinline__ dacc2 band_col_t(const Geo& g, const float2* B0, cons
 __device__ __forceinline__ double2 df_out(const dacc2& a) { return make_double2(df_result(a.re), df_result(a.im)); }
 
 __global__ void __launch_bounds__(kTK* kTG) k_curl_df(Geo g, const double2* __restrict__ u, double2* __restrict__ w) {
+    grid_dep_sync();
     __shared__ DfTile tz, tt;
     const TBlk t = tdecode(g);
     u += t.off;
@@ -367,6 +374,7 @@ __global__ void __launch_bounds__(kTK* kTG) k_curl_df(Geo g, const double2* __re
 
 __global__ void __launch_bounds__(kTK* kTG) k_curlT_acc_df(Geo g, const double2* __restrict__ wb,
                                                          double2* __restrict__ ub) {
+    grid_dep_sync();
     __shared__ DfTile tz, tt;
     const TBlk t = tdecode(g);
     wb += t.off;
@@ -409,6 +417,7 @@ __global__ void __launch_bounds__(kTK* kTG) k_curlT_acc_df(Geo g, const double2*
 
 __global__ void __launch_bounds__(kTK* kTG) k_stage_div_df(Geo g, const double2* __restrict__ F,
                                                          double2* __restrict__ q) {
+    grid_dep_sync();
     __shared__ DfTile tr;
     const TBlk t = tdecode(g);
     F += t.off;
@@ -442,6 +451,7 @@ __global__ void __launch_bounds__(kTK* kTG) k_stage_div_df(Geo g, const double2*
 __global__ void __launch_bounds__(kTK* kTG) k_stage_rhs_df(Geo g, const double2* __restrict__ u,
                                                          const double2* __restrict__ F,
                                                          const double2* __restrict__ p, double2* __restrict__ R) {
+    grid_dep_sync();
     __shared__ DfTile tp;
     const TBlk t = tdecode(g);
     u = moved(u, t.off);
@@ -513,6 +523,7 @@ __global__ void __launch_bounds__(kTK* kTG) k_stage_rhs_df(Geo g, const double2*
 
 __global__ void __launch_bounds__(kTK* kTG) k_stageT_qbar_df(Geo g, const double2* __restrict__ Fb,
                                                            double2* __restrict__ q) {
+    grid_dep_sync();
     __shared__ DfTile tr;
     const TBlk t = tdecode(g);
     Fb += t.off;
@@ -541,6 +552,7 @@ __global__ void __launch_bounds__(kTK* kTG) k_stageT_qbar_df(Geo g, const double
 
 __global__ void __launch_bounds__(kTK* kTG) k_stageT_div_df(Geo g, const double2* __restrict__ z,
                                                           double2* __restrict__ Fb) {
+    grid_dep_sync();
     __shared__ DfTile tz;
     const TBlk t = tdecode(g);
     z += t.off;
@@ -572,6 +584,7 @@ __global__ void __launch_bounds__(kTK* kTG) k_stageT_div_df(Geo g, const double2
 // ------------------------------------------------------------------ radial stage (forward)
 // q = div F (rows j >= 1; q_0 = 0 is the tentative Neumann datum)
 __global__ void k_stage_div(Geo g, const double2* __restrict__ F, double2* __restrict__ q) {
+    grid_dep_sync();
     Idx d;
     if (!decode(g, d)) return;
     F += d.off;
@@ -620,6 +633,7 @@ __global__ void __launch_bounds__(2 * kSK) k_band_solve(Geo g, const double* __r
                                                   double2* __restrict__ X, const double2* __restrict__ add, int helm,
                                                   int zero_row0, double* __restrict__ pw,
                                                   const double2* __restrict__ usub) {
+    grid_dep_sync();
     constexpr int NC1 = NL + (DIAG1 ? 1 : 0);  // forward sweep: columns [0, NC1)
     constexpr int NC2 = kB - NC1;               // backward sweep: columns [NC1, 13)
     constexpr int NCM = NC1 > NC2 ? NC1 : NC2;
@@ -764,6 +778,7 @@ __global__ void __launch_bounds__(2 * kSK, 6) k_band_solve_reg(Geo g, const doub
                                                       double2* __restrict__ X, const double2* __restrict__ add,
                                                       int helm, int zero_row0, double* __restrict__ pw,
                                                       const double2* __restrict__ usub) {
+    grid_dep_sync();
     constexpr int NC1 = NL + (DIAG1 ? 1 : 0);
     constexpr int NC2 = kB - NC1;
     constexpr int NCM = NC1 > NC2 ? NC1 : NC2;
@@ -915,6 +930,7 @@ __global__ void __launch_bounds__(2 * kSK, 6) k_band_solve_reg(Geo g, const doub
 // gives A_v^{-1} E (B_v T u + F') + T u.
 __global__ void k_stage_rhs(Geo g, const double2* __restrict__ u, const double2* __restrict__ F,
                             const double2* __restrict__ p, double2* __restrict__ R) {
+    grid_dep_sync();
     Idx d;
     if (!decode(g, d)) return;
     u = moved(u, d.off);
@@ -974,6 +990,7 @@ __device__ __forceinline__ double infl_at(const double* h, const Geo& g, int im,
 __global__ void k_stage_finish(Geo g, const double2* __restrict__ R, const double2* __restrict__ addto,
                                const double2* __restrict__ usub, const double2* __restrict__ pw,
                                double2* __restrict__ out) {
+    grid_dep_sync();
     Idx d;
     if (!decode(g, d)) return;
     R += d.off;
@@ -1027,6 +1044,7 @@ __global__ void k_stage_finish(Geo g, const double2* __restrict__ R, const doubl
 __global__ void k_stage_finish_df(Geo g, const double2* __restrict__ R, const double2* __restrict__ addto,
                                   const double2* __restrict__ usub, const double2* __restrict__ pw,
                                   double2* __restrict__ out) {
+    grid_dep_sync();
     Idx d;
     if (!decode(g, d)) return;
     R += d.off;
@@ -1111,6 +1129,7 @@ __global__ void k_stage_finish_df(Geo g, const double2* __restrict__ R, const do
 __global__ void __launch_bounds__(kFK* kFJ) k_stageT_finish(Geo g, const double2* __restrict__ un,
                                                            double2* __restrict__ R, double2* __restrict__ ac,
                                                            int ac_add) {
+    grid_dep_sync();
     __shared__ double2 red[kFJ][kFK];
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int k = blockIdx.x * kFK + tx, im = blockIdx.y, m = im - g.M;
@@ -1181,6 +1200,7 @@ __global__ void k_stageT_rhs(Geo g, const double2* __restrict__ X, const double2
                              double cf2, double2* __restrict__ ub, int acc, double2* __restrict__ Fb,
                              const double2* __restrict__ V1, const double2* __restrict__ V2,
                              const double2* __restrict__ ac) {
+    grid_dep_sync();
     Idx d;
     if (!decode(g, d)) return;
     X += d.off;
@@ -1250,6 +1270,7 @@ __global__ void k_stageT_rhs_df(Geo g, const double2* __restrict__ X, const doub
                                 double cf2, double2* __restrict__ ub, int acc, double2* __restrict__ Fb,
                                 const double2* __restrict__ V1, const double2* __restrict__ V2,
                                 const double2* __restrict__ ac) {
+    grid_dep_sync();
     Idx d;
     if (!decode(g, d)) return;
     X += d.off;
@@ -1361,6 +1382,7 @@ __global__ void k_stageT_rhs_df(Geo g, const double2* __restrict__ X, const doub
 
 // qbar = G^H Fb' = D1p^T Fb'_r - i (m/r) Fb'_t - i kz Fb'_z
 __global__ void k_stageT_qbar(Geo g, const double2* __restrict__ Fb, double2* __restrict__ q) {
+    grid_dep_sync();
     Idx d;
     if (!decode(g, d)) return;
     Fb += d.off;
@@ -1380,6 +1402,7 @@ __global__ void k_stageT_qbar(Geo g, const double2* __restrict__ Fb, double2* __
 
 // Fb = Fb' - Dv^H z: Fb_r -= D1v^T z + z/r ; Fb_t += i (m/r) z ; Fb_z += i kz z
 __global__ void k_stageT_div(Geo g, const double2* __restrict__ z, double2* __restrict__ Fb) {
+    grid_dep_sync();
     Idx d;
     if (!decode(g, d)) return;
     z += d.off;
@@ -1406,6 +1429,7 @@ __global__ void k_stageT_div(Geo g, const double2* __restrict__ z, double2* __re
 
 // u(m, 0) and u(-m, 0) <- their Hermitian average; one thread per (c, j, m >= 0)
 __global__ void k_proj_herm(Geo g, double2* __restrict__ u) {
+    grid_dep_sync();
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= 3 * g.nr * (g.M + 1)) return;
     const int m = t % (g.M + 1), cj = t / (g.M + 1);
@@ -1421,6 +1445,7 @@ __global__ void k_proj_herm(Geo g, double2* __restrict__ u) {
 
 // y_j = sum_{c >= 1} D1[j][c] u_r[c] + u_r[j] / r_j + (i m / r_j) u_theta[j] + i k_z u_z[j]  (wall values excluded)
 __global__ void k_proj_div(Geo g, const double2* __restrict__ u, double2* __restrict__ y) {
+    grid_dep_sync();
     Idx d;
     if (!decode(g, d)) return;
     const size_t o = sidx(g, d.j, d.im, d.k), S = d.S;
@@ -1447,6 +1472,7 @@ __global__ void k_proj_div(Geo g, const double2* __restrict__ u, double2* __rest
 // mean-mode threads store the W-weighted mean of u_z over j >= 1 in y(0, mean).
 __global__ void k_proj_solve(Geo g, const double* __restrict__ L, const double2* __restrict__ u,
                              double2* __restrict__ y) {
+    grid_dep_sync();
     constexpr int B = 12, W1 = B + 1;
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= 2 * g.nm * g.nk) return;
@@ -1479,6 +1505,7 @@ __global__ void k_proj_solve(Geo g, const double* __restrict__ L, const double2*
 
 // u -= W^-1 C^H z; wall values zero; mean mode: u_r = 0, u_z -= its weighted mean
 __global__ void k_proj_update(Geo g, double2* __restrict__ u, const double2* __restrict__ z) {
+    grid_dep_sync();
     Idx d;
     if (!decode(g, d)) return;
     const size_t o = sidx(g, d.j, d.im, d.k), S = d.S;
@@ -1510,6 +1537,7 @@ __global__ void k_proj_update(Geo g, double2* __restrict__ u, const double2* __r
 // energy inner product (2 pi Lz W_j c_k / 2).  One thread per mode, fixed
 // summation order.
 __global__ void k_mode_energy(Geo g, const double2* __restrict__ u, double* __restrict__ E) {
+    grid_dep_sync();
     const int mode = blockIdx.x * blockDim.x + threadIdx.x;
     if (mode >= g.nm * g.nk) return;
     const int im = mode / g.nk, k = mode % g.nk;
@@ -1534,6 +1562,7 @@ __global__ void k_mode_energy(Geo g, const double2* __restrict__ u, double* __re
 // stored (-M, k); (M, 0) counts once.  For K = 0 the axial mode is k = 0 and
 // every stored (m, 0) counts once.
 __global__ void __launch_bounds__(1024) k_resolution(Geo g, const double2* __restrict__ u, double* __restrict__ out) {
+    grid_dep_sync();
     __shared__ double red[2][1024];
     const size_t S = (size_t)g.nr * g.nm * g.nk;
     const double w0 = 0.5 * g.ewt;
@@ -1575,6 +1604,7 @@ __global__ void __launch_bounds__(1024) k_resolution(Geo g, const double2* __res
 // n values of batch entry blockIdx.y
 __global__ void k_axpby(Geo g, size_t n, double a, const double2* __restrict__ x, double b,
                         const double2* __restrict__ y, double2* __restrict__ out) {
+    grid_dep_sync();
     const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const size_t off = (size_t)g.slot[blockIdx.y] * g.fs;
@@ -1592,6 +1622,7 @@ __global__ void k_axpby(Geo g, size_t n, double a, const double2* __restrict__ x
 }
 
 __global__ void k_weight(Geo g, const double2* __restrict__ x, double2* __restrict__ out, int divide) {
+    grid_dep_sync();
     Idx d;
     if (!decode(g, d)) return;
     x += d.off;
@@ -1607,6 +1638,7 @@ __global__ void k_weight(Geo g, const double2* __restrict__ x, double2* __restri
 // One partial per block of the 3-D spectral grid (fixed order: deterministic).
 __global__ void k_inner_partial(Geo g, const double2* __restrict__ a, const double2* __restrict__ b,
                                 double* __restrict__ partial) {
+    grid_dep_sync();
     __shared__ double red[128];
     Idx d;
     double acc = 0;
@@ -1632,6 +1664,7 @@ __global__ void k_inner_partial(Geo g, const double2* __restrict__ a, const doub
 // Block b sums the np partials of batch entry b into out[slot[b]].
 __global__ void k_inner_final(Geo g, const double* __restrict__ partial, int np, double scale,
                               double* __restrict__ out) {
+    grid_dep_sync();
     __shared__ double red[1024];
     double acc = 0;
     partial += (size_t)blockIdx.x * np;
@@ -1648,6 +1681,7 @@ __global__ void k_inner_final(Geo g, const double* __restrict__ partial, int np,
 // x *= sqrt(E0 / (scale e2[slot])) over the 3 S values of batch entry blockIdx.y
 __global__ void k_scale_energy(Geo g, size_t n, double2* __restrict__ x, double E0, double scale,
                                const double* __restrict__ e2) {
+    grid_dep_sync();
     const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const int slot = g.slot[blockIdx.y];
@@ -1675,30 +1709,30 @@ static void single_only(const Geo& g, const char* what) {
 }
 
 void launch_curl(const Geo& g, const double2* u, double2* w, cudaStream_t s) {
-    if (g.df) k_curl_df<<<tile_grid(g), tile_block(), 0, s>>>(g, u, w);
-    else k_curl<<<spec_grid(g), spec_bx(g), 0, s>>>(g, u, w);
+    if (g.df) launch_pdl(k_curl_df, tile_grid(g), tile_block(), 0, s, g, u, w);
+    else launch_pdl(k_curl, spec_grid(g), spec_bx(g), 0, s, g, u, w);
     check_launch("curl");
 }
 void launch_curlT_acc(const Geo& g, const double2* wb, double2* ub, cudaStream_t s) {
-    if (g.df) k_curlT_acc_df<<<tile_grid(g), tile_block(), 0, s>>>(g, wb, ub);
-    else k_curlT_acc<<<spec_grid(g), spec_bx(g), 0, s>>>(g, wb, ub);
+    if (g.df) launch_pdl(k_curlT_acc_df, tile_grid(g), tile_block(), 0, s, g, wb, ub);
+    else launch_pdl(k_curlT_acc, spec_grid(g), spec_bx(g), 0, s, g, wb, ub);
     check_launch("curlT");
 }
 void launch_grad_u(const Geo& g, const double2* u, double2* G, cudaStream_t s) {
     single_only(g, "grad_u");
-    k_grad_u<<<spec_grid(g), spec_bx(g), 0, s>>>(g, u, G);
+    launch_pdl(k_grad_u, spec_grid(g), spec_bx(g), 0, s, g, u, G);
     check_launch("grad_u");
 }
 void launch_base_adj(const Geo& g, const double2* w, double2* N, cudaStream_t s) {
-    k_base_adj<<<spec_grid(g), spec_bx(g), 0, s>>>(g, w, N);
+    launch_pdl(k_base_adj, spec_grid(g), spec_bx(g), 0, s, g, w, N);
     check_launch("base_adj");
 }
 void launch_base(const Geo& g, const double2* u, double2* N, cudaStream_t s) {
-    k_base<<<spec_grid(g), spec_bx(g), 0, s>>>(g, u, N);
+    launch_pdl(k_base, spec_grid(g), spec_bx(g), 0, s, g, u, N);
     check_launch("base");
 }
 void launch_baseT(const Geo& g, const double2* nb, double2* ub, cudaStream_t s) {
-    k_baseT<<<spec_grid(g), spec_bx(g), 0, s>>>(g, nb, ub);
+    launch_pdl(k_baseT, spec_grid(g), spec_bx(g), 0, s, g, nb, ub);
     check_launch("baseT");
 }
 
@@ -1716,42 +1750,29 @@ static void launch_band_solve(const Geo& g, const double* fac, size_t fac_stride
     // Helmholtz instance carries the wall-partial epilogue (pw).
     if (helm && g.nr <= kRegRows) {
         const size_t sm = 2 * (size_t)kRC * 9 * kSK * sizeof(double);
-        if (!trans && pw) {
-            smem_limit((const void*)k_band_solve_reg<4, 8, false, kRegRows, true>);
-            k_band_solve_reg<4, 8, false, kRegRows, true><<<nblocks, 2 * kSK, sm, s>>>(g, fac, fac_stride, X, add,
-                                                                                       helm, zero_row0, pw, usub);
-        } else if (!trans) {
-            smem_limit((const void*)k_band_solve_reg<4, 8, false, kRegRows, false>);
-            k_band_solve_reg<4, 8, false, kRegRows, false><<<nblocks, 2 * kSK, sm, s>>>(g, fac, fac_stride, X, add,
-                                                                                        helm, zero_row0, nullptr,
-                                                                                        nullptr);
-        } else {
-            smem_limit((const void*)k_band_solve_reg<8, 4, true, kRegRows, false>);
-            k_band_solve_reg<8, 4, true, kRegRows, false><<<nblocks, 2 * kSK, sm, s>>>(g, fac, fac_stride, X, add,
-                                                                                       helm, zero_row0, nullptr,
-                                                                                       nullptr);
-        }
+        auto go = [&](auto kernel, double* wall_pw, const double2* wall_u) {
+            smem_limit((const void*)kernel);
+            launch_serial(kernel, nblocks, 2 * kSK, sm, s, g, fac, fac_stride, X, add, helm, zero_row0, wall_pw,
+                          wall_u);
+        };
+        if (!trans && pw) go(k_band_solve_reg<4, 8, false, kRegRows, true>, pw, usub);
+        else if (!trans) go(k_band_solve_reg<4, 8, false, kRegRows, false>, nullptr, nullptr);
+        else go(k_band_solve_reg<8, 4, true, kRegRows, false>, nullptr, nullptr);
         return;
     }
     const size_t sm = (size_t)g.nr * kSK * sizeof(double2) + 2 * (size_t)kRC * 9 * kSK * sizeof(double);
-    if (!trans && pw) {
-        smem_limit((const void*)k_band_solve<4, 8, false, true>);
-        k_band_solve<4, 8, false, true><<<nblocks, 2 * kSK, sm, s>>>(g, fac, fac_stride, X, add, helm, zero_row0, pw,
-                                                                     usub);
-    } else if (!trans) {
-        smem_limit((const void*)k_band_solve<4, 8, false, false>);
-        k_band_solve<4, 8, false, false><<<nblocks, 2 * kSK, sm, s>>>(g, fac, fac_stride, X, add, helm, zero_row0,
-                                                                      nullptr, nullptr);
-    } else {
-        smem_limit((const void*)k_band_solve<8, 4, true, false>);
-        k_band_solve<8, 4, true, false><<<nblocks, 2 * kSK, sm, s>>>(g, fac, fac_stride, X, add, helm, zero_row0,
-                                                                     nullptr, nullptr);
-    }
+    auto go = [&](auto kernel, double* wall_pw, const double2* wall_u) {
+        smem_limit((const void*)kernel);
+        launch_serial(kernel, nblocks, 2 * kSK, sm, s, g, fac, fac_stride, X, add, helm, zero_row0, wall_pw, wall_u);
+    };
+    if (!trans && pw) go(k_band_solve<4, 8, false, true>, pw, usub);
+    else if (!trans) go(k_band_solve<4, 8, false, false>, nullptr, nullptr);
+    else go(k_band_solve<8, 4, true, false>, nullptr, nullptr);
 }
 
 void launch_stage_div(const Geo& g, const double2* F, double2* q, cudaStream_t s) {
-    if (g.df) k_stage_div_df<<<tile_grid(g), tile_block(), 0, s>>>(g, F, q);
-    else k_stage_div<<<spec_grid(g), spec_bx(g), 0, s>>>(g, F, q);
+    if (g.df) launch_pdl(k_stage_div_df, tile_grid(g), tile_block(), 0, s, g, F, q);
+    else launch_pdl(k_stage_div, spec_grid(g), spec_bx(g), 0, s, g, F, q);
     check_launch("stage_div");
 }
 void launch_stage_psolve(const Geo& g, double2* q, cudaStream_t s) {
@@ -1759,8 +1780,8 @@ void launch_stage_psolve(const Geo& g, double2* q, cudaStream_t s) {
     check_launch("stage_psolve");
 }
 void launch_stage_rhs(const Geo& g, const double2* u, const double2* F, const double2* p, double2* R, cudaStream_t s) {
-    if (g.df) k_stage_rhs_df<<<tile_grid(g), tile_block(), 0, s>>>(g, u, F, p, R);
-    else k_stage_rhs<<<spec_grid(g), spec_bx(g), 0, s>>>(g, u, F, p, R);
+    if (g.df) launch_pdl(k_stage_rhs_df, tile_grid(g), tile_block(), 0, s, g, u, F, p, R);
+    else launch_pdl(k_stage_rhs, spec_grid(g), spec_bx(g), 0, s, g, u, F, p, R);
     check_launch("stage_rhs");
 }
 void launch_stage_hsolve(const Geo& g, double2* R, const double2* usub, double* pw, cudaStream_t s) {
@@ -1771,12 +1792,12 @@ static inline dim3 mode_grid(const Geo& g) { return dim3((g.nk + kFK - 1) / kFK,
 void launch_stage_finish(const Geo& g, const double2* R, const double2* addto, const double2* usub, const double* pw,
                          double2* out, cudaStream_t s) {
     const double2* p2 = reinterpret_cast<const double2*>(pw);
-    if (g.df) k_stage_finish_df<<<spec_grid(g), spec_bx(g), 0, s>>>(g, R, addto, usub, p2, out);
-    else k_stage_finish<<<spec_grid(g), spec_bx(g), 0, s>>>(g, R, addto, usub, p2, out);
+    if (g.df) launch_pdl(k_stage_finish_df, spec_grid(g), spec_bx(g), 0, s, g, R, addto, usub, p2, out);
+    else launch_pdl(k_stage_finish, spec_grid(g), spec_bx(g), 0, s, g, R, addto, usub, p2, out);
     check_launch("stage_finish");
 }
 void launch_stageT_finish(const Geo& g, const double2* ubn, double2* R, double2* ac, int ac_add, cudaStream_t s) {
-    k_stageT_finish<<<mode_grid(g), dim3(kFK, kFJ), 0, s>>>(g, ubn, R, ac, ac_add);
+    launch_serial(k_stageT_finish, mode_grid(g), dim3(kFK, kFJ), 0, s, g, ubn, R, ac, ac_add);
     check_launch("stageT_finish");
 }
 void launch_stageT_hsolve(const Geo& g, double2* R, const double2* add, cudaStream_t s) {
@@ -1788,19 +1809,21 @@ void launch_stageT_rhs(const Geo& g, const double2* X, const double2* Y, double 
     if (ub && (!V1 || !ac)) throw std::runtime_error("stageT_rhs: the velocity part needs its input and coefficients");
     if (g.df) {
         if (Y)
-            k_stageT_rhs_df<true><<<spec_grid(g), spec_bx(g), 0, s>>>(g, X, Y, cf1, cf2, ub, acc, Fb, V1, V2, ac);
+            launch_pdl(k_stageT_rhs_df<true>, spec_grid(g), spec_bx(g), 0, s, g, X, Y, cf1, cf2, ub, acc, Fb, V1, V2,
+                       ac);
         else
-            k_stageT_rhs_df<false><<<spec_grid(g), spec_bx(g), 0, s>>>(g, X, Y, cf1, cf2, ub, acc, Fb, V1, V2, ac);
+            launch_pdl(k_stageT_rhs_df<false>, spec_grid(g), spec_bx(g), 0, s, g, X, Y, cf1, cf2, ub, acc, Fb, V1, V2,
+                       ac);
     } else if (Y) {
-        k_stageT_rhs<true><<<spec_grid(g), spec_bx(g), 0, s>>>(g, X, Y, cf1, cf2, ub, acc, Fb, V1, V2, ac);
+        launch_pdl(k_stageT_rhs<true>, spec_grid(g), spec_bx(g), 0, s, g, X, Y, cf1, cf2, ub, acc, Fb, V1, V2, ac);
     } else {
-        k_stageT_rhs<false><<<spec_grid(g), spec_bx(g), 0, s>>>(g, X, Y, cf1, cf2, ub, acc, Fb, V1, V2, ac);
+        launch_pdl(k_stageT_rhs<false>, spec_grid(g), spec_bx(g), 0, s, g, X, Y, cf1, cf2, ub, acc, Fb, V1, V2, ac);
     }
     check_launch("stageT_rhs");
 }
 void launch_stageT_qbar(const Geo& g, const double2* Fb, double2* q, cudaStream_t s) {
-    if (g.df) k_stageT_qbar_df<<<tile_grid(g), tile_block(), 0, s>>>(g, Fb, q);
-    else k_stageT_qbar<<<spec_grid(g), spec_bx(g), 0, s>>>(g, Fb, q);
+    if (g.df) launch_pdl(k_stageT_qbar_df, tile_grid(g), tile_block(), 0, s, g, Fb, q);
+    else launch_pdl(k_stageT_qbar, spec_grid(g), spec_bx(g), 0, s, g, Fb, q);
     check_launch("stageT_qbar");
 }
 void launch_stageT_psolve(const Geo& g, double2* q, cudaStream_t s) {
@@ -1808,39 +1831,39 @@ void launch_stageT_psolve(const Geo& g, double2* q, cudaStream_t s) {
     check_launch("stageT_psolve");
 }
 void launch_stageT_div(const Geo& g, const double2* z, double2* Fb, cudaStream_t s) {
-    if (g.df) k_stageT_div_df<<<tile_grid(g), tile_block(), 0, s>>>(g, z, Fb);
-    else k_stageT_div<<<spec_grid(g), spec_bx(g), 0, s>>>(g, z, Fb);
+    if (g.df) launch_pdl(k_stageT_div_df, tile_grid(g), tile_block(), 0, s, g, z, Fb);
+    else launch_pdl(k_stageT_div, spec_grid(g), spec_bx(g), 0, s, g, z, Fb);
     check_launch("stageT_div");
 }
 
 void launch_mode_energy(const Geo& g, const double2* u, double* E, cudaStream_t s) {
     single_only(g, "mode_energy");
-    k_mode_energy<<<nblk((size_t)g.nm * g.nk, 128), 128, 0, s>>>(g, u, E);
+    launch_pdl(k_mode_energy, nblk((size_t)g.nm * g.nk, 128), 128, 0, s, g, u, E);
     check_launch("mode_energy");
 }
 
 void launch_resolution(const Geo& g, const double2* u, double* out, cudaStream_t s) {
     single_only(g, "resolution");
-    k_resolution<<<1, 1024, 0, s>>>(g, u, out);
+    launch_pdl(k_resolution, 1, 1024, 0, s, g, u, out);
     check_launch("resolution");
 }
 
 void launch_project(const Geo& g, double2* u, double2* y, const double* L, cudaStream_t s) {
     single_only(g, "project");
-    k_proj_herm<<<nblk((size_t)3 * g.nr * (g.M + 1), 128), 128, 0, s>>>(g, u);
-    k_proj_div<<<spec_grid(g), spec_bx(g), 0, s>>>(g, u, y);
-    k_proj_solve<<<nblk((size_t)2 * g.nm * g.nk, 64), 64, 0, s>>>(g, L, u, y);
-    k_proj_update<<<spec_grid(g), spec_bx(g), 0, s>>>(g, u, y);
+    launch_pdl(k_proj_herm, nblk((size_t)3 * g.nr * (g.M + 1), 128), 128, 0, s, g, u);
+    launch_pdl(k_proj_div, spec_grid(g), spec_bx(g), 0, s, g, u, y);
+    launch_pdl(k_proj_solve, nblk((size_t)2 * g.nm * g.nk, 64), 64, 0, s, g, L, u, y);
+    launch_pdl(k_proj_update, spec_grid(g), spec_bx(g), 0, s, g, u, y);
     check_launch("project");
 }
 
 void launch_axpby(const Geo& g, size_t n, double a, const double2* x, double b, const double2* y, double2* out,
                   cudaStream_t s) {
-    k_axpby<<<dim3(nblk(n, 256), g.nb), 256, 0, s>>>(g, n, a, x, b, y, out);
+    launch_pdl(k_axpby, dim3(nblk(n, 256), g.nb), 256, 0, s, g, n, a, x, b, y, out);
     check_launch("axpby");
 }
 void launch_weight(const Geo& g, const double2* x, double2* out, int divide, cudaStream_t s) {
-    k_weight<<<spec_grid(g), spec_bx(g), 0, s>>>(g, x, out, divide);
+    launch_pdl(k_weight, spec_grid(g), spec_bx(g), 0, s, g, x, out, divide);
     check_launch("weight");
 }
 size_t inner_partials(const Geo& g) {
@@ -1849,13 +1872,13 @@ size_t inner_partials(const Geo& g) {
 }
 void launch_inner(const Geo& g, const double2* a, const double2* b, double* partial, double* dev_out, cudaStream_t s) {
     const dim3 grid = spec_grid(g);
-    k_inner_partial<<<grid, spec_bx(g), 0, s>>>(g, a, b, partial);
-    k_inner_final<<<g.nb, 1024, 0, s>>>(g, partial, (int)(grid.x * grid.y * (grid.z / g.nb)), g.ewt, dev_out);
+    launch_pdl(k_inner_partial, grid, spec_bx(g), 0, s, g, a, b, partial);
+    launch_pdl(k_inner_final, g.nb, 1024, 0, s, g, partial, (int)(grid.x * grid.y * (grid.z / g.nb)), g.ewt, dev_out);
     check_launch("inner");
 }
 void launch_scale_energy(const Geo& g, double2* x, double E0, double scale, const double* e2, cudaStream_t s) {
     const size_t n = 3 * (size_t)g.nr * g.nm * g.nk;
-    k_scale_energy<<<dim3(nblk(n, 256), g.nb), 256, 0, s>>>(g, n, x, E0, scale, e2);
+    launch_pdl(k_scale_energy, dim3(nblk(n, 256), g.nb), 256, 0, s, g, n, x, E0, scale, e2);
     check_launch("scale_energy");
 }
 

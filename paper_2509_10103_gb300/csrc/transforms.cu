@@ -117,6 +117,7 @@ __device__ T2* fft_cols(T2* a, T2* b, int N, const T2* tw) {
 // Y[f][j][a][k] = sum_m X_f[j][m][k] e^{i m theta_a}   (zero-padded to nt points)
 template <class T2, int KB>
 __global__ void k_synth_theta(Geo g, FieldPtrs f, T2* __restrict__ Y, const T2* __restrict__ twg) {
+    grid_dep_sync();
     extern __shared__ __align__(16) unsigned char smem[];
     T2* buf0 = reinterpret_cast<T2*>(smem);
     T2* buf1 = buf0 + g.nt * KB;
@@ -176,6 +177,7 @@ __device__ __forceinline__ void cadj_products(const T2* row, T2* out) {
 //   ZADJ: inputs u (3), w (3), g (3)   -> outputs w x g (3), g x u (3)
 template <class T2, int MODE>
 __global__ void k_zpass(Geo g, const T2* __restrict__ Y, T2* __restrict__ Z, ZScales sc, const T2* __restrict__ twg) {
+    grid_dep_sync();
     using T = typename RealOf<T2>::T;
     constexpr int NIN = MODE == ZFWD ? 6 : (MODE == ZADJ ? 9 : 18);
     constexpr int NPI = (NIN + 1) / 2;
@@ -262,6 +264,7 @@ __global__ void k_zpass(Geo g, const T2* __restrict__ Y, T2* __restrict__ Z, ZSc
 // plane projected onto Hermitian symmetry.
 template <class T2, int KB>
 __global__ void k_anal_theta(Geo g, FieldPtrs f, const T2* __restrict__ Z, const T2* __restrict__ twg) {
+    grid_dep_sync();
     extern __shared__ __align__(16) unsigned char smem[];
     T2* buf0 = reinterpret_cast<T2*>(smem);
     T2* buf1 = buf0 + g.nt * KB;
@@ -429,6 +432,7 @@ __device__ __forceinline__ void rdft(T2 (&v)[L]) {
 // (s / N2) + N1 (s % N2).
 template <class T2, int KB, int N1, int N2>
 __global__ void __launch_bounds__(128) k_synth2(Geo g, FieldPtrs f, T2* __restrict__ Y, const T2* __restrict__ twg) {
+    grid_dep_sync();
     constexpr int N = N1 * N2;
     extern __shared__ __align__(16) unsigned char smem[];
     T2* buf = reinterpret_cast<T2*>(smem);  // [N][KB]
@@ -472,6 +476,7 @@ __global__ void __launch_bounds__(128) k_synth2(Geo g, FieldPtrs f, T2* __restri
 template <class T2, int KB, int N1, int N2>
 __global__ void __launch_bounds__(128) k_anal2(Geo g, FieldPtrs f, const T2* __restrict__ Z,
                                                const T2* __restrict__ twg) {
+    grid_dep_sync();
     constexpr int N = N1 * N2;
     extern __shared__ __align__(16) unsigned char smem[];
     T2* buf = reinterpret_cast<T2*>(smem);  // [N][KB]
@@ -530,21 +535,37 @@ __global__ void __launch_bounds__(128) k_anal2(Geo g, FieldPtrs f, const T2* __r
     }
 }
 
+// Compile-time loop: f(std::integral_constant<int, 0>()) ... f(<N - 1>).
+template <class F, int... I>
+__device__ __forceinline__ void static_for_impl(F& f, std::integer_sequence<int, I...>) {
+    (f(std::integral_constant<int, I>()), ...);
+}
+template <int N, class F> __device__ __forceinline__ void static_for(F&& f) {
+    static_for_impl(f, std::make_integer_sequence<int, N>());
+}
+
 // z pass, two-pass FFTs in place in padded shared-memory columns (one gap
 // after every run of N2 slots keeps both access patterns free of bank
-// conflicts).  Same contract as k_zpass.
-template <class T2, int MODE, int N1, int N2>
-__global__ void k_zpass2(Geo g, const T2* __restrict__ Y, T2* __restrict__ Z, ZScales sc, const T2* __restrict__ twg) {
+// conflicts), RB rows (theta indices a) of one radial index per block.  The
+// spectra are 3/2-padded: K = N/3 - 1 is a compile-time constant here (the
+// launcher checks it), so the inverse pass knows at compile time which of its
+// strided inputs fall in the zero band K < n < N - K and loads none of them,
+// and the forward pass stores no output of that band (the separation never
+// reads it).  Same contract as k_zpass.
+template <class T2, int MODE, int N1, int N2, int RB>
+__global__ void __launch_bounds__(96, 6)
+    k_zpass2(Geo g, const T2* __restrict__ Y, T2* __restrict__ Z, ZScales sc, const T2* __restrict__ twg) {
+    grid_dep_sync();
     using T = typename RealOf<T2>::T;
-    constexpr int N = N1 * N2, NP = N + N1;
+    constexpr int N = N1 * N2, NP = N + N1, KC = N / 3 - 1, NK = KC + 1;
     constexpr int NIN = MODE == ZFWD ? 6 : (MODE == ZADJ ? 9 : 18);
     constexpr int NPI = (NIN + 1) / 2;
     constexpr int NOUT = MODE == ZADJ ? 6 : 3;
     constexpr int NPO = (NOUT + 1) / 2;
     extern __shared__ __align__(16) unsigned char smem[];
-    T2* col = reinterpret_cast<T2*>(smem);  // [NPI][NP]
-    T2* tw = col + NPI * NP;                 // [N]
-    const int K = g.K, nk = g.nk, a = blockIdx.x, j = blockIdx.y;
+    T2* col = reinterpret_cast<T2*>(smem);  // [RB][NPI][NP]
+    T2* tw = col + RB * NPI * NP;            // [N]
+    const int a0 = blockIdx.x * RB, j = blockIdx.y;
     const size_t poff = (size_t)g.slot[blockIdx.z] * g.ps;  // batch entry blockIdx.z
     Y += poff;
     Z += poff;
@@ -552,111 +573,128 @@ __global__ void k_zpass2(Geo g, const T2* __restrict__ Y, T2* __restrict__ Z, ZS
     for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = twg[i];
     __syncthreads();
     // inverse, strided pass: Hermitian-extended spectra, two real fields per column
-    for (int t = threadIdx.x; t < NPI * N2; t += blockDim.x) {
-        const int p = t / N2, n2 = t % N2;
+    for (int t = threadIdx.x; t < RB * NPI * N2; t += blockDim.x) {
+        const int r = t / (NPI * N2), pn = t - r * (NPI * N2), p = pn / N2, n2 = pn - p * N2;
         const int f1 = 2 * p, f2 = 2 * p + 1;
-        const T2* y1 = Y + ((size_t)(f1 * g.nr + j) * g.nt + a) * nk;
         const bool has2 = f2 < NIN;
-        const T2* y2 = Y + ((size_t)((has2 ? f2 : f1) * g.nr + j) * g.nt + a) * nk;
+        const T2* y1 = Y + ((size_t)(f1 * g.nr + j) * g.nt + a0 + r) * NK;
+        const T2* y2 = Y + ((size_t)((has2 ? f2 : f1) * g.nr + j) * g.nt + a0 + r) * NK;
         const T h01 = zs<T>(sc.h0, sc.fh0, f1), hk1 = zs<T>(sc.hk, sc.fhk, f1);
         const T h02 = has2 ? zs<T>(sc.h0, sc.fh0, f2) : (T)0, hk2 = has2 ? zs<T>(sc.hk, sc.fhk, f2) : (T)0;
+        // H1 + i H2 at z-wavenumber k (positive side) or conj(H1) + i conj(H2)
+        // (negative side); only k = 0 drops its imaginary parts
+        auto entry = [&](int k, bool neg, bool may0) {
+            const T2 a1 = y1[k], a2 = has2 ? y2[k] : mk<T2>(0, 0);
+            const bool z0 = may0 && k == 0;
+            const T2 h1 = z0 ? mk<T2>(h01 * a1.x, 0) : mk<T2>(hk1 * a1.x, hk1 * a1.y);
+            const T2 h2 = z0 ? mk<T2>(h02 * a2.x, 0) : mk<T2>(hk2 * a2.x, hk2 * a2.y);
+            return !neg ? mk<T2>(h1.x - h2.y, h1.y + h2.x) : mk<T2>(h1.x + h2.y, -h1.y + h2.x);
+        };
         T2 v[N1];
-#pragma unroll
-        for (int n1 = 0; n1 < N1; ++n1) {
-            const int n = n2 + N2 * n1;
-            int k = -1;
-            bool neg = false;
-            if (n <= K) k = n;
-            else if (n >= N - K) { k = N - n; neg = true; }
-            T2 q = mk<T2>(0, 0);
-            if (k >= 0) {
-                const T2 a1 = y1[k], a2 = has2 ? y2[k] : mk<T2>(0, 0);
-                const T2 h1 = k == 0 ? mk<T2>(h01 * a1.x, 0) : mk<T2>(hk1 * a1.x, hk1 * a1.y);
-                const T2 h2 = k == 0 ? mk<T2>(h02 * a2.x, 0) : mk<T2>(hk2 * a2.x, hk2 * a2.y);
-                q = !neg ? mk<T2>(h1.x - h2.y, h1.y + h2.x)    // H1 + i H2
-                         : mk<T2>(h1.x + h2.y, -h1.y + h2.x);  // conj(H1) + i conj(H2)
+        static_for<N1>([&](auto I) {
+            constexpr int n1 = decltype(I)::value;
+            constexpr int lo = N2 * n1, hi = lo + N2 - 1;
+            const int n = n2 + lo;
+            if constexpr (hi <= KC) {
+                v[n1] = entry(n, false, n1 == 0);
+            } else if constexpr (lo >= N - KC) {
+                v[n1] = entry(N - n, true, false);
+            } else if constexpr (lo > KC && hi < N - KC) {
+                v[n1] = mk<T2>(0, 0);
+            } else {
+                v[n1] = n <= KC ? entry(n, false, n1 == 0) : (n >= N - KC ? entry(N - n, true, false) : mk<T2>(0, 0));
             }
-            v[n1] = q;
-        }
+        });
         rdft<T2, N1, +1>(v);
+        T2* c = col + (r * NPI + p) * NP;
 #pragma unroll
-        for (int k1 = 0; k1 < N1; ++k1) col[p * NP + at(n2 + N2 * k1)] = twr<T2, +1>(v[k1], tw, n2 * k1);
+        for (int k1 = 0; k1 < N1; ++k1) c[at(n2 + N2 * k1)] = twr<T2, +1>(v[k1], tw, n2 * k1);
     }
     __syncthreads();
     // inverse, contiguous pass: physical values
-    for (int t = threadIdx.x; t < NPI * N1; t += blockDim.x) {
-        const int p = t / N1, k1 = t % N1;
+    for (int t = threadIdx.x; t < RB * NPI * N1; t += blockDim.x) {
+        const int rp = t / N1, k1 = t - rp * N1;
+        T2* c = col + rp * NP;
         T2 v[N2];
 #pragma unroll
-        for (int n2 = 0; n2 < N2; ++n2) v[n2] = col[p * NP + at(N2 * k1 + n2)];
+        for (int n2 = 0; n2 < N2; ++n2) v[n2] = c[at(N2 * k1 + n2)];
         rdft<T2, N2, +1>(v);
 #pragma unroll
-        for (int k2 = 0; k2 < N2; ++k2) col[p * NP + at(N2 * k1 + k2)] = v[k2];
+        for (int k2 = 0; k2 < N2; ++k2) c[at(N2 * k1 + k2)] = v[k2];
     }
     __syncthreads();
     // pointwise products, in place (each slot read and written by one thread)
-    for (int s = threadIdx.x; s < N; s += blockDim.x) {
+    for (int t = threadIdx.x; t < RB * N; t += blockDim.x) {
+        const int r = t / N, s = t - r * N;
+        T2* c = col + r * NPI * NP;
         const int o = at(s);
         if constexpr (MODE == ZCADJ) {
             T2 row[NPI], res[2];
 #pragma unroll
-            for (int p = 0; p < NPI; ++p) row[p] = col[p * NP + o];
+            for (int p = 0; p < NPI; ++p) row[p] = c[p * NP + o];
             cadj_products<T2>(row, res);
-            col[o] = res[0];
-            col[NP + o] = res[1];
+            c[o] = res[0];
+            c[NP + o] = res[1];
             continue;
         }
-        const T2 c0 = col[o], c1 = col[NP + o], c2 = col[2 * NP + o];
+        const T2 c0 = c[o], c1 = c[NP + o], c2 = c[2 * NP + o];
         const T ur = c0.x, ut = c0.y, uz = c1.x;
         const T wr = c1.y, wt = c2.x, wz = c2.y;
         if (MODE == ZFWD) {
-            col[o] = mk<T2>(ut * wz - uz * wt, uz * wr - ur * wz);
-            col[NP + o] = mk<T2>(ur * wt - ut * wr, 0);
+            c[o] = mk<T2>(ut * wz - uz * wt, uz * wr - ur * wz);
+            c[NP + o] = mk<T2>(ur * wt - ut * wr, 0);
         } else {
-            const T2 c3 = col[3 * NP + o], c4 = col[4 * NP + o];
+            const T2 c3 = c[3 * NP + o], c4 = c[4 * NP + o];
             const T gr = c3.x, gt = c3.y, gz = c4.x;
-            col[o] = mk<T2>(wt * gz - wz * gt, wz * gr - wr * gz);           // w x g
-            col[NP + o] = mk<T2>(wr * gt - wt * gr, gt * uz - gz * ut);      // (w x g)_z, (g x u)_r
-            col[2 * NP + o] = mk<T2>(gz * ur - gr * uz, gr * ut - gt * ur);  // (g x u)_theta, (g x u)_z
+            c[o] = mk<T2>(wt * gz - wz * gt, wz * gr - wr * gz);           // w x g
+            c[NP + o] = mk<T2>(wr * gt - wt * gr, gt * uz - gz * ut);      // (w x g)_z, (g x u)_r
+            c[2 * NP + o] = mk<T2>(gz * ur - gr * uz, gr * ut - gt * ur);  // (g x u)_theta, (g x u)_z
         }
     }
     __syncthreads();
     // forward, contiguous pass
-    for (int t = threadIdx.x; t < NPO * N1; t += blockDim.x) {
-        const int p = t / N1, k1 = t % N1;
+    for (int t = threadIdx.x; t < RB * NPO * N1; t += blockDim.x) {
+        const int r = t / (NPO * N1), pk = t - r * (NPO * N1), p = pk / N1, k1 = pk - p * N1;
+        T2* c = col + (r * NPI + p) * NP;
         T2 v[N2];
 #pragma unroll
-        for (int k2 = 0; k2 < N2; ++k2) v[k2] = col[p * NP + at(N2 * k1 + k2)];
+        for (int k2 = 0; k2 < N2; ++k2) v[k2] = c[at(N2 * k1 + k2)];
         rdft<T2, N2, -1>(v);
 #pragma unroll
-        for (int m2 = 0; m2 < N2; ++m2) col[p * NP + at(N2 * k1 + m2)] = twr<T2, -1>(v[m2], tw, k1 * m2);
+        for (int m2 = 0; m2 < N2; ++m2) c[at(N2 * k1 + m2)] = twr<T2, -1>(v[m2], tw, k1 * m2);
     }
     __syncthreads();
-    // forward, strided pass: natural-order spectra
-    for (int t = threadIdx.x; t < NPO * N2; t += blockDim.x) {
-        const int p = t / N2, m2 = t % N2;
+    // forward, strided pass: natural-order spectra, the zero band left out
+    for (int t = threadIdx.x; t < RB * NPO * N2; t += blockDim.x) {
+        const int r = t / (NPO * N2), pm = t - r * (NPO * N2), p = pm / N2, m2 = pm - p * N2;
+        T2* c = col + (r * NPI + p) * NP;
         T2 v[N1];
 #pragma unroll
-        for (int k1 = 0; k1 < N1; ++k1) v[k1] = col[p * NP + at(m2 + N2 * k1)];
+        for (int k1 = 0; k1 < N1; ++k1) v[k1] = c[at(m2 + N2 * k1)];
         rdft<T2, N1, -1>(v);
-#pragma unroll
-        for (int m1 = 0; m1 < N1; ++m1) col[p * NP + at(m2 + N2 * m1)] = v[m1];
+        static_for<N1>([&](auto I) {
+            constexpr int m1 = decltype(I)::value;
+            constexpr int lo = N2 * m1, hi = lo + N2 - 1;
+            if constexpr (!(lo > KC && hi < N - KC)) c[at(m2 + lo)] = v[m1];
+        });
     }
     __syncthreads();
     // separate the two real products of each column, truncate to k <= K, scale
-    for (int p = 0; p < NPO; ++p)
-        for (int k = threadIdx.x; k < nk; k += blockDim.x) {
-            const T2 P = col[p * NP + at(k)];
-            const T2 Pm = col[p * NP + at((N - k) % N)];
-            const int o1 = 2 * p, o2 = 2 * p + 1;
-            const T s1 = k == 0 ? zs<T>(sc.o0, sc.fo0, o1) : zs<T>(sc.ok, sc.fok, o1);
-            Z[((size_t)(o1 * g.nr + j) * g.nt + a) * nk + k] = mk<T2>((T)0.5 * (P.x + Pm.x) * s1, (T)0.5 * (P.y - Pm.y) * s1);
-            if (o2 < NOUT) {
-                const T s2 = k == 0 ? zs<T>(sc.o0, sc.fo0, o2) : zs<T>(sc.ok, sc.fok, o2);
-                Z[((size_t)(o2 * g.nr + j) * g.nt + a) * nk + k] =
-                    mk<T2>((T)0.5 * (P.y + Pm.y) * s2, (T)-0.5 * (P.x - Pm.x) * s2);
-            }
+    for (int t = threadIdx.x; t < RB * NPO * NK; t += blockDim.x) {
+        const int r = t / (NPO * NK), pk = t - r * (NPO * NK), p = pk / NK, k = pk - p * NK;
+        const T2* c = col + (r * NPI + p) * NP;
+        const T2 P = c[at(k)];
+        const T2 Pm = c[at((N - k) % N)];
+        const int o1 = 2 * p, o2 = 2 * p + 1;
+        const size_t row = (size_t)j * g.nt + a0 + r;
+        const T s1 = k == 0 ? zs<T>(sc.o0, sc.fo0, o1) : zs<T>(sc.ok, sc.fok, o1);
+        Z[((size_t)o1 * g.nr * g.nt + row) * NK + k] = mk<T2>((T)0.5 * (P.x + Pm.x) * s1, (T)0.5 * (P.y - Pm.y) * s1);
+        if (o2 < NOUT) {
+            const T s2 = k == 0 ? zs<T>(sc.o0, sc.fo0, o2) : zs<T>(sc.ok, sc.fok, o2);
+            Z[((size_t)o2 * g.nr * g.nt + row) * NK + k] =
+                mk<T2>((T)0.5 * (P.y + Pm.y) * s2, (T)-0.5 * (P.x - Pm.x) * s2);
         }
+    }
 }
 
 // ------------------------------------------------------------------ launchers
@@ -678,7 +716,7 @@ static void synth_theta_kb(const Geo& g, const FieldPtrs& f, int nfield, T2* Y, 
     const size_t sm = (size_t)(2 * g.nt * KB + g.nt) * sizeof(T2);
     smem_limit((const void*)k_synth_theta<T2, KB>);
     dim3 grid((g.nk + KB - 1) / KB, g.nr, nfield * g.nb);
-    k_synth_theta<T2, KB><<<grid, 256, sm, s>>>(g, f, Y, tw);
+    launch_pdl(k_synth_theta<T2, KB>, grid, 256, sm, s, g, f, Y, tw);
 }
 
 template <class T2, int KB>
@@ -686,7 +724,7 @@ static void anal_theta_kb(const Geo& g, const FieldPtrs& f, int nfield, const T2
     const size_t sm = (size_t)(2 * g.nt * KB + g.nt) * sizeof(T2);
     smem_limit((const void*)k_anal_theta<T2, KB>);
     dim3 grid((g.nk + KB - 1) / KB, g.nr, nfield * g.nb);
-    k_anal_theta<T2, KB><<<grid, 256, sm, s>>>(g, f, Z, tw);
+    launch_pdl(k_anal_theta<T2, KB>, grid, 256, sm, s, g, f, Z, tw);
 }
 
 // Two-pass register kernels serve the lengths with a split N = N1 N2 below;
@@ -697,14 +735,14 @@ static void synth2(const Geo& g, const FieldPtrs& f, int nfield, T2* Y, const T2
     const size_t sm = (size_t)(N1 * N2 * KB + N1 * N2) * sizeof(T2);
     smem_limit((const void*)k_synth2<T2, KB, N1, N2>);
     dim3 grid((g.nk + KB - 1) / KB, g.nr, nfield * g.nb);
-    k_synth2<T2, KB, N1, N2><<<grid, 128, sm, s>>>(g, f, Y, tw);
+    launch_pdl(k_synth2<T2, KB, N1, N2>, grid, 128, sm, s, g, f, Y, tw);
 }
 template <class T2, int KB, int N1, int N2>
 static void anal2(const Geo& g, const FieldPtrs& f, int nfield, const T2* Z, const T2* tw, cudaStream_t s) {
     const size_t sm = (size_t)(N1 * N2 * KB + N1 * N2) * sizeof(T2);
     smem_limit((const void*)k_anal2<T2, KB, N1, N2>);
     dim3 grid((g.nk + KB - 1) / KB, g.nr, nfield * g.nb);
-    k_anal2<T2, KB, N1, N2><<<grid, 128, sm, s>>>(g, f, Z, tw);
+    launch_pdl(k_anal2<T2, KB, N1, N2>, grid, 128, sm, s, g, f, Z, tw);
 }
 
 template <class T2>
@@ -748,19 +786,36 @@ static unsigned zpass_threads(const Geo& g) {
     return (unsigned)std::max(32, std::min(256, t));
 }
 
-template <class T2, int MODE, int N1, int N2>
+// rows per block of the two-pass z kernel: two for the forward pass (its
+// three packed columns then fill the block's threads better, at 22 KB of
+// shared memory: 16.6 against 18.4 ms per 64x64x256 gradient), one for the
+// adjoint passes, whose five and nine columns fill them already (two rows
+// measured slower there: 13.6 against 12.8 ms)
+template <int MODE> constexpr int zpass_rows() { return MODE == ZFWD ? 2 : 1; }
+
+template <class T2, int MODE, int N1, int N2, int RB>
 static void zpass2(const Geo& g, const T2* Y, T2* Z, const ZScales& sc, const T2* tw, cudaStream_t s) {
     constexpr int NPI = MODE == ZFWD ? 3 : (MODE == ZADJ ? 5 : 9);
-    const size_t sm = (size_t)(NPI * (N1 * N2 + N1) + N1 * N2) * sizeof(T2);
-    smem_limit((const void*)k_zpass2<T2, MODE, N1, N2>);
-    k_zpass2<T2, MODE, N1, N2><<<dim3(g.nt, g.nr, g.nb), zpass_threads(g), sm, s>>>(g, Y, Z, sc, tw);
+    const size_t sm = (size_t)(RB * NPI * (N1 * N2 + N1) + N1 * N2) * sizeof(T2);
+    smem_limit((const void*)k_zpass2<T2, MODE, N1, N2, RB>);
+    launch_pdl(k_zpass2<T2, MODE, N1, N2, RB>, dim3(g.nt / RB, g.nr, g.nb), zpass_threads(g), sm, s, g, Y, Z, sc,
+               tw);
 }
+template <class T2, int MODE, int N1, int N2>
+static void zpass2_rows(const Geo& g, const T2* Y, T2* Z, const ZScales& sc, const T2* tw, cudaStream_t s) {
+    constexpr int RB = zpass_rows<MODE>();
+    if (g.nt % RB == 0) zpass2<T2, MODE, N1, N2, RB>(g, Y, Z, sc, tw, s);
+    else zpass2<T2, MODE, N1, N2, 1>(g, Y, Z, sc, tw, s);
+}
+// The two-pass kernel serves the 3/2-padded lengths N = 3 (K + 1) below; any
+// other length goes to the Stockham kernel.
 template <class T2, int MODE>
 static bool zpass2_any(const Geo& g, const T2* Y, T2* Z, const ZScales& sc, const T2* tw, cudaStream_t s) {
+    if (g.nzp != 3 * g.nk || g.K != g.nk - 1) return false;
     switch (g.nzp) {
-        case 96: zpass2<T2, MODE, 8, 12>(g, Y, Z, sc, tw, s); return true;
-        case 192: zpass2<T2, MODE, 16, 12>(g, Y, Z, sc, tw, s); return true;
-        case 384: zpass2<T2, MODE, 16, 24>(g, Y, Z, sc, tw, s); return true;
+        case 96: zpass2_rows<T2, MODE, 8, 12>(g, Y, Z, sc, tw, s); return true;
+        case 192: zpass2_rows<T2, MODE, 16, 12>(g, Y, Z, sc, tw, s); return true;
+        case 384: zpass2_rows<T2, MODE, 16, 24>(g, Y, Z, sc, tw, s); return true;
         default: return false;
     }
 }
@@ -770,7 +825,7 @@ static void zpass_stockham(const Geo& g, const T2* Y, T2* Z, const ZScales& sc, 
     constexpr int LD = MODE == ZFWD ? 3 : (MODE == ZADJ ? 5 : 9);
     const size_t sm = (size_t)(2 * g.nzp * LD + g.nzp) * sizeof(T2);
     smem_limit((const void*)k_zpass<T2, MODE>);
-    k_zpass<T2, MODE><<<dim3(g.nt, g.nr, g.nb), zpass_threads(g), sm, s>>>(g, Y, Z, sc, tw);
+    launch_pdl(k_zpass<T2, MODE>, dim3(g.nt, g.nr, g.nb), zpass_threads(g), sm, s, g, Y, Z, sc, tw);
 }
 
 template <class T2>
