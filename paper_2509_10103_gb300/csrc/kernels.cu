@@ -87,7 +87,13 @@ __device__ __forceinline__ double2 band_col(const Geo& g, const double* B0, cons
     return acc;
 }
 
-__global__ void k_curl(Geo g, const double2* __restrict__ u, double2* __restrict__ w) {
+// vorticity output in FP64, or in FP32 for the mixed-precision transforms,
+// which consume it only after rounding to FP32
+__device__ __forceinline__ void put_w(double2* p, double2 v) { *p = v; }
+__device__ __forceinline__ void put_w(float2* p, double2 v) { *p = make_float2((float)v.x, (float)v.y); }
+
+template <class W2>
+__global__ void k_curl(Geo g, const double2* __restrict__ u, W2* __restrict__ w) {
     grid_dep_sync();
     Idx d;
     if (!decode(g, d)) return;
@@ -99,9 +105,9 @@ __global__ void k_curl(Geo g, const double2* __restrict__ u, double2* __restrict
     const double2 dz = band_row(g, g.D1 + ((size_t)par_idx(d.m) * g.nr + d.j) * kB, uz, d.j, d.im, d.k);
     const double2 dt = band_row(g, g.D1 + ((size_t)par_idx(d.m + 1) * g.nr + d.j) * kB, ut, d.j, d.im, d.k);
     const double2 a = ur[o], b = ut[o], c = uz[o];
-    w[o] = make_double2(-mr * c.y + kz * b.y, mr * c.x - kz * b.x);
-    w[o + d.S] = make_double2(-kz * a.y - dz.x, kz * a.x - dz.y);
-    w[o + 2 * d.S] = make_double2(dt.x + ir * b.x + mr * a.y, dt.y + ir * b.y - mr * a.x);
+    put_w(w + o, make_double2(-mr * c.y + kz * b.y, mr * c.x - kz * b.x));
+    put_w(w + o + d.S, make_double2(-kz * a.y - dz.x, kz * a.x - dz.y));
+    put_w(w + o + 2 * d.S, make_double2(dt.x + ir * b.x + mr * a.y, dt.y + ir * b.y - mr * a.x));
 }
 
 __global__ void k_curlT_acc(Geo g, const double2* __restrict__ wb, double2* __restrict__ ub) {
@@ -334,8 +340,12 @@ __device__ __forceinline__ dacc2 band_col_t(const Geo& g, const float2* B0, cons
     return a;
 }
 __device__ __forceinline__ double2 df_out(const dacc2& a) { return make_double2(df_result(a.re), df_result(a.im)); }
+// the accumulated value rounded once to FP32 (s + c is the rounding of the pair)
+__device__ __forceinline__ void df_put(double2* p, const dacc2& a) { *p = df_out(a); }
+__device__ __forceinline__ void df_put(float2* p, const dacc2& a) { *p = make_float2(a.re.s + a.re.c, a.im.s + a.im.c); }
 
-__global__ void __launch_bounds__(kTK* kTG) k_curl_df(Geo g, const double2* __restrict__ u, double2* __restrict__ w) {
+template <class W2>
+__global__ void __launch_bounds__(kTK* kTG) k_curl_df(Geo g, const double2* __restrict__ u, W2* __restrict__ w) {
     grid_dep_sync();
     __shared__ DfTile tz, tt;
     const TBlk t = tdecode(g);
@@ -366,9 +376,9 @@ __global__ void __launch_bounds__(kTK* kTG) k_curl_df(Geo g, const double2* __re
         df_fma(wz.re, mr, a.im);
         df_fma(wz.im, ir, b.im);
         df_fma(wz.im, df_neg(mr), a.re);
-        w[o] = df_out(wr);
-        w[o + t.S] = df_out(wt);
-        w[o + 2 * t.S] = df_out(wz);
+        df_put(w + o, wr);
+        df_put(w + o + t.S, wt);
+        df_put(w + o + 2 * t.S, wz);
     }
 }
 
@@ -1708,11 +1718,13 @@ static void single_only(const Geo& g, const char* what) {
         throw std::runtime_error(std::string(what) + ": not available on batched launches");
 }
 
-void launch_curl(const Geo& g, const double2* u, double2* w, cudaStream_t s) {
-    if (g.df) launch_pdl(k_curl_df, tile_grid(g), tile_block(), 0, s, g, u, w);
-    else launch_pdl(k_curl, spec_grid(g), spec_bx(g), 0, s, g, u, w);
+template <class W2> static void curl_any(const Geo& g, const double2* u, W2* w, cudaStream_t s) {
+    if (g.df) launch_pdl(k_curl_df<W2>, tile_grid(g), tile_block(), 0, s, g, u, w);
+    else launch_pdl(k_curl<W2>, spec_grid(g), spec_bx(g), 0, s, g, u, w);
     check_launch("curl");
 }
+void launch_curl(const Geo& g, const double2* u, double2* w, cudaStream_t s) { curl_any(g, u, w, s); }
+void launch_curl_f32(const Geo& g, const double2* u, float2* w, cudaStream_t s) { curl_any(g, u, w, s); }
 void launch_curlT_acc(const Geo& g, const double2* wb, double2* ub, cudaStream_t s) {
     if (g.df) launch_pdl(k_curlT_acc_df, tile_grid(g), tile_block(), 0, s, g, wb, ub);
     else launch_pdl(k_curlT_acc, spec_grid(g), spec_bx(g), 0, s, g, wb, ub);

@@ -470,7 +470,10 @@ void transforms(pnop_ctx* c, const pnop::FieldPtrs& f, int nin, int nout, int zm
     const double cols = (double)g.nr * g.nk, rows = (double)g.nr * g.nt;
     const int zk = zmode == pnop::ZFWD ? PNOP_K_ZPASS_FWD : PNOP_K_ZPASS_ADJ;
     pnop::FieldPtrs fs = f;
-    for (int i = 0; i + cached < nin; ++i) fs.in[i] = f.in[cached + i];
+    for (int i = 0; i + cached < nin; ++i) {
+        fs.in[i] = f.in[cached + i];
+        fs.inf[i] = f.inf[cached + i];
+    }
     const int ns = nin - cached;
     const size_t plane = (size_t)g.nr * g.nt * g.nk;
     if (mixed(c)) {
@@ -516,6 +519,23 @@ void queue_base(pnop_ctx* c, const double2* u, double t) {
     ck(cudaEventRecord(c->ev_base, c->side), "record");
 }
 
+// w = curl u into the context's vorticity buffer, which becomes transform
+// inputs first..first+2: stored in FP32 when the transforms run in FP32 (they
+// are its only reader, and take it rounded to FP32 anyway), in FP64 otherwise.
+void curl_into(pnop_ctx* c, const double2* u, pnop::FieldPtrs& f, int first) {
+    const Geo& g = c->geo;
+    const size_t S = c->S();
+    cudaStream_t s = c->stream;
+    if (mixed(c)) {
+        float2* w = reinterpret_cast<float2*>(c->omega);
+        run(c, PNOP_K_SPECTRAL, 1, flops::curl * S, [&] { pnop::launch_curl_f32(g, u, w, s); });
+        for (int i = 0; i < 3; ++i) f.inf[first + i] = w + i * S;
+    } else {
+        run(c, PNOP_K_SPECTRAL, 1, flops::curl * S, [&] { pnop::launch_curl(g, u, c->omega, s); });
+        for (int i = 0; i < 3; ++i) f.in[first + i] = c->omega + i * S;
+    }
+}
+
 // N = P[I(u) x I(w)] - U du/dz - u_r dU/dr e_z, w = curl u  (Eq. 2.5; base-flow
 // terms in advective form, computed on the side stream while the curl and the
 // transforms run).  The physical u and w are left in Y (fields 0..5).  With
@@ -529,11 +549,10 @@ void nonlinear(pnop_ctx* c, const double2* u, double t, double2* N, void* Y, boo
         fork_side(c);
         queue_base(c, u, t);
     }
-    run(c, PNOP_K_SPECTRAL, 1, flops::curl * S, [&] { pnop::launch_curl(g, u, c->omega, s); });
     pnop::FieldPtrs f{};
+    curl_into(c, u, f, 3);
     for (int i = 0; i < 3; ++i) {
         f.in[i] = u + i * S;
-        f.in[3 + i] = c->omega + i * S;
         f.out[i] = N + i * S;
         f.add[i] = c->Nbase + i * S;
     }
@@ -556,11 +575,10 @@ void nonlinearT(pnop_ctx* c, const double2* u, double t, const double2* nb, doub
     set_phase(c, t);
     run(c, PNOP_K_SPECTRAL, 1, flops::base * S, [&] { pnop::launch_baseT(g, nb, c->Nbase, c->side); }, c->side);
     ck(cudaEventRecord(c->ev_base, c->side), "record");
-    if (!cached) run(c, PNOP_K_SPECTRAL, 1, flops::curl * S, [&] { pnop::launch_curl(g, u, c->omega, s); });
     pnop::FieldPtrs f{};
+    if (!cached) curl_into(c, u, f, 3);
     for (int i = 0; i < 3; ++i) {
         f.in[i] = u + i * S;
-        f.in[3 + i] = c->omega + i * S;
         f.in[6 + i] = nb + i * S;
         f.out[i] = ub + i * S;
         f.out[3 + i] = c->wb + i * S;
@@ -609,12 +627,11 @@ void nonlinear_adj(pnop_ctx* c, const double2* w, const double2* u, double t, do
         fork_side(c);
         queue_base_adj(c, w, t);
     }
-    run(c, PNOP_K_SPECTRAL, 1, flops::curl * S, [&] { pnop::launch_curl(g, w, c->omega, s); });
-    run(c, PNOP_K_SPECTRAL, 1, flops::grad_u * S, [&] { pnop::launch_grad_u(g, u, c->Gu, s); });
     pnop::FieldPtrs f{};
+    curl_into(c, w, f, 3);
+    run(c, PNOP_K_SPECTRAL, 1, flops::grad_u * S, [&] { pnop::launch_grad_u(g, u, c->Gu, s); });
     for (int i = 0; i < 3; ++i) {
         f.in[i] = u + i * S;
-        f.in[3 + i] = c->omega + i * S;
         f.in[6 + i] = w + i * S;
         f.out[i] = N + i * S;
         f.add[i] = c->Nbase + i * S;

@@ -113,6 +113,16 @@ __device__ T2* fft_cols(T2* a, T2* b, int N, const T2* tw) {
     return a;
 }
 
+// spectral input value of a synthesis: fields stored in FP32 (FieldPtrs::inf)
+// are read as they are, FP64 fields converted to the transform precision
+template <class T2> __device__ __forceinline__ T2 from_f(float2 v);
+template <> __device__ __forceinline__ float2 from_f<float2>(float2 v) { return v; }
+template <> __device__ __forceinline__ double2 from_f<double2>(float2 v) { return to_d(v); }
+template <class T2>
+__device__ __forceinline__ T2 synth_in(const double2* src, const float2* srcf, size_t i) {
+    return srcf ? from_f<T2>(srcf[i]) : from_d<T2>(src[i]);
+}
+
 // ------------------------------------------------------------------ theta synthesis
 // Y[f][j][a][k] = sum_m X_f[j][m][k] e^{i m theta_a}   (zero-padded to nt points)
 template <class T2, int KB>
@@ -129,13 +139,15 @@ __global__ void k_synth_theta(Geo g, FieldPtrs f, T2* __restrict__ Y, const T2* 
     for (int i = threadIdx.x; i < g.nt; i += blockDim.x) tw[i] = twg[i];
     for (int i = threadIdx.x; i < g.nt * KB; i += blockDim.x) buf0[i] = mk<T2>(0, 0);
     __syncthreads();
-    const double2* src = f.in[fi] + (size_t)slot * g.fs + (size_t)j * g.nm * g.nk;
+    const size_t base = (size_t)slot * g.fs + (size_t)j * g.nm * g.nk;
+    const float2* srcf = f.inf[fi] ? f.inf[fi] + base : nullptr;
+    const double2* src = srcf ? nullptr : f.in[fi] + base;
     for (int i = threadIdx.x; i < g.nm * KB; i += blockDim.x) {
         const int im = i / KB, kk = i % KB;
         if (kk < kw) {
             const int m = im - g.M;
             const int a = m < 0 ? m + g.nt : m;
-            buf0[a * KB + kk] = from_d<T2>(src[(size_t)im * g.nk + k0 + kk]);
+            buf0[a * KB + kk] = synth_in<T2>(src, srcf, (size_t)im * g.nk + k0 + kk);
         }
     }
     __syncthreads();
@@ -427,39 +439,64 @@ __device__ __forceinline__ void rdft(T2 (&v)[L]) {
     }
 }
 
-// theta synthesis, two-pass: block (k tile of KB, j, field), KB * N1 or
-// KB * N2 tasks per pass.  Slot s of the output rows holds theta index
-// (s / N2) + N1 (s % N2).
+// theta synthesis, two-pass: block (k tile of KB, j, field) of kT2 threads,
+// KB * N1 or KB * N2 tasks per pass.  Slot s of the output rows holds theta
+// index (s / N2) + N1 (s % N2).  The task counts are multiples of the block
+// size, so each thread runs a fixed number of tasks; where their inputs fit
+// in registers (at most 24 values) it loads all of them before the first DFT,
+// so that one memory latency is exposed per pass instead of one per task.
+constexpr int kT2 = 128;
 template <class T2, int KB, int N1, int N2>
-__global__ void __launch_bounds__(128) k_synth2(Geo g, FieldPtrs f, T2* __restrict__ Y, const T2* __restrict__ twg) {
+__global__ void __launch_bounds__(kT2) k_synth2(Geo g, FieldPtrs f, T2* __restrict__ Y, const T2* __restrict__ twg) {
     grid_dep_sync();
-    constexpr int N = N1 * N2;
+    constexpr int N = N1 * N2, IT1 = KB * N2 / kT2, IT2 = KB * N1 / kT2;
+    static_assert(KB * N2 % kT2 == 0 && KB * N1 % kT2 == 0, "whole tasks per thread");
     extern __shared__ __align__(16) unsigned char smem[];
     T2* buf = reinterpret_cast<T2*>(smem);  // [N][KB]
     T2* tw = buf + N * KB;                   // [N]
     const int k0 = blockIdx.x * KB, j = blockIdx.y;
     const int nf = gridDim.z / g.nb, b = blockIdx.z / nf, fi = blockIdx.z - b * nf, slot = g.slot[b];
     Y += (size_t)slot * g.ps;
-    for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = twg[i];
-    __syncthreads();
-    const double2* src = f.in[fi] + (size_t)slot * g.fs + (size_t)j * g.nm * g.nk;
-    for (int t = threadIdx.x; t < KB * N2; t += blockDim.x) {
-        const int kk = t % KB, n2 = t / KB, k = k0 + kk;
-        T2 v[N1];
+    for (int i = threadIdx.x; i < N; i += kT2) tw[i] = twg[i];
+    const size_t base = (size_t)slot * g.fs + (size_t)j * g.nm * g.nk;
+    const float2* srcf = f.inf[fi] ? f.inf[fi] + base : nullptr;
+    const double2* src = srcf ? nullptr : f.in[fi] + base;
+    auto load = [&](int it, T2 (&v)[N1]) {
+        const int t = threadIdx.x + it * kT2, kk = t % KB, n2 = t / KB, k = k0 + kk;
 #pragma unroll
         for (int n1 = 0; n1 < N1; ++n1) {
             const int n = n2 + N2 * n1;  // m mod N; zero padding for |m| > M
             const int m = n <= g.M ? n : n - N;
-            v[n1] = (k < g.nk && m >= -g.M) ? from_d<T2>(src[(size_t)(m + g.M) * g.nk + k]) : mk<T2>(0, 0);
+            v[n1] = (k < g.nk && m >= -g.M) ? synth_in<T2>(src, srcf, (size_t)(m + g.M) * g.nk + k) : mk<T2>(0, 0);
         }
+    };
+    auto dft1 = [&](int it, T2 (&v)[N1]) {
+        const int t = threadIdx.x + it * kT2, kk = t % KB, n2 = t / KB;
         rdft<T2, N1, +1>(v);
 #pragma unroll
         for (int k1 = 0; k1 < N1; ++k1) buf[(n2 + N2 * k1) * KB + kk] = twr<T2, +1>(v[k1], tw, n2 * k1);
+    };
+    if constexpr (IT1 * N1 <= 24) {
+        T2 v[IT1][N1];
+#pragma unroll
+        for (int it = 0; it < IT1; ++it) load(it, v[it]);
+        __syncthreads();  // twiddles
+#pragma unroll
+        for (int it = 0; it < IT1; ++it) dft1(it, v[it]);
+    } else {
+        __syncthreads();  // twiddles
+#pragma unroll 1
+        for (int it = 0; it < IT1; ++it) {
+            T2 v[N1];
+            load(it, v);
+            dft1(it, v);
+        }
     }
     __syncthreads();
     T2* dst = Y + ((size_t)(fi * g.nr + j) * N) * g.nk;
-    for (int t = threadIdx.x; t < KB * N1; t += blockDim.x) {
-        const int kk = t % KB, k1 = t / KB, k = k0 + kk;
+#pragma unroll
+    for (int it = 0; it < IT2; ++it) {
+        const int t = threadIdx.x + it * kT2, kk = t % KB, k1 = t / KB, k = k0 + kk;
         T2 v[N2];
 #pragma unroll
         for (int n2 = 0; n2 < N2; ++n2) v[n2] = buf[(N2 * k1 + n2) * KB + kk];
@@ -472,12 +509,16 @@ __global__ void __launch_bounds__(128) k_synth2(Geo g, FieldPtrs f, T2* __restri
 }
 
 // theta analysis, two-pass (input rows in the slot order of k_synth2), with
-// the k = 0 plane projected onto Hermitian symmetry.
+// the k = 0 plane projected onto Hermitian symmetry.  Same thread layout as
+// k_synth2; the first pass loads all its inputs before its DFTs where they
+// fit in registers, and each task of the second pass loads the values to add
+// (the base-flow terms) before its DFT.
 template <class T2, int KB, int N1, int N2>
-__global__ void __launch_bounds__(128) k_anal2(Geo g, FieldPtrs f, const T2* __restrict__ Z,
+__global__ void __launch_bounds__(kT2, 6) k_anal2(Geo g, FieldPtrs f, const T2* __restrict__ Z,
                                                const T2* __restrict__ twg) {
     grid_dep_sync();
-    constexpr int N = N1 * N2;
+    constexpr int N = N1 * N2, IT1 = KB * N1 / kT2, IT2 = KB * N2 / kT2;
+    static_assert(KB * N2 % kT2 == 0 && KB * N1 % kT2 == 0, "whole tasks per thread");
     extern __shared__ __align__(16) unsigned char smem[];
     T2* buf = reinterpret_cast<T2*>(smem);  // [N][KB]
     T2* tw = buf + N * KB;                   // [N]
@@ -485,23 +526,52 @@ __global__ void __launch_bounds__(128) k_anal2(Geo g, FieldPtrs f, const T2* __r
     const int nf = gridDim.z / g.nb, b = blockIdx.z / nf, fi = blockIdx.z - b * nf, slot = g.slot[b];
     const size_t off = (size_t)slot * g.fs;
     Z += (size_t)slot * g.ps;
-    for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = twg[i];
-    __syncthreads();
+    for (int i = threadIdx.x; i < N; i += kT2) tw[i] = twg[i];
     const T2* src = Z + ((size_t)(fi * g.nr + j) * N) * g.nk;
-    for (int t = threadIdx.x; t < KB * N1; t += blockDim.x) {
-        const int kk = t % KB, k1 = t / KB, k = k0 + kk;
-        T2 v[N2];
+    auto load = [&](int it, T2 (&v)[N2]) {
+        const int t = threadIdx.x + it * kT2, kk = t % KB, k1 = t / KB, k = k0 + kk;
 #pragma unroll
         for (int n2 = 0; n2 < N2; ++n2) v[n2] = k < g.nk ? src[(size_t)(N2 * k1 + n2) * g.nk + k] : mk<T2>(0, 0);
+    };
+    auto dft1 = [&](int it, T2 (&v)[N2]) {
+        const int t = threadIdx.x + it * kT2, kk = t % KB, k1 = t / KB;
         rdft<T2, N2, -1>(v);
 #pragma unroll
         for (int m2 = 0; m2 < N2; ++m2) buf[(N2 * k1 + m2) * KB + kk] = twr<T2, -1>(v[m2], tw, k1 * m2);
+    };
+    if constexpr (IT1 * N2 <= 24) {
+        T2 v[IT1][N2];
+#pragma unroll
+        for (int it = 0; it < IT1; ++it) load(it, v[it]);
+        __syncthreads();  // twiddles
+#pragma unroll
+        for (int it = 0; it < IT1; ++it) dft1(it, v[it]);
+    } else {
+        __syncthreads();  // twiddles
+#pragma unroll 1
+        for (int it = 0; it < IT1; ++it) {
+            T2 v[N2];
+            load(it, v);
+            dft1(it, v);
+        }
     }
     __syncthreads();
     double2* dst = f.out[fi] + off + (size_t)j * g.nm * g.nk;
     const double2* add = f.add[fi] ? f.add[fi] + off + (size_t)j * g.nm * g.nk : nullptr;
-    for (int t = threadIdx.x; t < KB * N2; t += blockDim.x) {
-        const int kk = t % KB, m2 = t / KB, k = k0 + kk;
+#pragma unroll 1
+    for (int it = 0; it < IT2; ++it) {
+        const int t = threadIdx.x + it * kT2, kk = t % KB, m2 = t / KB, k = k0 + kk;
+        constexpr bool kEarly = N1 <= 8;  // the added values of larger tasks do not fit in registers
+        double2 ad[kEarly ? N1 : 1];
+        if constexpr (kEarly) {
+#pragma unroll
+            for (int m1 = 0; m1 < N1; ++m1) {
+                const int n = m2 + N2 * m1;
+                const int m = n <= g.M ? n : n - N;
+                ad[m1] = (add && k > 0 && k < g.nk && m >= -g.M) ? add[(size_t)(m + g.M) * g.nk + k]
+                                                                  : make_double2(0, 0);
+            }
+        }
         T2 v[N1];
 #pragma unroll
         for (int k1 = 0; k1 < N1; ++k1) v[k1] = buf[(m2 + N2 * k1) * KB + kk];
@@ -516,7 +586,10 @@ __global__ void __launch_bounds__(128) k_anal2(Geo g, FieldPtrs f, const T2* __r
                 } else {
                     const size_t o = (size_t)(m + g.M) * g.nk + k;
                     double2 x = to_d(v[m1]);
-                    if (add) x = make_double2(x.x + add[o].x, x.y + add[o].y);
+                    if (add) {
+                        const double2 a = kEarly ? ad[kEarly ? m1 : 0] : add[o];
+                        x = make_double2(x.x + a.x, x.y + a.y);
+                    }
                     dst[o] = x;
                 }
             }
@@ -735,14 +808,14 @@ static void synth2(const Geo& g, const FieldPtrs& f, int nfield, T2* Y, const T2
     const size_t sm = (size_t)(N1 * N2 * KB + N1 * N2) * sizeof(T2);
     smem_limit((const void*)k_synth2<T2, KB, N1, N2>);
     dim3 grid((g.nk + KB - 1) / KB, g.nr, nfield * g.nb);
-    launch_pdl(k_synth2<T2, KB, N1, N2>, grid, 128, sm, s, g, f, Y, tw);
+    launch_pdl(k_synth2<T2, KB, N1, N2>, grid, kT2, sm, s, g, f, Y, tw);
 }
 template <class T2, int KB, int N1, int N2>
 static void anal2(const Geo& g, const FieldPtrs& f, int nfield, const T2* Z, const T2* tw, cudaStream_t s) {
     const size_t sm = (size_t)(N1 * N2 * KB + N1 * N2) * sizeof(T2);
     smem_limit((const void*)k_anal2<T2, KB, N1, N2>);
     dim3 grid((g.nk + KB - 1) / KB, g.nr, nfield * g.nb);
-    launch_pdl(k_anal2<T2, KB, N1, N2>, grid, 128, sm, s, g, f, Z, tw);
+    launch_pdl(k_anal2<T2, KB, N1, N2>, grid, kT2, sm, s, g, f, Z, tw);
 }
 
 template <class T2>
