@@ -69,19 +69,23 @@ __device__ __forceinline__ double2 band_row(const Geo& g, const double* B, const
 // Transposed banded product (B^T x)_j = sum_{j'} B[j'][j - j' + 4] x[j'].
 // Column j > 8 is reached only from rows j-4..j+4; columns 0..8 also from the
 // wall rows 0..3.
-__device__ __forceinline__ double2 band_col(const Geo& g, const double* B0, const double2* x, int j, int im, int k) {
+__device__ __forceinline__ double2 ldd(const double2* p) { return *p; }
+__device__ __forceinline__ double2 ldd(const float2* p) { return to_d(*p); }  // exact
+template <class X2>
+__device__ __forceinline__ double2 band_col(const Geo& g, const double* B0, const X2* x, int j, int im, int k) {
     double2 acc = make_double2(0, 0);
     if (j > 8) {
 #pragma unroll
         for (int t = -4; t <= 4; ++t) {
             const int c = j + t;
-            if (c < g.nr) acc = dfma(__ldg(B0 + (size_t)c * kB + (4 - t)), x[sidx(g, c, im, k)], acc);
+            if (c < g.nr) acc = dfma(__ldg(B0 + (size_t)c * kB + (4 - t)), ldd(x + sidx(g, c, im, k)), acc);
         }
     } else {
 #pragma unroll
         for (int t = -8; t <= 4; ++t) {
             const int c = j + t;
-            if (c >= 0 && c < g.nr) acc = dfma(__ldg(B0 + (size_t)c * kB + (4 - t)), x[sidx(g, c, im, k)], acc);
+            if (c >= 0 && c < g.nr)
+                acc = dfma(__ldg(B0 + (size_t)c * kB + (4 - t)), ldd(x + sidx(g, c, im, k)), acc);
         }
     }
     return acc;
@@ -93,7 +97,7 @@ __device__ __forceinline__ void put_w(double2* p, double2 v) { *p = v; }
 __device__ __forceinline__ void put_w(float2* p, double2 v) { *p = make_float2((float)v.x, (float)v.y); }
 
 template <class W2>
-__global__ void k_curl(Geo g, const double2* __restrict__ u, W2* __restrict__ w) {
+__global__ void k_curl(Geo g, const double2* __restrict__ u, W2* __restrict__ w, float2* __restrict__ uf) {
     grid_dep_sync();
     Idx d;
     if (!decode(g, d)) return;
@@ -105,23 +109,30 @@ __global__ void k_curl(Geo g, const double2* __restrict__ u, W2* __restrict__ w)
     const double2 dz = band_row(g, g.D1 + ((size_t)par_idx(d.m) * g.nr + d.j) * kB, uz, d.j, d.im, d.k);
     const double2 dt = band_row(g, g.D1 + ((size_t)par_idx(d.m + 1) * g.nr + d.j) * kB, ut, d.j, d.im, d.k);
     const double2 a = ur[o], b = ut[o], c = uz[o];
+    if (uf) {  // u itself rounded to FP32, for the same transforms
+        uf += d.off;
+        put_w(uf + o, a);
+        put_w(uf + o + d.S, b);
+        put_w(uf + o + 2 * d.S, c);
+    }
     put_w(w + o, make_double2(-mr * c.y + kz * b.y, mr * c.x - kz * b.x));
     put_w(w + o + d.S, make_double2(-kz * a.y - dz.x, kz * a.x - dz.y));
     put_w(w + o + 2 * d.S, make_double2(dt.x + ir * b.x + mr * a.y, dt.y + ir * b.y - mr * a.x));
 }
 
-__global__ void k_curlT_acc(Geo g, const double2* __restrict__ wb, double2* __restrict__ ub) {
+template <class WB2>
+__global__ void k_curlT_acc(Geo g, const WB2* __restrict__ wb, double2* __restrict__ ub) {
     grid_dep_sync();
     Idx d;
     if (!decode(g, d)) return;
     wb += d.off;
     ub += d.off;
-    const double2 *wr = wb, *wt = wb + d.S, *wz = wb + 2 * d.S;
+    const WB2 *wr = wb, *wt = wb + d.S, *wz = wb + 2 * d.S;
     const double kz = __ldg(g.kzt + d.k), ir = g.invr[d.j], mr = __ldg(g.mrt + (size_t)d.im * g.nr + d.j);
     const size_t o = sidx(g, d.j, d.im, d.k);
     const double2 sT = band_col(g, g.D1 + (size_t)par_idx(d.m + 1) * g.nr * kB, wz, d.j, d.im, d.k);
     const double2 sP = band_col(g, g.D1 + (size_t)par_idx(d.m) * g.nr * kB, wt, d.j, d.im, d.k);
-    const double2 a = wr[o], b = wt[o], c = wz[o];
+    const double2 a = ldd(wr + o), b = ldd(wt + o), c = ldd(wz + o);
     double2 x = ub[o];
     ub[o] = make_double2(x.x + kz * b.y - mr * c.y, x.y - kz * b.x + mr * c.x);
     x = ub[o + d.S];
@@ -294,6 +305,26 @@ __device__ __forceinline__ void tile_load(const Geo& g, const TBlk& t, const dou
         tl[r - t.lo][threadIdx.x] = v;
     }
 }
+// an FP32 field is a pair with a zero low part: no splitting
+__device__ __forceinline__ void tile_load(const Geo& g, const TBlk& t, const float2* f, DfTile& tl) {
+    for (int r = t.lo + (int)threadIdx.y; r < t.hi; r += kTG) {
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (t.on) {
+            const float2 x = f[sidx(g, r, t.im, t.k)];
+            v = make_float4(x.x, 0.f, x.y, 0.f);
+        }
+        tl[r - t.lo][threadIdx.x] = v;
+    }
+}
+__device__ __forceinline__ dfc df_load(const float2* p) {
+    const float2 v = *p;
+    dfc r;
+    r.re.h = v.x;
+    r.re.l = 0.f;
+    r.im.h = v.y;
+    r.im.l = 0.f;
+    return r;
+}
 __device__ __forceinline__ dfc tile_at(const DfTile& tl, int lo, int r) {
     const float4 v = tl[r - lo][threadIdx.x];
     dfc x;
@@ -344,8 +375,12 @@ __device__ __forceinline__ double2 df_out(const dacc2& a) { return make_double2(
 __device__ __forceinline__ void df_put(double2* p, const dacc2& a) { *p = df_out(a); }
 __device__ __forceinline__ void df_put(float2* p, const dacc2& a) { *p = make_float2(a.re.s + a.re.c, a.im.s + a.im.c); }
 
+// the pair rounded once to FP32
+__device__ __forceinline__ float2 df_f32(const dfc& x) { return make_float2(x.re.h + x.re.l, x.im.h + x.im.l); }
+
 template <class W2>
-__global__ void __launch_bounds__(kTK* kTG) k_curl_df(Geo g, const double2* __restrict__ u, W2* __restrict__ w) {
+__global__ void __launch_bounds__(kTK* kTG) k_curl_df(Geo g, const double2* __restrict__ u, W2* __restrict__ w,
+                                                      float2* __restrict__ uf) {
     grid_dep_sync();
     __shared__ DfTile tz, tt;
     const TBlk t = tdecode(g);
@@ -379,17 +414,23 @@ __global__ void __launch_bounds__(kTK* kTG) k_curl_df(Geo g, const double2* __re
         df_put(w + o, wr);
         df_put(w + o + t.S, wt);
         df_put(w + o + 2 * t.S, wz);
+        if (uf) {  // u itself rounded to FP32, for the same transforms
+            uf[t.off + o] = df_f32(a);
+            uf[t.off + o + t.S] = df_f32(b);
+            uf[t.off + o + 2 * t.S] = df_f32(c);
+        }
     }
 }
 
-__global__ void __launch_bounds__(kTK* kTG) k_curlT_acc_df(Geo g, const double2* __restrict__ wb,
+template <class WB2>
+__global__ void __launch_bounds__(kTK* kTG) k_curlT_acc_df(Geo g, const WB2* __restrict__ wb,
                                                          double2* __restrict__ ub) {
     grid_dep_sync();
     __shared__ DfTile tz, tt;
     const TBlk t = tdecode(g);
     wb += t.off;
     ub += t.off;
-    const double2 *wr = wb, *wt = wb + t.S, *wz = wb + 2 * t.S;
+    const WB2 *wr = wb, *wt = wb + t.S, *wz = wb + 2 * t.S;
     tile_load(g, t, wz, tz);
     tile_load(g, t, wt, tt);
     __syncthreads();
@@ -1718,18 +1759,22 @@ static void single_only(const Geo& g, const char* what) {
         throw std::runtime_error(std::string(what) + ": not available on batched launches");
 }
 
-template <class W2> static void curl_any(const Geo& g, const double2* u, W2* w, cudaStream_t s) {
-    if (g.df) launch_pdl(k_curl_df<W2>, tile_grid(g), tile_block(), 0, s, g, u, w);
-    else launch_pdl(k_curl<W2>, spec_grid(g), spec_bx(g), 0, s, g, u, w);
+template <class W2> static void curl_any(const Geo& g, const double2* u, W2* w, float2* uf, cudaStream_t s) {
+    if (g.df) launch_pdl(k_curl_df<W2>, tile_grid(g), tile_block(), 0, s, g, u, w, uf);
+    else launch_pdl(k_curl<W2>, spec_grid(g), spec_bx(g), 0, s, g, u, w, uf);
     check_launch("curl");
 }
-void launch_curl(const Geo& g, const double2* u, double2* w, cudaStream_t s) { curl_any(g, u, w, s); }
-void launch_curl_f32(const Geo& g, const double2* u, float2* w, cudaStream_t s) { curl_any(g, u, w, s); }
-void launch_curlT_acc(const Geo& g, const double2* wb, double2* ub, cudaStream_t s) {
-    if (g.df) launch_pdl(k_curlT_acc_df, tile_grid(g), tile_block(), 0, s, g, wb, ub);
-    else launch_pdl(k_curlT_acc, spec_grid(g), spec_bx(g), 0, s, g, wb, ub);
+void launch_curl(const Geo& g, const double2* u, double2* w, cudaStream_t s) { curl_any(g, u, w, nullptr, s); }
+void launch_curl_f32(const Geo& g, const double2* u, float2* w, float2* uf, cudaStream_t s) {
+    curl_any(g, u, w, uf, s);
+}
+template <class WB2> static void curlT_any(const Geo& g, const WB2* wb, double2* ub, cudaStream_t s) {
+    if (g.df) launch_pdl(k_curlT_acc_df<WB2>, tile_grid(g), tile_block(), 0, s, g, wb, ub);
+    else launch_pdl(k_curlT_acc<WB2>, spec_grid(g), spec_bx(g), 0, s, g, wb, ub);
     check_launch("curlT");
 }
+void launch_curlT_acc(const Geo& g, const double2* wb, double2* ub, cudaStream_t s) { curlT_any(g, wb, ub, s); }
+void launch_curlT_acc_f32(const Geo& g, const float2* wb, double2* ub, cudaStream_t s) { curlT_any(g, wb, ub, s); }
 void launch_grad_u(const Geo& g, const double2* u, double2* G, cudaStream_t s) {
     single_only(g, "grad_u");
     launch_pdl(k_grad_u, spec_grid(g), spec_bx(g), 0, s, g, u, G);

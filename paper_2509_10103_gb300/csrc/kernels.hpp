@@ -70,6 +70,7 @@ struct FieldPtrs {
     const double2* in[kMaxIn];
     const float2* inf[kMaxIn];  // non-null: input field stored in FP32 (in[] unused)
     double2* out[6];
+    float2* outf[6];  // non-null: output written in FP32 (out[] unused, add[] must be null)
     const double2* add[6];
 };
 
@@ -96,9 +97,12 @@ enum ZMode { ZFWD = 0, ZADJ = 1, ZCADJ = 2 };
 
 // ---- spectral FP64 kernels ----
 void launch_curl(const Geo& g, const double2* u, double2* w, cudaStream_t s);
-// the same vorticity rounded to FP32 (input of the mixed-precision transforms)
-void launch_curl_f32(const Geo& g, const double2* u, float2* w, cudaStream_t s);
+// the same vorticity rounded to FP32 (input of the mixed-precision
+// transforms), and u itself rounded to FP32 into uf when uf is not null
+void launch_curl_f32(const Geo& g, const double2* u, float2* w, float2* uf, cudaStream_t s);
 void launch_curlT_acc(const Geo& g, const double2* wb, double2* ub, cudaStream_t s);
+// the same with wb stored in FP32
+void launch_curlT_acc_f32(const Geo& g, const float2* wb, double2* ub, cudaStream_t s);
 // continuous adjoint: G[3 i + j] = (grad u)_ij (9 component planes, i the
 // derivative direction), and the base-flow part of its forcing
 // Nb = U dw/dz - w_z dU/dr e_r (written)

@@ -520,19 +520,29 @@ void queue_base(pnop_ctx* c, const double2* u, double t) {
 }
 
 // w = curl u into the context's vorticity buffer, which becomes transform
-// inputs first..first+2: stored in FP32 when the transforms run in FP32 (they
-// are its only reader, and take it rounded to FP32 anyway), in FP64 otherwise.
-void curl_into(pnop_ctx* c, const double2* u, pnop::FieldPtrs& f, int first) {
+// inputs first_w..first_w+2, and u itself inputs first_u..first_u+2.  When
+// the transforms run in FP32 (the vorticity's only reader, which takes it
+// rounded to FP32 anyway), w is stored in FP32 and the curl also writes u
+// rounded to FP32 into the buffer's second half, so that the synthesis reads
+// both without converting; in FP64 u is read where it is.
+void curl_into(pnop_ctx* c, const double2* u, pnop::FieldPtrs& f, int first_w, int first_u) {
     const Geo& g = c->geo;
     const size_t S = c->S();
     cudaStream_t s = c->stream;
     if (mixed(c)) {
-        float2* w = reinterpret_cast<float2*>(c->omega);
-        run(c, PNOP_K_SPECTRAL, 1, flops::curl * S, [&] { pnop::launch_curl_f32(g, u, w, s); });
-        for (int i = 0; i < 3; ++i) f.inf[first + i] = w + i * S;
+        float2* w = reinterpret_cast<float2*>(c->omega);  // 3 S values of 6 S float2 places
+        float2* uf = w + 3 * S;
+        run(c, PNOP_K_SPECTRAL, 1, flops::curl * S, [&] { pnop::launch_curl_f32(g, u, w, uf, s); });
+        for (int i = 0; i < 3; ++i) {
+            f.inf[first_w + i] = w + i * S;
+            f.inf[first_u + i] = uf + i * S;
+        }
     } else {
         run(c, PNOP_K_SPECTRAL, 1, flops::curl * S, [&] { pnop::launch_curl(g, u, c->omega, s); });
-        for (int i = 0; i < 3; ++i) f.in[first + i] = c->omega + i * S;
+        for (int i = 0; i < 3; ++i) {
+            f.in[first_w + i] = c->omega + i * S;
+            f.in[first_u + i] = u + i * S;
+        }
     }
 }
 
@@ -550,9 +560,8 @@ void nonlinear(pnop_ctx* c, const double2* u, double t, double2* N, void* Y, boo
         queue_base(c, u, t);
     }
     pnop::FieldPtrs f{};
-    curl_into(c, u, f, 3);
+    curl_into(c, u, f, 3, 0);
     for (int i = 0; i < 3; ++i) {
-        f.in[i] = u + i * S;
         f.out[i] = N + i * S;
         f.add[i] = c->Nbase + i * S;
     }
@@ -576,12 +585,15 @@ void nonlinearT(pnop_ctx* c, const double2* u, double t, const double2* nb, doub
     run(c, PNOP_K_SPECTRAL, 1, flops::base * S, [&] { pnop::launch_baseT(g, nb, c->Nbase, c->side); }, c->side);
     ck(cudaEventRecord(c->ev_base, c->side), "record");
     pnop::FieldPtrs f{};
-    if (!cached) curl_into(c, u, f, 3);
+    if (!cached) curl_into(c, u, f, 3, 0);
+    // the vorticity cotangent is a pure FP32 product in the mixed path (no
+    // FP64 term is added to it): the analysis writes it in FP32
+    float2* wbf = mixed(c) ? reinterpret_cast<float2*>(c->wb) : nullptr;
     for (int i = 0; i < 3; ++i) {
-        f.in[i] = u + i * S;
         f.in[6 + i] = nb + i * S;
         f.out[i] = ub + i * S;
-        f.out[3 + i] = c->wb + i * S;
+        if (wbf) f.outf[3 + i] = wbf + i * S;
+        else f.out[3 + i] = c->wb + i * S;
         f.add[i] = c->Nbase + i * S;
     }
     pnop::ZScales sc{};
@@ -598,7 +610,10 @@ void nonlinearT(pnop_ctx* c, const double2* u, double t, const double2* nb, doub
         sc.ok[i] = 2.0;
     }
     transforms(c, f, 9, 6, pnop::ZADJ, sc, Y, cached ? 6 : 0, c->ev_base);
-    run(c, PNOP_K_SPECTRAL, 1, flops::curlT * S, [&] { pnop::launch_curlT_acc(g, c->wb, ub, s); });
+    run(c, PNOP_K_SPECTRAL, 1, flops::curlT * S, [&] {
+        if (wbf) pnop::launch_curlT_acc_f32(g, wbf, ub, s);
+        else pnop::launch_curlT_acc(g, c->wb, ub, s);
+    });
 }
 
 // ------------------------------------------------------------------ continuous adjoint
@@ -628,11 +643,10 @@ void nonlinear_adj(pnop_ctx* c, const double2* w, const double2* u, double t, do
         queue_base_adj(c, w, t);
     }
     pnop::FieldPtrs f{};
-    curl_into(c, w, f, 3);
+    curl_into(c, w, f, 3, 6);
     run(c, PNOP_K_SPECTRAL, 1, flops::grad_u * S, [&] { pnop::launch_grad_u(g, u, c->Gu, s); });
     for (int i = 0; i < 3; ++i) {
         f.in[i] = u + i * S;
-        f.in[6 + i] = w + i * S;
         f.out[i] = N + i * S;
         f.add[i] = c->Nbase + i * S;
     }

@@ -118,6 +118,9 @@ __device__ T2* fft_cols(T2* a, T2* b, int N, const T2* tw) {
 template <class T2> __device__ __forceinline__ T2 from_f(float2 v);
 template <> __device__ __forceinline__ float2 from_f<float2>(float2 v) { return v; }
 template <> __device__ __forceinline__ double2 from_f<double2>(float2 v) { return to_d(v); }
+// an analysis result for an FP32 output field (FP64 transforms round it)
+__device__ __forceinline__ float2 to_f(float2 v) { return v; }
+__device__ __forceinline__ float2 to_f(double2 v) { return make_float2((float)v.x, (float)v.y); }
 template <class T2>
 __device__ __forceinline__ T2 synth_in(const double2* src, const float2* srcf, size_t i) {
     return srcf ? from_f<T2>(srcf[i]) : from_d<T2>(src[i]);
@@ -294,18 +297,30 @@ __global__ void k_anal_theta(Geo g, FieldPtrs f, const T2* __restrict__ Z, const
     }
     __syncthreads();
     T2* res = fft_cols<T2, KB, KB, -1>(buf0, buf1, g.nt, tw);
-    double2* dst = f.out[fi] + off + (size_t)j * g.nm * g.nk;
-    const double2* add = f.add[fi] ? f.add[fi] + off + (size_t)j * g.nm * g.nk : nullptr;
+    const size_t base = off + (size_t)j * g.nm * g.nk;
+    float2* dstf = f.outf[fi] ? f.outf[fi] + base : nullptr;
+    double2* dst = dstf ? nullptr : f.out[fi] + base;
+    const double2* add = f.add[fi] ? f.add[fi] + base : nullptr;
     for (int i = threadIdx.x; i < g.nm * KB; i += blockDim.x) {
         const int im = i / KB, kk = i % KB;
         if (kk >= kw) continue;
         const int m = im - g.M;
+        const size_t o = (size_t)im * g.nk + k0 + kk;
+        if (dstf) {
+            using T = typename RealOf<T2>::T;
+            T2 v = res[(m < 0 ? m + g.nt : m) * KB + kk];
+            if (k0 + kk == 0) {
+                const T2 vm = res[(m > 0 ? g.nt - m : -m) * KB + kk];
+                v = mk<T2>((T)0.5 * (v.x + vm.x), (T)0.5 * (v.y - vm.y));
+            }
+            dstf[o] = to_f(v);
+            continue;
+        }
         double2 v = to_d(res[(m < 0 ? m + g.nt : m) * KB + kk]);
         if (k0 + kk == 0) {
             double2 vm = to_d(res[(m > 0 ? g.nt - m : -m) * KB + kk]);
             v = make_double2(0.5 * (v.x + vm.x), 0.5 * (v.y - vm.y));
         }
-        const size_t o = (size_t)im * g.nk + k0 + kk;
         if (add) v = make_double2(v.x + add[o].x, v.y + add[o].y);
         dst[o] = v;
     }
@@ -556,8 +571,10 @@ __global__ void __launch_bounds__(kT2, 6) k_anal2(Geo g, FieldPtrs f, const T2* 
         }
     }
     __syncthreads();
-    double2* dst = f.out[fi] + off + (size_t)j * g.nm * g.nk;
-    const double2* add = f.add[fi] ? f.add[fi] + off + (size_t)j * g.nm * g.nk : nullptr;
+    const size_t base = off + (size_t)j * g.nm * g.nk;
+    float2* dstf = f.outf[fi] ? f.outf[fi] + base : nullptr;
+    double2* dst = dstf ? nullptr : f.out[fi] + base;
+    const double2* add = f.add[fi] ? f.add[fi] + base : nullptr;
 #pragma unroll 1
     for (int it = 0; it < IT2; ++it) {
         const int t = threadIdx.x + it * kT2, kk = t % KB, m2 = t / KB, k = k0 + kk;
@@ -583,6 +600,8 @@ __global__ void __launch_bounds__(kT2, 6) k_anal2(Geo g, FieldPtrs f, const T2* 
             if (k < g.nk && m >= -g.M) {
                 if (k == 0) {
                     buf[n * KB + kk] = v[m1];
+                } else if (dstf) {
+                    dstf[(size_t)(m + g.M) * g.nk + k] = to_f(v[m1]);
                 } else {
                     const size_t o = (size_t)(m + g.M) * g.nk + k;
                     double2 x = to_d(v[m1]);
@@ -599,6 +618,12 @@ __global__ void __launch_bounds__(kT2, 6) k_anal2(Geo g, FieldPtrs f, const T2* 
         __syncthreads();
         for (int im = threadIdx.x; im < g.nm; im += blockDim.x) {
             const int m = im - g.M;
+            if (dstf) {
+                using T = typename RealOf<T2>::T;
+                const T2 v = buf[(m < 0 ? m + N : m) * KB], vm = buf[(m > 0 ? N - m : -m) * KB];
+                dstf[(size_t)im * g.nk] = to_f(mk<T2>((T)0.5 * (v.x + vm.x), (T)0.5 * (v.y - vm.y)));
+                continue;
+            }
             const double2 v = to_d(buf[(m < 0 ? m + N : m) * KB]);
             const double2 vm = to_d(buf[(m > 0 ? N - m : -m) * KB]);
             double2 x = make_double2(0.5 * (v.x + vm.x), 0.5 * (v.y - vm.y));
