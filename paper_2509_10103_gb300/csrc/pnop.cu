@@ -523,15 +523,17 @@ void queue_base(pnop_ctx* c, const double2* u, double t) {
 // inputs first_w..first_w+2, and u itself inputs first_u..first_u+2.  When
 // the transforms run in FP32 (the vorticity's only reader, which takes it
 // rounded to FP32 anyway), w is stored in FP32 and the curl also writes u
-// rounded to FP32 into the buffer's second half, so that the synthesis reads
-// both without converting; in FP64 u is read where it is.
+// rounded to FP32, so that the synthesis reads both without converting; in
+// FP64 u is read where it is.  The buffer holds nslot slots of 3 S double2,
+// i.e. 6 S nslot float2; the kernels offset an FP32 field of slot s by
+// s * 3 S values, so w takes the first 3 S nslot float2 and u the rest.
 void curl_into(pnop_ctx* c, const double2* u, pnop::FieldPtrs& f, int first_w, int first_u) {
     const Geo& g = c->geo;
     const size_t S = c->S();
     cudaStream_t s = c->stream;
     if (mixed(c)) {
-        float2* w = reinterpret_cast<float2*>(c->omega);  // 3 S values of 6 S float2 places
-        float2* uf = w + 3 * S;
+        float2* w = reinterpret_cast<float2*>(c->omega);
+        float2* uf = w + (size_t)c->nslot * 3 * S;
         run(c, PNOP_K_SPECTRAL, 1, flops::curl * S, [&] { pnop::launch_curl_f32(g, u, w, uf, s); });
         for (int i = 0; i < 3; ++i) {
             f.inf[first_w + i] = w + i * S;
