@@ -295,25 +295,46 @@ __device__ __forceinline__ TBlk tdecode(const Geo& g) {
     return t;
 }
 typedef float4 DfTile[kTR][kTK];  // (re.hi, re.lo, im.hi, im.lo) per (row - lo, k)
-__device__ __forceinline__ void tile_load(const Geo& g, const TBlk& t, const double2* f, DfTile& tl) {
-    for (int r = t.lo + (int)threadIdx.y; r < t.hi; r += kTG) {
-        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (t.on) {
-            const dfc x = df_load(f + sidx(g, r, t.im, t.k));
-            v = make_float4(x.re.h, x.re.l, x.im.h, x.im.l);
-        }
-        tl[r - t.lo][threadIdx.x] = v;
-    }
+// a field value as a tile entry: FP64 values are split, an FP32 field is a
+// pair with a zero low part
+__device__ __forceinline__ float4 tile_entry(double2 v) {
+    const dfl re = df_split(v.x), im = df_split(v.y);
+    return make_float4(re.h, re.l, im.h, im.l);
 }
-// an FP32 field is a pair with a zero low part: no splitting
-__device__ __forceinline__ void tile_load(const Geo& g, const TBlk& t, const float2* f, DfTile& tl) {
-    for (int r = t.lo + (int)threadIdx.y; r < t.hi; r += kTG) {
-        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (t.on) {
-            const float2 x = f[sidx(g, r, t.im, t.k)];
-            v = make_float4(x.x, 0.f, x.y, 0.f);
+__device__ __forceinline__ float4 tile_entry(float2 v) { return make_float4(v.x, 0.f, v.y, 0.f); }
+template <class F2> __device__ __forceinline__ F2 zero2() {
+    F2 z;
+    z.x = 0;
+    z.y = 0;
+    return z;
+}
+// rows lo + y, lo + y + kTG, ... of one banded field into its tile
+template <class F2> __device__ __forceinline__ void tile_load(const Geo& g, const TBlk& t, const F2* f, DfTile& tl) {
+    for (int r = t.lo + (int)threadIdx.y; r < t.hi; r += kTG)
+        tl[r - t.lo][threadIdx.x] = tile_entry(t.on ? f[sidx(g, r, t.im, t.k)] : zero2<F2>());
+}
+// The same for two fields, every load of the thread issued before the first
+// split: the two-tile kernels (curl and its transpose) measured faster so
+// (26.9 against 28.7 ms per gradient), the one-tile kernels did not.
+constexpr int kTI = (kTR + kTG - 1) / kTG;  // rows per thread in a tile load
+template <class F2>
+__device__ __forceinline__ void tile_load2(const Geo& g, const TBlk& t, const F2* f0, DfTile& t0, const F2* f1,
+                                           DfTile& t1) {
+    F2 raw[2][kTI];
+#pragma unroll
+    for (int i = 0; i < kTI; ++i) {
+        const int r = t.lo + (int)threadIdx.y + i * kTG;
+        const bool in = t.on && r < t.hi;
+        raw[0][i] = in ? f0[sidx(g, r, t.im, t.k)] : zero2<F2>();
+        raw[1][i] = in ? f1[sidx(g, r, t.im, t.k)] : zero2<F2>();
+    }
+#pragma unroll
+    for (int i = 0; i < kTI; ++i) {
+        const int r = t.lo + (int)threadIdx.y + i * kTG;
+        if (r < t.hi) {
+            t0[r - t.lo][threadIdx.x] = tile_entry(raw[0][i]);
+            t1[r - t.lo][threadIdx.x] = tile_entry(raw[1][i]);
         }
-        tl[r - t.lo][threadIdx.x] = v;
     }
 }
 __device__ __forceinline__ dfc df_load(const float2* p) {
@@ -373,7 +394,9 @@ __device__ __forceinline__ dacc2 band_col_t(const Geo& g, const float2* B0, cons
 __device__ __forceinline__ double2 df_out(const dacc2& a) { return make_double2(df_result(a.re), df_result(a.im)); }
 // the accumulated value rounded once to FP32 (s + c is the rounding of the pair)
 __device__ __forceinline__ void df_put(double2* p, const dacc2& a) { *p = df_out(a); }
-__device__ __forceinline__ void df_put(float2* p, const dacc2& a) { *p = make_float2(a.re.s + a.re.c, a.im.s + a.im.c); }
+__device__ __forceinline__ void df_put(float2* p, const dacc2& a) {
+    *p = make_float2(a.re.s + a.re.c, a.im.s + a.im.c);
+}
 
 // the pair rounded once to FP32
 __device__ __forceinline__ float2 df_f32(const dfc& x) { return make_float2(x.re.h + x.re.l, x.im.h + x.im.l); }
@@ -387,8 +410,7 @@ __global__ void __launch_bounds__(kTK* kTG) k_curl_df(Geo g, const double2* __re
     u += t.off;
     w += t.off;
     const double2 *ur = u, *ut = u + t.S, *uz = u + 2 * t.S;
-    tile_load(g, t, uz, tz);
-    tile_load(g, t, ut, tt);
+    tile_load2(g, t, uz, tz, ut, tt);
     __syncthreads();
     if (!t.on) return;
     const dfl kz = dff(__ldg(g.kztf + t.k));
@@ -431,8 +453,7 @@ __global__ void __launch_bounds__(kTK* kTG) k_curlT_acc_df(Geo g, const WB2* __r
     wb += t.off;
     ub += t.off;
     const WB2 *wr = wb, *wt = wb + t.S, *wz = wb + 2 * t.S;
-    tile_load(g, t, wz, tz);
-    tile_load(g, t, wt, tt);
+    tile_load2(g, t, wz, tz, wt, tt);
     __syncthreads();
     if (!t.on) return;
     const dfl kz = dff(__ldg(g.kztf + t.k));

@@ -462,7 +462,7 @@ __device__ __forceinline__ void rdft(T2 (&v)[L]) {
 // so that one memory latency is exposed per pass instead of one per task.
 constexpr int kT2 = 128;
 template <class T2, int KB, int N1, int N2>
-__global__ void __launch_bounds__(kT2) k_synth2(Geo g, FieldPtrs f, T2* __restrict__ Y, const T2* __restrict__ twg) {
+__global__ void __launch_bounds__(kT2, 8) k_synth2(Geo g, FieldPtrs f, T2* __restrict__ Y, const T2* __restrict__ twg) {
     grid_dep_sync();
     constexpr int N = N1 * N2, IT1 = KB * N2 / kT2, IT2 = KB * N1 / kT2;
     static_assert(KB * N2 % kT2 == 0 && KB * N1 % kT2 == 0, "whole tasks per thread");
