@@ -268,6 +268,17 @@ enum { PNOP_ADJOINT_DISCRETE = 0, PNOP_ADJOINT_CONTINUOUS = 1 };
 int pnop_optimise_ex(pnop_ctx* ctx, void* u0, double E0, double horizon, int max_iter, double tol, int adjoint,
                      double* gain_history, pnop_opt_stats* stats);
 
+/* First trial step of every line search of pnop_optimise and
+ * pnop_optimise_ex, as a fraction of alpha_max: 0 < alpha_frac <= 1, with 1
+ * (the default) the paper's choice.  At alpha = alpha_max the discriminant of
+ * the scaling lambda (Eq. 2.14) is zero, and its square root amplifies the
+ * rounding of the update, so two implementations agree on the iterates only
+ * to about the square root of their gradients' agreement; a fraction below 1
+ * keeps the update well conditioned, which lets a caller compare iterates at
+ * full precision.  PNOP_ERR_INVALID_ARG for a null context or a fraction
+ * outside (0, 1]. */
+int pnop_set_optimiser_first_step(pnop_ctx* ctx, double alpha_frac);
+
 /* Operators of the step, applied to device fields (for testing and for
  * users who compose their own schemes; layout as above, all FP64 in/out):
  *   PNOP_OP_CURL       out = curl a                              (Eq. 2.5)

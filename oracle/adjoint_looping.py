@@ -106,11 +106,14 @@ def project_admissible(o, g: np.ndarray) -> np.ndarray:
 
 
 def optimise(o, u0: np.ndarray, t0: float, nsteps: int, E0: float, max_iter: int, tol: float = 1e-8,
-             max_halvings: int = 60, continuous: bool = False):
+             max_halvings: int = 60, continuous: bool = False, alpha_frac: float = 1.0):
     """Adjoint looping from u0 (rescaled to E0).  Returns (u, history, info):
     history[s] is G after s accepted updates; info counts gradients (forward +
     adjoint sweeps) and forward-only gain evaluations of the line search.  With
-    continuous, the gradients come from the continuous adjoint equations."""
+    continuous, the gradients come from the continuous adjoint equations.
+    alpha_frac scales the first trial step of each line search: 1 is the
+    paper's alpha_max; a smaller fraction keeps the discriminant of Eq. 2.14
+    away from zero (a conditioning choice for comparisons, not the method)."""
     grad = o.gradient_continuous if continuous else o.gradient
     u = o.scale_to(project_admissible(o, u0), E0)
     ET, g = grad(u, t0, nsteps)
@@ -126,6 +129,7 @@ def optimise(o, u0: np.ndarray, t0: float, nsteps: int, E0: float, max_iter: int
         if not math.isfinite(a):
             info["converged"] = True
             break
+        a *= alpha_frac
         accepted = None
         for _h in range(max_halvings):
             lam = lambda_pm(a, E0, E0d, C0)[1]

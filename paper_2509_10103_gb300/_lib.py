@@ -27,7 +27,7 @@ EXPORTS = (
     "pnop_create", "pnop_set_base_flow", "pnop_dims", "pnop_grid_points", "pnop_step_forward", "pnop_step_adjoint",
     "pnop_gradient", "pnop_gradient_continuous", "pnop_gradient_forward", "pnop_gradient_backward",
     "pnop_gradient_host", "pnop_gradient_stats", "pnop_optimise", "pnop_optimise_ex", "pnop_set_host_tier", "pnop_host_tier_stats",
-    "pnop_two_level_counts", "pnop_mode_energy", "pnop_resolution", "pnop_energy", "pnop_inner", "pnop_apply", "pnop_set_timeout",
+    "pnop_two_level_counts", "pnop_mode_energy", "pnop_resolution", "pnop_energy", "pnop_inner", "pnop_apply", "pnop_set_timeout", "pnop_set_optimiser_first_step",
     "pnop_sync", "pnop_profile", "pnop_profile_read", "pnop_revolve_counts", "pnop_context_bytes", "pnop_device_bytes",
     "pnop_energy_noalloc", "pnop_measure_fma_peak", "pnop_last_error", "pnop_error_string", "pnop_destroy",
     "pnop_batch_create", "pnop_batch_submit", "pnop_batch_run", "pnop_batch_poll", "pnop_batch_result",
@@ -82,6 +82,7 @@ def _load():
         "pnop_inner": (c_int, [c_void_p, c_void_p, c_void_p, POINTER(c_double)]),
         "pnop_apply": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_void_p, c_double]),
         "pnop_set_timeout": (c_int, [c_void_p, c_double]),
+        "pnop_set_optimiser_first_step": (c_int, [c_void_p, c_double]),
         "pnop_sync": (c_int, [c_void_p]),
         "pnop_profile": (c_int, [c_void_p, ctypes.c_uint]),
         "pnop_profile_read": (c_int, [c_void_p, POINTER(c_double), POINTER(c_longlong), POINTER(c_double)]),
@@ -319,6 +320,10 @@ class Context:
     def pnop_apply(self, op, a, b, out, t=0.0):
         bp = c_void_p(_ptr(b)) if b is not None else c_void_p(0)
         self._check(lib.pnop_apply(self._h, op, c_void_p(_ptr(a)), bp, c_void_p(_ptr(out)), t), "apply")
+
+    def pnop_set_optimiser_first_step(self, alpha_frac):
+        """First line-search step of pnop_optimise as a fraction of alpha_max (1: the paper's)."""
+        self._check(lib.pnop_set_optimiser_first_step(self._h, alpha_frac), "set_optimiser_first_step")
 
     def pnop_set_timeout(self, seconds):
         self._check(lib.pnop_set_timeout(self._h, seconds), "set_timeout")

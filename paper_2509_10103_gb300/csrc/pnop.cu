@@ -156,6 +156,7 @@ struct pnop_ctx {
     bool pending = false;
     int st_slots = 0;
     double timeout_s = 0;  // host limit on waits for device work (0: none)
+    double opt_alpha_frac = 1.0;  // first line-search step of the optimiser, in units of alpha_max
     // recomputation beside the adjoint: a second workspace on its own streams
     // that runs the reverse sweep's forward advances while the adjoint steps
     // run on this context's stream (single-request contexts, discrete adjoint,
@@ -1278,7 +1279,7 @@ void optimise_impl(pnop_ctx* c, double2* u, double E0, double horizon, int max_i
             st->converged = 1;
             break;
         }
-        double alpha = 1.0 / std::sqrt(d);
+        double alpha = c->opt_alpha_frac / std::sqrt(d);
         bool accepted = false;
         double Gn = G, R = 0;
         for (int h = 0; h < kMaxHalvings; ++h) {
@@ -1979,6 +1980,12 @@ int pnop_apply(pnop_ctx* ctx, int op, const void* a, const void* b, void* out, d
         wait_stream(ctx, "apply");
         return PNOP_OK;
     });
+}
+
+int pnop_set_optimiser_first_step(pnop_ctx* ctx, double alpha_frac) {
+    if (!ctx || !(alpha_frac > 0.0 && alpha_frac <= 1.0)) return PNOP_ERR_INVALID_ARG;
+    ctx->opt_alpha_frac = alpha_frac;
+    return PNOP_OK;
 }
 
 int pnop_set_timeout(pnop_ctx* ctx, double seconds) {

@@ -115,6 +115,7 @@ def test_new_entry_points_reject_bad_arguments_without_a_device(L):
     assert L.lib.pnop_host_tier_stats(None, None, None, None, None) == -1
     assert L.lib.pnop_mode_energy(None, None, None) == -1
     assert L.lib.pnop_gradient_continuous(None, None, 1e-3, 1.0, None, None) == -1
+    assert L.lib.pnop_set_optimiser_first_step(None, 0.5) == -1
     nf, adv = ctypes.c_int(), ctypes.c_longlong()
     for args in ((0, 2, 4, 0.0), (10, 0, 4, 0.0), (10, 2, -1, 0.0), (10, 2, 4, -1.0), (10, 2, 4, float("nan"))):
         assert L.lib.pnop_two_level_counts(*args, ctypes.byref(nf), ctypes.byref(adv)) == -1

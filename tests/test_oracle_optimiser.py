@@ -121,6 +121,19 @@ def test_adjoint_looping_reaches_the_exact_linear_optimum(tiny, tiny_optimum):
     assert abs(hist[-1] / Gopt - 1) < 1e-6
 
 
+def test_shorter_first_step_reaches_the_same_linear_optimum(tiny, tiny_optimum):
+    """A first trial step of half alpha_max (the conditioning choice the GPU
+    parity test of the optimiser uses) changes the path, not the optimum."""
+    o, N = tiny
+    E0 = 1e-20
+    u0 = synth.random_field(o.r, o.p.M, o.p.K, o.p.Lz, seed=1)
+    u, hist, info = al.optimise(o, u0, 0.0, N, E0, max_iter=60, tol=1e-10, alpha_frac=0.5)
+    assert info["converged"]
+    assert abs(o.energy(u) / E0 - 1) < 1e-12
+    assert all(b > a for a, b in zip(hist, hist[1:]))
+    assert abs(hist[-1] / tiny_optimum - 1) < 1e-6
+
+
 def test_continuous_adjoint_looping_stays_below_the_exact_optimum(tiny, tiny_optimum):
     """With gradients from the continuous adjoint (Eq. 2.9-2.11) the loop still
     only accepts growth of the exactly evaluated G, so it climbs toward, and can

@@ -148,12 +148,12 @@ def test_batch_server_slots_follow_the_arrival_mix():
     kind gets further batches (its waiting requests take new slots instead of
     queueing), the other keeps one, and the budget bounds the total."""
     FakeBatch.made.clear()
-    reqs = [_breq(i, 1, 6) for i in range(9)] + [_breq(9, 2, 6)]
+    reqs = [_breq(i, 1, 16) for i in range(9)] + [_breq(9, 2, 16)]
     res, srv = serving.serve_stream(reqs, hbm_budget=4, max_active=3, batched=True, ticks=1,
                                     batch_factory=SlowerBatch, sizer=lambda r, slots: 1)
     assert all(x.error is None for x in res), [x.error for x in res]
     assert [x.gain for x in res] == [float(i) for i in range(10)]
-    assert srv.peak_batches_per_kind == 3          # 9 requests / 3 slots (each holds its slot ~0.3 s)
+    assert srv.peak_batches_per_kind == 3          # 9 requests / 3 slots (each holds its slot ~0.8 s)
     assert srv.peak_bytes <= 4 and len(FakeBatch.made) == 4
     assert all(b.max_live <= 3 for b in FakeBatch.made)
 
