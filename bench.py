@@ -107,13 +107,17 @@ def class_work(cls, units, mixed):
 
 
 KERNEL_SOURCES = ("kernels.cu", "transforms.cu", "kernels.hpp", "dev_common.cuh", "dev_df.cuh")
+# the translation unit and headers that define a class's kernels: the banded
+# solves live in kernels.cu, which the transforms' unit cannot change
+CLASS_SOURCES = {"radial_solve": ("kernels.cu", "kernels.hpp", "dev_common.cuh", "dev_df.cuh")}
 
 
-def kernel_digest():
-    """Digest of the kernel sources, recorded beside every committed ncu traffic figure."""
+def kernel_digest(cls=None):
+    """Digest of the sources of a kernel class (all kernel sources when the
+    class is not listed), recorded beside every committed ncu traffic figure."""
     import hashlib
     h = hashlib.sha256()
-    for f in KERNEL_SOURCES:
+    for f in CLASS_SOURCES.get(cls, KERNEL_SOURCES):
         with open(os.path.join(ROOT, "paper_2509_10103_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -121,15 +125,15 @@ def kernel_digest():
 
 def traffic_table():
     """DRAM bytes per launch from the committed ncu capture, per (class,
-    precision), kept only when the capture was taken of the kernel sources as
-    they are now (its digest matches): a figure of an older kernel is null."""
+    precision), kept only when the capture was taken of the class's kernel
+    sources as they are now (its digest matches): a figure of an older kernel
+    is null."""
     out = {}
     p = os.path.join(ROOT, "profiles", "dram_traffic_per_launch.txt")
     if os.path.exists(p):
-        dig = kernel_digest()
         for line in open(p):
             parts = line.split()
-            if len(parts) == 5 and parts[0] == "traffic" and parts[4] == dig:
+            if len(parts) == 5 and parts[0] == "traffic" and parts[4] == kernel_digest(parts[1]):
                 out[(parts[1], parts[2])] = float(parts[3])
     return out
 

@@ -457,12 +457,14 @@ __device__ __forceinline__ void rdft(T2 (&v)[L]) {
 // theta synthesis, two-pass: block (k tile of KB, j, field) of kT2 threads,
 // KB * N1 or KB * N2 tasks per pass.  Slot s of the output rows holds theta
 // index (s / N2) + N1 (s % N2).  The task counts are multiples of the block
-// size, so each thread runs a fixed number of tasks; where their inputs fit
-// in registers (at most 24 values) it loads all of them before the first DFT,
-// so that one memory latency is exposed per pass instead of one per task.
+// size, so each thread runs a fixed number of tasks; in FP32, where their
+// inputs fit in registers (at most 24 values), it loads all of them before the
+// first DFT, so that one memory latency is exposed per pass instead of one per
+// task, and runs at 64 registers (eight blocks per SM).
 constexpr int kT2 = 128;
 template <class T2, int KB, int N1, int N2>
-__global__ void __launch_bounds__(kT2, 8) k_synth2(Geo g, FieldPtrs f, T2* __restrict__ Y, const T2* __restrict__ twg) {
+__global__ void __launch_bounds__(kT2, sizeof(T2) == 8 ? 8 : 1)
+    k_synth2(Geo g, FieldPtrs f, T2* __restrict__ Y, const T2* __restrict__ twg) {
     grid_dep_sync();
     constexpr int N = N1 * N2, IT1 = KB * N2 / kT2, IT2 = KB * N1 / kT2;
     static_assert(KB * N2 % kT2 == 0 && KB * N1 % kT2 == 0, "whole tasks per thread");
@@ -491,7 +493,7 @@ __global__ void __launch_bounds__(kT2, 8) k_synth2(Geo g, FieldPtrs f, T2* __res
 #pragma unroll
         for (int k1 = 0; k1 < N1; ++k1) buf[(n2 + N2 * k1) * KB + kk] = twr<T2, +1>(v[k1], tw, n2 * k1);
     };
-    if constexpr (IT1 * N1 <= 24) {
+    if constexpr (sizeof(T2) == 8 && IT1 * N1 <= 24) {  // FP32 values only: FP64 ones would spill
         T2 v[IT1][N1];
 #pragma unroll
         for (int it = 0; it < IT1; ++it) load(it, v[it]);
@@ -509,7 +511,8 @@ __global__ void __launch_bounds__(kT2, 8) k_synth2(Geo g, FieldPtrs f, T2* __res
     }
     __syncthreads();
     T2* dst = Y + ((size_t)(fi * g.nr + j) * N) * g.nk;
-#pragma unroll
+    constexpr int kUnroll2 = sizeof(T2) == 8 ? IT2 : 1;  // FP64 tasks one at a time (registers)
+#pragma unroll kUnroll2
     for (int it = 0; it < IT2; ++it) {
         const int t = threadIdx.x + it * kT2, kk = t % KB, k1 = t / KB, k = k0 + kk;
         T2 v[N2];
@@ -529,7 +532,7 @@ __global__ void __launch_bounds__(kT2, 8) k_synth2(Geo g, FieldPtrs f, T2* __res
 // fit in registers, and each task of the second pass loads the values to add
 // (the base-flow terms) before its DFT.
 template <class T2, int KB, int N1, int N2>
-__global__ void __launch_bounds__(kT2, 6) k_anal2(Geo g, FieldPtrs f, const T2* __restrict__ Z,
+__global__ void __launch_bounds__(kT2, sizeof(T2) == 8 ? 6 : 1) k_anal2(Geo g, FieldPtrs f, const T2* __restrict__ Z,
                                                const T2* __restrict__ twg) {
     grid_dep_sync();
     constexpr int N = N1 * N2, IT1 = KB * N1 / kT2, IT2 = KB * N2 / kT2;
@@ -554,7 +557,7 @@ __global__ void __launch_bounds__(kT2, 6) k_anal2(Geo g, FieldPtrs f, const T2* 
 #pragma unroll
         for (int m2 = 0; m2 < N2; ++m2) buf[(N2 * k1 + m2) * KB + kk] = twr<T2, -1>(v[m2], tw, k1 * m2);
     };
-    if constexpr (IT1 * N2 <= 24) {
+    if constexpr (sizeof(T2) == 8 && IT1 * N2 <= 24) {  // FP32 values only: FP64 ones would spill
         T2 v[IT1][N2];
 #pragma unroll
         for (int it = 0; it < IT1; ++it) load(it, v[it]);
@@ -578,7 +581,7 @@ __global__ void __launch_bounds__(kT2, 6) k_anal2(Geo g, FieldPtrs f, const T2* 
 #pragma unroll 1
     for (int it = 0; it < IT2; ++it) {
         const int t = threadIdx.x + it * kT2, kk = t % KB, m2 = t / KB, k = k0 + kk;
-        constexpr bool kEarly = N1 <= 8;  // the added values of larger tasks do not fit in registers
+        constexpr bool kEarly = sizeof(T2) == 8 && N1 <= 8;  // larger or FP64 tasks: no room in registers
         double2 ad[kEarly ? N1 : 1];
         if constexpr (kEarly) {
 #pragma unroll
