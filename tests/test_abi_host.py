@@ -186,3 +186,29 @@ def test_fma_probe_rejects_bad_arguments_without_a_device(L):
     for prec, secs in ((0, 0.0), (0, -1.0), (0, 11.0), (7, 0.1)):
         assert L.lib.pnop_measure_fma_peak(prec, secs, None, ctypes.byref(t)) == -1
     assert L.lib.pnop_measure_fma_peak(0, 0.1, None, None) == -1
+
+
+def test_a_plain_c_program_uses_the_abi(L, tmp_path):
+    """The public header compiles as C99 with warnings as errors, and a C
+    program linked against the library calls host-only entry points."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    src = tmp_path / "use_pnop.c"
+    src.write_text(
+        "#include <stdio.h>\n#include \"pnop.h\"\n"
+        "int main(void) {\n"
+        "    long long adv = 0, st = 0;\n"
+        "    if (pnop_revolve_counts(100, 4, &adv, &st) != PNOP_OK) return 1;\n"
+        "    if (pnop_set_optimiser_first_step((pnop_ctx*)0, 0.5) != PNOP_ERR_INVALID_ARG) return 2;\n"
+        "    printf(\"%lld %lld\\n\", adv, st);\n"
+        "    return 0;\n"
+        "}\n")
+    libdir = os.path.dirname(os.path.abspath(L.lib._name))
+    exe = tmp_path / "use_pnop"
+    subprocess.run([cc, "-std=c99", "-Wall", "-Wextra", "-Werror", "-I", os.path.join(ROOT, "include"), str(src),
+                    "-L", libdir, "-lpnop", "-Wl,-rpath," + libdir, "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split()
+    assert int(out[0]) == po.revolve_advances(100, 4)
